@@ -1,0 +1,218 @@
+"""Python access to the plain FP64 CPU oracle (``dg_oracle.c``).
+
+TEST INFRASTRUCTURE: only ``tests/``, ``__graft_entry__.smoke()`` and the CPU
+baseline / reference arm of ``bench.py`` may import this package. The CUDA
+library and its Python binding never do.
+
+``build()`` compiles ``dg_oracle.c`` with gcc (OpenMP, ``-ffp-contract=off``)
+into ``oracle/_build/``; the functions below marshal numpy arrays into it.
+Parity status of each function is recorded in its pins under ``tests/``.
+"""
+from __future__ import annotations
+
+import contextlib
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dg_oracle.c")
+_OUT = os.path.join(_HERE, "_build", "libdg_oracle.so")
+_LOCK = threading.Lock()
+_LIB = None
+
+
+class Grid(C.Structure):
+    _fields_ = [("lat0_deg", C.c_double), ("lon0_deg", C.c_double), ("dlat_m", C.c_double),
+                ("dlon_m", C.c_double), ("nlat", C.c_int32), ("nlon", C.c_int32)]
+
+    @classmethod
+    def from_dict(cls, d):
+        return cls(float(d["lat0_deg"]), float(d["lon0_deg"]), float(d["dlat_m"]),
+                   float(d["dlon_m"]), int(d["nlat"]), int(d["nlon"]))
+
+
+def build(force: bool = False, src: str = _SRC, out: str = _OUT) -> str:
+    """Compile an oracle source (default: dg_oracle.c) if missing or stale."""
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
+        tmp = out + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+               "-fPIC", "-shared", "-o", tmp, src, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, out)
+    return out
+
+
+def _bind(path):
+    L = C.CDLL(path)
+    dp = C.POINTER(C.c_double)
+    L.dgo_geodetic_to_ecef.argtypes = [C.c_double, C.c_double, C.c_double, dp]
+    L.dgo_grid_step_rad.argtypes = [C.POINTER(Grid), dp, dp]
+    L.dgo_grid_node.argtypes = [C.POINTER(Grid), C.c_int64, C.c_int64, dp, dp]
+    L.dgo_grid_ecef.argtypes = [C.POINTER(Grid), dp]
+    L.dgo_geometry.argtypes = [dp, dp, C.c_double, C.c_double, dp]
+    L.dgo_lagrange4.argtypes = [C.c_double, dp]
+    L.dgo_correlate.argtypes = [dp, dp, C.c_int64, C.c_double, C.c_double, C.c_int, dp]
+    L.dgo_cost_points.argtypes = [C.POINTER(Grid), dp, C.c_int32, C.c_double, C.c_double,
+                                  dp, dp, C.c_int64, C.c_int, C.c_int,
+                                  C.POINTER(C.c_int64), C.c_int64, dp, dp, dp, C.c_int]
+    L.dgo_cost_points.restype = C.c_int
+    L.dgo_argmax.argtypes = [dp, C.c_int64]
+    L.dgo_argmax.restype = C.c_int64
+    return L
+
+
+def lib():
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            _LIB = _bind(build())
+    return _LIB
+
+
+@contextlib.contextmanager
+def using(path):
+    """Route this module's functions to another build of an oracle source.
+
+    The mutation tests plant one mistake in a copy of dg_oracle.c, build it,
+    and run the pins through this to check that some pin catches it."""
+    global _LIB
+    lib()
+    alt = _bind(path)
+    with _LOCK:
+        prev, _LIB = _LIB, alt
+    try:
+        yield
+    finally:
+        with _LOCK:
+            _LIB = prev
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64c(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def iq_to_f64(y):
+    """(…, N, 2) interleaved I/Q of any storage type -> float64, exactly."""
+    return _f64c(np.asarray(y).astype(np.float64))
+
+
+def geodetic_to_ecef(lat_rad, lon_rad, h=0.0):
+    out = np.empty(3)
+    lib().dgo_geodetic_to_ecef(float(lat_rad), float(lon_rad), float(h), _dp(out))
+    return out
+
+
+def grid_step_rad(grid):
+    a, b = C.c_double(), C.c_double()
+    lib().dgo_grid_step_rad(C.byref(Grid.from_dict(grid)), C.byref(a), C.byref(b))
+    return a.value, b.value
+
+
+def grid_node(grid, i, j):
+    a, b = C.c_double(), C.c_double()
+    lib().dgo_grid_node(C.byref(Grid.from_dict(grid)), int(i), int(j), C.byref(a), C.byref(b))
+    return a.value, b.value
+
+
+def grid_ecef(grid):
+    g = Grid.from_dict(grid)
+    out = np.empty((g.nlat * g.nlon, 3))
+    lib().dgo_grid_ecef(C.byref(g), _dp(out))
+    return out
+
+
+def geometry(pc, eph, fs, fc):
+    """-> (dtau s, dfreq Hz, D samples, nu cycles/sample)."""
+    out = np.empty(4)
+    lib().dgo_geometry(_dp(_f64c(pc)), _dp(_f64c(eph)), float(fs), float(fc), _dp(out))
+    return tuple(out)
+
+
+def lagrange4(mu):
+    out = np.empty(4)
+    lib().dgo_lagrange4(float(mu), _dp(out))
+    return out
+
+
+def correlate(y1, y2, D, nu, delay_mode=0):
+    """Complex C of Eq. 11 for one (candidate, snapshot); y1/y2 complex or (N, 2)."""
+    y1 = np.asarray(y1)
+    y2 = np.asarray(y2)
+    if np.iscomplexobj(y1):
+        y1 = np.stack([y1.real, y1.imag], -1)
+    if np.iscomplexobj(y2):
+        y2 = np.stack([y2.real, y2.imag], -1)
+    a, b = iq_to_f64(y1), iq_to_f64(y2)
+    if a.shape != b.shape or a.ndim != 2 or a.shape[1] != 2:
+        raise ValueError("y1, y2 must both be (N, 2)")
+    out = np.empty(2)
+    lib().dgo_correlate(_dp(a), _dp(b), a.shape[0], float(D), float(nu), int(delay_mode), _dp(out))
+    return complex(out[0], out[1])
+
+
+def cost_points(grid, ephem, fs, fc, y1, y2, idx, delay_mode=0, acc_mode=0, nthreads=0,
+                want_corr=False, want_geom=False):
+    """Cost at selected candidates (linear indices). y1/y2 are (K, N, 2).
+
+    Returns cost (npts,) and, if asked, C_k (npts, K) complex and the
+    geometry (npts, K, 4)."""
+    eph = _f64c(ephem)
+    a, b = iq_to_f64(y1), iq_to_f64(y2)
+    K, N = a.shape[0], a.shape[1]
+    if eph.shape != (K, 12) or b.shape != a.shape:
+        raise ValueError("shape mismatch")
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    cost = np.empty(idx.size)
+    corr = np.empty((idx.size, K, 2)) if want_corr else None
+    geom = np.empty((idx.size, K, 4)) if want_geom else None
+    rc = lib().dgo_cost_points(C.byref(Grid.from_dict(grid)), _dp(eph), K, float(fs), float(fc),
+                               _dp(a), _dp(b), N, int(delay_mode), int(acc_mode),
+                               idx.ctypes.data_as(C.POINTER(C.c_int64)), idx.size, _dp(cost),
+                               _dp(corr) if corr is not None else None,
+                               _dp(geom) if geom is not None else None, int(nthreads))
+    if rc != 0:
+        raise ValueError("dgo_cost_points rejected its arguments")
+    out = [cost]
+    if want_corr:
+        out.append(corr[..., 0] + 1j * corr[..., 1])
+    if want_geom:
+        out.append(geom)
+    return out[0] if len(out) == 1 else tuple(out)
+
+
+def cost_surface(grid, ephem, fs, fc, y1, y2, delay_mode=0, acc_mode=0, nthreads=0, rows=None):
+    """Whole cost surface (nlat, nlon), or rows [r0, r1) of it."""
+    nlat, nlon = int(grid["nlat"]), int(grid["nlon"])
+    r0, r1 = (0, nlat) if rows is None else rows
+    idx = np.arange(r0 * nlon, r1 * nlon, dtype=np.int64)
+    c = cost_points(grid, ephem, fs, fc, y1, y2, idx, delay_mode, acc_mode, nthreads)
+    return c.reshape(r1 - r0, nlon)
+
+
+def argmax(cost):
+    c = _f64c(np.ravel(cost))
+    return int(lib().dgo_argmax(_dp(c), c.size))
+
+
+def refine_grid(grid, index, spacing_m, window_m):
+    """Local grid for dense re-evaluation around a coarse cell: centred on the
+    cell's latitude/longitude, spacing_m apart, half-width window_m."""
+    nlon = int(grid["nlon"])
+    lat, lon = grid_node(grid, index // nlon, index % nlon)
+    half = int(round(window_m / spacing_m))
+    return dict(lat0_deg=np.degrees(lat), lon0_deg=np.degrees(lon), dlat_m=float(spacing_m),
+                dlon_m=float(spacing_m), nlat=2 * half + 1, nlon=2 * half + 1)
+
+
+def scene_args(scene):
+    """(grid, ephem, fs, fc, y1, y2) of a sim.Scene."""
+    return scene.grid, scene.ephem, scene.fs_hz, scene.fc_hz, scene.y1, scene.y2
