@@ -1,0 +1,367 @@
+"""Throughput of direct geolocation on GB300: candidate*sample correlations/s.
+
+One step = one pass of the whole hot path over the workload: the cost surface
+(geometry, delay/Doppler alignment, correlation, accumulation over all K
+snapshots; Sec. III, Eq. 11, Algorithm 1) and the argmax with a dense local
+refinement. The default workload is the mid-size one: a 1001 x 1001 grid at
+100 m, K = 20 snapshots of N = 65536 complex int16 samples at 12.5 MHz from a
+10 MHz / 10 us chirp jammer at -15 dB SNR.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dg|reference]
+
+Rank 0 prints one JSON line. --impl reference times the CPU oracle on a
+bounded sample of the same workload (same metric and unit).
+Under torchrun each rank processes its own block of 1001 grid rows (weak
+scaling: the grid grows with the number of GPUs).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FLOPS_PER_CAND_SAMPLE = 14          # conj product 6 + derotation 6 + accumulation 2
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+METRIC = "candidate·sample correlations/s"
+UNIT = "cand·samples/s"
+REFINE_SPACING_M, REFINE_WINDOW_M = 10.0, 200.0
+
+
+def workload(name, rank=0, world=1, grid=None):
+    import sim
+
+    if name == "mid":
+        s = sim.mid()
+        desc = ("mid: 1001x1001 grid at 100 m, K=20 x N=65536 complex int16, chirp 10 MHz / 10 us, "
+                "fs 12.5 MHz, fc 1575.42 MHz, SNR -15 dB, 2 LEO receivers 50 km apart at 550 km")
+    elif name == "tiny":
+        s = sim.tiny()
+        desc = "tiny: 101x101 grid at 1 km, K=1 x N=4096 complex64, 2 MHz noise, fs 5 MHz, SNR -5 dB"
+    elif name == "large":
+        s = sim.large()
+        desc = ("large: 4001x4001 grid at 400 m, K=50 x N=131072 complex int8, 18 MHz noise, "
+                "fs 20 MHz, SNR -20 dB")
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    if grid:
+        # a smaller (or larger) square grid at the same spacing, same centre
+        s.grid = dict(s.grid, nlat=grid, nlon=grid)
+        desc += f" [grid overridden to {grid}x{grid}]"
+    if world > 1:
+        # weak scaling: a grid world times taller, this rank's block of rows
+        s.grid = dict(s.grid, nlat=s.grid["nlat"] * world)
+    return s, desc
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ oracle (CPU)
+def oracle_rate(scene, target_s, seed=0, max_pts=None):
+    """Time the FP64 oracle on a bounded sample of the workload's candidates.
+    Returns (cand*samples/s, seconds, points, cores)."""
+    import oracle
+
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    KN = scene.k_steps * scene.n_samples
+    y1, y2 = oracle.iq_to_f64(scene.y1), oracle.iq_to_f64(scene.y2)
+    args = (scene.grid, scene.ephem, scene.fs_hz, scene.fc_hz, y1, y2)
+    cores = host_cores()
+    # calibrate on a few points, then size the sample for ~target_s
+    cal = rng.integers(0, scene.G, max(4, cores))
+    t0 = time.perf_counter()
+    oracle.cost_points(*args, idx=cal)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    rate = cal.size * KN / dt
+    npts = int(max(cores, min(target_s * rate / KN, max_pts or 1e12)))
+    idx = rng.integers(0, scene.G, npts)
+    t0 = time.perf_counter()
+    oracle.cost_points(*args, idx=idx)
+    dt = time.perf_counter() - t0
+    return npts * KN / dt, dt, npts, cores
+
+
+def run_reference(a, rank, world):
+    """The reference arm: the CPU oracle on the same metric and workload."""
+    if rank != 0:
+        return
+    scene, desc = workload(a.workload, grid=a.grid)
+    KN = scene.k_steps * scene.n_samples
+    rates = []
+    npts = None
+    for it in range(a.warmup + a.steps):
+        r, dt, n, cores = oracle_rate(scene, a.reference_step_s, seed=it, max_pts=npts)
+        npts = npts or n
+        if it >= a.warmup:
+            rates.append((r, dt))
+    total_units = sum(r * dt for r, dt in rates)
+    total_s = sum(dt for _, dt in rates)
+    value = total_units / total_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total_s / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": desc, "G": scene.G, "K": scene.k_steps, "N": scene.n_samples},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{npts} random grid nodes x all {scene.k_steps} snapshots x {scene.n_samples} samples per step (FP64, OpenMP over nodes), {cpu_model()}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- GPU arm
+def run_dg(a, rank, world, local_rank):
+    import torch
+
+    import paper_2508_06672_gb300 as P
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    scene, desc = workload(a.workload, rank, world, a.grid)
+    nrows = scene.grid["nlat"] // world
+    row0 = rank * nrows
+    G_rank = nrows * scene.grid["nlon"]
+    KN = scene.k_steps * scene.n_samples
+    stream = torch.cuda.Stream(dev)
+    g = P.Geolocator(scene.grid, scene.ephem, scene.fs_hz, scene.fc_hz, algo=a.algo, row0=row0,
+                     nrows=nrows, timing=True, stream=stream, device=local_rank)
+    y1d = torch.from_numpy(scene.y1).to(dev)
+    y2d = torch.from_numpy(scene.y2).to(dev)
+    y1h = torch.from_numpy(scene.y1).pin_memory()
+    y2h = torch.from_numpy(scene.y2).pin_memory()
+    with torch.cuda.stream(stream):
+        g.load_captures(scene.fmt, y1d, y2d)
+        cost = torch.empty((nrows, scene.grid["nlon"]), dtype=torch.float32, device=dev)
+        flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step():
+        g.cost_surface(cost)
+        return g.argmax_refine(cost, REFINE_SPACING_M, REFINE_WINDOW_M)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(a.warmup):
+            step()
+    barrier()
+    g.reset_counters()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    fixes = []
+    gpu_id = _smi_id(local_rank)
+    with ClockSampler(gpu_id) as clk:
+        barrier()
+        t_wall = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for i in range(a.steps):
+                flush.zero_()                     # L2 flush, outside the timed events
+                ev[i][0].record(stream)
+                fixes.append(step())
+                ev[i][1].record(stream)
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    corr_ms, corr_launches = g.kernel_time(P.DG_K_CORR)
+    launches = g.launch_count()
+    dev_s = sum(step_ms) / 1e3
+
+    # end to end through the public API: pinned host captures in, fix out
+    g.reset_counters()
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            g.load_captures(scene.fmt, y1h, y2h)
+            step()
+    barrier()
+    e2e_ms = []
+    for i in range(a.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            g.load_captures(scene.fmt, y1h, y2h)
+            step()                                # synchronises and copies the fix back
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    h2d = int(scene.y1.nbytes + scene.y2.nbytes)
+    d2h = 2 * 32 + 2 * 4                           # two argmax records, two error words
+
+    worst = torch.tensor([dev_s, corr_ms / 1e3, sum(e2e_ms) / 1e3], dtype=torch.float64)
+    if dist:
+        worst = worst.to(dev)
+        dist.all_reduce(worst, op=dist.ReduceOp.MAX)
+        worst = worst.cpu()
+    dev_s, corr_s, e2e_s = (float(x) for x in worst)
+    units = world * G_rank * KN * a.steps
+
+    if rank == 0:
+        fix = fixes[-1]
+        centre = ((scene.grid["nlat"] // world) // 2, scene.grid["nlon"] // 2)
+        achieved = FLOPS_PER_CAND_SAMPLE * G_rank * KN * a.steps / corr_s / 1e12
+        peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        clocks = clk.summary()
+        line = {
+            "metric": METRIC, "value": units / dev_s, "unit": UNIT, "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * dev_s / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": desc, "G": G_rank * world, "K": scene.k_steps, "N": scene.n_samples,
+                       "fmt": scene.fmt, "delay": "integer", "algo": a.algo, "acc": "power",
+                       "refine": f"{REFINE_SPACING_M:g} m spacing, +-{REFINE_WINDOW_M:g} m",
+                       "l2": "flushed between timed steps (256 MB write outside the events)",
+                       "parallelism": f"grid rows sharded over {world} GPU(s)", "seed": scene.meta["seed"]},
+            "e2e": {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_corr_direct (FP32, integer lag, ci16)",
+                         "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
+                         "achieved_basis": f"{FLOPS_PER_CAND_SAMPLE} flop per candidate*sample x G*K*N per launch / CUDA-event time of the launch",
+                         "launches": corr_launches, "ms_per_launch": 1e3 * corr_s / max(1, corr_launches)},
+            "clocks": clocks,
+            "fix": {"i": fix["i"], "j": fix["j"], "emitter_cell": list(centre),
+                    "offset_cells": [fix["i"] - centre[0], fix["j"] - centre[1]],
+                    "refined_latlon_deg": [fix["refined_lat_deg"], fix["refined_lon_deg"]]},
+            "wall_s": t_wall,
+        }
+        if world == 1 and not a.no_cpu_baseline:
+            r, dt, npts, cores = oracle_rate(scene, a.cpu_baseline_s)
+            line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                    "sample": f"{npts} random grid nodes x all {scene.k_steps} snapshots x {scene.n_samples} samples ({dt:.1f} s, FP64, OpenMP over nodes), {cpu_model()}"}
+        print(json.dumps(line), flush=True)
+    g.close()
+
+
+def _smi_id(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    return local_rank
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["dg", "reference"], default="dg")
+    ap.add_argument("--workload", choices=["mid", "tiny", "large"], default="mid")
+    ap.add_argument("--algo", default="direct")
+    ap.add_argument("--grid", type=int, default=0, help="override the grid to GRID x GRID nodes")
+    ap.add_argument("--cpu-baseline-s", type=float, default=15.0)
+    ap.add_argument("--reference-step-s", type=float, default=6.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    a = ap.parse_args()
+    if a.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    run_dg(a, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

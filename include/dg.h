@@ -1,0 +1,202 @@
+/*
+ * dg.h -- C ABI of libdg, the GB300 (sm_103a) direct-geolocation library.
+ *
+ * Direct geolocation (Sec. III, Algorithm 1): for every candidate point of a
+ * latitude/longitude grid on the Earth's surface and every snapshot, the
+ * expected TDOA and FDOA follow from the two receivers' ECEF states (Eq. 3-10);
+ * receiver 2's samples are aligned by that delay and receiver 1's derotated by
+ * that FDOA, and the position-domain correlation of Eq. 11 is formed. The
+ * per-snapshot grids are summed non-coherently and the maximum is the emitter
+ * estimate.
+ *
+ * Conventions for every call:
+ *   - Every function returns dg_status and never aborts; no C++ exception
+ *     crosses this boundary. On error, outputs are left unchanged, the context
+ *     stays usable and dg_last_error() describes the failure.
+ *   - Device work is enqueued on the CUDA stream given to dg_create, in call
+ *     order. Calls on one context must not run concurrently from several host
+ *     threads.
+ *   - "device pointer" means memory of the context's device (cudaMalloc,
+ *     cudaMallocAsync or a torch CUDA tensor); "host pointer" means ordinary
+ *     or pinned host memory.
+ *   - Errors found by a kernel (see DG_EUNSUPPORTED) are latched and reported
+ *     by the next dg_sync or dg_argmax_refine call.
+ *   - Grids are row-major [lat][lon]: the linear index of node (i, j) is
+ *     i * nlon + j, i counting latitude rows from south to north, j counting
+ *     longitude columns from west to east.
+ */
+#ifndef DG_H
+#define DG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DG_ABI_VERSION 1
+
+typedef enum {
+    DG_OK = 0,
+    DG_EINVAL = 1,        /* a null pointer, a size out of range, a bad enum    */
+    DG_ENOMEM = 2,        /* device allocation failed                           */
+    DG_ECUDA = 3,         /* a CUDA runtime call failed                         */
+    DG_ESTATE = 4,        /* call out of order (e.g. a snapshot not loaded yet) */
+    DG_ETIMEOUT = 5,      /* a bounded device wait ran out                      */
+    DG_EUNSUPPORTED = 6   /* valid but outside what the kernels handle          */
+} dg_status;
+
+/* Raw IQ storage, interleaved I,Q, little-endian: float32 pairs, int16 pairs,
+ * int8 pairs. Integer samples are converted exactly to float, scale 1. */
+enum { DG_IQ_C64 = 0, DG_IQ_CI16 = 1, DG_IQ_CI8 = 2 };
+
+/* Delay alignment. INTEGER is Eq. 9: lag L = round(dtau * fs), half away from
+ * zero (the printed "/ f_s" in Eq. 9 is read as "* f_s"). LAGRANGE4 aligns at
+ * the fractional delay with 4-tap cubic Lagrange interpolation at taps
+ * floor(D)-1 .. floor(D)+2 (not in the paper). Samples outside [0, N) are 0. */
+enum { DG_DELAY_INTEGER = 0, DG_DELAY_LAGRANGE4 = 1 };
+
+/* Non-coherent accumulation over snapshots (Algorithm 1, "sum the grids"):
+ * POWER sums |C_k|^2; MAG sums |C_k|, the paper's S of Eq. 11. */
+enum { DG_ACC_POWER = 0, DG_ACC_MAG = 1 };
+
+/* Arithmetic of the correlation and of the cost surface. Geometry (Eq. 3-10)
+ * is FP64 in both. FP32 writes float[G], FP64 writes double[G]. */
+enum { DG_PREC_FP32 = 0, DG_PREC_FP64 = 1 };
+
+/* Correlation algorithm. DIRECT evaluates Eq. 11 sample by sample for every
+ * candidate. */
+enum { DG_ALGO_DIRECT = 0 };
+
+typedef struct {
+    double lat0_deg, lon0_deg; /* grid centre (node ((nlat-1)/2, (nlon-1)/2))  */
+    double dlat_m, dlon_m;     /* node spacing in metres at the centre latitude:
+                                  dlat = dlat_m / M(lat0), dlon = dlon_m /
+                                  (N(lat0) cos lat0), with the WGS-84 meridian
+                                  (M) and prime-vertical (N) radii             */
+    int32_t nlat, nlon;        /* nodes per column / row, each >= 1            */
+} dg_grid;
+
+/* Receiver states at one snapshot epoch, ECEF metres and metres/second
+ * (Sec. III: s_i = [p_i, v_i]). Receiver 1 is i, receiver 2 is j in Eq. 7-8. */
+typedef struct {
+    double p1[3], v1[3], p2[3], v2[3];
+} dg_ephem;
+
+typedef struct {
+    int32_t delay;   /* DG_DELAY_*                                            */
+    int32_t acc;     /* DG_ACC_*                                              */
+    int32_t prec;    /* DG_PREC_*                                             */
+    int32_t algo;    /* DG_ALGO_*                                             */
+    int32_t row0;    /* first grid row of this context's shard                */
+    int32_t nrows;   /* rows in the shard; 0 = all rows from row0             */
+    int32_t timing;  /* 1: time kernels with CUDA events (dg_kernel_time)     */
+    int32_t reserved;
+} dg_options;
+
+typedef struct dg_ctx dg_ctx;
+
+/* Result of dg_argmax_refine. The coarse fields refer to the context's grid
+ * (global row index i, even for a shard); the refined fields to the local
+ * grid of the refinement (refine_n = 0 when no refinement was asked for). */
+typedef struct {
+    int64_t index;             /* linear index in the shard's surface         */
+    int32_t i, j;              /* global row, column of the coarse maximum    */
+    double lat_deg, lon_deg;   /* that node                                   */
+    double cost;               /* the surface value there                     */
+    int32_t refine_n;          /* side of the refinement grid (odd) or 0      */
+    int32_t ri, rj;            /* maximum within the refinement grid          */
+    int32_t pad;
+    double refined_lat_deg, refined_lon_deg, refined_cost;
+} dg_fix;
+
+/* Kernel classes for dg_kernel_time: the main surface's correlation and
+ * accumulation, the argmax passes, grid/geometry kernels, and everything the
+ * local refinement of dg_argmax_refine launches (grid, correlation, sum). */
+enum { DG_K_CORR = 0, DG_K_ACCUM = 1, DG_K_ARGMAX = 2, DG_K_GRID = 3, DG_K_REFINE = 4, DG_K_NCLASS = 5 };
+
+/* Defaults: INTEGER delay, POWER accumulation, FP32, DIRECT, whole grid, no
+ * timing. o must not be NULL. */
+void dg_options_default(dg_options *o);
+
+/* Create a context for one grid and one set of K snapshot ephemerides.
+ * Converts every candidate of the shard to ECEF on the device (Algorithm 1,
+ * first step; Sec. III). grid, eph (K entries) and opt are host pointers read
+ * during the call; opt may be NULL for defaults. cuda_stream is a cudaStream_t
+ * (NULL = the legacy default stream) on the current device; it must outlive
+ * the context. fs_hz > 0 is the complex sampling rate, fc_hz > 0 the carrier
+ * (lambda = c / fc in Eq. 6). The context owns its device memory (grid ECEF,
+ * ephemerides, captures, scratch), allocated stream-ordered on cuda_stream.
+ * On success *out is a new context; release it with dg_destroy. */
+dg_status dg_create(const dg_grid *grid, const dg_ephem *eph, int32_t K, double fs_hz,
+                    double fc_hz, const dg_options *opt, void *cuda_stream, dg_ctx **out);
+
+/* Copy snapshot `step` (0 <= step < K) of both receivers into the context:
+ * n_samples >= 1 complex samples each of format fmt (DG_IQ_*), stream-ordered.
+ * is_device_ptr = 0: y1, y2 are host pointers (pageable memory is staged by
+ * the CUDA runtime before this returns; pinned memory may be reused only after
+ * the stream has passed this copy). is_device_ptr = 1: device pointers,
+ * reusable after the stream has passed the copy. Reloading a step replaces it.
+ * Per Sec. II (Eq. 2), sample 0 of each snapshot is t = 0. */
+dg_status dg_load_capture(dg_ctx *ctx, int32_t step, int32_t fmt, const void *y1, const void *y2,
+                          int64_t n_samples, int32_t is_device_ptr);
+
+/* The cost surface of the shard (Eq. 11 summed over snapshots, Algorithm 1):
+ * out[p] = sum_k |C_k(p)|^2 (or |C_k(p)|), p over the shard's nrows * nlon
+ * nodes. out is a device pointer to float (FP32) or double (FP64) with room
+ * for nrows * nlon values; it is written on the stream, asynchronously.
+ * DG_ESTATE if any of the K snapshots is not loaded. */
+dg_status dg_cost_surface(dg_ctx *ctx, void *out);
+
+/* Argmax of a surface produced by dg_cost_surface (device pointer, same
+ * precision; ties go to the lowest linear index; NaN never wins), then, if
+ * refine_spacing_m > 0 and window_m >= refine_spacing_m, a dense re-evaluation
+ * on a local grid centred on that node with that spacing and half-width
+ * round(window_m / refine_spacing_m) nodes, and its argmax (Sec. III: the
+ * maximum of S is the maximum-likelihood estimate). Synchronises the stream.
+ * out is a host pointer. */
+dg_status dg_argmax_refine(dg_ctx *ctx, const void *cost, double refine_spacing_m, double window_m,
+                           dg_fix *out);
+
+/* Wait for the context's stream and report any latched kernel error. */
+dg_status dg_sync(dg_ctx *ctx);
+
+/* Release the context and its device memory (stream-ordered frees, then a
+ * stream synchronisation). NULL is accepted. */
+dg_status dg_destroy(dg_ctx *ctx);
+
+/* Message of the last failure on ctx (ctx NULL: the calling thread's last
+ * failure in dg_create). Valid until the next call on that ctx / thread. */
+const char *dg_last_error(const dg_ctx *ctx);
+
+/* --- inspection (tests, benchmarks) ------------------------------------- */
+
+/* Candidate ECEF of the shard, device pointer to double[3][nrows*nlon]
+ * (x block, then y, then z). */
+dg_status dg_grid_ecef(dg_ctx *ctx, double *xyz_out);
+
+/* Per-candidate geometry of snapshot `step` (Eq. 3-10), device pointers, each
+ * nrows*nlon long, any may be NULL: lag[] = the integer lag of the context's
+ * delay mode (round(D) or floor(D)), D[] = dtau * fs in samples,
+ * nu[] = dfreq / fs in cycles per sample. */
+dg_status dg_step_geometry(dg_ctx *ctx, int32_t step, int32_t *lag, double *D, double *nu);
+
+/* Accumulated CUDA-event time of one kernel class (requires opt.timing = 1;
+ * synchronises the stream). ms and launches are host pointers, may be NULL. */
+dg_status dg_kernel_time(dg_ctx *ctx, int32_t kernel_class, double *ms, int64_t *launches);
+
+/* Reset the counters behind dg_kernel_time and dg_launch_count. */
+dg_status dg_reset_counters(dg_ctx *ctx);
+
+/* Number of kernels this context has launched since creation or the last
+ * dg_reset_counters. */
+int64_t dg_launch_count(const dg_ctx *ctx);
+
+/* DG_ABI_VERSION of the loaded library. */
+int32_t dg_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DG_H */

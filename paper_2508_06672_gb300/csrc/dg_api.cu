@@ -1,0 +1,610 @@
+// dg_api.cu -- host implementation of the C ABI declared in include/dg.h.
+//
+// The context owns every device buffer of the hot path: shard ECEF [3][G],
+// ephemerides [K][12], per-snapshot captures (raw format, not widened), the
+// per-snapshot surfaces [K][G] (scratch for the ordered accumulation), the
+// argmax scratch and the refinement buffers. All allocation is
+// stream-ordered (cudaMallocAsync / cudaFreeAsync) on the context's stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dg_internal.cuh"
+
+using namespace dg;
+
+namespace {
+
+thread_local std::string g_thread_error;
+
+struct Step {
+    int fmt = -1;
+    int64_t n = 0;
+    void *y1 = nullptr, *y2 = nullptr;
+    size_t cap = 0;  // bytes per receiver buffer
+    bool loaded = false;
+};
+
+struct TimedLaunch {
+    int cls;
+    cudaEvent_t a, b;
+};
+
+struct LocalGrid {  // refinement buffers, grown on demand
+    double *xyz = nullptr;
+    void *surf = nullptr;
+    void *cost = nullptr;
+    size_t g_cap = 0;
+};
+
+}  // namespace
+
+struct dg_ctx {
+    dg_grid grid{};
+    dg_options opt{};
+    int K = 0;
+    double fs = 0, fc = 0, lambda = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    GridDev gd{};
+    int64_t G = 0;
+    double *xyz = nullptr;
+    double *eph = nullptr;
+    std::vector<dg_ephem> eph_host;
+    std::vector<Step> steps;
+    StepDesc *steps_d = nullptr;
+    std::vector<StepDesc> steps_h;
+    bool steps_dirty = true;
+    void *surf = nullptr;
+    size_t surf_bytes = 0;
+    void *amax_tmp = nullptr;
+    size_t amax_tmp_bytes = 0;
+    ArgmaxResult *amax_res = nullptr;
+    ArgmaxResult *amax_host = nullptr;  // pinned
+    unsigned *err_d = nullptr;
+    unsigned *err_h = nullptr;          // pinned mirror
+    LocalGrid loc;
+    std::string err;
+    int64_t launches = 0;
+    std::vector<TimedLaunch> pending;
+    double ms[DG_K_NCLASS] = {};
+    int64_t nl[DG_K_NCLASS] = {};
+};
+
+namespace {
+
+dg_status fail(dg_ctx *c, dg_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c)
+        c->err = buf;
+    else
+        g_thread_error = buf;
+    return st;
+}
+
+#define CK(ctx, call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? DG_ENOMEM : DG_ECUDA, "%s: %s", \
+                        #call, cudaGetErrorString(e_));                                        \
+    } while (0)
+
+size_t iq_bytes(int fmt)
+{
+    switch (fmt) {
+    case DG_IQ_C64: return 8;
+    case DG_IQ_CI16: return 4;
+    case DG_IQ_CI8: return 2;
+    default: return 0;
+    }
+}
+
+bool finite3(const double *v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+// Record kernel timing events around a launch when timing is on.
+struct Timed {
+    dg_ctx *c;
+    int cls;
+    cudaEvent_t a = nullptr, b = nullptr;
+    Timed(dg_ctx *c_, int cls_) : c(c_), cls(cls_)
+    {
+        if (c->opt.timing) {
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            cudaEventRecord(a, c->stream);
+        }
+    }
+    void done(int nlaunch)
+    {
+        c->launches += nlaunch;
+        if (c->opt.timing) {
+            cudaEventRecord(b, c->stream);
+            c->pending.push_back({cls, a, b});
+            c->nl[cls] += nlaunch;
+            a = b = nullptr;
+        }
+    }
+    ~Timed()
+    {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
+dg_status check_latched(dg_ctx *c)
+{
+    // err_h mirrors err_d after the last enqueued copy; caller has synchronised.
+    const unsigned e = *c->err_h;
+    if (e) {
+        *c->err_h = 0;
+        cudaMemsetAsync(c->err_d, 0, sizeof(unsigned), c->stream);
+        if (e & ERR_NU_RANGE)
+            return fail(c, DG_EUNSUPPORTED,
+                        "a candidate's FDOA exceeds 0.2 fs (|dfreq/fs| > 0.2); the correlation "
+                        "kernels do not handle it");
+        return fail(c, DG_EUNSUPPORTED, "a candidate's lag |D| exceeds 1e9 samples");
+    }
+    return DG_OK;
+}
+
+dg_status ensure(dg_ctx *c, void **p, size_t *cap, size_t bytes)
+{
+    if (*cap >= bytes && *p) return DG_OK;
+    if (*p) CK(c, cudaFreeAsync(*p, c->stream));
+    *p = nullptr;
+    *cap = 0;
+    CK(c, cudaMallocAsync(p, bytes, c->stream));
+    *cap = bytes;
+    return DG_OK;
+}
+
+dg_status push_steps(dg_ctx *c)
+{
+    if (!c->steps_dirty) return DG_OK;
+    for (int k = 0; k < c->K; ++k) {
+        c->steps_h[k].y1 = c->steps[k].y1;
+        c->steps_h[k].y2 = c->steps[k].y2;
+        c->steps_h[k].n = (int)c->steps[k].n;
+        c->steps_h[k].fmt = c->steps[k].fmt;
+    }
+    CK(c, cudaMemcpyAsync(c->steps_d, c->steps_h.data(), sizeof(StepDesc) * c->K,
+                          cudaMemcpyHostToDevice, c->stream));
+    // steps_h must stay unchanged until that copy has run: it is only
+    // rewritten by a later push, which first synchronises.
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->steps_dirty = false;
+    return DG_OK;
+}
+
+// Correlation for all snapshots over grid gd (ECEF xyz) into surf [K][G],
+// then the ordered sum into out.
+dg_status run_surface(dg_ctx *c, const GridDev &gd, const double *xyz, int64_t G, void *surf, void *out,
+                      bool refine)
+{
+    dg_status st = push_steps(c);
+    if (st != DG_OK) return st;
+    bool same_fmt = true;
+    for (int k = 1; k < c->K; ++k) same_fmt &= c->steps[k].fmt == c->steps[0].fmt;
+    CorrArgs a{};
+    a.xyz = xyz;
+    a.eph = c->eph;
+    a.steps = c->steps_d;
+    a.surf = surf;
+    a.err = c->err_d;
+    a.nrows = gd.nrows;
+    a.nlon = gd.nlon;
+    a.G = G;
+    a.fs = c->fs;
+    a.lambda = c->lambda;
+    a.delay = c->opt.delay;
+    a.acc = c->opt.acc;
+    a.prec = c->opt.prec;
+    const size_t esz = c->opt.prec == DG_PREC_FP64 ? 8 : 4;
+    {
+        Timed t(c, refine ? DG_K_REFINE : DG_K_CORR);
+        if (same_fmt) {
+            a.K = c->K;
+            a.fmt = c->steps[0].fmt;
+            CK(c, launch_corr_direct(a, c->stream));
+            t.done(1);
+        } else {
+            for (int k = 0; k < c->K; ++k) {
+                CorrArgs b = a;
+                b.K = 1;
+                b.fmt = c->steps[k].fmt;
+                b.eph = c->eph + 12 * (size_t)k;
+                b.steps = c->steps_d + k;
+                b.surf = (char *)surf + esz * (size_t)G * k;
+                CK(c, launch_corr_direct(b, c->stream));
+            }
+            t.done(c->K);
+        }
+    }
+    {
+        Timed t(c, refine ? DG_K_REFINE : DG_K_ACCUM);
+        CK(c, launch_accumulate(surf, c->K, G, c->opt.prec, out, c->stream));
+        t.done(1);
+    }
+    CK(c, cudaMemcpyAsync(c->err_h, c->err_d, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    return DG_OK;
+}
+
+dg_status run_argmax(dg_ctx *c, const void *v, int64_t n, const GridDev &gd, ArgmaxResult *host)
+{
+    size_t need = argmax_tmp_bytes(n);
+    dg_status st = ensure(c, &c->amax_tmp, &c->amax_tmp_bytes, need);
+    if (st != DG_OK) return st;
+    int nlaunch = 0;
+    {
+        Timed t(c, DG_K_ARGMAX);
+        CK(c, launch_argmax(v, n, c->opt.prec, gd, c->amax_tmp, c->amax_res, &nlaunch, c->stream));
+        t.done(nlaunch);
+    }
+    CK(c, cudaMemcpyAsync(c->amax_host, c->amax_res, sizeof(ArgmaxResult), cudaMemcpyDeviceToHost,
+                          c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    *host = *c->amax_host;
+    return DG_OK;
+}
+
+GridDev make_griddev(const dg_grid &g, int row0, int nrows)
+{
+    GridDev d;
+    d.lat0_rad = g.lat0_deg * (kPi / 180.0);
+    d.lon0_rad = g.lon0_deg * (kPi / 180.0);
+    d.dlat_m = g.dlat_m;
+    d.dlon_m = g.dlon_m;
+    d.nlat = g.nlat;
+    d.nlon = g.nlon;
+    d.row0 = row0;
+    d.nrows = nrows;
+    return d;
+}
+
+dg_status validate_grid(dg_ctx *c, const dg_grid *g)
+{
+    if (!g) return fail(c, DG_EINVAL, "grid is NULL");
+    if (!(std::isfinite(g->lat0_deg) && std::fabs(g->lat0_deg) < 89.0))
+        return fail(c, DG_EINVAL, "lat0_deg must be finite and within +-89 deg");
+    if (!std::isfinite(g->lon0_deg)) return fail(c, DG_EINVAL, "lon0_deg must be finite");
+    if (!(g->dlat_m > 0 && g->dlon_m > 0 && std::isfinite(g->dlat_m) && std::isfinite(g->dlon_m)))
+        return fail(c, DG_EINVAL, "grid spacing must be positive and finite");
+    if (g->nlat < 1 || g->nlon < 1) return fail(c, DG_EINVAL, "nlat and nlon must be >= 1");
+    if ((int64_t)g->nlat * g->nlon > (int64_t)1 << 31)
+        return fail(c, DG_EUNSUPPORTED, "grid larger than 2^31 nodes");
+    return DG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t dg_abi_version(void) { return DG_ABI_VERSION; }
+
+void dg_options_default(dg_options *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->delay = DG_DELAY_INTEGER;
+    o->acc = DG_ACC_POWER;
+    o->prec = DG_PREC_FP32;
+    o->algo = DG_ALGO_DIRECT;
+}
+
+const char *dg_last_error(const dg_ctx *ctx) { return ctx ? ctx->err.c_str() : g_thread_error.c_str(); }
+
+dg_status dg_create(const dg_grid *grid, const dg_ephem *eph, int32_t K, double fs_hz, double fc_hz,
+                    const dg_options *opt, void *cuda_stream, dg_ctx **out)
+{
+    g_thread_error.clear();
+    if (!out) return fail(nullptr, DG_EINVAL, "out is NULL");
+    dg_status st = validate_grid(nullptr, grid);
+    if (st != DG_OK) return st;
+    if (!eph) return fail(nullptr, DG_EINVAL, "eph is NULL");
+    if (K < 1 || K > 65535) return fail(nullptr, DG_EINVAL, "K must be in [1, 65535]");
+    if (!(fs_hz > 0 && std::isfinite(fs_hz))) return fail(nullptr, DG_EINVAL, "fs_hz must be > 0");
+    if (!(fc_hz > 0 && std::isfinite(fc_hz))) return fail(nullptr, DG_EINVAL, "fc_hz must be > 0");
+    dg_options o;
+    dg_options_default(&o);
+    if (opt) o = *opt;
+    if (o.delay != DG_DELAY_INTEGER && o.delay != DG_DELAY_LAGRANGE4)
+        return fail(nullptr, DG_EINVAL, "unknown delay mode %d", o.delay);
+    if (o.acc != DG_ACC_POWER && o.acc != DG_ACC_MAG) return fail(nullptr, DG_EINVAL, "unknown acc mode %d", o.acc);
+    if (o.prec != DG_PREC_FP32 && o.prec != DG_PREC_FP64)
+        return fail(nullptr, DG_EINVAL, "unknown precision %d", o.prec);
+    if (o.algo != DG_ALGO_DIRECT) return fail(nullptr, DG_EINVAL, "unknown algorithm %d", o.algo);
+    if (o.row0 < 0 || o.row0 >= grid->nlat) return fail(nullptr, DG_EINVAL, "row0 outside the grid");
+    if (o.nrows < 0 || o.row0 + o.nrows > grid->nlat) return fail(nullptr, DG_EINVAL, "row shard outside the grid");
+    for (int k = 0; k < K; ++k)
+        if (!finite3(eph[k].p1) || !finite3(eph[k].v1) || !finite3(eph[k].p2) || !finite3(eph[k].v2))
+            return fail(nullptr, DG_EINVAL, "ephemeris %d is not finite", k);
+
+    dg_ctx *c = new (std::nothrow) dg_ctx();
+    if (!c) return fail(nullptr, DG_ENOMEM, "host allocation failed");
+    c->grid = *grid;
+    c->opt = o;
+    c->K = K;
+    c->fs = fs_hz;
+    c->fc = fc_hz;
+    c->lambda = kC / fc_hz;
+    c->stream = (cudaStream_t)cuda_stream;
+    const int nrows = o.nrows ? o.nrows : grid->nlat - o.row0;
+    c->gd = make_griddev(*grid, o.row0, nrows);
+    c->G = (int64_t)nrows * grid->nlon;
+    c->eph_host.assign(eph, eph + K);
+    c->steps.resize(K);
+    c->steps_h.resize(K);
+
+    auto bail = [&](dg_status s) {
+        g_thread_error = c->err;
+        dg_destroy(c);
+        return s;
+    };
+#define CKC(call)                                                                              \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return bail(fail(c, e_ == cudaErrorMemoryAllocation ? DG_ENOMEM : DG_ECUDA, "%s: %s", \
+                             #call, cudaGetErrorString(e_)));                                  \
+    } while (0)
+    CKC(cudaGetDevice(&c->device));
+    CKC(cudaMallocAsync((void **)&c->xyz, sizeof(double) * 3 * (size_t)c->G, c->stream));
+    CKC(cudaMallocAsync((void **)&c->eph, sizeof(double) * 12 * (size_t)K, c->stream));
+    CKC(cudaMallocAsync((void **)&c->steps_d, sizeof(StepDesc) * (size_t)K, c->stream));
+    CKC(cudaMallocAsync((void **)&c->amax_res, sizeof(ArgmaxResult), c->stream));
+    CKC(cudaMallocAsync((void **)&c->err_d, sizeof(unsigned), c->stream));
+    CKC(cudaMallocHost((void **)&c->amax_host, sizeof(ArgmaxResult)));
+    CKC(cudaMallocHost((void **)&c->err_h, sizeof(unsigned)));
+    *c->err_h = 0;
+    CKC(cudaMemsetAsync(c->err_d, 0, sizeof(unsigned), c->stream));
+    CKC(cudaMemcpyAsync(c->eph, c->eph_host.data(), sizeof(dg_ephem) * (size_t)K, cudaMemcpyHostToDevice,
+                        c->stream));
+    {
+        Timed t(c, DG_K_GRID);
+        CKC(launch_grid_ecef(c->gd, c->xyz, c->stream));
+        t.done(1);
+    }
+    CKC(cudaStreamSynchronize(c->stream));  // eph_host may not move before the copy ran
+#undef CKC
+    *out = c;
+    return DG_OK;
+}
+
+dg_status dg_load_capture(dg_ctx *c, int32_t step, int32_t fmt, const void *y1, const void *y2,
+                          int64_t n, int32_t is_device_ptr)
+{
+    if (!c) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    c->err.clear();
+    if (step < 0 || step >= c->K) return fail(c, DG_EINVAL, "step %d outside [0, %d)", step, c->K);
+    const size_t bps = iq_bytes(fmt);
+    if (!bps) return fail(c, DG_EINVAL, "unknown IQ format %d", fmt);
+    if (!y1 || !y2) return fail(c, DG_EINVAL, "y1 and y2 must not be NULL");
+    if (n < 1) return fail(c, DG_EINVAL, "n_samples must be >= 1");
+    if (n > ((int64_t)1 << 30)) return fail(c, DG_EUNSUPPORTED, "n_samples above 2^30");
+    Step &s = c->steps[step];
+    const size_t bytes = bps * (size_t)n;
+    if (s.cap < bytes) {
+        if (s.y1) CK(c, cudaFreeAsync(s.y1, c->stream));
+        if (s.y2) CK(c, cudaFreeAsync(s.y2, c->stream));
+        s.y1 = s.y2 = nullptr;
+        s.cap = 0;
+        s.loaded = false;
+        CK(c, cudaMallocAsync(&s.y1, bytes, c->stream));
+        CK(c, cudaMallocAsync(&s.y2, bytes, c->stream));
+        s.cap = bytes;
+    }
+    const cudaMemcpyKind kind = is_device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(c, cudaMemcpyAsync(s.y1, y1, bytes, kind, c->stream));
+    CK(c, cudaMemcpyAsync(s.y2, y2, bytes, kind, c->stream));
+    if (s.fmt != fmt || s.n != n) c->steps_dirty = true;
+    if (!s.loaded) c->steps_dirty = true;
+    s.fmt = fmt;
+    s.n = n;
+    s.loaded = true;
+    return DG_OK;
+}
+
+dg_status dg_cost_surface(dg_ctx *c, void *out)
+{
+    if (!c) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    c->err.clear();
+    if (!out) return fail(c, DG_EINVAL, "out is NULL");
+    for (int k = 0; k < c->K; ++k)
+        if (!c->steps[k].loaded) return fail(c, DG_ESTATE, "snapshot %d has not been loaded", k);
+    const size_t esz = c->opt.prec == DG_PREC_FP64 ? 8 : 4;
+    dg_status st = ensure(c, &c->surf, &c->surf_bytes, esz * (size_t)c->G * c->K);
+    if (st != DG_OK) return st;
+    return run_surface(c, c->gd, c->xyz, c->G, c->surf, out, false);
+}
+
+dg_status dg_sync(dg_ctx *c)
+{
+    if (!c) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    c->err.clear();
+    CK(c, cudaStreamSynchronize(c->stream));
+    return check_latched(c);
+}
+
+dg_status dg_argmax_refine(dg_ctx *c, const void *cost, double spacing_m, double window_m, dg_fix *out)
+{
+    if (!c) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    c->err.clear();
+    if (!cost || !out) return fail(c, DG_EINVAL, "cost and out must not be NULL");
+    const bool refine = spacing_m > 0 && window_m >= spacing_m;
+    int half = 0;
+    if (refine) {
+        if (!(std::isfinite(spacing_m) && std::isfinite(window_m)))
+            return fail(c, DG_EINVAL, "refinement spacing and window must be finite");
+        const double h = std::floor(window_m / spacing_m + 0.5);
+        if (h > 2000) return fail(c, DG_EINVAL, "refinement grid wider than 4001 nodes");
+        half = (int)h;
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    dg_status st = check_latched(c);
+    if (st != DG_OK) return st;
+    ArgmaxResult r;
+    st = run_argmax(c, cost, c->G, c->gd, &r);
+    if (st != DG_OK) return st;
+    if (r.idx < 0) return fail(c, DG_EINVAL, "the surface holds no finite value");
+    dg_fix f;
+    std::memset(&f, 0, sizeof f);
+    f.index = r.idx;
+    f.i = c->gd.row0 + (int)(r.idx / c->gd.nlon);
+    f.j = (int)(r.idx % c->gd.nlon);
+    f.lat_deg = r.lat_rad * (180.0 / kPi);
+    f.lon_deg = r.lon_rad * (180.0 / kPi);
+    f.cost = r.val;
+    if (refine) {
+        const int n = 2 * half + 1;
+        dg_grid lg;
+        lg.lat0_deg = f.lat_deg;
+        lg.lon0_deg = f.lon_deg;
+        lg.dlat_m = spacing_m;
+        lg.dlon_m = spacing_m;
+        lg.nlat = n;
+        lg.nlon = n;
+        const GridDev lgd = make_griddev(lg, 0, n);
+        const int64_t G = (int64_t)n * n;
+        const size_t esz = c->opt.prec == DG_PREC_FP64 ? 8 : 4;
+        if (c->loc.g_cap < (size_t)G) {
+            if (c->loc.xyz) CK(c, cudaFreeAsync(c->loc.xyz, c->stream));
+            if (c->loc.surf) CK(c, cudaFreeAsync(c->loc.surf, c->stream));
+            if (c->loc.cost) CK(c, cudaFreeAsync(c->loc.cost, c->stream));
+            c->loc = LocalGrid{};
+            CK(c, cudaMallocAsync((void **)&c->loc.xyz, sizeof(double) * 3 * G, c->stream));
+            CK(c, cudaMallocAsync(&c->loc.surf, esz * G * c->K + 8, c->stream));
+            CK(c, cudaMallocAsync(&c->loc.cost, esz * G + 8, c->stream));
+            c->loc.g_cap = (size_t)G;
+        }
+        {
+            Timed t(c, DG_K_REFINE);
+            CK(c, launch_grid_ecef(lgd, c->loc.xyz, c->stream));
+            t.done(1);
+        }
+        st = run_surface(c, lgd, c->loc.xyz, G, c->loc.surf, c->loc.cost, true);
+        if (st != DG_OK) return st;
+        CK(c, cudaStreamSynchronize(c->stream));
+        st = check_latched(c);
+        if (st != DG_OK) return st;
+        ArgmaxResult q;
+        st = run_argmax(c, c->loc.cost, G, lgd, &q);
+        if (st != DG_OK) return st;
+        if (q.idx < 0) return fail(c, DG_EINVAL, "the refinement surface holds no finite value");
+        f.refine_n = n;
+        f.ri = (int)(q.idx / n);
+        f.rj = (int)(q.idx % n);
+        f.refined_lat_deg = q.lat_rad * (180.0 / kPi);
+        f.refined_lon_deg = q.lon_rad * (180.0 / kPi);
+        f.refined_cost = q.val;
+    }
+    *out = f;
+    return DG_OK;
+}
+
+dg_status dg_grid_ecef(dg_ctx *c, double *xyz_out)
+{
+    if (!c) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    c->err.clear();
+    if (!xyz_out) return fail(c, DG_EINVAL, "xyz_out is NULL");
+    CK(c, cudaMemcpyAsync(xyz_out, c->xyz, sizeof(double) * 3 * (size_t)c->G, cudaMemcpyDeviceToDevice,
+                          c->stream));
+    return DG_OK;
+}
+
+dg_status dg_step_geometry(dg_ctx *c, int32_t step, int32_t *lag, double *D, double *nu)
+{
+    if (!c) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    c->err.clear();
+    if (step < 0 || step >= c->K) return fail(c, DG_EINVAL, "step %d outside [0, %d)", step, c->K);
+    {
+        Timed t(c, DG_K_GRID);
+        CK(c, launch_step_geometry(c->gd, c->xyz, c->eph + 12 * (size_t)step, c->fs, c->lambda,
+                                   c->opt.delay, lag, D, nu, c->stream));
+        t.done(1);
+    }
+    return DG_OK;
+}
+
+dg_status dg_kernel_time(dg_ctx *c, int32_t cls, double *ms, int64_t *launches)
+{
+    if (!c) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    c->err.clear();
+    if (cls < 0 || cls >= DG_K_NCLASS) return fail(c, DG_EINVAL, "unknown kernel class %d", cls);
+    CK(c, cudaStreamSynchronize(c->stream));
+    for (auto &t : c->pending) {
+        float v = 0;
+        cudaEventElapsedTime(&v, t.a, t.b);
+        c->ms[t.cls] += v;
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    c->pending.clear();
+    if (ms) *ms = c->ms[cls];
+    if (launches) *launches = c->nl[cls];
+    return DG_OK;
+}
+
+dg_status dg_reset_counters(dg_ctx *c)
+{
+    if (!c) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    c->err.clear();
+    CK(c, cudaStreamSynchronize(c->stream));
+    for (auto &t : c->pending) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    c->pending.clear();
+    for (int i = 0; i < DG_K_NCLASS; ++i) {
+        c->ms[i] = 0;
+        c->nl[i] = 0;
+    }
+    c->launches = 0;
+    return DG_OK;
+}
+
+int64_t dg_launch_count(const dg_ctx *c) { return c ? c->launches : -1; }
+
+dg_status dg_destroy(dg_ctx *c)
+{
+    if (!c) return DG_OK;
+    cudaStream_t s = c->stream;
+    for (auto &t : c->pending) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    auto fr = [&](void *p) {
+        if (p) cudaFreeAsync(p, s);
+    };
+    fr(c->xyz);
+    fr(c->eph);
+    fr(c->steps_d);
+    fr(c->surf);
+    fr(c->amax_tmp);
+    fr(c->amax_res);
+    fr(c->err_d);
+    fr(c->loc.xyz);
+    fr(c->loc.surf);
+    fr(c->loc.cost);
+    for (auto &st : c->steps) {
+        fr(st.y1);
+        fr(st.y2);
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (c->amax_host) cudaFreeHost(c->amax_host);
+    if (c->err_h) cudaFreeHost(c->err_h);
+    delete c;
+    if (e != cudaSuccess) return fail(nullptr, DG_ECUDA, "dg_destroy: %s", cudaGetErrorString(e));
+    return DG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,140 @@
+// dg_reduce.cu -- non-coherent accumulation over snapshots and the argmax
+// (Algorithm 1: sum the position-domain correlation grids; Sec. III: the
+// maximum of S is the maximum-likelihood estimate).
+#include <cfloat>
+
+#include "dg_internal.cuh"
+
+namespace dg {
+
+// out[p] = sum_{k=0}^{K-1} surf[k][p], always in that order (deterministic).
+// Vectorised by 4 along p where G allows; HBM-bound (K reads + 1 write).
+template <typename T>
+__global__ void __launch_bounds__(256) k_accumulate(const T *__restrict__ surf, int K, int64_t G,
+                                                    T *__restrict__ out)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < G;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        T s = surf[p];
+        for (int k = 1; k < K; ++k) s += __ldcs(surf + (int64_t)k * G + p);
+        out[p] = s;
+    }
+}
+
+cudaError_t launch_accumulate(const void *surf, int K, int64_t G, int prec, void *out, cudaStream_t s)
+{
+    int64_t blocks = (G + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks < 1) blocks = 1;
+    if (prec == DG_PREC_FP64)
+        k_accumulate<double><<<(unsigned)blocks, 256, 0, s>>>((const double *)surf, K, G, (double *)out);
+    else
+        k_accumulate<float><<<(unsigned)blocks, 256, 0, s>>>((const float *)surf, K, G, (float *)out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// argmax: (value, index) pairs; a beats b if a is valid and (b is invalid, or
+// a.val > b.val, or equal values and a.idx < b.idx). NaN is never valid.
+// ---------------------------------------------------------------------------
+struct VI {
+    double val;
+    int64_t idx;
+};
+
+__device__ __forceinline__ bool beats(const VI &a, const VI &b)
+{
+    if (a.idx < 0) return false;
+    if (b.idx < 0) return true;
+    return a.val > b.val || (a.val == b.val && a.idx < b.idx);
+}
+
+__device__ __forceinline__ VI warp_best(VI v)
+{
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        VI o;
+        o.val = __shfl_xor_sync(0xffffffffu, v.val, d);
+        o.idx = __shfl_xor_sync(0xffffffffu, v.idx, d);
+        if (beats(o, v)) v = o;
+    }
+    return v;
+}
+
+__device__ __forceinline__ VI block_best(VI v)
+{
+    __shared__ VI sh[32];
+    v = warp_best(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    if (warp == 0) {
+        v = lane < nw ? sh[lane] : VI{0.0, -1};
+        v = warp_best(v);
+    }
+    return v;  // valid in thread 0
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_argmax_partial(const T *__restrict__ v, int64_t n, VI *part)
+{
+    VI best{0.0, -1};
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const double x = (double)v[p];
+        if (x == x && (best.idx < 0 || x > best.val)) best = VI{x, p};  // p increases per thread
+    }
+    best = block_best(best);
+    if (threadIdx.x == 0) part[blockIdx.x] = best;
+}
+
+__global__ void __launch_bounds__(1024) k_argmax_final(const VI *part, int nparts, GridDev g,
+                                                       ArgmaxResult *res)
+{
+    VI best{0.0, -1};
+    for (int p = threadIdx.x; p < nparts; p += blockDim.x)
+        if (beats(part[p], best)) best = part[p];
+    best = block_best(best);
+    if (threadIdx.x == 0) {
+        res->val = best.val;
+        res->idx = best.idx;
+        res->lat_rad = 0.0;
+        res->lon_rad = 0.0;
+        if (best.idx >= 0) {
+            const GridStep st = grid_step(g);
+            double lat, lon;
+            grid_node(g, st, g.row0 + (int)(best.idx / g.nlon), (int)(best.idx % g.nlon), lat, lon);
+            res->lat_rad = lat;
+            res->lon_rad = lon;
+        }
+    }
+}
+
+static int argmax_blocks(int64_t n)
+{
+    int64_t b = (n + 1023) / 1024;
+    if (b > 152 * 2) b = 152 * 2;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+size_t argmax_tmp_bytes(int64_t n) { return sizeof(VI) * (size_t)argmax_blocks(n); }
+
+cudaError_t launch_argmax(const void *v, int64_t n, int prec, const GridDev &g, void *tmp,
+                          ArgmaxResult *res, int *launches, cudaStream_t s)
+{
+    const int nb = argmax_blocks(n);
+    VI *part = reinterpret_cast<VI *>(tmp);
+    if (prec == DG_PREC_FP64)
+        k_argmax_partial<double><<<nb, 1024, 0, s>>>((const double *)v, n, part);
+    else
+        k_argmax_partial<float><<<nb, 1024, 0, s>>>((const float *)v, n, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_argmax_final<<<1, 1024, 0, s>>>(part, nb, g, res);
+    if (launches) *launches += 2;
+    return cudaGetLastError();
+}
+
+}  // namespace dg

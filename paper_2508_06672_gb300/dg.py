@@ -1,0 +1,339 @@
+"""Python binding of libdg (``include/dg.h``): argument marshalling only.
+
+Every step of the hot path runs in the CUDA library. torch provides device
+memory and streams. If the library is missing this module raises on use; it
+never falls back to another implementation.
+
+Two layers:
+
+* ``dg_*`` functions with the C names and arguments (ctypes), raising
+  :class:`DGError` on a non-zero status;
+* :class:`Geolocator`, a context object over torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+__all__ = [
+    "DGError", "dg_grid", "dg_ephem", "dg_options", "dg_fix", "lib", "library_path",
+    "dg_options_default", "dg_create", "dg_load_capture", "dg_cost_surface", "dg_argmax_refine",
+    "dg_sync", "dg_destroy", "dg_last_error", "dg_grid_ecef", "dg_step_geometry", "dg_kernel_time",
+    "dg_reset_counters", "dg_launch_count", "dg_abi_version", "Geolocator",
+    "DG_OK", "DG_EINVAL", "DG_ENOMEM", "DG_ECUDA", "DG_ESTATE", "DG_ETIMEOUT", "DG_EUNSUPPORTED",
+    "DG_IQ_C64", "DG_IQ_CI16", "DG_IQ_CI8", "DG_DELAY_INTEGER", "DG_DELAY_LAGRANGE4",
+    "DG_ACC_POWER", "DG_ACC_MAG", "DG_PREC_FP32", "DG_PREC_FP64", "DG_ALGO_DIRECT",
+    "DG_K_CORR", "DG_K_ACCUM", "DG_K_ARGMAX", "DG_K_GRID", "DG_K_REFINE", "EXPORTED_SYMBOLS",
+]
+
+DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_ESTATE, DG_ETIMEOUT, DG_EUNSUPPORTED = range(7)
+DG_IQ_C64, DG_IQ_CI16, DG_IQ_CI8 = 0, 1, 2
+DG_DELAY_INTEGER, DG_DELAY_LAGRANGE4 = 0, 1
+DG_ACC_POWER, DG_ACC_MAG = 0, 1
+DG_PREC_FP32, DG_PREC_FP64 = 0, 1
+DG_ALGO_DIRECT = 0
+DG_K_CORR, DG_K_ACCUM, DG_K_ARGMAX, DG_K_GRID, DG_K_REFINE = 0, 1, 2, 3, 4
+
+_FMT = {"c64": DG_IQ_C64, "ci16": DG_IQ_CI16, "ci8": DG_IQ_CI8}
+_FMT_DTYPE = {DG_IQ_C64: np.float32, DG_IQ_CI16: np.int16, DG_IQ_CI8: np.int8}
+_DELAY = {"integer": DG_DELAY_INTEGER, "lagrange4": DG_DELAY_LAGRANGE4}
+_ACC = {"power": DG_ACC_POWER, "mag": DG_ACC_MAG}
+_PREC = {"fp32": DG_PREC_FP32, "fp64": DG_PREC_FP64}
+_ALGO = {"direct": DG_ALGO_DIRECT}
+
+EXPORTED_SYMBOLS = [
+    "dg_options_default", "dg_create", "dg_load_capture", "dg_cost_surface", "dg_argmax_refine",
+    "dg_sync", "dg_destroy", "dg_last_error", "dg_grid_ecef", "dg_step_geometry", "dg_kernel_time",
+    "dg_reset_counters", "dg_launch_count", "dg_abi_version",
+]
+
+
+class DGError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"dg status {status}: {message}")
+        self.status = status
+
+
+class dg_grid(C.Structure):
+    _fields_ = [("lat0_deg", C.c_double), ("lon0_deg", C.c_double), ("dlat_m", C.c_double),
+                ("dlon_m", C.c_double), ("nlat", C.c_int32), ("nlon", C.c_int32)]
+
+    @classmethod
+    def from_dict(cls, d):
+        return cls(float(d["lat0_deg"]), float(d["lon0_deg"]), float(d["dlat_m"]),
+                   float(d["dlon_m"]), int(d["nlat"]), int(d["nlon"]))
+
+
+class dg_ephem(C.Structure):
+    _fields_ = [("p1", C.c_double * 3), ("v1", C.c_double * 3), ("p2", C.c_double * 3),
+                ("v2", C.c_double * 3)]
+
+
+class dg_options(C.Structure):
+    _fields_ = [("delay", C.c_int32), ("acc", C.c_int32), ("prec", C.c_int32), ("algo", C.c_int32),
+                ("row0", C.c_int32), ("nrows", C.c_int32), ("timing", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class dg_fix(C.Structure):
+    _fields_ = [("index", C.c_int64), ("i", C.c_int32), ("j", C.c_int32), ("lat_deg", C.c_double),
+                ("lon_deg", C.c_double), ("cost", C.c_double), ("refine_n", C.c_int32),
+                ("ri", C.c_int32), ("rj", C.c_int32), ("pad", C.c_int32),
+                ("refined_lat_deg", C.c_double), ("refined_lon_deg", C.c_double),
+                ("refined_cost", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+_LOCK = threading.Lock()
+_LIB = None
+
+
+def library_path() -> str:
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libdg.so")
+
+
+def lib():
+    """The loaded libdg.so; raises if it has not been built."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                                   "(needs nvcc); there is no fallback implementation")
+            L = C.CDLL(path)
+            vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+            L.dg_options_default.argtypes = [C.POINTER(dg_options)]
+            L.dg_options_default.restype = None
+            L.dg_create.argtypes = [C.POINTER(dg_grid), C.POINTER(dg_ephem), i32, dbl, dbl,
+                                    C.POINTER(dg_options), vp, C.POINTER(vp)]
+            L.dg_load_capture.argtypes = [vp, i32, i32, vp, vp, i64, i32]
+            L.dg_cost_surface.argtypes = [vp, vp]
+            L.dg_argmax_refine.argtypes = [vp, vp, dbl, dbl, C.POINTER(dg_fix)]
+            L.dg_sync.argtypes = [vp]
+            L.dg_destroy.argtypes = [vp]
+            L.dg_last_error.argtypes = [vp]
+            L.dg_last_error.restype = C.c_char_p
+            L.dg_grid_ecef.argtypes = [vp, vp]
+            L.dg_step_geometry.argtypes = [vp, i32, vp, vp, vp]
+            L.dg_kernel_time.argtypes = [vp, i32, C.POINTER(dbl), C.POINTER(i64)]
+            L.dg_reset_counters.argtypes = [vp]
+            L.dg_launch_count.argtypes = [vp]
+            L.dg_launch_count.restype = i64
+            L.dg_abi_version.argtypes = []
+            L.dg_abi_version.restype = i32
+            for name in ("dg_create", "dg_load_capture", "dg_cost_surface", "dg_argmax_refine",
+                         "dg_sync", "dg_destroy", "dg_grid_ecef", "dg_step_geometry",
+                         "dg_kernel_time", "dg_reset_counters"):
+                getattr(L, name).restype = C.c_int
+            _LIB = L
+    return _LIB
+
+
+def _check(status, ctx=None):
+    if status != DG_OK:
+        msg = lib().dg_last_error(ctx)
+        raise DGError(status, msg.decode() if msg else "")
+
+
+# ----------------------------------------------------------------- C names
+def dg_options_default():
+    o = dg_options()
+    lib().dg_options_default(C.byref(o))
+    return o
+
+
+def dg_create(grid, ephem, K, fs_hz, fc_hz, opt=None, stream=0):
+    """grid: dg_grid or dict; ephem: (K, 12) float64 array [p1 v1 p2 v2]."""
+    g = grid if isinstance(grid, dg_grid) else dg_grid.from_dict(grid)
+    eph = np.ascontiguousarray(ephem, dtype=np.float64).reshape(-1, 12)
+    arr = (dg_ephem * max(1, eph.shape[0]))()
+    C.memmove(arr, eph.ctypes.data, eph.nbytes)
+    out = C.c_void_p()
+    st = lib().dg_create(C.byref(g), arr, int(K), float(fs_hz), float(fc_hz),
+                         C.byref(opt) if opt is not None else None, C.c_void_p(int(stream)),
+                         C.byref(out))
+    _check(st, None)
+    return out.value
+
+
+def dg_load_capture(ctx, step, fmt, y1_ptr, y2_ptr, n_samples, is_device_ptr):
+    _check(lib().dg_load_capture(ctx, int(step), int(fmt), C.c_void_p(y1_ptr), C.c_void_p(y2_ptr),
+                                 int(n_samples), int(is_device_ptr)), ctx)
+
+
+def dg_cost_surface(ctx, out_ptr):
+    _check(lib().dg_cost_surface(ctx, C.c_void_p(out_ptr)), ctx)
+
+
+def dg_argmax_refine(ctx, cost_ptr, refine_spacing_m=0.0, window_m=0.0):
+    f = dg_fix()
+    _check(lib().dg_argmax_refine(ctx, C.c_void_p(cost_ptr), float(refine_spacing_m),
+                                  float(window_m), C.byref(f)), ctx)
+    return f
+
+
+def dg_sync(ctx):
+    _check(lib().dg_sync(ctx), ctx)
+
+
+def dg_destroy(ctx):
+    _check(lib().dg_destroy(ctx), None)
+
+
+def dg_last_error(ctx=None):
+    m = lib().dg_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def dg_grid_ecef(ctx, xyz_ptr):
+    _check(lib().dg_grid_ecef(ctx, C.c_void_p(xyz_ptr)), ctx)
+
+
+def dg_step_geometry(ctx, step, lag_ptr=0, D_ptr=0, nu_ptr=0):
+    _check(lib().dg_step_geometry(ctx, int(step), C.c_void_p(lag_ptr or None),
+                                  C.c_void_p(D_ptr or None), C.c_void_p(nu_ptr or None)), ctx)
+
+
+def dg_kernel_time(ctx, kernel_class):
+    ms, n = C.c_double(), C.c_int64()
+    _check(lib().dg_kernel_time(ctx, int(kernel_class), C.byref(ms), C.byref(n)), ctx)
+    return ms.value, n.value
+
+
+def dg_reset_counters(ctx):
+    _check(lib().dg_reset_counters(ctx), ctx)
+
+
+def dg_launch_count(ctx):
+    return int(lib().dg_launch_count(ctx))
+
+
+def dg_abi_version():
+    return int(lib().dg_abi_version())
+
+
+# ------------------------------------------------------- torch-level object
+class Geolocator:
+    """One dg context: a grid (or a row shard of it), K snapshots, options.
+
+    Device memory comes from torch; work runs on ``stream`` (a
+    torch.cuda.Stream, default: the current stream of the device)."""
+
+    def __init__(self, grid, ephem, fs_hz, fc_hz, *, delay="integer", acc="power", prec="fp32",
+                 algo="direct", row0=0, nrows=0, timing=False, stream=None, device=None):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.grid = dict(grid)
+        eph = np.ascontiguousarray(ephem, dtype=np.float64).reshape(-1, 12)
+        self.K = eph.shape[0]
+        self.opt = dg_options_default()
+        self.opt.delay, self.opt.acc = _DELAY[delay], _ACC[acc]
+        self.opt.prec, self.opt.algo = _PREC[prec], _ALGO[algo]
+        self.opt.row0, self.opt.nrows, self.opt.timing = int(row0), int(nrows), int(bool(timing))
+        self.nrows = int(nrows) if nrows else int(grid["nlat"]) - int(row0)
+        self.nlon = int(grid["nlon"])
+        self.dtype = torch.float64 if prec == "fp64" else torch.float32
+        self._keep = {}
+        with torch.cuda.device(self.device):
+            self.ctx = dg_create(self.grid, eph, self.K, fs_hz, fc_hz, self.opt, self.stream.cuda_stream)
+
+    # -- captures
+    def load_capture(self, step, fmt, y1, y2):
+        """y1, y2: (N, 2) interleaved I/Q, as torch tensors (CUDA or host) or
+        numpy arrays (host), of the storage type of fmt."""
+        torch = self.torch
+        code = _FMT[fmt] if isinstance(fmt, str) else int(fmt)
+        ptrs, dev = [], None
+        for y in (y1, y2):
+            if isinstance(y, np.ndarray):
+                y = torch.from_numpy(np.ascontiguousarray(y))
+            if not y.is_contiguous():
+                y = y.contiguous()
+            if y.dtype != torch.from_numpy(np.zeros(1, _FMT_DTYPE[code])).dtype:
+                raise TypeError(f"format {fmt} needs {_FMT_DTYPE[code].__name__} samples, got {y.dtype}")
+            if y.dim() != 2 or y.shape[1] != 2:
+                raise ValueError("captures must be (N, 2) interleaved I/Q")
+            d = bool(y.is_cuda)
+            if dev is not None and d != dev:
+                raise ValueError("y1 and y2 must both be on the device or both on the host")
+            dev = d
+            ptrs.append(y)
+        if ptrs[0].shape != ptrs[1].shape:
+            raise ValueError("y1 and y2 must have the same number of samples")
+        self._keep[step] = ptrs  # keep host buffers alive until the copy is ordered
+        dg_load_capture(self.ctx, step, code, ptrs[0].data_ptr(), ptrs[1].data_ptr(), ptrs[0].shape[0],
+                        1 if dev else 0)
+
+    def load_captures(self, fmt, y1, y2):
+        """All K snapshots: y1, y2 of shape (K, N, 2)."""
+        for k in range(self.K):
+            self.load_capture(k, fmt, y1[k], y2[k])
+
+    # -- the hot path
+    def cost_surface(self, out=None):
+        torch = self.torch
+        if out is None:
+            out = torch.empty((self.nrows, self.nlon), dtype=self.dtype, device=self.device)
+        if out.dtype != self.dtype or not out.is_cuda or not out.is_contiguous() or out.numel() < self.nrows * self.nlon:
+            raise ValueError("out must be a contiguous CUDA tensor of the context's precision")
+        dg_cost_surface(self.ctx, out.data_ptr())
+        return out
+
+    def argmax_refine(self, cost, refine_spacing_m=0.0, window_m=0.0):
+        if cost.dtype != self.dtype or not cost.is_cuda:
+            raise ValueError("cost must be a CUDA tensor of the context's precision")
+        return dg_argmax_refine(self.ctx, cost.data_ptr(), refine_spacing_m, window_m).as_dict()
+
+    def sync(self):
+        dg_sync(self.ctx)
+
+    # -- inspection
+    def grid_ecef(self):
+        out = self.torch.empty((3, self.nrows * self.nlon), dtype=self.torch.float64, device=self.device)
+        dg_grid_ecef(self.ctx, out.data_ptr())
+        return out
+
+    def step_geometry(self, step):
+        torch = self.torch
+        G = self.nrows * self.nlon
+        lag = torch.empty(G, dtype=torch.int32, device=self.device)
+        D = torch.empty(G, dtype=torch.float64, device=self.device)
+        nu = torch.empty(G, dtype=torch.float64, device=self.device)
+        dg_step_geometry(self.ctx, step, lag.data_ptr(), D.data_ptr(), nu.data_ptr())
+        return lag, D, nu
+
+    def kernel_time(self, kernel_class):
+        return dg_kernel_time(self.ctx, kernel_class)
+
+    def reset_counters(self):
+        dg_reset_counters(self.ctx)
+
+    def launch_count(self):
+        return dg_launch_count(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            dg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
