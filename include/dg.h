@@ -195,6 +195,50 @@ int64_t dg_launch_count(const dg_ctx *ctx);
 /* DG_ABI_VERSION of the loaded library. */
 int32_t dg_abi_version(void);
 
+/* --- cost surface without device allocation ---------------------------------
+ * The paper has no counterpart to this call. It serves callers that may not
+ * allocate GPU memory while they process data -- for example a real-time
+ * receiver chain that reserves all of its device memory at start-up so that no
+ * allocation can stall or fail mid-pass, or a program whose device memory is
+ * owned by another allocator (a framework's caching allocator, a pool with a
+ * fixed quota). dg_create allocates; this call does not.
+ *
+ * It computes the same surface as dg_create + dg_load_capture (every
+ * snapshot) + dg_cost_surface, with the same kernels and options. Scratch
+ * (candidate ECEF, per-snapshot surfaces, snapshot table, ephemerides, an
+ * error word) lives in one static device array of DG_NOALLOC_SCRATCH_BYTES
+ * owned by the library; it is reserved on every GPU that loads the library's
+ * device code and stays reserved until the process exits. A call needs
+ * 24*G + e*K*G + 128*K bytes plus alignment, with G = shard rows * nlon and
+ * e = 4 (FP32) or 8 (FP64); a larger call is rejected with DG_EINVAL and
+ * nothing is launched. The call makes no cudaMalloc, cudaFree or other
+ * allocating call.
+ *
+ * Arguments: grid, eph (K entries) and opt (NULL = defaults; timing ignored)
+ * are host pointers read during the call. y1 and y2 are device pointers to
+ * K * n_samples samples each of format fmt, snapshot k starting at sample
+ * k * n_samples. out is a device pointer as for dg_cost_surface.
+ * cuda_stream is a cudaStream_t of the current device (NULL = legacy stream).
+ *
+ * Behaviour: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture. The call is synchronous: it returns
+ * after the stream has completed the work, so kernel-detected errors
+ * (DG_EUNSUPPORTED) are returned directly. Every call uses the same array and
+ * leaves its contents behind (the error word is cleared at the start of each
+ * call; everything else is rewritten before it is read), so calls that
+ * overlap on the GPU -- from several host threads or on several streams --
+ * race and must be serialised by the caller. On failure,
+ * dg_noalloc_last_error() (per host thread) says why. */
+#define DG_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+
+dg_status dg_cost_surface_noalloc(const dg_grid *grid, const dg_ephem *eph, int32_t K, double fs_hz,
+                                  double fc_hz, int32_t fmt, const void *y1, const void *y2,
+                                  int64_t n_samples, const dg_options *opt, void *out, void *cuda_stream);
+
+/* Message of the calling thread's last failed dg_cost_surface_noalloc. */
+const char *dg_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

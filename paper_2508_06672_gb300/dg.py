@@ -23,6 +23,7 @@ __all__ = [
     "dg_options_default", "dg_create", "dg_load_capture", "dg_cost_surface", "dg_argmax_refine",
     "dg_sync", "dg_destroy", "dg_last_error", "dg_grid_ecef", "dg_step_geometry", "dg_kernel_time",
     "dg_reset_counters", "dg_launch_count", "dg_abi_version", "Geolocator",
+    "dg_cost_surface_noalloc", "dg_noalloc_last_error", "DG_NOALLOC_SCRATCH_BYTES",
     "DG_OK", "DG_EINVAL", "DG_ENOMEM", "DG_ECUDA", "DG_ESTATE", "DG_ETIMEOUT", "DG_EUNSUPPORTED",
     "DG_IQ_C64", "DG_IQ_CI16", "DG_IQ_CI8", "DG_DELAY_INTEGER", "DG_DELAY_LAGRANGE4",
     "DG_ACC_POWER", "DG_ACC_MAG", "DG_PREC_FP32", "DG_PREC_FP64", "DG_ALGO_DIRECT",
@@ -47,8 +48,10 @@ _ALGO = {"direct": DG_ALGO_DIRECT}
 EXPORTED_SYMBOLS = [
     "dg_options_default", "dg_create", "dg_load_capture", "dg_cost_surface", "dg_argmax_refine",
     "dg_sync", "dg_destroy", "dg_last_error", "dg_grid_ecef", "dg_step_geometry", "dg_kernel_time",
-    "dg_reset_counters", "dg_launch_count", "dg_abi_version",
+    "dg_reset_counters", "dg_launch_count", "dg_abi_version", "dg_cost_surface_noalloc",
+    "dg_noalloc_last_error",
 ]
+DG_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
 
 class DGError(RuntimeError):
@@ -127,6 +130,11 @@ def lib():
             L.dg_launch_count.restype = i64
             L.dg_abi_version.argtypes = []
             L.dg_abi_version.restype = i32
+            L.dg_cost_surface_noalloc.argtypes = [C.POINTER(dg_grid), C.POINTER(dg_ephem), i32, dbl, dbl,
+                                                  i32, vp, vp, i64, C.POINTER(dg_options), vp, vp]
+            L.dg_cost_surface_noalloc.restype = C.c_int
+            L.dg_noalloc_last_error.argtypes = []
+            L.dg_noalloc_last_error.restype = C.c_char_p
             for name in ("dg_create", "dg_load_capture", "dg_cost_surface", "dg_argmax_refine",
                          "dg_sync", "dg_destroy", "dg_grid_ecef", "dg_step_geometry",
                          "dg_kernel_time", "dg_reset_counters"):
@@ -216,6 +224,27 @@ def dg_launch_count(ctx):
 
 def dg_abi_version():
     return int(lib().dg_abi_version())
+
+
+def dg_noalloc_last_error():
+    m = lib().dg_noalloc_last_error()
+    return m.decode() if m else ""
+
+
+def dg_cost_surface_noalloc(grid, ephem, fs_hz, fc_hz, fmt, y1_ptr, y2_ptr, n_samples, out_ptr,
+                            opt=None, stream=0):
+    """The allocation-free surface (see include/dg.h): captures y1/y2 and out
+    are device pointers the caller owns; nothing is allocated on the device."""
+    g = grid if isinstance(grid, dg_grid) else dg_grid.from_dict(grid)
+    eph = np.ascontiguousarray(ephem, dtype=np.float64).reshape(-1, 12)
+    arr = (dg_ephem * max(1, eph.shape[0]))()
+    C.memmove(arr, eph.ctypes.data, eph.nbytes)
+    st = lib().dg_cost_surface_noalloc(C.byref(g), arr, eph.shape[0], float(fs_hz), float(fc_hz),
+                                       int(fmt), C.c_void_p(y1_ptr), C.c_void_p(y2_ptr), int(n_samples),
+                                       C.byref(opt) if opt is not None else None, C.c_void_p(out_ptr),
+                                       C.c_void_p(int(stream)))
+    if st != DG_OK:
+        raise DGError(st, dg_noalloc_last_error())
 
 
 # ------------------------------------------------------- torch-level object
