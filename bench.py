@@ -196,6 +196,7 @@ def run_dg(a, rank, world, local_rank):
     import torch
 
     import paper_2508_06672_gb300 as P
+    from paper_2508_06672_gb300.shard import allreduce_argmax, shard_rows
 
     dist = None
     if world > 1:
@@ -204,8 +205,7 @@ def run_dg(a, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     scene, desc = workload(a.workload, rank, world, a.grid)
-    nrows = scene.grid["nlat"] // world
-    row0 = rank * nrows
+    row0, nrows = shard_rows(scene.grid["nlat"], world, rank)
     G_rank = nrows * scene.grid["nlon"]
     KN = scene.k_steps * scene.n_samples
     stream = torch.cuda.Stream(dev)
@@ -280,10 +280,14 @@ def run_dg(a, rank, world, local_rank):
         worst = worst.cpu()
     dev_s, corr_s, e2e_s = (float(x) for x in worst)
     units = world * G_rank * KN * a.steps
+    gfix = (fixes[-1]["cost"], row0 * scene.grid["nlon"] + fixes[-1]["index"])
+    if dist:
+        gfix = allreduce_argmax(*gfix)  # max-loc over the row blocks (after timing)
 
     if rank == 0:
         fix = fixes[-1]
-        centre = ((scene.grid["nlat"] // world) // 2, scene.grid["nlon"] // 2)
+        centre = (scene.grid["nlat"] // 2, scene.grid["nlon"] // 2)  # the emitter's node
+        gi, gj = divmod(int(gfix[1]), scene.grid["nlon"])
         achieved = FLOPS_PER_CAND_SAMPLE * G_rank * KN * a.steps / corr_s / 1e12
         peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
         clocks = clk.summary()
@@ -307,8 +311,8 @@ def run_dg(a, rank, world, local_rank):
                          "achieved_basis": f"{FLOPS_PER_CAND_SAMPLE} flop per candidate*sample x G*K*N per launch / CUDA-event time of the launch",
                          "launches": corr_launches, "ms_per_launch": 1e3 * corr_s / max(1, corr_launches)},
             "clocks": clocks,
-            "fix": {"i": fix["i"], "j": fix["j"], "emitter_cell": list(centre),
-                    "offset_cells": [fix["i"] - centre[0], fix["j"] - centre[1]],
+            "fix": {"i": gi, "j": gj, "emitter_cell": list(centre),
+                    "offset_cells": [gi - centre[0], gj - centre[1]],
                     "refined_latlon_deg": [fix["refined_lat_deg"], fix["refined_lon_deg"]]},
             "wall_s": t_wall,
         }
