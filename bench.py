@@ -31,6 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FLOPS_PER_CAND_SAMPLE = 14          # conj product 6 + derotation 6 + accumulation 2
+CDFT_COMBINE_FLOPS = 14             # per candidate x chunk: bin interpolation 6 + phase MAC 8
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 METRIC = "candidate·sample correlations/s"
 UNIT = "cand·samples/s"
@@ -210,7 +211,8 @@ def run_dg(a, rank, world, local_rank):
     KN = scene.k_steps * scene.n_samples
     stream = torch.cuda.Stream(dev)
     g = P.Geolocator(scene.grid, scene.ephem, scene.fs_hz, scene.fc_hz, algo=a.algo, row0=row0,
-                     nrows=nrows, timing=True, stream=stream, device=local_rank)
+                     nrows=nrows, timing=True, stream=stream, device=local_rank, chunk=a.chunk,
+                     contract=a.contract)
     y1d = torch.from_numpy(scene.y1).to(dev)
     y2d = torch.from_numpy(scene.y2).to(dev)
     y1h = torch.from_numpy(scene.y1).pin_memory()
@@ -249,7 +251,13 @@ def run_dg(a, rank, world, local_rank):
         barrier()
         t_wall = time.perf_counter() - t_wall
     step_ms = [s.elapsed_time(e) for s, e in ev]
-    corr_ms, corr_launches = g.kernel_time(P.DG_K_CORR)
+    kt = {name: g.kernel_time(cls) for name, cls in (("corr", P.DG_K_CORR), ("plan", P.DG_K_CDFT_PLAN),
+                                                     ("contract", P.DG_K_CDFT_CONTRACT),
+                                                     ("combine", P.DG_K_CDFT_COMBINE),
+                                                     ("accumulate", P.DG_K_ACCUM), ("argmax", P.DG_K_ARGMAX),
+                                                     ("refine", P.DG_K_REFINE))}
+    bucket_chunks, cand_chunks = g.cdft_work()
+    corr_ms, corr_launches = kt["corr"]
     launches = g.launch_count()
     dev_s = sum(step_ms) / 1e3
 
@@ -273,6 +281,21 @@ def run_dg(a, rank, world, local_rank):
     h2d = int(scene.y1.nbytes + scene.y2.nbytes)
     d2h = 2 * 32 + 2 * 4                           # two argmax records, two error words
 
+    if a.algo == "cdft":
+        # dominant kernel of the chunked-DFT path and its algorithmic flops per launch
+        dom = max(("contract", "combine"), key=lambda n: kt[n][0])
+        chunk = a.chunk or 256
+        flops_per_step = (8 * chunk * 64 * bucket_chunks if dom == "contract"
+                          else CDFT_COMBINE_FLOPS * cand_chunks)
+        corr_ms, corr_launches = kt[dom]
+        roof_kernel = {"contract": f"k_cdft_contract_f32 (FP32 CUDA cores, {chunk}-sample chunks x 64 bins)",
+                       "combine": "k_cdft_combine (FP32, per-candidate interpolation + chunk phase sum)"}[dom]
+        roof_basis = ({"contract": "8 flop per complex MAC x chunk x 64 bins x (lag buckets x chunks) per snapshot",
+                       "combine": f"{CDFT_COMBINE_FLOPS} flop per candidate x chunk (bin interpolation 6 + phase MAC 8)"}[dom])
+    else:
+        flops_per_step = FLOPS_PER_CAND_SAMPLE * G_rank * KN
+        roof_kernel = "k_corr_direct (FP32, integer lag, ci16)"
+        roof_basis = f"{FLOPS_PER_CAND_SAMPLE} flop per candidate*sample x G*K*N per launch"
     worst = torch.tensor([dev_s, corr_ms / 1e3, sum(e2e_ms) / 1e3], dtype=torch.float64)
     if dist:
         worst = worst.to(dev)
@@ -288,7 +311,7 @@ def run_dg(a, rank, world, local_rank):
         fix = fixes[-1]
         centre = (scene.grid["nlat"] // 2, scene.grid["nlon"] // 2)  # the emitter's node
         gi, gj = divmod(int(gfix[1]), scene.grid["nlon"])
-        achieved = FLOPS_PER_CAND_SAMPLE * G_rank * KN * a.steps / corr_s / 1e12
+        achieved = flops_per_step * a.steps / corr_s / 1e12
         peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
         clocks = clk.summary()
         line = {
@@ -298,6 +321,8 @@ def run_dg(a, rank, world, local_rank):
             "data": "synthetic",
             "config": {"workload": desc, "G": G_rank * world, "K": scene.k_steps, "N": scene.n_samples,
                        "fmt": scene.fmt, "delay": "integer", "algo": a.algo, "acc": "power",
+                       "chunk": (a.chunk or 256) if a.algo == "cdft" else None,
+                       "contract": a.contract if a.algo == "cdft" else None,
                        "refine": f"{REFINE_SPACING_M:g} m spacing, +-{REFINE_WINDOW_M:g} m",
                        "l2": "flushed between timed steps (256 MB write outside the events)",
                        "parallelism": f"grid rows sharded over {world} GPU(s)", "seed": scene.meta["seed"]},
@@ -306,10 +331,11 @@ def run_dg(a, rank, world, local_rank):
             "gpu_launches": int(launches),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "k_corr_direct (FP32, integer lag, ci16)",
+                         "kernel": roof_kernel,
                          "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
-                         "achieved_basis": f"{FLOPS_PER_CAND_SAMPLE} flop per candidate*sample x G*K*N per launch / CUDA-event time of the launch",
+                         "achieved_basis": roof_basis + " / CUDA-event time of the launches",
                          "launches": corr_launches, "ms_per_launch": 1e3 * corr_s / max(1, corr_launches)},
+            "kernel_ms_per_step": {n: v[0] / a.steps for n, v in kt.items() if v[1]},
             "clocks": clocks,
             "fix": {"i": gi, "j": gj, "emitter_cell": list(centre),
                     "offset_cells": [gi - centre[0], gj - centre[1]],
@@ -340,7 +366,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["dg", "reference"], default="dg")
     ap.add_argument("--workload", choices=["mid", "tiny", "large"], default="mid")
-    ap.add_argument("--algo", default="direct")
+    ap.add_argument("--algo", choices=["direct", "cdft"], default="direct")
+    ap.add_argument("--chunk", type=int, default=0, help="CDFT samples per chunk (0 = 256)")
+    ap.add_argument("--contract", choices=["fp32", "bf16", "fp16"], default="fp32")
     ap.add_argument("--grid", type=int, default=0, help="override the grid to GRID x GRID nodes")
     ap.add_argument("--cpu-baseline-s", type=float, default=15.0)
     ap.add_argument("--reference-step-s", type=float, default=6.0)

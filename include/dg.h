@@ -65,8 +65,20 @@ enum { DG_ACC_POWER = 0, DG_ACC_MAG = 1 };
 enum { DG_PREC_FP32 = 0, DG_PREC_FP64 = 1 };
 
 /* Correlation algorithm. DIRECT evaluates Eq. 11 sample by sample for every
- * candidate. */
-enum { DG_ALGO_DIRECT = 0 };
+ * candidate. CDFT (integer delay only) groups the candidates of a snapshot by
+ * their integer lag L (Eq. 9): all of them share the lag product
+ * z_L[n] = y1[n] conj(y2[n + L]), so Eq. 11 becomes, per lag, a DFT of z_L
+ * in chunks of `chunk` samples at `bins` Doppler frequencies spanning that
+ * lag's FDOA range (a dense contraction), followed per candidate by a linear
+ * interpolation between bins and a sum over chunks with the FDOA phase of
+ * each chunk's first sample. Its error against the definition is bounded by
+ * the bin interpolation and by the arithmetic of the contraction
+ * (DG_CONTRACT_*). */
+enum { DG_ALGO_DIRECT = 0, DG_ALGO_CDFT = 1 };
+
+/* Arithmetic of the CDFT contraction: FP32 on CUDA cores, or BF16 / FP16
+ * tensor-core products accumulated in FP32. */
+enum { DG_CONTRACT_FP32 = 0, DG_CONTRACT_BF16 = 1, DG_CONTRACT_FP16 = 2 };
 
 typedef struct {
     double lat0_deg, lon0_deg; /* grid centre (node ((nlat-1)/2, (nlon-1)/2))  */
@@ -91,6 +103,10 @@ typedef struct {
     int32_t row0;    /* first grid row of this context's shard                */
     int32_t nrows;   /* rows in the shard; 0 = all rows from row0             */
     int32_t timing;  /* 1: time kernels with CUDA events (dg_kernel_time)     */
+    int32_t chunk;   /* CDFT: samples per chunk, a multiple of 64 in [64,4096];
+                        0 = 256                                               */
+    int32_t bins;    /* CDFT: Doppler bins per lag; 0 = 64 (the only value)   */
+    int32_t contract;/* CDFT: DG_CONTRACT_*                                   */
     int32_t reserved;
 } dg_options;
 
@@ -113,10 +129,14 @@ typedef struct {
 /* Kernel classes for dg_kernel_time: the main surface's correlation and
  * accumulation, the argmax passes, grid/geometry kernels, and everything the
  * local refinement of dg_argmax_refine launches (grid, correlation, sum). */
-enum { DG_K_CORR = 0, DG_K_ACCUM = 1, DG_K_ARGMAX = 2, DG_K_GRID = 3, DG_K_REFINE = 4, DG_K_NCLASS = 5 };
+enum { DG_K_CORR = 0, DG_K_ACCUM = 1, DG_K_ARGMAX = 2, DG_K_GRID = 3, DG_K_REFINE = 4,
+       DG_K_CDFT_PLAN = 5,      /* CDFT: lag ranges, histograms, scans, scatters */
+       DG_K_CDFT_CONTRACT = 6,  /* CDFT: the per-lag chunked DFT                 */
+       DG_K_CDFT_COMBINE = 7,   /* CDFT: per-candidate sums over chunks          */
+       DG_K_NCLASS = 8 };
 
 /* Defaults: INTEGER delay, POWER accumulation, FP32, DIRECT, whole grid, no
- * timing. o must not be NULL. */
+ * timing, CDFT chunk 256 / 64 bins / FP32 contraction. o must not be NULL. */
 void dg_options_default(dg_options *o);
 
 /* Create a context for one grid and one set of K snapshot ephemerides.
@@ -184,6 +204,12 @@ dg_status dg_step_geometry(dg_ctx *ctx, int32_t step, int32_t *lag, double *D, d
 /* Accumulated CUDA-event time of one kernel class (requires opt.timing = 1;
  * synchronises the stream). ms and launches are host pointers, may be NULL. */
 dg_status dg_kernel_time(dg_ctx *ctx, int32_t kernel_class, double *ms, int64_t *launches);
+
+/* Work units of the last CDFT surface (dg_cost_surface with DG_ALGO_CDFT),
+ * summed over snapshots: lag-bucket x chunk pairs contracted (each a
+ * chunk-by-bins complex DFT) and candidate x chunk pairs combined. Host
+ * pointers, may be NULL; zeros before the first CDFT surface. */
+dg_status dg_cdft_work(const dg_ctx *ctx, int64_t *bucket_chunks, int64_t *candidate_chunks);
 
 /* Reset the counters behind dg_kernel_time and dg_launch_count. */
 dg_status dg_reset_counters(dg_ctx *ctx);

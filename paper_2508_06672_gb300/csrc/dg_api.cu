@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -32,6 +33,20 @@ struct Step {
 struct TimedLaunch {
     int cls;
     cudaEvent_t a, b;
+};
+
+struct CdftBufs {  // chunked-DFT scratch, grown on demand
+    int *lr = nullptr;
+    size_t lr_cap = 0;
+    int *candB = nullptr, *order = nullptr;
+    double *candNu = nullptr;
+    size_t g_cap = 0;
+    int *count = nullptr, *cursor = nullptr, *offs = nullptr, *gofs = nullptr;
+    unsigned long long *nulo = nullptr, *nuhi = nullptr;
+    double *nulo_d = nullptr, *delta = nullptr;
+    size_t nb_cap = 0;
+    float2 *W = nullptr;
+    size_t w_cap = 0;
 };
 
 struct LocalGrid {  // refinement buffers, grown on demand
@@ -68,6 +83,8 @@ struct dg_ctx {
     unsigned *err_d = nullptr;
     unsigned *err_h = nullptr;          // pinned mirror
     LocalGrid loc;
+    CdftBufs cd;
+    int64_t cd_bucket_chunks = 0, cd_cand_chunks = 0;  // work of the last CDFT surface
     std::string err;
     int64_t launches = 0;
     std::vector<TimedLaunch> pending;
@@ -188,9 +205,13 @@ dg_status push_steps(dg_ctx *c)
 
 // Correlation for all snapshots over grid gd (ECEF xyz) into surf [K][G],
 // then the ordered sum into out.
+dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int64_t G, void *surf, void *out,
+                           bool refine);
+
 dg_status run_surface(dg_ctx *c, const GridDev &gd, const double *xyz, int64_t G, void *surf, void *out,
                       bool refine)
 {
+    if (c->opt.algo == DG_ALGO_CDFT) return run_surface_cdft(c, gd, xyz, G, surf, out, refine);
     dg_status st = push_steps(c);
     if (st != DG_OK) return st;
     bool same_fmt = true;
@@ -233,6 +254,134 @@ dg_status run_surface(dg_ctx *c, const GridDev &gd, const double *xyz, int64_t G
     {
         Timed t(c, refine ? DG_K_REFINE : DG_K_ACCUM);
         CK(c, launch_accumulate(surf, c->K, G, c->opt.prec, out, c->stream));
+        t.done(1);
+    }
+    CK(c, cudaMemcpyAsync(c->err_h, c->err_d, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    return DG_OK;
+}
+
+
+template <typename P>
+dg_status grow(dg_ctx *c, P **p, size_t n)
+{
+    if (*p) CK(c, cudaFreeAsync(*p, c->stream));
+    *p = nullptr;
+    CK(c, cudaMallocAsync((void **)p, sizeof(P) * (n ? n : 1), c->stream));
+    return DG_OK;
+}
+
+// Chunked-DFT surface: lag ranges of all snapshots (one launch, one small
+// device-to-host copy to size the buckets), then per snapshot the bucketing,
+// the contraction and the combine; then the ordered sum over snapshots.
+dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int64_t G, void *surf, void *out,
+                           bool refine)
+{
+    dg_status st = push_steps(c);
+    if (st != DG_OK) return st;
+    CdftBufs &b = c->cd;
+    const int M = c->opt.chunk ? c->opt.chunk : 256;
+    if (b.lr_cap < (size_t)c->K) {
+        if ((st = grow(c, &b.lr, 2 * (size_t)c->K)) != DG_OK) return st;
+        b.lr_cap = (size_t)c->K;
+    }
+    if (b.g_cap < (size_t)G) {
+        if ((st = grow(c, &b.candB, (size_t)G)) != DG_OK) return st;
+        if ((st = grow(c, &b.order, (size_t)G)) != DG_OK) return st;
+        if ((st = grow(c, &b.candNu, (size_t)G)) != DG_OK) return st;
+        b.g_cap = (size_t)G;
+    }
+    const int kplan = refine ? DG_K_REFINE : DG_K_CDFT_PLAN;
+    {
+        Timed t(c, kplan);
+        CK(c, launch_cdft_range(xyz, c->eph, c->K, G, c->fs, c->lambda, b.lr, c->err_d, c->stream));
+        t.done(2);
+    }
+    std::vector<int> lr(2 * (size_t)c->K);
+    CK(c, cudaMemcpyAsync(lr.data(), b.lr, sizeof(int) * lr.size(), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    int64_t nb_max = 1, b_max = 1;
+    for (int k = 0; k < c->K; ++k) {
+        if (lr[2 * k] <= lr[2 * k + 1]) nb_max = std::max<int64_t>(nb_max, (int64_t)lr[2 * k + 1] - lr[2 * k] + 1);
+        b_max = std::max<int64_t>(b_max, (c->steps[k].n + M - 1) / M);
+    }
+    if (nb_max > (1 << 22)) return fail(c, DG_EUNSUPPORTED, "CDFT: %lld lag buckets in one snapshot (max 4M); use DIRECT",
+                                        (long long)nb_max);
+    const size_t w_elems = (size_t)nb_max * (size_t)b_max * 64;
+    if (w_elems * sizeof(float2) > ((size_t)32 << 30))
+        return fail(c, DG_EUNSUPPORTED, "CDFT: the per-lag DFT buffer would exceed 32 GiB (%lld lags x %lld chunks); "
+                    "use a larger chunk or DIRECT", (long long)nb_max, (long long)b_max);
+    if (b.nb_cap < (size_t)nb_max) {
+        const size_t n = (size_t)nb_max;
+        if ((st = grow(c, &b.count, n)) != DG_OK) return st;
+        if ((st = grow(c, &b.cursor, n)) != DG_OK) return st;
+        if ((st = grow(c, &b.offs, n + 1)) != DG_OK) return st;
+        if ((st = grow(c, &b.gofs, n + 1)) != DG_OK) return st;
+        if ((st = grow(c, &b.nulo, n)) != DG_OK) return st;
+        if ((st = grow(c, &b.nuhi, n)) != DG_OK) return st;
+        if ((st = grow(c, &b.nulo_d, n)) != DG_OK) return st;
+        if (!b.delta && (st = grow(c, &b.delta, 1)) != DG_OK) return st;
+        b.nb_cap = n;
+    }
+    if (b.w_cap < w_elems) {
+        if ((st = grow(c, &b.W, w_elems)) != DG_OK) return st;
+        b.w_cap = w_elems;
+    }
+    if (!refine) c->cd_bucket_chunks = c->cd_cand_chunks = 0;
+    for (int k = 0; k < c->K; ++k) {
+        CdftStepArgs a{};
+        a.xyz = xyz;
+        a.eph_k = c->eph + 12 * (size_t)k;
+        a.sd_k = c->steps_d + k;
+        a.lr_k = b.lr + 2 * k;
+        a.G = G;
+        a.fs = c->fs;
+        a.lambda = c->lambda;
+        a.NB = lr[2 * k] <= lr[2 * k + 1] ? lr[2 * k + 1] - lr[2 * k] + 1 : 0;
+        a.M = M;
+        a.B = (int)((c->steps[k].n + M - 1) / M);
+        a.fmt = c->steps[k].fmt;
+        a.acc = c->opt.acc;
+        a.contract = c->opt.contract;
+        a.candB = b.candB;
+        a.candNu = b.candNu;
+        a.order = b.order;
+        a.count = b.count;
+        a.cursor = b.cursor;
+        a.nulo = b.nulo;
+        a.nuhi = b.nuhi;
+        a.offs = b.offs;
+        a.gofs = b.gofs;
+        a.nulo_d = b.nulo_d;
+        a.delta = b.delta;
+        a.W = b.W;
+        a.surf_k = (char *)surf + sizeof(float) * (size_t)G * k;
+        if (!refine) {
+            c->cd_bucket_chunks += (int64_t)a.NB * a.B;
+            c->cd_cand_chunks += G * (int64_t)a.B;
+        }
+        if (a.NB == 0) {  // no candidate with a representable lag: zero slice
+            CK(c, cudaMemsetAsync(a.surf_k, 0, sizeof(float) * (size_t)G, c->stream));
+            continue;
+        }
+        {
+            Timed t(c, kplan);
+            CK(c, launch_cdft_plan(a, c->stream));
+            t.done(3);
+        }
+        {
+            Timed t(c, refine ? DG_K_REFINE : DG_K_CDFT_CONTRACT);
+            CK(c, launch_cdft_contract(a, c->stream));
+            t.done(1);
+        }
+        {
+            Timed t(c, refine ? DG_K_REFINE : DG_K_CDFT_COMBINE);
+            CK(c, launch_cdft_combine(a, c->stream));
+            t.done(1);
+        }
+    }
+    {
+        Timed t(c, refine ? DG_K_REFINE : DG_K_ACCUM);
+        CK(c, launch_accumulate(surf, c->K, G, DG_PREC_FP32, out, c->stream));
         t.done(1);
     }
     CK(c, cudaMemcpyAsync(c->err_h, c->err_d, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
@@ -322,7 +471,17 @@ dg_status dg_create(const dg_grid *grid, const dg_ephem *eph, int32_t K, double 
     if (o.acc != DG_ACC_POWER && o.acc != DG_ACC_MAG) return fail(nullptr, DG_EINVAL, "unknown acc mode %d", o.acc);
     if (o.prec != DG_PREC_FP32 && o.prec != DG_PREC_FP64)
         return fail(nullptr, DG_EINVAL, "unknown precision %d", o.prec);
-    if (o.algo != DG_ALGO_DIRECT) return fail(nullptr, DG_EINVAL, "unknown algorithm %d", o.algo);
+    if (o.algo != DG_ALGO_DIRECT && o.algo != DG_ALGO_CDFT) return fail(nullptr, DG_EINVAL, "unknown algorithm %d", o.algo);
+    if (o.algo == DG_ALGO_CDFT) {
+        if (o.delay != DG_DELAY_INTEGER)
+            return fail(nullptr, DG_EUNSUPPORTED, "CDFT evaluates integer lags (Eq. 9) only");
+        if (o.prec != DG_PREC_FP32) return fail(nullptr, DG_EUNSUPPORTED, "CDFT writes FP32 surfaces only");
+        if (o.chunk != 0 && (o.chunk < 64 || o.chunk > 4096 || o.chunk % 64 != 0))
+            return fail(nullptr, DG_EINVAL, "chunk must be 0 or a multiple of 64 in [64, 4096]");
+        if (o.bins != 0 && o.bins != 64) return fail(nullptr, DG_EUNSUPPORTED, "bins must be 0 or 64");
+        if (o.contract != DG_CONTRACT_FP32)
+            return fail(nullptr, DG_EUNSUPPORTED, "unknown or unavailable contraction arithmetic %d", o.contract);
+    }
     if (o.row0 < 0 || o.row0 >= grid->nlat) return fail(nullptr, DG_EINVAL, "row0 outside the grid");
     if (o.nrows < 0 || o.row0 + o.nrows > grid->nlat) return fail(nullptr, DG_EINVAL, "row shard outside the grid");
     for (int k = 0; k < K; ++k)
@@ -574,6 +733,14 @@ dg_status dg_reset_counters(dg_ctx *c)
 
 int64_t dg_launch_count(const dg_ctx *c) { return c ? c->launches : -1; }
 
+dg_status dg_cdft_work(const dg_ctx *c, int64_t *bucket_chunks, int64_t *candidate_chunks)
+{
+    if (!c) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    if (bucket_chunks) *bucket_chunks = c->cd_bucket_chunks;
+    if (candidate_chunks) *candidate_chunks = c->cd_cand_chunks;
+    return DG_OK;
+}
+
 dg_status dg_destroy(dg_ctx *c)
 {
     if (!c) return DG_OK;
@@ -595,6 +762,19 @@ dg_status dg_destroy(dg_ctx *c)
     fr(c->loc.xyz);
     fr(c->loc.surf);
     fr(c->loc.cost);
+    fr(c->cd.lr);
+    fr(c->cd.candB);
+    fr(c->cd.order);
+    fr(c->cd.candNu);
+    fr(c->cd.count);
+    fr(c->cd.cursor);
+    fr(c->cd.offs);
+    fr(c->cd.gofs);
+    fr(c->cd.nulo);
+    fr(c->cd.nuhi);
+    fr(c->cd.nulo_d);
+    fr(c->cd.delta);
+    fr(c->cd.W);
     for (auto &st : c->steps) {
         fr(st.y1);
         fr(st.y2);

@@ -154,6 +154,42 @@ cudaError_t launch_corr_direct(const CorrArgs &a, cudaStream_t s);
 cudaError_t launch_accumulate(const void *surf, int K, int64_t G, int prec, void *out,
                               cudaStream_t s);
 
+// ---------------------------------------------------------------------------
+// Chunked-DFT evaluation (DG_ALGO_CDFT), csrc/dg_cdft.cu.
+// ---------------------------------------------------------------------------
+// Lag range of every snapshot: lr[2k] = min L, lr[2k+1] = max L.
+cudaError_t launch_cdft_range(const double *xyz, const double *eph, int K, int64_t G, double fs, double lambda,
+                              int *lr, unsigned *err, cudaStream_t s);
+
+struct CdftStepArgs {
+    const double *xyz;            // [3][G]
+    const double *eph_k;          // [12] of this snapshot
+    const StepDesc *sd_k;         // this snapshot's captures (device)
+    const int *lr_k;              // {min L, max L} of this snapshot (device)
+    int64_t G;
+    double fs, lambda;
+    int NB;                       // buckets = max L - min L + 1 (host copy)
+    int M, B;                     // samples per chunk, chunks
+    int fmt, acc, contract;
+    int *candB;                   // [G] bucket of each candidate
+    double *candNu;               // [G] nu of each candidate
+    int *order;                   // [G] candidates sorted by bucket
+    int *count, *cursor;          // [NB]
+    unsigned long long *nulo, *nuhi;  // [NB] ordered keys of the FDOA range
+    int *offs, *gofs;             // [NB + 1]
+    double *nulo_d;               // [NB]
+    double *delta;                // [1] bin spacing
+    float2 *W;                    // [NB][B][64]
+    void *surf_k;                 // this snapshot's slice of the surfaces (float)
+};
+
+// memsets + histogram + scan + scatter of one snapshot
+cudaError_t launch_cdft_plan(const CdftStepArgs &a, cudaStream_t s);
+// W[bucket][chunk][bin] of one snapshot
+cudaError_t launch_cdft_contract(const CdftStepArgs &a, cudaStream_t s);
+// per-candidate sums over chunks into the snapshot's surface slice
+cudaError_t launch_cdft_combine(const CdftStepArgs &a, cudaStream_t s);
+
 // Argmax record written by launch_argmax.
 struct ArgmaxResult {
     double val;

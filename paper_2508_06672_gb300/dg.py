@@ -23,11 +23,13 @@ __all__ = [
     "dg_options_default", "dg_create", "dg_load_capture", "dg_cost_surface", "dg_argmax_refine",
     "dg_sync", "dg_destroy", "dg_last_error", "dg_grid_ecef", "dg_step_geometry", "dg_kernel_time",
     "dg_reset_counters", "dg_launch_count", "dg_abi_version", "Geolocator",
-    "dg_cost_surface_noalloc", "dg_noalloc_last_error", "DG_NOALLOC_SCRATCH_BYTES",
+    "dg_cost_surface_noalloc", "dg_noalloc_last_error", "DG_NOALLOC_SCRATCH_BYTES", "dg_cdft_work",
     "DG_OK", "DG_EINVAL", "DG_ENOMEM", "DG_ECUDA", "DG_ESTATE", "DG_ETIMEOUT", "DG_EUNSUPPORTED",
     "DG_IQ_C64", "DG_IQ_CI16", "DG_IQ_CI8", "DG_DELAY_INTEGER", "DG_DELAY_LAGRANGE4",
-    "DG_ACC_POWER", "DG_ACC_MAG", "DG_PREC_FP32", "DG_PREC_FP64", "DG_ALGO_DIRECT",
+    "DG_ACC_POWER", "DG_ACC_MAG", "DG_PREC_FP32", "DG_PREC_FP64", "DG_ALGO_DIRECT", "DG_ALGO_CDFT",
+    "DG_CONTRACT_FP32", "DG_CONTRACT_BF16", "DG_CONTRACT_FP16",
     "DG_K_CORR", "DG_K_ACCUM", "DG_K_ARGMAX", "DG_K_GRID", "DG_K_REFINE", "EXPORTED_SYMBOLS",
+    "DG_K_CDFT_PLAN", "DG_K_CDFT_CONTRACT", "DG_K_CDFT_COMBINE",
 ]
 
 DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_ESTATE, DG_ETIMEOUT, DG_EUNSUPPORTED = range(7)
@@ -35,21 +37,24 @@ DG_IQ_C64, DG_IQ_CI16, DG_IQ_CI8 = 0, 1, 2
 DG_DELAY_INTEGER, DG_DELAY_LAGRANGE4 = 0, 1
 DG_ACC_POWER, DG_ACC_MAG = 0, 1
 DG_PREC_FP32, DG_PREC_FP64 = 0, 1
-DG_ALGO_DIRECT = 0
+DG_ALGO_DIRECT, DG_ALGO_CDFT = 0, 1
+DG_CONTRACT_FP32, DG_CONTRACT_BF16, DG_CONTRACT_FP16 = 0, 1, 2
 DG_K_CORR, DG_K_ACCUM, DG_K_ARGMAX, DG_K_GRID, DG_K_REFINE = 0, 1, 2, 3, 4
+DG_K_CDFT_PLAN, DG_K_CDFT_CONTRACT, DG_K_CDFT_COMBINE = 5, 6, 7
 
 _FMT = {"c64": DG_IQ_C64, "ci16": DG_IQ_CI16, "ci8": DG_IQ_CI8}
 _FMT_DTYPE = {DG_IQ_C64: np.float32, DG_IQ_CI16: np.int16, DG_IQ_CI8: np.int8}
 _DELAY = {"integer": DG_DELAY_INTEGER, "lagrange4": DG_DELAY_LAGRANGE4}
 _ACC = {"power": DG_ACC_POWER, "mag": DG_ACC_MAG}
 _PREC = {"fp32": DG_PREC_FP32, "fp64": DG_PREC_FP64}
-_ALGO = {"direct": DG_ALGO_DIRECT}
+_ALGO = {"direct": DG_ALGO_DIRECT, "cdft": DG_ALGO_CDFT}
+_CONTRACT = {"fp32": DG_CONTRACT_FP32, "bf16": DG_CONTRACT_BF16, "fp16": DG_CONTRACT_FP16}
 
 EXPORTED_SYMBOLS = [
     "dg_options_default", "dg_create", "dg_load_capture", "dg_cost_surface", "dg_argmax_refine",
     "dg_sync", "dg_destroy", "dg_last_error", "dg_grid_ecef", "dg_step_geometry", "dg_kernel_time",
     "dg_reset_counters", "dg_launch_count", "dg_abi_version", "dg_cost_surface_noalloc",
-    "dg_noalloc_last_error",
+    "dg_noalloc_last_error", "dg_cdft_work",
 ]
 DG_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
@@ -78,6 +83,7 @@ class dg_ephem(C.Structure):
 class dg_options(C.Structure):
     _fields_ = [("delay", C.c_int32), ("acc", C.c_int32), ("prec", C.c_int32), ("algo", C.c_int32),
                 ("row0", C.c_int32), ("nrows", C.c_int32), ("timing", C.c_int32),
+                ("chunk", C.c_int32), ("bins", C.c_int32), ("contract", C.c_int32),
                 ("reserved", C.c_int32)]
 
 
@@ -133,6 +139,8 @@ def lib():
             L.dg_cost_surface_noalloc.argtypes = [C.POINTER(dg_grid), C.POINTER(dg_ephem), i32, dbl, dbl,
                                                   i32, vp, vp, i64, C.POINTER(dg_options), vp, vp]
             L.dg_cost_surface_noalloc.restype = C.c_int
+            L.dg_cdft_work.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
+            L.dg_cdft_work.restype = C.c_int
             L.dg_noalloc_last_error.argtypes = []
             L.dg_noalloc_last_error.restype = C.c_char_p
             for name in ("dg_create", "dg_load_capture", "dg_cost_surface", "dg_argmax_refine",
@@ -214,6 +222,12 @@ def dg_kernel_time(ctx, kernel_class):
     return ms.value, n.value
 
 
+def dg_cdft_work(ctx):
+    a, b = C.c_int64(), C.c_int64()
+    _check(lib().dg_cdft_work(ctx, C.byref(a), C.byref(b)), ctx)
+    return a.value, b.value
+
+
 def dg_reset_counters(ctx):
     _check(lib().dg_reset_counters(ctx), ctx)
 
@@ -255,7 +269,8 @@ class Geolocator:
     torch.cuda.Stream, default: the current stream of the device)."""
 
     def __init__(self, grid, ephem, fs_hz, fc_hz, *, delay="integer", acc="power", prec="fp32",
-                 algo="direct", row0=0, nrows=0, timing=False, stream=None, device=None):
+                 algo="direct", row0=0, nrows=0, timing=False, stream=None, device=None,
+                 chunk=0, bins=0, contract="fp32"):
         import torch
 
         self.torch = torch
@@ -269,6 +284,7 @@ class Geolocator:
         self.opt.delay, self.opt.acc = _DELAY[delay], _ACC[acc]
         self.opt.prec, self.opt.algo = _PREC[prec], _ALGO[algo]
         self.opt.row0, self.opt.nrows, self.opt.timing = int(row0), int(nrows), int(bool(timing))
+        self.opt.chunk, self.opt.bins, self.opt.contract = int(chunk), int(bins), _CONTRACT[contract]
         self.nrows = int(nrows) if nrows else int(grid["nlat"]) - int(row0)
         self.nlon = int(grid["nlon"])
         self.dtype = torch.float64 if prec == "fp64" else torch.float32
@@ -349,6 +365,9 @@ class Geolocator:
 
     def launch_count(self):
         return dg_launch_count(self.ctx)
+
+    def cdft_work(self):
+        return dg_cdft_work(self.ctx)
 
     def close(self):
         if getattr(self, "ctx", None):

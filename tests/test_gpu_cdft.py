@@ -1,0 +1,104 @@
+"""Chunked-DFT evaluation (DG_ALGO_CDFT) against the CPU oracle.
+
+Same tolerances as the direct path: relative 1e-4 per point for FP32
+(floor of 1% of the mean for surfaces of one to three snapshots). The bin
+interpolation adds ~(pi M Delta)^2/8 < 1e-6 at these geometries."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+import sim
+from gpu_common import (assert_argmax_consistent, gpu_surface, lag_boundary_mask, oracle_surface, package,
+                        rel_err, torch_cuda)
+
+pytestmark = pytest.mark.gpu
+FP32_TOL = 1e-4
+
+
+@pytest.mark.parametrize("fmt", ["c64", "ci16", "ci8"])
+@pytest.mark.parametrize("acc", ["power", "mag"])
+def test_cdft_small_scenes(fmt, acc):
+    s = sim.make_scene(seed=21, fs_hz=12.5e6, n_samples=3001, k_steps=3, fmt=fmt, waveform="chirp",
+                       snr_db=-3.0, grid_n=(37, 45), grid_spacing_m=150.0)
+    am = 0 if acc == "power" else 1
+    g, c = gpu_surface(s, algo="cdft", acc=acc)
+    ref = oracle_surface(s, 0, am)
+    ok = ~lag_boundary_mask(s, np.arange(s.G))
+    assert rel_err(c.ravel()[ok], ref.ravel()[ok], 0.01) < FP32_TOL
+    g.close()
+
+
+@pytest.mark.parametrize("chunk", [64, 1024, 4096])
+def test_cdft_chunk_sizes(chunk):
+    s = sim.make_scene(seed=22, fs_hz=20e6, n_samples=9000, k_steps=2, fmt="ci8", waveform="noise",
+                       snr_db=-3.0, grid_n=(33, 29), grid_spacing_m=400.0, bw_hz=18e6)
+    g, c = gpu_surface(s, algo="cdft", chunk=chunk)
+    ref = oracle_surface(s)
+    ok = ~lag_boundary_mask(s, np.arange(s.G))
+    assert rel_err(c.ravel()[ok], ref.ravel()[ok], 0.01) < FP32_TOL
+    g.close()
+
+
+def test_cdft_mid_subgrid_full_k_n():
+    s = sim.mid(grid_n=(49, 41))
+    g, c = gpu_surface(s, algo="cdft")
+    ref = oracle_surface(s)
+    ok = ~lag_boundary_mask(s, np.arange(s.G))
+    assert rel_err(c.ravel()[ok], ref.ravel()[ok]) < FP32_TOL
+    assert_argmax_consistent(c, ref, FP32_TOL)
+    g.close()
+
+
+def _sampled(s, c, npts, seed):
+    rng = np.random.default_rng(seed)
+    am = int(np.argmax(c.ravel()))
+    nlon = s.grid["nlon"]
+    i, j = divmod(am, nlon)
+    nb = [(i + di) * nlon + (j + dj) for di in (-1, 0, 1) for dj in (-1, 0, 1)
+          if 0 <= i + di < s.grid["nlat"] and 0 <= j + dj < nlon]
+    idx = np.unique(np.concatenate([rng.integers(0, s.G, npts), nb]))
+    ref = oracle.cost_points(*oracle.scene_args(s), idx=idx)
+    ok = ~lag_boundary_mask(s, idx)
+    assert rel_err(c.ravel()[idx][ok], ref[ok]) < FP32_TOL
+    refnb = dict(zip(idx, ref))
+    assert max(nb, key=lambda p: (refnb[p], -p)) == am
+    return am
+
+
+def test_cdft_mid_full_size_sampled_and_against_direct():
+    s = sim.mid()
+    g, c = gpu_surface(s, algo="cdft")
+    _sampled(s, c, 48, 5)
+    g.close()
+    g, d = gpu_surface(s, algo="direct")
+    assert rel_err(c, d) < 2 * FP32_TOL
+    assert int(np.argmax(c.ravel())) == int(np.argmax(d.ravel()))
+    g.close()
+
+
+def test_cdft_large_full_size_sampled():
+    s = sim.large()
+    g, c = gpu_surface(s, algo="cdft")
+    _sampled(s, c, 16, 6)
+    g.close()
+
+
+def test_cdft_refine_and_unsupported_options():
+    torch = torch_cuda()
+    P = package()
+    s = sim.tiny(grid_n=41)
+    g, _ = gpu_surface(s, algo="cdft")
+    cost = g.cost_surface()
+    fix = g.argmax_refine(cost, 100.0, 1000.0)
+    ref = oracle_surface(s)
+    am = assert_argmax_consistent(cost.cpu().numpy(), ref, FP32_TOL)
+    lg = oracle.refine_grid(s.grid, fix["index"], 100.0, 1000.0)
+    lref = oracle.cost_surface(lg, s.ephem, s.fs_hz, s.fc_hz, s.y1, s.y2)
+    ri = fix["ri"] * lg["nlon"] + fix["rj"]
+    assert lref.ravel()[ri] >= lref.max() * (1 - 2 * FP32_TOL)
+    g.close()
+    for kw in (dict(delay="lagrange4"), dict(prec="fp64"), dict(chunk=100), dict(bins=32)):
+        with pytest.raises(P.DGError):
+            P.Geolocator(s.grid, s.ephem, s.fs_hz, s.fc_hz, algo="cdft", **kw)
