@@ -368,7 +368,7 @@ def main():
     ap.add_argument("--workload", choices=["mid", "tiny", "large"], default="mid")
     ap.add_argument("--algo", choices=["direct", "cdft"], default="direct")
     ap.add_argument("--chunk", type=int, default=0, help="CDFT samples per chunk (0 = 256)")
-    ap.add_argument("--contract", choices=["fp32", "bf16", "fp16"], default="fp32")
+    ap.add_argument("--contract", choices=["fp32", "bf16", "fp16", "bf16x3", "fp16x3"], default="fp32")
     ap.add_argument("--grid", type=int, default=0, help="override the grid to GRID x GRID nodes")
     ap.add_argument("--cpu-baseline-s", type=float, default=15.0)
     ap.add_argument("--reference-step-s", type=float, default=6.0)

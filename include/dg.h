@@ -76,9 +76,15 @@ enum { DG_PREC_FP32 = 0, DG_PREC_FP64 = 1 };
  * (DG_CONTRACT_*). */
 enum { DG_ALGO_DIRECT = 0, DG_ALGO_CDFT = 1 };
 
-/* Arithmetic of the CDFT contraction: FP32 on CUDA cores, or BF16 / FP16
- * tensor-core products accumulated in FP32. */
-enum { DG_CONTRACT_FP32 = 0, DG_CONTRACT_BF16 = 1, DG_CONTRACT_FP16 = 2 };
+/* Arithmetic of the CDFT contraction: FP32 on CUDA cores, or 16-bit
+ * tensor-core products accumulated in FP32. BF16 / FP16 round the lag products
+ * and the DFT matrix once to 16 bits. The X3 forms split each into a 16-bit
+ * high part and a 16-bit residual and add three products (hi*hi + lo*hi +
+ * hi*lo), leaving an error of about three unit roundoffs squared. FP16 forms
+ * scale int16 lag products by 2^-16 into range; c64 captures must keep
+ * |y1||y2| below 6e4 for them. */
+enum { DG_CONTRACT_FP32 = 0, DG_CONTRACT_BF16 = 1, DG_CONTRACT_FP16 = 2, DG_CONTRACT_BF16X3 = 3,
+       DG_CONTRACT_FP16X3 = 4 };
 
 typedef struct {
     double lat0_deg, lon0_deg; /* grid centre (node ((nlat-1)/2, (nlon-1)/2))  */

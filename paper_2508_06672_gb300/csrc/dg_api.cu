@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <algorithm>
+#include <climits>
 #include <cstring>
 #include <new>
 #include <string>
@@ -36,17 +37,28 @@ struct TimedLaunch {
 };
 
 struct CdftBufs {  // chunked-DFT scratch, grown on demand
-    int *lr = nullptr;
-    size_t lr_cap = 0;
-    int *candB = nullptr, *order = nullptr;
-    double *candNu = nullptr;
-    size_t g_cap = 0;
-    int *count = nullptr, *cursor = nullptr, *offs = nullptr, *gofs = nullptr;
-    unsigned long long *nulo = nullptr, *nuhi = nullptr;
-    double *nulo_d = nullptr, *delta = nullptr;
+    int *lr = nullptr, *bbase = nullptr, *gbase = nullptr;
+    unsigned *nur = nullptr;
+    float *nubase = nullptr;
+    size_t s_cap = 0;
+    int *candL = nullptr, *order = nullptr;
+    float *candNu = nullptr;
+    size_t sg_cap = 0;
+    float *xyzf = nullptr;
+    size_t xyzf_cap = 0;
+    float *ephf = nullptr;
+    size_t ephf_cap = 0;
+    int *count = nullptr, *offs = nullptr, *gofs = nullptr, *subcnt = nullptr;
     size_t nb_cap = 0;
-    float2 *W = nullptr;
+    float *delta = nullptr;
+    float2 *V = nullptr;
+    size_t v_cap = 0;
+    float *W = nullptr;
     size_t w_cap = 0;
+    int *tbase = nullptr;
+    size_t tbase_cap = 0;
+    void *btab = nullptr;
+    size_t btab_cap = 0;
 };
 
 struct LocalGrid {  // refinement buffers, grown on demand
@@ -165,10 +177,17 @@ dg_status check_latched(dg_ctx *c)
     if (e) {
         *c->err_h = 0;
         cudaMemsetAsync(c->err_d, 0, sizeof(unsigned), c->stream);
+        if (e & ERR_TIMEOUT)
+            return fail(c, DG_ETIMEOUT, "a tensor-core pipeline wait ran out of its iteration limit; the "
+                        "affected surface values are not valid");
         if (e & ERR_NU_RANGE)
             return fail(c, DG_EUNSUPPORTED,
                         "a candidate's FDOA exceeds 0.2 fs (|dfreq/fs| > 0.2); the correlation "
                         "kernels do not handle it");
+        if (e & ERR_BIN_SPACING)
+            return fail(c, DG_EUNSUPPORTED,
+                        "CDFT: a snapshot's FDOA span is too wide for its chunk (chunk x bin spacing > 4e-3 "
+                        "cycles); use a shorter chunk or DIRECT");
         return fail(c, DG_EUNSUPPORTED, "a candidate's lag |D| exceeds 1e9 samples");
     }
     return DG_OK;
@@ -270,114 +289,213 @@ dg_status grow(dg_ctx *c, P **p, size_t n)
     return DG_OK;
 }
 
-// Chunked-DFT surface: lag ranges of all snapshots (one launch, one small
-// device-to-host copy to size the buckets), then per snapshot the bucketing,
-// the contraction and the combine; then the ordered sum over snapshots.
+// Budget for the per-(candidate, snapshot) arrays of one CDFT batch.
+constexpr size_t kCdftBatchBytes = (size_t)3 << 30;
+
+// Chunked-DFT surface. Snapshots are processed in batches (same IQ format,
+// per-(candidate, snapshot) arrays within kCdftBatchBytes); per batch: the
+// geometry pass, one small device-to-host copy of the lag ranges to size the
+// buckets, the plan, the contraction and the combine. Then the ordered sum.
 dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int64_t G, void *surf, void *out,
                            bool refine)
 {
     dg_status st = push_steps(c);
     if (st != DG_OK) return st;
+    for (int k = 0; k < c->K; ++k)
+        if (c->steps[k].n > (1 << 24))
+            return fail(c, DG_EUNSUPPORTED, "CDFT: snapshots longer than 2^24 samples are not supported; use DIRECT");
     CdftBufs &b = c->cd;
     const int M = c->opt.chunk ? c->opt.chunk : 256;
-    if (b.lr_cap < (size_t)c->K) {
-        if ((st = grow(c, &b.lr, 2 * (size_t)c->K)) != DG_OK) return st;
-        b.lr_cap = (size_t)c->K;
+    int Bmax = 1;
+    for (int k = 0; k < c->K; ++k) Bmax = std::max<int>(Bmax, (int)((c->steps[k].n + M - 1) / M));
+    const int s_max = (int)std::max<int64_t>(1, std::min<int64_t>(c->K, (int64_t)(kCdftBatchBytes / (12 * (size_t)G))));
+    if (b.s_cap < (size_t)s_max) {
+        if ((st = grow(c, &b.lr, 2 * (size_t)s_max)) != DG_OK) return st;
+        if ((st = grow(c, &b.bbase, (size_t)s_max + 1)) != DG_OK) return st;
+        if ((st = grow(c, &b.gbase, (size_t)s_max + 1)) != DG_OK) return st;
+        if ((st = grow(c, &b.delta, (size_t)s_max)) != DG_OK) return st;
+        if ((st = grow(c, &b.nubase, (size_t)s_max)) != DG_OK) return st;
+        if ((st = grow(c, &b.nur, 2 * (size_t)s_max)) != DG_OK) return st;
+        b.s_cap = (size_t)s_max;
     }
-    if (b.g_cap < (size_t)G) {
-        if ((st = grow(c, &b.candB, (size_t)G)) != DG_OK) return st;
-        if ((st = grow(c, &b.order, (size_t)G)) != DG_OK) return st;
-        if ((st = grow(c, &b.candNu, (size_t)G)) != DG_OK) return st;
-        b.g_cap = (size_t)G;
+    if (b.sg_cap < (size_t)s_max * G) {
+        if ((st = grow(c, &b.candL, (size_t)s_max * G)) != DG_OK) return st;
+        if ((st = grow(c, &b.candNu, (size_t)s_max * G)) != DG_OK) return st;
+        if ((st = grow(c, &b.order, (size_t)s_max * G)) != DG_OK) return st;
+        b.sg_cap = (size_t)s_max * G;
+    }
+    if (b.v_cap < (size_t)s_max * M * 64) {
+        if ((st = grow(c, &b.V, (size_t)s_max * M * 64)) != DG_OK) return st;
+        b.v_cap = (size_t)s_max * M * 64;
     }
     const int kplan = refine ? DG_K_REFINE : DG_K_CDFT_PLAN;
+    if (!refine) c->cd_bucket_chunks = c->cd_cand_chunks = 0;
+    // constants of the geometry as double-float (hi, lo) pairs
+    auto split = [](double d, float &h, float &l) {
+        h = (float)d;
+        l = (float)(d - (double)h);
+    };
+    if (b.ephf_cap < (size_t)c->K) {
+        if ((st = grow(c, &b.ephf, 24 * (size_t)c->K)) != DG_OK) return st;
+        b.ephf_cap = (size_t)c->K;
+        std::vector<float> ef(24 * (size_t)c->K);
+        for (int k = 0; k < c->K; ++k) {
+            const double *v = &c->eph_host[k].p1[0];
+            for (int t = 0; t < 12; ++t) split(v[t], ef[24 * k + 2 * t], ef[24 * k + 2 * t + 1]);
+        }
+        // pageable source: staged before the call returns
+        CK(c, cudaMemcpyAsync(b.ephf, ef.data(), sizeof(float) * ef.size(), cudaMemcpyHostToDevice, c->stream));
+    }
+    if (b.xyzf_cap < (size_t)G) {
+        if ((st = grow(c, &b.xyzf, 6 * (size_t)G)) != DG_OK) return st;
+        b.xyzf_cap = (size_t)G;
+    }
     {
         Timed t(c, kplan);
-        CK(c, launch_cdft_range(xyz, c->eph, c->K, G, c->fs, c->lambda, b.lr, c->err_d, c->stream));
-        t.done(2);
+        CK(c, launch_ecef_split(xyz, G, b.xyzf, c->stream));
+        t.done(1);
     }
-    std::vector<int> lr(2 * (size_t)c->K);
-    CK(c, cudaMemcpyAsync(lr.data(), b.lr, sizeof(int) * lr.size(), cudaMemcpyDeviceToHost, c->stream));
-    CK(c, cudaStreamSynchronize(c->stream));
-    int64_t nb_max = 1, b_max = 1;
-    for (int k = 0; k < c->K; ++k) {
-        if (lr[2 * k] <= lr[2 * k + 1]) nb_max = std::max<int64_t>(nb_max, (int64_t)lr[2 * k + 1] - lr[2 * k] + 1);
-        b_max = std::max<int64_t>(b_max, (c->steps[k].n + M - 1) / M);
+    std::vector<int> lr(2 * (size_t)s_max), bbase(s_max + 1), gbase(s_max + 1), tbase(s_max + 1);
+    const bool mma = c->opt.contract != DG_CONTRACT_FP32;
+    if (mma) {
+        const size_t bt = (size_t)s_max * cdft_btab_bytes(c->opt.contract, M);
+        if (b.tbase_cap < (size_t)s_max + 1) {
+            if ((st = grow(c, &b.tbase, (size_t)s_max + 1)) != DG_OK) return st;
+            b.tbase_cap = (size_t)s_max + 1;
+        }
+        if (b.btab_cap < bt) {
+            unsigned char *p = reinterpret_cast<unsigned char *>(b.btab);
+            if ((st = grow(c, &p, bt)) != DG_OK) return st;
+            b.btab = p;
+            b.btab_cap = bt;
+        }
     }
-    if (nb_max > (1 << 22)) return fail(c, DG_EUNSUPPORTED, "CDFT: %lld lag buckets in one snapshot (max 4M); use DIRECT",
-                                        (long long)nb_max);
-    const size_t w_elems = (size_t)nb_max * (size_t)b_max * 64;
-    if (w_elems * sizeof(float2) > ((size_t)32 << 30))
-        return fail(c, DG_EUNSUPPORTED, "CDFT: the per-lag DFT buffer would exceed 32 GiB (%lld lags x %lld chunks); "
-                    "use a larger chunk or DIRECT", (long long)nb_max, (long long)b_max);
-    if (b.nb_cap < (size_t)nb_max) {
-        const size_t n = (size_t)nb_max;
-        if ((st = grow(c, &b.count, n)) != DG_OK) return st;
-        if ((st = grow(c, &b.cursor, n)) != DG_OK) return st;
-        if ((st = grow(c, &b.offs, n + 1)) != DG_OK) return st;
-        if ((st = grow(c, &b.gofs, n + 1)) != DG_OK) return st;
-        if ((st = grow(c, &b.nulo, n)) != DG_OK) return st;
-        if ((st = grow(c, &b.nuhi, n)) != DG_OK) return st;
-        if ((st = grow(c, &b.nulo_d, n)) != DG_OK) return st;
-        if (!b.delta && (st = grow(c, &b.delta, 1)) != DG_OK) return st;
-        b.nb_cap = n;
-    }
-    if (b.w_cap < w_elems) {
-        if ((st = grow(c, &b.W, w_elems)) != DG_OK) return st;
-        b.w_cap = w_elems;
-    }
-    if (!refine) c->cd_bucket_chunks = c->cd_cand_chunks = 0;
-    for (int k = 0; k < c->K; ++k) {
-        CdftStepArgs a{};
+    for (int k0 = 0; k0 < c->K;) {
+        int S = 1;  // batch: same format, at most s_max snapshots
+        while (k0 + S < c->K && S < s_max && c->steps[k0 + S].fmt == c->steps[k0].fmt) ++S;
+        CdftBatch a{};
         a.xyz = xyz;
-        a.eph_k = c->eph + 12 * (size_t)k;
-        a.sd_k = c->steps_d + k;
-        a.lr_k = b.lr + 2 * k;
+        a.xyzf = b.xyzf;
+        a.ephf = b.ephf + 24 * (size_t)k0;
+        split(c->fs, a.fs_hi, a.fs_lo);
+        split(c->lambda, a.lam_hi, a.lam_lo);
+        split(kC, a.c_hi, a.c_lo);
+        a.eph = c->eph + 12 * (size_t)k0;
+        a.sd = c->steps_d + k0;
+        a.S = S;
+        a.k0 = k0;
         a.G = G;
+        a.nrows = gd.nrows;
+        a.nlon = gd.nlon;
         a.fs = c->fs;
         a.lambda = c->lambda;
-        a.NB = lr[2 * k] <= lr[2 * k + 1] ? lr[2 * k + 1] - lr[2 * k] + 1 : 0;
         a.M = M;
-        a.B = (int)((c->steps[k].n + M - 1) / M);
-        a.fmt = c->steps[k].fmt;
+        a.Bmax = Bmax;
         a.acc = c->opt.acc;
-        a.contract = c->opt.contract;
-        a.candB = b.candB;
+        a.err = c->err_d;
+        a.lr = b.lr;
+        a.nur = b.nur;
+        a.nubase = b.nubase;
+        a.bbase = b.bbase;
+        a.gbase = b.gbase;
+        a.candL = b.candL;
         a.candNu = b.candNu;
         a.order = b.order;
+        a.delta = b.delta;
+        a.V = b.V;
+        {
+            Timed t(c, kplan);
+            CK(c, launch_cdft_geo(a, c->stream));
+            t.done(2);
+        }
+        CK(c, cudaMemcpyAsync(lr.data(), b.lr, sizeof(int) * 2 * (size_t)S, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        int64_t nbt = 0, groups = 0;
+        for (int s = 0; s < S; ++s) {
+            const int64_t nb = lr[2 * s] <= lr[2 * s + 1] ? (int64_t)lr[2 * s + 1] - lr[2 * s] + 1 : 0;
+            bbase[s] = (int)nbt;
+            gbase[s] = (int)groups;
+            nbt += nb;
+            groups += nb ? G / kCdftCombineThreads + nb + 1 : 0;
+            if (!refine) {
+                const int64_t B = (c->steps[k0 + s].n + M - 1) / M;
+                c->cd_bucket_chunks += nb * B;
+                c->cd_cand_chunks += G * B;
+            }
+        }
+        bbase[S] = (int)nbt;
+        gbase[S] = (int)groups;
+        int64_t tiles = 0;  // tensor-core tiles: 128 (lag, chunk) rows each
+        for (int s = 0; s < S; ++s) {
+            tbase[s] = (int)tiles;
+            const int64_t nb = (int64_t)bbase[s + 1] - bbase[s];
+            tiles += (nb * ((c->steps[k0 + s].n + M - 1) / M) + 127) / 128;
+        }
+        tbase[S] = (int)tiles;
+        if (nbt > ((int64_t)1 << 26) || groups > INT_MAX)
+            return fail(c, DG_EUNSUPPORTED, "CDFT: %lld lag buckets in one batch; use DIRECT", (long long)nbt);
+        const size_t w_elems = (size_t)std::max<int64_t>(nbt, 1) * (size_t)Bmax * 128;
+        if (w_elems * sizeof(float) > ((size_t)48 << 30))
+            return fail(c, DG_EUNSUPPORTED, "CDFT: the per-lag DFT buffer would exceed 48 GiB (%lld lags x %d chunks); "
+                        "use a larger chunk or DIRECT", (long long)nbt, Bmax);
+        if (b.nb_cap < (size_t)std::max<int64_t>(nbt, 1)) {
+            const size_t n = (size_t)std::max<int64_t>(nbt, 1);
+            if ((st = grow(c, &b.count, n)) != DG_OK) return st;
+            if ((st = grow(c, &b.offs, n)) != DG_OK) return st;
+            if ((st = grow(c, &b.gofs, n)) != DG_OK) return st;
+            if ((st = grow(c, &b.subcnt, 64 * n)) != DG_OK) return st;
+            b.nb_cap = n;
+        }
+        if (b.w_cap < w_elems) {
+            if ((st = grow(c, &b.W, w_elems)) != DG_OK) return st;
+            b.w_cap = w_elems;
+        }
         a.count = b.count;
-        a.cursor = b.cursor;
-        a.nulo = b.nulo;
-        a.nuhi = b.nuhi;
         a.offs = b.offs;
         a.gofs = b.gofs;
-        a.nulo_d = b.nulo_d;
-        a.delta = b.delta;
+        a.subcnt = b.subcnt;
         a.W = b.W;
-        a.surf_k = (char *)surf + sizeof(float) * (size_t)G * k;
-        if (!refine) {
-            c->cd_bucket_chunks += (int64_t)a.NB * a.B;
-            c->cd_cand_chunks += G * (int64_t)a.B;
+        CK(c, cudaMemcpyAsync(b.bbase, bbase.data(), sizeof(int) * (S + 1), cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(b.gbase, gbase.data(), sizeof(int) * (S + 1), cudaMemcpyHostToDevice, c->stream));
+        if (mma) {
+            CK(c, cudaMemcpyAsync(b.tbase, tbase.data(), sizeof(int) * (S + 1), cudaMemcpyHostToDevice, c->stream));
+            a.tbase = b.tbase;
+            a.btab = b.btab;
+            // FP16 needs the lag products inside its range: int16 products reach 2^31
+            const int f = c->steps[k0].fmt;
+            const bool fp16 = c->opt.contract == DG_CONTRACT_FP16 || c->opt.contract == DG_CONTRACT_FP16X3;
+            a.zscale = (fp16 && f == DG_IQ_CI16) ? 1.0f / 65536.0f : 1.0f;
         }
-        if (a.NB == 0) {  // no candidate with a representable lag: zero slice
-            CK(c, cudaMemsetAsync(a.surf_k, 0, sizeof(float) * (size_t)G, c->stream));
+        float *surf_f = reinterpret_cast<float *>(surf);
+        if (nbt == 0) {  // no node with a representable lag in the whole batch
+            CK(c, cudaMemsetAsync(surf_f + (size_t)k0 * G, 0, sizeof(float) * (size_t)G * S, c->stream));
+            k0 += S;
             continue;
         }
         {
             Timed t(c, kplan);
-            CK(c, launch_cdft_plan(a, c->stream));
-            t.done(3);
+            CK(c, launch_cdft_plan(a, (int)nbt, c->stream));
+            t.done(6);
         }
         {
             Timed t(c, refine ? DG_K_REFINE : DG_K_CDFT_CONTRACT);
-            CK(c, launch_cdft_contract(a, c->stream));
-            t.done(1);
+            if (mma) {
+                CK(c, launch_cdft_btab(a, c->opt.contract, b.btab, c->stream));
+                CK(c, launch_cdft_contract_mma(a, tbase[S], c->steps[k0].fmt, c->opt.contract, c->stream));
+                t.done(2);
+            } else {
+                CK(c, launch_cdft_contract_fp32(a, (int)nbt, c->steps[k0].fmt, c->stream));
+                t.done(1);
+            }
         }
         {
             Timed t(c, refine ? DG_K_REFINE : DG_K_CDFT_COMBINE);
-            CK(c, launch_cdft_combine(a, c->stream));
+            CK(c, launch_cdft_combine(a, (int)groups, surf_f, c->stream));
             t.done(1);
         }
+        // lr, bbase and gbase are rewritten by the next batch only after its
+        // geometry pass has been synchronised, so reuse is ordered.
+        k0 += S;
     }
     {
         Timed t(c, refine ? DG_K_REFINE : DG_K_ACCUM);
@@ -479,8 +597,8 @@ dg_status dg_create(const dg_grid *grid, const dg_ephem *eph, int32_t K, double 
         if (o.chunk != 0 && (o.chunk < 64 || o.chunk > 4096 || o.chunk % 64 != 0))
             return fail(nullptr, DG_EINVAL, "chunk must be 0 or a multiple of 64 in [64, 4096]");
         if (o.bins != 0 && o.bins != 64) return fail(nullptr, DG_EUNSUPPORTED, "bins must be 0 or 64");
-        if (o.contract != DG_CONTRACT_FP32)
-            return fail(nullptr, DG_EUNSUPPORTED, "unknown or unavailable contraction arithmetic %d", o.contract);
+        if (o.contract < DG_CONTRACT_FP32 || o.contract > DG_CONTRACT_FP16X3)
+            return fail(nullptr, DG_EINVAL, "unknown contraction arithmetic %d", o.contract);
     }
     if (o.row0 < 0 || o.row0 >= grid->nlat) return fail(nullptr, DG_EINVAL, "row0 outside the grid");
     if (o.nrows < 0 || o.row0 + o.nrows > grid->nlat) return fail(nullptr, DG_EINVAL, "row shard outside the grid");
@@ -763,18 +881,24 @@ dg_status dg_destroy(dg_ctx *c)
     fr(c->loc.surf);
     fr(c->loc.cost);
     fr(c->cd.lr);
-    fr(c->cd.candB);
+    fr(c->cd.bbase);
+    fr(c->cd.gbase);
+    fr(c->cd.candL);
     fr(c->cd.order);
     fr(c->cd.candNu);
+    fr(c->cd.xyzf);
+    fr(c->cd.ephf);
     fr(c->cd.count);
-    fr(c->cd.cursor);
     fr(c->cd.offs);
     fr(c->cd.gofs);
-    fr(c->cd.nulo);
-    fr(c->cd.nuhi);
-    fr(c->cd.nulo_d);
+    fr(c->cd.subcnt);
+    fr(c->cd.nur);
+    fr(c->cd.nubase);
     fr(c->cd.delta);
+    fr(c->cd.V);
     fr(c->cd.W);
+    fr(c->cd.tbase);
+    fr(c->cd.btab);
     for (auto &st : c->steps) {
         fr(st.y1);
         fr(st.y2);

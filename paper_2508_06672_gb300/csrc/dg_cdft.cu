@@ -5,160 +5,230 @@
 // share the lag product z_L[n] = y1[n] conj(y2[n + L]), so
 //     C_c = sum_n z_L[n] e^{j 2 pi nu_c n}
 //         = sum_b e^{j 2 pi nu_c b M} W_b(nu_c),
-//     W_b(nu) = sum_{m<M} z_L[bM + m] e^{j 2 pi nu m}        (chunk b, M samples).
-// W_b is a smooth function of nu (its spectral width is ~1/M), and the FDOAs
-// that share one lag span a narrow band [nu_lo(L), nu_hi(L)], so W_b is
-// evaluated once per lag on Q = 64 bins nu_lo + q * Delta (a dense [chunks x
-// M] x [M x Q] contraction) and each candidate interpolates linearly between
-// the two bins around its own nu_c. Delta is the widest per-lag span of the
-// snapshot divided by Q - 1; with the spans of LEO geometry (< 1e-4 cycles
-// per sample) M * Delta < 1e-3 and the interpolation error is ~(pi M Delta)^2/8.
+//     W_b(nu) = sum_{m<M} z_L[bM + m] e^{j 2 pi nu m}          (chunk b).
+// W_b is smooth in nu (spectral width ~1/M) and the FDOAs of one snapshot
+// span a narrow band [nu_min, nu_max] (LEO geometry: < 2e-4 cycles/sample),
+// so W_b is evaluated once per (lag, chunk) on Q = 64 bins
+// nu_q = nu_min + q Delta, Delta = (nu_max - nu_min) / 63 -- a dense
+// [lag x chunk rows] x [M] x [64 bins] contraction whose DFT matrix
+// V[m][q] = e^{j 2 pi nu_q m} is shared by every row of the snapshot -- and
+// each candidate interpolates linearly between the two bins around its own
+// FDOA. The interpolation error is about (pi M Delta)^2 / 6 relative; the
+// snapshot is rejected (DG_EUNSUPPORTED) if M * Delta > 4e-3.
 //
-// Pipeline per snapshot: lag range (all snapshots at once) -> histogram of
-// lags with each lag's FDOA range -> scan (bucket offsets, bin spacing) ->
-// scatter of candidate indices into lag buckets -> contraction W[L][b][q] ->
-// per-candidate combine into the snapshot's surface slice.
+// All snapshots of a batch are processed by the same launches:
+//   geo      FP64 geometry once per (candidate, snapshot): lag and FDOA kept,
+//            per-snapshot lag and FDOA ranges by atomics (the host sizes the
+//            buckets from the lag range);
+//   hist     count per (snapshot, lag) bucket, aggregated in shared memory;
+//   scan     one CTA per snapshot: bucket offsets, combine-group offsets and
+//            the snapshot's bins;
+//   subhist  count per (bucket, interpolation bin);
+//   subscan  offsets of the bins inside each bucket;
+//   scatter  candidate indices sorted by (bucket, interpolation bin), so that
+//            the warps of the combine read the same bins;
+//   contract W[bucket][chunk] = 64 bins, stored planar (64 real parts then 64
+//            imaginary parts); FP32 CUDA cores here, tensor cores in
+//            dg_cdft_mma.cu;
+//   combine  one thread per candidate: interpolate, rotate by the chunk's
+//            FDOA phase, sum over chunks, |C|^2 or |C| into the surface.
 #include <climits>
 
 #include "dg_internal.cuh"
 
 namespace dg {
 
-// Order-preserving map of doubles to unsigned 64-bit keys (for atomic min/max).
-__device__ __forceinline__ unsigned long long okey(double x)
+__device__ __forceinline__ unsigned fkey(float x)
 {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+    const unsigned b = __float_as_uint(x);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
-__device__ __forceinline__ double unokey(unsigned long long k)
+__device__ __forceinline__ float unfkey(unsigned k)
 {
-    return __longlong_as_double((long long)((k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k));
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-__device__ __forceinline__ void load_eph(const double *p, double e[12])
+// frac(nu * x) for an integer-valued x < 2^24, to ~1e-7 cycles: the product
+// is split exactly into p + e with an FMA, and p - floor(p) is exact.
+__device__ __forceinline__ float frac_mul(float nu, float x)
 {
-#pragma unroll
-    for (int t = 0; t < 12; ++t) e[t] = __ldg(p + t);
+    const float p = nu * x;
+    const float e = fmaf(nu, x, -p);
+    return (p - floorf(p)) + e;
+}
+
+// Step of the batch that owns global bucket b (bbase[s] <= b < bbase[s+1]).
+__device__ __forceinline__ int step_of(const int *base, int S, int b)
+{
+    int lo = 0, hi = S - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
 }
 
 // ---------------------------------------------------------------------------
-// 1. Lag range of every snapshot: lr[k] = {min L, max L} (init INT_MAX/INT_MIN).
+// geo: lag and FDOA of every (candidate, snapshot), lag range per snapshot.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_cdft_range(const double *__restrict__ xyz, const double *__restrict__ eph,
-                                                    int64_t G, double fs, double lambda, int *lr, unsigned *err)
+__global__ void __launch_bounds__(256) k_cdft_geo(CdftBatch a)
 {
     __shared__ int smin[8], smax[8];
-    const int k = blockIdx.y;
-    double e[12];
-    load_eph(eph + 12 * (size_t)k, e);
+    const int s = blockIdx.y;
+    dfl ed[12];
+#pragma unroll
+    for (int t = 0; t < 12; ++t) ed[t] = {__ldg(a.ephf + 24 * (size_t)s + 2 * t), __ldg(a.ephf + 24 * (size_t)s + 2 * t + 1)};
+    const dfl fsd = {a.fs_hi, a.fs_lo}, lamd = {a.lam_hi, a.lam_lo}, cd = {a.c_hi, a.c_lo};
+    __shared__ unsigned sflo[8], sfhi[8];
     int lo = INT_MAX, hi = INT_MIN;
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < G; p += (int64_t)gridDim.x * blockDim.x) {
-        double D, nu;
-        geometry(xyz[p], xyz[G + p], xyz[2 * G + p], e, fs, lambda, D, nu);
-        if (!(fabs(D) < 1.0e9)) {
-            atomicOr(err, ERR_LAG_RANGE);
-            continue;
+    unsigned flo = 0xffffffffu, fhi = 0u;
+    const float *xf = a.xyzf;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.G; p += (int64_t)gridDim.x * blockDim.x) {
+        // double-float geometry; the lag is decided by the FP64 expression
+        // (the oracle's) only when D lies within 1e-6 of a rounding boundary
+        dfl D;
+        float nuf;
+        geometry_df({xf[p], xf[a.G + p]}, {xf[2 * a.G + p], xf[3 * a.G + p]}, {xf[4 * a.G + p], xf[5 * a.G + p]},
+                    ed, fsd, lamd, cd, D, nuf);
+        int L = INT_MIN;
+        bool ok = fabsf(D.hi) < 1.0e9f;
+        if (ok && !round_df(D, L)) {
+            double e[12], D64, nu64;
+            for (int t = 0; t < 12; ++t) e[t] = a.eph[12 * (size_t)s + t];
+            geometry(a.xyz[p], a.xyz[a.G + p], a.xyz[2 * a.G + p], e, a.fs, a.lambda, D64, nu64);
+            ok = fabs(D64) < 1.0e9;
+            if (ok) L = (int)round(D64);
         }
-        const int L = (int)round(D);
-        lo = min(lo, L);
-        hi = max(hi, L);
+        if (ok) {
+            lo = min(lo, L);
+            hi = max(hi, L);
+            flo = min(flo, fkey(nuf));
+            fhi = max(fhi, fkey(nuf));
+        } else {
+            atomicOr(a.err, ERR_LAG_RANGE);
+        }
+        a.candL[(size_t)s * a.G + p] = L;
+        a.candNu[(size_t)s * a.G + p] = nuf;
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
         lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, d));
         hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, d));
+        flo = min(flo, __shfl_xor_sync(0xffffffffu, flo, d));
+        fhi = max(fhi, __shfl_xor_sync(0xffffffffu, fhi, d));
     }
     if ((threadIdx.x & 31) == 0) {
         smin[threadIdx.x >> 5] = lo;
         smax[threadIdx.x >> 5] = hi;
+        sflo[threadIdx.x >> 5] = flo;
+        sfhi[threadIdx.x >> 5] = fhi;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        for (int w = 1; w < 8; ++w) {
             lo = min(lo, smin[w]);
             hi = max(hi, smax[w]);
+            flo = min(flo, sflo[w]);
+            fhi = max(fhi, sfhi[w]);
         }
         if (lo <= hi) {
-            atomicMin(lr + 2 * k, lo);
-            atomicMax(lr + 2 * k + 1, hi);
+            atomicMin(a.lr + 2 * s, lo);
+            atomicMax(a.lr + 2 * s + 1, hi);
+            atomicMin(a.nur + 2 * s, flo);
+            atomicMax(a.nur + 2 * s + 1, fhi);
         }
     }
 }
 
-__global__ void k_cdft_range_init(int *lr, int K)
+__global__ void k_cdft_lr_init(int *lr, unsigned *nur, int S)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < K) {
-        lr[2 * k] = INT_MAX;
-        lr[2 * k + 1] = INT_MIN;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < S) {
+        lr[2 * s] = INT_MAX;
+        lr[2 * s + 1] = INT_MIN;
+        nur[2 * s] = 0xffffffffu;
+        nur[2 * s + 1] = 0u;
     }
 }
 
 // ---------------------------------------------------------------------------
-// 2. Histogram of lags and each lag's FDOA range (one snapshot).
+// hist: per bucket count and FDOA range. A CTA takes a 64 x 64 tile of grid
+// nodes of one snapshot; their lags span a few hundred values at most, so
+// counts and ranges are aggregated in shared memory first (global atomics
+// only for tiles whose lag span exceeds kHistBins).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_cdft_hist(const double *__restrict__ xyz, const double *__restrict__ eph_k,
-                                                   int64_t G, double fs, double lambda, const int *lr_k,
-                                                   int *candB, double *candNu, int *count,
-                                                   unsigned long long *nulo, unsigned long long *nuhi)
+constexpr int kHistTile = 64;     // tile side (nodes)
+constexpr int kHistBins = 2048;   // shared-memory buckets per CTA
+
+__global__ void __launch_bounds__(256) k_cdft_hist(CdftBatch a)
 {
-    double e[12];
-    load_eph(eph_k, e);
-    const int lmin = lr_k[0];
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < G; p += (int64_t)gridDim.x * blockDim.x) {
-        double D, nu;
-        geometry(xyz[p], xyz[G + p], xyz[2 * G + p], e, fs, lambda, D, nu);
-        if (!(fabs(D) < 1.0e9)) {
-            candB[p] = -1;
-            continue;
-        }
-        const int b = (int)round(D) - lmin;
-        candB[p] = b;
-        candNu[p] = nu;
-        atomicAdd(count + b, 1);
-        const unsigned long long key = okey(nu);
-        atomicMin(nulo + b, key);
-        atomicMax(nuhi + b, key);
+    __shared__ int s_cnt[kHistBins];
+    __shared__ int s_min, s_max;
+    const int s = blockIdx.y;
+    const int tiles_j = (a.nlon + kHistTile - 1) / kHistTile;
+    const int r0 = (blockIdx.x / tiles_j) * kHistTile, c0 = (blockIdx.x % tiles_j) * kHistTile;
+    const int *L = a.candL + (size_t)s * a.G;
+    const int lmin = a.lr[2 * s], bb = a.bbase[s];
+    if (threadIdx.x == 0) {
+        s_min = INT_MAX;
+        s_max = INT_MIN;
     }
+    __syncthreads();
+    int lo = INT_MAX, hi = INT_MIN;
+    for (int i = threadIdx.x; i < kHistTile * kHistTile; i += blockDim.x) {
+        const int r = r0 + i / kHistTile, c = c0 + i % kHistTile;
+        if (r >= a.nrows || c >= a.nlon) continue;
+        const int l = L[(int64_t)r * a.nlon + c];
+        if (l == INT_MIN) continue;
+        lo = min(lo, l);
+        hi = max(hi, l);
+    }
+    atomicMin(&s_min, lo);
+    atomicMax(&s_max, hi);
+    __syncthreads();
+    if (s_max < s_min) return;  // no node with a representable lag (uniform)
+    const int tlo = s_min;
+    const bool local = (int64_t)s_max - s_min < kHistBins;
+    const int span = local ? s_max - s_min + 1 : 0;
+    for (int i = threadIdx.x; i < span; i += blockDim.x) s_cnt[i] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < kHistTile * kHistTile; i += blockDim.x) {
+        const int r = r0 + i / kHistTile, c = c0 + i % kHistTile;
+        if (r >= a.nrows || c >= a.nlon) continue;
+        const int l = L[(int64_t)r * a.nlon + c];
+        if (l == INT_MIN) continue;
+        if (local)
+            atomicAdd(s_cnt + (l - tlo), 1);
+        else
+            atomicAdd(a.count + bb + l - lmin, 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < span; i += blockDim.x)
+        if (s_cnt[i]) atomicAdd(a.count + bb + tlo + i - lmin, s_cnt[i]);
 }
 
 // ---------------------------------------------------------------------------
-// 3. Scan (one CTA of 1024 threads): bucket offsets, combine-group offsets
-//    (groups of kCombineThreads candidates never straddle buckets), the
-//    per-bucket lowest FDOA as a double, and the bin spacing of the snapshot.
+// scan: one CTA (1024 threads) per snapshot.
+// offs[b]  = offset of bucket b's candidates within the snapshot's order slice
+// gofs[b]  = first combine group of bucket b, counted from the snapshot's base
+// nubase[s], delta[s] = the snapshot's bins (from its FDOA range).
 // ---------------------------------------------------------------------------
-constexpr int kCombineThreads = 256;
-
-__global__ void __launch_bounds__(1024) k_cdft_scan(int NB, const int *count, const unsigned long long *nulo,
-                                                    const unsigned long long *nuhi, int *offs, int *gofs,
-                                                    double *nulo_d, double *delta, int Q)
+__global__ void __launch_bounds__(1024) k_cdft_scan(CdftBatch a)
 {
     __shared__ int s_c[1024], s_g[1024];
-    __shared__ double s_span[32];
-    const int t = threadIdx.x;
+    const int s = blockIdx.x, t = threadIdx.x;
+    const int b_first = a.bbase[s], NB = a.bbase[s + 1] - b_first;
     const int per = (NB + 1023) / 1024;
     const int b0 = min(NB, t * per), b1 = min(NB, b0 + per);
     int c = 0, g = 0;
-    double span = 0.0;
-    for (int b = b0; b < b1; ++b) {
-        const int n = count[b];
+    for (int i = b0; i < b1; ++i) {
+        const int n = a.count[b_first + i];
         c += n;
-        g += (n + kCombineThreads - 1) / kCombineThreads;
-        if (n > 0) {
-            const double lo = unokey(nulo[b]), hi = unokey(nuhi[b]);
-            nulo_d[b] = lo;
-            span = fmax(span, hi - lo);
-        } else {
-            nulo_d[b] = 0.0;
-        }
+        g += (n + kCdftCombineThreads - 1) / kCdftCombineThreads;
     }
     s_c[t] = c;
     s_g[t] = g;
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) span = fmax(span, __shfl_xor_sync(0xffffffffu, span, d));
-    if ((t & 31) == 0) s_span[t >> 5] = span;
     __syncthreads();
-    // inclusive Hillis-Steele scan over the 1024 per-thread totals
     for (int d = 1; d < 1024; d <<= 1) {
         const int vc = t >= d ? s_c[t - d] : 0, vg = t >= d ? s_g[t - d] : 0;
         __syncthreads();
@@ -167,181 +237,229 @@ __global__ void __launch_bounds__(1024) k_cdft_scan(int NB, const int *count, co
         __syncthreads();
     }
     int oc = t ? s_c[t - 1] : 0, og = t ? s_g[t - 1] : 0;
-    for (int b = b0; b < b1; ++b) {
-        offs[b] = oc;
-        gofs[b] = og;
-        const int n = count[b];
+    for (int i = b0; i < b1; ++i) {
+        const int b = b_first + i;
+        a.offs[b] = oc;
+        a.gofs[b] = og;
+        const int n = a.count[b];
         oc += n;
-        og += (n + kCombineThreads - 1) / kCombineThreads;
-    }
-    if (t == 1023) {
-        offs[NB] = s_c[1023];
-        gofs[NB] = s_g[1023];
+        og += (n + kCdftCombineThreads - 1) / kCdftCombineThreads;
     }
     if (t == 0) {
-        double m = 0.0;
-        for (int w = 0; w < 32; ++w) m = fmax(m, s_span[w]);
-        // bins must cover [nu_lo, nu_lo + span]; keep Delta > 0 for single-FDOA lags
-        *delta = fmax(m / (double)(Q - 1), 1e-15);
+        const float lo = unfkey(a.nur[2 * s]), hi = unfkey(a.nur[2 * s + 1]);
+        // 64 bins over [lo, hi], a little wider so that rounding keeps every
+        // candidate strictly inside
+        const float d = fmaxf((hi - lo) * (1.0f + 1e-5f) / 63.0f, 1e-20f);
+        a.nubase[s] = lo;
+        a.delta[s] = d;
+        if ((double)d * (double)a.M > 4e-3) atomicOr(a.err, ERR_BIN_SPACING);
     }
 }
 
-// ---------------------------------------------------------------------------
-// 4. Scatter candidate indices into their lag buckets (order inside a bucket
-//    is arbitrary; each candidate's result does not depend on it).
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_cdft_scatter(int64_t G, const int *candB, const int *offs, int *cursor,
-                                                      int *order)
+// Interpolation bin of a candidate: q0 in [0, 62], weight t of bin q0 + 1.
+__device__ __forceinline__ int bin_of(float nu, float nubase, float delta, float &t)
 {
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < G; p += (int64_t)gridDim.x * blockDim.x) {
-        const int b = candB[p];
-        if (b < 0) continue;
-        order[offs[b] + atomicAdd(cursor + b, 1)] = (int)p;
+    const float u = (nu - nubase) / delta;
+    int q0 = (int)floorf(u);
+    q0 = max(0, min(62, q0));
+    t = u - (float)q0;
+    return q0;
+}
+
+// ---------------------------------------------------------------------------
+// subhist / subscan / scatter: counting sort by (bucket, bin).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_cdft_subhist(CdftBatch a)
+{
+    const int s = blockIdx.y;
+    const int lmin = a.lr[2 * s], bb = a.bbase[s];
+    const float delta = a.delta[s];
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.G; p += (int64_t)gridDim.x * blockDim.x) {
+        const int l = a.candL[(size_t)s * a.G + p];
+        if (l == INT_MIN) continue;
+        const int b = bb + l - lmin;
+        float t;
+        const int q0 = bin_of(a.candNu[(size_t)s * a.G + p], a.nubase[s], delta, t);
+        atomicAdd(a.subcnt + (size_t)b * 64 + q0, 1);
+    }
+}
+
+// One warp per bucket: exclusive scan of its 64 bin counts (in place).
+__global__ void __launch_bounds__(256) k_cdft_subscan(CdftBatch a, int NBT)
+{
+    const int b = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (b >= NBT) return;
+    int *c = a.subcnt + (size_t)b * 64;
+    const int v0 = c[2 * lane], v1 = c[2 * lane + 1];
+    int x = v0 + v1;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    const int ex = x - v0 - v1;
+    c[2 * lane] = ex;
+    c[2 * lane + 1] = ex + v0;
+}
+
+__global__ void __launch_bounds__(256) k_cdft_scatter(CdftBatch a)
+{
+    const int s = blockIdx.y;
+    const int lmin = a.lr[2 * s], bb = a.bbase[s];
+    const float delta = a.delta[s];
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.G; p += (int64_t)gridDim.x * blockDim.x) {
+        const int l = a.candL[(size_t)s * a.G + p];
+        if (l == INT_MIN) continue;
+        const int b = bb + l - lmin;
+        float t;
+        const int q0 = bin_of(a.candNu[(size_t)s * a.G + p], a.nubase[s], delta, t);
+        const int pos = a.offs[b] + atomicAdd(a.subcnt + (size_t)b * 64 + q0, 1);
+        a.order[(size_t)s * a.G + pos] = (int)p;
     }
 }
 
 // ---------------------------------------------------------------------------
-// 5. Contraction on CUDA cores (FP32): W[bucket][chunk][q] for 16 chunks per
-//    CTA. Thread (q, s) keeps 4 chunks' accumulators for bin q; the bin's
-//    phasor e^{j 2 pi (nu_lo + q Delta) m} runs by recurrence, restarted
-//    exactly (FP64-reduced phase) every 64 samples.
+// contract (FP32 CUDA cores): CTA = (bucket, 64 chunks); thread = 4 bins x 4
+// chunks. Per sample m of the chunk: z_L[bM + m] for the CTA's 64 chunks and
+// V[m][q] (the snapshot's table) in shared memory, 16 complex MACs per thread.
 // ---------------------------------------------------------------------------
-constexpr int kCG = 16;     // chunks per contraction CTA
-constexpr int kSub = 256;   // samples staged per pass
+constexpr int kCtChunks = 64;  // chunks per CTA
+constexpr int kCtSub = 32;     // samples per shared-memory pass
+
+__global__ void __launch_bounds__(256) k_cdft_vtable(float2 *V, const float *nubase, const float *delta, int M, int S)
+{
+    const int s = blockIdx.y;
+    const double b0 = (double)nubase[s], d = (double)delta[s];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M * 64; i += gridDim.x * blockDim.x) {
+        const int m = i >> 6, q = i & 63;
+        const double ph = (b0 + d * (double)q) * (double)m;
+        float sn, cs;
+        sincospif(2.0f * (float)(ph - floor(ph)), &sn, &cs);
+        V[(size_t)s * M * 64 + i] = make_float2(cs, sn);
+    }
+}
 
 template <int FMT>
-__global__ void __launch_bounds__(256) k_cdft_contract_f32(const StepDesc *__restrict__ sd_k, const int *lr_k,
-                                                           const int *count, const double *nulo_d, const double *delta,
-                                                           int M, int B, float2 *__restrict__ W)
+__global__ void __launch_bounds__(256) k_cdft_contract_f32(CdftBatch a)
 {
-    __shared__ float2 zs[kSub][kCG];
+    __shared__ __align__(16) float2 zs[kCtSub][kCtChunks + 1];  // +1: staging stores 2-way, not 32-way
+    __shared__ __align__(16) float2 vs[kCtSub][64];
     const int b = blockIdx.x;
-    if (count[b] == 0) return;
-    const int c0 = blockIdx.y * kCG;
-    const StepDesc sd = *sd_k;
-    const int N = sd.n;
-    const int L = lr_k[0] + b;
-    const int q = threadIdx.x & 63, s = threadIdx.x >> 6;
-    const double fq = nulo_d[b] + (double)q * (*delta);
-    float sf, cf;
-    {
-        double st, ct;
-        sincospi(2.0 * (fq - floor(fq)), &st, &ct);
-        sf = (float)st;
-        cf = (float)ct;
-    }
-    float2 acc[4];
+    if (a.count[b] == 0) return;
+    const int s = step_of(a.bbase, a.S, b);
+    const StepDesc sd = a.sd[s];
+    const int N = sd.n, M = a.M;
+    const int B = (N + M - 1) / M;
+    const int c0 = blockIdx.y * kCtChunks;
+    if (c0 >= B) return;
+    const int L = a.lr[2 * s] + (b - a.bbase[s]);
+    const float2 *V = a.V + (size_t)s * M * 64;
+    const int tq = threadIdx.x & 15, tc = threadIdx.x >> 4;  // bins 4tq..4tq+3, chunks 4tc..4tc+3
+    float2 acc[4][4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) acc[u] = make_float2(0.f, 0.f);
-    for (int m0 = 0; m0 < M; m0 += kSub) {
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    for (int m0 = 0; m0 < M; m0 += kCtSub) {
         __syncthreads();
-        for (int i = threadIdx.x; i < kSub * kCG; i += blockDim.x) {
-            const int cc = i / kSub, m = i % kSub;
-            const int n = (c0 + cc) * M + m0 + m, n2 = n + L;
+        // z' for 32 samples x 64 chunks; the modulation phase is per sample
+        for (int i = threadIdx.x; i < kCtSub * kCtChunks; i += 256) {
+            const int mm = i & (kCtSub - 1), cc = i / kCtSub;
+            const int n = (c0 + cc) * M + m0 + mm, n2 = n + L;
             float2 z = make_float2(0.f, 0.f);
-            if (c0 + cc < B && m0 + m < M && n < N && n2 >= 0 && n2 < N) {
-                const float2 a = IQ<FMT>::load(sd.y1, n), bb = IQ<FMT>::load(sd.y2, n2);
-                z.x = fmaf(a.x, bb.x, a.y * bb.y);
-                z.y = fmaf(a.y, bb.x, -a.x * bb.y);
+            if (c0 + cc < B && n < N && n2 >= 0 && n2 < N) {
+                const float2 x = IQ<FMT>::load(sd.y1, n), y = IQ<FMT>::load(sd.y2, n2);
+                z.x = fmaf(x.x, y.x, x.y * y.y);
+                z.y = fmaf(x.y, y.x, -x.x * y.y);
             }
-            zs[m][cc] = z;
+            zs[mm][cc] = z;
         }
+        for (int i = threadIdx.x; i < kCtSub * 64; i += 256) vs[i >> 6][i & 63] = V[(size_t)(m0 + (i >> 6)) * 64 + (i & 63)];
         __syncthreads();
-        const int mlen = min(kSub, M - m0);
-        for (int mm = 0; mm < mlen; mm += 64) {
-            // exact phasor at sample m0 + mm of the chunk
-            float px, py;
-            {
-                const double ph = fq * (double)(m0 + mm);
-                double st, ct;
-                sincospi(2.0 * (ph - floor(ph)), &st, &ct);
-                px = (float)ct;
-                py = (float)st;
-            }
-            const int mend = min(mm + 64, mlen);
-            for (int m = mm; m < mend; ++m) {
-                const float4 z01 = *reinterpret_cast<const float4 *>(&zs[m][4 * s]);
-                const float4 z23 = *reinterpret_cast<const float4 *>(&zs[m][4 * s + 2]);
-                acc[0].x = fmaf(z01.x, px, fmaf(-z01.y, py, acc[0].x));
-                acc[0].y = fmaf(z01.x, py, fmaf(z01.y, px, acc[0].y));
-                acc[1].x = fmaf(z01.z, px, fmaf(-z01.w, py, acc[1].x));
-                acc[1].y = fmaf(z01.z, py, fmaf(z01.w, px, acc[1].y));
-                acc[2].x = fmaf(z23.x, px, fmaf(-z23.y, py, acc[2].x));
-                acc[2].y = fmaf(z23.x, py, fmaf(z23.y, px, acc[2].y));
-                acc[3].x = fmaf(z23.z, px, fmaf(-z23.w, py, acc[3].x));
-                acc[3].y = fmaf(z23.z, py, fmaf(z23.w, px, acc[3].y));
-                const float nx = fmaf(px, cf, -py * sf);
-                py = fmaf(px, sf, py * cf);
-                px = nx;
-            }
+#pragma unroll 4
+        for (int mm = 0; mm < kCtSub; ++mm) {
+            const float2 z0 = zs[mm][4 * tc], z1 = zs[mm][4 * tc + 1], z2 = zs[mm][4 * tc + 2], z3 = zs[mm][4 * tc + 3];
+            // vs rows are 512 B and 4 tq is even: these 16-byte loads are aligned
+            const float4 v01 = *reinterpret_cast<const float4 *>(&vs[mm][4 * tq]);
+            const float4 v23 = *reinterpret_cast<const float4 *>(&vs[mm][4 * tq + 2]);
+            const float zr[4] = {z0.x, z1.x, z2.x, z3.x}, zi[4] = {z0.y, z1.y, z2.y, z3.y};
+            const float vr[4] = {v01.x, v01.z, v23.x, v23.z}, vi[4] = {v01.y, v01.w, v23.y, v23.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    acc[i][j].x = fmaf(zr[i], vr[j], fmaf(-zi[i], vi[j], acc[i][j].x));
+                    acc[i][j].y = fmaf(zr[i], vi[j], fmaf(zi[i], vr[j], acc[i][j].y));
+                }
         }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int ch = c0 + 4 * s + u;
-        if (ch < B) W[((size_t)b * B + ch) * 64 + q] = acc[u];
+    for (int i = 0; i < 4; ++i) {
+        const int ch = c0 + 4 * tc + i;
+        if (ch < B) {  // planar row: 64 real parts, then 64 imaginary parts
+            float *w = a.W + ((size_t)b * a.Bmax + ch) * 128 + 4 * tq;
+            *reinterpret_cast<float4 *>(w) = make_float4(acc[i][0].x, acc[i][1].x, acc[i][2].x, acc[i][3].x);
+            *reinterpret_cast<float4 *>(w + 64) = make_float4(acc[i][0].y, acc[i][1].y, acc[i][2].y, acc[i][3].y);
+        }
     }
 }
 
 // ---------------------------------------------------------------------------
-// 6. Combine: one thread per candidate, kCombineThreads candidates of one
-//    bucket per CTA; W of the bucket streams through shared memory in
-//    segments of kSeg chunks.
+// combine: one thread per candidate, kCdftCombineThreads candidates of one
+// bucket per CTA (sorted by interpolation bin); the bucket's W streams through
+// shared memory in segments of kSeg chunks.
 // ---------------------------------------------------------------------------
 constexpr int kSeg = 32;
 
 template <typename T>
-__global__ void __launch_bounds__(kCombineThreads) k_cdft_combine(int NB, const int *count, const int *offs,
-                                                                  const int *gofs, const int *order,
-                                                                  const double *candNu, const double *nulo_d,
-                                                                  const double *delta, const float2 *__restrict__ W,
-                                                                  int M, int B, int acc_mode, T *surf_k)
+__global__ void __launch_bounds__(kCdftCombineThreads) k_cdft_combine(CdftBatch a, T *surf)
 {
-    __shared__ float2 ws[kSeg][64];
+    // per chunk and bin q: (re q, re q+1, im q, im q+1), so that a candidate
+    // reads both neighbouring bins with one 16-byte load
+    __shared__ __align__(16) float4 ws[kSeg][64];
     const int gid = blockIdx.x;
-    if (gid >= gofs[NB]) return;
-    int lo = 0, hi = NB - 1;  // bucket b with gofs[b] <= gid < gofs[b+1]
+    const int s = step_of(a.gbase, a.S, gid);
+    const int b_first = a.bbase[s], NB = a.bbase[s + 1] - b_first;
+    const int lgid = gid - a.gbase[s];
+    if (NB == 0) return;  // uniform
+    // bucket b with gofs[b] <= lgid < gofs[b] + groups(b)
+    int lo = 0, hi = NB - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (gofs[mid] <= gid) lo = mid; else hi = mid - 1;
+        if (a.gofs[b_first + mid] <= lgid) lo = mid; else hi = mid - 1;
     }
-    const int b = lo;
-    const int j = (gid - gofs[b]) * kCombineThreads + threadIdx.x;
-    const bool active = j < count[b];
-    const int c = active ? order[offs[b] + j] : 0;
-    const double nu = active ? candNu[c] : nulo_d[b];
-    const double u = (nu - nulo_d[b]) / (*delta);
-    int q0 = (int)floor(u);
-    q0 = max(0, min(62, q0));
-    const float t = (float)(u - (double)q0);
+    const int b = b_first + lo;
+    const int n_b = a.count[b];
+    const int j = (lgid - a.gofs[b]) * kCdftCombineThreads + threadIdx.x;
+    if ((lgid - a.gofs[b]) * kCdftCombineThreads >= n_b) return;  // past the snapshot's last group (uniform)
+    const bool active = j < n_b;
+    const int c = active ? a.order[(size_t)s * a.G + a.offs[b] + j] : 0;
+    const float nuf = active ? a.candNu[(size_t)s * a.G + c] : a.nubase[s];
+    float t;
+    const int q0 = bin_of(nuf, a.nubase[s], a.delta[s], t);
     const float w0 = 1.f - t, w1 = t;
-    // e^{j 2 pi nu M}: chunk-to-chunk phase step
+    const int M = a.M;
+    const int B = (a.sd[s].n + M - 1) / M;
+    // chunk-to-chunk phase step e^{j 2 pi nu M}
     float ex, ey;
-    {
-        const double ph = nu * (double)M;
-        double st, ct;
-        sincospi(2.0 * (ph - floor(ph)), &st, &ct);
-        ex = (float)ct;
-        ey = (float)st;
-    }
-    float cx = 0.f, cy = 0.f, px = 1.f, py = 0.f;
-    const float2 *Wb = W + (size_t)b * B * 64;
+    sincospif(2.0f * frac_mul(nuf, (float)M), &ey, &ex);
+    float cx = 0.f, cy = 0.f;
+    const float *Wb = a.W + (size_t)b * a.Bmax * 128;
     for (int s0 = 0; s0 < B; s0 += kSeg) {
         const int slen = min(kSeg, B - s0);
         __syncthreads();
-        for (int i = threadIdx.x; i < slen * 64; i += kCombineThreads) ws[i >> 6][i & 63] = Wb[(size_t)s0 * 64 + i];
-        __syncthreads();
-        // exact chunk phase at the segment start
-        {
-            const double ph = nu * (double)s0 * (double)M;
-            double st, ct;
-            sincospi(2.0 * (ph - floor(ph)), &st, &ct);
-            px = (float)ct;
-            py = (float)st;
+        for (int i = threadIdx.x; i < slen * 64; i += kCdftCombineThreads) {
+            const int ch = i >> 6, q = i & 63, q1 = min(q + 1, 63);
+            const float *row = Wb + (size_t)(s0 + ch) * 128;
+            ws[ch][q] = make_float4(row[q], row[q1], row[64 + q], row[64 + q1]);
         }
+        __syncthreads();
+        float px, py;  // phase of the segment's first sample, e^{j 2 pi nu s0 M}
+        sincospif(2.0f * frac_mul(nuf, (float)s0 * (float)M), &py, &px);
+#pragma unroll 4
         for (int i = 0; i < slen; ++i) {
-            const float2 a = ws[i][q0], bb = ws[i][q0 + 1];
-            const float zx = fmaf(w0, a.x, w1 * bb.x), zy = fmaf(w0, a.y, w1 * bb.y);
+            const float4 v = ws[i][q0];
+            const float zx = fmaf(w0, v.x, w1 * v.y), zy = fmaf(w0, v.z, w1 * v.w);
             cx = fmaf(px, zx, fmaf(-py, zy, cx));
             cy = fmaf(px, zy, fmaf(py, zx, cy));
             const float nx = fmaf(px, ex, -py * ey);
@@ -350,70 +468,84 @@ __global__ void __launch_bounds__(kCombineThreads) k_cdft_combine(int NB, const 
         }
     }
     if (active) {
-        const double pw = (double)cx * cx + (double)cy * cy;
-        surf_k[c] = (T)(acc_mode == DG_ACC_POWER ? pw : sqrt(pw));
+        const float pw = fmaf(cx, cx, cy * cy);
+        surf[(size_t)(a.k0 + s) * a.G + c] = (T)(a.acc == DG_ACC_POWER ? pw : sqrtf(pw));
     }
 }
 
 // ---------------------------------------------------------------------------
 // host-side launchers
 // ---------------------------------------------------------------------------
-static unsigned grid_for(int64_t n, int per)
+static unsigned grid_for(int64_t n, int per, int cap = 152 * 16)
 {
     int64_t b = (n + per - 1) / per;
-    if (b > 152 * 16) b = 152 * 16;
+    if (b > cap) b = cap;
     return (unsigned)(b < 1 ? 1 : b);
 }
 
-cudaError_t launch_cdft_range(const double *xyz, const double *eph, int K, int64_t G, double fs, double lambda,
-                              int *lr, unsigned *err, cudaStream_t s)
+__global__ void __launch_bounds__(256) k_ecef_split(const double *__restrict__ xyz, int64_t G, float *__restrict__ xf)
 {
-    k_cdft_range_init<<<(K + 127) / 128, 128, 0, s>>>(lr, K);
-    dim3 grid(grid_for(G, 256 * 4), (unsigned)K);
-    k_cdft_range<<<grid, 256, 0, s>>>(xyz, eph, G, fs, lambda, lr, err);
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < G; p += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const dfl v = df_from(xyz[c * G + p]);
+            xf[(2 * c) * G + p] = v.hi;
+            xf[(2 * c + 1) * G + p] = v.lo;
+        }
+    }
+}
+
+cudaError_t launch_ecef_split(const double *xyz, int64_t G, float *xyzf, cudaStream_t st)
+{
+    k_ecef_split<<<grid_for(G, 256), 256, 0, st>>>(xyz, G, xyzf);
     return cudaGetLastError();
 }
 
-cudaError_t launch_cdft_plan(const CdftStepArgs &a, cudaStream_t s)
+cudaError_t launch_cdft_geo(const CdftBatch &a, cudaStream_t st)
+{
+    k_cdft_lr_init<<<(a.S + 127) / 128, 128, 0, st>>>(a.lr, a.nur, a.S);
+    dim3 grid(grid_for(a.G, 256 * 4, 152 * 8), (unsigned)a.S);
+    k_cdft_geo<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cdft_plan(const CdftBatch &a, int NBT, cudaStream_t st)
 {
     cudaError_t e;
-    if ((e = cudaMemsetAsync(a.count, 0, sizeof(int) * (size_t)a.NB, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(a.cursor, 0, sizeof(int) * (size_t)a.NB, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(a.nulo, 0xff, sizeof(unsigned long long) * (size_t)a.NB, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(a.nuhi, 0, sizeof(unsigned long long) * (size_t)a.NB, s)) != cudaSuccess) return e;
-    k_cdft_hist<<<grid_for(a.G, 256), 256, 0, s>>>(a.xyz, a.eph_k, a.G, a.fs, a.lambda, a.lr_k, a.candB, a.candNu,
-                                                    a.count, a.nulo, a.nuhi);
+    if ((e = cudaMemsetAsync(a.count, 0, sizeof(int) * (size_t)NBT, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(a.subcnt, 0, sizeof(int) * 64 * (size_t)NBT, st)) != cudaSuccess) return e;
+    const int64_t tiles = (int64_t)((a.nrows + kHistTile - 1) / kHistTile) * ((a.nlon + kHistTile - 1) / kHistTile);
+    dim3 gh((unsigned)tiles, (unsigned)a.S);
+    k_cdft_hist<<<gh, 256, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_cdft_scan<<<1, 1024, 0, s>>>(a.NB, a.count, a.nulo, a.nuhi, a.offs, a.gofs, a.nulo_d, a.delta, 64);
+    k_cdft_scan<<<a.S, 1024, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_cdft_scatter<<<grid_for(a.G, 256), 256, 0, s>>>(a.G, a.candB, a.offs, a.cursor, a.order);
+    dim3 gp(grid_for(a.G, 256 * 4, 152 * 8), (unsigned)a.S);
+    k_cdft_subhist<<<gp, 256, 0, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_cdft_subscan<<<(NBT + 7) / 8, 256, 0, st>>>(a, NBT);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_cdft_scatter<<<gp, 256, 0, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    dim3 gv(grid_for((int64_t)a.M * 64, 256, 64), (unsigned)a.S);
+    k_cdft_vtable<<<gv, 256, 0, st>>>(a.V, a.nubase, a.delta, a.M, a.S);
     return cudaGetLastError();
 }
 
-cudaError_t launch_cdft_contract(const CdftStepArgs &a, cudaStream_t s)
+cudaError_t launch_cdft_contract_fp32(const CdftBatch &a, int NBT, int fmt, cudaStream_t st)
 {
-    dim3 cg((unsigned)a.NB, (unsigned)((a.B + kCG - 1) / kCG));
-    switch (a.fmt) {
-    case DG_IQ_C64:
-        k_cdft_contract_f32<DG_IQ_C64><<<cg, 256, 0, s>>>(a.sd_k, a.lr_k, a.count, a.nulo_d, a.delta, a.M, a.B, a.W);
-        break;
-    case DG_IQ_CI16:
-        k_cdft_contract_f32<DG_IQ_CI16><<<cg, 256, 0, s>>>(a.sd_k, a.lr_k, a.count, a.nulo_d, a.delta, a.M, a.B, a.W);
-        break;
-    default:
-        k_cdft_contract_f32<DG_IQ_CI8><<<cg, 256, 0, s>>>(a.sd_k, a.lr_k, a.count, a.nulo_d, a.delta, a.M, a.B, a.W);
-        break;
+    dim3 grid((unsigned)NBT, (unsigned)((a.Bmax + kCtChunks - 1) / kCtChunks));
+    switch (fmt) {
+    case DG_IQ_C64: k_cdft_contract_f32<DG_IQ_C64><<<grid, 256, 0, st>>>(a); break;
+    case DG_IQ_CI16: k_cdft_contract_f32<DG_IQ_CI16><<<grid, 256, 0, st>>>(a); break;
+    default: k_cdft_contract_f32<DG_IQ_CI8><<<grid, 256, 0, st>>>(a); break;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_cdft_combine(const CdftStepArgs &a, cudaStream_t s)
+cudaError_t launch_cdft_combine(const CdftBatch &a, int groups, float *surf, cudaStream_t st)
 {
-    // an upper bound on the number of groups: G / 256 + one partial group per bucket
-    const int64_t groups = a.G / kCombineThreads + a.NB + 1;
-    k_cdft_combine<float><<<(unsigned)groups, kCombineThreads, 0, s>>>(
-        a.NB, a.count, a.offs, a.gofs, a.order, a.candNu, a.nulo_d, a.delta, a.W, a.M, a.B, a.acc,
-        reinterpret_cast<float *>(a.surf_k));
+    k_cdft_combine<float><<<(unsigned)groups, kCdftCombineThreads, 0, st>>>(a, surf);
     return cudaGetLastError();
 }
 

@@ -18,7 +18,7 @@ constexpr int kThreads = 256;                    // threads per correlation CTA
 constexpr int kWarps = kThreads / 32;
 
 // Error bits latched by kernels into the context's device error word.
-enum : unsigned { ERR_NU_RANGE = 1u, ERR_LAG_RANGE = 2u };
+enum : unsigned { ERR_NU_RANGE = 1u, ERR_LAG_RANGE = 2u, ERR_BIN_SPACING = 4u, ERR_TIMEOUT = 8u };
 
 // A grid (or a shard of rows of it) as the kernels see it.
 struct GridDev {
@@ -65,6 +65,108 @@ __device__ __forceinline__ void geometry(double cx, double cy, double cz, const 
     const double dtau = __ddiv_rn(__dsub_rn(rho2, rho1), kC);
     D = __dmul_rn(dtau, fs);
     nu = __ddiv_rn(__dsub_rn(f2, f1), fs);
+}
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic: a value is hi + lo with two floats (about 46
+// significant bits), built from error-free transformations (two-sum, FMA
+// products). It runs on the FP32 pipes, which on this chip are far wider than
+// FP64. Used for the per-(candidate, snapshot) geometry of the chunked-DFT
+// path; the integer lag is still decided by the FP64 expression wherever the
+// double-float value lies near a rounding boundary.
+// ---------------------------------------------------------------------------
+struct dfl {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dfl df_from(double d)
+{
+    const float h = (float)d;
+    return {h, (float)(d - (double)h)};
+}
+__device__ __forceinline__ dfl df_fast_two_sum(float a, float b)
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ dfl df_two_sum(float a, float b)
+{
+    const float s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b)
+{
+    dfl s = df_two_sum(a.hi, b.hi);
+    const dfl t = df_two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = df_fast_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return df_fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, {-b.hi, -b.lo}); }
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b)
+{
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ dfl df_div(dfl a, dfl b)
+{
+    const float q1 = a.hi / b.hi;
+    const dfl r = df_sub(a, df_mul({q1, 0.f}, b));
+    const float q2 = r.hi / b.hi;
+    const dfl r2 = df_sub(r, df_mul({q2, 0.f}, b));
+    const float q3 = r2.hi / b.hi;
+    const dfl q = df_fast_two_sum(q1, q2);
+    return df_add(q, {q3, 0.f});
+}
+__device__ __forceinline__ dfl df_sqrt(dfl a)
+{
+    const float y = sqrtf(a.hi);
+    const dfl r = df_sub(a, df_mul({y, 0.f}, {y, 0.f}));
+    return df_fast_two_sum(y, r.hi / (2.f * y));
+}
+
+// Eq. 3-10 in double-float: D = dtau * fs (samples, as hi + lo) and
+// nu = dfreq / fs. Same expression as geometry().
+__device__ __forceinline__ void geometry_df(dfl x, dfl y, dfl z, const dfl *e, dfl fs, dfl lambda, dfl c_light,
+                                            dfl &D, float &nu)
+{
+    const dfl r1x = df_sub(e[0], x), r1y = df_sub(e[1], y), r1z = df_sub(e[2], z);
+    const dfl r2x = df_sub(e[6], x), r2y = df_sub(e[7], y), r2z = df_sub(e[8], z);
+    const dfl rho1 = df_sqrt(df_add(df_add(df_mul(r1x, r1x), df_mul(r1y, r1y)), df_mul(r1z, r1z)));
+    const dfl rho2 = df_sqrt(df_add(df_add(df_mul(r2x, r2x), df_mul(r2y, r2y)), df_mul(r2z, r2z)));
+    const dfl f1 = df_div(df_add(df_add(df_mul(r1x, e[3]), df_mul(r1y, e[4])), df_mul(r1z, e[5])), df_mul(rho1, lambda));
+    const dfl f2 = df_div(df_add(df_add(df_mul(r2x, e[9]), df_mul(r2y, e[10])), df_mul(r2z, e[11])), df_mul(rho2, lambda));
+    const dfl dtau = df_div(df_sub(rho2, rho1), c_light);
+    D = df_mul(dtau, fs);
+    const dfl nud = df_div(df_sub(f1, f2), fs);  // f_i carry the minus sign of Eq. 6
+    nu = nud.hi + nud.lo;
+}
+
+// Eq. 9 on a double-float D: round half away from zero, in FP32 only.
+// Returns false (undecided) when |D| >= 2^22 or when D lies within 1e-6 of a
+// rounding boundary; the caller then decides with the FP64 expression.
+__device__ __forceinline__ bool round_df(dfl D, int &L)
+{
+    const float ah = fabsf(D.hi);
+    if (!(ah < 4194304.0f)) return false;
+    const float al = D.hi < 0.f ? -D.lo : D.lo;  // |D| = ah + al
+    float n = floorf(ah);
+    float f = (ah - n) + al;                     // ah - n is exact
+    if (f < 0.f) {
+        n -= 1.f;
+        f += 1.f;
+    } else if (f >= 1.f) {
+        n += 1.f;
+        f -= 1.f;
+    }
+    if (fabsf(f - 0.5f) < 1e-6f || f < 1e-6f || f > 1.f - 1e-6f) return false;
+    const int mag = (int)n + (f > 0.5f ? 1 : 0);
+    L = D.hi < 0.f ? -mag : mag;
+    return true;
 }
 
 // Integer lag of the delay mode: Eq. 9 (round half away from zero) or floor.
@@ -155,40 +257,55 @@ cudaError_t launch_accumulate(const void *surf, int K, int64_t G, int prec, void
                               cudaStream_t s);
 
 // ---------------------------------------------------------------------------
-// Chunked-DFT evaluation (DG_ALGO_CDFT), csrc/dg_cdft.cu.
+// Chunked-DFT evaluation (DG_ALGO_CDFT), csrc/dg_cdft.cu, csrc/dg_cdft_mma.cu.
+// A batch is S consecutive snapshots [k0, k0 + S) processed by the same
+// launches. Global bucket ids of snapshot s are bbase[s] .. bbase[s+1]-1, one
+// per lag lr[2s] .. lr[2s+1]; combine groups of snapshot s are gbase[s] ..
+// gbase[s+1]-1 (an upper bound; surplus CTAs exit).
 // ---------------------------------------------------------------------------
-// Lag range of every snapshot: lr[2k] = min L, lr[2k+1] = max L.
-cudaError_t launch_cdft_range(const double *xyz, const double *eph, int K, int64_t G, double fs, double lambda,
-                              int *lr, unsigned *err, cudaStream_t s);
+constexpr int kCdftCombineThreads = 256;
 
-struct CdftStepArgs {
+struct CdftBatch {
     const double *xyz;            // [3][G]
-    const double *eph_k;          // [12] of this snapshot
-    const StepDesc *sd_k;         // this snapshot's captures (device)
-    const int *lr_k;              // {min L, max L} of this snapshot (device)
+    const double *eph;            // [S][12] (first snapshot of the batch)
+    const StepDesc *sd;           // [S] captures
+    int S, k0;
     int64_t G;
+    int nrows, nlon;              // shard shape (G = nrows * nlon)
     double fs, lambda;
-    int NB;                       // buckets = max L - min L + 1 (host copy)
-    int M, B;                     // samples per chunk, chunks
-    int fmt, acc, contract;
-    int *candB;                   // [G] bucket of each candidate
-    double *candNu;               // [G] nu of each candidate
-    int *order;                   // [G] candidates sorted by bucket
-    int *count, *cursor;          // [NB]
-    unsigned long long *nulo, *nuhi;  // [NB] ordered keys of the FDOA range
-    int *offs, *gofs;             // [NB + 1]
-    double *nulo_d;               // [NB]
-    double *delta;                // [1] bin spacing
-    float2 *W;                    // [NB][B][64]
-    void *surf_k;                 // this snapshot's slice of the surfaces (float)
+    int M, Bmax, acc;
+    unsigned *err;
+    int *lr;                      // [S][2] lag range
+    unsigned *nur;                // [S][2] FDOA range (ordered float keys)
+    const int *bbase, *gbase;     // [S + 1] (device)
+    const float *xyzf;            // [6][G] ECEF as double-float: x hi, x lo, y hi, y lo, z hi, z lo
+    const float *ephf;            // [S][24] ephemerides as double-float (hi, lo) pairs
+    float fs_hi, fs_lo, lam_hi, lam_lo, c_hi, c_lo;  // fs, lambda, c as double-float
+    int *candL;                   // [S][G] lag (INT_MIN: not representable)
+    float *candNu;                // [S][G] FDOA / fs
+    int *order;                   // [S][G] candidates sorted by (bucket, bin)
+    int *count;                   // [NBT]
+    int *offs, *gofs;             // [NBT]
+    int *subcnt;                  // [NBT][64]
+    float *nubase, *delta;        // [S] bins nu_q = nubase + q delta
+    float2 *V;                    // [S][M][64] DFT table e^{j 2 pi nu_q m}
+    float *W;                     // [NBT][Bmax][128]: per chunk 64 bins, re[64] | im[64]
+    const int *tbase;             // [S + 1] first tensor-core tile of each snapshot (device)
+    const void *btab;             // [S][M/32][2][128 x 32] 16-bit DFT operand (tensor cores)
+    float zscale;                 // lag products are multiplied by this before 16-bit rounding
 };
 
-// memsets + histogram + scan + scatter of one snapshot
-cudaError_t launch_cdft_plan(const CdftStepArgs &a, cudaStream_t s);
-// W[bucket][chunk][bin] of one snapshot
-cudaError_t launch_cdft_contract(const CdftStepArgs &a, cudaStream_t s);
-// per-candidate sums over chunks into the snapshot's surface slice
-cudaError_t launch_cdft_combine(const CdftStepArgs &a, cudaStream_t s);
+cudaError_t launch_cdft_geo(const CdftBatch &a, cudaStream_t s);
+// xyzf[6][G] = double-float split of xyz[3][G]
+cudaError_t launch_ecef_split(const double *xyz, int64_t G, float *xyzf, cudaStream_t s);
+cudaError_t launch_cdft_plan(const CdftBatch &a, int NBT, cudaStream_t s);
+cudaError_t launch_cdft_contract_fp32(const CdftBatch &a, int NBT, int fmt, cudaStream_t s);
+cudaError_t launch_cdft_combine(const CdftBatch &a, int groups, float *surf, cudaStream_t s);
+// tensor-core contraction (dg_cdft_mma.cu): mode DG_CONTRACT_BF16 / FP16 /
+// BF16X3 / FP16X3; tiles = total 128-row tiles of the batch (tbase[S])
+cudaError_t launch_cdft_btab(const CdftBatch &a, int mode, void *btab, cudaStream_t s);
+cudaError_t launch_cdft_contract_mma(const CdftBatch &a, int tiles, int fmt, int mode, cudaStream_t s);
+size_t cdft_btab_bytes(int mode, int M);  // per snapshot
 
 // Argmax record written by launch_argmax.
 struct ArgmaxResult {

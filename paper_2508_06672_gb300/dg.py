@@ -27,7 +27,7 @@ __all__ = [
     "DG_OK", "DG_EINVAL", "DG_ENOMEM", "DG_ECUDA", "DG_ESTATE", "DG_ETIMEOUT", "DG_EUNSUPPORTED",
     "DG_IQ_C64", "DG_IQ_CI16", "DG_IQ_CI8", "DG_DELAY_INTEGER", "DG_DELAY_LAGRANGE4",
     "DG_ACC_POWER", "DG_ACC_MAG", "DG_PREC_FP32", "DG_PREC_FP64", "DG_ALGO_DIRECT", "DG_ALGO_CDFT",
-    "DG_CONTRACT_FP32", "DG_CONTRACT_BF16", "DG_CONTRACT_FP16",
+    "DG_CONTRACT_FP32", "DG_CONTRACT_BF16", "DG_CONTRACT_FP16", "DG_CONTRACT_BF16X3", "DG_CONTRACT_FP16X3",
     "DG_K_CORR", "DG_K_ACCUM", "DG_K_ARGMAX", "DG_K_GRID", "DG_K_REFINE", "EXPORTED_SYMBOLS",
     "DG_K_CDFT_PLAN", "DG_K_CDFT_CONTRACT", "DG_K_CDFT_COMBINE",
 ]
@@ -38,7 +38,7 @@ DG_DELAY_INTEGER, DG_DELAY_LAGRANGE4 = 0, 1
 DG_ACC_POWER, DG_ACC_MAG = 0, 1
 DG_PREC_FP32, DG_PREC_FP64 = 0, 1
 DG_ALGO_DIRECT, DG_ALGO_CDFT = 0, 1
-DG_CONTRACT_FP32, DG_CONTRACT_BF16, DG_CONTRACT_FP16 = 0, 1, 2
+DG_CONTRACT_FP32, DG_CONTRACT_BF16, DG_CONTRACT_FP16, DG_CONTRACT_BF16X3, DG_CONTRACT_FP16X3 = 0, 1, 2, 3, 4
 DG_K_CORR, DG_K_ACCUM, DG_K_ARGMAX, DG_K_GRID, DG_K_REFINE = 0, 1, 2, 3, 4
 DG_K_CDFT_PLAN, DG_K_CDFT_CONTRACT, DG_K_CDFT_COMBINE = 5, 6, 7
 
@@ -48,7 +48,8 @@ _DELAY = {"integer": DG_DELAY_INTEGER, "lagrange4": DG_DELAY_LAGRANGE4}
 _ACC = {"power": DG_ACC_POWER, "mag": DG_ACC_MAG}
 _PREC = {"fp32": DG_PREC_FP32, "fp64": DG_PREC_FP64}
 _ALGO = {"direct": DG_ALGO_DIRECT, "cdft": DG_ALGO_CDFT}
-_CONTRACT = {"fp32": DG_CONTRACT_FP32, "bf16": DG_CONTRACT_BF16, "fp16": DG_CONTRACT_FP16}
+_CONTRACT = {"fp32": DG_CONTRACT_FP32, "bf16": DG_CONTRACT_BF16, "fp16": DG_CONTRACT_FP16,
+             "bf16x3": DG_CONTRACT_BF16X3, "fp16x3": DG_CONTRACT_FP16X3}
 
 EXPORTED_SYMBOLS = [
     "dg_options_default", "dg_create", "dg_load_capture", "dg_cost_surface", "dg_argmax_refine",

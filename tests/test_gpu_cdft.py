@@ -102,3 +102,50 @@ def test_cdft_refine_and_unsupported_options():
     for kw in (dict(delay="lagrange4"), dict(prec="fp64"), dict(chunk=100), dict(bins=32)):
         with pytest.raises(P.DGError):
             P.Geolocator(s.grid, s.ephem, s.fs_hz, s.fc_hz, algo="cdft", **kw)
+
+
+# --------------------------------------------------- tensor-core contraction
+# Stated bounds of the 16-bit contractions against the FP64 oracle: the lag
+# products and the DFT matrix are each rounded once to 16 bits (unit roundoff
+# u = 2^-9 for bf16, 2^-11 for fp16) and the products are summed in FP32, so
+# W carries a relative error of order 2u and |C|^2 about twice that:
+# bf16 <= 1e-2, fp16 <= 2e-3 (about 2.5x the ~4u estimate). The split forms
+# (16-bit high part + 16-bit residual, three products) leave ~3u^2 per
+# product and are held to the FP32 bound itself.
+TC_TOL = {"bf16": 1e-2, "fp16": 2e-3, "bf16x3": FP32_TOL, "fp16x3": FP32_TOL}
+
+
+@pytest.mark.parametrize("contract", ["bf16", "fp16", "bf16x3", "fp16x3"])
+@pytest.mark.parametrize("fmt", ["c64", "ci16", "ci8"])
+def test_cdft_tensor_core_error_bounds(contract, fmt):
+    s = sim.make_scene(seed=21, fs_hz=12.5e6, n_samples=3001, k_steps=3, fmt=fmt, waveform="chirp",
+                       snr_db=-3.0, grid_n=(37, 45), grid_spacing_m=150.0)
+    g, c = gpu_surface(s, algo="cdft", contract=contract)
+    ref = oracle_surface(s)
+    ok = ~lag_boundary_mask(s, np.arange(s.G))
+    err = rel_err(c.ravel()[ok], ref.ravel()[ok], 0.01)
+    assert err < TC_TOL[contract], err
+    g.close()
+
+
+@pytest.mark.parametrize("contract", ["bf16", "fp16", "bf16x3", "fp16x3"])
+def test_cdft_tensor_core_mid_subgrid(contract):
+    s = sim.mid(grid_n=(49, 41))
+    g, c = gpu_surface(s, algo="cdft", contract=contract, chunk=1024)
+    ref = oracle_surface(s)
+    ok = ~lag_boundary_mask(s, np.arange(s.G))
+    assert rel_err(c.ravel()[ok], ref.ravel()[ok]) < TC_TOL[contract]
+    assert_argmax_consistent(c, ref, TC_TOL[contract])
+    g.close()
+
+
+@pytest.mark.parametrize("contract", ["fp16", "fp16x3"])
+def test_cdft_tensor_core_large_full_size_sampled(contract):
+    s = sim.large()
+    g, c = gpu_surface(s, algo="cdft", contract=contract, chunk=1024)
+    rng = np.random.default_rng(7)
+    idx = rng.integers(0, s.G, 16)
+    ref = oracle.cost_points(*oracle.scene_args(s), idx=idx)
+    ok = ~lag_boundary_mask(s, idx)
+    assert rel_err(c.ravel()[idx][ok], ref[ok]) < TC_TOL[contract]
+    g.close()
