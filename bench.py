@@ -64,6 +64,21 @@ def workload(name, rank=0, world=1, grid=None):
     return s, desc
 
 
+PEAK_BASIS_TENSOR = ("measured cuBLAS bf16 dense GEMM burst (MEASURED_PEAKS.json bf16_tflops); fp16 has the same "
+                     "nominal dense rate (2.25 PFLOP/s)")
+
+
+def tensor_peak(contract):
+    """Dense 16-bit tensor peak: the measured bf16 burst figure (fp16 runs at
+    the same nominal rate), else the recipe's fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1900.0
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -281,21 +296,41 @@ def run_dg(a, rank, world, local_rank):
     h2d = int(scene.y1.nbytes + scene.y2.nbytes)
     d2h = 2 * 32 + 2 * 4                           # two argmax records, two error words
 
+    kernels = {}
     if a.algo == "cdft":
-        # dominant kernel of the chunked-DFT path and its algorithmic flops per launch
-        dom = max(("contract", "combine"), key=lambda n: kt[n][0])
+        # every kernel of the chunked-DFT path against its own roofline; the
+        # dominant one is the headline
         chunk = a.chunk or 256
-        flops_per_step = (8 * chunk * 64 * bucket_chunks if dom == "contract"
-                          else CDFT_COMBINE_FLOPS * cand_chunks)
+        nprod = 3 if a.contract.endswith("x3") else 1
+        tensor = a.contract != "fp32"
+        # contraction: one chunk x 64-bin complex DFT per (lag, chunk) = 512 * chunk
+        # real flops; the split forms issue three such products on the tensor cores
+        contract_flops = (nprod if tensor else 1) * 512 * chunk * bucket_chunks
+        alu_peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        tc_peak = tensor_peak(a.contract)
+        for name, flops, bound, peak, basis in (
+                ("contract", contract_flops, "tensor" if tensor else "alu", tc_peak if tensor else alu_peak,
+                 f"{'3 x ' if nprod == 3 and tensor else ''}512 flop x chunk per (lag, chunk) row"),
+                ("combine", CDFT_COMBINE_FLOPS * cand_chunks, "alu", alu_peak,
+                 f"{CDFT_COMBINE_FLOPS} flop per candidate x chunk (bin interpolation 6 + phase MAC 8)")):
+            ms, n = kt[name]
+            if n:
+                ach = flops * a.steps / (ms / 1e3) / 1e12
+                kernels[name] = {"bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                                 "frac": ach / peak, "ms_per_step": ms / a.steps, "basis": basis}
+        dom = max(("contract", "combine"), key=lambda n: kt[n][0])
+        flops_per_step = contract_flops if dom == "contract" else CDFT_COMBINE_FLOPS * cand_chunks
         corr_ms, corr_launches = kt[dom]
-        roof_kernel = {"contract": f"k_cdft_contract_f32 (FP32 CUDA cores, {chunk}-sample chunks x 64 bins)",
+        roof_kernel = {"contract": (f"k_cdft_contract_mma ({a.contract} tcgen05, {chunk}-sample chunks x 64 bins)"
+                                    if tensor else f"k_cdft_contract_f32 (FP32 CUDA cores, {chunk}-sample chunks)"),
                        "combine": "k_cdft_combine (FP32, per-candidate interpolation + chunk phase sum)"}[dom]
-        roof_basis = ({"contract": "8 flop per complex MAC x chunk x 64 bins x (lag buckets x chunks) per snapshot",
-                       "combine": f"{CDFT_COMBINE_FLOPS} flop per candidate x chunk (bin interpolation 6 + phase MAC 8)"}[dom])
+        roof_basis = kernels[dom]["basis"]
+        roof_bound, roof_peak = kernels[dom]["bound"], kernels[dom]["peak"]
     else:
         flops_per_step = FLOPS_PER_CAND_SAMPLE * G_rank * KN
         roof_kernel = "k_corr_direct (FP32, integer lag, ci16)"
         roof_basis = f"{FLOPS_PER_CAND_SAMPLE} flop per candidate*sample x G*K*N per launch"
+        roof_bound, roof_peak = "alu", SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     worst = torch.tensor([dev_s, corr_ms / 1e3, sum(e2e_ms) / 1e3], dtype=torch.float64)
     if dist:
         worst = worst.to(dev)
@@ -312,7 +347,7 @@ def run_dg(a, rank, world, local_rank):
         centre = (scene.grid["nlat"] // 2, scene.grid["nlon"] // 2)  # the emitter's node
         gi, gj = divmod(int(gfix[1]), scene.grid["nlon"])
         achieved = flops_per_step * a.steps / corr_s / 1e12
-        peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        peak = roof_peak
         clocks = clk.summary()
         line = {
             "metric": METRIC, "value": units / dev_s, "unit": UNIT, "n_gpus": world,
@@ -329,25 +364,64 @@ def run_dg(a, rank, world, local_rank):
             "e2e": {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "roofline": {"bound": roof_bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": roof_kernel,
-                         "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)",
+                         "peak_basis": (PEAK_BASIS_TENSOR if roof_bound == "tensor"
+                                        else "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"),
                          "achieved_basis": roof_basis + " / CUDA-event time of the launches",
                          "launches": corr_launches, "ms_per_launch": 1e3 * corr_s / max(1, corr_launches)},
             "kernel_ms_per_step": {n: v[0] / a.steps for n, v in kt.items() if v[1]},
+            "kernels": kernels,
             "clocks": clocks,
             "fix": {"i": gi, "j": gj, "emitter_cell": list(centre),
                     "offset_cells": [gi - centre[0], gj - centre[1]],
                     "refined_latlon_deg": [fix["refined_lat_deg"], fix["refined_lon_deg"]]},
             "wall_s": t_wall,
         }
+        if world == 1 and a.algo == "cdft" and not a.no_direct:
+            line["direct_path"] = direct_reference(scene, local_rank, stream)
         if world == 1 and not a.no_cpu_baseline:
             r, dt, npts, cores = oracle_rate(scene, a.cpu_baseline_s)
             line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
                                     "sample": f"{npts} random grid nodes x all {scene.k_steps} snapshots x {scene.n_samples} samples ({dt:.1f} s, FP64, OpenMP over nodes), {cpu_model()}"}
         print(json.dumps(line), flush=True)
     g.close()
+
+
+def direct_reference(scene, local_rank, stream, steps=3, warmup=1):
+    """The direct (sample-by-sample) evaluation of the same surface, timed
+    the same way, for context: cand*samples/s and its FP32 roofline."""
+    import torch
+
+    import paper_2508_06672_gb300 as P
+
+    dev = torch.device("cuda", local_rank)
+    g = P.Geolocator(scene.grid, scene.ephem, scene.fs_hz, scene.fc_hz, algo="direct", timing=True,
+                     stream=stream, device=local_rank)
+    with torch.cuda.stream(stream):
+        g.load_captures(scene.fmt, torch.from_numpy(scene.y1).to(dev), torch.from_numpy(scene.y2).to(dev))
+        cost = torch.empty((scene.grid["nlat"], scene.grid["nlon"]), dtype=torch.float32, device=dev)
+        for _ in range(warmup):
+            g.cost_surface(cost)
+    torch.cuda.synchronize(dev)
+    g.reset_counters()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(steps):
+            g.cost_surface(cost)
+        ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev0.elapsed_time(ev1) / steps
+    corr_ms, n = g.kernel_time(P.DG_K_CORR)
+    g.close()
+    units = scene.G * scene.k_steps * scene.n_samples
+    ach = FLOPS_PER_CAND_SAMPLE * units * steps / (corr_ms / 1e3) / 1e12
+    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    return {"value": units / (ms / 1e3), "unit": UNIT, "ms_per_surface": ms,
+            "roofline": {"bound": "alu", "kernel": "k_corr_direct", "achieved": ach, "peak": peak,
+                         "unit": "TFLOP/s", "frac": ach / peak}}
 
 
 def _smi_id(local_rank):
@@ -366,9 +440,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["dg", "reference"], default="dg")
     ap.add_argument("--workload", choices=["mid", "tiny", "large"], default="mid")
-    ap.add_argument("--algo", choices=["direct", "cdft"], default="direct")
-    ap.add_argument("--chunk", type=int, default=0, help="CDFT samples per chunk (0 = 256)")
-    ap.add_argument("--contract", choices=["fp32", "bf16", "fp16", "bf16x3", "fp16x3"], default="fp32")
+    ap.add_argument("--algo", choices=["direct", "cdft"], default="cdft")
+    ap.add_argument("--chunk", type=int, default=1024, help="CDFT samples per chunk")
+    ap.add_argument("--contract", choices=["fp32", "bf16", "fp16", "bf16x3", "fp16x3"], default="fp16x3")
+    ap.add_argument("--no-direct", action="store_true", help="skip the direct-path reference measurement")
     ap.add_argument("--grid", type=int, default=0, help="override the grid to GRID x GRID nodes")
     ap.add_argument("--cpu-baseline-s", type=float, default=15.0)
     ap.add_argument("--reference-step-s", type=float, default=6.0)

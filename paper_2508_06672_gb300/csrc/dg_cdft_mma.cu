@@ -2,7 +2,7 @@
 // cores (tcgen05, sm_103a), 16-bit products accumulated in FP32.
 //
 // For one snapshot the contraction is one tall GEMM. Its rows are the
-// (lag bucket, chunk) pairs (NB x B rows). For chunk b of lag L the row holds
+// (lag bucket, chunk) pairs (NB x B rows), 128 consecutive rows per CTA. For chunk b of lag L the row holds
 // the lag products z[m] = y1[bM + m] conj(y2[bM + m + L]), m < M. Its 128
 // output columns are the real and imaginary parts of
 // W_b(nu_q) = sum_m z[m] e^{j 2 pi nu_q m} on the snapshot's 64 bins. In real
@@ -15,12 +15,14 @@
 // the same layout.
 //
 // One CTA = 128 rows x 128 columns, the accumulator in tensor memory (128
-// columns). Pipeline: two A buffers (while the tensor cores run stage j the
-// CUDA cores fill stage j + 1) and three B buffers (the bulk copy of stage
-// j + 1 is issued during stage j). A single thread issues the MMAs and commits
-// them to an mbarrier. Each lane of the producer forms 8 consecutive lag
-// products of one row and writes them as one 16-byte core-matrix row, so the
-// shared-memory stores are conflict-free. The epilogue reads the accumulator with tcgen05.ld and writes
+// columns). The pipeline is warp-specialised over a ring of three stages:
+// eight producer warps form the lag products of a stage on the CUDA cores
+// (each lane 8 consecutive samples of one row, written as one 16-byte
+// core-matrix row, so the stores are conflict-free) and arrive on the stage's
+// "A full" mbarrier; one control thread issues the bulk copy of the stage's
+// DFT operand, waits for both, issues the MMAs and commits them to the
+// stage's "empty" mbarrier, which frees the slot for the producers and for
+// the next bulk copy. The epilogue reads the accumulator with tcgen05.ld and writes
 // W rows (planar: 64 real parts, then 64 imaginary parts) scaled back by
 // 1 / zscale. Every mbarrier wait is bounded: on a timeout the kernel latches
 // ERR_TIMEOUT, stops issuing, waits (bounded) for what it issued, frees its
@@ -45,11 +47,6 @@ constexpr int kRows = 128;                         // GEMM rows per CTA
 constexpr int kN = 128;                            // 64 bins x (re, im)
 constexpr int kKS = 32;                            // samples per stage
 constexpr int kBlockBytes = kRows * kKS * 2;       // one 128 x 32 16-bit block
-constexpr int kStages = 2;                         // A buffers (re, im blocks per part)
-constexpr int kBStages = 3;                        // B buffers (re, im blocks per part), prefetched one stage ahead
-// shared memory of a CTA for P 16-bit parts (1, or 2 for the split forms)
-constexpr int smem_bytes(int P) { return (kStages + kBStages) * 2 * P * kBlockBytes; }
-constexpr int kMmaThreads = 512;
 constexpr uint32_t kWaitLimit = 1u << 24;          // try_wait polls before giving up
 
 __device__ __forceinline__ uint32_t blk_off(int row, int k)
@@ -235,93 +232,108 @@ __global__ void __launch_bounds__(256) k_cdft_btab(const float *nubase, const fl
     }
 }
 
-// 8 consecutive samples starting at a multiple of 8, as floats.
-template <int FMT> __device__ __forceinline__ void load8_aligned(const void *base, int idx, float2 (&v)[8]);
-template <> __device__ __forceinline__ void load8_aligned<DG_IQ_C64>(const void *base, int idx, float2 (&v)[8])
-{
-    const float4 *p = reinterpret_cast<const float4 *>(base) + idx / 2;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float4 q = __ldg(p + i);
-        v[2 * i] = make_float2(q.x, q.y);
-        v[2 * i + 1] = make_float2(q.z, q.w);
-    }
-}
-template <> __device__ __forceinline__ void load8_aligned<DG_IQ_CI16>(const void *base, int idx, float2 (&v)[8])
-{
-    const int4 *p = reinterpret_cast<const int4 *>(base) + idx / 4;
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const int4 q = __ldg(p + i);
-        const int w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-        for (int u = 0; u < 4; ++u) v[4 * i + u] = make_float2((float)(short)(w[u] & 0xffff), (float)(short)(w[u] >> 16));
-    }
-}
-template <> __device__ __forceinline__ void load8_aligned<DG_IQ_CI8>(const void *base, int idx, float2 (&v)[8])
-{
-    const int4 q = __ldg(reinterpret_cast<const int4 *>(base) + idx / 8);
-    const int w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        v[2 * u] = make_float2((float)(signed char)(w[u] & 0xff), (float)(signed char)((w[u] >> 8) & 0xff));
-        v[2 * u + 1] = make_float2((float)(signed char)((w[u] >> 16) & 0xff), (float)(signed char)(w[u] >> 24));
-    }
-}
+// Raw loads of one lane's 8 samples of y1 (index n, a multiple of 8) and of
+// y2 (index n2, any) for a stage, issued one stage ahead and decoded when
+// used. The aligned 16-byte windows are only loaded when they lie inside
+// [0, N); otherwise decode() reads the samples one by one with bounds.
+template <int FMT> struct Raw;
 
-// 8 consecutive samples starting at any index i0 with [i0, i0 + 8) inside
-// [0, N): aligned 16-byte loads of the covering window, then a register
-// shift. Falls back to bounded scalar loads when the aligned window would
-// leave [0, N).
-template <int FMT> __device__ __forceinline__ void load8_any(const void *base, int i0, int N, float2 (&v)[8]);
-
-template <> __device__ __forceinline__ void load8_any<DG_IQ_CI16>(const void *base, int i0, int N, float2 (&v)[8])
-{
-    const int a0 = i0 & ~3, sh = i0 - a0;  // 4 samples per 16 bytes
-    if (a0 >= 0 && a0 + 12 <= N) {
-        const int4 *p = reinterpret_cast<const int4 *>(base) + (a0 >> 2);
-        const int4 q0 = __ldg(p), q1 = __ldg(p + 1), q2 = __ldg(p + 2);
-        const int w[12] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z, q2.w};
-        int o[8];
-        switch (sh) {
-        case 0:
-#pragma unroll
-            for (int u = 0; u < 8; ++u) o[u] = w[u];
-            break;
-        case 1:
-#pragma unroll
-            for (int u = 0; u < 8; ++u) o[u] = w[u + 1];
-            break;
-        case 2:
-#pragma unroll
-            for (int u = 0; u < 8; ++u) o[u] = w[u + 2];
-            break;
-        default:
-#pragma unroll
-            for (int u = 0; u < 8; ++u) o[u] = w[u + 3];
-            break;
+template <> struct Raw<DG_IQ_CI16> {
+    int4 a[2], b[3];
+    int n, n2;
+    bool f1, f2;
+    __device__ __forceinline__ void fetch(const void *y1, const void *y2, int n_, int n2_, int N, bool v)
+    {
+        n = n_;
+        n2 = n2_;
+        const int a0 = n2 & ~3;
+        f1 = v && n + 8 <= N;
+        f2 = v && a0 >= 0 && a0 + 12 <= N;
+        if (f1) {
+            const int4 *p = reinterpret_cast<const int4 *>(y1) + (n >> 2);
+            a[0] = __ldg(p);
+            a[1] = __ldg(p + 1);
         }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = make_float2((float)(short)(o[u] & 0xffff), (float)(short)(o[u] >> 16));
-        return;
+        if (f2) {
+            const int4 *p = reinterpret_cast<const int4 *>(y2) + (a0 >> 2);
+            b[0] = __ldg(p);
+            b[1] = __ldg(p + 1);
+            b[2] = __ldg(p + 2);
+        }
     }
+    __device__ __forceinline__ void decode(const void *y1, const void *y2, int N, bool v, float2 (&x)[8],
+                                           float2 (&y)[8]) const
+    {
+        if (f1) {
+            const int w[8] = {a[0].x, a[0].y, a[0].z, a[0].w, a[1].x, a[1].y, a[1].z, a[1].w};
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
-        v[u] = (i0 + u >= 0 && i0 + u < N) ? IQ<DG_IQ_CI16>::load(base, i0 + u) : make_float2(0.f, 0.f);
-}
+            for (int u = 0; u < 8; ++u) x[u] = make_float2((float)(short)(w[u] & 0xffff), (float)(short)(w[u] >> 16));
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                x[u] = (v && n + u < N) ? IQ<DG_IQ_CI16>::load(y1, n + u) : make_float2(0.f, 0.f);
+        }
+        if (f2) {
+            const int w[12] = {b[0].x, b[0].y, b[0].z, b[0].w, b[1].x, b[1].y, b[1].z, b[1].w,
+                               b[2].x, b[2].y, b[2].z, b[2].w};
+            const int sh = n2 & 3;
+            int o[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) o[u] = sh == 0 ? w[u] : sh == 1 ? w[u + 1] : sh == 2 ? w[u + 2] : w[u + 3];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) y[u] = make_float2((float)(short)(o[u] & 0xffff), (float)(short)(o[u] >> 16));
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                y[u] = (v && n2 + u >= 0 && n2 + u < N) ? IQ<DG_IQ_CI16>::load(y2, n2 + u) : make_float2(0.f, 0.f);
+        }
+    }
+};
 
-template <> __device__ __forceinline__ void load8_any<DG_IQ_CI8>(const void *base, int i0, int N, float2 (&v)[8])
-{
-    const int a0 = i0 & ~7, sh = i0 - a0;  // 8 samples per 16 bytes, 2 samples per word
-    if (a0 >= 0 && a0 + 16 <= N) {
-        const int4 *p = reinterpret_cast<const int4 *>(base) + (a0 >> 3);
-        const int4 q0 = __ldg(p), q1 = __ldg(p + 1);
-        const unsigned w[8] = {(unsigned)q0.x, (unsigned)q0.y, (unsigned)q0.z, (unsigned)q0.w,
-                               (unsigned)q1.x, (unsigned)q1.y, (unsigned)q1.z, (unsigned)q1.w};
-        // sample t of the window lives in half-word t of w; take half-words sh .. sh + 7
-        const int wo = sh >> 1;
-        unsigned o[4];
-        if (sh & 1) {
+template <> struct Raw<DG_IQ_CI8> {
+    int4 a, b[2];
+    int n, n2;
+    bool f1, f2;
+    __device__ __forceinline__ void fetch(const void *y1, const void *y2, int n_, int n2_, int N, bool v)
+    {
+        n = n_;
+        n2 = n2_;
+        const int a0 = n2 & ~7;
+        f1 = v && n + 8 <= N;
+        f2 = v && a0 >= 0 && a0 + 16 <= N;
+        if (f1) a = __ldg(reinterpret_cast<const int4 *>(y1) + (n >> 3));
+        if (f2) {
+            const int4 *p = reinterpret_cast<const int4 *>(y2) + (a0 >> 3);
+            b[0] = __ldg(p);
+            b[1] = __ldg(p + 1);
+        }
+    }
+    static __device__ __forceinline__ void unpack(const unsigned (&o)[4], float2 (&v)[8])
+    {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int x = (int)o[u];
+            v[2 * u] = make_float2((float)(signed char)(x & 0xff), (float)(signed char)((x >> 8) & 0xff));
+            v[2 * u + 1] = make_float2((float)(signed char)((x >> 16) & 0xff), (float)(signed char)(x >> 24));
+        }
+    }
+    __device__ __forceinline__ void decode(const void *y1, const void *y2, int N, bool v, float2 (&x)[8],
+                                           float2 (&y)[8]) const
+    {
+        if (f1) {
+            const unsigned o[4] = {(unsigned)a.x, (unsigned)a.y, (unsigned)a.z, (unsigned)a.w};
+            unpack(o, x);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                x[u] = (v && n + u < N) ? IQ<DG_IQ_CI8>::load(y1, n + u) : make_float2(0.f, 0.f);
+        }
+        if (f2) {
+            const unsigned w[8] = {(unsigned)b[0].x, (unsigned)b[0].y, (unsigned)b[0].z, (unsigned)b[0].w,
+                                   (unsigned)b[1].x, (unsigned)b[1].y, (unsigned)b[1].z, (unsigned)b[1].w};
+            // sample t of the window is half-word t of w; take half-words sh .. sh + 7
+            const int sh = n2 & 7, wo = sh >> 1;
+            unsigned o[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 unsigned lo_w = 0, hi_w = 0;
@@ -331,58 +343,95 @@ template <> __device__ __forceinline__ void load8_any<DG_IQ_CI8>(const void *bas
                         lo_w = w[c + u];
                         hi_w = w[c + u + 1];
                     }
-                o[u] = __byte_perm(lo_w, hi_w, 0x5432);
+                o[u] = (sh & 1) ? __byte_perm(lo_w, hi_w, 0x5432) : lo_w;
+            }
+            unpack(o, y);
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                y[u] = (v && n2 + u >= 0 && n2 + u < N) ? IQ<DG_IQ_CI8>::load(y2, n2 + u) : make_float2(0.f, 0.f);
+        }
+    }
+};
+
+template <> struct Raw<DG_IQ_C64> {
+    float4 a[4], b[5];
+    int n, n2;
+    bool f1, f2;
+    __device__ __forceinline__ void fetch(const void *y1, const void *y2, int n_, int n2_, int N, bool v)
+    {
+        n = n_;
+        n2 = n2_;
+        const int a0 = n2 & ~1;
+        f1 = v && n + 8 <= N;
+        f2 = v && a0 >= 0 && a0 + 10 <= N;
+        if (f1) {
+            const float4 *p = reinterpret_cast<const float4 *>(y1) + (n >> 1);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = __ldg(p + i);
+        }
+        if (f2) {
+            const float4 *p = reinterpret_cast<const float4 *>(y2) + (a0 >> 1);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) b[i] = __ldg(p + i);
+        }
+    }
+    __device__ __forceinline__ void decode(const void *y1, const void *y2, int N, bool v, float2 (&x)[8],
+                                           float2 (&y)[8]) const
+    {
+        if (f1) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                x[2 * i] = make_float2(a[i].x, a[i].y);
+                x[2 * i + 1] = make_float2(a[i].z, a[i].w);
             }
         } else {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                unsigned x = 0;
+            for (int u = 0; u < 8; ++u)
+                x[u] = (v && n + u < N) ? IQ<DG_IQ_C64>::load(y1, n + u) : make_float2(0.f, 0.f);
+        }
+        if (f2) {
+            float2 w[10];
 #pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    if (wo == c) x = w[c + u];
-                o[u] = x;
+            for (int i = 0; i < 5; ++i) {
+                w[2 * i] = make_float2(b[i].x, b[i].y);
+                w[2 * i + 1] = make_float2(b[i].z, b[i].w);
             }
-        }
+            const bool sh = n2 & 1;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int x = (int)o[u];
-            v[2 * u] = make_float2((float)(signed char)(x & 0xff), (float)(signed char)((x >> 8) & 0xff));
-            v[2 * u + 1] = make_float2((float)(signed char)((x >> 16) & 0xff), (float)(signed char)(x >> 24));
+            for (int u = 0; u < 8; ++u) y[u] = sh ? w[u + 1] : w[u];
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                y[u] = (v && n2 + u >= 0 && n2 + u < N) ? IQ<DG_IQ_C64>::load(y2, n2 + u) : make_float2(0.f, 0.f);
         }
-        return;
     }
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-        v[u] = (i0 + u >= 0 && i0 + u < N) ? IQ<DG_IQ_CI8>::load(base, i0 + u) : make_float2(0.f, 0.f);
-}
+};
 
-template <> __device__ __forceinline__ void load8_any<DG_IQ_C64>(const void *base, int i0, int N, float2 (&v)[8])
+// Warp-specialised pipeline. Warps 0-7 produce A (lag products) into a ring of
+// kRing stages (A and B per slot); warp 8 lane 0 issues the bulk copies of B and the MMAs. Per
+// stage slot: full_a (8 producer-warp arrivals), full_b (bulk-copy bytes),
+// empty (tcgen05.commit of the MMAs that read the slot). No CTA-wide barrier
+// inside the loop.
+constexpr int kProducerWarps = 8;
+constexpr int kWsThreads = (kProducerWarps + 1) * 32;
+constexpr int kRing = 3;  // pipeline stages in the ring
+template <int P> __host__ __device__ constexpr int ws_smem_bytes() { return kRing * 2 * (2 * P * kBlockBytes); }
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
-    const int a0 = i0 & ~1, sh = i0 - a0;  // 2 samples per 16 bytes
-    if (a0 >= 0 && a0 + 10 <= N) {
-        const float4 *p = reinterpret_cast<const float4 *>(base) + (a0 >> 1);
-        float2 w[10];
-#pragma unroll
-        for (int i = 0; i < 5; ++i) {
-            const float4 q = __ldg(p + i);
-            w[2 * i] = make_float2(q.x, q.y);
-            w[2 * i + 1] = make_float2(q.z, q.w);
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = sh ? w[u + 1] : w[u];
-        return;
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-        v[u] = (i0 + u >= 0 && i0 + u < N) ? IQ<DG_IQ_C64>::load(base, i0 + u) : make_float2(0.f, 0.f);
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 template <int FMT, int DT, int P>
-__global__ void __launch_bounds__(kMmaThreads) k_cdft_contract_mma(CdftBatch a)
+__global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_mma(CdftBatch a)
 {
+    constexpr int NS = kRing;
+    constexpr int kSt = 2 * P * kBlockBytes;  // bytes of one stage's A (or B) blocks
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar_full[kBStages], bar_mma[kStages];
+    __shared__ __align__(8) uint64_t full_a[NS], full_b[NS], empty[NS];
     __shared__ uint32_t tmem_slot;
+    __shared__ volatile int s_abort;
     __shared__ int s_last_commit;
 
     const int tile = blockIdx.x;
@@ -395,34 +444,16 @@ __global__ void __launch_bounds__(kMmaThreads) k_cdft_contract_mma(CdftBatch a)
     const int64_t R = (int64_t)NB * Bs;
     const int NJ = M / kKS;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *sA0 = smem;
+    unsigned char *sB0 = smem + NS * kSt;
 
-    // producer tasks: lane = 8 rows x 4 groups of 8 samples (lanes 0-7 take
-    // group 0 of the warp's 8 rows, so each quarter-warp stores one 128-byte
-    // line of core-matrix rows); warp w covers rows 8 w .. 8 w + 7
-    const int rin = lane & 7, kg = lane >> 3;
-    int pL[1], pn0[1];
-    bool pv[1];
-#pragma unroll
-    for (int h = 0; h < 1; ++h) {
-        const int row = 8 * warp + rin;
-        const int64_t g = (int64_t)ltile * kRows + row;
-        pv[h] = g < R;
-        pL[h] = 0;
-        pn0[h] = 0;
-        if (pv[h]) {
-            const int bl = (int)(g / Bs);
-            pn0[h] = (int)(g % Bs) * M + 8 * kg;  // first sample of this lane at stage 0
-            pL[h] = a.lr[2 * s] + bl;
-            pv[h] = a.count[a.bbase[s] + bl] > 0;
-        }
-    }
-
-    constexpr int kSt = 2 * P * kBlockBytes;  // bytes of one stage's A (or B) blocks
-    unsigned char *sAbase = smem;
-    unsigned char *sBbase = smem + kStages * kSt;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kBStages; ++i) mbar_init(smem_u32(&bar_full[i]), 1);
-        for (int i = 0; i < kStages; ++i) mbar_init(smem_u32(&bar_mma[i]), 1);
+        for (int i = 0; i < NS; ++i) {
+            mbar_init(smem_u32(&full_a[i]), kProducerWarps);
+            mbar_init(smem_u32(&full_b[i]), 1);
+            mbar_init(smem_u32(&empty[i]), 1);
+        }
+        s_abort = 0;
         s_last_commit = -1;
         fence_mbar_init();
         fence_proxy_async_smem();
@@ -433,117 +464,128 @@ __global__ void __launch_bounds__(kMmaThreads) k_cdft_contract_mma(CdftBatch a)
     tc_after_sync();
     const uint32_t tmem = tmem_slot;
     const unsigned char *bsrc = reinterpret_cast<const unsigned char *>(a.btab) + (size_t)s * NJ * kSt;
-    const float zs = a.zscale;
-    bool aborted = false;  // meaningful in thread 0 (the issuer)
-    if (threadIdx.x == 0) {  // B of stage 0
-        mbar_expect_tx(smem_u32(&bar_full[0]), kSt);
-        bulk_g2s(smem_u32(sBbase), bsrc, kSt, smem_u32(&bar_full[0]));
-    }
 
-    for (int j = 0; j < NJ; ++j) {
-        const int st = j & 1, bt = j % kBStages;
-        unsigned char *sA = sAbase + st * kSt;
-        unsigned char *sB = sBbase + bt * kSt;
-        bool bad = false;
-        // the MMAs of stage j - 2 read A buffer st and B buffer (j + 1) % 3
-        if (j >= 2) bad = !mbar_wait(smem_u32(&bar_mma[st]), (uint32_t)((j - 2) >> 1) & 1u);
-        if (__syncthreads_or(bad || aborted)) {
-            if (threadIdx.x == 0) atomicOr(a.err, ERR_TIMEOUT);
-            aborted = true;
-            break;
-        }
-        if (threadIdx.x == 0 && j + 1 < NJ) {  // prefetch B of stage j + 1
-            const int nb = (j + 1) % kBStages;
-            mbar_expect_tx(smem_u32(&bar_full[nb]), kSt);
-            bulk_g2s(smem_u32(sBbase + nb * kSt), bsrc + (size_t)(j + 1) * kSt, kSt, smem_u32(&bar_full[nb]));
-        }
-        // lag products of 8 consecutive samples of one row, rounded to 16 bits
+    if (warp < kProducerWarps) {
+        // ---- producers: lane = 8 rows x 4 groups of 8 samples, two row sets per warp
+        const int rin = lane & 7, kg = lane >> 3;
+        int pL[2], pn0[2];
+        bool pv[2];
 #pragma unroll
-        for (int h = 0; h < 1; ++h) {
-            const int row = 8 * warp + rin;
-            float2 x[8];
-            float zr[8], zi[8];
-            const int n = pn0[h] + j * kKS;
-            if (pv[h] && n + 8 <= N) {
-                load8_aligned<FMT>(sd.y1, n, x);
-            } else {
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    x[u] = (pv[h] && n + u < N) ? IQ<FMT>::load(sd.y1, n + u) : make_float2(0.f, 0.f);
-            }
-            float2 y[8];
+        for (int h = 0; h < 2; ++h) {
+            const int row = 16 * warp + 8 * h + rin;
+            const int64_t g = (int64_t)ltile * kRows + row;
+            pv[h] = g < R;
+            pL[h] = 0;
+            pn0[h] = 0;
             if (pv[h]) {
-                load8_any<FMT>(sd.y2, n + pL[h], N, y);
-            } else {
-#pragma unroll
-                for (int u = 0; u < 8; ++u) y[u] = make_float2(0.f, 0.f);
+                const int bl = (int)(g / Bs);
+                pn0[h] = (int)(g % Bs) * M + 8 * kg;
+                pL[h] = a.lr[2 * s] + bl;
+                pv[h] = a.count[a.bbase[s] + bl] > 0;
             }
+        }
+        const float zs = a.zscale;
+        for (int j = 0; j < NJ; ++j) {
+            const int slot = j % NS;
+            if (j >= NS && !mbar_wait(smem_u32(&empty[slot]), (uint32_t)((j / NS) - 1) & 1u)) s_abort = 1;
+            if (s_abort) break;
+            unsigned char *sA = sA0 + slot * kSt;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                // samples beyond the end of y1 contribute nothing (x is zero there)
-                zr[u] = fmaf(x[u].x, y[u].x, x[u].y * y[u].y) * zs;
-                zi[u] = fmaf(x[u].y, y[u].x, -x[u].x * y[u].y) * zs;
-            }
-            uint16_t hr[8], hi[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                hr[u] = to16<DT>(zr[u]);
-                hi[u] = to16<DT>(zi[u]);
-            }
-            auto pk = [](const uint16_t *h) {
-                return make_uint4((uint32_t)h[0] | ((uint32_t)h[1] << 16), (uint32_t)h[2] | ((uint32_t)h[3] << 16),
-                                  (uint32_t)h[4] | ((uint32_t)h[5] << 16), (uint32_t)h[6] | ((uint32_t)h[7] << 16));
-            };
-            *reinterpret_cast<uint4 *>(sA + blk_off(row, 8 * kg)) = pk(hr);
-            *reinterpret_cast<uint4 *>(sA + kBlockBytes + blk_off(row, 8 * kg)) = pk(hi);
-            if (P == 2) {  // residuals z - high part, rounded to 16 bits
-                uint16_t lr[8], li[8];
+            for (int h = 0; h < 2; ++h) {
+                const int row = 16 * warp + 8 * h + rin;
+                Raw<FMT> raw;
+                const int n = pn0[h] + j * kKS;
+                raw.fetch(sd.y1, sd.y2, n, n + pL[h], N, pv[h]);
+                float2 x[8], y[8];
+                raw.decode(sd.y1, sd.y2, N, pv[h], x, y);
+                float zr[8], zi[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    lr[u] = to16<DT>(zr[u] - from16<DT>(hr[u]));
-                    li[u] = to16<DT>(zi[u] - from16<DT>(hi[u]));
+                    zr[u] = fmaf(x[u].x, y[u].x, x[u].y * y[u].y) * zs;
+                    zi[u] = fmaf(x[u].y, y[u].x, -x[u].x * y[u].y) * zs;
                 }
-                *reinterpret_cast<uint4 *>(sA + 2 * kBlockBytes + blk_off(row, 8 * kg)) = pk(lr);
-                *reinterpret_cast<uint4 *>(sA + 3 * kBlockBytes + blk_off(row, 8 * kg)) = pk(li);
+                uint16_t hr[8], hi[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    hr[u] = to16<DT>(zr[u]);
+                    hi[u] = to16<DT>(zi[u]);
+                }
+                auto pk = [](const uint16_t *q) {
+                    return make_uint4((uint32_t)q[0] | ((uint32_t)q[1] << 16), (uint32_t)q[2] | ((uint32_t)q[3] << 16),
+                                      (uint32_t)q[4] | ((uint32_t)q[5] << 16), (uint32_t)q[6] | ((uint32_t)q[7] << 16));
+                };
+                *reinterpret_cast<uint4 *>(sA + blk_off(row, 8 * kg)) = pk(hr);
+                *reinterpret_cast<uint4 *>(sA + kBlockBytes + blk_off(row, 8 * kg)) = pk(hi);
+                if (P == 2) {  // residuals z - high part, rounded to 16 bits
+                    uint16_t lr[8], li[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        lr[u] = to16<DT>(zr[u] - from16<DT>(hr[u]));
+                        li[u] = to16<DT>(zi[u] - from16<DT>(hi[u]));
+                    }
+                    *reinterpret_cast<uint4 *>(sA + 2 * kBlockBytes + blk_off(row, 8 * kg)) = pk(lr);
+                    *reinterpret_cast<uint4 *>(sA + 3 * kBlockBytes + blk_off(row, 8 * kg)) = pk(li);
+                }
             }
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&full_a[slot]));
         }
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            if (!mbar_wait(smem_u32(&bar_full[bt]), (uint32_t)(j / kBStages) & 1u)) {
-                aborted = true;  // reported at the top of the next iteration / after the loop
-            } else {
-                tc_after_sync();
-                const uint32_t id = idesc<DT>();
-                // products per block: high x high, and for the split forms also
-                // residual x high and high x residual (part p at p * 2 blocks)
-                constexpr int NPROD = P == 2 ? 3 : 1;
+    } else if (lane == 0) {
+        // ---- control: bulk copies of B, MMA issue, commits
+        for (int t = 0; t < NS && t < NJ; ++t) {
+            mbar_expect_tx(smem_u32(&full_b[t]), kSt);
+            bulk_g2s(smem_u32(sB0 + t * kSt), bsrc + (size_t)t * kSt, kSt, smem_u32(&full_b[t]));
+        }
+        const uint32_t id = idesc<DT>();
+        for (int j = 0; j < NJ; ++j) {
+            const int slot = j % NS;
+            const uint32_t ph = (uint32_t)(j / NS) & 1u;
+            if (!mbar_wait(smem_u32(&full_a[slot]), ph) || !mbar_wait(smem_u32(&full_b[slot]), ph) || s_abort) {
+                s_abort = 1;
+                break;
+            }
+            tc_after_sync();
+            const unsigned char *sA = sA0 + slot * kSt;
+            const unsigned char *sB = sB0 + slot * kSt;
+            // products per block: high x high, and for the split forms also
+            // residual x high and high x residual (part p at p * 2 blocks)
+            constexpr int NPROD = P == 2 ? 3 : 1;
 #pragma unroll
-                for (int blk = 0; blk < 2; ++blk)
+            for (int blk = 0; blk < 2; ++blk)
 #pragma unroll
-                    for (int kk = 0; kk < kKS; kk += 16)
+                for (int kk = 0; kk < kKS; kk += 16)
 #pragma unroll
-                        for (int pr = 0; pr < NPROD; ++pr) {
-                            const int pa = pr == 1 ? 1 : 0, pb = pr == 2 ? 1 : 0;
-                            const uint64_t ad = sdesc(smem_u32(sA + (2 * pa + blk) * kBlockBytes) + kk * 16);
-                            const uint64_t bd = sdesc(smem_u32(sB + (2 * pb + blk) * kBlockBytes) + kk * 16);
-                            mma_f16(tmem, ad, bd, id, (j > 0 || blk > 0 || kk > 0 || pr > 0) ? 1u : 0u);
-                        }
-                mma_commit(smem_u32(&bar_mma[st]));
-                s_last_commit = j;
+                    for (int pr = 0; pr < NPROD; ++pr) {
+                        const int pa = pr == 1 ? 1 : 0, pb = pr == 2 ? 1 : 0;
+                        const uint64_t ad = sdesc(smem_u32(sA + (2 * pa + blk) * kBlockBytes) + kk * 16);
+                        const uint64_t bd = sdesc(smem_u32(sB + (2 * pb + blk) * kBlockBytes) + kk * 16);
+                        mma_f16(tmem, ad, bd, id, (j > 0 || blk > 0 || kk > 0 || pr > 0) ? 1u : 0u);
+                    }
+            mma_commit(smem_u32(&empty[slot]));
+            s_last_commit = j;
+            // refill the slot of stage j - 1 with B of stage j - 1 + NS once its MMAs are done
+            if (j >= 1 && j - 1 + NS < NJ) {
+                const int s1 = (j - 1) % NS;
+                if (!mbar_wait(smem_u32(&empty[s1]), (uint32_t)((j - 1) / NS) & 1u)) {
+                    s_abort = 1;
+                    break;
+                }
+                mbar_expect_tx(smem_u32(&full_b[s1]), kSt);
+                bulk_g2s(smem_u32(sB0 + s1 * kSt), bsrc + (size_t)(j - 1 + NS) * kSt, kSt, smem_u32(&full_b[s1]));
             }
         }
     }
-    // the last commit covers every MMA this CTA issued
+    // every issued MMA is covered by the last commit
     __syncthreads();
     const int lc = s_last_commit;
-    bool ok = lc >= 0 && mbar_wait(smem_u32(&bar_mma[lc & 1]), (uint32_t)(lc >> 1) & 1u);
-    if (threadIdx.x == 0 && aborted) atomicOr(a.err, ERR_TIMEOUT);
-    ok = !__syncthreads_or(!ok || aborted || lc != NJ - 1);
+    bool ok = lc >= 0 && mbar_wait(smem_u32(&empty[lc % NS]), (uint32_t)(lc / NS) & 1u);
+    ok = !__syncthreads_or(!ok || s_abort || lc != NJ - 1);
+    if (threadIdx.x == 0 && (s_abort || lc != NJ - 1)) atomicOr(a.err, ERR_TIMEOUT);
     tc_after_sync();
-    if (ok) {
-        // warp w reads lanes 32 (w % 4) .. +31 (its rows), columns 32 (w / 4) .. +31
-        const int row = 32 * (warp & 3) + lane, quarter = warp >> 2;
+    if (ok && warp < 8) {
+        // warp w reads lanes 32 (w % 4) .. +31 (its rows), columns 64 (w / 4) .. +63
+        const int row = 32 * (warp & 3) + lane, half = warp >> 2;
         const int64_t g = (int64_t)ltile * kRows + row;
         bool valid = g < R;
         int64_t wrow = 0;
@@ -552,14 +594,14 @@ __global__ void __launch_bounds__(kMmaThreads) k_cdft_contract_mma(CdftBatch a)
             valid = a.count[a.bbase[s] + bl] > 0;
             wrow = ((int64_t)(a.bbase[s] + bl) * a.Bmax + g % Bs) * 128;
         }
-        const float inv = 1.0f / zs;
-        const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(32 * quarter);
-        {
-            const int c = 0;
+        const float inv = 1.0f / a.zscale;
+        const uint32_t tb = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * half);
+#pragma unroll
+        for (int c = 0; c < 64; c += 32) {
             uint32_t r[32];
-            tmem_ld32(tbase, r);
+            tmem_ld32(tb + (uint32_t)c, r);
             if (valid) {
-                float4 *w = reinterpret_cast<float4 *>(a.W + wrow + 32 * quarter + c);
+                float4 *w = reinterpret_cast<float4 *>(a.W + wrow + 64 * half + c);
 #pragma unroll
                 for (int v = 0; v < 8; ++v)
                     w[v] = make_float4(__uint_as_float(r[4 * v]) * inv, __uint_as_float(r[4 * v + 1]) * inv,
@@ -591,10 +633,15 @@ size_t cdft_btab_bytes(int mode, int M) { return (size_t)(M / kKS) * 2 * (mode >
 template <int FMT, int DT, int P>
 static cudaError_t launch_mma(const CdftBatch &a, int tiles, cudaStream_t st)
 {
-    const int smem = smem_bytes(P);
+    const int smem = ws_smem_bytes<P>();
     cudaError_t e = cudaFuncSetAttribute(k_cdft_contract_mma<FMT, DT, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    k_cdft_contract_mma<FMT, DT, P><<<(unsigned)tiles, kMmaThreads, smem, st>>>(a);
+    // all of the unified L1/shared storage as shared memory: two CTAs of the
+    // single-product forms fit on one SM
+    e = cudaFuncSetAttribute(k_cdft_contract_mma<FMT, DT, P>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    k_cdft_contract_mma<FMT, DT, P><<<(unsigned)tiles, kWsThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 

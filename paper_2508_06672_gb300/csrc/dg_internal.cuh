@@ -290,7 +290,7 @@ struct CdftBatch {
     float *nubase, *delta;        // [S] bins nu_q = nubase + q delta
     float2 *V;                    // [S][M][64] DFT table e^{j 2 pi nu_q m}
     float *W;                     // [NBT][Bmax][128]: per chunk 64 bins, re[64] | im[64]
-    const int *tbase;             // [S + 1] first tensor-core tile of each snapshot (device)
+    const int *tbase;             // [S + 1] first tensor-core tile (128 rows) of each snapshot (device)
     const void *btab;             // [S][M/32][2][128 x 32] 16-bit DFT operand (tensor cores)
     float zscale;                 // lag products are multiplied by this before 16-bit rounding
 };
