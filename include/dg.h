@@ -184,6 +184,27 @@ dg_status dg_cost_surface(dg_ctx *ctx, void *out);
 dg_status dg_argmax_refine(dg_ctx *ctx, const void *cost, double refine_spacing_m, double window_m,
                            dg_fix *out);
 
+/* One detected emitter (dg_detect). */
+typedef struct {
+    int64_t index;             /* linear index in the shard's surface          */
+    int32_t i, j;              /* global row, column                           */
+    double lat_deg, lon_deg;   /* that node                                    */
+    double value;              /* the surface value there                      */
+} dg_peak;
+
+/* Threshold detection of emitters on a surface from dg_cost_surface (device
+ * pointer, the context's precision; Algorithm 1, last step: apply a threshold
+ * to the summed grid). A node is reported when its value is >= the threshold
+ * and it is the maximum of the (2 radius + 1)^2 window of nodes around it
+ * (within the shard); among equal values the lowest linear index wins, so a
+ * plateau gives one peak. relative = 1 reads threshold as a fraction of the
+ * surface maximum. Peaks are ordered by value (descending, ties by index);
+ * at most max_peaks (<= 2048) are written to out (host, max_peaks entries) and
+ * their number to *n_out. 0 <= radius <= 64. DG_EUNSUPPORTED if more than
+ * 2048 nodes pass the test (raise the threshold). Synchronises the stream. */
+dg_status dg_detect(dg_ctx *ctx, const void *cost, double threshold, int32_t relative, int32_t radius,
+                    int32_t max_peaks, dg_peak *out, int32_t *n_out);
+
 /* Wait for the context's stream and report any latched kernel error. */
 dg_status dg_sync(dg_ctx *ctx);
 

@@ -63,6 +63,8 @@ def _bind(path):
     L.dgo_cost_points.restype = C.c_int
     L.dgo_argmax.argtypes = [dp, C.c_int64]
     L.dgo_argmax.restype = C.c_int64
+    L.dgo_detect.argtypes = [dp, C.c_int32, C.c_int32, C.c_double, C.c_int32, C.c_int64, C.POINTER(C.c_int64)]
+    L.dgo_detect.restype = C.c_int64
     return L
 
 
@@ -201,6 +203,20 @@ def cost_surface(grid, ephem, fs, fc, y1, y2, delay_mode=0, acc_mode=0, nthreads
 def argmax(cost):
     c = _f64c(np.ravel(cost))
     return int(lib().dgo_argmax(_dp(c), c.size))
+
+
+def detect(cost, threshold, radius, max_peaks=64):
+    """Threshold detection on a surface (nlat, nlon): linear indices of the
+    peaks, strongest first."""
+    c = _f64c(cost)
+    if c.ndim != 2:
+        raise ValueError("cost must be (nlat, nlon)")
+    out = np.empty(max(1, int(max_peaks)), dtype=np.int64)
+    n = lib().dgo_detect(_dp(c), c.shape[0], c.shape[1], float(threshold), int(radius), int(max_peaks),
+                         out.ctypes.data_as(C.POINTER(C.c_int64)))
+    if n < 0:
+        raise MemoryError("dgo_detect")
+    return out[:n].copy()
 
 
 def refine_grid(grid, index, spacing_m, window_m):

@@ -219,3 +219,48 @@ int64_t dgo_argmax(const double *cost, int64_t n)
         if (cost[p] == cost[p] && (best < 0 || cost[p] > cost[best])) best = p;
     return best;
 }
+
+/* Algorithm 1, last step: threshold detection of emitters on an accumulated
+ * surface [nlat][nlon]. A node is reported when its value is >= threshold and
+ * it is the maximum of the (2r+1) x (2r+1) window of nodes around it (within
+ * the grid); among equal values the lowest linear index wins, so a plateau
+ * yields one peak. Peaks are ordered by value, descending, ties by index;
+ * at most max_peaks are written to idx. Returns the number written. */
+int64_t dgo_detect(const double *v, int32_t nlat, int32_t nlon, double threshold, int32_t r,
+                   int64_t max_peaks, int64_t *idx)
+{
+    int64_t n = 0, cap = max_peaks;
+    int64_t *tmp = (int64_t *)malloc(sizeof(int64_t) * (size_t)((int64_t)nlat * nlon + 1));
+    if (!tmp) return -1;
+    for (int64_t i = 0; i < nlat; ++i)
+        for (int64_t j = 0; j < nlon; ++j) {
+            int64_t p = i * nlon + j;
+            double x = v[p];
+            if (!(x >= threshold)) continue;
+            int peak = 1;
+            for (int64_t di = -r; di <= r && peak; ++di)
+                for (int64_t dj = -r; dj <= r; ++dj) {
+                    int64_t ii = i + di, jj = j + dj;
+                    if ((di == 0 && dj == 0) || ii < 0 || jj < 0 || ii >= nlat || jj >= nlon) continue;
+                    int64_t q = ii * nlon + jj;
+                    if (v[q] > x || (v[q] == x && q < p)) {
+                        peak = 0;
+                        break;
+                    }
+                }
+            if (peak) tmp[n++] = p;
+        }
+    /* insertion sort by (value desc, index asc): peaks are few */
+    for (int64_t a = 1; a < n; ++a) {
+        int64_t key = tmp[a], b = a - 1;
+        while (b >= 0 && (v[tmp[b]] < v[key] || (v[tmp[b]] == v[key] && tmp[b] > key))) {
+            tmp[b + 1] = tmp[b];
+            --b;
+        }
+        tmp[b + 1] = key;
+    }
+    if (n > cap) n = cap;
+    memcpy(idx, tmp, sizeof(int64_t) * (size_t)n);
+    free(tmp);
+    return n;
+}

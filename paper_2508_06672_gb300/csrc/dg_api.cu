@@ -92,6 +92,9 @@ struct dg_ctx {
     size_t amax_tmp_bytes = 0;
     ArgmaxResult *amax_res = nullptr;
     ArgmaxResult *amax_host = nullptr;  // pinned
+    int *det_count = nullptr;
+    int64_t *det_cand = nullptr;
+    DetectPeak *det_out = nullptr;
     unsigned *err_d = nullptr;
     unsigned *err_h = nullptr;          // pinned mirror
     LocalGrid loc;
@@ -788,6 +791,58 @@ dg_status dg_argmax_refine(dg_ctx *c, const void *cost, double spacing_m, double
     return DG_OK;
 }
 
+dg_status dg_detect(dg_ctx *c, const void *cost, double threshold, int32_t relative, int32_t radius,
+                    int32_t max_peaks, dg_peak *out, int32_t *n_out)
+{
+    if (!c) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    c->err.clear();
+    if (!cost || !out || !n_out) return fail(c, DG_EINVAL, "cost, out and n_out must not be NULL");
+    if (radius < 0 || radius > 64) return fail(c, DG_EINVAL, "radius must be in [0, 64]");
+    if (max_peaks < 1 || max_peaks > kDetectCap) return fail(c, DG_EINVAL, "max_peaks must be in [1, %d]", kDetectCap);
+    if (!std::isfinite(threshold)) return fail(c, DG_EINVAL, "threshold must be finite");
+    constexpr int kCap = kDetectCap;
+    CK(c, cudaStreamSynchronize(c->stream));
+    dg_status st = check_latched(c);
+    if (st != DG_OK) return st;
+    double thr = threshold;
+    if (relative) {
+        ArgmaxResult r;
+        if ((st = run_argmax(c, cost, c->G, c->gd, &r)) != DG_OK) return st;
+        if (r.idx < 0) return fail(c, DG_EINVAL, "the surface holds no finite value");
+        thr = threshold * r.val;
+    }
+    if (!c->det_count) {
+        CK(c, cudaMallocAsync((void **)&c->det_count, sizeof(int), c->stream));
+        CK(c, cudaMallocAsync((void **)&c->det_cand, sizeof(int64_t) * kCap, c->stream));
+        CK(c, cudaMallocAsync((void **)&c->det_out, sizeof(DetectPeak) * kCap, c->stream));
+    }
+    {
+        Timed t(c, DG_K_ARGMAX);
+        CK(c, launch_detect(cost, c->opt.prec, c->gd, thr, radius, kCap, max_peaks, c->det_count, c->det_cand,
+                            c->det_out, c->stream));
+        t.done(2);
+    }
+    int count = 0;
+    std::vector<DetectPeak> pk((size_t)max_peaks);
+    CK(c, cudaMemcpyAsync(&count, c->det_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(pk.data(), c->det_out, sizeof(DetectPeak) * (size_t)max_peaks, cudaMemcpyDeviceToHost,
+                          c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (count > kCap)
+        return fail(c, DG_EUNSUPPORTED, "%d nodes pass the detection test (max %d); raise the threshold", count, kCap);
+    const int n = std::min(count, (int)max_peaks);
+    for (int k = 0; k < n; ++k) {
+        out[k].index = pk[k].index;
+        out[k].i = pk[k].i;
+        out[k].j = pk[k].j;
+        out[k].lat_deg = pk[k].lat_rad * (180.0 / kPi);
+        out[k].lon_deg = pk[k].lon_rad * (180.0 / kPi);
+        out[k].value = pk[k].value;
+    }
+    *n_out = n;
+    return DG_OK;
+}
+
 dg_status dg_grid_ecef(dg_ctx *c, double *xyz_out)
 {
     if (!c) return fail(nullptr, DG_EINVAL, "ctx is NULL");
@@ -877,6 +932,9 @@ dg_status dg_destroy(dg_ctx *c)
     fr(c->amax_tmp);
     fr(c->amax_res);
     fr(c->err_d);
+    fr(c->det_count);
+    fr(c->det_cand);
+    fr(c->det_out);
     fr(c->loc.xyz);
     fr(c->loc.surf);
     fr(c->loc.cost);

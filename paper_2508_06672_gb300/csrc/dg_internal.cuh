@@ -307,6 +307,17 @@ cudaError_t launch_cdft_btab(const CdftBatch &a, int mode, void *btab, cudaStrea
 cudaError_t launch_cdft_contract_mma(const CdftBatch &a, int tiles, int fmt, int mode, cudaStream_t s);
 size_t cdft_btab_bytes(int mode, int M);  // per snapshot
 
+// Threshold detection (dg_detect.cu). cap: power of two <= kDetectCap candidates
+// (the sort keeps value + index of each in static shared memory, 32 KiB).
+constexpr int kDetectCap = 2048;
+struct DetectPeak {
+    int64_t index;
+    int i, j;
+    double lat_rad, lon_rad, value;
+};
+cudaError_t launch_detect(const void *v, int prec, const GridDev &g, double thr, int r, int cap, int max_peaks,
+                          int *count, int64_t *cand, DetectPeak *out, cudaStream_t s);
+
 // Argmax record written by launch_argmax.
 struct ArgmaxResult {
     double val;

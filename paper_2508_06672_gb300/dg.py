@@ -19,7 +19,7 @@ import threading
 import numpy as np
 
 __all__ = [
-    "DGError", "dg_grid", "dg_ephem", "dg_options", "dg_fix", "lib", "library_path",
+    "DGError", "dg_grid", "dg_ephem", "dg_options", "dg_fix", "dg_peak", "lib", "library_path",
     "dg_options_default", "dg_create", "dg_load_capture", "dg_cost_surface", "dg_argmax_refine",
     "dg_sync", "dg_destroy", "dg_last_error", "dg_grid_ecef", "dg_step_geometry", "dg_kernel_time",
     "dg_reset_counters", "dg_launch_count", "dg_abi_version", "Geolocator",
@@ -55,7 +55,7 @@ EXPORTED_SYMBOLS = [
     "dg_options_default", "dg_create", "dg_load_capture", "dg_cost_surface", "dg_argmax_refine",
     "dg_sync", "dg_destroy", "dg_last_error", "dg_grid_ecef", "dg_step_geometry", "dg_kernel_time",
     "dg_reset_counters", "dg_launch_count", "dg_abi_version", "dg_cost_surface_noalloc",
-    "dg_noalloc_last_error", "dg_cdft_work",
+    "dg_noalloc_last_error", "dg_cdft_work", "dg_detect",
 ]
 DG_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
@@ -86,6 +86,14 @@ class dg_options(C.Structure):
                 ("row0", C.c_int32), ("nrows", C.c_int32), ("timing", C.c_int32),
                 ("chunk", C.c_int32), ("bins", C.c_int32), ("contract", C.c_int32),
                 ("reserved", C.c_int32)]
+
+
+class dg_peak(C.Structure):
+    _fields_ = [("index", C.c_int64), ("i", C.c_int32), ("j", C.c_int32), ("lat_deg", C.c_double),
+                ("lon_deg", C.c_double), ("value", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class dg_fix(C.Structure):
@@ -140,6 +148,8 @@ def lib():
             L.dg_cost_surface_noalloc.argtypes = [C.POINTER(dg_grid), C.POINTER(dg_ephem), i32, dbl, dbl,
                                                   i32, vp, vp, i64, C.POINTER(dg_options), vp, vp]
             L.dg_cost_surface_noalloc.restype = C.c_int
+            L.dg_detect.argtypes = [vp, vp, dbl, i32, i32, i32, C.POINTER(dg_peak), C.POINTER(i32)]
+            L.dg_detect.restype = C.c_int
             L.dg_cdft_work.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
             L.dg_cdft_work.restype = C.c_int
             L.dg_noalloc_last_error.argtypes = []
@@ -221,6 +231,14 @@ def dg_kernel_time(ctx, kernel_class):
     ms, n = C.c_double(), C.c_int64()
     _check(lib().dg_kernel_time(ctx, int(kernel_class), C.byref(ms), C.byref(n)), ctx)
     return ms.value, n.value
+
+
+def dg_detect(ctx, cost_ptr, threshold, relative=False, radius=3, max_peaks=16):
+    arr = (dg_peak * int(max_peaks))()
+    n = C.c_int32()
+    _check(lib().dg_detect(ctx, C.c_void_p(cost_ptr), float(threshold), int(bool(relative)), int(radius),
+                           int(max_peaks), arr, C.byref(n)), ctx)
+    return [arr[k].as_dict() for k in range(n.value)]
 
 
 def dg_cdft_work(ctx):
@@ -339,6 +357,11 @@ class Geolocator:
         if cost.dtype != self.dtype or not cost.is_cuda:
             raise ValueError("cost must be a CUDA tensor of the context's precision")
         return dg_argmax_refine(self.ctx, cost.data_ptr(), refine_spacing_m, window_m).as_dict()
+
+    def detect(self, cost, threshold, relative=False, radius=3, max_peaks=16):
+        if cost.dtype != self.dtype or not cost.is_cuda:
+            raise ValueError("cost must be a CUDA tensor of the context's precision")
+        return dg_detect(self.ctx, cost.data_ptr(), threshold, relative, radius, max_peaks)
 
     def sync(self):
         dg_sync(self.ctx)

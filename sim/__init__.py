@@ -341,6 +341,142 @@ def make_scene(
                  emitter_ecef=p_e, tau=taus, fdop=fds, meta=meta)
 
 
+def _cell_degrees(lat_deg, spacing_m):
+    """Degrees of latitude and longitude spanned by one grid cell of
+    spacing_m metres at lat_deg (meridian / prime-vertical radii)."""
+    s = math.sin(math.radians(lat_deg))
+    w = math.sqrt(1.0 - WGS84_E2 * s * s)
+    m_rad = WGS84_A * (1.0 - WGS84_E2) / w ** 3
+    n_rad = WGS84_A / w
+    return math.degrees(spacing_m / m_rad), math.degrees(spacing_m / (n_rad * math.cos(math.radians(lat_deg))))
+
+
+@dataclasses.dataclass
+class Emitter:
+    """One emitter of a multi-emitter scene: its node offset from the grid
+    centre (cells, lat and lon), waveform and SNR (dB, per receiver sample,
+    against the unit-power receiver noise)."""
+    di: int
+    dj: int
+    waveform: str
+    snr_db: float
+    bw_hz: float = 2e6
+
+
+@dataclasses.dataclass
+class MultiScene:
+    fs_hz: float
+    fc_hz: float
+    n_samples: int
+    k_steps: int
+    fmt: str
+    grid: dict
+    ephem: np.ndarray
+    y1: np.ndarray
+    y2: np.ndarray
+    emitters: list             # [Emitter]
+    emitter_nodes: list        # [(i, j)] grid node of each emitter
+    emitter_latlon_deg: list   # [(lat, lon)]
+    meta: dict
+
+    @property
+    def G(self) -> int:
+        return int(self.grid["nlat"]) * int(self.grid["nlon"])
+
+    @property
+    def fmt_code(self) -> int:
+        return FORMAT_CODE[self.fmt]
+
+
+def make_multi_scene(
+    *,
+    seed: int,
+    fs_hz: float,
+    n_samples: int,
+    k_steps: int,
+    fmt: str,
+    emitters: list,
+    grid_n: int,
+    grid_spacing_m: float,
+    noise: bool = True,
+    fc_hz: float = 1575.42e6,
+    chirp_bw_hz: float = 10e6,
+    chirp_period_s: float = 10e-6,
+    formation: Formation | None = None,
+) -> MultiScene:
+    """Several stationary emitters transmitting at once (Sec. I: a crowded
+    band where strong, weak and cyclostationary emitters share the
+    receivers). Each emitter sits on a grid node (offset from the grid
+    centre by whole cells); receiver i records the sum of every emitter's
+    delayed, Doppler-shifted waveform (Eq. 1, one term per emitter) plus one
+    unit-power noise. Waveforms are drawn independently per emitter.
+    """
+    rng = np.random.default_rng(seed)
+    form = formation or Formation()
+    t_mid = form.t0_s + 0.5 * (k_steps - 1) * form.dt_s
+    lat0, lon0 = pick_emitter(rng, form, t_mid)
+    dlat, dlon = _cell_degrees(lat0, grid_spacing_m)
+    c = (grid_n - 1) // 2
+    grid = dict(lat0_deg=lat0, lon0_deg=lon0, dlat_m=grid_spacing_m, dlon_m=grid_spacing_m,
+                nlat=int(grid_n), nlon=int(grid_n))
+    sites, nodes = [], []
+    for e in emitters:
+        if not (0 <= c + e.di < grid_n and 0 <= c + e.dj < grid_n):
+            raise ValueError("emitter outside the grid")
+        sites.append((lat0 + e.di * dlat, lon0 + e.dj * dlon))
+        nodes.append((c + e.di, c + e.dj))
+    p_e = [geodetic_to_ecef(la, lo, 0.0) for la, lo in sites]
+    ephem = form.ephemerides(k_steps)
+    n = n_samples
+    t_n = np.arange(n, dtype=np.float64) / fs_hz
+    amps = [math.sqrt(10.0 ** (e.snr_db / 10.0)) for e in emitters]
+    noise_p = 1.0 if noise else 0.0
+    chirp_t0 = [rng.uniform(0.0, chirp_period_s) for _ in emitters]
+    dt = {"c64": np.float32, "ci16": np.int16, "ci8": np.int8}[fmt]
+    y1 = np.empty((k_steps, n, 2), dtype=dt)
+    y2 = np.empty_like(y1)
+    for k in range(k_steps):
+        tk = form.t0_s + k * form.dt_s
+        acc = [np.zeros(n, np.complex128), np.zeros(n, np.complex128)]
+        for m, e in enumerate(emitters):
+            tau, fd = truth_delay_doppler(form, tk, p_e[m], fc_hz)
+            if e.waveform == "noise":
+                n_fft = 1 << int(math.ceil(math.log2(2 * n + 8192)))
+                spec, f = bandlimited_noise_spectrum(rng, n_fft, fs_hz, e.bw_hz)
+                sig = [delayed_noise(spec, f, tau[i] - tau[0], n) for i in range(2)]
+            elif e.waveform == "chirp":
+                sig = [chirp(chirp_t0[m] + t_n - tau[i], chirp_bw_hz, chirp_period_s) for i in range(2)]
+            elif e.waveform == "sawtooth":
+                sig = [sawtooth(chirp_t0[m] + t_n - tau[i], chirp_bw_hz, chirp_period_s) for i in range(2)]
+            else:
+                raise ValueError(f"waveform {e.waveform!r} not supported in a multi-emitter scene")
+            for i in range(2):
+                acc[i] += amps[m] * sig[i] * np.exp(2j * np.pi * fd[i] * t_n)
+        total = sum(a * a for a in amps) + noise_p
+        for i, dst in enumerate((y1, y2)):
+            y = acc[i]
+            if noise:
+                y = y + (rng.standard_normal(n) + 1j * rng.standard_normal(n)) * math.sqrt(0.5)
+            dst[k] = quantize(y, fmt, total)
+    meta = dict(seed=seed, emitters=[dataclasses.asdict(e) for e in emitters], noise=noise,
+                formation=dataclasses.asdict(form))
+    return MultiScene(fs_hz=fs_hz, fc_hz=fc_hz, n_samples=n, k_steps=k_steps, fmt=fmt, grid=grid,
+                      ephem=ephem, y1=y1, y2=y2, emitters=list(emitters), emitter_nodes=nodes,
+                      emitter_latlon_deg=sites, meta=meta)
+
+
+def crowded(seed: int = 4, **kw) -> MultiScene:
+    """Three emitters at once on a 121x121 grid at 1 km: two independent
+    2 MHz noise emitters (one 3 dB weaker) and a 10 MHz / 10 us chirp;
+    K=12 snapshots 15 s apart x N=16384 complex int16 at fs 12.5 MHz."""
+    args = dict(seed=seed, fs_hz=12.5e6, n_samples=16384, k_steps=12, fmt="ci16", grid_n=121,
+                grid_spacing_m=1000.0, formation=Formation(dt_s=15.0),
+                emitters=[Emitter(0, 0, "noise", -3.0), Emitter(-25, 30, "chirp", -3.0),
+                          Emitter(35, -20, "noise", -6.0)])
+    args.update(kw)
+    return make_multi_scene(**args)
+
+
 # --------------------------------------------------------------------------
 # the workloads (sizes, formats, waveforms and SNRs of the five workloads)
 # --------------------------------------------------------------------------
@@ -372,3 +508,4 @@ def large(seed: int = 3, **kw) -> Scene:
 
 
 WORKLOADS = {"tiny": tiny, "mid": mid, "large": large}
+MULTI_WORKLOADS = {"crowded": crowded}

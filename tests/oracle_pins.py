@@ -296,4 +296,55 @@ def pin_argmax_ties_and_nan():
     assert oracle.argmax(np.array([-5.0, -5.0])) == 0
 
 
+def _bumps(shape, centres, amps, width=1.5):
+    ii, jj = np.meshgrid(np.arange(shape[0]), np.arange(shape[1]), indexing="ij")
+    v = np.zeros(shape)
+    for (ci, cj), a in zip(centres, amps):
+        v += a * np.exp(-((ii - ci) ** 2 + (jj - cj) ** 2) / (2 * width * width))
+    return v
+
+
+def pin_detect_known_bumps():
+    """Algorithm 1's threshold step on a surface of separated Gaussian bumps:
+    exactly the bump centres pass, strongest first; the threshold and
+    max_peaks cut from the weak end; a value equal to the threshold passes."""
+    centres, amps = [(5, 40), (30, 7), (33, 44), (0, 0)], [5.0, 3.0, 1.0, 2.0]
+    v = _bumps((41, 53), centres, amps)
+    order = [centres[k][0] * 53 + centres[k][1] for k in np.argsort(amps)[::-1]]
+    assert list(oracle.detect(v, 0.5, 3)) == order
+    assert list(oracle.detect(v, 2.5, 3)) == order[:2]
+    assert list(oracle.detect(v, 0.5, 3, max_peaks=1)) == order[:1]
+    assert list(oracle.detect(v, float(v[0, 0]), 3)) == order[:3]
+    assert list(oracle.detect(v, np.nextafter(v[0, 0], np.inf), 3)) == order[:2]
+
+
+def pin_detect_plateau_edges_radius():
+    """A flat top gives one peak, at its lowest linear index; windows clip at
+    the grid edge; radius 0 makes every node above the threshold a peak;
+    a wider window suppresses a lower neighbour bump."""
+    v = np.zeros((9, 11))
+    v[3:6, 4:7] = 2.0
+    v[8, 10] = 1.0
+    assert list(oracle.detect(v, 0.5, 2)) == [3 * 11 + 4, 8 * 11 + 10]
+    assert len(oracle.detect(v, 0.5, 0)) == 10
+    w = _bumps((21, 21), [(10, 5), (10, 9)], [2.0, 1.0], width=0.8)
+    assert list(oracle.detect(w, 0.1, 2)) == [10 * 21 + 5, 10 * 21 + 9]
+    assert list(oracle.detect(w, 0.1, 4)) == [10 * 21 + 5]
+
+
+def pin_detect_matches_maximum_filter():
+    """On continuous random surfaces (no ties), a peak is exactly a node
+    equal to scipy's maximum filter over the (2r+1)^2 window (edges padded
+    with -inf) and at least the threshold."""
+    from scipy import ndimage
+    rng = np.random.default_rng(11)
+    for shape, r in (((17, 23), 1), ((30, 12), 2), ((25, 25), 3)):
+        v = ndimage.gaussian_filter(rng.standard_normal(shape), 1.0)
+        thr = float(np.quantile(v, 0.6))
+        mf = ndimage.maximum_filter(v, size=2 * r + 1, mode="constant", cval=-np.inf)
+        want = np.flatnonzero((v == mf) & (v >= thr))
+        want = want[np.lexsort((want, -v.ravel()[want]))]
+        assert list(oracle.detect(v, thr, r, max_peaks=1000)) == list(want)
+
+
 ALL_PINS = [v for k, v in sorted(globals().items()) if k.startswith("pin_") and callable(v)]

@@ -29,6 +29,10 @@ MUTANTS = [
     ("no_accumulation", "s += (acc_mode == 0) ? pw : sqrt(pw);", "s = (acc_mode == 0) ? pw : sqrt(pw);"),
     ("argmax_tie", "cost[p] > cost[best]", "cost[p] >= cost[best]"),
     ("zero_pad_edge", "if (q < 0 || q >= n) continue;", "if (q < 0 || q > n) continue;"),
+    ("detect_tie_rule", "(v[q] == x && q < p)", "(v[q] == x && q > p)"),
+    ("detect_window_short", "for (int64_t di = -r; di <= r && peak; ++di)", "for (int64_t di = -r; di < r && peak; ++di)"),
+    ("detect_strict_threshold", "if (!(x >= threshold)) continue;", "if (!(x > threshold)) continue;"),
+    ("detect_sort_order", "(v[tmp[b]] < v[key] ||", "(v[tmp[b]] > v[key] ||"),
     ("phase_not_reduced_wrong", "double ang = 2.0 * DGO_PI * (ph - floor(ph));", "double ang = DGO_PI * (ph - floor(ph));"),
 ]
 
