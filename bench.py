@@ -272,6 +272,7 @@ def run_dg(a, rank, world, local_rank):
                                                      ("accumulate", P.DG_K_ACCUM), ("argmax", P.DG_K_ARGMAX),
                                                      ("refine", P.DG_K_REFINE))}
     bucket_chunks, cand_chunks = g.cdft_work()
+    chunk_lo, chunk_hi = g.cdft_chunks() if a.algo == "cdft" else (0, 0)
     corr_ms, corr_launches = kt["corr"]
     launches = g.launch_count()
     dev_s = sum(step_ms) / 1e3
@@ -300,7 +301,9 @@ def run_dg(a, rank, world, local_rank):
     if a.algo == "cdft":
         # every kernel of the chunked-DFT path against its own roofline; the
         # dominant one is the headline
-        chunk = a.chunk or 256
+        # with the automatic choice every batch of this workload took the
+        # same chunk (checked below); the flop count assumes one chunk
+        chunk = chunk_hi
         nprod = 3 if a.contract.endswith("x3") else 1
         tensor = a.contract != "fp32"
         # contraction: one chunk x 64-bin complex DFT per (lag, chunk) = 512 * chunk
@@ -356,7 +359,8 @@ def run_dg(a, rank, world, local_rank):
             "data": "synthetic",
             "config": {"workload": desc, "G": G_rank * world, "K": scene.k_steps, "N": scene.n_samples,
                        "fmt": scene.fmt, "delay": "integer", "algo": a.algo, "acc": "power",
-                       "chunk": (a.chunk or 256) if a.algo == "cdft" else None,
+                       "chunk": ((a.chunk if a.chunk else f"auto: {chunk_lo}..{chunk_hi}" if chunk_lo != chunk_hi
+                                  else f"auto: {chunk_hi}") if a.algo == "cdft" else None),
                        "contract": a.contract if a.algo == "cdft" else None,
                        "refine": f"{REFINE_SPACING_M:g} m spacing, +-{REFINE_WINDOW_M:g} m",
                        "l2": "flushed between timed steps (256 MB write outside the events)",
@@ -441,7 +445,7 @@ def main():
     ap.add_argument("--impl", choices=["dg", "reference"], default="dg")
     ap.add_argument("--workload", choices=["mid", "tiny", "large"], default="mid")
     ap.add_argument("--algo", choices=["direct", "cdft"], default="cdft")
-    ap.add_argument("--chunk", type=int, default=1024, help="CDFT samples per chunk")
+    ap.add_argument("--chunk", type=int, default=0, help="CDFT samples per chunk; 0 = automatic")
     ap.add_argument("--contract", choices=["fp32", "bf16", "fp16", "bf16x3", "fp16x3"], default="fp16x3")
     ap.add_argument("--no-direct", action="store_true", help="skip the direct-path reference measurement")
     ap.add_argument("--grid", type=int, default=0, help="override the grid to GRID x GRID nodes")

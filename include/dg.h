@@ -110,7 +110,10 @@ typedef struct {
     int32_t nrows;   /* rows in the shard; 0 = all rows from row0             */
     int32_t timing;  /* 1: time kernels with CUDA events (dg_kernel_time)     */
     int32_t chunk;   /* CDFT: samples per chunk, a multiple of 64 in [64,4096];
-                        0 = 256                                               */
+                        0 = chosen per batch of snapshots: the longest power
+                        of two <= 1024 whose length x bin spacing is <= 4e-3
+                        cycles in every snapshot of the batch
+                        (dg_cdft_chunks)                                      */
     int32_t bins;    /* CDFT: Doppler bins per lag; 0 = 64 (the only value)   */
     int32_t contract;/* CDFT: DG_CONTRACT_*                                   */
     int32_t reserved;
@@ -142,7 +145,8 @@ enum { DG_K_CORR = 0, DG_K_ACCUM = 1, DG_K_ARGMAX = 2, DG_K_GRID = 3, DG_K_REFIN
        DG_K_NCLASS = 8 };
 
 /* Defaults: INTEGER delay, POWER accumulation, FP32, DIRECT, whole grid, no
- * timing, CDFT chunk 256 / 64 bins / FP32 contraction. o must not be NULL. */
+ * timing, CDFT automatic chunk / 64 bins / FP32 contraction. o must not be
+ * NULL. */
 void dg_options_default(dg_options *o);
 
 /* Create a context for one grid and one set of K snapshot ephemerides.
@@ -237,6 +241,11 @@ dg_status dg_kernel_time(dg_ctx *ctx, int32_t kernel_class, double *ms, int64_t 
  * chunk-by-bins complex DFT) and candidate x chunk pairs combined. Host
  * pointers, may be NULL; zeros before the first CDFT surface. */
 dg_status dg_cdft_work(const dg_ctx *ctx, int64_t *bucket_chunks, int64_t *candidate_chunks);
+
+/* Shortest and longest chunk (samples) the last CDFT surface used, 0 if none
+ * has been computed; with opt.chunk = 0 they follow each batch's FDOA spans.
+ * Host only; either pointer may be NULL. */
+dg_status dg_cdft_chunks(const dg_ctx *ctx, int32_t *min_chunk, int32_t *max_chunk);
 
 /* Reset the counters behind dg_kernel_time and dg_launch_count. */
 dg_status dg_reset_counters(dg_ctx *ctx);

@@ -100,6 +100,7 @@ struct dg_ctx {
     LocalGrid loc;
     CdftBufs cd;
     int64_t cd_bucket_chunks = 0, cd_cand_chunks = 0;  // work of the last CDFT surface
+    int cd_chunk_min = 0, cd_chunk_max = 0;              // chunks it used
     std::string err;
     int64_t launches = 0;
     std::vector<TimedLaunch> pending;
@@ -299,6 +300,35 @@ constexpr size_t kCdftBatchBytes = (size_t)3 << 30;
 // per-(candidate, snapshot) arrays within kCdftBatchBytes); per batch: the
 // geometry pass, one small device-to-host copy of the lag ranges to size the
 // buckets, the plan, the contraction and the combine. Then the ordered sum.
+// The FDOA range of a snapshot comes back as two order-preserving keys of
+// FP32 values (the smallest and largest nu of its candidates).
+static float key_to_float(unsigned k)
+{
+    const unsigned b = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+    float f;
+    std::memcpy(&f, &b, sizeof f);
+    return f;
+}
+
+// Longest chunk, a power of two in [64, kCdftAutoMaxChunk], whose length
+// times the bin spacing stays within kCdftAutoMDelta cycles for every
+// snapshot of the batch: the bin interpolation error, about
+// (pi M Delta)^2 / 6, is then below 2.7e-5. The spacing is computed as the
+// plan kernel computes it. A snapshot too wide even for 64 samples gets 64,
+// and the plan's check rejects it.
+static int auto_chunk(const unsigned *nur, int S)
+{
+    float dmax = 0.0f;
+    for (int s = 0; s < S; ++s) {
+        const float lo = key_to_float(nur[2 * s]), hi = key_to_float(nur[2 * s + 1]);
+        if (!(hi >= lo)) continue;  // no candidate with a representable lag
+        dmax = std::max(dmax, std::max((hi - lo) * (1.0f + 1e-5f) / 63.0f, 1e-20f));
+    }
+    int M = kCdftAutoMaxChunk;
+    while (M > 64 && (double)M * (double)dmax > kCdftAutoMDelta) M >>= 1;
+    return M;
+}
+
 dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int64_t G, void *surf, void *out,
                            bool refine)
 {
@@ -308,9 +338,9 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         if (c->steps[k].n > (1 << 24))
             return fail(c, DG_EUNSUPPORTED, "CDFT: snapshots longer than 2^24 samples are not supported; use DIRECT");
     CdftBufs &b = c->cd;
-    const int M = c->opt.chunk ? c->opt.chunk : 256;
-    int Bmax = 1;
-    for (int k = 0; k < c->K; ++k) Bmax = std::max<int>(Bmax, (int)((c->steps[k].n + M - 1) / M));
+    // chunk 0: chosen per batch once its FDOA spans are known (auto_chunk);
+    // the tables are sized for the longest chunk allowed
+    const int M_cap = c->opt.chunk ? c->opt.chunk : kCdftAutoMaxChunk;
     const int s_max = (int)std::max<int64_t>(1, std::min<int64_t>(c->K, (int64_t)(kCdftBatchBytes / (12 * (size_t)G))));
     if (b.s_cap < (size_t)s_max) {
         if ((st = grow(c, &b.lr, 2 * (size_t)s_max)) != DG_OK) return st;
@@ -327,12 +357,16 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         if ((st = grow(c, &b.order, (size_t)s_max * G)) != DG_OK) return st;
         b.sg_cap = (size_t)s_max * G;
     }
-    if (b.v_cap < (size_t)s_max * M * 64) {
-        if ((st = grow(c, &b.V, (size_t)s_max * M * 64)) != DG_OK) return st;
-        b.v_cap = (size_t)s_max * M * 64;
+    if (b.v_cap < (size_t)s_max * M_cap * 64) {
+        if ((st = grow(c, &b.V, (size_t)s_max * M_cap * 64)) != DG_OK) return st;
+        b.v_cap = (size_t)s_max * M_cap * 64;
     }
     const int kplan = refine ? DG_K_REFINE : DG_K_CDFT_PLAN;
-    if (!refine) c->cd_bucket_chunks = c->cd_cand_chunks = 0;
+    if (!refine) {
+        c->cd_bucket_chunks = c->cd_cand_chunks = 0;
+        c->cd_chunk_min = INT_MAX;
+        c->cd_chunk_max = 0;
+    }
     // constants of the geometry as double-float (hi, lo) pairs
     auto split = [](double d, float &h, float &l) {
         h = (float)d;
@@ -359,9 +393,10 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         t.done(1);
     }
     std::vector<int> lr(2 * (size_t)s_max), bbase(s_max + 1), gbase(s_max + 1), tbase(s_max + 1);
+    std::vector<unsigned> nur(2 * (size_t)s_max);
     const bool mma = c->opt.contract != DG_CONTRACT_FP32;
     if (mma) {
-        const size_t bt = (size_t)s_max * cdft_btab_bytes(c->opt.contract, M);
+        const size_t bt = (size_t)s_max * cdft_btab_bytes(c->opt.contract, M_cap);
         if (b.tbase_cap < (size_t)s_max + 1) {
             if ((st = grow(c, &b.tbase, (size_t)s_max + 1)) != DG_OK) return st;
             b.tbase_cap = (size_t)s_max + 1;
@@ -392,8 +427,8 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         a.nlon = gd.nlon;
         a.fs = c->fs;
         a.lambda = c->lambda;
-        a.M = M;
-        a.Bmax = Bmax;
+        a.M = M_cap;
+        a.Bmax = 1;
         a.acc = c->opt.acc;
         a.err = c->err_d;
         a.lr = b.lr;
@@ -412,7 +447,18 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
             t.done(2);
         }
         CK(c, cudaMemcpyAsync(lr.data(), b.lr, sizeof(int) * 2 * (size_t)S, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaMemcpyAsync(nur.data(), b.nur, sizeof(unsigned) * 2 * (size_t)S, cudaMemcpyDeviceToHost,
+                              c->stream));
         CK(c, cudaStreamSynchronize(c->stream));
+        const int M = c->opt.chunk ? c->opt.chunk : auto_chunk(nur.data(), S);
+        int Bmax = 1;
+        for (int s = 0; s < S; ++s) Bmax = std::max<int>(Bmax, (int)((c->steps[k0 + s].n + M - 1) / M));
+        a.M = M;
+        a.Bmax = Bmax;
+        if (!refine) {
+            c->cd_chunk_min = std::min(c->cd_chunk_min, M);
+            c->cd_chunk_max = std::max(c->cd_chunk_max, M);
+        }
         int64_t nbt = 0, groups = 0;
         for (int s = 0; s < S; ++s) {
             const int64_t nb = lr[2 * s] <= lr[2 * s + 1] ? (int64_t)lr[2 * s + 1] - lr[2 * s] + 1 : 0;
@@ -905,6 +951,15 @@ dg_status dg_reset_counters(dg_ctx *c)
 }
 
 int64_t dg_launch_count(const dg_ctx *c) { return c ? c->launches : -1; }
+
+dg_status dg_cdft_chunks(const dg_ctx *c, int32_t *min_chunk, int32_t *max_chunk)
+{
+    if (!c) return DG_EINVAL;
+    const bool any = c->cd_chunk_max > 0;
+    if (min_chunk) *min_chunk = any ? c->cd_chunk_min : 0;
+    if (max_chunk) *max_chunk = any ? c->cd_chunk_max : 0;
+    return DG_OK;
+}
 
 dg_status dg_cdft_work(const dg_ctx *c, int64_t *bucket_chunks, int64_t *candidate_chunks)
 {

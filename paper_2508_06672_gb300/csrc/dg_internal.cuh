@@ -307,6 +307,15 @@ cudaError_t launch_cdft_btab(const CdftBatch &a, int mode, void *btab, cudaStrea
 cudaError_t launch_cdft_contract_mma(const CdftBatch &a, int tiles, int fmt, int mode, cudaStream_t s);
 size_t cdft_btab_bytes(int mode, int M);  // per snapshot
 
+// CDFT chunk bounds: the longest chunk; the longest the automatic choice
+// takes (longer chunks shorten the combine but lengthen the tables and the
+// contraction's operand stream: 1024 was fastest on the 1001^2 and 4001^2
+// workloads); and the chunk x bin-spacing product (cycles) it keeps below,
+// the same bound the plan enforces.
+constexpr int kCdftMaxChunk = 4096;
+constexpr int kCdftAutoMaxChunk = 1024;
+constexpr double kCdftAutoMDelta = 4e-3;
+
 // Threshold detection (dg_detect.cu). cap: power of two <= kDetectCap candidates
 // (the sort keeps value + index of each in static shared memory, 32 KiB).
 constexpr int kDetectCap = 2048;

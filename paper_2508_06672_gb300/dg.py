@@ -55,7 +55,7 @@ EXPORTED_SYMBOLS = [
     "dg_options_default", "dg_create", "dg_load_capture", "dg_cost_surface", "dg_argmax_refine",
     "dg_sync", "dg_destroy", "dg_last_error", "dg_grid_ecef", "dg_step_geometry", "dg_kernel_time",
     "dg_reset_counters", "dg_launch_count", "dg_abi_version", "dg_cost_surface_noalloc",
-    "dg_noalloc_last_error", "dg_cdft_work", "dg_detect",
+    "dg_noalloc_last_error", "dg_cdft_work", "dg_detect", "dg_cdft_chunks",
 ]
 DG_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
@@ -150,6 +150,8 @@ def lib():
             L.dg_cost_surface_noalloc.restype = C.c_int
             L.dg_detect.argtypes = [vp, vp, dbl, i32, i32, i32, C.POINTER(dg_peak), C.POINTER(i32)]
             L.dg_detect.restype = C.c_int
+            L.dg_cdft_chunks.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+            L.dg_cdft_chunks.restype = C.c_int
             L.dg_cdft_work.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
             L.dg_cdft_work.restype = C.c_int
             L.dg_noalloc_last_error.argtypes = []
@@ -392,6 +394,12 @@ class Geolocator:
 
     def cdft_work(self):
         return dg_cdft_work(self.ctx)
+
+    def cdft_chunks(self):
+        """(shortest, longest) chunk the last CDFT surface used."""
+        lo, hi = C.c_int32(), C.c_int32()
+        _check(lib().dg_cdft_chunks(self.ctx, C.byref(lo), C.byref(hi)), self.ctx)
+        return lo.value, hi.value
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -171,6 +171,35 @@ def tone(t, f_hz=0.0):
     return np.exp(2j * np.pi * f_hz * np.asarray(t, dtype=np.float64))
 
 
+def gold_code_prn1():
+    """The 1023-chip C/A Gold code of GPS PRN 1 as +-1 (chip 0 -> +1): the
+    product of two 10-stage maximal-length sequences, G1 with feedback
+    polynomial 1 + x^3 + x^10 and G2 with 1 + x^2 + x^3 + x^6 + x^8 + x^9 +
+    x^10, G2 read at the phase given by the xor of its stages 2 and 6; both
+    registers start all ones."""
+    g1 = [1] * 10
+    g2 = [1] * 10
+    out = np.empty(1023, dtype=np.int8)
+    for k in range(1023):
+        chip = g1[9] ^ g2[1] ^ g2[5]
+        out[k] = 1 - 2 * chip
+        f1 = g1[2] ^ g1[9]
+        f2 = g2[1] ^ g2[2] ^ g2[5] ^ g2[7] ^ g2[8] ^ g2[9]
+        g1 = [f1] + g1[:9]
+        g2 = [f2] + g2[:9]
+    return out
+
+
+def gps_ca(t, code, bits, chip_rate_hz=1.023e6, bit_rate_hz=50.0):
+    """BPSK spoofing waveform: the repeating 1 ms C/A code, rectangular chips,
+    times a 50 bit/s navigation-data sequence (bits: +-1, indexed by
+    whole bit periods from t = 0, wrapping)."""
+    t = np.asarray(t, dtype=np.float64)
+    chip = np.floor(t * chip_rate_hz).astype(np.int64) % code.size
+    bit = np.floor(t * bit_rate_hz).astype(np.int64) % bits.size
+    return (code[chip] * bits[bit]).astype(np.complex128)
+
+
 def bandlimited_noise_spectrum(rng, n_fft, fs_hz, bw_hz):
     """Spectrum of a unit-power periodic complex Gaussian noise of two-sided
     bandwidth bw_hz (brick-wall mask), length n_fft samples at fs_hz."""
@@ -361,6 +390,8 @@ class Emitter:
     waveform: str
     snr_db: float
     bw_hz: float = 2e6
+    chirp_bw_hz: float | None = None      # None: the scene's chirp parameters
+    chirp_period_s: float | None = None
 
 
 @dataclasses.dataclass
@@ -396,7 +427,7 @@ def make_multi_scene(
     k_steps: int,
     fmt: str,
     emitters: list,
-    grid_n: int,
+    grid_n: int | tuple,
     grid_spacing_m: float,
     noise: bool = True,
     fc_hz: float = 1575.42e6,
@@ -416,22 +447,27 @@ def make_multi_scene(
     t_mid = form.t0_s + 0.5 * (k_steps - 1) * form.dt_s
     lat0, lon0 = pick_emitter(rng, form, t_mid)
     dlat, dlon = _cell_degrees(lat0, grid_spacing_m)
-    c = (grid_n - 1) // 2
+    nlat, nlon = (grid_n, grid_n) if isinstance(grid_n, int) else grid_n
+    ci, cj = (nlat - 1) // 2, (nlon - 1) // 2
     grid = dict(lat0_deg=lat0, lon0_deg=lon0, dlat_m=grid_spacing_m, dlon_m=grid_spacing_m,
-                nlat=int(grid_n), nlon=int(grid_n))
+                nlat=int(nlat), nlon=int(nlon))
     sites, nodes = [], []
     for e in emitters:
-        if not (0 <= c + e.di < grid_n and 0 <= c + e.dj < grid_n):
+        if not (0 <= ci + e.di < nlat and 0 <= cj + e.dj < nlon):
             raise ValueError("emitter outside the grid")
         sites.append((lat0 + e.di * dlat, lon0 + e.dj * dlon))
-        nodes.append((c + e.di, c + e.dj))
+        nodes.append((ci + e.di, cj + e.dj))
     p_e = [geodetic_to_ecef(la, lo, 0.0) for la, lo in sites]
     ephem = form.ephemerides(k_steps)
     n = n_samples
     t_n = np.arange(n, dtype=np.float64) / fs_hz
     amps = [math.sqrt(10.0 ** (e.snr_db / 10.0)) for e in emitters]
     noise_p = 1.0 if noise else 0.0
-    chirp_t0 = [rng.uniform(0.0, chirp_period_s) for _ in emitters]
+    cp = [(e.chirp_bw_hz or chirp_bw_hz, e.chirp_period_s or chirp_period_s) for e in emitters]
+    chirp_t0 = [rng.uniform(0.0, p) for _, p in cp]
+    code = gold_code_prn1()
+    bits = [rng.choice(np.array([-1, 1], dtype=np.int8), size=4096) if e.waveform == "gps_ca" else None
+            for e in emitters]
     dt = {"c64": np.float32, "ci16": np.int16, "ci8": np.int8}[fmt]
     y1 = np.empty((k_steps, n, 2), dtype=dt)
     y2 = np.empty_like(y1)
@@ -445,9 +481,13 @@ def make_multi_scene(
                 spec, f = bandlimited_noise_spectrum(rng, n_fft, fs_hz, e.bw_hz)
                 sig = [delayed_noise(spec, f, tau[i] - tau[0], n) for i in range(2)]
             elif e.waveform == "chirp":
-                sig = [chirp(chirp_t0[m] + t_n - tau[i], chirp_bw_hz, chirp_period_s) for i in range(2)]
+                sig = [chirp(chirp_t0[m] + t_n - tau[i], *cp[m]) for i in range(2)]
             elif e.waveform == "sawtooth":
-                sig = [sawtooth(chirp_t0[m] + t_n - tau[i], chirp_bw_hz, chirp_period_s) for i in range(2)]
+                sig = [sawtooth(chirp_t0[m] + t_n - tau[i], *cp[m]) for i in range(2)]
+            elif e.waveform == "tone":
+                sig = [tone(t_n - tau[i]) for i in range(2)]
+            elif e.waveform == "gps_ca":
+                sig = [gps_ca(tk + t_n - tau[i], code, bits[m]) for i in range(2)]
             else:
                 raise ValueError(f"waveform {e.waveform!r} not supported in a multi-emitter scene")
             for i in range(2):
@@ -473,6 +513,22 @@ def crowded(seed: int = 4, **kw) -> MultiScene:
                 grid_spacing_m=1000.0, formation=Formation(dt_s=15.0),
                 emitters=[Emitter(0, 0, "noise", -3.0), Emitter(-25, 30, "chirp", -3.0),
                           Emitter(35, -20, "noise", -6.0)])
+    args.update(kw)
+    return make_multi_scene(**args)
+
+
+def four_jammers(seed: int = 5, **kw) -> MultiScene:
+    """The paper's capture scenario (Sec. IV-B) at full size: a GPS L1 C/A
+    spoofer, a pure tone, a chirp (2 MHz, 20 us) and a sawtooth (200 kHz,
+    5 ms) at equal power on the corners of a rectangle; 58 captures 1 s apart,
+    each 50 ms at 5 MHz complex (N = 250000) on L1; a search grid of about
+    4 deg of latitude by 9 deg of longitude (401 x 801 nodes at 1.1 km).
+    The SNR (-10 dB per emitter) and the geometry are this simulator's."""
+    args = dict(seed=seed, fs_hz=5e6, n_samples=250_000, k_steps=58, fmt="ci16", grid_n=(401, 801),
+                grid_spacing_m=1100.0, formation=Formation(dt_s=1.0),
+                emitters=[Emitter(-60, -150, "gps_ca", -10.0), Emitter(-60, 150, "tone", -10.0),
+                          Emitter(60, -150, "chirp", -10.0, chirp_bw_hz=2e6, chirp_period_s=20e-6),
+                          Emitter(60, 150, "sawtooth", -10.0, chirp_bw_hz=200e3, chirp_period_s=5e-3)])
     args.update(kw)
     return make_multi_scene(**args)
 
@@ -508,4 +564,4 @@ def large(seed: int = 3, **kw) -> Scene:
 
 
 WORKLOADS = {"tiny": tiny, "mid": mid, "large": large}
-MULTI_WORKLOADS = {"crowded": crowded}
+MULTI_WORKLOADS = {"crowded": crowded, "four_jammers": four_jammers}

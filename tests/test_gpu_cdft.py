@@ -30,6 +30,26 @@ def test_cdft_small_scenes(fmt, acc):
     g.close()
 
 
+def test_cdft_auto_chunk():
+    """chunk 0: each batch takes the longest power-of-two chunk up to 1024
+    whose length times the bin spacing is within 4e-3 cycles; the result
+    stays within the FP32 tolerance, and a grid with a wider FDOA span gets a
+    shorter chunk."""
+    chunks = []
+    for fs, spacing in ((12.5e6, 100.0), (5e6, 25000.0)):
+        s = sim.make_scene(seed=23, fs_hz=fs, n_samples=40000, k_steps=2, fmt="ci16", waveform="chirp",
+                           snr_db=-3.0, grid_n=(41, 39), grid_spacing_m=spacing)
+        g, c = gpu_surface(s, algo="cdft")
+        lo, hi = g.cdft_chunks()
+        assert lo & (lo - 1) == 0 and hi & (hi - 1) == 0 and 64 <= lo <= hi <= 1024
+        ref = oracle_surface(s)
+        ok = ~lag_boundary_mask(s, np.arange(s.G))
+        assert rel_err(c.ravel()[ok], ref.ravel()[ok], 0.01) < FP32_TOL
+        chunks.append(hi)
+        g.close()
+    assert chunks[1] < chunks[0]
+
+
 @pytest.mark.parametrize("chunk", [64, 1024, 4096])
 def test_cdft_chunk_sizes(chunk):
     s = sim.make_scene(seed=22, fs_hz=20e6, n_samples=9000, k_steps=2, fmt="ci8", waveform="noise",
