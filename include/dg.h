@@ -76,6 +76,15 @@ enum { DG_PREC_FP32 = 0, DG_PREC_FP64 = 1 };
  * (DG_CONTRACT_*). */
 enum { DG_ALGO_DIRECT = 0, DG_ALGO_CDFT = 1 };
 
+/* Rows of one tensor-core tile of the CDFT contraction (128 rows each).
+ * ROWS: consecutive (lag, chunk) pairs, lag-major; each row reads its own
+ * capture segments. LAGS: 128 consecutive lags at one chunk; the rows share
+ * one y1 segment and one y2 window, staged once per tile (chunk <= 1024).
+ * AUTO takes LAGS unless padding the lags of a snapshot to whole blocks of
+ * 128 more than doubles the tile count. Both form the same lag products
+ * (the 16-bit scale is a power of two), so the surfaces are identical. */
+enum { DG_TILES_AUTO = 0, DG_TILES_ROWS = 1, DG_TILES_LAGS = 2 };
+
 /* Arithmetic of the CDFT contraction: FP32 on CUDA cores, or 16-bit
  * tensor-core products accumulated in FP32. BF16 / FP16 round the lag products
  * and the DFT matrix once to 16 bits. The X3 forms split each into a 16-bit
@@ -116,7 +125,7 @@ typedef struct {
                         (dg_cdft_chunks)                                      */
     int32_t bins;    /* CDFT: Doppler bins per lag; 0 = 64 (the only value)   */
     int32_t contract;/* CDFT: DG_CONTRACT_*                                   */
-    int32_t reserved;
+    int32_t tiles;   /* CDFT tensor-core tile shape: DG_TILES_*               */
 } dg_options;
 
 typedef struct dg_ctx dg_ctx;

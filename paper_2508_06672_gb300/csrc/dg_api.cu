@@ -474,11 +474,26 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         }
         bbase[S] = (int)nbt;
         gbase[S] = (int)groups;
-        int64_t tiles = 0;  // tensor-core tiles: 128 (lag, chunk) rows each
+        // tensor-core tiles of 128 rows: (lag, chunk) rows in lag-major order,
+        // or 128 consecutive lags of one chunk (lag tiles, which share their
+        // capture windows); lag tiles unless their padding to whole blocks of
+        // 128 lags more than doubles the tile count (few lags per snapshot)
+        int64_t tiles_row = 0, tiles_lag = 0;
+        for (int s = 0; s < S; ++s) {
+            const int64_t nb = (int64_t)bbase[s + 1] - bbase[s];
+            const int64_t B = (c->steps[k0 + s].n + M - 1) / M;
+            tiles_row += (nb * B + 127) / 128;
+            tiles_lag += B * ((nb + 127) / 128);
+        }
+        const int tl = c->opt.tiles;
+        a.lag_tiles = (mma && M <= kLagTileMaxChunk &&
+                       (tl == DG_TILES_LAGS || (tl == DG_TILES_AUTO && tiles_lag <= 2 * tiles_row))) ? 1 : 0;
+        int64_t tiles = 0;
         for (int s = 0; s < S; ++s) {
             tbase[s] = (int)tiles;
             const int64_t nb = (int64_t)bbase[s + 1] - bbase[s];
-            tiles += (nb * ((c->steps[k0 + s].n + M - 1) / M) + 127) / 128;
+            const int64_t B = (c->steps[k0 + s].n + M - 1) / M;
+            tiles += a.lag_tiles ? B * ((nb + 127) / 128) : (nb * B + 127) / 128;
         }
         tbase[S] = (int)tiles;
         if (nbt > ((int64_t)1 << 26) || groups > INT_MAX)
@@ -648,6 +663,10 @@ dg_status dg_create(const dg_grid *grid, const dg_ephem *eph, int32_t K, double 
         if (o.bins != 0 && o.bins != 64) return fail(nullptr, DG_EUNSUPPORTED, "bins must be 0 or 64");
         if (o.contract < DG_CONTRACT_FP32 || o.contract > DG_CONTRACT_FP16X3)
             return fail(nullptr, DG_EINVAL, "unknown contraction arithmetic %d", o.contract);
+        if (o.tiles < DG_TILES_AUTO || o.tiles > DG_TILES_LAGS)
+            return fail(nullptr, DG_EINVAL, "unknown tile shape %d", o.tiles);
+        if (o.tiles == DG_TILES_LAGS && o.chunk > kLagTileMaxChunk)
+            return fail(nullptr, DG_EINVAL, "lag tiles need chunk <= %d", kLagTileMaxChunk);
     }
     if (o.row0 < 0 || o.row0 >= grid->nlat) return fail(nullptr, DG_EINVAL, "row0 outside the grid");
     if (o.nrows < 0 || o.row0 + o.nrows > grid->nlat) return fail(nullptr, DG_EINVAL, "row shard outside the grid");

@@ -187,6 +187,16 @@ template <> __device__ __forceinline__ float from16<DG_CONTRACT_FP16>(uint16_t h
     return __half2float(*reinterpret_cast<const __half *>(&h));
 }
 
+template <int DT> __device__ __forceinline__ float2 unpack2(uint32_t v);
+template <> __device__ __forceinline__ float2 unpack2<DG_CONTRACT_BF16>(uint32_t v)
+{
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&v));
+}
+template <> __device__ __forceinline__ float2 unpack2<DG_CONTRACT_FP16>(uint32_t v)
+{
+    return __half22float2(*reinterpret_cast<const __half2 *>(&v));
+}
+
 // Step of the batch owning tile t (tbase[s] <= t < tbase[s+1]).
 __device__ __forceinline__ int step_of_tile(const int *base, int S, int t)
 {
@@ -614,6 +624,206 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_mma(CdftBatch a
     if (warp == 0) tmem_dealloc(tmem, 128);
 }
 
+// Lag-tile form of the same contraction. A tile is 128 consecutive lags
+// L0 .. L0 + 127 of one snapshot at one chunk b: every row needs y1 over the
+// chunk and y2 shifted by its own lag, so the tile stages y1[bM .. bM + M)
+// (pre-scaled by zscale) and the window y2[bM + L0 .. bM + L0 + M + 127) once,
+// decoded to FP32, in shared memory; the producers then form each stage's lag
+// products from shared memory only. Samples outside [0, N) are staged as
+// zero, so the sums run over the overlap. The ring, the control thread, the
+// bounded waits and the epilogue are those of k_cdft_contract_mma; rows are
+// lags here, so row r of the tile writes W[bucket L0 + r - Lmin][b].
+template <int P> __host__ __device__ constexpr int lag_smem_bytes()
+{
+    return ws_smem_bytes<P>() + (2 * kLagTileMaxChunk + kRows) * (int)sizeof(float2);
+}
+
+template <int FMT, int DT, int P>
+__global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_lag(CdftBatch a)
+{
+    constexpr int NS = kRing;
+    constexpr int kSt = 2 * P * kBlockBytes;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full_a[NS], full_b[NS], empty[NS];
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int s_abort;
+    __shared__ int s_last_commit;
+
+    const int tile = blockIdx.x;
+    const int s = step_of_tile(a.tbase, a.S, tile);
+    const int ltile = tile - a.tbase[s];
+    const StepDesc sd = a.sd[s];
+    const int N = sd.n, M = a.M;
+    const int NB = a.bbase[s + 1] - a.bbase[s];
+    const int NLB = (NB + kRows - 1) / kRows;
+    const int lb = ltile % NLB, b = ltile / NLB;
+    const int Lmin = a.lr[2 * s];
+    const int L0 = Lmin + lb * kRows;
+    const int NJ = M / kKS;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *sA0 = smem;
+    unsigned char *sB0 = smem + NS * kSt;
+    float2 *sy1 = reinterpret_cast<float2 *>(smem + 2 * NS * kSt);
+    float2 *sy2 = sy1 + kLagTileMaxChunk;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NS; ++i) {
+            mbar_init(smem_u32(&full_a[i]), kProducerWarps);
+            mbar_init(smem_u32(&full_b[i]), 1);
+            mbar_init(smem_u32(&empty[i]), 1);
+        }
+        s_abort = 0;
+        s_last_commit = -1;
+        fence_mbar_init();
+        fence_proxy_async_smem();
+    }
+    if (warp == 0) tmem_alloc(smem_u32(&tmem_slot), 128);
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = tmem_slot;
+    const unsigned char *bsrc = reinterpret_cast<const unsigned char *>(a.btab) + (size_t)s * NJ * kSt;
+
+    if (warp < kProducerWarps) {
+        // ---- stage the tile's windows (producers only; named barrier 1)
+        const int nb0 = b * M;
+        const float zs = a.zscale;
+        for (int i = threadIdx.x; i < M; i += kProducerWarps * 32) {
+            const int n = nb0 + i;
+            float2 v = n < N ? IQ<FMT>::load(sd.y1, n) : make_float2(0.f, 0.f);
+            sy1[i] = make_float2(v.x * zs, v.y * zs);
+        }
+        for (int i = threadIdx.x; i < M + kRows; i += kProducerWarps * 32) {
+            const int n2 = nb0 + L0 + i;
+            sy2[i] = (n2 >= 0 && n2 < N) ? IQ<FMT>::load(sd.y2, n2) : make_float2(0.f, 0.f);
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(kProducerWarps * 32) : "memory");
+        // ---- producers: lane = 8 rows x 4 groups of 8 samples, two row sets per warp
+        const int rin = lane & 7, kg = lane >> 3;
+        for (int j = 0; j < NJ; ++j) {
+            const int slot = j % NS;
+            if (j >= NS && !mbar_wait(smem_u32(&empty[slot]), (uint32_t)((j / NS) - 1) & 1u)) s_abort = 1;
+            if (s_abort) break;
+            unsigned char *sA = sA0 + slot * kSt;
+            const int m0 = j * kKS + 8 * kg;
+            float2 x[8];
+#pragma unroll
+            for (int u = 0; u < 8; u += 2) {
+                const float4 q = *reinterpret_cast<const float4 *>(sy1 + m0 + u);
+                x[u] = make_float2(q.x, q.y);
+                x[u + 1] = make_float2(q.z, q.w);
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int row = 16 * warp + 8 * h + rin;
+                const float2 *py = sy2 + m0 + row;
+                float zr[8], zi[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float2 y = py[u];
+                    zr[u] = fmaf(x[u].x, y.x, x[u].y * y.y);
+                    zi[u] = fmaf(x[u].y, y.x, -x[u].x * y.y);
+                }
+                uint32_t hr[4], hi[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    hr[u] = pack2<DT>(zr[2 * u], zr[2 * u + 1]);
+                    hi[u] = pack2<DT>(zi[2 * u], zi[2 * u + 1]);
+                }
+                *reinterpret_cast<uint4 *>(sA + blk_off(row, 8 * kg)) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+                *reinterpret_cast<uint4 *>(sA + kBlockBytes + blk_off(row, 8 * kg)) =
+                    make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                if (P == 2) {  // residuals z - high part, rounded to 16 bits
+                    uint32_t lr[4], li[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float2 fr = unpack2<DT>(hr[u]), fi = unpack2<DT>(hi[u]);
+                        lr[u] = pack2<DT>(zr[2 * u] - fr.x, zr[2 * u + 1] - fr.y);
+                        li[u] = pack2<DT>(zi[2 * u] - fi.x, zi[2 * u + 1] - fi.y);
+                    }
+                    *reinterpret_cast<uint4 *>(sA + 2 * kBlockBytes + blk_off(row, 8 * kg)) =
+                        make_uint4(lr[0], lr[1], lr[2], lr[3]);
+                    *reinterpret_cast<uint4 *>(sA + 3 * kBlockBytes + blk_off(row, 8 * kg)) =
+                        make_uint4(li[0], li[1], li[2], li[3]);
+                }
+            }
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&full_a[slot]));
+        }
+    } else if (lane == 0) {
+        // ---- control: bulk copies of B, MMA issue, commits
+        for (int t = 0; t < NS && t < NJ; ++t) {
+            mbar_expect_tx(smem_u32(&full_b[t]), kSt);
+            bulk_g2s(smem_u32(sB0 + t * kSt), bsrc + (size_t)t * kSt, kSt, smem_u32(&full_b[t]));
+        }
+        const uint32_t id = idesc<DT>();
+        for (int j = 0; j < NJ; ++j) {
+            const int slot = j % NS;
+            const uint32_t ph = (uint32_t)(j / NS) & 1u;
+            if (!mbar_wait(smem_u32(&full_a[slot]), ph) || !mbar_wait(smem_u32(&full_b[slot]), ph) || s_abort) {
+                s_abort = 1;
+                break;
+            }
+            tc_after_sync();
+            const unsigned char *sA = sA0 + slot * kSt;
+            const unsigned char *sB = sB0 + slot * kSt;
+            constexpr int NPROD = P == 2 ? 3 : 1;
+#pragma unroll
+            for (int blk = 0; blk < 2; ++blk)
+#pragma unroll
+                for (int kk = 0; kk < kKS; kk += 16)
+#pragma unroll
+                    for (int pr = 0; pr < NPROD; ++pr) {
+                        const int pa = pr == 1 ? 1 : 0, pb = pr == 2 ? 1 : 0;
+                        const uint64_t ad = sdesc(smem_u32(sA + (2 * pa + blk) * kBlockBytes) + kk * 16);
+                        const uint64_t bd = sdesc(smem_u32(sB + (2 * pb + blk) * kBlockBytes) + kk * 16);
+                        mma_f16(tmem, ad, bd, id, (j > 0 || blk > 0 || kk > 0 || pr > 0) ? 1u : 0u);
+                    }
+            mma_commit(smem_u32(&empty[slot]));
+            s_last_commit = j;
+            if (j >= 1 && j - 1 + NS < NJ) {
+                const int s1 = (j - 1) % NS;
+                if (!mbar_wait(smem_u32(&empty[s1]), (uint32_t)((j - 1) / NS) & 1u)) {
+                    s_abort = 1;
+                    break;
+                }
+                mbar_expect_tx(smem_u32(&full_b[s1]), kSt);
+                bulk_g2s(smem_u32(sB0 + s1 * kSt), bsrc + (size_t)(j - 1 + NS) * kSt, kSt, smem_u32(&full_b[s1]));
+            }
+        }
+    }
+    __syncthreads();
+    const int lc = s_last_commit;
+    bool ok = lc >= 0 && mbar_wait(smem_u32(&empty[lc % NS]), (uint32_t)(lc / NS) & 1u);
+    ok = !__syncthreads_or(!ok || s_abort || lc != NJ - 1);
+    if (threadIdx.x == 0 && (s_abort || lc != NJ - 1)) atomicOr(a.err, ERR_TIMEOUT);
+    tc_after_sync();
+    if (ok && warp < 8) {
+        const int row = 32 * (warp & 3) + lane, half = warp >> 2;
+        const int bl = lb * kRows + row;
+        const bool valid = bl < NB && a.count[a.bbase[s] + bl] > 0;
+        const int64_t wrow = ((int64_t)(a.bbase[s] + bl) * a.Bmax + b) * 128;
+        const float inv = 1.0f / a.zscale;
+        const uint32_t tb = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * half);
+#pragma unroll
+        for (int c = 0; c < 64; c += 32) {
+            uint32_t r[32];
+            tmem_ld32(tb + (uint32_t)c, r);
+            if (valid) {
+                float4 *w = reinterpret_cast<float4 *>(a.W + wrow + 64 * half + c);
+#pragma unroll
+                for (int v = 0; v < 8; ++v)
+                    w[v] = make_float4(__uint_as_float(r[4 * v]) * inv, __uint_as_float(r[4 * v + 1]) * inv,
+                                       __uint_as_float(r[4 * v + 2]) * inv, __uint_as_float(r[4 * v + 3]) * inv);
+            }
+        }
+    }
+    tc_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 128);
+}
+
 cudaError_t launch_cdft_btab(const CdftBatch &a, int mode, void *btab, cudaStream_t st)
 {
     const size_t n = (size_t)(a.M / kKS) * 2 * kRows * kKS;
@@ -633,6 +843,15 @@ size_t cdft_btab_bytes(int mode, int M) { return (size_t)(M / kKS) * 2 * (mode >
 template <int FMT, int DT, int P>
 static cudaError_t launch_mma(const CdftBatch &a, int tiles, cudaStream_t st)
 {
+    if (a.lag_tiles) {
+        if (a.M > kLagTileMaxChunk) return cudaErrorInvalidValue;
+        const int smem = lag_smem_bytes<P>();
+        cudaError_t e = cudaFuncSetAttribute(k_cdft_contract_lag<FMT, DT, P>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        k_cdft_contract_lag<FMT, DT, P><<<(unsigned)tiles, kWsThreads, smem, st>>>(a);
+        return cudaGetLastError();
+    }
     const int smem = ws_smem_bytes<P>();
     cudaError_t e = cudaFuncSetAttribute(k_cdft_contract_mma<FMT, DT, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;

@@ -293,6 +293,7 @@ struct CdftBatch {
     const int *tbase;             // [S + 1] first tensor-core tile (128 rows) of each snapshot (device)
     const void *btab;             // [S][M/32][2][128 x 32] 16-bit DFT operand (tensor cores)
     float zscale;                 // lag products are multiplied by this before 16-bit rounding
+    int lag_tiles;                // 1: tensor-core tiles are 128 consecutive lags x one chunk
 };
 
 cudaError_t launch_cdft_geo(const CdftBatch &a, cudaStream_t s);
@@ -306,6 +307,9 @@ cudaError_t launch_cdft_combine(const CdftBatch &a, int groups, float *surf, cud
 cudaError_t launch_cdft_btab(const CdftBatch &a, int mode, void *btab, cudaStream_t s);
 cudaError_t launch_cdft_contract_mma(const CdftBatch &a, int tiles, int fmt, int mode, cudaStream_t s);
 size_t cdft_btab_bytes(int mode, int M);  // per snapshot
+// Lag tiles (128 consecutive lags of one chunk share one y1 segment and one
+// y2 window, staged once in shared memory) need chunk <= this.
+constexpr int kLagTileMaxChunk = 1024;
 
 // CDFT chunk bounds: the longest chunk; the longest the automatic choice
 // takes (longer chunks shorten the combine but lengthen the tables and the

@@ -39,6 +39,7 @@ DG_ACC_POWER, DG_ACC_MAG = 0, 1
 DG_PREC_FP32, DG_PREC_FP64 = 0, 1
 DG_ALGO_DIRECT, DG_ALGO_CDFT = 0, 1
 DG_CONTRACT_FP32, DG_CONTRACT_BF16, DG_CONTRACT_FP16, DG_CONTRACT_BF16X3, DG_CONTRACT_FP16X3 = 0, 1, 2, 3, 4
+DG_TILES_AUTO, DG_TILES_ROWS, DG_TILES_LAGS = 0, 1, 2
 DG_K_CORR, DG_K_ACCUM, DG_K_ARGMAX, DG_K_GRID, DG_K_REFINE = 0, 1, 2, 3, 4
 DG_K_CDFT_PLAN, DG_K_CDFT_CONTRACT, DG_K_CDFT_COMBINE = 5, 6, 7
 
@@ -48,6 +49,7 @@ _DELAY = {"integer": DG_DELAY_INTEGER, "lagrange4": DG_DELAY_LAGRANGE4}
 _ACC = {"power": DG_ACC_POWER, "mag": DG_ACC_MAG}
 _PREC = {"fp32": DG_PREC_FP32, "fp64": DG_PREC_FP64}
 _ALGO = {"direct": DG_ALGO_DIRECT, "cdft": DG_ALGO_CDFT}
+_TILES = {"auto": DG_TILES_AUTO, "rows": DG_TILES_ROWS, "lags": DG_TILES_LAGS}
 _CONTRACT = {"fp32": DG_CONTRACT_FP32, "bf16": DG_CONTRACT_BF16, "fp16": DG_CONTRACT_FP16,
              "bf16x3": DG_CONTRACT_BF16X3, "fp16x3": DG_CONTRACT_FP16X3}
 
@@ -85,7 +87,7 @@ class dg_options(C.Structure):
     _fields_ = [("delay", C.c_int32), ("acc", C.c_int32), ("prec", C.c_int32), ("algo", C.c_int32),
                 ("row0", C.c_int32), ("nrows", C.c_int32), ("timing", C.c_int32),
                 ("chunk", C.c_int32), ("bins", C.c_int32), ("contract", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("tiles", C.c_int32)]
 
 
 class dg_peak(C.Structure):
@@ -291,7 +293,7 @@ class Geolocator:
 
     def __init__(self, grid, ephem, fs_hz, fc_hz, *, delay="integer", acc="power", prec="fp32",
                  algo="direct", row0=0, nrows=0, timing=False, stream=None, device=None,
-                 chunk=0, bins=0, contract="fp32"):
+                 chunk=0, bins=0, contract="fp32", tiles="auto"):
         import torch
 
         self.torch = torch
@@ -306,6 +308,7 @@ class Geolocator:
         self.opt.prec, self.opt.algo = _PREC[prec], _ALGO[algo]
         self.opt.row0, self.opt.nrows, self.opt.timing = int(row0), int(nrows), int(bool(timing))
         self.opt.chunk, self.opt.bins, self.opt.contract = int(chunk), int(bins), _CONTRACT[contract]
+        self.opt.tiles = _TILES[tiles]
         self.nrows = int(nrows) if nrows else int(grid["nlat"]) - int(row0)
         self.nlon = int(grid["nlon"])
         self.dtype = torch.float64 if prec == "fp64" else torch.float32

@@ -30,6 +30,32 @@ def test_cdft_small_scenes(fmt, acc):
     g.close()
 
 
+@pytest.mark.parametrize("fmt", ["c64", "ci16", "ci8"])
+@pytest.mark.parametrize("contract", ["bf16", "fp16x3"])
+def test_cdft_lag_tiles_match_row_tiles(fmt, contract):
+    """Tensor-core tiles of 128 consecutive lags at one chunk (shared capture
+    windows) and tiles of consecutive (lag, chunk) rows form the same lag
+    products: the surfaces are bit-identical, and within the form's bound of
+    the oracle. Five blocks of 128 lags (75 .. 707), a ragged last chunk, and
+    y2 windows that run off the end of the capture."""
+    s = sim.make_scene(seed=24, fs_hz=20e6, n_samples=5000, k_steps=2, fmt=fmt, waveform="noise",
+                       snr_db=-3.0, grid_n=(45, 41), grid_spacing_m=2000.0, bw_hz=18e6)
+    out = {}
+    for tiles in ("rows", "lags"):
+        g, c = gpu_surface(s, algo="cdft", contract=contract, chunk=1024, tiles=tiles)
+        out[tiles] = c
+        g.close()
+    assert np.array_equal(out["rows"], out["lags"])
+    ref = oracle_surface(s)
+    ok = ~lag_boundary_mask(s, np.arange(s.G))
+    # BF16 keeps 8 significant bits of each lag product and DFT entry: the
+    # power |C|^2 of a noise-like node then carries a relative error of std
+    # ~2^-8, and the maximum over ~1800 nodes of two snapshots reaches
+    # ~4 std; the split form is held to the FP32 bound
+    tol = TC_TOL[contract] if contract.endswith("x3") else 3e-2
+    assert rel_err(out["lags"].ravel()[ok], ref.ravel()[ok], 0.01) < tol
+
+
 def test_cdft_auto_chunk():
     """chunk 0: each batch takes the longest power-of-two chunk up to 1024
     whose length times the bin spacing is within 4e-3 cycles; the result
