@@ -79,6 +79,16 @@ def tensor_peak(contract):
         return 1900.0
 
 
+def hbm_peak():
+    """Measured HBM copy bandwidth (GB/s), else the recipe's fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -311,25 +321,38 @@ def run_dg(a, rank, world, local_rank):
         contract_flops = (nprod if tensor else 1) * 512 * chunk * bucket_chunks
         alu_peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
         tc_peak = tensor_peak(a.contract)
-        for name, flops, bound, peak, basis in (
+        # combine: when the super-chunks leave about one per candidate the
+        # kernel is a gather (order index, FDOA, surface write: 12 B per
+        # candidate and snapshot, plus the W rows the super-chunk pass reads
+        # and writes, 2 x 512 B per (lag, chunk)); otherwise it is FP32 work
+        gk = G_rank * scene.k_steps
+        combine_hbm = cand_chunks <= 2 * gk
+        combine_units = (12 * gk + 1024 * bucket_chunks) / 1e12 if combine_hbm else CDFT_COMBINE_FLOPS * cand_chunks
+        for name, flops, bound, peak, basis, unit in (
                 ("contract", contract_flops, "tensor" if tensor else "alu", tc_peak if tensor else alu_peak,
-                 f"{'3 x ' if nprod == 3 and tensor else ''}512 flop x chunk per (lag, chunk) row"),
-                ("combine", CDFT_COMBINE_FLOPS * cand_chunks, "alu", alu_peak,
-                 f"{CDFT_COMBINE_FLOPS} flop per candidate x chunk (bin interpolation 6 + phase MAC 8)")):
+                 f"{'3 x ' if nprod == 3 and tensor else ''}512 flop x chunk per (lag, chunk) row", "TFLOP/s"),
+                ("combine", combine_units * (1e12 if combine_hbm else 1), "hbm" if combine_hbm else "alu",
+                 hbm_peak() if combine_hbm else alu_peak,
+                 ("12 B per candidate x snapshot + 1024 B per (lag, chunk) (super-chunk pass)" if combine_hbm else
+                  f"{CDFT_COMBINE_FLOPS} flop per candidate x super-chunk (bin interpolation 6 + phase MAC 8)"),
+                 "GB/s" if combine_hbm else "TFLOP/s")):
             ms, n = kt[name]
             if n:
-                ach = flops * a.steps / (ms / 1e3) / 1e12
-                kernels[name] = {"bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                scale = 1e9 if unit == "GB/s" else 1e12
+                ach = flops * a.steps / (ms / 1e3) / scale
+                kernels[name] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit,
                                  "frac": ach / peak, "ms_per_step": ms / a.steps, "basis": basis}
         dom = max(("contract", "combine"), key=lambda n: kt[n][0])
-        flops_per_step = contract_flops if dom == "contract" else CDFT_COMBINE_FLOPS * cand_chunks
+        flops_per_step = contract_flops if dom == "contract" else combine_units * (1e12 if combine_hbm else 1)
         corr_ms, corr_launches = kt[dom]
         roof_kernel = {"contract": (f"k_cdft_contract_mma ({a.contract} tcgen05, {chunk}-sample chunks x 64 bins)"
                                     if tensor else f"k_cdft_contract_f32 (FP32 CUDA cores, {chunk}-sample chunks)"),
-                       "combine": "k_cdft_combine (FP32, per-candidate interpolation + chunk phase sum)"}[dom]
+                       "combine": "k_cdft_superchunk + k_cdft_combine (per-candidate interpolation + super-chunk phase sum)"}[dom]
         roof_basis = kernels[dom]["basis"]
         roof_bound, roof_peak = kernels[dom]["bound"], kernels[dom]["peak"]
+        roof_unit = kernels[dom]["unit"]
     else:
+        roof_unit = "TFLOP/s"
         flops_per_step = FLOPS_PER_CAND_SAMPLE * G_rank * KN
         roof_kernel = "k_corr_direct (FP32, integer lag, ci16)"
         roof_basis = f"{FLOPS_PER_CAND_SAMPLE} flop per candidate*sample x G*K*N per launch"
@@ -349,7 +372,7 @@ def run_dg(a, rank, world, local_rank):
         fix = fixes[-1]
         centre = (scene.grid["nlat"] // 2, scene.grid["nlon"] // 2)  # the emitter's node
         gi, gj = divmod(int(gfix[1]), scene.grid["nlon"])
-        achieved = flops_per_step * a.steps / corr_s / 1e12
+        achieved = flops_per_step * a.steps / corr_s / (1e9 if roof_unit == "GB/s" else 1e12)
         peak = roof_peak
         clocks = clk.summary()
         line = {
@@ -368,10 +391,11 @@ def run_dg(a, rank, world, local_rank):
             "e2e": {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
-            "roofline": {"bound": roof_bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "roofline": {"bound": roof_bound, "achieved": achieved, "peak": peak, "unit": roof_unit,
                          "frac": achieved / peak, "traffic": None,
                          "kernel": roof_kernel,
-                         "peak_basis": (PEAK_BASIS_TENSOR if roof_bound == "tensor"
+                         "peak_basis": (PEAK_BASIS_TENSOR if roof_bound == "tensor" else
+                                        "measured HBM copy (MEASURED_PEAKS.json hbm_gbs)" if roof_bound == "hbm"
                                         else "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"),
                          "achieved_basis": roof_basis + " / CUDA-event time of the launches",
                          "launches": corr_launches, "ms_per_launch": 1e3 * corr_s / max(1, corr_launches)},

@@ -247,8 +247,10 @@ dg_status dg_kernel_time(dg_ctx *ctx, int32_t kernel_class, double *ms, int64_t 
 
 /* Work units of the last CDFT surface (dg_cost_surface with DG_ALGO_CDFT),
  * summed over snapshots: lag-bucket x chunk pairs contracted (each a
- * chunk-by-bins complex DFT) and candidate x chunk pairs combined. Host
- * pointers, may be NULL; zeros before the first CDFT surface. */
+ * chunk-by-bins complex DFT) and candidate x super-chunk pairs combined (the
+ * combine merges chunks at the bin frequencies into the longest power-of-two
+ * multiple of the chunk whose length x bin spacing stays <= 4e-3 cycles).
+ * Host pointers, may be NULL; zeros before the first CDFT surface. */
 dg_status dg_cdft_work(const dg_ctx *ctx, int64_t *bucket_chunks, int64_t *candidate_chunks);
 
 /* Shortest and longest chunk (samples) the last CDFT surface used, 0 if none

@@ -42,8 +42,10 @@ struct CdftBufs {  // chunked-DFT scratch, grown on demand
     float *nubase = nullptr;
     size_t s_cap = 0;
     int *candL = nullptr, *order = nullptr;
-    float *candNu = nullptr;
+    float *candNu = nullptr, *nuS = nullptr;
     size_t sg_cap = 0;
+    int *g2b = nullptr;
+    size_t g2b_cap = 0;
     float *xyzf = nullptr;
     size_t xyzf_cap = 0;
     float *ephf = nullptr;
@@ -316,7 +318,7 @@ static float key_to_float(unsigned k)
 // (pi M Delta)^2 / 6, is then below 2.7e-5. The spacing is computed as the
 // plan kernel computes it. A snapshot too wide even for 64 samples gets 64,
 // and the plan's check rejects it.
-static int auto_chunk(const unsigned *nur, int S)
+static float max_bin_spacing(const unsigned *nur, int S)
 {
     float dmax = 0.0f;
     for (int s = 0; s < S; ++s) {
@@ -324,9 +326,28 @@ static int auto_chunk(const unsigned *nur, int S)
         if (!(hi >= lo)) continue;  // no candidate with a representable lag
         dmax = std::max(dmax, std::max((hi - lo) * (1.0f + 1e-5f) / 63.0f, 1e-20f));
     }
+    return dmax;
+}
+
+static int auto_chunk(const unsigned *nur, int S)
+{
+    const float dmax = max_bin_spacing(nur, S);
     int M = kCdftAutoMaxChunk;
     while (M > 64 && (double)M * (double)dmax > kCdftAutoMDelta) M >>= 1;
     return M;
+}
+
+// Combine chunk: the longest power-of-two multiple of the contraction chunk M
+// whose length times the bin spacing stays within the same bound, up to the
+// first length that covers the longest snapshot (one super-chunk) and at most
+// 2^24 samples. The interpolation error bound of the combine is then that of
+// reading 20 in the design (about (pi Mc Delta)^2 / 6).
+static int combine_chunk(const unsigned *nur, int S, int M, int64_t nmax)
+{
+    const float dmax = max_bin_spacing(nur, S);
+    int64_t Mc = M;
+    while (Mc < nmax && 2 * Mc <= ((int64_t)1 << 24) && (double)(2 * Mc) * (double)dmax <= kCdftAutoMDelta) Mc *= 2;
+    return (int)Mc;
 }
 
 dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int64_t G, void *surf, void *out,
@@ -355,6 +376,7 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         if ((st = grow(c, &b.candL, (size_t)s_max * G)) != DG_OK) return st;
         if ((st = grow(c, &b.candNu, (size_t)s_max * G)) != DG_OK) return st;
         if ((st = grow(c, &b.order, (size_t)s_max * G)) != DG_OK) return st;
+        if ((st = grow(c, &b.nuS, (size_t)s_max * G)) != DG_OK) return st;
         b.sg_cap = (size_t)s_max * G;
     }
     if (b.v_cap < (size_t)s_max * M_cap * 64) {
@@ -439,6 +461,7 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         a.candL = b.candL;
         a.candNu = b.candNu;
         a.order = b.order;
+        a.nuS = b.nuS;
         a.delta = b.delta;
         a.V = b.V;
         {
@@ -452,9 +475,14 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         CK(c, cudaStreamSynchronize(c->stream));
         const int M = c->opt.chunk ? c->opt.chunk : auto_chunk(nur.data(), S);
         int Bmax = 1;
-        for (int s = 0; s < S; ++s) Bmax = std::max<int>(Bmax, (int)((c->steps[k0 + s].n + M - 1) / M));
+        int64_t nmax = 1;
+        for (int s = 0; s < S; ++s) {
+            Bmax = std::max<int>(Bmax, (int)((c->steps[k0 + s].n + M - 1) / M));
+            nmax = std::max<int64_t>(nmax, c->steps[k0 + s].n);
+        }
         a.M = M;
         a.Bmax = Bmax;
+        a.Mc = combine_chunk(nur.data(), S, M, nmax);
         if (!refine) {
             c->cd_chunk_min = std::min(c->cd_chunk_min, M);
             c->cd_chunk_max = std::max(c->cd_chunk_max, M);
@@ -469,7 +497,7 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
             if (!refine) {
                 const int64_t B = (c->steps[k0 + s].n + M - 1) / M;
                 c->cd_bucket_chunks += nb * B;
-                c->cd_cand_chunks += G * B;
+                c->cd_cand_chunks += G * ((c->steps[k0 + s].n + a.Mc - 1) / a.Mc);
             }
         }
         bbase[S] = (int)nbt;
@@ -514,6 +542,12 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
             if ((st = grow(c, &b.W, w_elems)) != DG_OK) return st;
             b.w_cap = w_elems;
         }
+        if (b.g2b_cap < (size_t)std::max<int64_t>(groups, 1)) {
+            if ((st = grow(c, &b.g2b, (size_t)std::max<int64_t>(groups, 1))) != DG_OK) return st;
+            b.g2b_cap = (size_t)std::max<int64_t>(groups, 1);
+        }
+        a.g2b = b.g2b;
+        CK(c, cudaMemsetAsync(b.g2b, 0xff, sizeof(int) * (size_t)std::max<int64_t>(groups, 1), c->stream));
         a.count = b.count;
         a.offs = b.offs;
         a.gofs = b.gofs;
@@ -554,8 +588,9 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         }
         {
             Timed t(c, refine ? DG_K_REFINE : DG_K_CDFT_COMBINE);
+            if (a.Mc > a.M) CK(c, launch_cdft_superchunk(a, (int)nbt, c->stream));
             CK(c, launch_cdft_combine(a, (int)groups, surf_f, c->stream));
-            t.done(1);
+            t.done(a.Mc > a.M ? 2 : 1);
         }
         // lr, bbase and gbase are rewritten by the next batch only after its
         // geometry pass has been synchronised, so reuse is ordered.
@@ -1017,6 +1052,8 @@ dg_status dg_destroy(dg_ctx *c)
     fr(c->cd.gbase);
     fr(c->cd.candL);
     fr(c->cd.order);
+    fr(c->cd.nuS);
+    fr(c->cd.g2b);
     fr(c->cd.candNu);
     fr(c->cd.xyzf);
     fr(c->cd.ephf);

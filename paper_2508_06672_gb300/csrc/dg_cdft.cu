@@ -242,8 +242,10 @@ __global__ void __launch_bounds__(1024) k_cdft_scan(CdftBatch a)
         a.offs[b] = oc;
         a.gofs[b] = og;
         const int n = a.count[b];
+        const int ng = (n + kCdftCombineThreads - 1) / kCdftCombineThreads;
+        for (int g = 0; g < ng; ++g) a.g2b[a.gbase[s] + og + g] = b;
         oc += n;
-        og += (n + kCdftCombineThreads - 1) / kCdftCombineThreads;
+        og += ng;
     }
     if (t == 0) {
         const float lo = unfkey(a.nur[2 * s]), hi = unfkey(a.nur[2 * s + 1]);
@@ -315,6 +317,7 @@ __global__ void __launch_bounds__(256) k_cdft_scatter(CdftBatch a)
         const int q0 = bin_of(a.candNu[(size_t)s * a.G + p], a.nubase[s], delta, t);
         const int pos = a.offs[b] + atomicAdd(a.subcnt + (size_t)b * 64 + q0, 1);
         a.order[(size_t)s * a.G + pos] = (int)p;
+        a.nuS[(size_t)s * a.G + pos] = a.candNu[(size_t)s * a.G + p];
     }
 }
 
@@ -405,6 +408,50 @@ __global__ void __launch_bounds__(256) k_cdft_contract_f32(CdftBatch a)
 }
 
 // ---------------------------------------------------------------------------
+// superchunk: merge the per-chunk DFTs of a bucket into super-chunks of
+// Mc = R M samples, exactly at the bin frequencies:
+//     U_c(nu_q) = sum_{r<R} e^{j 2 pi nu_q r M} W_{cR + r}(nu_q).
+// The combine then interpolates U_c between bins, and its error is governed
+// by Mc Delta instead of M Delta; the host picks Mc so that Mc Delta stays
+// within the same bound. One thread per (bucket, bin); each reads its own
+// bin of chunks cR .. cR + R - 1 and writes super-chunk c in place (c <= cR,
+// and later super-chunks read only later chunks).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_cdft_superchunk(CdftBatch a, int NBT)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)NBT * 64) return;
+    const int bg = (int)(t >> 6), q = (int)(t & 63);
+    if (a.count[bg] == 0) return;  // no candidate: W rows were not written
+    const int s = step_of(a.bbase, a.S, bg);
+    const int M = a.M, R = a.Mc / a.M;
+    const int B = (a.sd[s].n + M - 1) / M;
+    const float nq = a.nubase[s] + (float)q * a.delta[s];
+    float ex, ey;  // e^{j 2 pi nu_q M}
+    sincospif(2.0f * frac_mul(nq, (float)M), &ey, &ex);
+    float *Wb = a.W + (size_t)bg * a.Bmax * 128;
+    for (int c = 0; c * R < B; ++c) {
+        float ux = 0.f, uy = 0.f, px = 1.f, py = 0.f;
+        const int r1 = min(R, B - c * R);
+        for (int r = 0; r < r1; ++r) {
+            const float *w = Wb + (size_t)(c * R + r) * 128;
+            const float wx = w[q], wy = w[64 + q];
+            ux = fmaf(px, wx, fmaf(-py, wy, ux));
+            uy = fmaf(px, wy, fmaf(py, wx, uy));
+            if ((r & 15) == 15) {  // re-anchor the rotation every 16 chunks
+                sincospif(2.0f * frac_mul(nq, (float)((r + 1) * M)), &py, &px);
+            } else {
+                const float nx = fmaf(px, ex, -py * ey);
+                py = fmaf(px, ey, py * ex);
+                px = nx;
+            }
+        }
+        Wb[(size_t)c * 128 + q] = ux;
+        Wb[(size_t)c * 128 + 64 + q] = uy;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // combine: one thread per candidate, kCdftCombineThreads candidates of one
 // bucket per CTA (sorted by interpolation bin); the bucket's W streams through
 // shared memory in segments of kSeg chunks.
@@ -418,27 +465,20 @@ __global__ void __launch_bounds__(kCdftCombineThreads) k_cdft_combine(CdftBatch 
     // reads both neighbouring bins with one 16-byte load
     __shared__ __align__(16) float4 ws[kSeg][64];
     const int gid = blockIdx.x;
+    const int b = a.g2b[gid];  // the scan's map from combine group to bucket
+    if (b < 0) return;         // past the snapshot's last group (uniform)
     const int s = step_of(a.gbase, a.S, gid);
-    const int b_first = a.bbase[s], NB = a.bbase[s + 1] - b_first;
     const int lgid = gid - a.gbase[s];
-    if (NB == 0) return;  // uniform
-    // bucket b with gofs[b] <= lgid < gofs[b] + groups(b)
-    int lo = 0, hi = NB - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (a.gofs[b_first + mid] <= lgid) lo = mid; else hi = mid - 1;
-    }
-    const int b = b_first + lo;
     const int n_b = a.count[b];
     const int j = (lgid - a.gofs[b]) * kCdftCombineThreads + threadIdx.x;
-    if ((lgid - a.gofs[b]) * kCdftCombineThreads >= n_b) return;  // past the snapshot's last group (uniform)
     const bool active = j < n_b;
-    const int c = active ? a.order[(size_t)s * a.G + a.offs[b] + j] : 0;
-    const float nuf = active ? a.candNu[(size_t)s * a.G + c] : a.nubase[s];
+    const size_t sp = (size_t)s * a.G + a.offs[b] + j;
+    const int c = active ? a.order[sp] : 0;
+    const float nuf = active ? a.nuS[sp] : a.nubase[s];
     float t;
     const int q0 = bin_of(nuf, a.nubase[s], a.delta[s], t);
     const float w0 = 1.f - t, w1 = t;
-    const int M = a.M;
+    const int M = a.Mc;
     const int B = (a.sd[s].n + M - 1) / M;
     // chunk-to-chunk phase step e^{j 2 pi nu M}
     float ex, ey;
@@ -540,6 +580,13 @@ cudaError_t launch_cdft_contract_fp32(const CdftBatch &a, int NBT, int fmt, cuda
     case DG_IQ_CI16: k_cdft_contract_f32<DG_IQ_CI16><<<grid, 256, 0, st>>>(a); break;
     default: k_cdft_contract_f32<DG_IQ_CI8><<<grid, 256, 0, st>>>(a); break;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cdft_superchunk(const CdftBatch &a, int NBT, cudaStream_t st)
+{
+    const int64_t n = (int64_t)NBT * 64;
+    k_cdft_superchunk<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, NBT);
     return cudaGetLastError();
 }
 

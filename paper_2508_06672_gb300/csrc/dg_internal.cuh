@@ -284,6 +284,8 @@ struct CdftBatch {
     int *candL;                   // [S][G] lag (INT_MIN: not representable)
     float *candNu;                // [S][G] FDOA / fs
     int *order;                   // [S][G] candidates sorted by (bucket, bin)
+    float *nuS;                   // [S][G] their FDOAs, in the same order
+    int *g2b;                     // [groups] global bucket of each combine group (-1: none)
     int *count;                   // [NBT]
     int *offs, *gofs;             // [NBT]
     int *subcnt;                  // [NBT][64]
@@ -294,6 +296,7 @@ struct CdftBatch {
     const void *btab;             // [S][M/32][2][128 x 32] 16-bit DFT operand (tensor cores)
     float zscale;                 // lag products are multiplied by this before 16-bit rounding
     int lag_tiles;                // 1: tensor-core tiles are 128 consecutive lags x one chunk
+    int Mc;                       // combine chunk: a power-of-two multiple of M (k_cdft_superchunk)
 };
 
 cudaError_t launch_cdft_geo(const CdftBatch &a, cudaStream_t s);
@@ -302,6 +305,9 @@ cudaError_t launch_ecef_split(const double *xyz, int64_t G, float *xyzf, cudaStr
 cudaError_t launch_cdft_plan(const CdftBatch &a, int NBT, cudaStream_t s);
 cudaError_t launch_cdft_contract_fp32(const CdftBatch &a, int NBT, int fmt, cudaStream_t s);
 cudaError_t launch_cdft_combine(const CdftBatch &a, int groups, float *surf, cudaStream_t s);
+// W[bucket][c] <- sum over the Mc / M chunks b of super-chunk c of
+// e^{j 2 pi nu_q (b M - c Mc)} W[bucket][b] (in place; Mc > M)
+cudaError_t launch_cdft_superchunk(const CdftBatch &a, int NBT, cudaStream_t s);
 // tensor-core contraction (dg_cdft_mma.cu): mode DG_CONTRACT_BF16 / FP16 /
 // BF16X3 / FP16X3; tiles = total 128-row tiles of the batch (tbase[S])
 cudaError_t launch_cdft_btab(const CdftBatch &a, int mode, void *btab, cudaStream_t s);

@@ -76,6 +76,28 @@ def test_cdft_auto_chunk():
     assert chunks[1] < chunks[0]
 
 
+@pytest.mark.parametrize("contract", ["fp32", "fp16x3"])
+def test_cdft_superchunks(contract):
+    """The combine sums chunks at the bin frequencies into super-chunks as
+    long as the bin-spacing bound allows: a 4 km grid (narrow FDOA span)
+    needs one super-chunk per snapshot; a 1000 km grid at 5 MHz with 64-sample
+    chunks gets 256-sample super-chunks. Both stay within the FP32 bound of
+    the oracle."""
+    for fs, spacing, chunk, one in ((12.5e6, 100.0, 256, True), (5e6, 25000.0, 64, False)):
+        s = sim.make_scene(seed=25, fs_hz=fs, n_samples=40000, k_steps=2, fmt="ci16", waveform="chirp",
+                           snr_db=-3.0, grid_n=(41, 39), grid_spacing_m=spacing)
+        g, c = gpu_surface(s, algo="cdft", chunk=chunk, contract=contract)
+        _, cand_chunks = g.cdft_work()
+        if one:
+            assert cand_chunks == s.G * s.k_steps
+        else:
+            assert s.G * s.k_steps < cand_chunks < s.G * s.k_steps * (40000 // chunk)
+        ref = oracle_surface(s)
+        ok = ~lag_boundary_mask(s, np.arange(s.G))
+        assert rel_err(c.ravel()[ok], ref.ravel()[ok], 0.01) < FP32_TOL
+        g.close()
+
+
 @pytest.mark.parametrize("chunk", [64, 1024, 4096])
 def test_cdft_chunk_sizes(chunk):
     s = sim.make_scene(seed=22, fs_hz=20e6, n_samples=9000, k_steps=2, fmt="ci8", waveform="noise",
