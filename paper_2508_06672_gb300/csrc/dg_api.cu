@@ -437,9 +437,8 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         a.xyz = xyz;
         a.xyzf = b.xyzf;
         a.ephf = b.ephf + 24 * (size_t)k0;
-        split(c->fs, a.fs_hi, a.fs_lo);
-        split(c->lambda, a.lam_hi, a.lam_lo);
-        split(kC, a.c_hi, a.c_lo);
+        split(c->fs / kC, a.fsc_hi, a.fsc_lo);
+        split(1.0 / (c->lambda * c->fs), a.ilf_hi, a.ilf_lo);
         a.eph = c->eph + 12 * (size_t)k0;
         a.sd = c->steps_d + k0;
         a.S = S;

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(256) k_cdft_geo(CdftBatch a)
     dfl ed[12];
 #pragma unroll
     for (int t = 0; t < 12; ++t) ed[t] = {__ldg(a.ephf + 24 * (size_t)s + 2 * t), __ldg(a.ephf + 24 * (size_t)s + 2 * t + 1)};
-    const dfl fsd = {a.fs_hi, a.fs_lo}, lamd = {a.lam_hi, a.lam_lo}, cd = {a.c_hi, a.c_lo};
+    const dfl fsc = {a.fsc_hi, a.fsc_lo};
     __shared__ unsigned sflo[8], sfhi[8];
     int lo = INT_MAX, hi = INT_MIN;
     unsigned flo = 0xffffffffu, fhi = 0u;
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(256) k_cdft_geo(CdftBatch a)
         dfl D;
         float nuf;
         geometry_df({xf[p], xf[a.G + p]}, {xf[2 * a.G + p], xf[3 * a.G + p]}, {xf[4 * a.G + p], xf[5 * a.G + p]},
-                    ed, fsd, lamd, cd, D, nuf);
+                    ed, fsc, {a.ilf_hi, a.ilf_lo}, D, nuf);
         int L = INT_MIN;
         bool ok = fabsf(D.hi) < 1.0e9f;
         if (ok && !round_df(D, L)) {

@@ -112,38 +112,57 @@ __device__ __forceinline__ dfl df_mul(dfl a, dfl b)
     e = fmaf(a.lo, b.hi, e);
     return df_fast_two_sum(p, e);
 }
-__device__ __forceinline__ dfl df_div(dfl a, dfl b)
+// a + b without the renormalisation of the low words' sum: relative error
+// ~2^-44 of |a| + |b| (enough here: see geometry_df).
+__device__ __forceinline__ dfl df_add_fast(dfl a, dfl b)
 {
-    const float q1 = a.hi / b.hi;
-    const dfl r = df_sub(a, df_mul({q1, 0.f}, b));
-    const float q2 = r.hi / b.hi;
-    const dfl r2 = df_sub(r, df_mul({q2, 0.f}, b));
-    const float q3 = r2.hi / b.hi;
-    const dfl q = df_fast_two_sum(q1, q2);
-    return df_add(q, {q3, 0.f});
+    const dfl s = df_two_sum(a.hi, b.hi);
+    return df_fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
 }
+__device__ __forceinline__ dfl df_sub_fast(dfl a, dfl b) { return df_add_fast(a, {-b.hi, -b.lo}); }
+// sqrt of a double-float: one Newton correction of the FP32 root. The
+// residual a.hi - y^2 of y = sqrtf(a.hi) is exact in FP32, so one FMA gives it.
 __device__ __forceinline__ dfl df_sqrt(dfl a)
 {
     const float y = sqrtf(a.hi);
-    const dfl r = df_sub(a, df_mul({y, 0.f}, {y, 0.f}));
-    return df_fast_two_sum(y, r.hi / (2.f * y));
+    const float r = fmaf(-y, y, a.hi) + a.lo;
+    return df_fast_two_sum(y, __fdividef(r, 2.f * y));
 }
 
-// Eq. 3-10 in double-float: D = dtau * fs (samples, as hi + lo) and
-// nu = dfreq / fs. Same expression as geometry().
-__device__ __forceinline__ void geometry_df(dfl x, dfl y, dfl z, const dfl *e, dfl fs, dfl lambda, dfl c_light,
+// a / b for a double-float quotient: the FP32 quotient plus one correction
+// from the exact-by-FMA residual (relative error ~1e-14).
+__device__ __forceinline__ dfl df_div_fast(dfl a, dfl b)
+{
+    const float q1 = __fdividef(a.hi, b.hi);
+    const float r = fmaf(-q1, b.hi, a.hi) + (a.lo - q1 * b.lo);
+    return df_fast_two_sum(q1, __fdividef(r, b.hi));
+}
+
+// Eq. 3-10 for the chunked-DFT plan. The lag needs D = (rho2 - rho1) fs / c
+// to ~1e-7 samples (so that Eq. 9 rounds it as the FP64 expression does
+// wherever D is farther than 1e-6 from a rounding boundary), i.e. the ranges
+// to ~1e-6 m out of 1e6 m: double-float. The candidate and the receivers
+// are exact double-float splits of the FP64 values; every sum carries an
+// error of at most ~2^-44 of its operands' magnitude (~1e-6 m on the range
+// vectors, ~1e-7 m on the ranges), and fs / c is a double-float constant.
+// The FDOA, nu = (f2 - f1) / fs with f_i = -(r_i . v_i) / (rho_i lambda),
+// is a difference of two range rates of ~7 km/s whose result is used as the
+// phase rate over the whole capture; at nodes where |C| is a small remainder
+// of a cancelling sum, an error of 1e-9 cycles per sample already shows at
+// 1e-4 in |C|^2. So the range rates r_i . v_i / rho_i and their difference
+// are double-float too, and nu is rounded to FP32 once, at the end.
+__device__ __forceinline__ void geometry_df(dfl x, dfl y, dfl z, const dfl *e, dfl fs_over_c, dfl inv_lam_fs,
                                             dfl &D, float &nu)
 {
-    const dfl r1x = df_sub(e[0], x), r1y = df_sub(e[1], y), r1z = df_sub(e[2], z);
-    const dfl r2x = df_sub(e[6], x), r2y = df_sub(e[7], y), r2z = df_sub(e[8], z);
-    const dfl rho1 = df_sqrt(df_add(df_add(df_mul(r1x, r1x), df_mul(r1y, r1y)), df_mul(r1z, r1z)));
-    const dfl rho2 = df_sqrt(df_add(df_add(df_mul(r2x, r2x), df_mul(r2y, r2y)), df_mul(r2z, r2z)));
-    const dfl f1 = df_div(df_add(df_add(df_mul(r1x, e[3]), df_mul(r1y, e[4])), df_mul(r1z, e[5])), df_mul(rho1, lambda));
-    const dfl f2 = df_div(df_add(df_add(df_mul(r2x, e[9]), df_mul(r2y, e[10])), df_mul(r2z, e[11])), df_mul(rho2, lambda));
-    const dfl dtau = df_div(df_sub(rho2, rho1), c_light);
-    D = df_mul(dtau, fs);
-    const dfl nud = df_div(df_sub(f1, f2), fs);  // f_i carry the minus sign of Eq. 6
-    nu = nud.hi + nud.lo;
+    const dfl r1x = df_sub_fast(e[0], x), r1y = df_sub_fast(e[1], y), r1z = df_sub_fast(e[2], z);
+    const dfl r2x = df_sub_fast(e[6], x), r2y = df_sub_fast(e[7], y), r2z = df_sub_fast(e[8], z);
+    const dfl rho1 = df_sqrt(df_add_fast(df_add_fast(df_mul(r1x, r1x), df_mul(r1y, r1y)), df_mul(r1z, r1z)));
+    const dfl rho2 = df_sqrt(df_add_fast(df_add_fast(df_mul(r2x, r2x), df_mul(r2y, r2y)), df_mul(r2z, r2z)));
+    D = df_mul(df_sub_fast(rho2, rho1), fs_over_c);
+    const dfl q1 = df_div_fast(df_add_fast(df_add_fast(df_mul(r1x, e[3]), df_mul(r1y, e[4])), df_mul(r1z, e[5])), rho1);
+    const dfl q2 = df_div_fast(df_add_fast(df_add_fast(df_mul(r2x, e[9]), df_mul(r2y, e[10])), df_mul(r2z, e[11])), rho2);
+    const dfl n = df_mul(df_sub_fast(q1, q2), inv_lam_fs);  // (f2 - f1) lambda / (lambda fs)
+    nu = n.hi + n.lo;
 }
 
 // Eq. 9 on a double-float D: round half away from zero, in FP32 only.
@@ -280,7 +299,8 @@ struct CdftBatch {
     const int *bbase, *gbase;     // [S + 1] (device)
     const float *xyzf;            // [6][G] ECEF as double-float: x hi, x lo, y hi, y lo, z hi, z lo
     const float *ephf;            // [S][24] ephemerides as double-float (hi, lo) pairs
-    float fs_hi, fs_lo, lam_hi, lam_lo, c_hi, c_lo;  // fs, lambda, c as double-float
+    float fsc_hi, fsc_lo;         // fs / c as double-float (samples per metre)
+    float ilf_hi, ilf_lo;         // 1 / (lambda fs) as double-float
     int *candL;                   // [S][G] lag (INT_MIN: not representable)
     float *candNu;                // [S][G] FDOA / fs
     int *order;                   // [S][G] candidates sorted by (bucket, bin)
