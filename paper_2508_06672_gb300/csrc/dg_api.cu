@@ -36,8 +36,25 @@ struct TimedLaunch {
     cudaEvent_t a, b;
 };
 
+struct CdftLayout {  // batches and bucket / group bases of one grid size
+    struct Batch {
+        int k0, S, base;      // snapshots k0 .. k0 + S - 1; offset of its bases
+        int64_t nbt, groups;  // lag slots and combine groups (upper bounds)
+    };
+    int64_t G = -1;
+    double diam = 0.0;      // grid diameter bound the lag slots were sized for
+    std::vector<Batch> batches;
+    int s_max = 0;
+    int64_t nbt_max = 0, groups_max = 0;
+    int *bbase = nullptr, *gbase = nullptr;  // device, per batch: [S + 1] each
+};
+
 struct CdftBufs {  // chunked-DFT scratch, grown on demand
-    int *lr = nullptr, *bbase = nullptr, *gbase = nullptr;
+    int *lr = nullptr;
+    CdftLayout main_layout, loc_layout;
+    std::vector<double> main_span, loc_span;  // FDOA span estimates per snapshot
+    int *layout = nullptr, *Mcs = nullptr;
+    unsigned long long *work = nullptr;
     unsigned *nur = nullptr;
     float *nubase = nullptr;
     size_t s_cap = 0;
@@ -58,7 +75,6 @@ struct CdftBufs {  // chunked-DFT scratch, grown on demand
     float *W = nullptr;
     size_t w_cap = 0;
     int *tbase = nullptr;
-    size_t tbase_cap = 0;
     void *btab = nullptr;
     size_t btab_cap = 0;
 };
@@ -79,6 +95,7 @@ struct dg_ctx {
     double fs = 0, fc = 0, lambda = 0;
     cudaStream_t stream = nullptr;
     int device = 0;
+    int sm_count = 1;
     GridDev gd{};
     int64_t G = 0;
     double *xyz = nullptr;
@@ -101,7 +118,6 @@ struct dg_ctx {
     unsigned *err_h = nullptr;          // pinned mirror
     LocalGrid loc;
     CdftBufs cd;
-    int64_t cd_bucket_chunks = 0, cd_cand_chunks = 0;  // work of the last CDFT surface
     int cd_chunk_min = 0, cd_chunk_max = 0;              // chunks it used
     std::string err;
     int64_t launches = 0;
@@ -298,58 +314,150 @@ dg_status grow(dg_ctx *c, P **p, size_t n)
 // Budget for the per-(candidate, snapshot) arrays of one CDFT batch.
 constexpr size_t kCdftBatchBytes = (size_t)3 << 30;
 
-// Chunked-DFT surface. Snapshots are processed in batches (same IQ format,
-// per-(candidate, snapshot) arrays within kCdftBatchBytes); per batch: the
-// geometry pass, one small device-to-host copy of the lag ranges to size the
-// buckets, the plan, the contraction and the combine. Then the ordered sum.
-// The FDOA range of a snapshot comes back as two order-preserving keys of
-// FP32 values (the smallest and largest nu of its candidates).
-static float key_to_float(unsigned k)
+// ---------------------------------------------------------------------------
+// Host-side planning for the chunked-DFT surface. Nothing here reads device
+// results: every size is an upper bound known from the grid and the
+// ephemerides, so the device work of a surface is one stream of launches with
+// no host synchronisation (and can be captured in a CUDA graph).
+// ---------------------------------------------------------------------------
+
+// Lag slots of snapshot k over a grid of diameter diam (metres). By the
+// triangle inequality |rho2 - rho1| <= |p2 - p1|, so |D| <= |p2 - p1| fs / c;
+// and each range moves by at most the displacement of the candidate, so D
+// varies by at most 2 diam fs / c over the grid. Eq. 9 then gives at most
+// 2 ceil(bound) + 1 lags; 2 more absorb rounding.
+static int lag_slots(const dg_ephem &e, double fs, double diam)
 {
-    const unsigned b = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
-    float f;
-    std::memcpy(&f, &b, sizeof f);
-    return f;
+    const double dx = e.p2[0] - e.p1[0], dy = e.p2[1] - e.p1[1], dz = e.p2[2] - e.p1[2];
+    const double span = std::min(2.0 * std::sqrt(dx * dx + dy * dy + dz * dz), 2.0 * diam) * fs / kC;
+    return (int)std::ceil(span) + 3;
 }
 
-// Longest chunk, a power of two in [64, kCdftAutoMaxChunk], whose length
-// times the bin spacing stays within kCdftAutoMDelta cycles for every
-// snapshot of the batch: the bin interpolation error, about
-// (pi M Delta)^2 / 6, is then below 2.7e-5. The spacing is computed as the
-// plan kernel computes it. A snapshot too wide even for 64 samples gets 64,
-// and the plan's check rejects it.
-static float max_bin_spacing(const unsigned *nur, int S)
+// FP64 WGS-84 node position and Eq. 3-10 FDOA on the host (planning only).
+static void host_node_ecef(const GridDev &g, double i, double j, double p[3])
 {
-    float dmax = 0.0f;
-    for (int s = 0; s < S; ++s) {
-        const float lo = key_to_float(nur[2 * s]), hi = key_to_float(nur[2 * s + 1]);
-        if (!(hi >= lo)) continue;  // no candidate with a representable lag
-        dmax = std::max(dmax, std::max((hi - lo) * (1.0f + 1e-5f) / 63.0f, 1e-20f));
+    const double e2 = kF * (2.0 - kF);
+    const double s0 = std::sin(g.lat0_rad), w = std::sqrt(1.0 - e2 * s0 * s0);
+    const double mr = kA * (1.0 - e2) / (w * w * w), nr = kA / w;
+    const double lat = g.lat0_rad + (i - 0.5 * (g.nlat - 1)) * (g.dlat_m / mr);
+    const double lon = g.lon0_rad + (j - 0.5 * (g.nlon - 1)) * (g.dlon_m / (nr * std::cos(g.lat0_rad)));
+    const double sl = std::sin(lat), n = kA / std::sqrt(1.0 - e2 * sl * sl);
+    p[0] = n * std::cos(lat) * std::cos(lon);
+    p[1] = n * std::cos(lat) * std::sin(lon);
+    p[2] = n * (1.0 - e2) * sl;
+}
+
+static double host_nu(const double p[3], const dg_ephem &e, double fs, double lambda)
+{
+    double f[2];
+    for (int r = 0; r < 2; ++r) {
+        const double *pp = r ? e.p2 : e.p1, *vv = r ? e.v2 : e.v1;
+        const double x = pp[0] - p[0], y = pp[1] - p[1], z = pp[2] - p[2];
+        f[r] = -(x * vv[0] + y * vv[1] + z * vv[2]) / (std::sqrt(x * x + y * y + z * z) * lambda);
     }
-    return dmax;
+    return (f[1] - f[0]) / fs;
 }
 
-static int auto_chunk(const unsigned *nur, int S)
+// Diameter bound of the shard: the largest distance between its corners and
+// edge midpoints (the grid is a lat/lon rectangle), with a 10 % margin.
+static double grid_diameter(const GridDev &g)
 {
-    const float dmax = max_bin_spacing(nur, S);
+    double p[9][3];
+    int n = 0;
+    const double r0 = g.row0, r1 = g.row0 + g.nrows - 1, c1 = g.nlon - 1;
+    const double is[3] = {r0, std::round(0.5 * (r0 + r1)), r1}, js[3] = {0.0, std::round(0.5 * c1), c1};
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) host_node_ecef(g, is[a], js[b], p[n++]);
+    double d = 0.0;
+    for (int a = 0; a < n; ++a)
+        for (int b = a + 1; b < n; ++b)
+            d = std::max(d, std::sqrt((p[a][0] - p[b][0]) * (p[a][0] - p[b][0]) + (p[a][1] - p[b][1]) * (p[a][1] - p[b][1]) +
+                                      (p[a][2] - p[b][2]) * (p[a][2] - p[b][2])));
+    return 1.1 * d + 1.0;
+}
+
+// FDOA span of snapshot k over the shard, from a lattice of nodes (its
+// corners, edges and interior; the FDOA field is smooth at these scales).
+static double fdoa_span(const dg_ctx *c, const GridDev &g, int k, int lattice)
+{
+    const int ni = std::min(lattice, g.nrows), nj = std::min(lattice, g.nlon);
+    double lo = 1e300, hi = -1e300;
+    for (int a = 0; a < ni; ++a)
+        for (int b = 0; b < nj; ++b) {
+            const double i = g.row0 + (ni > 1 ? (double)a * (g.nrows - 1) / (ni - 1) : 0.0);
+            const double j = nj > 1 ? (double)b * (g.nlon - 1) / (nj - 1) : 0.0;
+            double p[3];
+            host_node_ecef(g, std::round(i), std::round(j), p);
+            const double nu = host_nu(p, c->eph_host[k], c->fs, c->lambda);
+            lo = std::min(lo, nu);
+            hi = std::max(hi, nu);
+        }
+    return hi - lo;
+}
+
+// Chunk of a batch with chunk = 0: the longest power of two in
+// [64, kCdftAutoMaxChunk] whose length times the estimated bin spacing stays
+// within kCdftAutoMDelta / 1.25 (a margin for the lattice estimate; the plan
+// kernel checks the bound against the exact spacing).
+static int auto_chunk(const std::vector<double> &span, int k0, int S)
+{
+    double dmax = 0.0;
+    for (int s = 0; s < S; ++s) dmax = std::max(dmax, span[k0 + s] * (1.0 + 1e-5) / 63.0);
     int M = kCdftAutoMaxChunk;
-    while (M > 64 && (double)M * (double)dmax > kCdftAutoMDelta) M >>= 1;
+    while (M > 64 && 1.25 * M * dmax > kCdftAutoMDelta) M >>= 1;
     return M;
 }
 
-// Combine chunk: the longest power-of-two multiple of the contraction chunk M
-// whose length times the bin spacing stays within the same bound, up to the
-// first length that covers the longest snapshot (one super-chunk) and at most
-// 2^24 samples. The interpolation error bound of the combine is then that of
-// reading 20 in the design (about (pi Mc Delta)^2 / 6).
-static int combine_chunk(const unsigned *nur, int S, int M, int64_t nmax)
+// The batches of a surface and their bucket / combine-group bases: static for
+// a grid size G (the main grid and the refinement grid each keep one).
+static dg_status cdft_layout(dg_ctx *c, const GridDev &gd, int64_t G, CdftLayout &L)
 {
-    const float dmax = max_bin_spacing(nur, S);
-    int64_t Mc = M;
-    while (Mc < nmax && 2 * Mc <= ((int64_t)1 << 24) && (double)(2 * Mc) * (double)dmax <= kCdftAutoMDelta) Mc *= 2;
-    return (int)Mc;
+    const double diam = grid_diameter(gd);
+    if (L.G == G && L.diam >= diam && !L.batches.empty()) return DG_OK;
+    int *old_bb = L.bbase, *old_gb = L.gbase;
+    L = CdftLayout{};
+    L.G = G;
+    L.diam = diam;
+    L.bbase = old_bb;
+    L.gbase = old_gb;
+    const int s_max = (int)std::max<int64_t>(1, std::min<int64_t>(c->K, (int64_t)(kCdftBatchBytes / (16 * (size_t)G))));
+    std::vector<int> bb, gb;
+    for (int k0 = 0; k0 < c->K;) {
+        int S = 1;  // same format, at most s_max snapshots
+        while (k0 + S < c->K && S < s_max && c->steps[k0 + S].fmt == c->steps[k0].fmt) ++S;
+        CdftLayout::Batch t{k0, S, (int)bb.size(), 0, 0};
+        int64_t nb = 0, ng = 0;
+        for (int s = 0; s <= S; ++s) {
+            bb.push_back((int)nb);
+            gb.push_back((int)ng);
+            if (s == S) break;
+            const int slots = lag_slots(c->eph_host[k0 + s], c->fs, diam);
+            nb += slots;
+            ng += G / kCdftCombineThreads + slots + 1;
+        }
+        if (nb > INT_MAX / 64 || ng > INT_MAX)
+            return fail(c, DG_EUNSUPPORTED, "CDFT: %lld lag slots in one batch; use DIRECT", (long long)nb);
+        t.nbt = nb;
+        t.groups = ng;
+        L.batches.push_back(t);
+        L.s_max = std::max(L.s_max, S);
+        L.nbt_max = std::max<int64_t>(L.nbt_max, nb);
+        L.groups_max = std::max<int64_t>(L.groups_max, ng);
+        k0 += S;
+    }
+    dg_status st;
+    if ((st = grow(c, &L.bbase, bb.size())) != DG_OK) return st;
+    if ((st = grow(c, &L.gbase, gb.size())) != DG_OK) return st;
+    // pageable sources: staged before the calls return
+    CK(c, cudaMemcpyAsync(L.bbase, bb.data(), sizeof(int) * bb.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(L.gbase, gb.data(), sizeof(int) * gb.size(), cudaMemcpyHostToDevice, c->stream));
+    return DG_OK;
 }
 
+// Chunked-DFT surface. Per batch of snapshots (same IQ format, per-(candidate,
+// snapshot) arrays within kCdftBatchBytes): geometry, plan (sort by lag
+// bucket and bin, bins, tiles), DFT tables, contraction, super-chunks,
+// combine. Then the ordered sum. No host synchronisation.
 dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int64_t G, void *surf, void *out,
                            bool refine)
 {
@@ -359,18 +467,38 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         if (c->steps[k].n > (1 << 24))
             return fail(c, DG_EUNSUPPORTED, "CDFT: snapshots longer than 2^24 samples are not supported; use DIRECT");
     CdftBufs &b = c->cd;
-    // chunk 0: chosen per batch once its FDOA spans are known (auto_chunk);
-    // the tables are sized for the longest chunk allowed
-    const int M_cap = c->opt.chunk ? c->opt.chunk : kCdftAutoMaxChunk;
-    const int s_max = (int)std::max<int64_t>(1, std::min<int64_t>(c->K, (int64_t)(kCdftBatchBytes / (12 * (size_t)G))));
+    CdftLayout &L = refine ? b.loc_layout : b.main_layout;
+    if ((st = cdft_layout(c, gd, G, L)) != DG_OK) return st;
+    const int s_max = L.s_max;
+    // FDOA spans for the automatic chunk: cached for the main grid; a
+    // refinement grid moves with each call and takes a 3 x 3 lattice
+    std::vector<double> &span = refine ? b.loc_span : b.main_span;
+    if (c->opt.chunk == 0 && (refine || span.size() != (size_t)c->K)) {
+        span.assign(c->K, 0.0);
+        for (int k = 0; k < c->K; ++k) span[k] = fdoa_span(c, gd, k, refine ? 3 : 65);
+    }
+    std::vector<int> Ms(L.batches.size());
+    int M_max = 64, B_max = 1;
+    for (size_t i = 0; i < L.batches.size(); ++i) {
+        const auto &t = L.batches[i];
+        Ms[i] = c->opt.chunk ? c->opt.chunk : auto_chunk(span, t.k0, t.S);
+        M_max = std::max(M_max, Ms[i]);
+        for (int s = 0; s < t.S; ++s) B_max = std::max<int>(B_max, (int)((c->steps[t.k0 + s].n + Ms[i] - 1) / Ms[i]));
+    }
+    // scratch, grown on demand (never inside a captured graph: a graph is
+    // captured after one uncaptured call of the same shape)
     if (b.s_cap < (size_t)s_max) {
         if ((st = grow(c, &b.lr, 2 * (size_t)s_max)) != DG_OK) return st;
-        if ((st = grow(c, &b.bbase, (size_t)s_max + 1)) != DG_OK) return st;
-        if ((st = grow(c, &b.gbase, (size_t)s_max + 1)) != DG_OK) return st;
         if ((st = grow(c, &b.delta, (size_t)s_max)) != DG_OK) return st;
         if ((st = grow(c, &b.nubase, (size_t)s_max)) != DG_OK) return st;
         if ((st = grow(c, &b.nur, 2 * (size_t)s_max)) != DG_OK) return st;
+        if ((st = grow(c, &b.tbase, (size_t)s_max + 1)) != DG_OK) return st;
+        if ((st = grow(c, &b.layout, (size_t)s_max)) != DG_OK) return st;
+        if ((st = grow(c, &b.Mcs, (size_t)s_max)) != DG_OK) return st;
         b.s_cap = (size_t)s_max;
+    }
+    if (!b.work) {
+        if ((st = grow(c, &b.work, 2)) != DG_OK) return st;
     }
     if (b.sg_cap < (size_t)s_max * G) {
         if ((st = grow(c, &b.candL, (size_t)s_max * G)) != DG_OK) return st;
@@ -379,13 +507,43 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         if ((st = grow(c, &b.nuS, (size_t)s_max * G)) != DG_OK) return st;
         b.sg_cap = (size_t)s_max * G;
     }
-    if (b.v_cap < (size_t)s_max * M_cap * 64) {
-        if ((st = grow(c, &b.V, (size_t)s_max * M_cap * 64)) != DG_OK) return st;
-        b.v_cap = (size_t)s_max * M_cap * 64;
+    if (b.v_cap < (size_t)s_max * M_max * 64) {
+        if ((st = grow(c, &b.V, (size_t)s_max * M_max * 64)) != DG_OK) return st;
+        b.v_cap = (size_t)s_max * M_max * 64;
+    }
+    if (b.nb_cap < (size_t)L.nbt_max) {
+        const size_t n = (size_t)L.nbt_max;
+        if ((st = grow(c, &b.count, n)) != DG_OK) return st;
+        if ((st = grow(c, &b.offs, n)) != DG_OK) return st;
+        if ((st = grow(c, &b.gofs, n)) != DG_OK) return st;
+        if ((st = grow(c, &b.subcnt, 64 * n)) != DG_OK) return st;
+        b.nb_cap = n;
+    }
+    const size_t w_elems = (size_t)L.nbt_max * (size_t)B_max * 128;
+    if (w_elems * sizeof(float) > ((size_t)64 << 30))
+        return fail(c, DG_EUNSUPPORTED, "CDFT: the per-lag DFT buffer would exceed 64 GiB (%lld lag slots x %d chunks); "
+                    "use a longer chunk or DIRECT", (long long)L.nbt_max, B_max);
+    if (b.w_cap < w_elems) {
+        if ((st = grow(c, &b.W, w_elems)) != DG_OK) return st;
+        b.w_cap = w_elems;
+    }
+    if (b.g2b_cap < (size_t)L.groups_max) {
+        if ((st = grow(c, &b.g2b, (size_t)L.groups_max)) != DG_OK) return st;
+        b.g2b_cap = (size_t)L.groups_max;
+    }
+    const bool mma = c->opt.contract != DG_CONTRACT_FP32;
+    if (mma) {
+        const size_t bt = (size_t)s_max * cdft_btab_bytes(c->opt.contract, M_max);
+        if (b.btab_cap < bt) {
+            unsigned char *p = reinterpret_cast<unsigned char *>(b.btab);
+            if ((st = grow(c, &p, bt)) != DG_OK) return st;
+            b.btab = p;
+            b.btab_cap = bt;
+        }
     }
     const int kplan = refine ? DG_K_REFINE : DG_K_CDFT_PLAN;
     if (!refine) {
-        c->cd_bucket_chunks = c->cd_cand_chunks = 0;
+        CK(c, cudaMemsetAsync(b.work, 0, 2 * sizeof(unsigned long long), c->stream));
         c->cd_chunk_min = INT_MAX;
         c->cd_chunk_max = 0;
     }
@@ -414,25 +572,16 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         CK(c, launch_ecef_split(xyz, G, b.xyzf, c->stream));
         t.done(1);
     }
-    std::vector<int> lr(2 * (size_t)s_max), bbase(s_max + 1), gbase(s_max + 1), tbase(s_max + 1);
-    std::vector<unsigned> nur(2 * (size_t)s_max);
-    const bool mma = c->opt.contract != DG_CONTRACT_FP32;
-    if (mma) {
-        const size_t bt = (size_t)s_max * cdft_btab_bytes(c->opt.contract, M_cap);
-        if (b.tbase_cap < (size_t)s_max + 1) {
-            if ((st = grow(c, &b.tbase, (size_t)s_max + 1)) != DG_OK) return st;
-            b.tbase_cap = (size_t)s_max + 1;
+    float *surf_f = reinterpret_cast<float *>(surf);
+    for (size_t bi = 0; bi < L.batches.size(); ++bi) {
+        const auto &bt = L.batches[bi];
+        const int k0 = bt.k0, S = bt.S, M = Ms[bi];
+        int Bmax = 1;
+        for (int s = 0; s < S; ++s) Bmax = std::max<int>(Bmax, (int)((c->steps[k0 + s].n + M - 1) / M));
+        if (!refine) {
+            c->cd_chunk_min = std::min(c->cd_chunk_min, M);
+            c->cd_chunk_max = std::max(c->cd_chunk_max, M);
         }
-        if (b.btab_cap < bt) {
-            unsigned char *p = reinterpret_cast<unsigned char *>(b.btab);
-            if ((st = grow(c, &p, bt)) != DG_OK) return st;
-            b.btab = p;
-            b.btab_cap = bt;
-        }
-    }
-    for (int k0 = 0; k0 < c->K;) {
-        int S = 1;  // batch: same format, at most s_max snapshots
-        while (k0 + S < c->K && S < s_max && c->steps[k0 + S].fmt == c->steps[k0].fmt) ++S;
         CdftBatch a{};
         a.xyz = xyz;
         a.xyzf = b.xyzf;
@@ -448,152 +597,73 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         a.nlon = gd.nlon;
         a.fs = c->fs;
         a.lambda = c->lambda;
-        a.M = M_cap;
-        a.Bmax = 1;
+        a.M = M;
+        a.Bmax = Bmax;
         a.acc = c->opt.acc;
         a.err = c->err_d;
         a.lr = b.lr;
         a.nur = b.nur;
         a.nubase = b.nubase;
-        a.bbase = b.bbase;
-        a.gbase = b.gbase;
+        a.bbase = L.bbase + bt.base;
+        a.gbase = L.gbase + bt.base;
         a.candL = b.candL;
         a.candNu = b.candNu;
         a.order = b.order;
         a.nuS = b.nuS;
+        a.g2b = b.g2b;
         a.delta = b.delta;
         a.V = b.V;
-        {
-            Timed t(c, kplan);
-            CK(c, launch_cdft_geo(a, c->stream));
-            t.done(2);
-        }
-        CK(c, cudaMemcpyAsync(lr.data(), b.lr, sizeof(int) * 2 * (size_t)S, cudaMemcpyDeviceToHost, c->stream));
-        CK(c, cudaMemcpyAsync(nur.data(), b.nur, sizeof(unsigned) * 2 * (size_t)S, cudaMemcpyDeviceToHost,
-                              c->stream));
-        CK(c, cudaStreamSynchronize(c->stream));
-        const int M = c->opt.chunk ? c->opt.chunk : auto_chunk(nur.data(), S);
-        int Bmax = 1;
-        int64_t nmax = 1;
-        for (int s = 0; s < S; ++s) {
-            Bmax = std::max<int>(Bmax, (int)((c->steps[k0 + s].n + M - 1) / M));
-            nmax = std::max<int64_t>(nmax, c->steps[k0 + s].n);
-        }
-        a.M = M;
-        a.Bmax = Bmax;
-        a.Mc = combine_chunk(nur.data(), S, M, nmax);
-        if (!refine) {
-            c->cd_chunk_min = std::min(c->cd_chunk_min, M);
-            c->cd_chunk_max = std::max(c->cd_chunk_max, M);
-        }
-        int64_t nbt = 0, groups = 0;
-        for (int s = 0; s < S; ++s) {
-            const int64_t nb = lr[2 * s] <= lr[2 * s + 1] ? (int64_t)lr[2 * s + 1] - lr[2 * s] + 1 : 0;
-            bbase[s] = (int)nbt;
-            gbase[s] = (int)groups;
-            nbt += nb;
-            groups += nb ? G / kCdftCombineThreads + nb + 1 : 0;
-            if (!refine) {
-                const int64_t B = (c->steps[k0 + s].n + M - 1) / M;
-                c->cd_bucket_chunks += nb * B;
-                c->cd_cand_chunks += G * ((c->steps[k0 + s].n + a.Mc - 1) / a.Mc);
-            }
-        }
-        bbase[S] = (int)nbt;
-        gbase[S] = (int)groups;
-        // tensor-core tiles of 128 rows: (lag, chunk) rows in lag-major order,
-        // or 128 consecutive lags of one chunk (lag tiles, which share their
-        // capture windows); lag tiles unless their padding to whole blocks of
-        // 128 lags more than doubles the tile count (few lags per snapshot)
-        int64_t tiles_row = 0, tiles_lag = 0;
-        for (int s = 0; s < S; ++s) {
-            const int64_t nb = (int64_t)bbase[s + 1] - bbase[s];
-            const int64_t B = (c->steps[k0 + s].n + M - 1) / M;
-            tiles_row += (nb * B + 127) / 128;
-            tiles_lag += B * ((nb + 127) / 128);
-        }
-        const int tl = c->opt.tiles;
-        a.lag_tiles = (mma && M <= kLagTileMaxChunk &&
-                       (tl == DG_TILES_LAGS || (tl == DG_TILES_AUTO && tiles_lag <= 2 * tiles_row))) ? 1 : 0;
-        int64_t tiles = 0;
-        for (int s = 0; s < S; ++s) {
-            tbase[s] = (int)tiles;
-            const int64_t nb = (int64_t)bbase[s + 1] - bbase[s];
-            const int64_t B = (c->steps[k0 + s].n + M - 1) / M;
-            tiles += a.lag_tiles ? B * ((nb + 127) / 128) : (nb * B + 127) / 128;
-        }
-        tbase[S] = (int)tiles;
-        if (nbt > ((int64_t)1 << 26) || groups > INT_MAX)
-            return fail(c, DG_EUNSUPPORTED, "CDFT: %lld lag buckets in one batch; use DIRECT", (long long)nbt);
-        const size_t w_elems = (size_t)std::max<int64_t>(nbt, 1) * (size_t)Bmax * 128;
-        if (w_elems * sizeof(float) > ((size_t)48 << 30))
-            return fail(c, DG_EUNSUPPORTED, "CDFT: the per-lag DFT buffer would exceed 48 GiB (%lld lags x %d chunks); "
-                        "use a larger chunk or DIRECT", (long long)nbt, Bmax);
-        if (b.nb_cap < (size_t)std::max<int64_t>(nbt, 1)) {
-            const size_t n = (size_t)std::max<int64_t>(nbt, 1);
-            if ((st = grow(c, &b.count, n)) != DG_OK) return st;
-            if ((st = grow(c, &b.offs, n)) != DG_OK) return st;
-            if ((st = grow(c, &b.gofs, n)) != DG_OK) return st;
-            if ((st = grow(c, &b.subcnt, 64 * n)) != DG_OK) return st;
-            b.nb_cap = n;
-        }
-        if (b.w_cap < w_elems) {
-            if ((st = grow(c, &b.W, w_elems)) != DG_OK) return st;
-            b.w_cap = w_elems;
-        }
-        if (b.g2b_cap < (size_t)std::max<int64_t>(groups, 1)) {
-            if ((st = grow(c, &b.g2b, (size_t)std::max<int64_t>(groups, 1))) != DG_OK) return st;
-            b.g2b_cap = (size_t)std::max<int64_t>(groups, 1);
-        }
-        a.g2b = b.g2b;
-        CK(c, cudaMemsetAsync(b.g2b, 0xff, sizeof(int) * (size_t)std::max<int64_t>(groups, 1), c->stream));
         a.count = b.count;
         a.offs = b.offs;
         a.gofs = b.gofs;
         a.subcnt = b.subcnt;
         a.W = b.W;
-        CK(c, cudaMemcpyAsync(b.bbase, bbase.data(), sizeof(int) * (S + 1), cudaMemcpyHostToDevice, c->stream));
-        CK(c, cudaMemcpyAsync(b.gbase, gbase.data(), sizeof(int) * (S + 1), cudaMemcpyHostToDevice, c->stream));
-        if (mma) {
-            CK(c, cudaMemcpyAsync(b.tbase, tbase.data(), sizeof(int) * (S + 1), cudaMemcpyHostToDevice, c->stream));
-            a.tbase = b.tbase;
-            a.btab = b.btab;
-            // FP16 needs the lag products inside its range: int16 products reach 2^31
-            const int f = c->steps[k0].fmt;
-            const bool fp16 = c->opt.contract == DG_CONTRACT_FP16 || c->opt.contract == DG_CONTRACT_FP16X3;
-            a.zscale = (fp16 && f == DG_IQ_CI16) ? 1.0f / 65536.0f : 1.0f;
-        }
-        float *surf_f = reinterpret_cast<float *>(surf);
-        if (nbt == 0) {  // no node with a representable lag in the whole batch
-            CK(c, cudaMemsetAsync(surf_f + (size_t)k0 * G, 0, sizeof(float) * (size_t)G * S, c->stream));
-            k0 += S;
-            continue;
-        }
+        a.tbase = b.tbase;
+        a.layout = b.layout;
+        a.Mcs = b.Mcs;
+        a.work = refine ? nullptr : b.work;
+        a.tiles_mode = c->opt.tiles;
+        a.mma = mma ? 1 : 0;
+        a.ngroups = (int)bt.groups;
+        a.btab = b.btab;
+        // FP16 needs the lag products inside its range: int16 products reach 2^31
+        const int f = c->steps[k0].fmt;
+        const bool fp16 = c->opt.contract == DG_CONTRACT_FP16 || c->opt.contract == DG_CONTRACT_FP16X3;
+        a.zscale = (mma && fp16 && f == DG_IQ_CI16) ? 1.0f / 65536.0f : 1.0f;
         {
             Timed t(c, kplan);
-            CK(c, launch_cdft_plan(a, (int)nbt, c->stream));
-            t.done(6);
+            CK(c, launch_cdft_geo(a, c->stream));
+            CK(c, cudaMemsetAsync(b.g2b, 0xff, sizeof(int) * (size_t)bt.groups, c->stream));
+            CK(c, launch_cdft_plan(a, (int)bt.nbt, c->stream));
+            CK(c, launch_cdft_tiles(a, c->stream));
+            t.done(mma ? 8 : 9);
         }
         {
             Timed t(c, refine ? DG_K_REFINE : DG_K_CDFT_CONTRACT);
             if (mma) {
+                // persistent: one CTA per SM, or fewer when the batch can
+                // have fewer tiles (the bound: lag tiles of every lag slot)
+                int64_t tiles_cap = 0;
+                for (int s = 0; s < S; ++s) {
+                    const int slots = lag_slots(c->eph_host[k0 + s], c->fs, L.diam);
+                    const int64_t B = (c->steps[k0 + s].n + M - 1) / M;
+                    tiles_cap += B * ((slots + 127) / 128);
+                }
+                const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles_cap, c->sm_count));
                 CK(c, launch_cdft_btab(a, c->opt.contract, b.btab, c->stream));
-                CK(c, launch_cdft_contract_mma(a, tbase[S], c->steps[k0].fmt, c->opt.contract, c->stream));
+                CK(c, launch_cdft_contract_mma(a, grid, f, c->opt.contract, c->stream));
                 t.done(2);
             } else {
-                CK(c, launch_cdft_contract_fp32(a, (int)nbt, c->steps[k0].fmt, c->stream));
+                CK(c, launch_cdft_contract_fp32(a, (int)bt.nbt, f, c->stream));
                 t.done(1);
             }
         }
         {
             Timed t(c, refine ? DG_K_REFINE : DG_K_CDFT_COMBINE);
-            if (a.Mc > a.M) CK(c, launch_cdft_superchunk(a, (int)nbt, c->stream));
-            CK(c, launch_cdft_combine(a, (int)groups, surf_f, c->stream));
-            t.done(a.Mc > a.M ? 2 : 1);
+            CK(c, launch_cdft_superchunk(a, (int)bt.nbt, c->stream));
+            CK(c, launch_cdft_combine(a, surf_f, c->stream));
+            t.done(2);
         }
-        // lr, bbase and gbase are rewritten by the next batch only after its
-        // geometry pass has been synchronised, so reuse is ordered.
-        k0 += S;
     }
     {
         Timed t(c, refine ? DG_K_REFINE : DG_K_ACCUM);
@@ -737,6 +807,7 @@ dg_status dg_create(const dg_grid *grid, const dg_ephem *eph, int32_t K, double 
                              #call, cudaGetErrorString(e_)));                                  \
     } while (0)
     CKC(cudaGetDevice(&c->device));
+    CKC(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
     CKC(cudaMallocAsync((void **)&c->xyz, sizeof(double) * 3 * (size_t)c->G, c->stream));
     CKC(cudaMallocAsync((void **)&c->eph, sizeof(double) * 12 * (size_t)K, c->stream));
     CKC(cudaMallocAsync((void **)&c->steps_d, sizeof(StepDesc) * (size_t)K, c->stream));
@@ -1017,8 +1088,14 @@ dg_status dg_cdft_chunks(const dg_ctx *c, int32_t *min_chunk, int32_t *max_chunk
 dg_status dg_cdft_work(const dg_ctx *c, int64_t *bucket_chunks, int64_t *candidate_chunks)
 {
     if (!c) return fail(nullptr, DG_EINVAL, "ctx is NULL");
-    if (bucket_chunks) *bucket_chunks = c->cd_bucket_chunks;
-    if (candidate_chunks) *candidate_chunks = c->cd_cand_chunks;
+    unsigned long long w[2] = {0, 0};
+    if (c->cd.work) {  // counted on the device by the plan: wait for the stream
+        if (cudaMemcpyAsync(w, c->cd.work, sizeof w, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+            return fail(nullptr, DG_ECUDA, "reading the CDFT work counters failed");
+    }
+    if (bucket_chunks) *bucket_chunks = (int64_t)w[0];
+    if (candidate_chunks) *candidate_chunks = (int64_t)w[1];
     return DG_OK;
 }
 
@@ -1047,8 +1124,13 @@ dg_status dg_destroy(dg_ctx *c)
     fr(c->loc.surf);
     fr(c->loc.cost);
     fr(c->cd.lr);
-    fr(c->cd.bbase);
-    fr(c->cd.gbase);
+    fr(c->cd.main_layout.bbase);
+    fr(c->cd.main_layout.gbase);
+    fr(c->cd.loc_layout.bbase);
+    fr(c->cd.loc_layout.gbase);
+    fr(c->cd.layout);
+    fr(c->cd.Mcs);
+    fr(c->cd.work);
     fr(c->cd.candL);
     fr(c->cd.order);
     fr(c->cd.nuS);

@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(256) k_cdft_hist(CdftBatch a)
     const int tiles_j = (a.nlon + kHistTile - 1) / kHistTile;
     const int r0 = (blockIdx.x / tiles_j) * kHistTile, c0 = (blockIdx.x % tiles_j) * kHistTile;
     const int *L = a.candL + (size_t)s * a.G;
-    const int lmin = a.lr[2 * s], bb = a.bbase[s];
+    const int lmin = a.lr[2 * s], bb = a.bbase[s], cap = a.bbase[s + 1] - bb;
     if (threadIdx.x == 0) {
         s_min = INT_MAX;
         s_max = INT_MIN;
@@ -187,6 +187,10 @@ __global__ void __launch_bounds__(256) k_cdft_hist(CdftBatch a)
     atomicMax(&s_max, hi);
     __syncthreads();
     if (s_max < s_min) return;  // no node with a representable lag (uniform)
+    if (a.lr[2 * s + 1] - lmin >= cap) {  // more lags than the snapshot's bucket slots
+        if (threadIdx.x == 0) atomicOr(a.err, ERR_LAG_RANGE);
+        return;
+    }
     const int tlo = s_min;
     const bool local = (int64_t)s_max - s_min < kHistBins;
     const int span = local ? s_max - s_min + 1 : 0;
@@ -217,7 +221,10 @@ __global__ void __launch_bounds__(1024) k_cdft_scan(CdftBatch a)
 {
     __shared__ int s_c[1024], s_g[1024];
     const int s = blockIdx.x, t = threadIdx.x;
-    const int b_first = a.bbase[s], NB = a.bbase[s + 1] - b_first;
+    const int b_first = a.bbase[s];
+    const int lo_l = a.lr[2 * s], hi_l = a.lr[2 * s + 1];
+    int NB = hi_l >= lo_l ? hi_l - lo_l + 1 : 0;
+    if (NB > a.bbase[s + 1] - b_first) NB = 0;  // reported by k_cdft_hist
     const int per = (NB + 1023) / 1024;
     const int b0 = min(NB, t * per), b1 = min(NB, b0 + per);
     int c = 0, g = 0;
@@ -275,6 +282,7 @@ __global__ void __launch_bounds__(256) k_cdft_subhist(CdftBatch a)
 {
     const int s = blockIdx.y;
     const int lmin = a.lr[2 * s], bb = a.bbase[s];
+    if (a.lr[2 * s + 1] - lmin >= a.bbase[s + 1] - bb) return;  // reported by k_cdft_hist
     const float delta = a.delta[s];
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.G; p += (int64_t)gridDim.x * blockDim.x) {
         const int l = a.candL[(size_t)s * a.G + p];
@@ -308,6 +316,7 @@ __global__ void __launch_bounds__(256) k_cdft_scatter(CdftBatch a)
 {
     const int s = blockIdx.y;
     const int lmin = a.lr[2 * s], bb = a.bbase[s];
+    if (a.lr[2 * s + 1] - lmin >= a.bbase[s + 1] - bb) return;  // reported by k_cdft_hist
     const float delta = a.delta[s];
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.G; p += (int64_t)gridDim.x * blockDim.x) {
         const int l = a.candL[(size_t)s * a.G + p];
@@ -424,7 +433,8 @@ __global__ void __launch_bounds__(256) k_cdft_superchunk(CdftBatch a, int NBT)
     const int bg = (int)(t >> 6), q = (int)(t & 63);
     if (a.count[bg] == 0) return;  // no candidate: W rows were not written
     const int s = step_of(a.bbase, a.S, bg);
-    const int M = a.M, R = a.Mc / a.M;
+    const int M = a.M, R = a.Mcs[s] / a.M;
+    if (R == 1) return;
     const int B = (a.sd[s].n + M - 1) / M;
     const float nq = a.nubase[s] + (float)q * a.delta[s];
     float ex, ey;  // e^{j 2 pi nu_q M}
@@ -464,54 +474,100 @@ __global__ void __launch_bounds__(kCdftCombineThreads) k_cdft_combine(CdftBatch 
     // per chunk and bin q: (re q, re q+1, im q, im q+1), so that a candidate
     // reads both neighbouring bins with one 16-byte load
     __shared__ __align__(16) float4 ws[kSeg][64];
-    const int gid = blockIdx.x;
-    const int b = a.g2b[gid];  // the scan's map from combine group to bucket
-    if (b < 0) return;         // past the snapshot's last group (uniform)
-    const int s = step_of(a.gbase, a.S, gid);
-    const int lgid = gid - a.gbase[s];
-    const int n_b = a.count[b];
-    const int j = (lgid - a.gofs[b]) * kCdftCombineThreads + threadIdx.x;
-    const bool active = j < n_b;
-    const size_t sp = (size_t)s * a.G + a.offs[b] + j;
-    const int c = active ? a.order[sp] : 0;
-    const float nuf = active ? a.nuS[sp] : a.nubase[s];
-    float t;
-    const int q0 = bin_of(nuf, a.nubase[s], a.delta[s], t);
-    const float w0 = 1.f - t, w1 = t;
-    const int M = a.Mc;
-    const int B = (a.sd[s].n + M - 1) / M;
-    // chunk-to-chunk phase step e^{j 2 pi nu M}
-    float ex, ey;
-    sincospif(2.0f * frac_mul(nuf, (float)M), &ey, &ex);
-    float cx = 0.f, cy = 0.f;
-    const float *Wb = a.W + (size_t)b * a.Bmax * 128;
-    for (int s0 = 0; s0 < B; s0 += kSeg) {
-        const int slen = min(kSeg, B - s0);
-        __syncthreads();
-        for (int i = threadIdx.x; i < slen * 64; i += kCdftCombineThreads) {
-            const int ch = i >> 6, q = i & 63, q1 = min(q + 1, 63);
-            const float *row = Wb + (size_t)(s0 + ch) * 128;
-            ws[ch][q] = make_float4(row[q], row[q1], row[64 + q], row[64 + q1]);
-        }
-        __syncthreads();
-        float px, py;  // phase of the segment's first sample, e^{j 2 pi nu s0 M}
-        sincospif(2.0f * frac_mul(nuf, (float)s0 * (float)M), &py, &px);
+    // one CTA per combine group of the batch's upper bound; groups past a
+    // snapshot's last are -1 in the scan's group-to-bucket map
+    {
+        const int gid = blockIdx.x;
+        const int b = a.g2b[gid];
+        if (b < 0) return;  // uniform
+        const int s = step_of(a.gbase, a.S, gid);
+        const int lgid = gid - a.gbase[s];
+        const int n_b = a.count[b];
+        const int j = (lgid - a.gofs[b]) * kCdftCombineThreads + threadIdx.x;
+        const bool active = j < n_b;
+        const size_t sp = (size_t)s * a.G + a.offs[b] + j;
+        const int c = active ? a.order[sp] : 0;
+        const float nuf = active ? a.nuS[sp] : a.nubase[s];
+        float t;
+        const int q0 = bin_of(nuf, a.nubase[s], a.delta[s], t);
+        const float w0 = 1.f - t, w1 = t;
+        const int M = a.Mcs[s];
+        const int B = (a.sd[s].n + M - 1) / M;
+        // chunk-to-chunk phase step e^{j 2 pi nu M}
+        float ex, ey;
+        sincospif(2.0f * frac_mul(nuf, (float)M), &ey, &ex);
+        float cx = 0.f, cy = 0.f;
+        const float *Wb = a.W + (size_t)b * a.Bmax * 128;
+        for (int s0 = 0; s0 < B; s0 += kSeg) {
+            const int slen = min(kSeg, B - s0);
+            __syncthreads();
+            for (int i = threadIdx.x; i < slen * 64; i += kCdftCombineThreads) {
+                const int ch = i >> 6, q = i & 63, q1 = min(q + 1, 63);
+                const float *row = Wb + (size_t)(s0 + ch) * 128;
+                ws[ch][q] = make_float4(row[q], row[q1], row[64 + q], row[64 + q1]);
+            }
+            __syncthreads();
+            float px, py;  // phase of the segment's first sample, e^{j 2 pi nu s0 M}
+            sincospif(2.0f * frac_mul(nuf, (float)s0 * (float)M), &py, &px);
 #pragma unroll 4
-        for (int i = 0; i < slen; ++i) {
-            const float4 v = ws[i][q0];
-            const float zx = fmaf(w0, v.x, w1 * v.y), zy = fmaf(w0, v.z, w1 * v.w);
-            cx = fmaf(px, zx, fmaf(-py, zy, cx));
-            cy = fmaf(px, zy, fmaf(py, zx, cy));
-            const float nx = fmaf(px, ex, -py * ey);
-            py = fmaf(px, ey, py * ex);
-            px = nx;
+            for (int i = 0; i < slen; ++i) {
+                const float4 v = ws[i][q0];
+                const float zx = fmaf(w0, v.x, w1 * v.y), zy = fmaf(w0, v.z, w1 * v.w);
+                cx = fmaf(px, zx, fmaf(-py, zy, cx));
+                cy = fmaf(px, zy, fmaf(py, zx, cy));
+                const float nx = fmaf(px, ex, -py * ey);
+                py = fmaf(px, ey, py * ex);
+                px = nx;
+            }
         }
-    }
-    if (active) {
-        const float pw = fmaf(cx, cx, cy * cy);
-        surf[(size_t)(a.k0 + s) * a.G + c] = (T)(a.acc == DG_ACC_POWER ? pw : sqrtf(pw));
+        if (active) {
+            const float pw = fmaf(cx, cx, cy * cy);
+            surf[(size_t)(a.k0 + s) * a.G + c] = (T)(a.acc == DG_ACC_POWER ? pw : sqrtf(pw));
+        }
     }
 }
+
+// ---------------------------------------------------------------------------
+// tiles: one thread, after the scan. Per snapshot of the batch: its lag
+// buckets (from the lag range), the tensor-core tile layout (128 lags x one
+// chunk unless padding the lags to blocks of 128 more than doubles the tile
+// count, or the chunk exceeds kLagTileMaxChunk), the tile offsets, and the
+// combine chunk: the longest power-of-two multiple of M with
+// Mc x bin spacing <= kCdftAutoMDelta, up to the first length that covers the
+// snapshot and at most 2^24. Also the work counters.
+// ---------------------------------------------------------------------------
+__global__ void k_cdft_tiles(CdftBatch a)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int tiles = 0;
+    unsigned long long rows = 0, cands = 0;
+    for (int s = 0; s < a.S; ++s) {
+        const int lo = a.lr[2 * s], hi = a.lr[2 * s + 1];
+        int NB = hi >= lo ? hi - lo + 1 : 0;
+        if (NB > a.bbase[s + 1] - a.bbase[s]) NB = 0;
+        const int n = a.sd[s].n, M = a.M;
+        const int B = (n + M - 1) / M;
+        const int t_row = (int)(((int64_t)NB * B + 127) / 128), t_lag = B * ((NB + 127) / 128);
+        int lay = 0;
+        if (a.mma && M <= kLagTileMaxChunk)
+            lay = a.tiles_mode == DG_TILES_LAGS || (a.tiles_mode == DG_TILES_AUTO && t_lag <= 2 * t_row);
+        a.layout[s] = lay;
+        a.tbase[s] = tiles;
+        tiles += lay ? t_lag : t_row;
+        int64_t Mc = M;
+        const double d = (double)a.delta[s];
+        while (Mc < n && 2 * Mc <= ((int64_t)1 << 24) && (double)(2 * Mc) * d <= kCdftAutoMDelta) Mc *= 2;
+        a.Mcs[s] = (int)Mc;
+        rows += (unsigned long long)NB * B;
+        cands += (unsigned long long)a.G * ((n + Mc - 1) / Mc);
+    }
+    a.tbase[a.S] = tiles;
+    if (a.work) {
+        a.work[0] += rows;
+        a.work[1] += cands;
+    }
+}
+
 
 // ---------------------------------------------------------------------------
 // host-side launchers
@@ -567,6 +623,7 @@ cudaError_t launch_cdft_plan(const CdftBatch &a, int NBT, cudaStream_t st)
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_cdft_scatter<<<gp, 256, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (a.mma) return cudaSuccess;  // the FP32 table serves the CUDA-core contraction only
     dim3 gv(grid_for((int64_t)a.M * 64, 256, 64), (unsigned)a.S);
     k_cdft_vtable<<<gv, 256, 0, st>>>(a.V, a.nubase, a.delta, a.M, a.S);
     return cudaGetLastError();
@@ -590,9 +647,15 @@ cudaError_t launch_cdft_superchunk(const CdftBatch &a, int NBT, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_cdft_combine(const CdftBatch &a, int groups, float *surf, cudaStream_t st)
+cudaError_t launch_cdft_combine(const CdftBatch &a, float *surf, cudaStream_t st)
 {
-    k_cdft_combine<float><<<(unsigned)groups, kCdftCombineThreads, 0, st>>>(a, surf);
+    k_cdft_combine<float><<<(unsigned)a.ngroups, kCdftCombineThreads, 0, st>>>(a, surf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cdft_tiles(const CdftBatch &a, cudaStream_t st)
+{
+    k_cdft_tiles<<<1, 32, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -433,8 +433,35 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+// Lag buckets of snapshot s in this batch (0 if it has no representable lag).
+__device__ __forceinline__ int nb_of(const CdftBatch &a, int s)
+{
+    const int lo = a.lr[2 * s], hi = a.lr[2 * s + 1];
+    return hi >= lo ? hi - lo + 1 : 0;
+}
+
+// Persistent, warp-specialised contraction over every tile of the batch.
+// The tile list (tbase, per-snapshot layout) is computed on the device by
+// k_cdft_tiles, so the host launches a fixed grid without knowing it. Each
+// CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...; a tile is either
+//   rows: 128 consecutive (lag, chunk) rows, lag-major; each producer lane
+//         loads its row's capture segments (Raw<FMT>), or
+//   lags: 128 consecutive lags L0 .. L0 + 127 at one chunk b; the tile
+//         stages y1[bM .. bM + M) (scaled by zscale) and the window
+//         y2[bM + L0 .. bM + L0 + M + 127) in shared memory once, decoded to
+//         FP32, and the producers read only shared memory.
+// Samples outside [0, N) are zero in both, so the sums run over the overlap.
+// Stage counters run across tiles, so every mbarrier keeps one phase
+// sequence for the CTA's lifetime; one TMEM accumulator is reused, and the
+// epilogue of a tile (tcgen05.ld -> W) completes before the next tile's
+// first MMA (CTA barrier between tiles).
+template <int P> __host__ __device__ constexpr int tc_smem_bytes()
+{
+    return ws_smem_bytes<P>() + (2 * kLagTileMaxChunk + kRows) * (int)sizeof(float2);
+}
+
 template <int FMT, int DT, int P>
-__global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_mma(CdftBatch a)
+__global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
 {
     constexpr int NS = kRing;
     constexpr int kSt = 2 * P * kBlockBytes;  // bytes of one stage's A (or B) blocks
@@ -444,227 +471,13 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_mma(CdftBatch a
     __shared__ volatile int s_abort;
     __shared__ int s_last_commit;
 
-    const int tile = blockIdx.x;
-    const int s = step_of_tile(a.tbase, a.S, tile);
-    const int ltile = tile - a.tbase[s];
-    const StepDesc sd = a.sd[s];
-    const int N = sd.n, M = a.M;
-    const int Bs = (N + M - 1) / M;
-    const int NB = a.bbase[s + 1] - a.bbase[s];
-    const int64_t R = (int64_t)NB * Bs;
-    const int NJ = M / kKS;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char *sA0 = smem;
-    unsigned char *sB0 = smem + NS * kSt;
-
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < NS; ++i) {
-            mbar_init(smem_u32(&full_a[i]), kProducerWarps);
-            mbar_init(smem_u32(&full_b[i]), 1);
-            mbar_init(smem_u32(&empty[i]), 1);
-        }
-        s_abort = 0;
-        s_last_commit = -1;
-        fence_mbar_init();
-        fence_proxy_async_smem();
-    }
-    if (warp == 0) tmem_alloc(smem_u32(&tmem_slot), 128);
-    tc_before_sync();
-    __syncthreads();
-    tc_after_sync();
-    const uint32_t tmem = tmem_slot;
-    const unsigned char *bsrc = reinterpret_cast<const unsigned char *>(a.btab) + (size_t)s * NJ * kSt;
-
-    if (warp < kProducerWarps) {
-        // ---- producers: lane = 8 rows x 4 groups of 8 samples, two row sets per warp
-        const int rin = lane & 7, kg = lane >> 3;
-        int pL[2], pn0[2];
-        bool pv[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int row = 16 * warp + 8 * h + rin;
-            const int64_t g = (int64_t)ltile * kRows + row;
-            pv[h] = g < R;
-            pL[h] = 0;
-            pn0[h] = 0;
-            if (pv[h]) {
-                const int bl = (int)(g / Bs);
-                pn0[h] = (int)(g % Bs) * M + 8 * kg;
-                pL[h] = a.lr[2 * s] + bl;
-                pv[h] = a.count[a.bbase[s] + bl] > 0;
-            }
-        }
-        const float zs = a.zscale;
-        for (int j = 0; j < NJ; ++j) {
-            const int slot = j % NS;
-            if (j >= NS && !mbar_wait(smem_u32(&empty[slot]), (uint32_t)((j / NS) - 1) & 1u)) s_abort = 1;
-            if (s_abort) break;
-            unsigned char *sA = sA0 + slot * kSt;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int row = 16 * warp + 8 * h + rin;
-                Raw<FMT> raw;
-                const int n = pn0[h] + j * kKS;
-                raw.fetch(sd.y1, sd.y2, n, n + pL[h], N, pv[h]);
-                float2 x[8], y[8];
-                raw.decode(sd.y1, sd.y2, N, pv[h], x, y);
-                float zr[8], zi[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    zr[u] = fmaf(x[u].x, y[u].x, x[u].y * y[u].y) * zs;
-                    zi[u] = fmaf(x[u].y, y[u].x, -x[u].x * y[u].y) * zs;
-                }
-                uint16_t hr[8], hi[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    hr[u] = to16<DT>(zr[u]);
-                    hi[u] = to16<DT>(zi[u]);
-                }
-                auto pk = [](const uint16_t *q) {
-                    return make_uint4((uint32_t)q[0] | ((uint32_t)q[1] << 16), (uint32_t)q[2] | ((uint32_t)q[3] << 16),
-                                      (uint32_t)q[4] | ((uint32_t)q[5] << 16), (uint32_t)q[6] | ((uint32_t)q[7] << 16));
-                };
-                *reinterpret_cast<uint4 *>(sA + blk_off(row, 8 * kg)) = pk(hr);
-                *reinterpret_cast<uint4 *>(sA + kBlockBytes + blk_off(row, 8 * kg)) = pk(hi);
-                if (P == 2) {  // residuals z - high part, rounded to 16 bits
-                    uint16_t lr[8], li[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        lr[u] = to16<DT>(zr[u] - from16<DT>(hr[u]));
-                        li[u] = to16<DT>(zi[u] - from16<DT>(hi[u]));
-                    }
-                    *reinterpret_cast<uint4 *>(sA + 2 * kBlockBytes + blk_off(row, 8 * kg)) = pk(lr);
-                    *reinterpret_cast<uint4 *>(sA + 3 * kBlockBytes + blk_off(row, 8 * kg)) = pk(li);
-                }
-            }
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&full_a[slot]));
-        }
-    } else if (lane == 0) {
-        // ---- control: bulk copies of B, MMA issue, commits
-        for (int t = 0; t < NS && t < NJ; ++t) {
-            mbar_expect_tx(smem_u32(&full_b[t]), kSt);
-            bulk_g2s(smem_u32(sB0 + t * kSt), bsrc + (size_t)t * kSt, kSt, smem_u32(&full_b[t]));
-        }
-        const uint32_t id = idesc<DT>();
-        for (int j = 0; j < NJ; ++j) {
-            const int slot = j % NS;
-            const uint32_t ph = (uint32_t)(j / NS) & 1u;
-            if (!mbar_wait(smem_u32(&full_a[slot]), ph) || !mbar_wait(smem_u32(&full_b[slot]), ph) || s_abort) {
-                s_abort = 1;
-                break;
-            }
-            tc_after_sync();
-            const unsigned char *sA = sA0 + slot * kSt;
-            const unsigned char *sB = sB0 + slot * kSt;
-            // products per block: high x high, and for the split forms also
-            // residual x high and high x residual (part p at p * 2 blocks)
-            constexpr int NPROD = P == 2 ? 3 : 1;
-#pragma unroll
-            for (int blk = 0; blk < 2; ++blk)
-#pragma unroll
-                for (int kk = 0; kk < kKS; kk += 16)
-#pragma unroll
-                    for (int pr = 0; pr < NPROD; ++pr) {
-                        const int pa = pr == 1 ? 1 : 0, pb = pr == 2 ? 1 : 0;
-                        const uint64_t ad = sdesc(smem_u32(sA + (2 * pa + blk) * kBlockBytes) + kk * 16);
-                        const uint64_t bd = sdesc(smem_u32(sB + (2 * pb + blk) * kBlockBytes) + kk * 16);
-                        mma_f16(tmem, ad, bd, id, (j > 0 || blk > 0 || kk > 0 || pr > 0) ? 1u : 0u);
-                    }
-            mma_commit(smem_u32(&empty[slot]));
-            s_last_commit = j;
-            // refill the slot of stage j - 1 with B of stage j - 1 + NS once its MMAs are done
-            if (j >= 1 && j - 1 + NS < NJ) {
-                const int s1 = (j - 1) % NS;
-                if (!mbar_wait(smem_u32(&empty[s1]), (uint32_t)((j - 1) / NS) & 1u)) {
-                    s_abort = 1;
-                    break;
-                }
-                mbar_expect_tx(smem_u32(&full_b[s1]), kSt);
-                bulk_g2s(smem_u32(sB0 + s1 * kSt), bsrc + (size_t)(j - 1 + NS) * kSt, kSt, smem_u32(&full_b[s1]));
-            }
-        }
-    }
-    // every issued MMA is covered by the last commit
-    __syncthreads();
-    const int lc = s_last_commit;
-    bool ok = lc >= 0 && mbar_wait(smem_u32(&empty[lc % NS]), (uint32_t)(lc / NS) & 1u);
-    ok = !__syncthreads_or(!ok || s_abort || lc != NJ - 1);
-    if (threadIdx.x == 0 && (s_abort || lc != NJ - 1)) atomicOr(a.err, ERR_TIMEOUT);
-    tc_after_sync();
-    if (ok && warp < 8) {
-        // warp w reads lanes 32 (w % 4) .. +31 (its rows), columns 64 (w / 4) .. +63
-        const int row = 32 * (warp & 3) + lane, half = warp >> 2;
-        const int64_t g = (int64_t)ltile * kRows + row;
-        bool valid = g < R;
-        int64_t wrow = 0;
-        if (valid) {
-            const int bl = (int)(g / Bs);
-            valid = a.count[a.bbase[s] + bl] > 0;
-            wrow = ((int64_t)(a.bbase[s] + bl) * a.Bmax + g % Bs) * 128;
-        }
-        const float inv = 1.0f / a.zscale;
-        const uint32_t tb = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * half);
-#pragma unroll
-        for (int c = 0; c < 64; c += 32) {
-            uint32_t r[32];
-            tmem_ld32(tb + (uint32_t)c, r);
-            if (valid) {
-                float4 *w = reinterpret_cast<float4 *>(a.W + wrow + 64 * half + c);
-#pragma unroll
-                for (int v = 0; v < 8; ++v)
-                    w[v] = make_float4(__uint_as_float(r[4 * v]) * inv, __uint_as_float(r[4 * v + 1]) * inv,
-                                       __uint_as_float(r[4 * v + 2]) * inv, __uint_as_float(r[4 * v + 3]) * inv);
-            }
-        }
-    }
-    tc_before_sync();
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, 128);
-}
-
-// Lag-tile form of the same contraction. A tile is 128 consecutive lags
-// L0 .. L0 + 127 of one snapshot at one chunk b: every row needs y1 over the
-// chunk and y2 shifted by its own lag, so the tile stages y1[bM .. bM + M)
-// (pre-scaled by zscale) and the window y2[bM + L0 .. bM + L0 + M + 127) once,
-// decoded to FP32, in shared memory; the producers then form each stage's lag
-// products from shared memory only. Samples outside [0, N) are staged as
-// zero, so the sums run over the overlap. The ring, the control thread, the
-// bounded waits and the epilogue are those of k_cdft_contract_mma; rows are
-// lags here, so row r of the tile writes W[bucket L0 + r - Lmin][b].
-template <int P> __host__ __device__ constexpr int lag_smem_bytes()
-{
-    return ws_smem_bytes<P>() + (2 * kLagTileMaxChunk + kRows) * (int)sizeof(float2);
-}
-
-template <int FMT, int DT, int P>
-__global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_lag(CdftBatch a)
-{
-    constexpr int NS = kRing;
-    constexpr int kSt = 2 * P * kBlockBytes;
-    extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t full_a[NS], full_b[NS], empty[NS];
-    __shared__ uint32_t tmem_slot;
-    __shared__ volatile int s_abort;
-    __shared__ int s_last_commit;
-
-    const int tile = blockIdx.x;
-    const int s = step_of_tile(a.tbase, a.S, tile);
-    const int ltile = tile - a.tbase[s];
-    const StepDesc sd = a.sd[s];
-    const int N = sd.n, M = a.M;
-    const int NB = a.bbase[s + 1] - a.bbase[s];
-    const int NLB = (NB + kRows - 1) / kRows;
-    const int lb = ltile % NLB, b = ltile / NLB;
-    const int Lmin = a.lr[2 * s];
-    const int L0 = Lmin + lb * kRows;
-    const int NJ = M / kKS;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *sA0 = smem;
     unsigned char *sB0 = smem + NS * kSt;
     float2 *sy1 = reinterpret_cast<float2 *>(smem + 2 * NS * kSt);
     float2 *sy2 = sy1 + kLagTileMaxChunk;
+    const int M = a.M, NJ = M / kKS;
+    const int ntiles = a.tbase[a.S];
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < NS; ++i) {
@@ -673,7 +486,6 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_lag(CdftBatch a
             mbar_init(smem_u32(&empty[i]), 1);
         }
         s_abort = 0;
-        s_last_commit = -1;
         fence_mbar_init();
         fence_proxy_async_smem();
     }
@@ -682,142 +494,211 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_lag(CdftBatch a
     __syncthreads();
     tc_after_sync();
     const uint32_t tmem = tmem_slot;
-    const unsigned char *bsrc = reinterpret_cast<const unsigned char *>(a.btab) + (size_t)s * NJ * kSt;
+    const uint32_t id = idesc<DT>();
 
-    if (warp < kProducerWarps) {
-        // ---- stage the tile's windows (producers only; named barrier 1)
-        const int nb0 = b * M;
-        const float zs = a.zscale;
-        for (int i = threadIdx.x; i < M; i += kProducerWarps * 32) {
-            const int n = nb0 + i;
-            float2 v = n < N ? IQ<FMT>::load(sd.y1, n) : make_float2(0.f, 0.f);
-            sy1[i] = make_float2(v.x * zs, v.y * zs);
-        }
-        for (int i = threadIdx.x; i < M + kRows; i += kProducerWarps * 32) {
-            const int n2 = nb0 + L0 + i;
-            sy2[i] = (n2 >= 0 && n2 < N) ? IQ<FMT>::load(sd.y2, n2) : make_float2(0.f, 0.f);
-        }
-        asm volatile("bar.sync 1, %0;" ::"r"(kProducerWarps * 32) : "memory");
-        // ---- producers: lane = 8 rows x 4 groups of 8 samples, two row sets per warp
-        const int rin = lane & 7, kg = lane >> 3;
-        for (int j = 0; j < NJ; ++j) {
-            const int slot = j % NS;
-            if (j >= NS && !mbar_wait(smem_u32(&empty[slot]), (uint32_t)((j / NS) - 1) & 1u)) s_abort = 1;
-            if (s_abort) break;
-            unsigned char *sA = sA0 + slot * kSt;
-            const int m0 = j * kKS + 8 * kg;
-            float2 x[8];
-#pragma unroll
-            for (int u = 0; u < 8; u += 2) {
-                const float4 q = *reinterpret_cast<const float4 *>(sy1 + m0 + u);
-                x[u] = make_float2(q.x, q.y);
-                x[u + 1] = make_float2(q.z, q.w);
+    uint32_t g0 = 0;  // global index of this tile's first stage
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, g0 += (uint32_t)NJ) {
+        const int s = step_of_tile(a.tbase, a.S, tile);
+        const int ltile = tile - a.tbase[s];
+        const StepDesc sd = a.sd[s];
+        const int N = sd.n;
+        const int Bs = (N + M - 1) / M;
+        const int NB = nb_of(a, s);
+        const int lay = a.layout[s];
+        const int NLB = (NB + kRows - 1) / kRows;
+        const int lb = lay ? ltile % max(NLB, 1) : 0, bch = lay ? ltile / max(NLB, 1) : 0;
+        const int Lmin = a.lr[2 * s];
+        const unsigned char *bsrc = reinterpret_cast<const unsigned char *>(a.btab) + (size_t)s * NJ * kSt;
+
+        if (warp < kProducerWarps) {
+            const int rin = lane & 7, kg = lane >> 3;
+            const float zs = a.zscale;
+            if (lay) {
+                // ---- stage the tile's capture windows (producers only)
+                const int nb0 = bch * M, L0 = Lmin + lb * kRows;
+                for (int i = threadIdx.x; i < M; i += kProducerWarps * 32) {
+                    const int n = nb0 + i;
+                    const float2 v = n < N ? IQ<FMT>::load(sd.y1, n) : make_float2(0.f, 0.f);
+                    sy1[i] = make_float2(v.x * zs, v.y * zs);
+                }
+                for (int i = threadIdx.x; i < M + kRows; i += kProducerWarps * 32) {
+                    const int n2 = nb0 + L0 + i;
+                    sy2[i] = (n2 >= 0 && n2 < N) ? IQ<FMT>::load(sd.y2, n2) : make_float2(0.f, 0.f);
+                }
+                asm volatile("bar.sync 1, %0;" ::"r"(kProducerWarps * 32) : "memory");
             }
+            // rows (row layout): two row sets per warp, 8 rows x 4 sample groups per set
+            int pL[2] = {0, 0}, pn0[2] = {0, 0};
+            bool pv[2] = {false, false};
+            if (!lay) {
+                const int64_t R = (int64_t)NB * Bs;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int row = 16 * warp + 8 * h + rin;
-                const float2 *py = sy2 + m0 + row;
-                float zr[8], zi[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const float2 y = py[u];
-                    zr[u] = fmaf(x[u].x, y.x, x[u].y * y.y);
-                    zi[u] = fmaf(x[u].y, y.x, -x[u].x * y.y);
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t g = (int64_t)ltile * kRows + 16 * warp + 8 * h + rin;
+                    if (g < R) {
+                        const int bl = (int)(g / Bs);
+                        pn0[h] = (int)(g % Bs) * M + 8 * kg;
+                        pL[h] = Lmin + bl;
+                        pv[h] = a.count[a.bbase[s] + bl] > 0;
+                    }
                 }
-                uint32_t hr[4], hi[4];
+            }
+            for (int j = 0; j < NJ; ++j) {
+                const uint32_t g = g0 + (uint32_t)j;
+                const int slot = (int)(g % NS);
+                if (g >= NS && !mbar_wait(smem_u32(&empty[slot]), ((g / NS) - 1) & 1u)) s_abort = 1;
+                if (s_abort) break;
+                unsigned char *sA = sA0 + slot * kSt;
+                float2 x[8];
+                if (lay) {
+                    const int m0 = j * kKS + 8 * kg;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    hr[u] = pack2<DT>(zr[2 * u], zr[2 * u + 1]);
-                    hi[u] = pack2<DT>(zi[2 * u], zi[2 * u + 1]);
+                    for (int u = 0; u < 8; u += 2) {
+                        const float4 q = *reinterpret_cast<const float4 *>(sy1 + m0 + u);
+                        x[u] = make_float2(q.x, q.y);
+                        x[u + 1] = make_float2(q.z, q.w);
+                    }
                 }
-                *reinterpret_cast<uint4 *>(sA + blk_off(row, 8 * kg)) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
-                *reinterpret_cast<uint4 *>(sA + kBlockBytes + blk_off(row, 8 * kg)) =
-                    make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                if (P == 2) {  // residuals z - high part, rounded to 16 bits
-                    uint32_t lr[4], li[4];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int row = 16 * warp + 8 * h + rin;
+                    float2 y[8];
+                    if (lay) {
+                        const float2 *py = sy2 + j * kKS + 8 * kg + row;
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) y[u] = py[u];
+                    } else {
+                        Raw<FMT> raw;
+                        const int n = pn0[h] + j * kKS;
+                        raw.fetch(sd.y1, sd.y2, n, n + pL[h], N, pv[h]);
+                        raw.decode(sd.y1, sd.y2, N, pv[h], x, y);
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) x[u] = make_float2(x[u].x * zs, x[u].y * zs);
+                    }
+                    float zr[8], zi[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        zr[u] = fmaf(x[u].x, y[u].x, x[u].y * y[u].y);
+                        zi[u] = fmaf(x[u].y, y[u].x, -x[u].x * y[u].y);
+                    }
+                    uint32_t hr[4], hi[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const float2 fr = unpack2<DT>(hr[u]), fi = unpack2<DT>(hi[u]);
-                        lr[u] = pack2<DT>(zr[2 * u] - fr.x, zr[2 * u + 1] - fr.y);
-                        li[u] = pack2<DT>(zi[2 * u] - fi.x, zi[2 * u + 1] - fi.y);
+                        hr[u] = pack2<DT>(zr[2 * u], zr[2 * u + 1]);
+                        hi[u] = pack2<DT>(zi[2 * u], zi[2 * u + 1]);
                     }
-                    *reinterpret_cast<uint4 *>(sA + 2 * kBlockBytes + blk_off(row, 8 * kg)) =
-                        make_uint4(lr[0], lr[1], lr[2], lr[3]);
-                    *reinterpret_cast<uint4 *>(sA + 3 * kBlockBytes + blk_off(row, 8 * kg)) =
-                        make_uint4(li[0], li[1], li[2], li[3]);
+                    *reinterpret_cast<uint4 *>(sA + blk_off(row, 8 * kg)) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+                    *reinterpret_cast<uint4 *>(sA + kBlockBytes + blk_off(row, 8 * kg)) =
+                        make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                    if (P == 2) {  // residuals z - high part, rounded to 16 bits
+                        uint32_t lr[4], li[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const float2 fr = unpack2<DT>(hr[u]), fi = unpack2<DT>(hi[u]);
+                            lr[u] = pack2<DT>(zr[2 * u] - fr.x, zr[2 * u + 1] - fr.y);
+                            li[u] = pack2<DT>(zi[2 * u] - fi.x, zi[2 * u + 1] - fi.y);
+                        }
+                        *reinterpret_cast<uint4 *>(sA + 2 * kBlockBytes + blk_off(row, 8 * kg)) =
+                            make_uint4(lr[0], lr[1], lr[2], lr[3]);
+                        *reinterpret_cast<uint4 *>(sA + 3 * kBlockBytes + blk_off(row, 8 * kg)) =
+                            make_uint4(li[0], li[1], li[2], li[3]);
+                    }
                 }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&full_a[slot]));
             }
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&full_a[slot]));
-        }
-    } else if (lane == 0) {
-        // ---- control: bulk copies of B, MMA issue, commits
-        for (int t = 0; t < NS && t < NJ; ++t) {
-            mbar_expect_tx(smem_u32(&full_b[t]), kSt);
-            bulk_g2s(smem_u32(sB0 + t * kSt), bsrc + (size_t)t * kSt, kSt, smem_u32(&full_b[t]));
-        }
-        const uint32_t id = idesc<DT>();
-        for (int j = 0; j < NJ; ++j) {
-            const int slot = j % NS;
-            const uint32_t ph = (uint32_t)(j / NS) & 1u;
-            if (!mbar_wait(smem_u32(&full_a[slot]), ph) || !mbar_wait(smem_u32(&full_b[slot]), ph) || s_abort) {
-                s_abort = 1;
-                break;
-            }
-            tc_after_sync();
-            const unsigned char *sA = sA0 + slot * kSt;
-            const unsigned char *sB = sB0 + slot * kSt;
-            constexpr int NPROD = P == 2 ? 3 : 1;
-#pragma unroll
-            for (int blk = 0; blk < 2; ++blk)
-#pragma unroll
-                for (int kk = 0; kk < kKS; kk += 16)
-#pragma unroll
-                    for (int pr = 0; pr < NPROD; ++pr) {
-                        const int pa = pr == 1 ? 1 : 0, pb = pr == 2 ? 1 : 0;
-                        const uint64_t ad = sdesc(smem_u32(sA + (2 * pa + blk) * kBlockBytes) + kk * 16);
-                        const uint64_t bd = sdesc(smem_u32(sB + (2 * pb + blk) * kBlockBytes) + kk * 16);
-                        mma_f16(tmem, ad, bd, id, (j > 0 || blk > 0 || kk > 0 || pr > 0) ? 1u : 0u);
-                    }
-            mma_commit(smem_u32(&empty[slot]));
-            s_last_commit = j;
-            if (j >= 1 && j - 1 + NS < NJ) {
-                const int s1 = (j - 1) % NS;
-                if (!mbar_wait(smem_u32(&empty[s1]), (uint32_t)((j - 1) / NS) & 1u)) {
-                    s_abort = 1;
+        } else if (lane == 0) {
+            // ---- control: bulk copies of B, MMA issue, commits. B of stage
+            // g goes into slot g % NS once the MMAs of stage g - NS are done.
+            s_last_commit = -1;
+            auto load_b = [&](uint32_t g) -> bool {
+                const int slot = (int)(g % NS);
+                if (g >= NS && !mbar_wait(smem_u32(&empty[slot]), ((g / NS) - 1) & 1u)) return false;
+                mbar_expect_tx(smem_u32(&full_b[slot]), kSt);
+                bulk_g2s(smem_u32(sB0 + slot * kSt), bsrc + (size_t)(g - g0) * kSt, kSt, smem_u32(&full_b[slot]));
+                return true;
+            };
+            bool alive = true;
+            for (int t = 0; t < NS && t < NJ && alive; ++t) alive = load_b(g0 + (uint32_t)t);
+            for (int j = 0; j < NJ && alive; ++j) {
+                const uint32_t g = g0 + (uint32_t)j;
+                const int slot = (int)(g % NS);
+                const uint32_t ph = (g / NS) & 1u;
+                if (!mbar_wait(smem_u32(&full_a[slot]), ph) || !mbar_wait(smem_u32(&full_b[slot]), ph) || s_abort) {
+                    alive = false;
                     break;
                 }
-                mbar_expect_tx(smem_u32(&full_b[s1]), kSt);
-                bulk_g2s(smem_u32(sB0 + s1 * kSt), bsrc + (size_t)(j - 1 + NS) * kSt, kSt, smem_u32(&full_b[s1]));
+                tc_after_sync();
+                const unsigned char *sA = sA0 + slot * kSt;
+                const unsigned char *sB = sB0 + slot * kSt;
+                constexpr int NPROD = P == 2 ? 3 : 1;
+#pragma unroll
+                for (int blk = 0; blk < 2; ++blk)
+#pragma unroll
+                    for (int kk = 0; kk < kKS; kk += 16)
+#pragma unroll
+                        for (int pr = 0; pr < NPROD; ++pr) {
+                            const int pa = pr == 1 ? 1 : 0, pb = pr == 2 ? 1 : 0;
+                            const uint64_t ad = sdesc(smem_u32(sA + (2 * pa + blk) * kBlockBytes) + kk * 16);
+                            const uint64_t bd = sdesc(smem_u32(sB + (2 * pb + blk) * kBlockBytes) + kk * 16);
+                            mma_f16(tmem, ad, bd, id, (j > 0 || blk > 0 || kk > 0 || pr > 0) ? 1u : 0u);
+                        }
+                mma_commit(smem_u32(&empty[slot]));
+                s_last_commit = j;
+                // B of stage j - 1 + NS into the slot of stage j - 1
+                if (j >= 1 && j - 1 + NS < NJ && !load_b(g - 1 + NS)) {
+                    alive = false;
+                    break;
+                }
+            }
+            if (!alive) s_abort = 1;
+        }
+        // every issued MMA of the tile is covered by its last commit
+        __syncthreads();
+        const int lc = s_last_commit;
+        bool ok = lc >= 0 && mbar_wait(smem_u32(&empty[(g0 + (uint32_t)lc) % NS]), ((g0 + (uint32_t)lc) / NS) & 1u);
+        ok = !__syncthreads_or(!ok || s_abort || lc != NJ - 1);
+        if (!ok) {
+            if (threadIdx.x == 0) atomicOr(a.err, ERR_TIMEOUT);
+            break;
+        }
+        tc_after_sync();
+        if (warp < 8) {
+            // warp w reads lanes 32 (w % 4) .. +31 (its rows), columns 64 (w / 4) .. +63
+            const int row = 32 * (warp & 3) + lane, half = warp >> 2;
+            bool valid;
+            int64_t wrow;
+            if (lay) {
+                const int bl = lb * kRows + row;
+                valid = bl < NB && a.count[a.bbase[s] + bl] > 0;
+                wrow = ((int64_t)(a.bbase[s] + bl) * a.Bmax + bch) * 128;
+            } else {
+                const int64_t g = (int64_t)ltile * kRows + row;
+                valid = g < (int64_t)NB * Bs;
+                const int bl = valid ? (int)(g / Bs) : 0;
+                valid = valid && a.count[a.bbase[s] + bl] > 0;
+                wrow = ((int64_t)(a.bbase[s] + bl) * a.Bmax + (valid ? g % Bs : 0)) * 128;
+            }
+            const float inv = 1.0f / a.zscale;
+            const uint32_t tb = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * half);
+#pragma unroll
+            for (int c = 0; c < 64; c += 32) {
+                uint32_t r[32];
+                tmem_ld32(tb + (uint32_t)c, r);
+                if (valid) {
+                    float4 *w = reinterpret_cast<float4 *>(a.W + wrow + 64 * half + c);
+#pragma unroll
+                    for (int v = 0; v < 8; ++v)
+                        w[v] = make_float4(__uint_as_float(r[4 * v]) * inv, __uint_as_float(r[4 * v + 1]) * inv,
+                                           __uint_as_float(r[4 * v + 2]) * inv, __uint_as_float(r[4 * v + 3]) * inv);
+                }
             }
         }
-    }
-    __syncthreads();
-    const int lc = s_last_commit;
-    bool ok = lc >= 0 && mbar_wait(smem_u32(&empty[lc % NS]), (uint32_t)(lc / NS) & 1u);
-    ok = !__syncthreads_or(!ok || s_abort || lc != NJ - 1);
-    if (threadIdx.x == 0 && (s_abort || lc != NJ - 1)) atomicOr(a.err, ERR_TIMEOUT);
-    tc_after_sync();
-    if (ok && warp < 8) {
-        const int row = 32 * (warp & 3) + lane, half = warp >> 2;
-        const int bl = lb * kRows + row;
-        const bool valid = bl < NB && a.count[a.bbase[s] + bl] > 0;
-        const int64_t wrow = ((int64_t)(a.bbase[s] + bl) * a.Bmax + b) * 128;
-        const float inv = 1.0f / a.zscale;
-        const uint32_t tb = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * half);
-#pragma unroll
-        for (int c = 0; c < 64; c += 32) {
-            uint32_t r[32];
-            tmem_ld32(tb + (uint32_t)c, r);
-            if (valid) {
-                float4 *w = reinterpret_cast<float4 *>(a.W + wrow + 64 * half + c);
-#pragma unroll
-                for (int v = 0; v < 8; ++v)
-                    w[v] = make_float4(__uint_as_float(r[4 * v]) * inv, __uint_as_float(r[4 * v + 1]) * inv,
-                                       __uint_as_float(r[4 * v + 2]) * inv, __uint_as_float(r[4 * v + 3]) * inv);
-            }
-        }
+        // the accumulator is read before the next tile's first MMA
+        tc_before_sync();
+        __syncthreads();
+        tc_after_sync();
     }
     tc_before_sync();
     __syncthreads();
@@ -841,26 +722,14 @@ cudaError_t launch_cdft_btab(const CdftBatch &a, int mode, void *btab, cudaStrea
 size_t cdft_btab_bytes(int mode, int M) { return (size_t)(M / kKS) * 2 * (mode >= DG_CONTRACT_BF16X3 ? 2 : 1) * kBlockBytes; }
 
 template <int FMT, int DT, int P>
-static cudaError_t launch_mma(const CdftBatch &a, int tiles, cudaStream_t st)
+static cudaError_t launch_mma(const CdftBatch &a, int grid, cudaStream_t st)
 {
-    if (a.lag_tiles) {
-        if (a.M > kLagTileMaxChunk) return cudaErrorInvalidValue;
-        const int smem = lag_smem_bytes<P>();
-        cudaError_t e = cudaFuncSetAttribute(k_cdft_contract_lag<FMT, DT, P>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        k_cdft_contract_lag<FMT, DT, P><<<(unsigned)tiles, kWsThreads, smem, st>>>(a);
-        return cudaGetLastError();
-    }
-    const int smem = ws_smem_bytes<P>();
-    cudaError_t e = cudaFuncSetAttribute(k_cdft_contract_mma<FMT, DT, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    // lag tiles stage M + 128 samples; k_cdft_tiles gives batches with
+    // M > kLagTileMaxChunk row tiles only
+    const int smem = tc_smem_bytes<P>();
+    cudaError_t e = cudaFuncSetAttribute(k_cdft_contract_tc<FMT, DT, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    // all of the unified L1/shared storage as shared memory: two CTAs of the
-    // single-product forms fit on one SM
-    e = cudaFuncSetAttribute(k_cdft_contract_mma<FMT, DT, P>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
-    if (e != cudaSuccess) return e;
-    k_cdft_contract_mma<FMT, DT, P><<<(unsigned)tiles, kWsThreads, smem, st>>>(a);
+    k_cdft_contract_tc<FMT, DT, P><<<(unsigned)grid, kWsThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -312,11 +312,15 @@ struct CdftBatch {
     float *nubase, *delta;        // [S] bins nu_q = nubase + q delta
     float2 *V;                    // [S][M][64] DFT table e^{j 2 pi nu_q m}
     float *W;                     // [NBT][Bmax][128]: per chunk 64 bins, re[64] | im[64]
-    const int *tbase;             // [S + 1] first tensor-core tile (128 rows) of each snapshot (device)
+    int *tbase;                   // [S + 1] first tensor-core tile of each snapshot (k_cdft_tiles)
+    int *layout;                  // [S] 1: tiles of 128 lags x one chunk, 0: 128 (lag, chunk) rows
+    int *Mcs;                     // [S] combine chunk: a power-of-two multiple of M (k_cdft_tiles)
+    unsigned long long *work;     // [2] lag x chunk rows, candidate x super-chunk pairs (or NULL)
+    int tiles_mode;               // DG_TILES_*; tensor-core contraction or not (mma)
+    int mma;
+    int ngroups;                  // combine groups of the batch (upper bound; unused ones are -1 in g2b)
     const void *btab;             // [S][M/32][2][128 x 32] 16-bit DFT operand (tensor cores)
     float zscale;                 // lag products are multiplied by this before 16-bit rounding
-    int lag_tiles;                // 1: tensor-core tiles are 128 consecutive lags x one chunk
-    int Mc;                       // combine chunk: a power-of-two multiple of M (k_cdft_superchunk)
 };
 
 cudaError_t launch_cdft_geo(const CdftBatch &a, cudaStream_t s);
@@ -324,14 +328,16 @@ cudaError_t launch_cdft_geo(const CdftBatch &a, cudaStream_t s);
 cudaError_t launch_ecef_split(const double *xyz, int64_t G, float *xyzf, cudaStream_t s);
 cudaError_t launch_cdft_plan(const CdftBatch &a, int NBT, cudaStream_t s);
 cudaError_t launch_cdft_contract_fp32(const CdftBatch &a, int NBT, int fmt, cudaStream_t s);
-cudaError_t launch_cdft_combine(const CdftBatch &a, int groups, float *surf, cudaStream_t s);
+cudaError_t launch_cdft_combine(const CdftBatch &a, float *surf, cudaStream_t s);
+// per snapshot: lag buckets, tile layout, tiles (tbase), combine chunk, work
+cudaError_t launch_cdft_tiles(const CdftBatch &a, cudaStream_t s);
 // W[bucket][c] <- sum over the Mc / M chunks b of super-chunk c of
 // e^{j 2 pi nu_q (b M - c Mc)} W[bucket][b] (in place; Mc > M)
 cudaError_t launch_cdft_superchunk(const CdftBatch &a, int NBT, cudaStream_t s);
 // tensor-core contraction (dg_cdft_mma.cu): mode DG_CONTRACT_BF16 / FP16 /
-// BF16X3 / FP16X3; tiles = total 128-row tiles of the batch (tbase[S])
+// BF16X3 / FP16X3; a persistent launch of `grid` CTAs over the batch's tiles
 cudaError_t launch_cdft_btab(const CdftBatch &a, int mode, void *btab, cudaStream_t s);
-cudaError_t launch_cdft_contract_mma(const CdftBatch &a, int tiles, int fmt, int mode, cudaStream_t s);
+cudaError_t launch_cdft_contract_mma(const CdftBatch &a, int grid, int fmt, int mode, cudaStream_t s);
 size_t cdft_btab_bytes(int mode, int M);  // per snapshot
 // Lag tiles (128 consecutive lags of one chunk share one y1 segment and one
 // y2 window, staged once in shared memory) need chunk <= this.
