@@ -218,6 +218,43 @@ typedef struct {
 dg_status dg_detect(dg_ctx *ctx, const void *cost, double threshold, int32_t relative, int32_t radius,
                     int32_t max_peaks, dg_peak *out, int32_t *n_out);
 
+/* CUDA-graph replay of whole steps (the paper has no counterpart: this
+ * takes the host out of the per-step loop of Algorithm 1). A step is
+ * dg_cost_surface(ctx, cost), the argmax of cost and, if refine_spacing_m > 0
+ * and refine_window_m >= refine_spacing_m, the refinement of
+ * dg_argmax_refine, whose grid is centred on the argmax on the device.
+ * dg_graph_capture runs one step uncaptured (allocating and planning
+ * everything), then records the next as a CUDA graph owned by the context.
+ * It needs every snapshot loaded and a context created on a non-default
+ * stream (DG_EUNSUPPORTED otherwise). Captures reloaded with dg_load_capture
+ * in the same formats and lengths feed the same graph; a change of format,
+ * length or capacity makes dg_graph_launch return DG_ESTATE until the next
+ * capture. dg_graph_launch enqueues one step on the context's stream
+ * (asynchronous). dg_graph_fix waits for the stream, reports latched kernel
+ * errors, and returns the fix of the last step (the same fields as
+ * dg_argmax_refine; DG_EINVAL if the surface held no finite value). */
+dg_status dg_graph_capture(dg_ctx *ctx, void *cost, double refine_spacing_m, double refine_window_m);
+dg_status dg_graph_launch(dg_ctx *ctx);
+dg_status dg_graph_fix(dg_ctx *ctx, dg_fix *out);
+
+/* Many independent captures as one graph (the batching of many uneven
+ * geolocation problems): one step of each context (its own grid, snapshots,
+ * lengths, formats and options; all on one device, each on its own
+ * non-default stream) is a branch forked from and joined to `stream`, so
+ * independent steps run concurrently on the GPU. costs[i] is context i's
+ * surface (device). dg_batch_capture runs each step once uncaptured first.
+ * dg_batch_launch enqueues all n steps on `stream`; dg_batch_fixes waits
+ * for it and writes n fixes (host); a context whose step failed gets
+ * index = -1 and the first failure is returned. A context must not be used
+ * by other calls while a launch of its batch is in flight. */
+typedef struct dg_batch dg_batch;
+dg_status dg_batch_capture(dg_ctx *const *ctxs, int32_t n, void *const *costs, double refine_spacing_m,
+                           double refine_window_m, void *stream, dg_batch **out);
+dg_status dg_batch_launch(dg_batch *batch);
+dg_status dg_batch_fixes(dg_batch *batch, dg_fix *out);
+int64_t dg_batch_launch_count(const dg_batch *batch); /* kernels per launch */
+dg_status dg_batch_destroy(dg_batch *batch);
+
 /* Wait for the context's stream and report any latched kernel error. */
 dg_status dg_sync(dg_ctx *ctx);
 

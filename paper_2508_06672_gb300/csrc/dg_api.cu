@@ -52,7 +52,7 @@ struct CdftLayout {  // batches and bucket / group bases of one grid size
 struct CdftBufs {  // chunked-DFT scratch, grown on demand
     int *lr = nullptr;
     CdftLayout main_layout, loc_layout;
-    std::vector<double> main_span, loc_span;  // FDOA span estimates per snapshot
+    std::vector<double> main_span;  // FDOA span estimates per snapshot (main grid)
     int *layout = nullptr, *Mcs = nullptr;
     unsigned long long *work = nullptr;
     unsigned *nur = nullptr;
@@ -119,6 +119,13 @@ struct dg_ctx {
     LocalGrid loc;
     CdftBufs cd;
     int cd_chunk_min = 0, cd_chunk_max = 0;              // chunks it used
+    // whole-step CUDA graph (dg_graph_*)
+    ArgmaxResult *amax_fine = nullptr;  // refinement argmax (device)
+    dg_fix *fix_dev = nullptr;
+    dg_fix *fix_host = nullptr;         // pinned
+    cudaGraphExec_t graph = nullptr;
+    int64_t graph_launches = 0;         // kernels per replay
+    uint64_t steps_gen = 1, graph_gen = 0;  // capture buffers / formats / lengths generation
     std::string err;
     int64_t launches = 0;
     std::vector<TimedLaunch> pending;
@@ -468,14 +475,22 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
             return fail(c, DG_EUNSUPPORTED, "CDFT: snapshots longer than 2^24 samples are not supported; use DIRECT");
     CdftBufs &b = c->cd;
     CdftLayout &L = refine ? b.loc_layout : b.main_layout;
-    if ((st = cdft_layout(c, gd, G, L)) != DG_OK) return st;
+    // a refinement grid is planned from its shape only (as if centred on the
+    // main grid's centre), so that a step captured in a CUDA graph, whose
+    // refinement centre is known on the device only, plans it alike
+    GridDev shape = gd;
+    if (refine) {
+        shape.lat0_rad = c->gd.lat0_rad;
+        shape.lon0_rad = c->gd.lon0_rad;
+    }
+    if ((st = cdft_layout(c, shape, G, L)) != DG_OK) return st;
     const int s_max = L.s_max;
-    // FDOA spans for the automatic chunk: cached for the main grid; a
-    // refinement grid moves with each call and takes a 3 x 3 lattice
-    std::vector<double> &span = refine ? b.loc_span : b.main_span;
-    if (c->opt.chunk == 0 && (refine || span.size() != (size_t)c->K)) {
+    // FDOA spans for the automatic chunk, from the main grid (a refinement
+    // grid lies around one of its nodes and spans far less)
+    std::vector<double> &span = b.main_span;
+    if (c->opt.chunk == 0 && span.size() != (size_t)c->K) {
         span.assign(c->K, 0.0);
-        for (int k = 0; k < c->K; ++k) span[k] = fdoa_span(c, gd, k, refine ? 3 : 65);
+        for (int k = 0; k < c->K; ++k) span[k] = fdoa_span(c, c->gd, k, 65);
     }
     std::vector<int> Ms(L.batches.size());
     int M_max = 64, B_max = 1;
@@ -852,12 +867,15 @@ dg_status dg_load_capture(dg_ctx *c, int32_t step, int32_t fmt, const void *y1, 
         CK(c, cudaMallocAsync(&s.y1, bytes, c->stream));
         CK(c, cudaMallocAsync(&s.y2, bytes, c->stream));
         s.cap = bytes;
+        ++c->steps_gen;
     }
     const cudaMemcpyKind kind = is_device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     CK(c, cudaMemcpyAsync(s.y1, y1, bytes, kind, c->stream));
     CK(c, cudaMemcpyAsync(s.y2, y2, bytes, kind, c->stream));
-    if (s.fmt != fmt || s.n != n) c->steps_dirty = true;
-    if (!s.loaded) c->steps_dirty = true;
+    if (s.fmt != fmt || s.n != n || !s.loaded) {
+        c->steps_dirty = true;
+        ++c->steps_gen;
+    }
     s.fmt = fmt;
     s.n = n;
     s.loaded = true;
@@ -883,6 +901,36 @@ dg_status dg_sync(dg_ctx *c)
     c->err.clear();
     CK(c, cudaStreamSynchronize(c->stream));
     return check_latched(c);
+}
+
+// Buffers of a refinement grid of G nodes.
+static dg_status ensure_local(dg_ctx *c, int64_t G)
+{
+    const size_t esz = c->opt.prec == DG_PREC_FP64 ? 8 : 4;
+    if (c->loc.g_cap < (size_t)G) {
+        if (c->loc.xyz) CK(c, cudaFreeAsync(c->loc.xyz, c->stream));
+        if (c->loc.surf) CK(c, cudaFreeAsync(c->loc.surf, c->stream));
+        if (c->loc.cost) CK(c, cudaFreeAsync(c->loc.cost, c->stream));
+        c->loc = LocalGrid{};
+        CK(c, cudaMallocAsync((void **)&c->loc.xyz, sizeof(double) * 3 * G, c->stream));
+        CK(c, cudaMallocAsync(&c->loc.surf, esz * G * c->K + 8, c->stream));
+        CK(c, cudaMallocAsync(&c->loc.cost, esz * G + 8, c->stream));
+        c->loc.g_cap = (size_t)G;
+    }
+    return DG_OK;
+}
+
+// Half-width (nodes) of the refinement grid of dg_argmax_refine; 0 = none.
+static dg_status refine_half(dg_ctx *c, double spacing_m, double window_m, int *half)
+{
+    *half = 0;
+    if (!(spacing_m > 0 && window_m >= spacing_m)) return DG_OK;
+    if (!(std::isfinite(spacing_m) && std::isfinite(window_m)))
+        return fail(c, DG_EINVAL, "refinement spacing and window must be finite");
+    const double h = std::floor(window_m / spacing_m + 0.5);
+    if (h > 2000) return fail(c, DG_EINVAL, "refinement grid wider than 4001 nodes");
+    *half = (int)h;
+    return DG_OK;
 }
 
 dg_status dg_argmax_refine(dg_ctx *c, const void *cost, double spacing_m, double window_m, dg_fix *out)
@@ -925,17 +973,7 @@ dg_status dg_argmax_refine(dg_ctx *c, const void *cost, double spacing_m, double
         lg.nlon = n;
         const GridDev lgd = make_griddev(lg, 0, n);
         const int64_t G = (int64_t)n * n;
-        const size_t esz = c->opt.prec == DG_PREC_FP64 ? 8 : 4;
-        if (c->loc.g_cap < (size_t)G) {
-            if (c->loc.xyz) CK(c, cudaFreeAsync(c->loc.xyz, c->stream));
-            if (c->loc.surf) CK(c, cudaFreeAsync(c->loc.surf, c->stream));
-            if (c->loc.cost) CK(c, cudaFreeAsync(c->loc.cost, c->stream));
-            c->loc = LocalGrid{};
-            CK(c, cudaMallocAsync((void **)&c->loc.xyz, sizeof(double) * 3 * G, c->stream));
-            CK(c, cudaMallocAsync(&c->loc.surf, esz * G * c->K + 8, c->stream));
-            CK(c, cudaMallocAsync(&c->loc.cost, esz * G + 8, c->stream));
-            c->loc.g_cap = (size_t)G;
-        }
+        if ((st = ensure_local(c, G)) != DG_OK) return st;
         {
             Timed t(c, DG_K_REFINE);
             CK(c, launch_grid_ecef(lgd, c->loc.xyz, c->stream));
@@ -1010,6 +1048,262 @@ dg_status dg_detect(dg_ctx *c, const void *cost, double threshold, int32_t relat
         out[k].value = pk[k].value;
     }
     *n_out = n;
+    return DG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Whole steps as CUDA graphs
+// ---------------------------------------------------------------------------
+
+// Buffers a device-only step needs (allocated outside any capture).
+static dg_status prepare_step(dg_ctx *c, int half)
+{
+    for (int k = 0; k < c->K; ++k)
+        if (!c->steps[k].loaded) return fail(c, DG_ESTATE, "snapshot %d has not been loaded", k);
+    const size_t esz = c->opt.prec == DG_PREC_FP64 ? 8 : 4;
+    dg_status st = ensure(c, &c->surf, &c->surf_bytes, esz * (size_t)c->G * c->K);
+    if (st != DG_OK) return st;
+    const int n = 2 * half + 1;
+    const int64_t Gl = half > 0 ? (int64_t)n * n : 0;
+    if ((st = ensure(c, &c->amax_tmp, &c->amax_tmp_bytes, argmax_tmp_bytes(std::max<int64_t>(c->G, Gl)))) != DG_OK)
+        return st;
+    if (half > 0 && (st = ensure_local(c, Gl)) != DG_OK) return st;
+    if (!c->amax_fine) CK(c, cudaMallocAsync((void **)&c->amax_fine, sizeof(ArgmaxResult), c->stream));
+    if (!c->fix_dev) CK(c, cudaMallocAsync((void **)&c->fix_dev, sizeof(dg_fix), c->stream));
+    if (!c->fix_host) CK(c, cudaMallocHost((void **)&c->fix_host, sizeof(dg_fix)));
+    return push_steps(c);
+}
+
+// One step on the device only: the surface into cost, its argmax, the
+// refinement grid centred on it (built on the device), the refinement
+// surface and argmax, and the fix record copied to the pinned fix_host. No
+// host synchronisation and no allocation (prepare_step ran before).
+static dg_status step_device(dg_ctx *c, void *cost, double spacing_m, int half)
+{
+    dg_status st = run_surface(c, c->gd, c->xyz, c->G, c->surf, cost, false);
+    if (st != DG_OK) return st;
+    int nl = 0;
+    CK(c, launch_argmax(cost, c->G, c->opt.prec, c->gd, c->amax_tmp, c->amax_res, &nl, c->stream));
+    const ArgmaxResult *fine = nullptr;
+    const int n = 2 * half + 1;
+    if (half > 0) {
+        dg_grid lg;
+        lg.lat0_deg = c->grid.lat0_deg;  // replaced on the device by the argmax node
+        lg.lon0_deg = c->grid.lon0_deg;
+        lg.dlat_m = lg.dlon_m = spacing_m;
+        lg.nlat = lg.nlon = n;
+        const GridDev lgd = make_griddev(lg, 0, n);
+        const int64_t Gl = (int64_t)n * n;
+        CK(c, launch_grid_ecef(lgd, c->loc.xyz, c->stream, c->amax_res));
+        ++nl;
+        st = run_surface(c, lgd, c->loc.xyz, Gl, c->loc.surf, c->loc.cost, true);
+        if (st != DG_OK) return st;
+        CK(c, launch_argmax(c->loc.cost, Gl, c->opt.prec, lgd, c->amax_tmp, c->amax_fine, &nl, c->stream,
+                            c->amax_res));
+        fine = c->amax_fine;
+    }
+    CK(c, launch_make_fix(c->amax_res, fine, c->gd, half > 0 ? n : 0, c->fix_dev, c->stream));
+    ++nl;
+    c->launches += nl;
+    CK(c, cudaMemcpyAsync(c->fix_host, c->fix_dev, sizeof(dg_fix), cudaMemcpyDeviceToHost, c->stream));
+    return DG_OK;
+}
+
+static dg_status read_fix(dg_ctx *c, dg_fix *out)
+{
+    CK(c, cudaStreamSynchronize(c->stream));
+    dg_status st = check_latched(c);
+    if (st != DG_OK) return st;
+    if (c->fix_host->index < 0) return fail(c, DG_EINVAL, "the surface holds no finite value");
+    if (c->fix_host->refine_n > 0 && c->fix_host->ri < 0)
+        return fail(c, DG_EINVAL, "the refinement surface holds no finite value");
+    *out = *c->fix_host;
+    return DG_OK;
+}
+
+// Capture one step of each context as a branch of one graph: forked from and
+// joined to `stream`. Timing is off inside the capture.
+static dg_status capture_steps(dg_ctx *const *ctxs, int n, void *const *costs, double spacing_m, const int *half,
+                               cudaStream_t stream, cudaGraphExec_t *exec, int64_t *launches)
+{
+    dg_ctx *c0 = ctxs[0];
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join((size_t)n, nullptr);
+    CK(c0, cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    for (auto &e : join) CK(c0, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    std::vector<int> timing((size_t)n);
+    std::vector<int64_t> l0((size_t)n);
+    dg_status st = DG_OK;
+    cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaEventRecord(fork, stream);
+    for (int i = 0; i < n && e == cudaSuccess && st == DG_OK; ++i) {
+        dg_ctx *c = ctxs[i];
+        timing[i] = c->opt.timing;
+        c->opt.timing = 0;
+        l0[i] = c->launches;
+        e = cudaStreamWaitEvent(c->stream, fork, 0);
+        if (e == cudaSuccess) st = step_device(c, costs[i], spacing_m, half[i]);
+        if (e == cudaSuccess && st == DG_OK) e = cudaEventRecord(join[i], c->stream);
+        if (e == cudaSuccess && st == DG_OK) e = cudaStreamWaitEvent(stream, join[i], 0);
+        c->opt.timing = timing[i];
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(stream, &g);
+    if (e == cudaSuccess) e = e2;
+    int64_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        const int64_t d = ctxs[i]->launches - l0[i];
+        total += d;
+        ctxs[i]->launches = l0[i];  // counted again at each replay
+    }
+    if (st == DG_OK && e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaEventDestroy(fork);
+    for (auto &j : join) cudaEventDestroy(j);
+    if (st != DG_OK) return st;
+    if (e != cudaSuccess) return fail(c0, DG_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    *launches = total;
+    return DG_OK;
+}
+
+dg_status dg_graph_capture(dg_ctx *c, void *cost, double spacing_m, double window_m)
+{
+    if (!c) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    c->err.clear();
+    if (!cost) return fail(c, DG_EINVAL, "cost is NULL");
+    if (!c->stream || c->stream == cudaStreamLegacy || c->stream == cudaStreamPerThread)
+        return fail(c, DG_EUNSUPPORTED, "graph capture needs a context created on a non-default stream");
+    int half = 0;
+    dg_status st = refine_half(c, spacing_m, window_m, &half);
+    if (st != DG_OK) return st;
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    // one uncaptured step allocates and plans everything; then the capture
+    if ((st = prepare_step(c, half)) != DG_OK) return st;
+    if ((st = step_device(c, cost, spacing_m, half)) != DG_OK) return st;
+    dg_fix f;
+    if ((st = read_fix(c, &f)) != DG_OK) return st;
+    dg_ctx *const cs[1] = {c};
+    void *const costs[1] = {cost};
+    if ((st = capture_steps(cs, 1, costs, spacing_m, &half, c->stream, &c->graph, &c->graph_launches)) != DG_OK)
+        return st;
+    c->graph_gen = c->steps_gen;
+    return DG_OK;
+}
+
+dg_status dg_graph_launch(dg_ctx *c)
+{
+    if (!c) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    c->err.clear();
+    if (!c->graph) return fail(c, DG_ESTATE, "no graph has been captured");
+    if (c->graph_gen != c->steps_gen || c->steps_dirty)
+        return fail(c, DG_ESTATE, "a capture changed format, length or buffer since the graph was captured");
+    CK(c, cudaGraphLaunch(c->graph, c->stream));
+    c->launches += c->graph_launches;
+    return DG_OK;
+}
+
+dg_status dg_graph_fix(dg_ctx *c, dg_fix *out)
+{
+    if (!c) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    c->err.clear();
+    if (!out) return fail(c, DG_EINVAL, "out is NULL");
+    if (!c->fix_host) return fail(c, DG_ESTATE, "no step has run");
+    return read_fix(c, out);
+}
+
+}  // extern "C" (reopened below)
+
+struct dg_batch {
+    std::vector<dg_ctx *> ctxs;
+    std::vector<uint64_t> gens;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int64_t launches = 0;
+    std::string err;
+};
+
+extern "C" {
+
+dg_status dg_batch_capture(dg_ctx *const *ctxs, int32_t n, void *const *costs, double spacing_m, double window_m,
+                           void *stream, dg_batch **out)
+{
+    if (!out) return fail(nullptr, DG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!ctxs || !costs || n < 1) return fail(nullptr, DG_EINVAL, "ctxs and costs must hold n >= 1 entries");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!s || s == cudaStreamLegacy || s == cudaStreamPerThread)
+        return fail(nullptr, DG_EUNSUPPORTED, "graph capture needs a non-default stream");
+    std::vector<int> half((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        dg_ctx *c = ctxs[i];
+        if (!c || !costs[i]) return fail(nullptr, DG_EINVAL, "context or cost %d is NULL", i);
+        if (c->device != ctxs[0]->device) return fail(nullptr, DG_EINVAL, "the contexts must share one device");
+        if (!c->stream || c->stream == cudaStreamLegacy || c->stream == cudaStreamPerThread)
+            return fail(nullptr, DG_EUNSUPPORTED, "context %d is on a default stream", i);
+        c->err.clear();
+        dg_status st = refine_half(c, spacing_m, window_m, &half[i]);
+        if (st == DG_OK) st = prepare_step(c, half[i]);
+        if (st == DG_OK) st = step_device(c, costs[i], spacing_m, half[i]);
+        dg_fix f;
+        if (st == DG_OK) st = read_fix(c, &f);
+        if (st != DG_OK) return fail(nullptr, st, "context %d: %s", i, c->err.c_str());
+    }
+    dg_batch *b = new (std::nothrow) dg_batch();
+    if (!b) return fail(nullptr, DG_ENOMEM, "host allocation failed");
+    b->ctxs.assign(ctxs, ctxs + n);
+    for (int i = 0; i < n; ++i) b->gens.push_back(ctxs[i]->steps_gen);
+    b->stream = s;
+    dg_status st = capture_steps(ctxs, n, costs, spacing_m, half.data(), s, &b->graph, &b->launches);
+    if (st != DG_OK) {
+        const std::string m = ctxs[0]->err;
+        delete b;
+        return fail(nullptr, st, "%s", m.c_str());
+    }
+    *out = b;
+    return DG_OK;
+}
+
+dg_status dg_batch_launch(dg_batch *b)
+{
+    if (!b || !b->graph) return fail(nullptr, DG_EINVAL, "no batch graph");
+    for (size_t i = 0; i < b->ctxs.size(); ++i)
+        if (b->ctxs[i]->steps_gen != b->gens[i] || b->ctxs[i]->steps_dirty)
+            return fail(nullptr, DG_ESTATE, "context %zu changed a capture's format, length or buffer", i);
+    const cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+    if (e != cudaSuccess) return fail(nullptr, DG_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+    return DG_OK;
+}
+
+dg_status dg_batch_fixes(dg_batch *b, dg_fix *out)
+{
+    if (!b || !out) return fail(nullptr, DG_EINVAL, "batch and out must not be NULL");
+    const cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return fail(nullptr, DG_ECUDA, "cudaStreamSynchronize: %s", cudaGetErrorString(e));
+    dg_status worst = DG_OK;
+    for (size_t i = 0; i < b->ctxs.size(); ++i) {
+        dg_status st = read_fix(b->ctxs[i], &out[i]);
+        if (st != DG_OK) {
+            std::memset(&out[i], 0, sizeof(dg_fix));
+            out[i].index = -1;
+            if (worst == DG_OK) {
+                worst = st;
+                fail(nullptr, st, "context %zu: %s", i, b->ctxs[i]->err.c_str());
+            }
+        }
+    }
+    return worst;
+}
+
+int64_t dg_batch_launch_count(const dg_batch *b) { return b ? b->launches : -1; }
+
+dg_status dg_batch_destroy(dg_batch *b)
+{
+    if (!b) return DG_OK;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    delete b;
     return DG_OK;
 }
 
@@ -1116,6 +1410,9 @@ dg_status dg_destroy(dg_ctx *c)
     fr(c->surf);
     fr(c->amax_tmp);
     fr(c->amax_res);
+    fr(c->amax_fine);
+    fr(c->fix_dev);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
     fr(c->err_d);
     fr(c->det_count);
     fr(c->det_cand);
@@ -1155,6 +1452,7 @@ dg_status dg_destroy(dg_ctx *c)
     }
     cudaError_t e = cudaStreamSynchronize(s);
     if (c->amax_host) cudaFreeHost(c->amax_host);
+    if (c->fix_host) cudaFreeHost(c->fix_host);
     if (c->err_h) cudaFreeHost(c->err_h);
     delete c;
     if (e != cudaSuccess) return fail(nullptr, DG_ECUDA, "dg_destroy: %s", cudaGetErrorString(e));

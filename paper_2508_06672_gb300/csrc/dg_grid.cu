@@ -7,8 +7,9 @@ namespace dg {
 // One thread per node of the shard. Geodetic (lat, lon, h = 0) on WGS-84 to
 // ECEF: N = a / sqrt(1 - e2 sin^2 lat), x = N cos lat cos lon,
 // y = N cos lat sin lon, z = N (1 - e2) sin lat. Output SoA [3][G].
-__global__ void __launch_bounds__(256) k_grid_ecef(GridDev g, double *__restrict__ xyz)
+__global__ void __launch_bounds__(256) k_grid_ecef(GridDev g, double *__restrict__ xyz, const ArgmaxResult *centre)
 {
+    if (centre) centre_on(g, centre);
     const int64_t G = (int64_t)g.nrows * g.nlon;
     const GridStep st = grid_step(g);
     const double e2 = kF * (2.0 - kF);
@@ -28,13 +29,13 @@ __global__ void __launch_bounds__(256) k_grid_ecef(GridDev g, double *__restrict
     }
 }
 
-cudaError_t launch_grid_ecef(const GridDev &g, double *xyz, cudaStream_t s)
+cudaError_t launch_grid_ecef(const GridDev &g, double *xyz, cudaStream_t s, const ArgmaxResult *centre)
 {
     const int64_t G = (int64_t)g.nrows * g.nlon;
     int64_t blocks = (G + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks < 1) blocks = 1;
-    k_grid_ecef<<<(unsigned)blocks, 256, 0, s>>>(g, xyz);
+    k_grid_ecef<<<(unsigned)blocks, 256, 0, s>>>(g, xyz, centre);
     return cudaGetLastError();
 }
 

@@ -248,7 +248,11 @@ template <> struct IQ<DG_IQ_CI8> {
 // ---------------------------------------------------------------------------
 // Launchers (host functions; each returns the launch's cudaError_t).
 // ---------------------------------------------------------------------------
-cudaError_t launch_grid_ecef(const GridDev &g, double *xyz, cudaStream_t s);
+struct ArgmaxResult;
+// centre (device, optional): take the grid's centre from an argmax record, as
+// the refinement grid does (its latitude / longitude rounded through degrees
+// exactly as the host would pass them)
+cudaError_t launch_grid_ecef(const GridDev &g, double *xyz, cudaStream_t s, const ArgmaxResult *centre = nullptr);
 
 cudaError_t launch_step_geometry(const GridDev &g, const double *xyz, const double *eph_k,
                                  double fs, double lambda, int delay_mode, int *lag, double *D,
@@ -373,7 +377,20 @@ struct ArgmaxResult {
 // Argmax of v[0..n) (ties to the lowest index, NaN never wins); tmp must hold
 // argmax_tmp_bytes(n) bytes; writes *res (device).
 size_t argmax_tmp_bytes(int64_t n);
+// The refinement grid centred on an argmax record (device): the same
+// degrees round trip as the host's dg_grid of the local grid.
+__device__ __forceinline__ void centre_on(GridDev &g, const ArgmaxResult *c)
+{
+    g.lat0_rad = (c->lat_rad * (180.0 / kPi)) * (kPi / 180.0);
+    g.lon0_rad = (c->lon_rad * (180.0 / kPi)) * (kPi / 180.0);
+}
+
+// The fix of a step from its argmax records (device), as dg_argmax_refine
+// assembles it on the host; fine may be NULL (no refinement, n = 0).
+cudaError_t launch_make_fix(const ArgmaxResult *coarse, const ArgmaxResult *fine, const GridDev &g, int n,
+                            dg_fix *out, cudaStream_t s);
+
 cudaError_t launch_argmax(const void *v, int64_t n, int prec, const GridDev &g, void *tmp,
-                          ArgmaxResult *res, int *launches, cudaStream_t s);
+                          ArgmaxResult *res, int *launches, cudaStream_t s, const ArgmaxResult *centre = nullptr);
 
 }  // namespace dg

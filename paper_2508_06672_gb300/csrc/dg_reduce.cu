@@ -90,8 +90,9 @@ __global__ void __launch_bounds__(1024) k_argmax_partial(const T *__restrict__ v
 }
 
 __global__ void __launch_bounds__(1024) k_argmax_final(const VI *part, int nparts, GridDev g,
-                                                       ArgmaxResult *res)
+                                                       ArgmaxResult *res, const ArgmaxResult *centre)
 {
+    if (centre) centre_on(g, centre);
     VI best{0.0, -1};
     for (int p = threadIdx.x; p < nparts; p += blockDim.x)
         if (beats(part[p], best)) best = part[p];
@@ -122,7 +123,7 @@ static int argmax_blocks(int64_t n)
 size_t argmax_tmp_bytes(int64_t n) { return sizeof(VI) * (size_t)argmax_blocks(n); }
 
 cudaError_t launch_argmax(const void *v, int64_t n, int prec, const GridDev &g, void *tmp,
-                          ArgmaxResult *res, int *launches, cudaStream_t s)
+                          ArgmaxResult *res, int *launches, cudaStream_t s, const ArgmaxResult *centre)
 {
     const int nb = argmax_blocks(n);
     VI *part = reinterpret_cast<VI *>(tmp);
@@ -132,8 +133,43 @@ cudaError_t launch_argmax(const void *v, int64_t n, int prec, const GridDev &g, 
         k_argmax_partial<float><<<nb, 1024, 0, s>>>((const float *)v, n, part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_argmax_final<<<1, 1024, 0, s>>>(part, nb, g, res);
+    k_argmax_final<<<1, 1024, 0, s>>>(part, nb, g, res, centre);
     if (launches) *launches += 2;
+    return cudaGetLastError();
+}
+
+// One thread: the fields of dg_fix as dg_argmax_refine fills them.
+__global__ void k_make_fix(const ArgmaxResult *coarse, const ArgmaxResult *fine, GridDev g, int n, dg_fix *out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    dg_fix f;
+    memset(&f, 0, sizeof f);
+    f.index = coarse->idx;
+    if (coarse->idx >= 0) {
+        f.i = g.row0 + (int)(coarse->idx / g.nlon);
+        f.j = (int)(coarse->idx % g.nlon);
+    }
+    f.lat_deg = coarse->lat_rad * (180.0 / kPi);
+    f.lon_deg = coarse->lon_rad * (180.0 / kPi);
+    f.cost = coarse->val;
+    if (fine && coarse->idx >= 0) {
+        f.refine_n = n;
+        f.ri = f.rj = -1;  // no finite value on the refinement grid
+        if (fine->idx >= 0) {
+            f.ri = (int)(fine->idx / n);
+            f.rj = (int)(fine->idx % n);
+        }
+        f.refined_lat_deg = fine->lat_rad * (180.0 / kPi);
+        f.refined_lon_deg = fine->lon_rad * (180.0 / kPi);
+        f.refined_cost = fine->val;
+    }
+    *out = f;
+}
+
+cudaError_t launch_make_fix(const ArgmaxResult *coarse, const ArgmaxResult *fine, const GridDev &g, int n,
+                            dg_fix *out, cudaStream_t s)
+{
+    k_make_fix<<<1, 32, 0, s>>>(coarse, fine, g, n, out);
     return cudaGetLastError();
 }
 

@@ -19,7 +19,7 @@ import threading
 import numpy as np
 
 __all__ = [
-    "DGError", "dg_grid", "dg_ephem", "dg_options", "dg_fix", "dg_peak", "lib", "library_path",
+    "DGError", "dg_grid", "dg_ephem", "dg_options", "dg_fix", "dg_peak", "lib", "library_path", "Batch",
     "dg_options_default", "dg_create", "dg_load_capture", "dg_cost_surface", "dg_argmax_refine",
     "dg_sync", "dg_destroy", "dg_last_error", "dg_grid_ecef", "dg_step_geometry", "dg_kernel_time",
     "dg_reset_counters", "dg_launch_count", "dg_abi_version", "Geolocator",
@@ -58,6 +58,8 @@ EXPORTED_SYMBOLS = [
     "dg_sync", "dg_destroy", "dg_last_error", "dg_grid_ecef", "dg_step_geometry", "dg_kernel_time",
     "dg_reset_counters", "dg_launch_count", "dg_abi_version", "dg_cost_surface_noalloc",
     "dg_noalloc_last_error", "dg_cdft_work", "dg_detect", "dg_cdft_chunks",
+    "dg_graph_capture", "dg_graph_launch", "dg_graph_fix", "dg_batch_capture", "dg_batch_launch",
+    "dg_batch_fixes", "dg_batch_launch_count", "dg_batch_destroy",
 ]
 DG_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
@@ -152,6 +154,18 @@ def lib():
             L.dg_cost_surface_noalloc.restype = C.c_int
             L.dg_detect.argtypes = [vp, vp, dbl, i32, i32, i32, C.POINTER(dg_peak), C.POINTER(i32)]
             L.dg_detect.restype = C.c_int
+            L.dg_graph_capture.argtypes = [vp, vp, dbl, dbl]
+            L.dg_graph_launch.argtypes = [vp]
+            L.dg_graph_fix.argtypes = [vp, C.POINTER(dg_fix)]
+            L.dg_batch_capture.argtypes = [C.POINTER(vp), i32, C.POINTER(vp), dbl, dbl, vp, C.POINTER(vp)]
+            L.dg_batch_launch.argtypes = [vp]
+            L.dg_batch_fixes.argtypes = [vp, C.POINTER(dg_fix)]
+            L.dg_batch_launch_count.argtypes = [vp]
+            L.dg_batch_launch_count.restype = C.c_int64
+            L.dg_batch_destroy.argtypes = [vp]
+            for f in ("dg_graph_capture", "dg_graph_launch", "dg_graph_fix", "dg_batch_capture", "dg_batch_launch",
+                      "dg_batch_fixes", "dg_batch_destroy"):
+                getattr(L, f).restype = C.c_int
             L.dg_cdft_chunks.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
             L.dg_cdft_chunks.restype = C.c_int
             L.dg_cdft_work.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
@@ -235,6 +249,53 @@ def dg_kernel_time(ctx, kernel_class):
     ms, n = C.c_double(), C.c_int64()
     _check(lib().dg_kernel_time(ctx, int(kernel_class), C.byref(ms), C.byref(n)), ctx)
     return ms.value, n.value
+
+
+class Batch:
+    """Many Geolocator steps as one CUDA graph (dg_batch_*): each context's
+    step -- surface into costs[i], argmax, refinement -- is a branch forked
+    from and joined to `stream`; launch() enqueues all of them, fixes()
+    waits and returns one fix per context."""
+
+    def __init__(self, geolocators, costs, refine_spacing_m=0.0, refine_window_m=0.0, stream=None):
+        import torch
+        self.gs = list(geolocators)
+        self.costs = list(costs)
+        if len(self.gs) != len(self.costs) or not self.gs:
+            raise ValueError("one cost tensor per geolocator")
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.gs[0].device)
+        n = len(self.gs)
+        ctxs = (C.c_void_p * n)(*[g.ctx for g in self.gs])
+        ptrs = (C.c_void_p * n)(*[c.data_ptr() for c in self.costs])
+        out = C.c_void_p()
+        with torch.cuda.device(self.gs[0].device):
+            st = lib().dg_batch_capture(ctxs, n, ptrs, float(refine_spacing_m), float(refine_window_m),
+                                        C.c_void_p(self.stream.cuda_stream), C.byref(out))
+        _check(st, None)
+        self.handle = out
+
+    def launch(self):
+        _check(lib().dg_batch_launch(self.handle), None)
+
+    def fixes(self):
+        n = len(self.gs)
+        arr = (dg_fix * n)()
+        _check(lib().dg_batch_fixes(self.handle, arr), None)
+        return [arr[i].as_dict() for i in range(n)]
+
+    def launch_count(self):
+        return int(lib().dg_batch_launch_count(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().dg_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def dg_detect(ctx, cost_ptr, threshold, relative=False, radius=3, max_peaks=16):
@@ -362,6 +423,23 @@ class Geolocator:
         if cost.dtype != self.dtype or not cost.is_cuda:
             raise ValueError("cost must be a CUDA tensor of the context's precision")
         return dg_argmax_refine(self.ctx, cost.data_ptr(), refine_spacing_m, window_m).as_dict()
+
+    # -- whole steps as CUDA graphs (the context needs a non-default stream)
+    def graph_capture(self, cost, refine_spacing_m=0.0, refine_window_m=0.0):
+        if cost.dtype != self.dtype or not cost.is_cuda or cost.numel() != self.nrows * self.nlon:
+            raise ValueError("cost must be a CUDA tensor of the context's precision and grid size")
+        self._keep["graph_cost"] = cost
+        with self.torch.cuda.device(self.device):
+            _check(lib().dg_graph_capture(self.ctx, C.c_void_p(cost.data_ptr()), float(refine_spacing_m),
+                                          float(refine_window_m)), self.ctx)
+
+    def graph_launch(self):
+        _check(lib().dg_graph_launch(self.ctx), self.ctx)
+
+    def graph_fix(self):
+        f = dg_fix()
+        _check(lib().dg_graph_fix(self.ctx, C.byref(f)), self.ctx)
+        return f.as_dict()
 
     def detect(self, cost, threshold, relative=False, radius=3, max_peaks=16):
         if cost.dtype != self.dtype or not cost.is_cuda:

@@ -1,0 +1,128 @@
+"""Whole steps replayed as CUDA graphs (dg_graph_*) and many uneven
+captures as one graph (dg_batch_*): the fixes equal those of the
+synchronising calls (dg_cost_surface + dg_argmax_refine) field for field,
+on the same inputs, for both evaluations of Eq. 11."""
+import numpy as np
+import pytest
+
+import sim
+from gpu_common import package, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+REFINE = (10.0, 200.0)
+
+
+def _geo(scene, stream, **opts):
+    torch = torch_cuda()
+    P = package()
+    g = P.Geolocator(scene.grid, scene.ephem, scene.fs_hz, scene.fc_hz, stream=stream, **opts)
+    g.load_captures(scene.fmt, torch.from_numpy(scene.y1).cuda(), torch.from_numpy(scene.y2).cuda())
+    return g
+
+
+def _reference_fix(g, refine=REFINE):
+    with g.torch.cuda.stream(g.stream):
+        c = g.cost_surface()
+        return c, g.argmax_refine(c, *refine)
+
+
+def _scene(seed, **kw):
+    args = dict(seed=seed, fs_hz=12.5e6, n_samples=20000, k_steps=4, fmt="ci16", waveform="chirp", snr_db=-5.0,
+                grid_n=(121, 131), grid_spacing_m=200.0)
+    args.update(kw)
+    return sim.make_scene(**args)
+
+
+ALGOS = [dict(), dict(algo="cdft", contract="fp16x3")]
+
+
+@pytest.mark.parametrize("opts", ALGOS, ids=["direct", "cdft"])
+def test_graph_fix_equals_synchronous_step(opts):
+    torch = torch_cuda()
+    s = _scene(31)
+    stream = torch.cuda.Stream()
+    g = _geo(s, stream, **opts)
+    ref_cost, ref = _reference_fix(g)
+    cost = torch.empty_like(ref_cost)
+    g.graph_capture(cost, *REFINE)
+    for _ in range(3):
+        g.graph_launch()
+    fix = g.graph_fix()
+    assert fix == ref
+    stream.synchronize()
+    assert torch.equal(cost, ref_cost)
+    g.close()
+
+
+@pytest.mark.parametrize("opts", ALGOS, ids=["direct", "cdft"])
+def test_graph_replays_reloaded_captures(opts):
+    """New captures of the same formats and lengths feed the captured graph;
+    its fix equals the synchronising step on the new data."""
+    torch = torch_cuda()
+    a, b = _scene(32), _scene(33)
+    stream = torch.cuda.Stream()
+    g = _geo(a, stream, **opts)
+    cost = torch.empty((g.nrows, g.nlon), dtype=g.dtype, device=g.device)
+    g.graph_capture(cost, *REFINE)
+    g.load_captures(b.fmt, torch.from_numpy(b.y1).cuda(), torch.from_numpy(b.y2).cuda())
+    g.graph_launch()
+    fix_b = g.graph_fix()
+    _, ref_b = _reference_fix(g)
+    assert fix_b == ref_b
+    g.close()
+
+
+def test_graph_state_errors():
+    torch = torch_cuda()
+    P = package()
+    s = _scene(34, k_steps=2)
+    stream = torch.cuda.Stream()
+    g = _geo(s, stream)
+    with pytest.raises(P.DGError):
+        g.graph_launch()  # nothing captured yet
+    cost = torch.empty((g.nrows, g.nlon), dtype=g.dtype, device=g.device)
+    g.graph_capture(cost)
+    g.graph_launch()
+    assert g.graph_fix()["refine_n"] == 0
+    # a different length changes the captured buffers' shape: refused
+    g.load_capture(0, s.fmt, torch.from_numpy(s.y1[0][:15000].copy()).cuda(),
+                   torch.from_numpy(s.y2[0][:15000].copy()).cuda())
+    with pytest.raises(P.DGError) as e:
+        g.graph_launch()
+    assert e.value.status == P.DG_ESTATE
+    g.close()
+    # a context on the default stream cannot be captured
+    d = _geo(s, None)
+    with pytest.raises(P.DGError) as e:
+        d.graph_capture(torch.empty((d.nrows, d.nlon), dtype=d.dtype, device=d.device))
+    assert e.value.status == P.DG_EUNSUPPORTED
+    d.close()
+
+
+def test_batch_of_uneven_captures():
+    """Six independent problems with different grids, snapshot counts,
+    lengths, formats and algorithms in one graph: every fix equals its own
+    synchronising step."""
+    torch = torch_cuda()
+    P = package()
+    rng = np.random.default_rng(5)
+    gs, costs, refs = [], [], []
+    for i in range(6):
+        fmt = ["ci16", "ci8", "c64"][i % 3]
+        s = _scene(40 + i, fmt=fmt, k_steps=int(rng.integers(1, 5)), n_samples=int(rng.choice([4096, 9000, 16384])),
+                   grid_n=(int(rng.integers(31, 90)) | 1, int(rng.integers(31, 90)) | 1),
+                   grid_spacing_m=float(rng.uniform(100, 400)), waveform=["chirp", "noise"][i % 2])
+        g = _geo(s, torch.cuda.Stream(), **ALGOS[i % 2])
+        _, ref = _reference_fix(g)
+        gs.append(g)
+        refs.append(ref)
+        costs.append(torch.empty((g.nrows, g.nlon), dtype=g.dtype, device=g.device))
+    b = P.Batch(gs, costs, *REFINE)
+    assert b.launch_count() > 6
+    for _ in range(2):
+        b.launch()
+    assert b.fixes() == refs
+    b.close()
+    for g in gs:
+        g.close()
