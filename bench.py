@@ -452,6 +452,130 @@ def direct_reference(scene, local_rank, stream, steps=3, warmup=1):
                          "unit": "TFLOP/s", "frac": ach / peak}}
 
 
+# ------------------------------------------------------- many uneven captures
+BATCH_CAPTURES = 64
+
+
+def batch_scenes(seed, n=BATCH_CAPTURES):
+    """Seeded stand-in for a stream of uneven captures: per capture K in
+    5..20 snapshots, N = 2^e samples with e in 13..16, an odd grid side in
+    129..513 at 50..500 m, a tone, chirp or noise emitter at -25..0 dB,
+    complex int16 at 12.5 MHz."""
+    import sim
+
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        side = int(rng.integers(64, 257)) * 2 + 1
+        out.append(sim.make_scene(seed=int(rng.integers(1 << 30)), fs_hz=12.5e6,
+                                  n_samples=1 << int(rng.integers(13, 17)), k_steps=int(rng.integers(5, 21)),
+                                  fmt="ci16", waveform=["tone", "chirp", "noise"][int(rng.integers(3))],
+                                  snr_db=float(rng.uniform(-25.0, 0.0)), grid_n=side,
+                                  grid_spacing_m=float(rng.uniform(50.0, 500.0)), bw_hz=2e6))
+    return out
+
+
+def run_batch(a, rank, world, local_rank):
+    """All captures' steps as one CUDA graph (dg_batch_*), against the same
+    steps issued one after the other through the synchronising calls."""
+    import torch
+
+    import paper_2508_06672_gb300 as P
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    scenes = batch_scenes(1000 + rank)
+    units = sum(s.G * s.k_steps * s.n_samples for s in scenes)
+    gs, costs, hosts = [], [], []
+    for sc in scenes:
+        st = torch.cuda.Stream(dev)
+        g = P.Geolocator(sc.grid, sc.ephem, sc.fs_hz, sc.fc_hz, algo="cdft", contract=a.contract, stream=st,
+                         device=local_rank, scratch_mib=256)
+        y1, y2 = torch.from_numpy(sc.y1).pin_memory(), torch.from_numpy(sc.y2).pin_memory()
+        with torch.cuda.stream(st):
+            g.load_captures(sc.fmt, y1, y2)
+            costs.append(torch.empty((g.nrows, g.nlon), dtype=torch.float32, device=dev))
+        gs.append(g)
+        hosts.append((sc.fmt, y1, y2))
+    torch.cuda.synchronize(dev)
+    bstream = torch.cuda.Stream(dev)
+    batch = P.Batch(gs, costs, REFINE_SPACING_M, REFINE_WINDOW_M, stream=bstream)
+    with torch.cuda.stream(bstream):
+        flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    for _ in range(a.warmup):
+        batch.launch()
+        batch.fixes()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    clk = ClockSampler(_smi_id(local_rank))
+    torch.cuda.synchronize(dev)
+    with clk:
+        for i in range(a.steps):
+            with torch.cuda.stream(bstream):
+                flush.zero_()
+                ev[i][0].record(bstream)
+            batch.launch()
+            ev[i][1].record(bstream)
+            batch.fixes()
+    dev_ms = [x.elapsed_time(y) for x, y in ev]
+    # the same steps, one context after the other, synchronising calls
+    seq_ms = []
+    for _ in range(max(1, min(a.steps, 3))):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for g, c in zip(gs, costs):
+            with torch.cuda.stream(g.stream):
+                g.cost_surface(c)
+                g.argmax_refine(c, REFINE_SPACING_M, REFINE_WINDOW_M)
+        torch.cuda.synchronize(dev)
+        seq_ms.append(1e3 * (time.perf_counter() - t0))
+    # end to end: pinned host captures in, every fix out, one graph launch
+    e2e_ms = []
+    h2d = sum(y1.numel() * y1.element_size() + y2.numel() * y2.element_size() for _, y1, y2 in hosts)
+    for _ in range(max(1, min(a.steps, 3))):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for g, (fmt, y1, y2) in zip(gs, hosts):
+            with torch.cuda.stream(g.stream):
+                g.load_captures(fmt, y1, y2)
+        batch.launch()
+        batch.fixes()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    nprod = 3 if a.contract.endswith("x3") else 1
+    step_s = statistics.median(dev_ms) / 1e3
+    # issued tensor flops: 512 x chunk per (lag, chunk) row of every context
+    flops = sum(nprod * 512 * g.cdft_work()[0] * g.cdft_chunks()[1] for g in gs) if a.contract != "fp32" else 0
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": units / step_s, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batch: {len(scenes)} uneven captures (K 5-20, N 2^13-2^16, grids 129-513^2 "
+                                   f"at 50-500 m, tone/chirp/noise, ci16, fs 12.5 MHz), one CUDA graph per step",
+                       "captures": len(scenes), "cand_samples_per_step": units, "algo": "cdft",
+                       "contract": a.contract, "refine": f"{REFINE_SPACING_M:g} m spacing, +-{REFINE_WINDOW_M:g} m",
+                       "l2": "flushed between timed steps (256 MB write inside the batch stream, before the start "
+                             "event)", "seed": 1000 + rank},
+            "e2e": {"value": units / (statistics.median(e2e_ms) / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": len(scenes) * 84},
+            "gpu_launches": batch.launch_count() * a.steps,
+            "roofline": {"bound": "tensor", "achieved": flops / step_s / 1e12, "peak": tensor_peak(a.contract),
+                         "unit": "TFLOP/s", "frac": flops / step_s / 1e12 / tensor_peak(a.contract),
+                         "traffic": None,
+                         "kernel": "k_cdft_contract_tc (issued tensor flops over the whole step: a lower bound)",
+                         "peak_basis": PEAK_BASIS_TENSOR},
+            "sequential": {"ms_per_step": statistics.median(seq_ms),
+                           "value": units / (statistics.median(seq_ms) / 1e3),
+                           "note": "the same steps issued one context after the other (dg_cost_surface + "
+                                   "dg_argmax_refine, host synchronisation per step)"},
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    batch.close()
+    for g in gs:
+        g.close()
+
+
 def _smi_id(local_rank):
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     if vis:
@@ -467,7 +591,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["dg", "reference"], default="dg")
-    ap.add_argument("--workload", choices=["mid", "tiny", "large"], default="mid")
+    ap.add_argument("--workload", choices=["mid", "tiny", "large", "batch"], default="mid")
     ap.add_argument("--algo", choices=["direct", "cdft"], default="cdft")
     ap.add_argument("--chunk", type=int, default=0, help="CDFT samples per chunk; 0 = automatic")
     ap.add_argument("--contract", choices=["fp32", "bf16", "fp16", "bf16x3", "fp16x3"], default="fp16x3")
@@ -491,7 +615,10 @@ def main():
 
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    run_dg(a, rank, world, local_rank)
+    if a.workload == "batch":
+        run_batch(a, rank, world, local_rank)
+    else:
+        run_dg(a, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist
 

@@ -126,6 +126,10 @@ typedef struct {
     int32_t bins;    /* CDFT: Doppler bins per lag; 0 = 64 (the only value)   */
     int32_t contract;/* CDFT: DG_CONTRACT_*                                   */
     int32_t tiles;   /* CDFT tensor-core tile shape: DG_TILES_*               */
+    int32_t scratch_mib; /* CDFT: target for the scratch of one batch of
+                        snapshots (per-candidate arrays and per-lag DFTs),
+                        MiB; 0 = 12288. Fewer snapshots per batch below it
+                        (at least one); many contexts sharing a GPU lower it */
 } dg_options;
 
 typedef struct dg_ctx dg_ctx;
@@ -243,7 +247,8 @@ dg_status dg_graph_fix(dg_ctx *ctx, dg_fix *out);
  * non-default stream) is a branch forked from and joined to `stream`, so
  * independent steps run concurrently on the GPU. costs[i] is context i's
  * surface (device). dg_batch_capture runs each step once uncaptured first.
- * dg_batch_launch enqueues all n steps on `stream`; dg_batch_fixes waits
+ * dg_batch_launch enqueues all n steps on `stream`, after the work queued
+ * on each context's stream so far (capture loads); dg_batch_fixes waits
  * for it and writes n fixes (host); a context whose step failed gets
  * index = -1 and the first failure is returned. A context must not be used
  * by other calls while a launch of its batch is in flight. */
@@ -254,6 +259,29 @@ dg_status dg_batch_launch(dg_batch *batch);
 dg_status dg_batch_fixes(dg_batch *batch, dg_fix *out);
 int64_t dg_batch_launch_count(const dg_batch *batch); /* kernels per launch */
 dg_status dg_batch_destroy(dg_batch *batch);
+
+/* Autotuning of the CDFT launch shape (no counterpart in the paper; it is
+ * the successor of the paper's batch-size sweep, Sec. V-B). For every chunk
+ * length in {256, 512, 1024} that the bin-spacing bound admits for this
+ * grid and these snapshots, and for tensor-core contractions both tile
+ * shapes (DG_TILES_ROWS, DG_TILES_LAGS), it times dg_cost_surface into cost
+ * (device, the context's precision; its contents are overwritten) with CUDA
+ * events on the context's stream: one untimed run, then reps >= 1 timed runs,
+ * keeping the median. The fastest shape is written into the context's
+ * options (chunk, tiles) and reported in *out. Every candidate meets the
+ * same interpolation bound, so the choice changes speed, not the error
+ * class. Results are cached per process by grid size, snapshot count,
+ * lengths and formats, sampling rate and contraction: a cached shape is
+ * applied without timing (out->cached = 1). Synchronises. DG_EUNSUPPORTED
+ * for DG_ALGO_DIRECT (its tile shape is fixed). */
+typedef struct {
+    int32_t chunk;    /* samples per chunk chosen                             */
+    int32_t tiles;    /* DG_TILES_* chosen                                    */
+    double ms;        /* its median surface time (0 when cached)              */
+    int32_t tried;    /* shapes timed                                         */
+    int32_t cached;   /* 1: taken from the process-wide cache                 */
+} dg_tuning;
+dg_status dg_autotune(dg_ctx *ctx, void *cost, int32_t reps, dg_tuning *out);
 
 /* Wait for the context's stream and report any latched kernel error. */
 dg_status dg_sync(dg_ctx *ctx);

@@ -11,6 +11,8 @@
 #include <algorithm>
 #include <climits>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -318,8 +320,6 @@ dg_status grow(dg_ctx *c, P **p, size_t n)
     return DG_OK;
 }
 
-// Budget for the per-(candidate, snapshot) arrays of one CDFT batch.
-constexpr size_t kCdftBatchBytes = (size_t)3 << 30;
 
 // ---------------------------------------------------------------------------
 // Host-side planning for the chunked-DFT surface. Nothing here reads device
@@ -427,7 +427,19 @@ static dg_status cdft_layout(dg_ctx *c, const GridDev &gd, int64_t G, CdftLayout
     L.diam = diam;
     L.bbase = old_bb;
     L.gbase = old_gb;
-    const int s_max = (int)std::max<int64_t>(1, std::min<int64_t>(c->K, (int64_t)(kCdftBatchBytes / (16 * (size_t)G))));
+    // snapshots per batch: per-candidate arrays (16 B per candidate) and the
+    // per-lag DFTs (lag slots x chunks x 512 B, chunks at the longest
+    // automatic chunk unless one is fixed) within the scratch target
+    const double budget = (double)(c->opt.scratch_mib ? c->opt.scratch_mib : 12288) * 1048576.0;
+    int64_t nmax = 1;
+    int slots_max = 1;
+    for (int k = 0; k < c->K; ++k) {
+        nmax = std::max<int64_t>(nmax, c->steps[k].n);
+        slots_max = std::max(slots_max, lag_slots(c->eph_host[k], c->fs, diam));
+    }
+    const int m_est = c->opt.chunk ? c->opt.chunk : kCdftAutoMaxChunk;
+    const double per_snap = 16.0 * (double)G + (double)slots_max * (double)((nmax + m_est - 1) / m_est) * 512.0;
+    const int s_max = (int)std::max<int64_t>(1, std::min<int64_t>(c->K, (int64_t)(budget / per_snap)));
     std::vector<int> bb, gb;
     for (int k0 = 0; k0 < c->K;) {
         int S = 1;  // same format, at most s_max snapshots
@@ -461,8 +473,8 @@ static dg_status cdft_layout(dg_ctx *c, const GridDev &gd, int64_t G, CdftLayout
     return DG_OK;
 }
 
-// Chunked-DFT surface. Per batch of snapshots (same IQ format, per-(candidate,
-// snapshot) arrays within kCdftBatchBytes): geometry, plan (sort by lag
+// Chunked-DFT surface. Per batch of snapshots (same IQ format, scratch
+// within the context's target): geometry, plan (sort by lag
 // bucket and bin, bins, tiles), DFT tables, contraction, super-chunks,
 // combine. Then the ordered sum. No host synchronisation.
 dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int64_t G, void *surf, void *out,
@@ -786,6 +798,7 @@ dg_status dg_create(const dg_grid *grid, const dg_ephem *eph, int32_t K, double 
             return fail(nullptr, DG_EINVAL, "unknown tile shape %d", o.tiles);
         if (o.tiles == DG_TILES_LAGS && o.chunk > kLagTileMaxChunk)
             return fail(nullptr, DG_EINVAL, "lag tiles need chunk <= %d", kLagTileMaxChunk);
+        if (o.scratch_mib < 0) return fail(nullptr, DG_EINVAL, "scratch_mib must be >= 0");
     }
     if (o.row0 < 0 || o.row0 >= grid->nlat) return fail(nullptr, DG_EINVAL, "row0 outside the grid");
     if (o.nrows < 0 || o.row0 + o.nrows > grid->nlat) return fail(nullptr, DG_EINVAL, "row shard outside the grid");
@@ -1219,6 +1232,7 @@ dg_status dg_graph_fix(dg_ctx *c, dg_fix *out)
 struct dg_batch {
     std::vector<dg_ctx *> ctxs;
     std::vector<uint64_t> gens;
+    std::vector<cudaEvent_t> ready;  // work queued on each context's stream
     cudaStream_t stream = nullptr;
     cudaGraphExec_t graph = nullptr;
     int64_t launches = 0;
@@ -1255,10 +1269,19 @@ dg_status dg_batch_capture(dg_ctx *const *ctxs, int32_t n, void *const *costs, d
     if (!b) return fail(nullptr, DG_ENOMEM, "host allocation failed");
     b->ctxs.assign(ctxs, ctxs + n);
     for (int i = 0; i < n; ++i) b->gens.push_back(ctxs[i]->steps_gen);
+    b->ready.assign((size_t)n, nullptr);
+    for (auto &e : b->ready)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            for (auto &x : b->ready)
+                if (x) cudaEventDestroy(x);
+            delete b;
+            return fail(nullptr, DG_ECUDA, "event creation failed");
+        }
     b->stream = s;
     dg_status st = capture_steps(ctxs, n, costs, spacing_m, half.data(), s, &b->graph, &b->launches);
     if (st != DG_OK) {
         const std::string m = ctxs[0]->err;
+        for (auto &e : b->ready) cudaEventDestroy(e);
         delete b;
         return fail(nullptr, st, "%s", m.c_str());
     }
@@ -1272,6 +1295,13 @@ dg_status dg_batch_launch(dg_batch *b)
     for (size_t i = 0; i < b->ctxs.size(); ++i)
         if (b->ctxs[i]->steps_gen != b->gens[i] || b->ctxs[i]->steps_dirty)
             return fail(nullptr, DG_ESTATE, "context %zu changed a capture's format, length or buffer", i);
+    // the steps read what was queued on the contexts' own streams (capture
+    // loads): order the launch after it
+    for (size_t i = 0; i < b->ctxs.size(); ++i) {
+        cudaError_t e = cudaEventRecord(b->ready[i], b->ctxs[i]->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ready[i], 0);
+        if (e != cudaSuccess) return fail(nullptr, DG_ECUDA, "ordering the launch: %s", cudaGetErrorString(e));
+    }
     const cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
     if (e != cudaSuccess) return fail(nullptr, DG_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
     return DG_OK;
@@ -1303,7 +1333,118 @@ dg_status dg_batch_destroy(dg_batch *b)
 {
     if (!b) return DG_OK;
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (auto &e : b->ready)
+        if (e) cudaEventDestroy(e);
     delete b;
+    return DG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuning of the CDFT launch shape
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_tune_mutex;
+std::map<std::string, std::pair<int, int>> g_tune_cache;
+
+std::string tune_key(const dg_ctx *c)
+{
+    std::string k = std::to_string(c->G) + "/" + std::to_string(c->gd.nlon) + "/" + std::to_string(c->K) + "/" +
+                    std::to_string(c->opt.contract) + "/" + std::to_string(c->opt.acc) + "/" + std::to_string(c->fs);
+    for (const auto &st : c->steps) k += "/" + std::to_string(st.n) + ":" + std::to_string(st.fmt);
+    return k;
+}
+}  // namespace
+
+dg_status dg_autotune(dg_ctx *c, void *cost, int32_t reps, dg_tuning *out)
+{
+    if (!c) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    c->err.clear();
+    if (!cost || !out) return fail(c, DG_EINVAL, "cost and out must not be NULL");
+    if (reps < 1 || reps > 100) return fail(c, DG_EINVAL, "reps must be in [1, 100]");
+    if (c->opt.algo != DG_ALGO_CDFT) return fail(c, DG_EUNSUPPORTED, "only the CDFT launch shape is tuned");
+    for (int k = 0; k < c->K; ++k)
+        if (!c->steps[k].loaded) return fail(c, DG_ESTATE, "snapshot %d has not been loaded", k);
+    std::memset(out, 0, sizeof *out);
+    const std::string key = tune_key(c);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            c->opt.chunk = it->second.first;
+            c->opt.tiles = it->second.second;
+            out->chunk = c->opt.chunk;
+            out->tiles = c->opt.tiles;
+            out->cached = 1;
+            return DG_OK;
+        }
+    }
+    // admissible chunks: the automatic rule's bound on the estimated spacing
+    std::vector<double> &span = c->cd.main_span;
+    if (span.size() != (size_t)c->K) {
+        span.assign(c->K, 0.0);
+        for (int k = 0; k < c->K; ++k) span[k] = fdoa_span(c, c->gd, k, 65);
+    }
+    double dmax = 0.0;
+    for (int k = 0; k < c->K; ++k) dmax = std::max(dmax, span[k] * (1.0 + 1e-5) / 63.0);
+    std::vector<int> chunks;
+    for (int m : {256, 512, 1024})
+        if (1.25 * m * dmax <= kCdftAutoMDelta) chunks.push_back(m);
+    if (chunks.empty()) chunks.push_back(auto_chunk(span, 0, c->K));
+    std::vector<int> tiles = {DG_TILES_ROWS};
+    if (c->opt.contract != DG_CONTRACT_FP32) tiles.push_back(DG_TILES_LAGS);
+    const dg_options saved = c->opt;
+    const size_t esz = c->opt.prec == DG_PREC_FP64 ? 8 : 4;
+    dg_status st = ensure(c, &c->surf, &c->surf_bytes, esz * (size_t)c->G * c->K);
+    if (st != DG_OK) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(c, cudaEventCreate(&e0));
+    CK(c, cudaEventCreate(&e1));
+    double best = 1e300;
+    int best_m = chunks[0], best_t = tiles[0];
+    const int timing = c->opt.timing;
+    c->opt.timing = 0;
+    for (int m : chunks)
+        for (int t : tiles) {
+            if (t == DG_TILES_LAGS && m > kLagTileMaxChunk) continue;
+            c->opt.chunk = m;
+            c->opt.tiles = t;
+            std::vector<float> ms;
+            for (int r = 0; r <= reps && st == DG_OK; ++r) {
+                if (r > 0 && cudaEventRecord(e0, c->stream) != cudaSuccess) st = DG_ECUDA;
+                if (st == DG_OK) st = run_surface(c, c->gd, c->xyz, c->G, c->surf, cost, false);
+                if (st == DG_OK && r > 0 && cudaEventRecord(e1, c->stream) != cudaSuccess) st = DG_ECUDA;
+                if (st == DG_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = DG_ECUDA;
+                if (st == DG_OK) st = check_latched(c);
+                float x = 0.f;
+                if (st == DG_OK && r > 0) {
+                    cudaEventElapsedTime(&x, e0, e1);
+                    ms.push_back(x);
+                }
+            }
+            if (st != DG_OK) break;
+            std::sort(ms.begin(), ms.end());
+            const double med = ms[ms.size() / 2];
+            ++out->tried;
+            if (med < best) {
+                best = med;
+                best_m = m;
+                best_t = t;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->opt = saved;
+    if (st != DG_OK) {
+        if (c->err.empty()) fail(c, st, "a timed surface failed");
+        return st;
+    }
+    c->opt.chunk = best_m;
+    c->opt.tiles = best_t;
+    out->chunk = best_m;
+    out->tiles = best_t;
+    out->ms = best;
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    g_tune_cache[key] = {best_m, best_t};
     return DG_OK;
 }
 

@@ -19,7 +19,8 @@ import threading
 import numpy as np
 
 __all__ = [
-    "DGError", "dg_grid", "dg_ephem", "dg_options", "dg_fix", "dg_peak", "lib", "library_path", "Batch",
+    "DGError", "dg_grid", "dg_ephem", "dg_options", "dg_fix", "dg_peak", "dg_tuning", "lib", "library_path",
+    "Batch",
     "dg_options_default", "dg_create", "dg_load_capture", "dg_cost_surface", "dg_argmax_refine",
     "dg_sync", "dg_destroy", "dg_last_error", "dg_grid_ecef", "dg_step_geometry", "dg_kernel_time",
     "dg_reset_counters", "dg_launch_count", "dg_abi_version", "Geolocator",
@@ -59,7 +60,7 @@ EXPORTED_SYMBOLS = [
     "dg_reset_counters", "dg_launch_count", "dg_abi_version", "dg_cost_surface_noalloc",
     "dg_noalloc_last_error", "dg_cdft_work", "dg_detect", "dg_cdft_chunks",
     "dg_graph_capture", "dg_graph_launch", "dg_graph_fix", "dg_batch_capture", "dg_batch_launch",
-    "dg_batch_fixes", "dg_batch_launch_count", "dg_batch_destroy",
+    "dg_batch_fixes", "dg_batch_launch_count", "dg_batch_destroy", "dg_autotune",
 ]
 DG_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
@@ -89,7 +90,15 @@ class dg_options(C.Structure):
     _fields_ = [("delay", C.c_int32), ("acc", C.c_int32), ("prec", C.c_int32), ("algo", C.c_int32),
                 ("row0", C.c_int32), ("nrows", C.c_int32), ("timing", C.c_int32),
                 ("chunk", C.c_int32), ("bins", C.c_int32), ("contract", C.c_int32),
-                ("tiles", C.c_int32)]
+                ("tiles", C.c_int32), ("scratch_mib", C.c_int32)]
+
+
+class dg_tuning(C.Structure):
+    _fields_ = [("chunk", C.c_int32), ("tiles", C.c_int32), ("ms", C.c_double), ("tried", C.c_int32),
+                ("cached", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class dg_peak(C.Structure):
@@ -166,6 +175,8 @@ def lib():
             for f in ("dg_graph_capture", "dg_graph_launch", "dg_graph_fix", "dg_batch_capture", "dg_batch_launch",
                       "dg_batch_fixes", "dg_batch_destroy"):
                 getattr(L, f).restype = C.c_int
+            L.dg_autotune.argtypes = [vp, vp, i32, C.POINTER(dg_tuning)]
+            L.dg_autotune.restype = C.c_int
             L.dg_cdft_chunks.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
             L.dg_cdft_chunks.restype = C.c_int
             L.dg_cdft_work.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
@@ -354,7 +365,7 @@ class Geolocator:
 
     def __init__(self, grid, ephem, fs_hz, fc_hz, *, delay="integer", acc="power", prec="fp32",
                  algo="direct", row0=0, nrows=0, timing=False, stream=None, device=None,
-                 chunk=0, bins=0, contract="fp32", tiles="auto"):
+                 chunk=0, bins=0, contract="fp32", tiles="auto", scratch_mib=0):
         import torch
 
         self.torch = torch
@@ -370,6 +381,7 @@ class Geolocator:
         self.opt.row0, self.opt.nrows, self.opt.timing = int(row0), int(nrows), int(bool(timing))
         self.opt.chunk, self.opt.bins, self.opt.contract = int(chunk), int(bins), _CONTRACT[contract]
         self.opt.tiles = _TILES[tiles]
+        self.opt.scratch_mib = int(scratch_mib)
         self.nrows = int(nrows) if nrows else int(grid["nlat"]) - int(row0)
         self.nlon = int(grid["nlon"])
         self.dtype = torch.float64 if prec == "fp64" else torch.float32
@@ -423,6 +435,14 @@ class Geolocator:
         if cost.dtype != self.dtype or not cost.is_cuda:
             raise ValueError("cost must be a CUDA tensor of the context's precision")
         return dg_argmax_refine(self.ctx, cost.data_ptr(), refine_spacing_m, window_m).as_dict()
+
+    def autotune(self, cost=None, reps=3):
+        """Time the admissible CDFT launch shapes and keep the fastest."""
+        if cost is None:
+            cost = self.torch.empty((self.nrows, self.nlon), dtype=self.dtype, device=self.device)
+        t = dg_tuning()
+        _check(lib().dg_autotune(self.ctx, C.c_void_p(cost.data_ptr()), int(reps), C.byref(t)), self.ctx)
+        return t.as_dict()
 
     # -- whole steps as CUDA graphs (the context needs a non-default stream)
     def graph_capture(self, cost, refine_spacing_m=0.0, refine_window_m=0.0):

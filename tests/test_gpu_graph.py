@@ -126,3 +126,31 @@ def test_batch_of_uneven_captures():
     b.close()
     for g in gs:
         g.close()
+
+
+@pytest.mark.parametrize("contract", ["fp32", "fp16x3"])
+def test_autotune_picks_an_admissible_shape(contract):
+    """The tuner times the admissible (chunk, tile) shapes, keeps the fastest
+    in the context, and caches it; the tuned context's surface equals one
+    created with that shape explicitly, bit for bit."""
+    torch = torch_cuda()
+    s = _scene(50, k_steps=3, n_samples=30000)
+    g = _geo(s, torch.cuda.Stream(), algo="cdft", contract=contract)
+    t = g.autotune(reps=2)
+    assert t["chunk"] in (256, 512, 1024)
+    assert t["tiles"] in (1, 2) and (contract != "fp32" or t["tiles"] == 1)
+    assert t["cached"] == 0 and t["tried"] >= 3 and t["ms"] > 0
+    with torch.cuda.stream(g.stream):
+        tuned = g.cost_surface().clone()
+    tiles = {1: "rows", 2: "lags"}[t["tiles"]]
+    h = _geo(s, torch.cuda.Stream(), algo="cdft", contract=contract, chunk=t["chunk"], tiles=tiles)
+    with torch.cuda.stream(h.stream):
+        explicit = h.cost_surface().clone()
+    torch.cuda.synchronize()
+    assert torch.equal(tuned, explicit)
+    # a second context of the same shape takes the cached choice
+    u = _geo(s, torch.cuda.Stream(), algo="cdft", contract=contract)
+    t2 = u.autotune()
+    assert t2["cached"] == 1 and (t2["chunk"], t2["tiles"]) == (t["chunk"], t["tiles"])
+    for x in (g, h, u):
+        x.close()
