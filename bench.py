@@ -400,6 +400,8 @@ def run_dg(a, rank, world, local_rank):
                          "achieved_basis": roof_basis + " / CUDA-event time of the launches",
                          "launches": corr_launches, "ms_per_launch": 1e3 * corr_s / max(1, corr_launches)},
             "kernel_ms_per_step": {n: v[0] / a.steps for n, v in kt.items() if v[1]},
+            "cdft_work": ({"lag_chunk_rows": bucket_chunks, "candidate_superchunks": cand_chunks}
+                          if a.algo == "cdft" else None),
             "kernels": kernels,
             "clocks": clocks,
             "fix": {"i": gi, "j": gj, "emitter_cell": list(centre),
