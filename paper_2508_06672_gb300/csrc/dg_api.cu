@@ -209,7 +209,7 @@ dg_status check_latched(dg_ctx *c)
         *c->err_h = 0;
         cudaMemsetAsync(c->err_d, 0, sizeof(unsigned), c->stream);
         if (e & ERR_TIMEOUT)
-            return fail(c, DG_ETIMEOUT, "a tensor-core pipeline wait ran out of its iteration limit; the "
+            return fail(c, DG_ETIMEOUT, "a tensor-core pipeline wait ran out of its time budget; the "
                         "affected surface values are not valid");
         if (e & ERR_NU_RANGE)
             return fail(c, DG_EUNSUPPORTED,
@@ -1401,8 +1401,7 @@ dg_status dg_autotune(dg_ctx *c, void *cost, int32_t reps, dg_tuning *out)
     CK(c, cudaEventCreate(&e1));
     double best = 1e300;
     int best_m = chunks[0], best_t = tiles[0];
-    const int timing = c->opt.timing;
-    c->opt.timing = 0;
+    c->opt.timing = 0;  // restored with the saved options
     for (int m : chunks)
         for (int t : tiles) {
             if (t == DG_TILES_LAGS && m > kLagTileMaxChunk) continue;

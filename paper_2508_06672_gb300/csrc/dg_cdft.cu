@@ -48,15 +48,6 @@ __device__ __forceinline__ float unfkey(unsigned k)
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
-// frac(nu * x) for an integer-valued x < 2^24, to ~1e-7 cycles: the product
-// is split exactly into p + e with an FMA, and p - floor(p) is exact.
-__device__ __forceinline__ float frac_mul(float nu, float x)
-{
-    const float p = nu * x;
-    const float e = fmaf(nu, x, -p);
-    return (p - floorf(p)) + e;
-}
-
 // Step of the batch that owns global bucket b (bbase[s] <= b < bbase[s+1]).
 __device__ __forceinline__ int step_of(const int *base, int S, int b)
 {
@@ -290,7 +281,11 @@ __global__ void __launch_bounds__(256) k_cdft_subhist(CdftBatch a)
         const int b = bb + l - lmin;
         float t;
         const int q0 = bin_of(a.candNu[(size_t)s * a.G + p], a.nubase[s], delta, t);
-        atomicAdd(a.subcnt + (size_t)b * 64 + q0, 1);
+        // neighbouring candidates share their (bucket, bin): one atomic per
+        // distinct key in the warp
+        const int key = b * 64 + q0;
+        const unsigned peers = __match_any_sync(__activemask(), key);
+        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(a.subcnt + key, __popc(peers));
     }
 }
 
@@ -324,7 +319,15 @@ __global__ void __launch_bounds__(256) k_cdft_scatter(CdftBatch a)
         const int b = bb + l - lmin;
         float t;
         const int q0 = bin_of(a.candNu[(size_t)s * a.G + p], a.nubase[s], delta, t);
-        const int pos = a.offs[b] + atomicAdd(a.subcnt + (size_t)b * 64 + q0, 1);
+        // one atomic per distinct (bucket, bin) in the warp; the peers take
+        // consecutive positions in lane order
+        const int key = b * 64 + q0;
+        const unsigned peers = __match_any_sync(__activemask(), key);
+        const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(a.subcnt + key, __popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        const int pos = a.offs[b] + base + __popc(peers & ((1u << lane) - 1u));
         a.order[(size_t)s * a.G + pos] = (int)p;
         a.nuS[(size_t)s * a.G + pos] = a.candNu[(size_t)s * a.G + p];
     }
@@ -341,12 +344,11 @@ constexpr int kCtSub = 32;     // samples per shared-memory pass
 __global__ void __launch_bounds__(256) k_cdft_vtable(float2 *V, const float *nubase, const float *delta, int M, int S)
 {
     const int s = blockIdx.y;
-    const double b0 = (double)nubase[s], d = (double)delta[s];
+    const float b0 = nubase[s], d = delta[s];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M * 64; i += gridDim.x * blockDim.x) {
         const int m = i >> 6, q = i & 63;
-        const double ph = (b0 + d * (double)q) * (double)m;
-        float sn, cs;
-        sincospif(2.0f * (float)(ph - floor(ph)), &sn, &cs);
+        float sn, cs;  // bin frequency in FP32 as the combine forms it; exact product split
+        sincospif(2.0f * frac_mul(fmaf((float)q, d, b0), (float)m), &sn, &cs);
         V[(size_t)s * M * 64 + i] = make_float2(cs, sn);
     }
 }
@@ -528,7 +530,7 @@ __global__ void __launch_bounds__(kCdftCombineThreads) k_cdft_combine(CdftBatch 
 }
 
 // ---------------------------------------------------------------------------
-// tiles: one thread, after the scan. Per snapshot of the batch: its lag
+// tiles: one warp, after the scan. Per snapshot of the batch: its lag
 // buckets (from the lag range), the tensor-core tile layout (128 lags x one
 // chunk unless padding the lags to blocks of 128 more than doubles the tile
 // count, or the chunk exceeds kLagTileMaxChunk), the tile offsets, and the
@@ -538,36 +540,56 @@ __global__ void __launch_bounds__(kCdftCombineThreads) k_cdft_combine(CdftBatch 
 // ---------------------------------------------------------------------------
 __global__ void k_cdft_tiles(CdftBatch a)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int tiles = 0;
+    // one warp; lane l plans snapshots l, l + 32, ...; the tile offsets are a
+    // warp prefix sum
+    const int lane = threadIdx.x;
+    if (blockIdx.x != 0 || lane >= 32) return;
+    int running = 0;
     unsigned long long rows = 0, cands = 0;
-    for (int s = 0; s < a.S; ++s) {
-        const int lo = a.lr[2 * s], hi = a.lr[2 * s + 1];
-        int NB = hi >= lo ? hi - lo + 1 : 0;
-        if (NB > a.bbase[s + 1] - a.bbase[s]) NB = 0;
-        const int n = a.sd[s].n, M = a.M;
-        const int B = (n + M - 1) / M;
-        const int t_row = (int)(((int64_t)NB * B + 127) / 128), t_lag = B * ((NB + 127) / 128);
-        int lay = 0;
-        if (a.mma && M <= kLagTileMaxChunk)
-            lay = a.tiles_mode == DG_TILES_LAGS || (a.tiles_mode == DG_TILES_AUTO && t_lag <= 2 * t_row);
-        a.layout[s] = lay;
-        a.tbase[s] = tiles;
-        tiles += lay ? t_lag : t_row;
-        int64_t Mc = M;
-        const double d = (double)a.delta[s];
-        while (Mc < n && 2 * Mc <= ((int64_t)1 << 24) && (double)(2 * Mc) * d <= kCdftAutoMDelta) Mc *= 2;
-        a.Mcs[s] = (int)Mc;
-        rows += (unsigned long long)NB * B;
-        cands += (unsigned long long)a.G * ((n + Mc - 1) / Mc);
+    for (int s0 = 0; s0 < a.S; s0 += 32) {
+        const int s = s0 + lane;
+        int tiles = 0;
+        if (s < a.S) {
+            const int lo = a.lr[2 * s], hi = a.lr[2 * s + 1];
+            int NB = hi >= lo ? hi - lo + 1 : 0;
+            if (NB > a.bbase[s + 1] - a.bbase[s]) NB = 0;
+            const int n = a.sd[s].n, M = a.M;
+            const int B = (n + M - 1) / M;
+            const int t_row = (int)(((int64_t)NB * B + 127) / 128), t_lag = B * ((NB + 127) / 128);
+            int lay = 0;
+            if (a.mma && M <= kLagTileMaxChunk)
+                lay = a.tiles_mode == DG_TILES_LAGS || (a.tiles_mode == DG_TILES_AUTO && t_lag <= 2 * t_row);
+            a.layout[s] = lay;
+            tiles = lay ? t_lag : t_row;
+            int64_t Mc = M;
+            const double d = (double)a.delta[s];
+            while (Mc < n && 2 * Mc <= ((int64_t)1 << 24) && (double)(2 * Mc) * d <= kCdftAutoMDelta) Mc *= 2;
+            a.Mcs[s] = (int)Mc;
+            rows += (unsigned long long)NB * B;
+            cands += (unsigned long long)a.G * ((n + Mc - 1) / Mc);
+        }
+        int incl = tiles;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += y;
+        }
+        if (s < a.S) a.tbase[s] = running + incl - tiles;
+        running += __shfl_sync(0xffffffffu, incl, 31);
     }
-    a.tbase[a.S] = tiles;
-    if (a.work) {
-        a.work[0] += rows;
-        a.work[1] += cands;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        rows += __shfl_xor_sync(0xffffffffu, rows, d);
+        cands += __shfl_xor_sync(0xffffffffu, cands, d);
+    }
+    if (lane == 0) {
+        a.tbase[a.S] = running;
+        if (a.work) {
+            a.work[0] += rows;
+            a.work[1] += cands;
+        }
     }
 }
-
 
 // ---------------------------------------------------------------------------
 // host-side launchers

@@ -48,6 +48,7 @@ constexpr int kN = 128;                            // 64 bins x (re, im)
 constexpr int kKS = 32;                            // samples per stage
 constexpr int kBlockBytes = kRows * kKS * 2;       // one 128 x 32 16-bit block
 constexpr uint32_t kWaitLimit = 1u << 24;          // try_wait polls before giving up
+constexpr uint64_t kWaitBudgetNs = 2000000000ull;  // and the clock budget of one wait (2 s)
 
 __device__ __forceinline__ uint32_t blk_off(int row, int k)
 {
@@ -82,8 +83,19 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait on an mbarrier phase: gives up after kWaitBudgetNs of the
+// global timer (checked every 256 polls) or kWaitLimit polls, whichever
+// comes first (try_wait may suspend the thread for a while per poll).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
 {
+    uint64_t t0 = 0;
     for (uint32_t i = 0; i < kWaitLimit; ++i) {
         uint32_t ok;
         asm volatile(
@@ -94,6 +106,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
             : "r"(bar), "r"(parity)
             : "memory");
         if (ok) return true;
+        if ((i & 255) == 255) {
+            const uint64_t now = globaltimer_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > kWaitBudgetNs) return false;
+        }
     }
     return false;
 }
@@ -221,7 +238,7 @@ __global__ void __launch_bounds__(256) k_cdft_btab(const float *nubase, const fl
     const int NJ = M / kKS;
     const size_t per_stage = (size_t)P * 2 * kRows * kKS;  // 16-bit elements
     const size_t per_step = (size_t)NJ * per_stage;
-    const double b0 = (double)nubase[s], d = (double)delta[s];
+    const float b0 = nubase[s], d = delta[s];
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)NJ * 2 * kRows * kKS;
          i += (size_t)gridDim.x * blockDim.x) {
         const int k = (int)(i % kKS);
@@ -229,9 +246,10 @@ __global__ void __launch_bounds__(256) k_cdft_btab(const float *nubase, const fl
         const int blk = (int)((i / (kKS * kRows)) % 2);
         const int j = (int)(i / (2 * kKS * kRows));
         const int m = j * kKS + k, q = n & 63;
-        const double ph = (b0 + d * (double)q) * (double)m;
+        // bin frequency in FP32 as the combine forms it; the phase of
+        // sample m (< 2^24) from the exact product split
         float sn, cs;
-        sincospif(2.0f * (float)(ph - floor(ph)), &sn, &cs);
+        sincospif(2.0f * frac_mul(fmaf((float)q, d, b0), (float)m), &sn, &cs);
         float v;
         if (blk == 0) v = n < 64 ? cs : sn;   // z_re * (V_re | V_im)
         else v = n < 64 ? -sn : cs;           // z_im * (-V_im | V_re)
@@ -424,7 +442,8 @@ template <> struct Raw<DG_IQ_C64> {
 // empty (tcgen05.commit of the MMAs that read the slot). No CTA-wide barrier
 // inside the loop.
 constexpr int kProducerWarps = 8;
-constexpr int kWsThreads = (kProducerWarps + 1) * 32;
+constexpr int kEpilogueWarps = 4;  // one per 32-lane quarter of the accumulator
+constexpr int kWsThreads = (kProducerWarps + 1 + kEpilogueWarps) * 32;
 constexpr int kRing = 3;  // pipeline stages in the ring
 template <int P> __host__ __device__ constexpr int ws_smem_bytes() { return kRing * 2 * (2 * P * kBlockBytes); }
 
@@ -451,13 +470,57 @@ __device__ __forceinline__ int nb_of(const CdftBatch &a, int s)
 //         y2[bM + L0 .. bM + L0 + M + 127) in shared memory once, decoded to
 //         FP32, and the producers read only shared memory.
 // Samples outside [0, N) are zero in both, so the sums run over the overlap.
-// Stage counters run across tiles, so every mbarrier keeps one phase
-// sequence for the CTA's lifetime; one TMEM accumulator is reused, and the
-// epilogue of a tile (tcgen05.ld -> W) completes before the next tile's
-// first MMA (CTA barrier between tiles).
+// Roles: warps 0-7 produce the lag products of each stage into a ring of
+// kRing slots; warp 8 (one thread) streams the DFT operand by bulk copy and
+// issues the MMAs; warps 9-12 drain finished accumulators (tcgen05.ld -> W).
+// Two accumulators of 128 TMEM columns alternate between tiles, so the
+// drain of tile i overlaps the MMAs of tile i + 1. Stage and tile counters
+// run across tiles: every mbarrier keeps one phase sequence for the CTA's
+// lifetime. Every wait is bounded (mbar_wait); a timeout stops all roles,
+// latches ERR_TIMEOUT, and the CTA frees its TMEM after waiting (bounded)
+// for the MMAs it issued.
 template <int P> __host__ __device__ constexpr int tc_smem_bytes()
 {
     return ws_smem_bytes<P>() + (2 * kLagTileMaxChunk + kRows) * (int)sizeof(float2);
+}
+
+// Barrier of the producer warps (named barrier 1) that also ORs a flag over
+// them: every producer gets the same answer, so they leave the tile loop
+// together (no producer is left waiting at a later barrier).
+__device__ __forceinline__ bool producers_sync_or(bool flag)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\t"
+        "setp.ne.u32 pi, %1, 0;\n\t"
+        "barrier.cta.red.or.pred po, 1, %2, pi;\n\t"
+        "selp.u32 %0, 1, 0, po;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)flag), "r"(kProducerWarps * 32)
+        : "memory");
+    return r != 0;
+}
+
+struct TileInfo {
+    int s, ltile, N, Bs, NB, lay, lb, bch, Lmin;
+    StepDesc sd;
+};
+
+__device__ __forceinline__ TileInfo tile_info(const CdftBatch &a, int tile)
+{
+    TileInfo t;
+    t.s = step_of_tile(a.tbase, a.S, tile);
+    t.ltile = tile - a.tbase[t.s];
+    t.sd = a.sd[t.s];
+    t.N = t.sd.n;
+    t.Bs = (t.N + a.M - 1) / a.M;
+    t.NB = nb_of(a, t.s);
+    t.lay = a.layout[t.s];
+    const int NLB = max((t.NB + kRows - 1) / kRows, 1);
+    t.lb = t.lay ? t.ltile % NLB : 0;
+    t.bch = t.lay ? t.ltile / NLB : 0;
+    t.Lmin = a.lr[2 * t.s];
+    return t;
 }
 
 template <int FMT, int DT, int P>
@@ -466,10 +529,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
     constexpr int NS = kRing;
     constexpr int kSt = 2 * P * kBlockBytes;  // bytes of one stage's A (or B) blocks
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t full_a[NS], full_b[NS], empty[NS];
+    __shared__ __align__(8) uint64_t full_a[NS], full_b[NS], empty[NS], acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_abort;
-    __shared__ int s_last_commit;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *sA0 = smem;
@@ -485,61 +547,55 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
             mbar_init(smem_u32(&full_b[i]), 1);
             mbar_init(smem_u32(&empty[i]), 1);
         }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_u32(&acc_full[i]), 1);
+            mbar_init(smem_u32(&acc_empty[i]), kEpilogueWarps);
+        }
         s_abort = 0;
         fence_mbar_init();
         fence_proxy_async_smem();
     }
-    if (warp == 0) tmem_alloc(smem_u32(&tmem_slot), 128);
+    if (warp == 0) tmem_alloc(smem_u32(&tmem_slot), 256);
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
     const uint32_t tmem = tmem_slot;
-    const uint32_t id = idesc<DT>();
 
-    uint32_t g0 = 0;  // global index of this tile's first stage
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, g0 += (uint32_t)NJ) {
-        const int s = step_of_tile(a.tbase, a.S, tile);
-        const int ltile = tile - a.tbase[s];
-        const StepDesc sd = a.sd[s];
-        const int N = sd.n;
-        const int Bs = (N + M - 1) / M;
-        const int NB = nb_of(a, s);
-        const int lay = a.layout[s];
-        const int NLB = (NB + kRows - 1) / kRows;
-        const int lb = lay ? ltile % max(NLB, 1) : 0, bch = lay ? ltile / max(NLB, 1) : 0;
-        const int Lmin = a.lr[2 * s];
-        const unsigned char *bsrc = reinterpret_cast<const unsigned char *>(a.btab) + (size_t)s * NJ * kSt;
-
-        if (warp < kProducerWarps) {
-            const int rin = lane & 7, kg = lane >> 3;
-            const float zs = a.zscale;
-            if (lay) {
-                // ---- stage the tile's capture windows (producers only)
-                const int nb0 = bch * M, L0 = Lmin + lb * kRows;
+    if (warp < kProducerWarps) {
+        // ---------------- producers
+        const int rin = lane & 7, kg = lane >> 3;
+        const float zs = a.zscale;
+        uint32_t g0 = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, g0 += (uint32_t)NJ) {
+            // every producer is done with the previous tile's windows; all
+            // leave together on an abort
+            if (producers_sync_or(s_abort != 0)) break;
+            const TileInfo t = tile_info(a, tile);
+            if (t.lay) {
+                const int nb0 = t.bch * M, L0 = t.Lmin + t.lb * kRows;
                 for (int i = threadIdx.x; i < M; i += kProducerWarps * 32) {
                     const int n = nb0 + i;
-                    const float2 v = n < N ? IQ<FMT>::load(sd.y1, n) : make_float2(0.f, 0.f);
+                    const float2 v = n < t.N ? IQ<FMT>::load(t.sd.y1, n) : make_float2(0.f, 0.f);
                     sy1[i] = make_float2(v.x * zs, v.y * zs);
                 }
                 for (int i = threadIdx.x; i < M + kRows; i += kProducerWarps * 32) {
                     const int n2 = nb0 + L0 + i;
-                    sy2[i] = (n2 >= 0 && n2 < N) ? IQ<FMT>::load(sd.y2, n2) : make_float2(0.f, 0.f);
+                    sy2[i] = (n2 >= 0 && n2 < t.N) ? IQ<FMT>::load(t.sd.y2, n2) : make_float2(0.f, 0.f);
                 }
                 asm volatile("bar.sync 1, %0;" ::"r"(kProducerWarps * 32) : "memory");
             }
-            // rows (row layout): two row sets per warp, 8 rows x 4 sample groups per set
             int pL[2] = {0, 0}, pn0[2] = {0, 0};
             bool pv[2] = {false, false};
-            if (!lay) {
-                const int64_t R = (int64_t)NB * Bs;
+            if (!t.lay) {
+                const int64_t R = (int64_t)t.NB * t.Bs;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const int64_t g = (int64_t)ltile * kRows + 16 * warp + 8 * h + rin;
+                    const int64_t g = (int64_t)t.ltile * kRows + 16 * warp + 8 * h + rin;
                     if (g < R) {
-                        const int bl = (int)(g / Bs);
-                        pn0[h] = (int)(g % Bs) * M + 8 * kg;
-                        pL[h] = Lmin + bl;
-                        pv[h] = a.count[a.bbase[s] + bl] > 0;
+                        const int bl = (int)(g / t.Bs);
+                        pn0[h] = (int)(g % t.Bs) * M + 8 * kg;
+                        pL[h] = t.Lmin + bl;
+                        pv[h] = a.count[a.bbase[t.s] + bl] > 0;
                     }
                 }
             }
@@ -550,7 +606,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                 if (s_abort) break;
                 unsigned char *sA = sA0 + slot * kSt;
                 float2 x[8];
-                if (lay) {
+                if (t.lay) {
                     const int m0 = j * kKS + 8 * kg;
 #pragma unroll
                     for (int u = 0; u < 8; u += 2) {
@@ -563,15 +619,15 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                 for (int h = 0; h < 2; ++h) {
                     const int row = 16 * warp + 8 * h + rin;
                     float2 y[8];
-                    if (lay) {
+                    if (t.lay) {
                         const float2 *py = sy2 + j * kKS + 8 * kg + row;
 #pragma unroll
                         for (int u = 0; u < 8; ++u) y[u] = py[u];
                     } else {
                         Raw<FMT> raw;
                         const int n = pn0[h] + j * kKS;
-                        raw.fetch(sd.y1, sd.y2, n, n + pL[h], N, pv[h]);
-                        raw.decode(sd.y1, sd.y2, N, pv[h], x, y);
+                        raw.fetch(t.sd.y1, t.sd.y2, n, n + pL[h], t.N, pv[h]);
+                        raw.decode(t.sd.y1, t.sd.y2, t.N, pv[h], x, y);
 #pragma unroll
                         for (int u = 0; u < 8; ++u) x[u] = make_float2(x[u].x * zs, x[u].y * zs);
                     }
@@ -608,101 +664,123 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&full_a[slot]));
             }
-        } else if (lane == 0) {
-            // ---- control: bulk copies of B, MMA issue, commits. B of stage
-            // g goes into slot g % NS once the MMAs of stage g - NS are done.
-            s_last_commit = -1;
-            auto load_b = [&](uint32_t g) -> bool {
-                const int slot = (int)(g % NS);
-                if (g >= NS && !mbar_wait(smem_u32(&empty[slot]), ((g / NS) - 1) & 1u)) return false;
-                mbar_expect_tx(smem_u32(&full_b[slot]), kSt);
-                bulk_g2s(smem_u32(sB0 + slot * kSt), bsrc + (size_t)(g - g0) * kSt, kSt, smem_u32(&full_b[slot]));
-                return true;
-            };
-            bool alive = true;
-            for (int t = 0; t < NS && t < NJ && alive; ++t) alive = load_b(g0 + (uint32_t)t);
-            for (int j = 0; j < NJ && alive; ++j) {
-                const uint32_t g = g0 + (uint32_t)j;
-                const int slot = (int)(g % NS);
-                const uint32_t ph = (g / NS) & 1u;
-                if (!mbar_wait(smem_u32(&full_a[slot]), ph) || !mbar_wait(smem_u32(&full_b[slot]), ph) || s_abort) {
+        }
+    } else if (warp == kProducerWarps) {
+        // ---------------- control (one thread): B copies, MMAs, commits
+        if (lane == 0) {
+            const uint32_t id = idesc<DT>();
+            uint32_t g0 = 0;
+            int it = 0;
+            for (int tile = blockIdx.x; tile < ntiles && !s_abort; tile += gridDim.x, g0 += (uint32_t)NJ, ++it) {
+                const int s = step_of_tile(a.tbase, a.S, tile);
+                const unsigned char *bsrc = reinterpret_cast<const unsigned char *>(a.btab) + (size_t)s * NJ * kSt;
+                // B of stage g goes into slot g % NS once the MMAs of stage g - NS are done
+                auto load_b = [&](uint32_t g) -> bool {
+                    const int slot = (int)(g % NS);
+                    if (g >= NS && !mbar_wait(smem_u32(&empty[slot]), ((g / NS) - 1) & 1u)) return false;
+                    mbar_expect_tx(smem_u32(&full_b[slot]), kSt);
+                    bulk_g2s(smem_u32(sB0 + slot * kSt), bsrc + (size_t)(g - g0) * kSt, kSt, smem_u32(&full_b[slot]));
+                    return true;
+                };
+                bool alive = true;
+                for (int t = 0; t < NS && t < NJ && alive; ++t) alive = load_b(g0 + (uint32_t)t);
+                // the accumulator of this tile was drained (tile it - 2)
+                const int acc = it & 1;
+                if (alive && it >= 2 && !mbar_wait(smem_u32(&acc_empty[acc]), ((uint32_t)(it / 2) - 1) & 1u))
                     alive = false;
-                    break;
-                }
                 tc_after_sync();
-                const unsigned char *sA = sA0 + slot * kSt;
-                const unsigned char *sB = sB0 + slot * kSt;
-                constexpr int NPROD = P == 2 ? 3 : 1;
+                const uint32_t dtm = tmem + (uint32_t)(128 * acc);
+                for (int j = 0; j < NJ && alive; ++j) {
+                    const uint32_t g = g0 + (uint32_t)j;
+                    const int slot = (int)(g % NS);
+                    const uint32_t ph = (g / NS) & 1u;
+                    if (!mbar_wait(smem_u32(&full_a[slot]), ph) || !mbar_wait(smem_u32(&full_b[slot]), ph) ||
+                        s_abort) {
+                        alive = false;
+                        break;
+                    }
+                    tc_after_sync();
+                    const unsigned char *sA = sA0 + slot * kSt;
+                    const unsigned char *sB = sB0 + slot * kSt;
+                    constexpr int NPROD = P == 2 ? 3 : 1;
 #pragma unroll
-                for (int blk = 0; blk < 2; ++blk)
+                    for (int blk = 0; blk < 2; ++blk)
 #pragma unroll
-                    for (int kk = 0; kk < kKS; kk += 16)
+                        for (int kk = 0; kk < kKS; kk += 16)
 #pragma unroll
-                        for (int pr = 0; pr < NPROD; ++pr) {
-                            const int pa = pr == 1 ? 1 : 0, pb = pr == 2 ? 1 : 0;
-                            const uint64_t ad = sdesc(smem_u32(sA + (2 * pa + blk) * kBlockBytes) + kk * 16);
-                            const uint64_t bd = sdesc(smem_u32(sB + (2 * pb + blk) * kBlockBytes) + kk * 16);
-                            mma_f16(tmem, ad, bd, id, (j > 0 || blk > 0 || kk > 0 || pr > 0) ? 1u : 0u);
-                        }
-                mma_commit(smem_u32(&empty[slot]));
-                s_last_commit = j;
-                // B of stage j - 1 + NS into the slot of stage j - 1
-                if (j >= 1 && j - 1 + NS < NJ && !load_b(g - 1 + NS)) {
-                    alive = false;
-                    break;
+                            for (int pr = 0; pr < NPROD; ++pr) {
+                                const int pa = pr == 1 ? 1 : 0, pb = pr == 2 ? 1 : 0;
+                                const uint64_t ad = sdesc(smem_u32(sA + (2 * pa + blk) * kBlockBytes) + kk * 16);
+                                const uint64_t bd = sdesc(smem_u32(sB + (2 * pb + blk) * kBlockBytes) + kk * 16);
+                                mma_f16(dtm, ad, bd, id, (j > 0 || blk > 0 || kk > 0 || pr > 0) ? 1u : 0u);
+                            }
+                    mma_commit(smem_u32(&empty[slot]));
+                    if (j == NJ - 1) mma_commit(smem_u32(&acc_full[acc]));  // the tile's accumulator is final
+                    if (j >= 1 && j - 1 + NS < NJ && !load_b(g - 1 + NS)) {
+                        alive = false;
+                        break;
+                    }
                 }
+                if (!alive) s_abort = 1;
             }
-            if (!alive) s_abort = 1;
         }
-        // every issued MMA of the tile is covered by its last commit
-        __syncthreads();
-        const int lc = s_last_commit;
-        bool ok = lc >= 0 && mbar_wait(smem_u32(&empty[(g0 + (uint32_t)lc) % NS]), ((g0 + (uint32_t)lc) / NS) & 1u);
-        ok = !__syncthreads_or(!ok || s_abort || lc != NJ - 1);
-        if (!ok) {
-            if (threadIdx.x == 0) atomicOr(a.err, ERR_TIMEOUT);
-            break;
-        }
-        tc_after_sync();
-        if (warp < 8) {
-            // warp w reads lanes 32 (w % 4) .. +31 (its rows), columns 64 (w / 4) .. +63
-            const int row = 32 * (warp & 3) + lane, half = warp >> 2;
+    } else {
+        // ---------------- epilogue: warps 9-12, TMEM lanes 32 (warp % 4) .. +31
+        const int q = warp & 3;
+        int it = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            const int acc = it & 1;
+            if (!mbar_wait(smem_u32(&acc_full[acc]), (uint32_t)(it / 2) & 1u)) {
+                s_abort = 1;
+                break;
+            }
+            tc_after_sync();
+            const TileInfo t = tile_info(a, tile);
+            const int row = 32 * q + lane;
             bool valid;
             int64_t wrow;
-            if (lay) {
-                const int bl = lb * kRows + row;
-                valid = bl < NB && a.count[a.bbase[s] + bl] > 0;
-                wrow = ((int64_t)(a.bbase[s] + bl) * a.Bmax + bch) * 128;
+            if (t.lay) {
+                const int bl = t.lb * kRows + row;
+                valid = bl < t.NB && a.count[a.bbase[t.s] + bl] > 0;
+                wrow = ((int64_t)(a.bbase[t.s] + bl) * a.Bmax + t.bch) * 128;
             } else {
-                const int64_t g = (int64_t)ltile * kRows + row;
-                valid = g < (int64_t)NB * Bs;
-                const int bl = valid ? (int)(g / Bs) : 0;
-                valid = valid && a.count[a.bbase[s] + bl] > 0;
-                wrow = ((int64_t)(a.bbase[s] + bl) * a.Bmax + (valid ? g % Bs : 0)) * 128;
+                const int64_t g = (int64_t)t.ltile * kRows + row;
+                valid = g < (int64_t)t.NB * t.Bs;
+                const int bl = valid ? (int)(g / t.Bs) : 0;
+                valid = valid && a.count[a.bbase[t.s] + bl] > 0;
+                wrow = ((int64_t)(a.bbase[t.s] + bl) * a.Bmax + (valid ? g % t.Bs : 0)) * 128;
             }
             const float inv = 1.0f / a.zscale;
-            const uint32_t tb = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * half);
-#pragma unroll
-            for (int c = 0; c < 64; c += 32) {
+            const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(128 * acc);
+#pragma unroll 1
+            for (int c = 0; c < 128; c += 32) {
                 uint32_t r[32];
                 tmem_ld32(tb + (uint32_t)c, r);
                 if (valid) {
-                    float4 *w = reinterpret_cast<float4 *>(a.W + wrow + 64 * half + c);
+                    float4 *w = reinterpret_cast<float4 *>(a.W + wrow + c);
 #pragma unroll
                     for (int v = 0; v < 8; ++v)
                         w[v] = make_float4(__uint_as_float(r[4 * v]) * inv, __uint_as_float(r[4 * v + 1]) * inv,
                                            __uint_as_float(r[4 * v + 2]) * inv, __uint_as_float(r[4 * v + 3]) * inv);
                 }
             }
+            tc_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&acc_empty[acc]));
         }
-        // the accumulator is read before the next tile's first MMA
-        tc_before_sync();
-        __syncthreads();
-        tc_after_sync();
+    }
+    __syncthreads();
+    // the MMAs of the last tile (if any) must complete before TMEM is freed
+    const int mine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    if (s_abort && mine > 0 && threadIdx.x == 0) {
+        const int last = mine - 1;
+        mbar_wait(smem_u32(&acc_full[last & 1]), (uint32_t)(last / 2) & 1u);
+        atomicOr(a.err, ERR_TIMEOUT);
     }
     tc_before_sync();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, 128);
+    tc_after_sync();
+    if (warp == 0) tmem_dealloc(tmem, 256);
 }
 
 cudaError_t launch_cdft_btab(const CdftBatch &a, int mode, void *btab, cudaStream_t st)

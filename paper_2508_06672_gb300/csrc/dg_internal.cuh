@@ -165,6 +165,15 @@ __device__ __forceinline__ void geometry_df(dfl x, dfl y, dfl z, const dfl *e, d
     nu = n.hi + n.lo;
 }
 
+// frac(nu * x) for an integer-valued x < 2^24, to ~1e-7 cycles: the product
+// is split exactly into p + e with an FMA, and p - floor(p) is exact.
+__device__ __forceinline__ float frac_mul(float nu, float x)
+{
+    const float p = nu * x;
+    const float e = fmaf(nu, x, -p);
+    return (p - floorf(p)) + e;
+}
+
 // Eq. 9 on a double-float D: round half away from zero, in FP32 only.
 // Returns false (undecided) when |D| >= 2^22 or when D lies within 1e-6 of a
 // rounding boundary; the caller then decides with the FP64 expression.
@@ -334,6 +343,7 @@ cudaError_t launch_cdft_plan(const CdftBatch &a, int NBT, cudaStream_t s);
 cudaError_t launch_cdft_contract_fp32(const CdftBatch &a, int NBT, int fmt, cudaStream_t s);
 cudaError_t launch_cdft_combine(const CdftBatch &a, float *surf, cudaStream_t s);
 // per snapshot: lag buckets, tile layout, tiles (tbase), combine chunk, work
+// (one warp)
 cudaError_t launch_cdft_tiles(const CdftBatch &a, cudaStream_t s);
 // W[bucket][c] <- sum over the Mc / M chunks b of super-chunk c of
 // e^{j 2 pi nu_q (b M - c Mc)} W[bucket][b] (in place; Mc > M)
