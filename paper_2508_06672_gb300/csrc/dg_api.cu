@@ -439,7 +439,8 @@ static dg_status cdft_layout(dg_ctx *c, const GridDev &gd, int64_t G, CdftLayout
     }
     const int m_est = c->opt.chunk ? c->opt.chunk : kCdftAutoMaxChunk;
     const double per_snap = 16.0 * (double)G + (double)slots_max * (double)((nmax + m_est - 1) / m_est) * 512.0;
-    const int s_max = (int)std::max<int64_t>(1, std::min<int64_t>(c->K, (int64_t)(budget / per_snap)));
+    int s_max = (int)std::max<int64_t>(1, std::min<int64_t>(c->K, (int64_t)(budget / per_snap)));
+    if (c->opt.contract != DG_CONTRACT_FP32) s_max = std::min(s_max, kTcMaxSnapshots);
     std::vector<int> bb, gb;
     for (int k0 = 0; k0 < c->K;) {
         int S = 1;  // same format, at most s_max snapshots

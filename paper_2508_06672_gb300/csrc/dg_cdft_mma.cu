@@ -443,6 +443,7 @@ template <> struct Raw<DG_IQ_C64> {
 // inside the loop.
 constexpr int kProducerWarps = 8;
 constexpr int kEpilogueWarps = 4;  // one per 32-lane quarter of the accumulator
+constexpr int kSnapCache = kTcMaxSnapshots;  // per-snapshot tables cached in shared memory
 constexpr int kWsThreads = (kProducerWarps + 1 + kEpilogueWarps) * 32;
 constexpr int kRing = 3;  // pipeline stages in the ring
 template <int P> __host__ __device__ constexpr int ws_smem_bytes() { return kRing * 2 * (2 * P * kBlockBytes); }
@@ -461,27 +462,80 @@ __device__ __forceinline__ int nb_of(const CdftBatch &a, int s)
 
 // Persistent, warp-specialised contraction over every tile of the batch.
 // The tile list (tbase, per-snapshot layout) is computed on the device by
-// k_cdft_tiles, so the host launches a fixed grid without knowing it. Each
-// CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...; a tile is either
+// k_cdft_tiles, so the host launches a fixed grid without knowing it; the
+// per-snapshot tables (at most kSnapCache snapshots per batch) are cached in
+// shared memory. Each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...;
+// a tile is either
 //   rows: 128 consecutive (lag, chunk) rows, lag-major; each producer lane
 //         loads its row's capture segments (Raw<FMT>), or
-//   lags: 128 consecutive lags L0 .. L0 + 127 at one chunk b; the tile
-//         stages y1[bM .. bM + M) (scaled by zscale) and the window
-//         y2[bM + L0 .. bM + L0 + M + 127) in shared memory once, decoded to
-//         FP32, and the producers read only shared memory.
+//   lags: 128 consecutive lags L0 .. L0 + 127 at one chunk b; the producers
+//         stage y1[bM .. bM + M) (scaled by zscale) and the window
+//         y2[bM + L0 .. bM + L0 + M + 127) in shared memory, decoded to FP32,
+//         and then read only shared memory.
 // Samples outside [0, N) are zero in both, so the sums run over the overlap.
-// Roles: warps 0-7 produce the lag products of each stage into a ring of
-// kRing slots; warp 8 (one thread) streams the DFT operand by bulk copy and
-// issues the MMAs; warps 9-12 drain finished accumulators (tcgen05.ld -> W).
-// Two accumulators of 128 TMEM columns alternate between tiles, so the
-// drain of tile i overlaps the MMAs of tile i + 1. Stage and tile counters
-// run across tiles: every mbarrier keeps one phase sequence for the CTA's
-// lifetime. Every wait is bounded (mbar_wait); a timeout stops all roles,
-// latches ERR_TIMEOUT, and the CTA frees its TMEM after waiting (bounded)
-// for the MMAs it issued.
+// Roles:
+//   warps 0-7  produce the lag products of each stage into a ring of kRing
+//              slots;
+//   warp 8     (one thread) streams the DFT operand by bulk copy and issues
+//              the MMAs;
+//   warps 9-12 drain each finished accumulator (tcgen05.ld -> W) while the
+//              next tile's MMAs run.
+// Two accumulators of 128 TMEM columns alternate between tiles. Every
+// mbarrier keeps one phase sequence for the CTA's lifetime; every wait is
+// bounded (mbar_wait); a timeout stops all roles, latches ERR_TIMEOUT, and the
+// CTA frees its TMEM after waiting (bounded) for the MMAs it issued.
 template <int P> __host__ __device__ constexpr int tc_smem_bytes()
 {
     return ws_smem_bytes<P>() + (2 * kLagTileMaxChunk + kRows) * (int)sizeof(float2);
+}
+
+struct SnapCache {  // per-snapshot tables of the batch, in shared memory
+    int tbase[kSnapCache + 1];
+    int bbase[kSnapCache + 1];
+    int lr[2 * kSnapCache];
+    int layout[kSnapCache];
+    StepDesc sd[kSnapCache];
+};
+
+struct TileInfo {
+    int s, ltile, N, Bs, NB, lay, lb, bch, Lmin, bb;
+    StepDesc sd;
+};
+
+__device__ __forceinline__ TileInfo tile_info(const SnapCache &c, int S, int M, int tile)
+{
+    TileInfo t;
+    t.s = step_of_tile(c.tbase, S, tile);
+    t.ltile = tile - c.tbase[t.s];
+    t.sd = c.sd[t.s];
+    t.N = t.sd.n;
+    t.Bs = (t.N + M - 1) / M;
+    const int lo = c.lr[2 * t.s], hi = c.lr[2 * t.s + 1];
+    t.NB = hi >= lo ? hi - lo + 1 : 0;
+    t.lay = c.layout[t.s];
+    const int NLB = max((t.NB + kRows - 1) / kRows, 1);
+    t.lb = t.lay ? t.ltile % NLB : 0;
+    t.bch = t.lay ? t.ltile / NLB : 0;
+    t.Lmin = lo;
+    t.bb = c.bbase[t.s];
+    return t;
+}
+
+// Windows of a lag tile into shared memory, by `nthreads` threads from `tid`.
+template <int FMT>
+__device__ __forceinline__ void stage_windows(const TileInfo &t, int M, float zs, float2 *sy1, float2 *sy2, int tid,
+                                              int nthreads)
+{
+    const int nb0 = t.bch * M, L0 = t.Lmin + t.lb * kRows;
+    for (int i = tid; i < M; i += nthreads) {
+        const int n = nb0 + i;
+        const float2 v = n < t.N ? IQ<FMT>::load(t.sd.y1, n) : make_float2(0.f, 0.f);
+        sy1[i] = make_float2(v.x * zs, v.y * zs);
+    }
+    for (int i = tid; i < M + kRows; i += nthreads) {
+        const int n2 = nb0 + L0 + i;
+        sy2[i] = (n2 >= 0 && n2 < t.N) ? IQ<FMT>::load(t.sd.y2, n2) : make_float2(0.f, 0.f);
+    }
 }
 
 // Barrier of the producer warps (named barrier 1) that also ORs a flag over
@@ -501,28 +555,6 @@ __device__ __forceinline__ bool producers_sync_or(bool flag)
     return r != 0;
 }
 
-struct TileInfo {
-    int s, ltile, N, Bs, NB, lay, lb, bch, Lmin;
-    StepDesc sd;
-};
-
-__device__ __forceinline__ TileInfo tile_info(const CdftBatch &a, int tile)
-{
-    TileInfo t;
-    t.s = step_of_tile(a.tbase, a.S, tile);
-    t.ltile = tile - a.tbase[t.s];
-    t.sd = a.sd[t.s];
-    t.N = t.sd.n;
-    t.Bs = (t.N + a.M - 1) / a.M;
-    t.NB = nb_of(a, t.s);
-    t.lay = a.layout[t.s];
-    const int NLB = max((t.NB + kRows - 1) / kRows, 1);
-    t.lb = t.lay ? t.ltile % NLB : 0;
-    t.bch = t.lay ? t.ltile / NLB : 0;
-    t.Lmin = a.lr[2 * t.s];
-    return t;
-}
-
 template <int FMT, int DT, int P>
 __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
 {
@@ -532,15 +564,25 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
     __shared__ __align__(8) uint64_t full_a[NS], full_b[NS], empty[NS], acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_abort;
+    __shared__ SnapCache sc;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *sA0 = smem;
     unsigned char *sB0 = smem + NS * kSt;
     float2 *sy1 = reinterpret_cast<float2 *>(smem + 2 * NS * kSt);
     float2 *sy2 = sy1 + kLagTileMaxChunk;
-    const int M = a.M, NJ = M / kKS;
-    const int ntiles = a.tbase[a.S];
+    const int M = a.M, NJ = M / kKS, S = a.S;
 
+    for (int i = threadIdx.x; i <= S; i += blockDim.x) {
+        sc.tbase[i] = a.tbase[i];
+        sc.bbase[i] = a.bbase[i];
+        if (i < S) {
+            sc.lr[2 * i] = a.lr[2 * i];
+            sc.lr[2 * i + 1] = a.lr[2 * i + 1];
+            sc.layout[i] = a.layout[i];
+            sc.sd[i] = a.sd[i];
+        }
+    }
     if (threadIdx.x == 0) {
         for (int i = 0; i < NS; ++i) {
             mbar_init(smem_u32(&full_a[i]), kProducerWarps);
@@ -560,28 +602,21 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
     __syncthreads();
     tc_after_sync();
     const uint32_t tmem = tmem_slot;
+    const int ntiles = sc.tbase[S];
+    const int mine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const float zs = a.zscale;
 
     if (warp < kProducerWarps) {
         // ---------------- producers
         const int rin = lane & 7, kg = lane >> 3;
-        const float zs = a.zscale;
-        uint32_t g0 = 0;
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, g0 += (uint32_t)NJ) {
+        for (int it = 0; it < mine; ++it) {
             // every producer is done with the previous tile's windows; all
             // leave together on an abort
             if (producers_sync_or(s_abort != 0)) break;
-            const TileInfo t = tile_info(a, tile);
+            const int tile = (int)blockIdx.x + it * (int)gridDim.x;
+            const TileInfo t = tile_info(sc, S, M, tile);
             if (t.lay) {
-                const int nb0 = t.bch * M, L0 = t.Lmin + t.lb * kRows;
-                for (int i = threadIdx.x; i < M; i += kProducerWarps * 32) {
-                    const int n = nb0 + i;
-                    const float2 v = n < t.N ? IQ<FMT>::load(t.sd.y1, n) : make_float2(0.f, 0.f);
-                    sy1[i] = make_float2(v.x * zs, v.y * zs);
-                }
-                for (int i = threadIdx.x; i < M + kRows; i += kProducerWarps * 32) {
-                    const int n2 = nb0 + L0 + i;
-                    sy2[i] = (n2 >= 0 && n2 < t.N) ? IQ<FMT>::load(t.sd.y2, n2) : make_float2(0.f, 0.f);
-                }
+                stage_windows<FMT>(t, M, zs, sy1, sy2, threadIdx.x, kProducerWarps * 32);
                 asm volatile("bar.sync 1, %0;" ::"r"(kProducerWarps * 32) : "memory");
             }
             int pL[2] = {0, 0}, pn0[2] = {0, 0};
@@ -595,10 +630,11 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                         const int bl = (int)(g / t.Bs);
                         pn0[h] = (int)(g % t.Bs) * M + 8 * kg;
                         pL[h] = t.Lmin + bl;
-                        pv[h] = a.count[a.bbase[t.s] + bl] > 0;
+                        pv[h] = a.count[t.bb + bl] > 0;
                     }
                 }
             }
+            const uint32_t g0 = (uint32_t)it * (uint32_t)NJ;
             for (int j = 0; j < NJ; ++j) {
                 const uint32_t g = g0 + (uint32_t)j;
                 const int slot = (int)(g % NS);
@@ -669,10 +705,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
         // ---------------- control (one thread): B copies, MMAs, commits
         if (lane == 0) {
             const uint32_t id = idesc<DT>();
-            uint32_t g0 = 0;
-            int it = 0;
-            for (int tile = blockIdx.x; tile < ntiles && !s_abort; tile += gridDim.x, g0 += (uint32_t)NJ, ++it) {
-                const int s = step_of_tile(a.tbase, a.S, tile);
+            for (int it = 0; it < mine && !s_abort; ++it) {
+                const uint32_t g0 = (uint32_t)it * (uint32_t)NJ;
+                const int s = step_of_tile(sc.tbase, S, (int)blockIdx.x + it * (int)gridDim.x);
                 const unsigned char *bsrc = reinterpret_cast<const unsigned char *>(a.btab) + (size_t)s * NJ * kSt;
                 // B of stage g goes into slot g % NS once the MMAs of stage g - NS are done
                 auto load_b = [&](uint32_t g) -> bool {
@@ -716,6 +751,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                             }
                     mma_commit(smem_u32(&empty[slot]));
                     if (j == NJ - 1) mma_commit(smem_u32(&acc_full[acc]));  // the tile's accumulator is final
+                    // B of stage j - 1 + NS into the slot of stage j - 1
                     if (j >= 1 && j - 1 + NS < NJ && !load_b(g - 1 + NS)) {
                         alive = false;
                         break;
@@ -725,30 +761,30 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
             }
         }
     } else {
-        // ---------------- epilogue: warps 9-12, TMEM lanes 32 (warp % 4) .. +31
+        // ---------------- drain finished accumulators: warps 9-12
         const int q = warp & 3;
-        int it = 0;
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-            const int acc = it & 1;
-            if (!mbar_wait(smem_u32(&acc_full[acc]), (uint32_t)(it / 2) & 1u)) {
+        for (int it = 1; it <= mine && !s_abort; ++it) {
+            // drain tile it - 1
+            const int d = it - 1, acc = d & 1;
+            if (!mbar_wait(smem_u32(&acc_full[acc]), (uint32_t)(d / 2) & 1u)) {
                 s_abort = 1;
                 break;
             }
             tc_after_sync();
-            const TileInfo t = tile_info(a, tile);
+            const TileInfo t = tile_info(sc, S, M, (int)blockIdx.x + d * (int)gridDim.x);
             const int row = 32 * q + lane;
             bool valid;
             int64_t wrow;
             if (t.lay) {
                 const int bl = t.lb * kRows + row;
-                valid = bl < t.NB && a.count[a.bbase[t.s] + bl] > 0;
-                wrow = ((int64_t)(a.bbase[t.s] + bl) * a.Bmax + t.bch) * 128;
+                valid = bl < t.NB && a.count[t.bb + bl] > 0;
+                wrow = ((int64_t)(t.bb + bl) * a.Bmax + t.bch) * 128;
             } else {
                 const int64_t g = (int64_t)t.ltile * kRows + row;
                 valid = g < (int64_t)t.NB * t.Bs;
                 const int bl = valid ? (int)(g / t.Bs) : 0;
-                valid = valid && a.count[a.bbase[t.s] + bl] > 0;
-                wrow = ((int64_t)(a.bbase[t.s] + bl) * a.Bmax + (valid ? g % t.Bs : 0)) * 128;
+                valid = valid && a.count[t.bb + bl] > 0;
+                wrow = ((int64_t)(t.bb + bl) * a.Bmax + (valid ? g % t.Bs : 0)) * 128;
             }
             const float inv = 1.0f / a.zscale;
             const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(128 * acc);
@@ -771,7 +807,6 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
     }
     __syncthreads();
     // the MMAs of the last tile (if any) must complete before TMEM is freed
-    const int mine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     if (s_abort && mine > 0 && threadIdx.x == 0) {
         const int last = mine - 1;
         mbar_wait(smem_u32(&acc_full[last & 1]), (uint32_t)(last / 2) & 1u);

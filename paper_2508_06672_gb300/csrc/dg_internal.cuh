@@ -356,6 +356,9 @@ size_t cdft_btab_bytes(int mode, int M);  // per snapshot
 // Lag tiles (128 consecutive lags of one chunk share one y1 segment and one
 // y2 window, staged once in shared memory) need chunk <= this.
 constexpr int kLagTileMaxChunk = 1024;
+// Snapshots per batch on the tensor-core path (the contraction caches their
+// tables in shared memory).
+constexpr int kTcMaxSnapshots = 64;
 
 // CDFT chunk bounds: the longest chunk; the longest the automatic choice
 // takes (longer chunks shorten the combine but lengthen the tables and the
