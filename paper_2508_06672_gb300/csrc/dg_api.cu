@@ -453,7 +453,7 @@ static dg_status cdft_layout(dg_ctx *c, const GridDev &gd, int64_t G, CdftLayout
             if (s == S) break;
             const int slots = lag_slots(c->eph_host[k0 + s], c->fs, diam);
             nb += slots;
-            ng += G / kCdftCombineThreads + slots + 1;
+            ng += G / kCdftCombineGroup + slots + 1;
         }
         if (nb > INT_MAX / 64 || ng > INT_MAX)
             return fail(c, DG_EUNSUPPORTED, "CDFT: %lld lag slots in one batch; use DIRECT", (long long)nb);

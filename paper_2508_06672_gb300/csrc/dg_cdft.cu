@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(1024) k_cdft_scan(CdftBatch a)
     for (int i = b0; i < b1; ++i) {
         const int n = a.count[b_first + i];
         c += n;
-        g += (n + kCdftCombineThreads - 1) / kCdftCombineThreads;
+        g += (n + kCdftCombineGroup - 1) / kCdftCombineGroup;
     }
     s_c[t] = c;
     s_g[t] = g;
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(1024) k_cdft_scan(CdftBatch a)
         a.offs[b] = oc;
         a.gofs[b] = og;
         const int n = a.count[b];
-        const int ng = (n + kCdftCombineThreads - 1) / kCdftCombineThreads;
+        const int ng = (n + kCdftCombineGroup - 1) / kCdftCombineGroup;
         for (int g = 0; g < ng; ++g) a.g2b[a.gbase[s] + og + g] = b;
         oc += n;
         og += ng;
@@ -464,9 +464,9 @@ __global__ void __launch_bounds__(256) k_cdft_superchunk(CdftBatch a, int NBT)
 }
 
 // ---------------------------------------------------------------------------
-// combine: one thread per candidate, kCdftCombineThreads candidates of one
-// bucket per CTA (sorted by interpolation bin); the bucket's W streams through
-// shared memory in segments of kSeg chunks.
+// combine: kCdftCombineGroup candidates of one bucket per CTA (sorted by
+// interpolation bin), kCdftCombinePer per thread; the bucket's super-chunk
+// DFTs stream through shared memory in segments of kSeg.
 // ---------------------------------------------------------------------------
 constexpr int kSeg = 32;
 
@@ -476,57 +476,86 @@ __global__ void __launch_bounds__(kCdftCombineThreads) k_cdft_combine(CdftBatch 
     // per chunk and bin q: (re q, re q+1, im q, im q+1), so that a candidate
     // reads both neighbouring bins with one 16-byte load
     __shared__ __align__(16) float4 ws[kSeg][64];
+    __shared__ int sh_b, sh_s, sh_first, sh_n, sh_M, sh_B;
+    __shared__ float sh_base, sh_inv;
     // one CTA per combine group of the batch's upper bound; groups past a
     // snapshot's last are -1 in the scan's group-to-bucket map
-    {
+    if (threadIdx.x == 0) {
         const int gid = blockIdx.x;
         const int b = a.g2b[gid];
-        if (b < 0) return;  // uniform
-        const int s = step_of(a.gbase, a.S, gid);
-        const int lgid = gid - a.gbase[s];
-        const int n_b = a.count[b];
-        const int j = (lgid - a.gofs[b]) * kCdftCombineThreads + threadIdx.x;
-        const bool active = j < n_b;
-        const size_t sp = (size_t)s * a.G + a.offs[b] + j;
-        const int c = active ? a.order[sp] : 0;
-        const float nuf = active ? a.nuS[sp] : a.nubase[s];
-        float t;
-        const int q0 = bin_of(nuf, a.nubase[s], a.delta[s], t);
-        const float w0 = 1.f - t, w1 = t;
-        const int M = a.Mcs[s];
-        const int B = (a.sd[s].n + M - 1) / M;
-        // chunk-to-chunk phase step e^{j 2 pi nu M}
-        float ex, ey;
-        sincospif(2.0f * frac_mul(nuf, (float)M), &ey, &ex);
-        float cx = 0.f, cy = 0.f;
-        const float *Wb = a.W + (size_t)b * a.Bmax * 128;
-        for (int s0 = 0; s0 < B; s0 += kSeg) {
-            const int slen = min(kSeg, B - s0);
-            __syncthreads();
-            for (int i = threadIdx.x; i < slen * 64; i += kCdftCombineThreads) {
-                const int ch = i >> 6, q = i & 63, q1 = min(q + 1, 63);
-                const float *row = Wb + (size_t)(s0 + ch) * 128;
-                ws[ch][q] = make_float4(row[q], row[q1], row[64 + q], row[64 + q1]);
-            }
-            __syncthreads();
-            float px, py;  // phase of the segment's first sample, e^{j 2 pi nu s0 M}
-            sincospif(2.0f * frac_mul(nuf, (float)s0 * (float)M), &py, &px);
-#pragma unroll 4
-            for (int i = 0; i < slen; ++i) {
-                const float4 v = ws[i][q0];
-                const float zx = fmaf(w0, v.x, w1 * v.y), zy = fmaf(w0, v.z, w1 * v.w);
-                cx = fmaf(px, zx, fmaf(-py, zy, cx));
-                cy = fmaf(px, zy, fmaf(py, zx, cy));
-                const float nx = fmaf(px, ex, -py * ey);
-                py = fmaf(px, ey, py * ex);
-                px = nx;
-            }
-        }
-        if (active) {
-            const float pw = fmaf(cx, cx, cy * cy);
-            surf[(size_t)(a.k0 + s) * a.G + c] = (T)(a.acc == DG_ACC_POWER ? pw : sqrtf(pw));
+        sh_b = b;
+        if (b >= 0) {
+            const int s = step_of(a.gbase, a.S, gid);
+            const int lgid = gid - a.gbase[s];
+            sh_s = s;
+            sh_first = (lgid - a.gofs[b]) * kCdftCombineGroup;
+            sh_n = a.count[b] - sh_first;
+            sh_M = a.Mcs[s];
+            sh_B = (a.sd[s].n + sh_M - 1) / sh_M;
+            sh_base = a.nubase[s];
+            sh_inv = 1.0f / a.delta[s];
         }
     }
+    __syncthreads();
+    const int b = sh_b;
+    if (b < 0) return;  // uniform
+    const int s = sh_s, M = sh_M, B = sh_B, n = sh_n;
+    const size_t sp0 = (size_t)s * a.G + a.offs[b] + sh_first;
+    int c[kCdftCombinePer], q0[kCdftCombinePer];
+    float w1[kCdftCombinePer], ex[kCdftCombinePer], ey[kCdftCombinePer], px[kCdftCombinePer],
+        py[kCdftCombinePer], cx[kCdftCombinePer], cy[kCdftCombinePer], nu[kCdftCombinePer];
+#pragma unroll
+    for (int k = 0; k < kCdftCombinePer; ++k) {
+        const int j = threadIdx.x + k * kCdftCombineThreads;
+        const bool act = j < n;
+        c[k] = act ? a.order[sp0 + j] : -1;
+        nu[k] = act ? a.nuS[sp0 + j] : sh_base;
+        // interpolation bin q0 in [0, 62] and weight of bin q0 + 1
+        const float u = (nu[k] - sh_base) * sh_inv;
+        q0[k] = max(0, min(62, (int)floorf(u)));
+        w1[k] = u - (float)q0[k];
+        // chunk-to-chunk phase step e^{j 2 pi nu M}
+        sincospif(2.0f * frac_mul(nu[k], (float)M), &ey[k], &ex[k]);
+        cx[k] = cy[k] = 0.f;
+    }
+    const float *Wb = a.W + (size_t)b * a.Bmax * 128;
+    for (int s0 = 0; s0 < B; s0 += kSeg) {
+        const int slen = min(kSeg, B - s0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < slen * 64; i += kCdftCombineThreads) {
+            const int ch = i >> 6, q = i & 63, q1 = min(q + 1, 63);
+            const float *row = Wb + (size_t)(s0 + ch) * 128;
+            ws[ch][q] = make_float4(row[q], row[q1], row[64 + q], row[64 + q1]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kCdftCombinePer; ++k) {
+            // phase of the segment's first sample, e^{j 2 pi nu s0 M}
+            if (s0 == 0) {
+                px[k] = 1.f;
+                py[k] = 0.f;
+            } else {
+                sincospif(2.0f * frac_mul(nu[k], (float)s0 * (float)M), &py[k], &px[k]);
+            }
+            const float w0 = 1.f - w1[k];
+#pragma unroll 4
+            for (int i = 0; i < slen; ++i) {
+                const float4 v = ws[i][q0[k]];
+                const float zx = fmaf(w0, v.x, w1[k] * v.y), zy = fmaf(w0, v.z, w1[k] * v.w);
+                cx[k] = fmaf(px[k], zx, fmaf(-py[k], zy, cx[k]));
+                cy[k] = fmaf(px[k], zy, fmaf(py[k], zx, cy[k]));
+                const float nx = fmaf(px[k], ex[k], -py[k] * ey[k]);
+                py[k] = fmaf(px[k], ey[k], py[k] * ex[k]);
+                px[k] = nx;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kCdftCombinePer; ++k)
+        if (c[k] >= 0) {
+            const float pw = fmaf(cx[k], cx[k], cy[k] * cy[k]);
+            surf[(size_t)(a.k0 + s) * a.G + c[k]] = (T)(a.acc == DG_ACC_POWER ? pw : sqrtf(pw));
+        }
 }
 
 // ---------------------------------------------------------------------------

@@ -296,6 +296,8 @@ cudaError_t launch_accumulate(const void *surf, int K, int64_t G, int prec, void
 // gbase[s+1]-1 (an upper bound; surplus CTAs exit).
 // ---------------------------------------------------------------------------
 constexpr int kCdftCombineThreads = 256;
+constexpr int kCdftCombinePer = 4;  // candidates per combine thread
+constexpr int kCdftCombineGroup = kCdftCombineThreads * kCdftCombinePer;  // candidates per combine CTA
 
 struct CdftBatch {
     const double *xyz;            // [3][G]
