@@ -69,9 +69,9 @@ enum { DG_PREC_FP32 = 0, DG_PREC_FP64 = 1 };
  * their integer lag L (Eq. 9): all of them share the lag product
  * z_L[n] = y1[n] conj(y2[n + L]), so Eq. 11 becomes, per lag, a DFT of z_L
  * in chunks of `chunk` samples at `bins` Doppler frequencies spanning that
- * lag's FDOA range (a dense contraction), followed per candidate by a linear
- * interpolation between bins and a sum over chunks with the FDOA phase of
- * each chunk's first sample. Its error against the definition is bounded by
+ * lag's FDOA range (a dense contraction), followed per candidate by a
+ * quadratic interpolation between the three nearest bins and a sum over
+ * chunks with the FDOA phase of each chunk's first sample. Its error against the definition is bounded by
  * the bin interpolation and by the arithmetic of the contraction
  * (DG_CONTRACT_*). */
 enum { DG_ALGO_DIRECT = 0, DG_ALGO_CDFT = 1 };
@@ -120,7 +120,7 @@ typedef struct {
     int32_t timing;  /* 1: time kernels with CUDA events (dg_kernel_time)     */
     int32_t chunk;   /* CDFT: samples per chunk, a multiple of 64 in [64,4096];
                         0 = chosen per batch of snapshots: the longest power
-                        of two <= 1024 whose length x bin spacing is <= 4e-3
+                        of two <= 1024 whose length x bin spacing is <= 1.2e-2
                         cycles in every snapshot of the batch
                         (dg_cdft_chunks)                                      */
     int32_t bins;    /* CDFT: Doppler bins per lag; 0 = 64 (the only value)   */
@@ -314,7 +314,7 @@ dg_status dg_kernel_time(dg_ctx *ctx, int32_t kernel_class, double *ms, int64_t 
  * summed over snapshots: lag-bucket x chunk pairs contracted (each a
  * chunk-by-bins complex DFT) and candidate x super-chunk pairs combined (the
  * combine merges chunks at the bin frequencies into the longest power-of-two
- * multiple of the chunk whose length x bin spacing stays <= 4e-3 cycles).
+ * multiple of the chunk whose length x bin spacing stays <= 1.2e-2 cycles).
  * Host pointers, may be NULL; zeros before the first CDFT surface. */
 dg_status dg_cdft_work(const dg_ctx *ctx, int64_t *bucket_chunks, int64_t *candidate_chunks);
 

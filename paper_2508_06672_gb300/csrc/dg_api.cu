@@ -217,7 +217,7 @@ dg_status check_latched(dg_ctx *c)
                         "kernels do not handle it");
         if (e & ERR_BIN_SPACING)
             return fail(c, DG_EUNSUPPORTED,
-                        "CDFT: a snapshot's FDOA span is too wide for its chunk (chunk x bin spacing > 4e-3 "
+                        "CDFT: a snapshot's FDOA span is too wide for its chunk (chunk x bin spacing > 1.2e-2 "
                         "cycles); use a shorter chunk or DIRECT");
         return fail(c, DG_EUNSUPPORTED, "a candidate's lag |D| exceeds 1e9 samples");
     }
@@ -404,14 +404,14 @@ static double fdoa_span(const dg_ctx *c, const GridDev &g, int k, int lattice)
 
 // Chunk of a batch with chunk = 0: the longest power of two in
 // [64, kCdftAutoMaxChunk] whose length times the estimated bin spacing stays
-// within kCdftAutoMDelta / 1.25 (a margin for the lattice estimate; the plan
+// within kCdftMDelta / 1.25 (a margin for the lattice estimate; the plan
 // kernel checks the bound against the exact spacing).
 static int auto_chunk(const std::vector<double> &span, int k0, int S)
 {
     double dmax = 0.0;
     for (int s = 0; s < S; ++s) dmax = std::max(dmax, span[k0 + s] * (1.0 + 1e-5) / 63.0);
     int M = kCdftAutoMaxChunk;
-    while (M > 64 && 1.25 * M * dmax > kCdftAutoMDelta) M >>= 1;
+    while (M > 64 && 1.25 * M * dmax > kCdftMDelta) M >>= 1;
     return M;
 }
 
@@ -1389,7 +1389,7 @@ dg_status dg_autotune(dg_ctx *c, void *cost, int32_t reps, dg_tuning *out)
     for (int k = 0; k < c->K; ++k) dmax = std::max(dmax, span[k] * (1.0 + 1e-5) / 63.0);
     std::vector<int> chunks;
     for (int m : {256, 512, 1024})
-        if (1.25 * m * dmax <= kCdftAutoMDelta) chunks.push_back(m);
+        if (1.25 * m * dmax <= kCdftMDelta) chunks.push_back(m);
     if (chunks.empty()) chunks.push_back(auto_chunk(span, 0, c->K));
     std::vector<int> tiles = {DG_TILES_ROWS};
     if (c->opt.contract != DG_CONTRACT_FP32) tiles.push_back(DG_TILES_LAGS);

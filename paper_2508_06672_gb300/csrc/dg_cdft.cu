@@ -12,9 +12,10 @@
 // nu_q = nu_min + q Delta, Delta = (nu_max - nu_min) / 63 -- a dense
 // [lag x chunk rows] x [M] x [64 bins] contraction whose DFT matrix
 // V[m][q] = e^{j 2 pi nu_q m} is shared by every row of the snapshot -- and
-// each candidate interpolates linearly between the two bins around its own
-// FDOA. The interpolation error is about (pi M Delta)^2 / 6 relative; the
-// snapshot is rejected (DG_EUNSUPPORTED) if M * Delta > 4e-3.
+// each candidate interpolates between the three bins around its own FDOA
+// (quadratic Lagrange). The interpolation error is at most about
+// 0.016 (2 pi M Delta)^3 of the coherent sum; the snapshot is rejected
+// (DG_EUNSUPPORTED) if M * Delta > kCdftMDelta.
 //
 // All snapshots of a batch are processed by the same launches:
 //   geo      FP64 geometry once per (candidate, snapshot): lag and FDOA kept,
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(1024) k_cdft_scan(CdftBatch a)
         const float d = fmaxf((hi - lo) * (1.0f + 1e-5f) / 63.0f, 1e-20f);
         a.nubase[s] = lo;
         a.delta[s] = d;
-        if ((double)d * (double)a.M > 4e-3) atomicOr(a.err, ERR_BIN_SPACING);
+        if ((double)d * (double)a.M > kCdftMDelta) atomicOr(a.err, ERR_BIN_SPACING);
     }
 }
 
@@ -466,16 +467,18 @@ __global__ void __launch_bounds__(256) k_cdft_superchunk(CdftBatch a, int NBT)
 // ---------------------------------------------------------------------------
 // combine: kCdftCombineGroup candidates of one bucket per CTA (sorted by
 // interpolation bin), kCdftCombinePer per thread; the bucket's super-chunk
-// DFTs stream through shared memory in segments of kSeg.
+// DFTs stream through shared memory in segments of kSeg. Each candidate
+// interpolates the DFT of every super-chunk at its own FDOA from the three
+// nearest bins (quadratic Lagrange), rotates it by the super-chunk's phase
+// e^{j 2 pi nu c Mc}, and sums.
 // ---------------------------------------------------------------------------
 constexpr int kSeg = 32;
 
 template <typename T>
 __global__ void __launch_bounds__(kCdftCombineThreads) k_cdft_combine(CdftBatch a, T *surf)
 {
-    // per chunk and bin q: (re q, re q+1, im q, im q+1), so that a candidate
-    // reads both neighbouring bins with one 16-byte load
-    __shared__ __align__(16) float4 ws[kSeg][64];
+    // per (super-)chunk and bin: the DFT value (re, im)
+    __shared__ __align__(16) float2 ws[kSeg][64];
     __shared__ int sh_b, sh_s, sh_first, sh_n, sh_M, sh_B;
     __shared__ float sh_base, sh_inv;
     // one CTA per combine group of the batch's upper bound; groups past a
@@ -502,18 +505,23 @@ __global__ void __launch_bounds__(kCdftCombineThreads) k_cdft_combine(CdftBatch 
     const int s = sh_s, M = sh_M, B = sh_B, n = sh_n;
     const size_t sp0 = (size_t)s * a.G + a.offs[b] + sh_first;
     int c[kCdftCombinePer], q0[kCdftCombinePer];
-    float w1[kCdftCombinePer], ex[kCdftCombinePer], ey[kCdftCombinePer], px[kCdftCombinePer],
-        py[kCdftCombinePer], cx[kCdftCombinePer], cy[kCdftCombinePer], nu[kCdftCombinePer];
+    float wm[kCdftCombinePer], w0[kCdftCombinePer], wp[kCdftCombinePer], ex[kCdftCombinePer],
+        ey[kCdftCombinePer], px[kCdftCombinePer], py[kCdftCombinePer], cx[kCdftCombinePer], cy[kCdftCombinePer],
+        nu[kCdftCombinePer];
 #pragma unroll
     for (int k = 0; k < kCdftCombinePer; ++k) {
         const int j = threadIdx.x + k * kCdftCombineThreads;
         const bool act = j < n;
         c[k] = act ? a.order[sp0 + j] : -1;
         nu[k] = act ? a.nuS[sp0 + j] : sh_base;
-        // interpolation bin q0 in [0, 62] and weight of bin q0 + 1
+        // quadratic (3-point Lagrange) interpolation on bins q0 - 1, q0, q0 + 1
+        // with q0 the nearest bin, kept in [1, 62]; t = offset from bin q0
         const float u = (nu[k] - sh_base) * sh_inv;
-        q0[k] = max(0, min(62, (int)floorf(u)));
-        w1[k] = u - (float)q0[k];
+        q0[k] = max(1, min(62, __float2int_rn(u)));
+        const float t = u - (float)q0[k];
+        wm[k] = 0.5f * t * (t - 1.f);
+        w0[k] = (1.f - t) * (1.f + t);
+        wp[k] = 0.5f * t * (t + 1.f);
         // chunk-to-chunk phase step e^{j 2 pi nu M}
         sincospif(2.0f * frac_mul(nu[k], (float)M), &ey[k], &ex[k]);
         cx[k] = cy[k] = 0.f;
@@ -523,9 +531,9 @@ __global__ void __launch_bounds__(kCdftCombineThreads) k_cdft_combine(CdftBatch 
         const int slen = min(kSeg, B - s0);
         __syncthreads();
         for (int i = threadIdx.x; i < slen * 64; i += kCdftCombineThreads) {
-            const int ch = i >> 6, q = i & 63, q1 = min(q + 1, 63);
+            const int ch = i >> 6, q = i & 63;
             const float *row = Wb + (size_t)(s0 + ch) * 128;
-            ws[ch][q] = make_float4(row[q], row[q1], row[64 + q], row[64 + q1]);
+            ws[ch][q] = make_float2(row[q], row[64 + q]);
         }
         __syncthreads();
 #pragma unroll
@@ -537,11 +545,11 @@ __global__ void __launch_bounds__(kCdftCombineThreads) k_cdft_combine(CdftBatch 
             } else {
                 sincospif(2.0f * frac_mul(nu[k], (float)s0 * (float)M), &py[k], &px[k]);
             }
-            const float w0 = 1.f - w1[k];
 #pragma unroll 4
             for (int i = 0; i < slen; ++i) {
-                const float4 v = ws[i][q0[k]];
-                const float zx = fmaf(w0, v.x, w1[k] * v.y), zy = fmaf(w0, v.z, w1[k] * v.w);
+                const float2 vm = ws[i][q0[k] - 1], v0 = ws[i][q0[k]], vp = ws[i][q0[k] + 1];
+                const float zx = fmaf(wm[k], vm.x, fmaf(w0[k], v0.x, wp[k] * vp.x));
+                const float zy = fmaf(wm[k], vm.y, fmaf(w0[k], v0.y, wp[k] * vp.y));
                 cx[k] = fmaf(px[k], zx, fmaf(-py[k], zy, cx[k]));
                 cy[k] = fmaf(px[k], zy, fmaf(py[k], zx, cy[k]));
                 const float nx = fmaf(px[k], ex[k], -py[k] * ey[k]);
@@ -564,7 +572,7 @@ __global__ void __launch_bounds__(kCdftCombineThreads) k_cdft_combine(CdftBatch 
 // chunk unless padding the lags to blocks of 128 more than doubles the tile
 // count, or the chunk exceeds kLagTileMaxChunk), the tile offsets, and the
 // combine chunk: the longest power-of-two multiple of M with
-// Mc x bin spacing <= kCdftAutoMDelta, up to the first length that covers the
+// Mc x bin spacing <= kCdftMDelta, up to the first length that covers the
 // snapshot and at most 2^24. Also the work counters.
 // ---------------------------------------------------------------------------
 __global__ void k_cdft_tiles(CdftBatch a)
@@ -592,7 +600,7 @@ __global__ void k_cdft_tiles(CdftBatch a)
             tiles = lay ? t_lag : t_row;
             int64_t Mc = M;
             const double d = (double)a.delta[s];
-            while (Mc < n && 2 * Mc <= ((int64_t)1 << 24) && (double)(2 * Mc) * d <= kCdftAutoMDelta) Mc *= 2;
+            while (Mc < n && 2 * Mc <= ((int64_t)1 << 24) && (double)(2 * Mc) * d <= kCdftMDelta) Mc *= 2;
             a.Mcs[s] = (int)Mc;
             rows += (unsigned long long)NB * B;
             cands += (unsigned long long)a.G * ((n + Mc - 1) / Mc);

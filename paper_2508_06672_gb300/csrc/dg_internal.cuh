@@ -365,11 +365,14 @@ constexpr int kTcMaxSnapshots = 64;
 // CDFT chunk bounds: the longest chunk; the longest the automatic choice
 // takes (longer chunks shorten the combine but lengthen the tables and the
 // contraction's operand stream: 1024 was fastest on the 1001^2 and 4001^2
-// workloads); and the chunk x bin-spacing product (cycles) it keeps below,
-// the same bound the plan enforces.
+// workloads); and the bound on (samples summed per DFT) x (bin spacing), in
+// cycles, for the 3-bin quadratic interpolation of the combine: its relative
+// error is at most about 0.016 (2 pi M Delta)^3 of the coherent sum, 7e-6 at
+// this bound. The plan rejects a chunk above it; the automatic chunk and the
+// super-chunks keep below it.
 constexpr int kCdftMaxChunk = 4096;
 constexpr int kCdftAutoMaxChunk = 1024;
-constexpr double kCdftAutoMDelta = 4e-3;
+constexpr double kCdftMDelta = 1.2e-2;
 
 // Threshold detection (dg_detect.cu). cap: power of two <= kDetectCap candidates
 // (the sort keeps value + index of each in static shared memory, 32 KiB).

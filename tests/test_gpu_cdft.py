@@ -58,11 +58,11 @@ def test_cdft_lag_tiles_match_row_tiles(fmt, contract):
 
 def test_cdft_auto_chunk():
     """chunk 0: each batch takes the longest power-of-two chunk up to 1024
-    whose length times the bin spacing is within 4e-3 cycles; the result
-    stays within the FP32 tolerance, and a grid with a wider FDOA span gets a
-    shorter chunk."""
+    whose length times the estimated bin spacing stays within the bound (with
+    a 25 % margin); the result stays within the FP32 tolerance, and a grid
+    with a wider FDOA span (1000 km at 2 MHz) gets a shorter chunk."""
     chunks = []
-    for fs, spacing in ((12.5e6, 100.0), (5e6, 25000.0)):
+    for fs, spacing in ((12.5e6, 100.0), (2e6, 25000.0)):
         s = sim.make_scene(seed=23, fs_hz=fs, n_samples=40000, k_steps=2, fmt="ci16", waveform="chirp",
                            snr_db=-3.0, grid_n=(41, 39), grid_spacing_m=spacing)
         g, c = gpu_surface(s, algo="cdft")
@@ -81,7 +81,7 @@ def test_cdft_superchunks(contract):
     """The combine sums chunks at the bin frequencies into super-chunks as
     long as the bin-spacing bound allows: a 4 km grid (narrow FDOA span)
     needs one super-chunk per snapshot; a 1000 km grid at 5 MHz with 64-sample
-    chunks gets 256-sample super-chunks. Both stay within the FP32 bound of
+    chunks gets 1024-sample super-chunks. Both stay within the FP32 bound of
     the oracle."""
     for fs, spacing, chunk, one in ((12.5e6, 100.0, 256, True), (5e6, 25000.0, 64, False)):
         s = sim.make_scene(seed=25, fs_hz=fs, n_samples=40000, k_steps=2, fmt="ci16", waveform="chirp",
@@ -96,6 +96,29 @@ def test_cdft_superchunks(contract):
         ok = ~lag_boundary_mask(s, np.arange(s.G))
         assert rel_err(c.ravel()[ok], ref.ravel()[ok], 0.01) < FP32_TOL
         g.close()
+
+
+def test_cdft_rejects_chunk_too_long_for_the_bins():
+    """A fixed chunk whose length times the bin spacing exceeds the
+    interpolation bound (4096 samples on a 1000 km grid at 5 MHz) is
+    refused with DG_EUNSUPPORTED when the surface is read; the context
+    stays usable with a shorter chunk."""
+    torch = torch_cuda()
+    P = package()
+    s = sim.make_scene(seed=26, fs_hz=5e6, n_samples=20000, k_steps=1, fmt="ci16", waveform="chirp",
+                       snr_db=-3.0, grid_n=(41, 39), grid_spacing_m=25000.0)
+    g = P.Geolocator(s.grid, s.ephem, s.fs_hz, s.fc_hz, algo="cdft", chunk=4096)
+    g.load_captures(s.fmt, torch.from_numpy(s.y1).cuda(), torch.from_numpy(s.y2).cuda())
+    g.cost_surface()
+    with pytest.raises(P.DGError) as e:
+        g.sync()
+    assert e.value.status == P.DG_EUNSUPPORTED
+    g.close()
+    g, c = gpu_surface(s, algo="cdft", chunk=1024)
+    ref = oracle_surface(s)
+    ok = ~lag_boundary_mask(s, np.arange(s.G))
+    assert rel_err(c.ravel()[ok], ref.ravel()[ok], 0.01) < FP32_TOL
+    g.close()
 
 
 @pytest.mark.parametrize("chunk", [64, 1024, 4096])

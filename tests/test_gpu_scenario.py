@@ -47,7 +47,7 @@ def test_four_jammers_accumulated(scene, opts):
         # the ~900 km wide grid spans a wide FDOA range: the automatic chunk
         # is short enough for the interpolation bound
         lo, hi = g.cdft_chunks()
-        assert 64 <= lo <= hi < 1024
+        assert 64 <= lo <= hi <= 1024
     assert sorted((p["i"], p["j"]) for p in peaks) == sorted(scene.emitter_nodes)
     # sampled parity with the oracle: the emitters' nodes plus seeded random nodes
     rng = np.random.default_rng(7)
