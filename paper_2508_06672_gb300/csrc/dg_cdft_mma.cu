@@ -436,17 +436,25 @@ template <> struct Raw<DG_IQ_C64> {
     }
 };
 
-// Warp-specialised pipeline. Warps 0-7 produce A (lag products) into a ring of
-// kRing stages (A and B per slot); warp 8 lane 0 issues the bulk copies of B and the MMAs. Per
-// stage slot: full_a (8 producer-warp arrivals), full_b (bulk-copy bytes),
-// empty (tcgen05.commit of the MMAs that read the slot). No CTA-wide barrier
-// inside the loop.
-constexpr int kProducerWarps = 8;
+// Warp-specialised pipeline. Producer warps write A (lag products) into a
+// ring of ring_a<P>() slots; one control thread streams B (the DFT operand)
+// by bulk copy into a ring of ring_b<P>() slots and issues the MMAs. Per slot:
+// full_a (one arrival per producer warp) / full_b (bulk-copy bytes), and
+// empty_a / empty_b (tcgen05.commit of the MMAs that read the slot).
+constexpr int kProducerWarps = 16;  // enough warps per scheduler to hide the producers' load-math-store latency
+constexpr int kRowSets = kRows / (8 * kProducerWarps);  // 8-row sets per producer warp
 constexpr int kEpilogueWarps = 4;  // one per 32-lane quarter of the accumulator
 constexpr int kSnapCache = kTcMaxSnapshots;  // per-snapshot tables cached in shared memory
-constexpr int kWsThreads = (kProducerWarps + 1 + kEpilogueWarps) * 32;
-constexpr int kRing = 3;  // pipeline stages in the ring
-template <int P> __host__ __device__ constexpr int ws_smem_bytes() { return kRing * 2 * (2 * P * kBlockBytes); }
+// warps: producers, then the MMA thread's warp, the operand loader's warp,
+// then the epilogue warps
+constexpr int kMmaWarp = kProducerWarps, kLoadWarp = kProducerWarps + 1;
+constexpr int kWsThreads = (kProducerWarps + 2 + kEpilogueWarps) * 32;
+template <int P> __host__ __device__ constexpr int ring_a() { return P == 2 ? 3 : 4; }
+template <int P> __host__ __device__ constexpr int ring_b() { return P == 2 ? 3 : 6; }
+template <int P> __host__ __device__ constexpr int ws_smem_bytes()
+{
+    return (ring_a<P>() + ring_b<P>()) * (2 * P * kBlockBytes);
+}
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
@@ -474,11 +482,13 @@ __device__ __forceinline__ int nb_of(const CdftBatch &a, int s)
 //         and then read only shared memory.
 // Samples outside [0, N) are zero in both, so the sums run over the overlap.
 // Roles:
-//   warps 0-7  produce the lag products of each stage into a ring of kRing
-//              slots;
-//   warp 8     (one thread) streams the DFT operand by bulk copy and issues
-//              the MMAs;
-//   warps 9-12 drain each finished accumulator (tcgen05.ld -> W) while the
+//   warps 0-15 produce the lag products of each stage into a ring of
+//              ring_a<P>() slots;
+//   warp 16    (one thread) issues the MMAs of each stage once its A and B
+//              are in, and commits them to the stage's empty barriers;
+//   warp 17    (one thread) streams the DFT operand by bulk copy, up to
+//              ring_b<P>() stages ahead of the MMAs, across tiles;
+//   warps 18-21 drain each finished accumulator (tcgen05.ld -> W) while the
 //              next tile's MMAs run.
 // Two accumulators of 128 TMEM columns alternate between tiles. Every
 // mbarrier keeps one phase sequence for the CTA's lifetime; every wait is
@@ -558,18 +568,18 @@ __device__ __forceinline__ bool producers_sync_or(bool flag)
 template <int FMT, int DT, int P>
 __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
 {
-    constexpr int NS = kRing;
+    constexpr int NA = ring_a<P>(), NB = ring_b<P>();
     constexpr int kSt = 2 * P * kBlockBytes;  // bytes of one stage's A (or B) blocks
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t full_a[NS], full_b[NS], empty[NS], acc_full[2], acc_empty[2];
+    __shared__ __align__(8) uint64_t full_a[NA], empty_a[NA], full_b[NB], empty_b[NB], acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_abort;
     __shared__ SnapCache sc;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *sA0 = smem;
-    unsigned char *sB0 = smem + NS * kSt;
-    float2 *sy1 = reinterpret_cast<float2 *>(smem + 2 * NS * kSt);
+    unsigned char *sB0 = smem + NA * kSt;
+    float2 *sy1 = reinterpret_cast<float2 *>(smem + (NA + NB) * kSt);
     float2 *sy2 = sy1 + kLagTileMaxChunk;
     const int M = a.M, NJ = M / kKS, S = a.S;
 
@@ -584,10 +594,13 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
         }
     }
     if (threadIdx.x == 0) {
-        for (int i = 0; i < NS; ++i) {
+        for (int i = 0; i < NA; ++i) {
             mbar_init(smem_u32(&full_a[i]), kProducerWarps);
+            mbar_init(smem_u32(&empty_a[i]), 1);
+        }
+        for (int i = 0; i < NB; ++i) {
             mbar_init(smem_u32(&full_b[i]), 1);
-            mbar_init(smem_u32(&empty[i]), 1);
+            mbar_init(smem_u32(&empty_b[i]), 1);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(smem_u32(&acc_full[i]), 1);
@@ -619,13 +632,13 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                 stage_windows<FMT>(t, M, zs, sy1, sy2, threadIdx.x, kProducerWarps * 32);
                 asm volatile("bar.sync 1, %0;" ::"r"(kProducerWarps * 32) : "memory");
             }
-            int pL[2] = {0, 0}, pn0[2] = {0, 0};
-            bool pv[2] = {false, false};
+            int pL[kRowSets] = {}, pn0[kRowSets] = {};
+            bool pv[kRowSets] = {};
             if (!t.lay) {
                 const int64_t R = (int64_t)t.NB * t.Bs;
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int64_t g = (int64_t)t.ltile * kRows + 16 * warp + 8 * h + rin;
+                for (int h = 0; h < kRowSets; ++h) {
+                    const int64_t g = (int64_t)t.ltile * kRows + 8 * (kRowSets * warp + h) + rin;
                     if (g < R) {
                         const int bl = (int)(g / t.Bs);
                         pn0[h] = (int)(g % t.Bs) * M + 8 * kg;
@@ -637,8 +650,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
             const uint32_t g0 = (uint32_t)it * (uint32_t)NJ;
             for (int j = 0; j < NJ; ++j) {
                 const uint32_t g = g0 + (uint32_t)j;
-                const int slot = (int)(g % NS);
-                if (g >= NS && !mbar_wait(smem_u32(&empty[slot]), ((g / NS) - 1) & 1u)) s_abort = 1;
+                const int slot = (int)(g % NA);
+                if (g >= NA && !mbar_wait(smem_u32(&empty_a[slot]), ((g / NA) - 1) & 1u)) s_abort = 1;
                 if (s_abort) break;
                 unsigned char *sA = sA0 + slot * kSt;
                 float2 x[8];
@@ -652,8 +665,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                     }
                 }
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int row = 16 * warp + 8 * h + rin;
+                for (int h = 0; h < kRowSets; ++h) {
+                    const int row = 8 * (kRowSets * warp + h) + rin;
                     float2 y[8];
                     if (t.lay) {
                         const float2 *py = sy2 + j * kKS + 8 * kg + row;
@@ -701,42 +714,56 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                 if (lane == 0) mbar_arrive(smem_u32(&full_a[slot]));
             }
         }
-    } else if (warp == kProducerWarps) {
-        // ---------------- control (one thread): B copies, MMAs, commits
+    } else if (warp == kLoadWarp) {
+        // ---------------- operand loader (one thread): B of every stage of
+        // every tile, in order, into slot g % NB once the MMAs of stage
+        // g - NB are done; it runs ahead of the MMAs by up to NB stages,
+        // across tile boundaries
         if (lane == 0) {
-            const uint32_t id = idesc<DT>();
             for (int it = 0; it < mine && !s_abort; ++it) {
                 const uint32_t g0 = (uint32_t)it * (uint32_t)NJ;
                 const int s = step_of_tile(sc.tbase, S, (int)blockIdx.x + it * (int)gridDim.x);
                 const unsigned char *bsrc = reinterpret_cast<const unsigned char *>(a.btab) + (size_t)s * NJ * kSt;
-                // B of stage g goes into slot g % NS once the MMAs of stage g - NS are done
-                auto load_b = [&](uint32_t g) -> bool {
-                    const int slot = (int)(g % NS);
-                    if (g >= NS && !mbar_wait(smem_u32(&empty[slot]), ((g / NS) - 1) & 1u)) return false;
+                for (int j = 0; j < NJ; ++j) {
+                    const uint32_t g = g0 + (uint32_t)j;
+                    const int slot = (int)(g % NB);
+                    if ((g >= NB && !mbar_wait(smem_u32(&empty_b[slot]), ((g / NB) - 1) & 1u)) || s_abort) {
+                        s_abort = 1;
+                        break;
+                    }
                     mbar_expect_tx(smem_u32(&full_b[slot]), kSt);
-                    bulk_g2s(smem_u32(sB0 + slot * kSt), bsrc + (size_t)(g - g0) * kSt, kSt, smem_u32(&full_b[slot]));
-                    return true;
-                };
-                bool alive = true;
-                for (int t = 0; t < NS && t < NJ && alive; ++t) alive = load_b(g0 + (uint32_t)t);
+                    bulk_g2s(smem_u32(sB0 + slot * kSt), bsrc + (size_t)j * kSt, kSt, smem_u32(&full_b[slot]));
+                }
+            }
+        }
+    } else if (warp == kMmaWarp) {
+        // ---------------- MMA thread: waits for A and B of each stage,
+        // issues its MMAs and commits them to the stage's empty barriers; it
+        // waits on MMA completion only to reuse an accumulator
+        if (lane == 0) {
+            const uint32_t id = idesc<DT>();
+            bool alive = true;
+            for (int it = 0; it < mine && alive && !s_abort; ++it) {
+                const uint32_t g0 = (uint32_t)it * (uint32_t)NJ;
                 // the accumulator of this tile was drained (tile it - 2)
                 const int acc = it & 1;
-                if (alive && it >= 2 && !mbar_wait(smem_u32(&acc_empty[acc]), ((uint32_t)(it / 2) - 1) & 1u))
+                if (it >= 2 && !mbar_wait(smem_u32(&acc_empty[acc]), ((uint32_t)(it / 2) - 1) & 1u)) {
                     alive = false;
+                    break;
+                }
                 tc_after_sync();
                 const uint32_t dtm = tmem + (uint32_t)(128 * acc);
-                for (int j = 0; j < NJ && alive; ++j) {
+                for (int j = 0; j < NJ; ++j) {
                     const uint32_t g = g0 + (uint32_t)j;
-                    const int slot = (int)(g % NS);
-                    const uint32_t ph = (g / NS) & 1u;
-                    if (!mbar_wait(smem_u32(&full_a[slot]), ph) || !mbar_wait(smem_u32(&full_b[slot]), ph) ||
-                        s_abort) {
+                    const int sa = (int)(g % NA), sb = (int)(g % NB);
+                    if (!mbar_wait(smem_u32(&full_a[sa]), (g / NA) & 1u) ||
+                        !mbar_wait(smem_u32(&full_b[sb]), (g / NB) & 1u) || s_abort) {
                         alive = false;
                         break;
                     }
                     tc_after_sync();
-                    const unsigned char *sA = sA0 + slot * kSt;
-                    const unsigned char *sB = sB0 + slot * kSt;
+                    const unsigned char *sA = sA0 + sa * kSt;
+                    const unsigned char *sB = sB0 + sb * kSt;
                     constexpr int NPROD = P == 2 ? 3 : 1;
 #pragma unroll
                     for (int blk = 0; blk < 2; ++blk)
@@ -749,19 +776,15 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                                 const uint64_t bd = sdesc(smem_u32(sB + (2 * pb + blk) * kBlockBytes) + kk * 16);
                                 mma_f16(dtm, ad, bd, id, (j > 0 || blk > 0 || kk > 0 || pr > 0) ? 1u : 0u);
                             }
-                    mma_commit(smem_u32(&empty[slot]));
+                    mma_commit(smem_u32(&empty_a[sa]));
+                    mma_commit(smem_u32(&empty_b[sb]));
                     if (j == NJ - 1) mma_commit(smem_u32(&acc_full[acc]));  // the tile's accumulator is final
-                    // B of stage j - 1 + NS into the slot of stage j - 1
-                    if (j >= 1 && j - 1 + NS < NJ && !load_b(g - 1 + NS)) {
-                        alive = false;
-                        break;
-                    }
                 }
-                if (!alive) s_abort = 1;
             }
+            if (!alive) s_abort = 1;
         }
     } else {
-        // ---------------- drain finished accumulators: warps 9-12
+        // ---------------- drain finished accumulators: the last four warps
         const int q = warp & 3;
         for (int it = 1; it <= mine && !s_abort; ++it) {
             // drain tile it - 1
