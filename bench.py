@@ -122,7 +122,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -345,7 +345,7 @@ def run_dg(a, rank, world, local_rank):
         dom = max(("contract", "combine"), key=lambda n: kt[n][0])
         flops_per_step = contract_flops if dom == "contract" else combine_units * (1e12 if combine_hbm else 1)
         corr_ms, corr_launches = kt[dom]
-        roof_kernel = {"contract": (f"k_cdft_contract_mma ({a.contract} tcgen05, {chunk}-sample chunks x 64 bins)"
+        roof_kernel = {"contract": (f"k_cdft_contract_tc ({a.contract} tcgen05, {chunk}-sample chunks x 64 bins)"
                                     if tensor else f"k_cdft_contract_f32 (FP32 CUDA cores, {chunk}-sample chunks)"),
                        "combine": "k_cdft_superchunk + k_cdft_combine (per-candidate interpolation + super-chunk phase sum)"}[dom]
         roof_basis = kernels[dom]["basis"]
@@ -590,7 +590,7 @@ def _smi_id(local_rank):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["dg", "reference"], default="dg")
     ap.add_argument("--workload", choices=["mid", "tiny", "large", "batch"], default="mid")
