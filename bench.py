@@ -64,6 +64,28 @@ def workload(name, rank=0, world=1, grid=None):
     return s, desc
 
 
+# DRAM traffic of one contraction launch on the default workload, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the
+# kernel source it was measured on
+CONTRACT_TRAFFIC = {"source_sha1_16": "3b9b0650da12366a", "workload": "mid", "contract": "fp16x3", "chunk": 1024,
+                    "bytes_per_launch": 242.15e6}
+
+
+def contract_traffic(workload, contract, chunk):
+    import hashlib
+
+    src = os.path.join(ROOT, "paper_2508_06672_gb300", "csrc", "dg_cdft_mma.cu")
+    try:
+        with open(src, "rb") as f:
+            sha = hashlib.sha1(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    t = CONTRACT_TRAFFIC
+    if (sha, workload, contract, chunk) != (t["source_sha1_16"], t["workload"], t["contract"], t["chunk"]):
+        return None
+    return t["bytes_per_launch"]
+
+
 PEAK_BASIS_TENSOR = ("measured cuBLAS bf16 dense GEMM burst (MEASURED_PEAKS.json bf16_tflops); fp16 has the same "
                      "nominal dense rate (2.25 PFLOP/s)")
 
@@ -431,7 +453,9 @@ def run_dg(a, rank, world, local_rank):
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "roofline": {"bound": roof_bound, "achieved": achieved, "peak": peak, "unit": roof_unit,
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": (contract_traffic(a.workload, a.contract, chunk_hi)
+                                     if a.algo == "cdft" and roof_bound == "tensor" and not a.grid else None),
                          "kernel": roof_kernel,
                          "peak_basis": (PEAK_BASIS_TENSOR if roof_bound == "tensor" else
                                         "measured HBM copy (MEASURED_PEAKS.json hbm_gbs)" if roof_bound == "hbm"
