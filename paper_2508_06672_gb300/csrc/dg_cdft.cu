@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(1024) k_cdft_scan(CdftBatch a)
         a.gofs[b] = og;
         const int n = a.count[b];
         const int ng = (n + kCdftCombineGroup - 1) / kCdftCombineGroup;
-        for (int g = 0; g < ng; ++g) a.g2b[a.gbase[s] + og + g] = b;
+        for (int g = 0; g < ng; ++g) a.g2b[a.gbase[s] + og + g] = make_int2(b, s);
         oc += n;
         og += ng;
     }
@@ -485,10 +485,11 @@ __global__ void __launch_bounds__(kCdftCombineThreads) k_cdft_combine(CdftBatch 
     // snapshot's last are -1 in the scan's group-to-bucket map
     if (threadIdx.x == 0) {
         const int gid = blockIdx.x;
-        const int b = a.g2b[gid];
+        const int2 bs = a.g2b[gid];
+        const int b = bs.x;
         sh_b = b;
         if (b >= 0) {
-            const int s = step_of(a.gbase, a.S, gid);
+            const int s = bs.y;
             const int lgid = gid - a.gbase[s];
             sh_s = s;
             sh_first = (lgid - a.gofs[b]) * kCdftCombineGroup;

@@ -320,7 +320,7 @@ struct CdftBatch {
     float *candNu;                // [S][G] FDOA / fs
     int *order;                   // [S][G] candidates sorted by (bucket, bin)
     float *nuS;                   // [S][G] their FDOAs, in the same order
-    int *g2b;                     // [groups] global bucket of each combine group (-1: none)
+    int2 *g2b;                    // [groups] (bucket, snapshot) of each combine group (x = -1: none)
     int *count;                   // [NBT]
     int *offs, *gofs;             // [NBT]
     int *subcnt;                  // [NBT][64]
