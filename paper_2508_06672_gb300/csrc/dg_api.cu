@@ -544,7 +544,7 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         if ((st = grow(c, &b.count, n)) != DG_OK) return st;
         if ((st = grow(c, &b.offs, n)) != DG_OK) return st;
         if ((st = grow(c, &b.gofs, n)) != DG_OK) return st;
-        if ((st = grow(c, &b.subcnt, 64 * n)) != DG_OK) return st;
+        if ((st = grow(c, &b.subcnt, n)) != DG_OK) return st;
         b.nb_cap = n;
     }
     const size_t w_elems = (size_t)L.nbt_max * (size_t)B_max * 128;
@@ -664,7 +664,7 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
             CK(c, cudaMemsetAsync(b.g2b, 0xff, sizeof(int2) * (size_t)bt.groups, c->stream));
             CK(c, launch_cdft_plan(a, (int)bt.nbt, c->stream));
             CK(c, launch_cdft_tiles(a, c->stream));
-            t.done(mma ? 8 : 9);
+            t.done(mma ? 6 : 7);
         }
         {
             Timed t(c, refine ? DG_K_REFINE : DG_K_CDFT_CONTRACT);

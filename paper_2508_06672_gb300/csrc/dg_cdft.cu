@@ -24,10 +24,8 @@
 //   hist     count per (snapshot, lag) bucket, aggregated in shared memory;
 //   scan     one CTA per snapshot: bucket offsets, combine-group offsets and
 //            the snapshot's bins;
-//   subhist  count per (bucket, interpolation bin);
-//   subscan  offsets of the bins inside each bucket;
-//   scatter  candidate indices sorted by (bucket, interpolation bin), so that
-//            the warps of the combine read the same bins;
+//   scatter  candidate indices sorted by bucket (grid order within), and
+//            their FDOAs in the same order;
 //   contract W[bucket][chunk] = 64 bins, stored planar (64 real parts then 64
 //            imaginary parts); FP32 CUDA cores here, tensor cores in
 //            dg_cdft_mma.cu;
@@ -257,76 +255,26 @@ __global__ void __launch_bounds__(1024) k_cdft_scan(CdftBatch a)
     }
 }
 
-// Interpolation bin of a candidate: q0 in [0, 62], weight t of bin q0 + 1.
-__device__ __forceinline__ int bin_of(float nu, float nubase, float delta, float &t)
-{
-    const float u = (nu - nubase) / delta;
-    int q0 = (int)floorf(u);
-    q0 = max(0, min(62, q0));
-    t = u - (float)q0;
-    return q0;
-}
-
 // ---------------------------------------------------------------------------
-// subhist / subscan / scatter: counting sort by (bucket, bin).
+// scatter: counting sort by lag bucket (the offsets come from the scan).
+// Within a bucket the candidates keep about their grid order, so the
+// combine's surface writes stay close together.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_cdft_subhist(CdftBatch a)
-{
-    const int s = blockIdx.y;
-    const int lmin = a.lr[2 * s], bb = a.bbase[s];
-    if (a.lr[2 * s + 1] - lmin >= a.bbase[s + 1] - bb) return;  // reported by k_cdft_hist
-    const float delta = a.delta[s];
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.G; p += (int64_t)gridDim.x * blockDim.x) {
-        const int l = a.candL[(size_t)s * a.G + p];
-        if (l == INT_MIN) continue;
-        const int b = bb + l - lmin;
-        float t;
-        const int q0 = bin_of(a.candNu[(size_t)s * a.G + p], a.nubase[s], delta, t);
-        // neighbouring candidates share their (bucket, bin): one atomic per
-        // distinct key in the warp
-        const int key = b * 64 + q0;
-        const unsigned peers = __match_any_sync(__activemask(), key);
-        if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(a.subcnt + key, __popc(peers));
-    }
-}
-
-// One warp per bucket: exclusive scan of its 64 bin counts (in place).
-__global__ void __launch_bounds__(256) k_cdft_subscan(CdftBatch a, int NBT)
-{
-    const int b = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (b >= NBT) return;
-    int *c = a.subcnt + (size_t)b * 64;
-    const int v0 = c[2 * lane], v1 = c[2 * lane + 1];
-    int x = v0 + v1;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, d);
-        if (lane >= d) x += y;
-    }
-    const int ex = x - v0 - v1;
-    c[2 * lane] = ex;
-    c[2 * lane + 1] = ex + v0;
-}
-
 __global__ void __launch_bounds__(256) k_cdft_scatter(CdftBatch a)
 {
     const int s = blockIdx.y;
     const int lmin = a.lr[2 * s], bb = a.bbase[s];
     if (a.lr[2 * s + 1] - lmin >= a.bbase[s + 1] - bb) return;  // reported by k_cdft_hist
-    const float delta = a.delta[s];
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.G; p += (int64_t)gridDim.x * blockDim.x) {
         const int l = a.candL[(size_t)s * a.G + p];
         if (l == INT_MIN) continue;
         const int b = bb + l - lmin;
-        float t;
-        const int q0 = bin_of(a.candNu[(size_t)s * a.G + p], a.nubase[s], delta, t);
-        // one atomic per distinct (bucket, bin) in the warp; the peers take
+        // one atomic per distinct bucket in the warp; the peers take
         // consecutive positions in lane order
-        const int key = b * 64 + q0;
-        const unsigned peers = __match_any_sync(__activemask(), key);
+        const unsigned peers = __match_any_sync(__activemask(), b);
         const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
         int base = 0;
-        if (lane == leader) base = atomicAdd(a.subcnt + key, __popc(peers));
+        if (lane == leader) base = atomicAdd(a.subcnt + b, __popc(peers));
         base = __shfl_sync(peers, base, leader);
         const int pos = a.offs[b] + base + __popc(peers & ((1u << lane) - 1u));
         a.order[(size_t)s * a.G + pos] = (int)p;
@@ -465,8 +413,8 @@ __global__ void __launch_bounds__(256) k_cdft_superchunk(CdftBatch a, int NBT)
 }
 
 // ---------------------------------------------------------------------------
-// combine: kCdftCombineGroup candidates of one bucket per CTA (sorted by
-// interpolation bin), kCdftCombinePer per thread; the bucket's super-chunk
+// combine: kCdftCombineGroup candidates of one bucket per CTA,
+// kCdftCombinePer per thread; the bucket's super-chunk
 // DFTs stream through shared memory in segments of kSeg. Each candidate
 // interpolates the DFT of every super-chunk at its own FDOA from the three
 // nearest bins (quadratic Lagrange), rotates it by the super-chunk's phase
@@ -669,7 +617,7 @@ cudaError_t launch_cdft_plan(const CdftBatch &a, int NBT, cudaStream_t st)
 {
     cudaError_t e;
     if ((e = cudaMemsetAsync(a.count, 0, sizeof(int) * (size_t)NBT, st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(a.subcnt, 0, sizeof(int) * 64 * (size_t)NBT, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(a.subcnt, 0, sizeof(int) * (size_t)NBT, st)) != cudaSuccess) return e;
     const int64_t tiles = (int64_t)((a.nrows + kHistTile - 1) / kHistTile) * ((a.nlon + kHistTile - 1) / kHistTile);
     dim3 gh((unsigned)tiles, (unsigned)a.S);
     k_cdft_hist<<<gh, 256, 0, st>>>(a);
@@ -677,10 +625,6 @@ cudaError_t launch_cdft_plan(const CdftBatch &a, int NBT, cudaStream_t st)
     k_cdft_scan<<<a.S, 1024, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     dim3 gp(grid_for(a.G, 256 * 4, 152 * 8), (unsigned)a.S);
-    k_cdft_subhist<<<gp, 256, 0, st>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_cdft_subscan<<<(NBT + 7) / 8, 256, 0, st>>>(a, NBT);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_cdft_scatter<<<gp, 256, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (a.mma) return cudaSuccess;  // the FP32 table serves the CUDA-core contraction only

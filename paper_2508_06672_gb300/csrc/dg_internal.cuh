@@ -323,7 +323,7 @@ struct CdftBatch {
     int2 *g2b;                    // [groups] (bucket, snapshot) of each combine group (x = -1: none)
     int *count;                   // [NBT]
     int *offs, *gofs;             // [NBT]
-    int *subcnt;                  // [NBT][64]
+    int *subcnt;                  // [NBT] fill cursor of each bucket (scatter)
     float *nubase, *delta;        // [S] bins nu_q = nubase + q delta
     float2 *V;                    // [S][M][64] DFT table e^{j 2 pi nu_q m}
     float *W;                     // [NBT][Bmax][128]: per chunk 64 bins, re[64] | im[64]
