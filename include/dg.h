@@ -333,6 +333,62 @@ int64_t dg_launch_count(const dg_ctx *ctx);
 /* DG_ABI_VERSION of the loaded library. */
 int32_t dg_abi_version(void);
 
+/* --- learned proposal network: layers, forward and backward -------------
+ * Not in the paper. A small convolutional network maps coarse per-snapshot
+ * delay-Doppler maps, back-projected onto the footprint (dg_coarse_maps), to
+ * a heatmap of where the emitter is; the dense grid is then evaluated only
+ * around the heatmap's top regions. These calls are its layers, FP32, for
+ * inference and for training on the GPU.
+ *
+ * Tensors are dense NCHW float arrays in device memory (B images, C channels,
+ * H rows, W columns, W fastest). The calls are stateless and allocate
+ * nothing: they enqueue kernels on `stream` (a cudaStream_t of the current
+ * device, NULL = the legacy stream) and return; the caller owns every buffer
+ * and keeps it alive until the stream has run the work. Outputs must not
+ * alias inputs unless stated. Results are deterministic (fixed-order
+ * reductions). On DG_EINVAL nothing is launched; dg_nn_last_error() (per
+ * host thread) says why. */
+
+/* 3 x 3 cross-correlation, zero padding 1, stride 1, with bias:
+ *   y[n,o,i,j] = b[o] + sum_c sum_{u,v=0..2} w[o,c,u,v] x[n,c,i+u-1,j+v-1].
+ * x: B*Ci*H*W, w: Co*Ci*3*3, b: Co, y: B*Co*H*W. */
+dg_status dg_nn_conv3x3_forward(const float *x, const float *w, const float *b, float *y, int32_t B,
+                                int32_t Ci, int32_t Co, int32_t H, int32_t W, void *stream);
+
+/* Gradients of sum(dy * y) for the forward above, overwritten (not added):
+ *   dx[n,c,i,j] = sum_o sum_{u,v} w[o,c,u,v] dy[n,o,i-u+1,j-v+1]   (dx may be NULL: skipped)
+ *   dw[o,c,u,v] = sum_{n,i,j} dy[n,o,i,j] x[n,c,i+u-1,j+v-1]
+ *   db[o]       = sum_{n,i,j} dy[n,o,i,j]. */
+dg_status dg_nn_conv3x3_backward(const float *x, const float *w, const float *dy, float *dx, float *dw,
+                                 float *db, int32_t B, int32_t Ci, int32_t Co, int32_t H, int32_t W,
+                                 void *stream);
+
+/* h = max(z, 0) over n elements (h may equal z). */
+dg_status dg_nn_relu_forward(const float *z, float *h, int64_t n, void *stream);
+
+/* dz = dh where z > 0, else 0 (dz may equal dh). */
+dg_status dg_nn_relu_backward(const float *z, const float *dh, float *dz, int64_t n, void *stream);
+
+/* Floats of scratch dg_nn_bce_logits needs for n elements. */
+int64_t dg_nn_bce_scratch(int64_t n);
+
+/* Mean weighted binary cross-entropy of sigmoid(z) against targets t in
+ * [0, 1]: loss = mean(-p t log s(z) - (1 - t) log(1 - s(z))), p = pos_weight
+ * > 0, and its gradient grad = (p t (s - 1) + (1 - t) s) / n. z, t, grad: n
+ * floats; loss: one float (device); scratch: dg_nn_bce_scratch(n) floats. */
+dg_status dg_nn_bce_logits(const float *z, const float *t, float pos_weight, int64_t n, float *grad,
+                           float *loss, float *scratch, void *stream);
+
+/* One Adam step (Kingma & Ba, 2015) in place on p, m, v (n floats each),
+ * gradient g, step counting from 1:
+ *   m = b1 m + (1 - b1) g;  v = b2 v + (1 - b2) g^2;
+ *   p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps). */
+dg_status dg_nn_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float beta1,
+                     float beta2, float eps, int32_t step, void *stream);
+
+/* Message of the calling thread's last failed dg_nn_* call. */
+const char *dg_nn_last_error(void);
+
 /* --- cost surface without device allocation ---------------------------------
  * The paper has no counterpart to this call. It serves callers that may not
  * allocate GPU memory while they process data -- for example a real-time

@@ -31,6 +31,8 @@ __all__ = [
     "DG_CONTRACT_FP32", "DG_CONTRACT_BF16", "DG_CONTRACT_FP16", "DG_CONTRACT_BF16X3", "DG_CONTRACT_FP16X3",
     "DG_K_CORR", "DG_K_ACCUM", "DG_K_ARGMAX", "DG_K_GRID", "DG_K_REFINE", "EXPORTED_SYMBOLS",
     "DG_K_CDFT_PLAN", "DG_K_CDFT_CONTRACT", "DG_K_CDFT_COMBINE",
+    "dg_nn_conv3x3_forward", "dg_nn_conv3x3_backward", "dg_nn_relu_forward", "dg_nn_relu_backward",
+    "dg_nn_bce_logits", "dg_nn_adam", "dg_nn_last_error",
 ]
 
 DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_ESTATE, DG_ETIMEOUT, DG_EUNSUPPORTED = range(7)
@@ -61,6 +63,8 @@ EXPORTED_SYMBOLS = [
     "dg_noalloc_last_error", "dg_cdft_work", "dg_detect", "dg_cdft_chunks",
     "dg_graph_capture", "dg_graph_launch", "dg_graph_fix", "dg_batch_capture", "dg_batch_launch",
     "dg_batch_fixes", "dg_batch_launch_count", "dg_batch_destroy", "dg_autotune",
+    "dg_nn_conv3x3_forward", "dg_nn_conv3x3_backward", "dg_nn_relu_forward", "dg_nn_relu_backward",
+    "dg_nn_bce_scratch", "dg_nn_bce_logits", "dg_nn_adam", "dg_nn_last_error",
 ]
 DG_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
@@ -183,6 +187,20 @@ def lib():
             L.dg_cdft_work.restype = C.c_int
             L.dg_noalloc_last_error.argtypes = []
             L.dg_noalloc_last_error.restype = C.c_char_p
+            flt = C.c_float
+            L.dg_nn_conv3x3_forward.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, i32, vp]
+            L.dg_nn_conv3x3_backward.argtypes = [vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, i32, vp]
+            L.dg_nn_relu_forward.argtypes = [vp, vp, i64, vp]
+            L.dg_nn_relu_backward.argtypes = [vp, vp, vp, i64, vp]
+            L.dg_nn_bce_scratch.argtypes = [i64]
+            L.dg_nn_bce_scratch.restype = i64
+            L.dg_nn_bce_logits.argtypes = [vp, vp, flt, i64, vp, vp, vp, vp]
+            L.dg_nn_adam.argtypes = [vp, vp, vp, vp, i64, flt, flt, flt, flt, i32, vp]
+            for f in ("dg_nn_conv3x3_forward", "dg_nn_conv3x3_backward", "dg_nn_relu_forward",
+                      "dg_nn_relu_backward", "dg_nn_bce_logits", "dg_nn_adam"):
+                getattr(L, f).restype = C.c_int
+            L.dg_nn_last_error.argtypes = []
+            L.dg_nn_last_error.restype = C.c_char_p
             for name in ("dg_create", "dg_load_capture", "dg_cost_surface", "dg_argmax_refine",
                          "dg_sync", "dg_destroy", "dg_grid_ecef", "dg_step_geometry",
                          "dg_kernel_time", "dg_reset_counters"):
@@ -354,6 +372,97 @@ def dg_cost_surface_noalloc(grid, ephem, fs_hz, fc_hz, fmt, y1_ptr, y2_ptr, n_sa
                                        C.c_void_p(int(stream)))
     if st != DG_OK:
         raise DGError(st, dg_noalloc_last_error())
+
+
+# ------------------------------------------------- proposal-network layers
+# Thin marshalling over the dg_nn_* calls: torch CUDA tensors in (FP32,
+# contiguous, NCHW), pointers and sizes out; the kernels do all the work.
+def dg_nn_last_error():
+    m = lib().dg_nn_last_error()
+    return m.decode() if m else ""
+
+
+def _nn_check(st):
+    if st != DG_OK:
+        raise DGError(st, dg_nn_last_error())
+
+
+def _f32(*ts):
+    for t in ts:
+        if t is None:
+            continue
+        if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 4 and t.is_contiguous()):
+            raise ValueError("dg_nn_*: tensors must be contiguous float32 CUDA tensors")
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr() if t is not None else 0)
+
+
+def _stream(stream, t):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream(t.device)
+    return C.c_void_p(s.cuda_stream)
+
+
+def dg_nn_conv3x3_forward(x, w, b, y, stream=None):
+    """y = conv3x3(x, w) + b (NCHW; w: Co x Ci x 3 x 3)."""
+    _f32(x, w, b, y)
+    B, Ci, H, W = x.shape
+    Co = w.shape[0]
+    if tuple(w.shape) != (Co, Ci, 3, 3) or tuple(b.shape) != (Co,) or tuple(y.shape) != (B, Co, H, W):
+        raise ValueError("dg_nn_conv3x3_forward: shape mismatch")
+    _nn_check(lib().dg_nn_conv3x3_forward(_ptr(x), _ptr(w), _ptr(b), _ptr(y), B, Ci, Co, H, W,
+                                          _stream(stream, x)))
+
+
+def dg_nn_conv3x3_backward(x, w, dy, dx, dw, db, stream=None):
+    """Gradients of sum(dy * conv3x3(x, w, b)): dx (None: skipped), dw, db."""
+    _f32(x, w, dy, dx, dw, db)
+    B, Ci, H, W = x.shape
+    Co = w.shape[0]
+    if (tuple(dy.shape) != (B, Co, H, W) or tuple(dw.shape) != (Co, Ci, 3, 3) or tuple(db.shape) != (Co,)
+            or (dx is not None and tuple(dx.shape) != tuple(x.shape))):
+        raise ValueError("dg_nn_conv3x3_backward: shape mismatch")
+    _nn_check(lib().dg_nn_conv3x3_backward(_ptr(x), _ptr(w), _ptr(dy), _ptr(dx), _ptr(dw), _ptr(db),
+                                           B, Ci, Co, H, W, _stream(stream, x)))
+
+
+def dg_nn_relu_forward(z, h, stream=None):
+    _f32(z, h)
+    if z.numel() != h.numel():
+        raise ValueError("dg_nn_relu_forward: size mismatch")
+    _nn_check(lib().dg_nn_relu_forward(_ptr(z), _ptr(h), z.numel(), _stream(stream, z)))
+
+
+def dg_nn_relu_backward(z, dh, dz, stream=None):
+    _f32(z, dh, dz)
+    if not (z.numel() == dh.numel() == dz.numel()):
+        raise ValueError("dg_nn_relu_backward: size mismatch")
+    _nn_check(lib().dg_nn_relu_backward(_ptr(z), _ptr(dh), _ptr(dz), z.numel(), _stream(stream, z)))
+
+
+def dg_nn_bce_logits(z, t, pos_weight, grad, loss, scratch=None, stream=None):
+    """Mean weighted BCE on logits into loss (1 float) and its gradient into
+    grad; scratch: dg_nn_bce_scratch(n) floats (allocated here when None)."""
+    import torch
+    n = z.numel()
+    if scratch is None:
+        scratch = torch.empty(max(1, int(lib().dg_nn_bce_scratch(n))), dtype=torch.float32, device=z.device)
+    _f32(z, t, grad, loss, scratch)
+    if not (t.numel() == n == grad.numel()) or loss.numel() < 1 or scratch.numel() < lib().dg_nn_bce_scratch(n):
+        raise ValueError("dg_nn_bce_logits: size mismatch")
+    _nn_check(lib().dg_nn_bce_logits(_ptr(z), _ptr(t), float(pos_weight), n, _ptr(grad), _ptr(loss),
+                                     _ptr(scratch), _stream(stream, z)))
+
+
+def dg_nn_adam(p, g, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """One Adam step in place on p, m, v."""
+    _f32(p, g, m, v)
+    if not (p.numel() == g.numel() == m.numel() == v.numel()):
+        raise ValueError("dg_nn_adam: size mismatch")
+    _nn_check(lib().dg_nn_adam(_ptr(p), _ptr(g), _ptr(m), _ptr(v), p.numel(), float(lr), float(beta1),
+                               float(beta2), float(eps), int(step), _stream(stream, p)))
 
 
 # ------------------------------------------------------- torch-level object
