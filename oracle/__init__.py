@@ -61,6 +61,8 @@ def _bind(path):
                                   dp, dp, C.c_int64, C.c_int, C.c_int,
                                   C.POINTER(C.c_int64), C.c_int64, dp, dp, dp, C.c_int]
     L.dgo_cost_points.restype = C.c_int
+    L.dgo_node_geometry.argtypes = [C.POINTER(Grid), dp, C.c_int32, C.c_double, C.c_double, dp, dp]
+    L.dgo_node_geometry.restype = C.c_int
     L.dgo_argmax.argtypes = [dp, C.c_int64]
     L.dgo_argmax.restype = C.c_int64
     L.dgo_detect.argtypes = [dp, C.c_int32, C.c_int32, C.c_double, C.c_int32, C.c_int64, C.POINTER(C.c_int64)]
@@ -198,6 +200,19 @@ def cost_surface(grid, ephem, fs, fc, y1, y2, delay_mode=0, acc_mode=0, nthreads
     idx = np.arange(r0 * nlon, r1 * nlon, dtype=np.int64)
     c = cost_points(grid, ephem, fs, fc, y1, y2, idx, delay_mode, acc_mode, nthreads)
     return c.reshape(r1 - r0, nlon)
+
+
+def node_geometry(grid, ephem, fs, fc):
+    """Eq. 3-10 at every node: D (K, nlat, nlon) in samples and nu (K, nlat,
+    nlon) in cycles per sample."""
+    g = Grid.from_dict(grid)
+    eph = _f64c(ephem).reshape(-1, 12)
+    K = eph.shape[0]
+    D = np.empty((K, g.nlat, g.nlon))
+    nu = np.empty((K, g.nlat, g.nlon))
+    if lib().dgo_node_geometry(C.byref(g), _dp(eph), K, float(fs), float(fc), _dp(D), _dp(nu)) != 0:
+        raise MemoryError("dgo_node_geometry")
+    return D, nu
 
 
 def argmax(cost):

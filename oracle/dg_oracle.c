@@ -211,6 +211,28 @@ int dgo_cost_points(const dgo_grid *g, const double *eph, int32_t K, double fs, 
     return 0;
 }
 
+/* Eq. 3-10 at every node of a grid for K snapshots: D[k][p] = dtau * fs
+ * (samples) and nu[k][p] = dfreq / fs (cycles per sample), p = i * nlon + j.
+ * Returns 0, or -1 if the scratch allocation fails. */
+int dgo_node_geometry(const dgo_grid *g, const double *eph, int32_t K, double fs, double fc, double *D,
+                      double *nu)
+{
+    const int64_t G = (int64_t)g->nlat * g->nlon;
+    double *xyz = (double *)malloc(sizeof(double) * 3 * (size_t)(G > 0 ? G : 1));
+    if (!xyz) return -1;
+    dgo_grid_ecef(g, xyz);
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < G; ++p)
+        for (int32_t k = 0; k < K; ++k) {
+            double geo[4];
+            dgo_geometry(xyz + 3 * p, eph + 12 * (int64_t)k, fs, fc, geo);
+            D[k * G + p] = geo[2];
+            nu[k * G + p] = geo[3];
+        }
+    free(xyz);
+    return 0;
+}
+
 /* Maximum with ties broken by the lowest index; NaN never wins. -1 if none. */
 int64_t dgo_argmax(const double *cost, int64_t n)
 {
