@@ -155,7 +155,8 @@ enum { DG_K_CORR = 0, DG_K_ACCUM = 1, DG_K_ARGMAX = 2, DG_K_GRID = 3, DG_K_REFIN
        DG_K_CDFT_PLAN = 5,      /* CDFT: lag ranges, histograms, scans, scatters */
        DG_K_CDFT_CONTRACT = 6,  /* CDFT: the per-lag chunked DFT                 */
        DG_K_CDFT_COMBINE = 7,   /* CDFT: per-candidate sums over chunks          */
-       DG_K_NCLASS = 8 };
+       DG_K_COARSE = 8,         /* dg_coarse_maps: the whole coarse pipeline     */
+       DG_K_NCLASS = 9 };
 
 /* Defaults: INTEGER delay, POWER accumulation, FP32, DIRECT, whole grid, no
  * timing, CDFT automatic chunk / 64 bins / FP32 contraction. o must not be
@@ -332,6 +333,51 @@ int64_t dg_launch_count(const dg_ctx *ctx);
 
 /* DG_ABI_VERSION of the loaded library. */
 int32_t dg_abi_version(void);
+
+/* --- coarse delay-Doppler maps on the footprint ---------------------------
+ * Not in the paper as such: the input of the learned proposal. For each
+ * snapshot k the cross-ambiguity function (the delay-Doppler map of the
+ * two-step TDOA/FDOA method of Sec. I; Eq. 11 at an integer lag l and FDOA
+ * nu, before the magnitude)
+ *     X(l, nu) = sum_n y1[n] conj(y2[n + l]) exp(j 2 pi nu n)
+ * is sampled at every lag l0 .. l0 + nlag - 1 that the context's grid nodes
+ * take (Eq. 9, round half away from zero) and at `bins` frequencies
+ * nu_q = nu_lo + q delta spanning the nodes' FDOA range [nu_lo, nu_hi]
+ * (Eq. 10), delta = (nu_hi - nu_lo) / (bins - 1). It is computed in chunks of
+ * `chunk` samples, each turned at nu_c = (nu_lo + nu_hi) / 2 and combined at
+ * the bin frequencies (each sample's phase is then off by at most
+ * |nu_q - nu_c| (chunk - 1) cycles). A = |X|^2 and mu = mean(A).
+ *
+ * maps (device pointer, float[K][nlat - 1][nlon - 1]) receives, for each cell
+ * (i, j) -- the quadrilateral of nodes (i, j), (i + 1, j), (i, j + 1),
+ * (i + 1, j + 1) -- the largest A / mu over the lags from the smallest to the
+ * largest of its corners' lags and the bins from
+ * floor((nu_min - nu_lo) / delta) to ceil((nu_max - nu_lo) / delta), clipped
+ * (every bin when delta = 0), nu_min / nu_max its corners' FDOA extremes;
+ * 0 where mu = 0. bins = 0 picks 2 bins per Doppler resolution cell (1 / N)
+ * over the span, 16..256; chunk = 0 picks the longest power of two <= 1024
+ * with a phase error under 1/8 cycle. Needs every snapshot loaded, a context
+ * over the whole grid (no row shard; DG_EUNSUPPORTED) and >= 2 x 2 nodes.
+ * The context's delay mode, accumulation and precision do not apply.
+ * Enqueued on the context's stream; no host synchronisation. */
+typedef struct {
+    int32_t l0;       /* first lag of the snapshot's map (samples)            */
+    int32_t nlag;     /* lags in the map                                      */
+    double nu_lo;     /* first bin frequency (cycles per sample)              */
+    double delta;     /* bin spacing                                          */
+    double nu_c;      /* chunk turning frequency                              */
+    double mu;        /* mean of A over its nlag x bins entries               */
+} dg_coarse_step;
+
+dg_status dg_coarse_maps(dg_ctx *ctx, int32_t bins, int32_t chunk, float *maps);
+
+/* The last coarse maps' internals (tests): shape (host int32[3], may be NULL)
+ * = bins, chunk, lag capacity C; caf (device float[K][C][bins], may be NULL)
+ * receives A (lag l0 + t at row t, rows t >= nlag undefined); steps (host,
+ * K entries, may be NULL) receives the per-snapshot parameters, which
+ * synchronises the stream and reports latched errors. DG_ESTATE before the
+ * first dg_coarse_maps. */
+dg_status dg_coarse_inspect(dg_ctx *ctx, float *caf, dg_coarse_step *steps, int32_t *shape);
 
 /* --- learned proposal network: layers, forward and backward -------------
  * Not in the paper. A small convolutional network maps coarse per-snapshot

@@ -68,8 +68,10 @@ def bce_logits(z, t, pos_weight=1.0):
     log_s = -np.logaddexp(0.0, -z)        # log sigmoid(z)
     log_1ms = -np.logaddexp(0.0, z)       # log (1 - sigmoid(z))
     loss = np.mean(-pos_weight * t * log_s - (1.0 - t) * log_1ms)
-    s = 1.0 / (1.0 + np.exp(-z))
-    grad = (pos_weight * t * (s - 1.0) + (1.0 - t) * s) / z.size
+    # dL/dz = (p t (s - 1) + (1 - t) s) / n, with s - 1 = -(1 - s) taken as
+    # exp(log(1 - s)) so that it keeps its digits where s rounds to 1
+    s, one_minus_s = np.exp(log_s), np.exp(log_1ms)
+    grad = (-pos_weight * t * one_minus_s + (1.0 - t) * s) / z.size
     return loss, grad
 
 

@@ -88,6 +88,19 @@ struct LocalGrid {  // refinement buffers, grown on demand
     size_t g_cap = 0;
 };
 
+struct CoarseBufs {  // coarse delay-Doppler maps (dg_coarse_maps), grown on demand
+    int *lag = nullptr;
+    double *nu = nullptr;
+    int *lmm = nullptr;
+    unsigned long long *nmm = nullptr;
+    CoarseStep *st = nullptr;
+    float2 *P = nullptr;
+    float *A = nullptr;
+    double *part = nullptr;
+    size_t lag_cap = 0, nu_cap = 0, lmm_cap = 0, nmm_cap = 0, st_cap = 0, P_cap = 0, A_cap = 0, part_cap = 0;
+    int Q = 0, M = 0, nlag_cap = 0, nb_max = 0;  // shape of the last maps (Q = 0: none yet)
+};
+
 }  // namespace
 
 struct dg_ctx {
@@ -120,6 +133,7 @@ struct dg_ctx {
     unsigned *err_h = nullptr;          // pinned mirror
     LocalGrid loc;
     CdftBufs cd;
+    CoarseBufs co;
     int cd_chunk_min = 0, cd_chunk_max = 0;              // chunks it used
     // whole-step CUDA graph (dg_graph_*)
     ArgmaxResult *amax_fine = nullptr;  // refinement argmax (device)
@@ -1562,6 +1576,14 @@ dg_status dg_destroy(dg_ctx *c)
     fr(c->loc.surf);
     fr(c->loc.cost);
     fr(c->cd.lr);
+    fr(c->co.lag);
+    fr(c->co.nu);
+    fr(c->co.lmm);
+    fr(c->co.nmm);
+    fr(c->co.st);
+    fr(c->co.P);
+    fr(c->co.A);
+    fr(c->co.part);
     fr(c->cd.main_layout.bbase);
     fr(c->cd.main_layout.gbase);
     fr(c->cd.loc_layout.bbase);
@@ -1597,6 +1619,126 @@ dg_status dg_destroy(dg_ctx *c)
     if (c->err_h) cudaFreeHost(c->err_h);
     delete c;
     if (e != cudaSuccess) return fail(nullptr, DG_ECUDA, "dg_destroy: %s", cudaGetErrorString(e));
+    return DG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Coarse delay-Doppler maps back-projected onto the grid's cells.
+// ---------------------------------------------------------------------------
+dg_status dg_coarse_maps(dg_ctx *c, int32_t bins, int32_t chunk, float *maps)
+{
+    if (!c) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    c->err.clear();
+    if (!maps) return fail(c, DG_EINVAL, "maps is NULL");
+    if (c->gd.row0 != 0 || c->gd.nrows != c->gd.nlat)
+        return fail(c, DG_EUNSUPPORTED, "dg_coarse_maps needs a context over the whole grid (no row shard)");
+    if (c->gd.nlat < 2 || c->gd.nlon < 2) return fail(c, DG_EINVAL, "dg_coarse_maps needs at least 2 x 2 nodes");
+    if (bins != 0 && (bins < 2 || bins > 256)) return fail(c, DG_EINVAL, "bins %d outside 2..256 (0: auto)", bins);
+    if (chunk != 0 && (chunk < 1 || chunk > 4096 || (chunk & (chunk - 1))))
+        return fail(c, DG_EINVAL, "chunk %d is not a power of two in 1..4096 (0: auto)", chunk);
+    int nmax = 0;
+    for (int k = 0; k < c->K; ++k) {
+        if (!c->steps[k].loaded) return fail(c, DG_ESTATE, "snapshot %d has not been loaded", k);
+        nmax = std::max(nmax, (int)c->steps[k].n);
+    }
+    // planning from the host's lattice estimate of the FDOA span (25 % margin)
+    double span = 0.0;
+    for (int k = 0; k < c->K; ++k) span = std::max(span, fdoa_span(c, c->gd, k, 65));
+    span *= 1.25;
+    int M = chunk;
+    if (M == 0) {  // the chunk's phase error (nu_q - nu_c) m stays below 1/8 cycle
+        M = 1024;
+        while (M > 1 && 0.5 * span * M > 0.125) M >>= 1;
+    }
+    int Q = bins;
+    if (Q == 0) {  // two bins per Doppler resolution cell 1 / N
+        Q = (int)std::ceil(2.0 * nmax * span) + 1;
+        Q = std::min(256, std::max(16, (Q + 7) / 8 * 8));
+    }
+    const int nb_max = (nmax + M - 1) / M;
+    if (nb_max > 65535) return fail(c, DG_EUNSUPPORTED, "chunk %d leaves %d chunks (at most 65535)", M, nb_max);
+    const double diam = grid_diameter(c->gd);
+    int nlag_cap = 0;
+    for (int k = 0; k < c->K; ++k) nlag_cap = std::max(nlag_cap, lag_slots(c->eph_host[k], c->fs, diam));
+    const size_t KG = (size_t)c->K * (size_t)c->G, K = (size_t)c->K;
+    CoarseBufs &b = c->co;
+    dg_status st;
+    if ((st = ensure(c, (void **)&b.lag, &b.lag_cap, sizeof(int) * KG)) != DG_OK) return st;
+    if ((st = ensure(c, (void **)&b.nu, &b.nu_cap, sizeof(double) * KG)) != DG_OK) return st;
+    if ((st = ensure(c, (void **)&b.lmm, &b.lmm_cap, sizeof(int) * 2 * K)) != DG_OK) return st;
+    if ((st = ensure(c, (void **)&b.nmm, &b.nmm_cap, sizeof(unsigned long long) * 2 * K)) != DG_OK) return st;
+    if ((st = ensure(c, (void **)&b.st, &b.st_cap, sizeof(CoarseStep) * K)) != DG_OK) return st;
+    if ((st = ensure(c, (void **)&b.P, &b.P_cap, sizeof(float2) * K * nb_max * (size_t)nlag_cap)) != DG_OK) return st;
+    if ((st = ensure(c, (void **)&b.A, &b.A_cap, sizeof(float) * K * (size_t)nlag_cap * Q)) != DG_OK) return st;
+    if ((st = ensure(c, (void **)&b.part, &b.part_cap, sizeof(double) * K * coarse_bin_tiles(nlag_cap))) != DG_OK)
+        return st;
+    if ((st = push_steps(c)) != DG_OK) return st;
+    CoarseArgs a{};
+    a.xyz = c->xyz;
+    a.G = c->G;
+    a.nlat = c->gd.nlat;
+    a.nlon = c->gd.nlon;
+    a.eph = c->eph;
+    a.steps = c->steps_d;
+    a.K = c->K;
+    a.fs = c->fs;
+    a.lambda = c->lambda;
+    a.Q = Q;
+    a.M = M;
+    a.nlag_cap = nlag_cap;
+    a.nb_max = nb_max;
+    a.lag = b.lag;
+    a.nu = b.nu;
+    a.lmm = b.lmm;
+    a.nmm = b.nmm;
+    a.st = b.st;
+    a.P = b.P;
+    a.A = b.A;
+    a.part = b.part;
+    a.maps = maps;
+    a.err = c->err_d;
+    {
+        Timed t(c, DG_K_COARSE);
+        int n = 0;
+        CK(c, launch_coarse(a, c->stream, &n));
+        t.done(n);
+    }
+    CK(c, cudaMemcpyAsync(c->err_h, c->err_d, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    b.Q = Q;
+    b.M = M;
+    b.nlag_cap = nlag_cap;
+    b.nb_max = nb_max;
+    return DG_OK;
+}
+
+dg_status dg_coarse_inspect(dg_ctx *c, float *caf, dg_coarse_step *steps, int32_t *shape)
+{
+    if (!c) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    c->err.clear();
+    const CoarseBufs &b = c->co;
+    if (b.Q == 0) return fail(c, DG_ESTATE, "no coarse maps have been computed on this context");
+    if (shape) {
+        shape[0] = b.Q;
+        shape[1] = b.M;
+        shape[2] = b.nlag_cap;
+    }
+    if (caf)
+        CK(c, cudaMemcpyAsync(caf, b.A, sizeof(float) * (size_t)c->K * b.nlag_cap * b.Q, cudaMemcpyDeviceToDevice,
+                              c->stream));
+    if (steps) {
+        std::vector<CoarseStep> h(c->K);
+        CK(c, cudaMemcpyAsync(h.data(), b.st, sizeof(CoarseStep) * c->K, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        for (int k = 0; k < c->K; ++k) {
+            steps[k].l0 = h[k].l0;
+            steps[k].nlag = h[k].nlag;
+            steps[k].nu_lo = h[k].nu_lo;
+            steps[k].delta = h[k].delta;
+            steps[k].nu_c = h[k].nu_c;
+            steps[k].mu = h[k].mu;
+        }
+        return check_latched(c);
+    }
     return DG_OK;
 }
 

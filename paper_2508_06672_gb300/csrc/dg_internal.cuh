@@ -411,4 +411,38 @@ cudaError_t launch_make_fix(const ArgmaxResult *coarse, const ArgmaxResult *fine
 cudaError_t launch_argmax(const void *v, int64_t n, int prec, const GridDev &g, void *tmp,
                           ArgmaxResult *res, int *launches, cudaStream_t s, const ArgmaxResult *centre = nullptr);
 
+// ---------------------------------------------------------------------------
+// Coarse delay-Doppler maps back-projected onto the grid's cells (the input
+// of the learned proposal), csrc/dg_coarse.cu.
+// ---------------------------------------------------------------------------
+struct CoarseStep {
+    int l0, nlag;                 // lags l0 .. l0 + nlag - 1 (node lags, Eq. 9)
+    double nu_lo, delta, nu_c;    // bins nu_lo + q delta; chunk turning frequency
+    double mu;                    // mean of the map
+};
+
+struct CoarseArgs {
+    const double *xyz;            // [3][G] node ECEF (whole grid)
+    int64_t G;
+    int nlat, nlon;
+    const double *eph;            // [K][12]
+    const StepDesc *steps;        // [K]
+    int K;
+    double fs, lambda;
+    int Q, M, nlag_cap, nb_max;   // bins, chunk, lag and chunk capacities
+    int *lag;                     // [K][G] node lags
+    double *nu;                   // [K][G] node FDOAs
+    int *lmm;                     // [K][2] lag min / max
+    unsigned long long *nmm;      // [K][2] FDOA min / max (ordered keys)
+    CoarseStep *st;               // [K]
+    float2 *P;                    // [K][nb_max][nlag_cap] chunk sums
+    float *A;                     // [K][nlag_cap][Q] the maps |X|^2
+    double *part;                 // [K][ceil(nlag_cap / 32)] partial sums of A
+    float *maps;                  // [K][nlat - 1][nlon - 1]
+    unsigned *err;
+};
+int coarse_bin_tiles(int nlag_cap);
+// The whole coarse pipeline (7 launches; *launches += 7).
+cudaError_t launch_coarse(const CoarseArgs &a, cudaStream_t s, int *launches);
+
 }  // namespace dg

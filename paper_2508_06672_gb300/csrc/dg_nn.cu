@@ -185,8 +185,9 @@ __global__ void __launch_bounds__(256) k_bce(const float *__restrict__ z, const 
         const float sp_pos = fmaxf(zz, 0.f) + log1pf(expf(-fabsf(zz)));  // softplus(z)
         const float sp_neg = sp_pos - zz;                                  // softplus(-z)
         acc[0] += pw * tt * sp_neg + (1.f - tt) * sp_pos;
-        const float s = 1.f / (1.f + expf(-zz));
-        grad[k] = (pw * tt * (s - 1.f) + (1.f - tt) * s) / (float)n;
+        // s(z) - 1 = -s(-z), formed directly so that it keeps its digits at large z
+        const float s = 1.f / (1.f + expf(-zz)), sm = 1.f / (1.f + expf(zz));
+        grad[k] = ((1.f - tt) * s - pw * tt * sm) / (float)n;
     }
     float out[1];
     block_sum<1>(acc, out);

@@ -32,7 +32,7 @@ __all__ = [
     "DG_K_CORR", "DG_K_ACCUM", "DG_K_ARGMAX", "DG_K_GRID", "DG_K_REFINE", "EXPORTED_SYMBOLS",
     "DG_K_CDFT_PLAN", "DG_K_CDFT_CONTRACT", "DG_K_CDFT_COMBINE",
     "dg_nn_conv3x3_forward", "dg_nn_conv3x3_backward", "dg_nn_relu_forward", "dg_nn_relu_backward",
-    "dg_nn_bce_logits", "dg_nn_adam", "dg_nn_last_error",
+    "dg_nn_bce_logits", "dg_nn_adam", "dg_nn_last_error", "dg_coarse_step", "DG_K_COARSE",
 ]
 
 DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_ESTATE, DG_ETIMEOUT, DG_EUNSUPPORTED = range(7)
@@ -44,7 +44,7 @@ DG_ALGO_DIRECT, DG_ALGO_CDFT = 0, 1
 DG_CONTRACT_FP32, DG_CONTRACT_BF16, DG_CONTRACT_FP16, DG_CONTRACT_BF16X3, DG_CONTRACT_FP16X3 = 0, 1, 2, 3, 4
 DG_TILES_AUTO, DG_TILES_ROWS, DG_TILES_LAGS = 0, 1, 2
 DG_K_CORR, DG_K_ACCUM, DG_K_ARGMAX, DG_K_GRID, DG_K_REFINE = 0, 1, 2, 3, 4
-DG_K_CDFT_PLAN, DG_K_CDFT_CONTRACT, DG_K_CDFT_COMBINE = 5, 6, 7
+DG_K_CDFT_PLAN, DG_K_CDFT_CONTRACT, DG_K_CDFT_COMBINE, DG_K_COARSE = 5, 6, 7, 8
 
 _FMT = {"c64": DG_IQ_C64, "ci16": DG_IQ_CI16, "ci8": DG_IQ_CI8}
 _FMT_DTYPE = {DG_IQ_C64: np.float32, DG_IQ_CI16: np.int16, DG_IQ_CI8: np.int8}
@@ -65,6 +65,7 @@ EXPORTED_SYMBOLS = [
     "dg_batch_fixes", "dg_batch_launch_count", "dg_batch_destroy", "dg_autotune",
     "dg_nn_conv3x3_forward", "dg_nn_conv3x3_backward", "dg_nn_relu_forward", "dg_nn_relu_backward",
     "dg_nn_bce_scratch", "dg_nn_bce_logits", "dg_nn_adam", "dg_nn_last_error",
+    "dg_coarse_maps", "dg_coarse_inspect",
 ]
 DG_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
@@ -108,6 +109,14 @@ class dg_tuning(C.Structure):
 class dg_peak(C.Structure):
     _fields_ = [("index", C.c_int64), ("i", C.c_int32), ("j", C.c_int32), ("lat_deg", C.c_double),
                 ("lon_deg", C.c_double), ("value", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class dg_coarse_step(C.Structure):
+    _fields_ = [("l0", C.c_int32), ("nlag", C.c_int32), ("nu_lo", C.c_double), ("delta", C.c_double),
+                ("nu_c", C.c_double), ("mu", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -188,6 +197,10 @@ def lib():
             L.dg_noalloc_last_error.argtypes = []
             L.dg_noalloc_last_error.restype = C.c_char_p
             flt = C.c_float
+            L.dg_coarse_maps.argtypes = [vp, i32, i32, vp]
+            L.dg_coarse_maps.restype = C.c_int
+            L.dg_coarse_inspect.argtypes = [vp, vp, C.POINTER(dg_coarse_step), C.POINTER(i32)]
+            L.dg_coarse_inspect.restype = C.c_int
             L.dg_nn_conv3x3_forward.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, i32, vp]
             L.dg_nn_conv3x3_backward.argtypes = [vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, i32, vp]
             L.dg_nn_relu_forward.argtypes = [vp, vp, i64, vp]
@@ -604,6 +617,30 @@ class Geolocator:
 
     def cdft_work(self):
         return dg_cdft_work(self.ctx)
+
+    def coarse_maps(self, bins=0, chunk=0, out=None):
+        """Coarse delay-Doppler maps back-projected onto the grid's cells:
+        float32 (K, nlat - 1, nlon - 1) on the device (dg_coarse_maps)."""
+        torch = self.torch
+        shape = (self.K, int(self.grid["nlat"]) - 1, self.nlon - 1)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, device=self.device)
+        if out.dtype != torch.float32 or not out.is_cuda or not out.is_contiguous() or out.numel() < np.prod(shape):
+            raise ValueError("out must be a contiguous float32 CUDA tensor of K x (nlat-1) x (nlon-1)")
+        _check(lib().dg_coarse_maps(self.ctx, int(bins), int(chunk), C.c_void_p(out.data_ptr())), self.ctx)
+        return out
+
+    def coarse_inspect(self):
+        """(A as float32 (K, C, bins) on the device, per-snapshot parameters
+        [dict], (bins, chunk, C)) of the last coarse maps."""
+        torch = self.torch
+        shape = (C.c_int32 * 3)()
+        _check(lib().dg_coarse_inspect(self.ctx, None, None, shape), self.ctx)
+        Q, M, cap = shape[0], shape[1], shape[2]
+        A = torch.empty((self.K, cap, Q), dtype=torch.float32, device=self.device)
+        steps = (dg_coarse_step * self.K)()
+        _check(lib().dg_coarse_inspect(self.ctx, C.c_void_p(A.data_ptr()), steps, shape), self.ctx)
+        return A, [st.as_dict() for st in steps], (Q, M, cap)
 
     def cdft_chunks(self):
         """(shortest, longest) chunk the last CDFT surface used."""
