@@ -185,6 +185,31 @@ dg_status dg_create(const dg_grid *grid, const dg_ephem *eph, int32_t K, double 
 dg_status dg_load_capture(dg_ctx *ctx, int32_t step, int32_t fmt, const void *y1, const void *y2,
                           int64_t n_samples, int32_t is_device_ptr);
 
+/* Move the context to another grid (no counterpart in the paper): the
+ * snapshots, ephemerides and options stay, the candidate ECEF is recomputed
+ * on the stream and every plan that depends on the grid is dropped, so that
+ * one context with its captures loaded can search several regions in turn.
+ * The grid may have any size (the ECEF buffer grows when needed, a
+ * stream-ordered reallocation). Needs a context over the whole grid (no row
+ * shard; DG_EUNSUPPORTED). A CUDA graph captured on the old grid, and a batch
+ * holding the context, become stale (DG_ESTATE on launch until recaptured).
+ * grid is a host pointer read during the call. */
+dg_status dg_set_grid(dg_ctx *ctx, const dg_grid *grid);
+
+/* Search several regions in turn (no counterpart in the paper; the dense
+ * stage of a proposal-based search): for each of the n (1..256) grids in
+ * regions (host array, all with the same nlat x nlon), the context moves to
+ * it (dg_set_grid) and the cost surface of Algorithm 1 is written to
+ * costs + r * nlat * nlon (device, the context's precision, room for
+ * n * nlat * nlon values) with its argmax, all stream-ordered; then one host
+ * synchronisation, and the region whose argmax holds the largest cost (ties:
+ * the first) gets the dense re-evaluation of dg_argmax_refine, whose fix is
+ * written to *out (host). *best (host, may be NULL) receives that region's
+ * index. The context is left on that region's grid. Needs a context over the
+ * whole grid and every snapshot loaded. */
+dg_status dg_search_regions(dg_ctx *ctx, const dg_grid *regions, int32_t n, void *costs,
+                            double refine_spacing_m, double refine_window_m, dg_fix *out, int32_t *best);
+
 /* The cost surface of the shard (Eq. 11 summed over snapshots, Algorithm 1):
  * out[p] = sum_k |C_k(p)|^2 (or |C_k(p)|), p over the shard's nrows * nlon
  * nodes. out is a device pointer to float (FP32) or double (FP64) with room
@@ -401,13 +426,18 @@ dg_status dg_coarse_inspect(dg_ctx *ctx, float *caf, dg_coarse_step *steps, int3
 dg_status dg_nn_conv3x3_forward(const float *x, const float *w, const float *b, float *y, int32_t B,
                                 int32_t Ci, int32_t Co, int32_t H, int32_t W, void *stream);
 
+/* Floats of scratch dg_nn_conv3x3_backward needs for this shape (-1 if the
+ * shape is out of range). */
+int64_t dg_nn_conv3x3_scratch(int32_t B, int32_t Ci, int32_t Co, int32_t H, int32_t W);
+
 /* Gradients of sum(dy * y) for the forward above, overwritten (not added):
  *   dx[n,c,i,j] = sum_o sum_{u,v} w[o,c,u,v] dy[n,o,i-u+1,j-v+1]   (dx may be NULL: skipped)
  *   dw[o,c,u,v] = sum_{n,i,j} dy[n,o,i,j] x[n,c,i+u-1,j+v-1]
- *   db[o]       = sum_{n,i,j} dy[n,o,i,j]. */
+ *   db[o]       = sum_{n,i,j} dy[n,o,i,j].
+ * scratch: dg_nn_conv3x3_scratch(...) floats (device), for partial sums. */
 dg_status dg_nn_conv3x3_backward(const float *x, const float *w, const float *dy, float *dx, float *dw,
                                  float *db, int32_t B, int32_t Ci, int32_t Co, int32_t H, int32_t W,
-                                 void *stream);
+                                 float *scratch, void *stream);
 
 /* h = max(z, 0) over n elements (h may equal z). */
 dg_status dg_nn_relu_forward(const float *z, float *h, int64_t n, void *stream);

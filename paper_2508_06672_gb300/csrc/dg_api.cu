@@ -90,7 +90,7 @@ struct LocalGrid {  // refinement buffers, grown on demand
 
 struct CoarseBufs {  // coarse delay-Doppler maps (dg_coarse_maps), grown on demand
     int *lag = nullptr;
-    double *nu = nullptr;
+    float *nu = nullptr;
     int *lmm = nullptr;
     unsigned long long *nmm = nullptr;
     CoarseStep *st = nullptr;
@@ -113,6 +113,10 @@ struct dg_ctx {
     int sm_count = 1;
     GridDev gd{};
     int64_t G = 0;
+    int64_t xyz_cap = 0;                // nodes the ECEF buffer holds
+    ArgmaxResult *reg_res = nullptr;    // dg_search_regions: argmax per region (device)
+    ArgmaxResult *reg_host = nullptr;   // pinned mirror
+    size_t reg_cap = 0;
     double *xyz = nullptr;
     double *eph = nullptr;
     std::vector<dg_ephem> eph_host;
@@ -397,23 +401,33 @@ static double grid_diameter(const GridDev &g)
     return 1.1 * d + 1.0;
 }
 
-// FDOA span of snapshot k over the shard, from a lattice of nodes (its
-// corners, edges and interior; the FDOA field is smooth at these scales).
-static double fdoa_span(const dg_ctx *c, const GridDev &g, int k, int lattice)
+// FDOA span of every snapshot over the shard, from a lattice of nodes (its
+// corners, edges and interior; the FDOA field is smooth at these scales): up
+// to 65 x 65 nodes, fewer on small shards (at least 9 x 9, about one lattice
+// node per 8 grid nodes), the node positions computed once for all
+// snapshots.
+static void fdoa_spans(const dg_ctx *c, const GridDev &g, std::vector<double> &span)
 {
+    const int side = std::max(g.nrows, g.nlon);
+    const int lattice = std::min(65, std::max(9, side / 8 + 1));
     const int ni = std::min(lattice, g.nrows), nj = std::min(lattice, g.nlon);
-    double lo = 1e300, hi = -1e300;
+    std::vector<double> p(3 * (size_t)ni * nj);
     for (int a = 0; a < ni; ++a)
         for (int b = 0; b < nj; ++b) {
             const double i = g.row0 + (ni > 1 ? (double)a * (g.nrows - 1) / (ni - 1) : 0.0);
             const double j = nj > 1 ? (double)b * (g.nlon - 1) / (nj - 1) : 0.0;
-            double p[3];
-            host_node_ecef(g, std::round(i), std::round(j), p);
-            const double nu = host_nu(p, c->eph_host[k], c->fs, c->lambda);
+            host_node_ecef(g, std::round(i), std::round(j), &p[3 * ((size_t)a * nj + b)]);
+        }
+    span.assign(c->K, 0.0);
+    for (int k = 0; k < c->K; ++k) {
+        double lo = 1e300, hi = -1e300;
+        for (size_t q = 0; q < (size_t)ni * nj; ++q) {
+            const double nu = host_nu(&p[3 * q], c->eph_host[k], c->fs, c->lambda);
             lo = std::min(lo, nu);
             hi = std::max(hi, nu);
         }
-    return hi - lo;
+        span[k] = hi - lo;
+    }
 }
 
 // Chunk of a batch with chunk = 0: the longest power of two in
@@ -492,6 +506,27 @@ static dg_status cdft_layout(dg_ctx *c, const GridDev &gd, int64_t G, CdftLayout
 // within the context's target): geometry, plan (sort by lag
 // bucket and bin, bins, tiles), DFT tables, contraction, super-chunks,
 // combine. Then the ordered sum. No host synchronisation.
+// The ephemerides as double-float (hi, lo) pairs on the device, [K][24].
+static dg_status ensure_ephf(dg_ctx *c)
+{
+    CdftBufs &b = c->cd;
+    if (b.ephf_cap >= (size_t)c->K) return DG_OK;
+    dg_status st;
+    if ((st = grow(c, &b.ephf, 24 * (size_t)c->K)) != DG_OK) return st;
+    b.ephf_cap = (size_t)c->K;
+    std::vector<float> ef(24 * (size_t)c->K);
+    for (int k = 0; k < c->K; ++k) {
+        const double *v = &c->eph_host[k].p1[0];
+        for (int t = 0; t < 12; ++t) {
+            ef[24 * k + 2 * t] = (float)v[t];
+            ef[24 * k + 2 * t + 1] = (float)(v[t] - (double)ef[24 * k + 2 * t]);
+        }
+    }
+    // pageable source: staged before the call returns
+    CK(c, cudaMemcpyAsync(b.ephf, ef.data(), sizeof(float) * ef.size(), cudaMemcpyHostToDevice, c->stream));
+    return DG_OK;
+}
+
 dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int64_t G, void *surf, void *out,
                            bool refine)
 {
@@ -515,10 +550,7 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
     // FDOA spans for the automatic chunk, from the main grid (a refinement
     // grid lies around one of its nodes and spans far less)
     std::vector<double> &span = b.main_span;
-    if (c->opt.chunk == 0 && span.size() != (size_t)c->K) {
-        span.assign(c->K, 0.0);
-        for (int k = 0; k < c->K; ++k) span[k] = fdoa_span(c, c->gd, k, 65);
-    }
+    if (c->opt.chunk == 0 && span.size() != (size_t)c->K) fdoa_spans(c, c->gd, span);
     std::vector<int> Ms(L.batches.size());
     int M_max = 64, B_max = 1;
     for (size_t i = 0; i < L.batches.size(); ++i) {
@@ -594,17 +626,7 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         h = (float)d;
         l = (float)(d - (double)h);
     };
-    if (b.ephf_cap < (size_t)c->K) {
-        if ((st = grow(c, &b.ephf, 24 * (size_t)c->K)) != DG_OK) return st;
-        b.ephf_cap = (size_t)c->K;
-        std::vector<float> ef(24 * (size_t)c->K);
-        for (int k = 0; k < c->K; ++k) {
-            const double *v = &c->eph_host[k].p1[0];
-            for (int t = 0; t < 12; ++t) split(v[t], ef[24 * k + 2 * t], ef[24 * k + 2 * t + 1]);
-        }
-        // pageable source: staged before the call returns
-        CK(c, cudaMemcpyAsync(b.ephf, ef.data(), sizeof(float) * ef.size(), cudaMemcpyHostToDevice, c->stream));
-    }
+    if ((st = ensure_ephf(c)) != DG_OK) return st;
     if (b.xyzf_cap < (size_t)G) {
         if ((st = grow(c, &b.xyzf, 6 * (size_t)G)) != DG_OK) return st;
         b.xyzf_cap = (size_t)G;
@@ -852,6 +874,7 @@ dg_status dg_create(const dg_grid *grid, const dg_ephem *eph, int32_t K, double 
     CKC(cudaGetDevice(&c->device));
     CKC(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
     CKC(cudaMallocAsync((void **)&c->xyz, sizeof(double) * 3 * (size_t)c->G, c->stream));
+    c->xyz_cap = c->G;
     CKC(cudaMallocAsync((void **)&c->eph, sizeof(double) * 12 * (size_t)K, c->stream));
     CKC(cudaMallocAsync((void **)&c->steps_d, sizeof(StepDesc) * (size_t)K, c->stream));
     CKC(cudaMallocAsync((void **)&c->amax_res, sizeof(ArgmaxResult), c->stream));
@@ -870,6 +893,37 @@ dg_status dg_create(const dg_grid *grid, const dg_ephem *eph, int32_t K, double 
     CKC(cudaStreamSynchronize(c->stream));  // eph_host may not move before the copy ran
 #undef CKC
     *out = c;
+    return DG_OK;
+}
+
+dg_status dg_set_grid(dg_ctx *c, const dg_grid *grid)
+{
+    if (!c) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    c->err.clear();
+    dg_status st = validate_grid(c, grid);
+    if (st != DG_OK) return st;
+    if (c->gd.row0 != 0 || c->gd.nrows != c->grid.nlat)
+        return fail(c, DG_EUNSUPPORTED, "dg_set_grid needs a context over the whole grid (no row shard)");
+    const int64_t G = (int64_t)grid->nlat * grid->nlon;
+    if (G > c->xyz_cap) {
+        CK(c, cudaFreeAsync(c->xyz, c->stream));
+        c->xyz = nullptr;
+        c->xyz_cap = 0;
+        CK(c, cudaMallocAsync((void **)&c->xyz, sizeof(double) * 3 * (size_t)G, c->stream));
+        c->xyz_cap = G;
+    }
+    c->grid = *grid;
+    c->opt.row0 = 0;
+    c->opt.nrows = 0;
+    c->gd = make_griddev(*grid, 0, grid->nlat);
+    c->G = G;
+    c->cd.main_span.clear();  // FDOA spans of the old grid
+    ++c->steps_gen;           // graphs and batches recorded on the old grid are stale
+    {
+        Timed t(c, DG_K_GRID);
+        CK(c, launch_grid_ecef(c->gd, c->xyz, c->stream));
+        t.done(1);
+    }
     return DG_OK;
 }
 
@@ -1395,10 +1449,7 @@ dg_status dg_autotune(dg_ctx *c, void *cost, int32_t reps, dg_tuning *out)
     }
     // admissible chunks: the automatic rule's bound on the estimated spacing
     std::vector<double> &span = c->cd.main_span;
-    if (span.size() != (size_t)c->K) {
-        span.assign(c->K, 0.0);
-        for (int k = 0; k < c->K; ++k) span[k] = fdoa_span(c, c->gd, k, 65);
-    }
+    if (span.size() != (size_t)c->K) fdoa_spans(c, c->gd, span);
     double dmax = 0.0;
     for (int k = 0; k < c->K; ++k) dmax = std::max(dmax, span[k] * (1.0 + 1e-5) / 63.0);
     std::vector<int> chunks;
@@ -1576,6 +1627,7 @@ dg_status dg_destroy(dg_ctx *c)
     fr(c->loc.surf);
     fr(c->loc.cost);
     fr(c->cd.lr);
+    fr(c->reg_res);
     fr(c->co.lag);
     fr(c->co.nu);
     fr(c->co.lmm);
@@ -1615,6 +1667,7 @@ dg_status dg_destroy(dg_ctx *c)
     }
     cudaError_t e = cudaStreamSynchronize(s);
     if (c->amax_host) cudaFreeHost(c->amax_host);
+    if (c->reg_host) cudaFreeHost(c->reg_host);
     if (c->fix_host) cudaFreeHost(c->fix_host);
     if (c->err_h) cudaFreeHost(c->err_h);
     delete c;
@@ -1642,8 +1695,10 @@ dg_status dg_coarse_maps(dg_ctx *c, int32_t bins, int32_t chunk, float *maps)
         nmax = std::max(nmax, (int)c->steps[k].n);
     }
     // planning from the host's lattice estimate of the FDOA span (25 % margin)
+    std::vector<double> &spans = c->cd.main_span;  // cached until the grid changes
+    if (spans.size() != (size_t)c->K) fdoa_spans(c, c->gd, spans);
     double span = 0.0;
-    for (int k = 0; k < c->K; ++k) span = std::max(span, fdoa_span(c, c->gd, k, 65));
+    for (int k = 0; k < c->K; ++k) span = std::max(span, spans[k]);
     span *= 1.25;
     int M = chunk;
     if (M == 0) {  // the chunk's phase error (nu_q - nu_c) m stays below 1/8 cycle
@@ -1664,7 +1719,7 @@ dg_status dg_coarse_maps(dg_ctx *c, int32_t bins, int32_t chunk, float *maps)
     CoarseBufs &b = c->co;
     dg_status st;
     if ((st = ensure(c, (void **)&b.lag, &b.lag_cap, sizeof(int) * KG)) != DG_OK) return st;
-    if ((st = ensure(c, (void **)&b.nu, &b.nu_cap, sizeof(double) * KG)) != DG_OK) return st;
+    if ((st = ensure(c, (void **)&b.nu, &b.nu_cap, sizeof(float) * KG)) != DG_OK) return st;
     if ((st = ensure(c, (void **)&b.lmm, &b.lmm_cap, sizeof(int) * 2 * K)) != DG_OK) return st;
     if ((st = ensure(c, (void **)&b.nmm, &b.nmm_cap, sizeof(unsigned long long) * 2 * K)) != DG_OK) return st;
     if ((st = ensure(c, (void **)&b.st, &b.st_cap, sizeof(CoarseStep) * K)) != DG_OK) return st;
@@ -1673,8 +1728,19 @@ dg_status dg_coarse_maps(dg_ctx *c, int32_t bins, int32_t chunk, float *maps)
     if ((st = ensure(c, (void **)&b.part, &b.part_cap, sizeof(double) * K * coarse_bin_tiles(nlag_cap))) != DG_OK)
         return st;
     if ((st = push_steps(c)) != DG_OK) return st;
+    if ((st = ensure_ephf(c)) != DG_OK) return st;
+    if (c->cd.xyzf_cap < (size_t)c->G) {
+        if ((st = grow(c, &c->cd.xyzf, 6 * (size_t)c->G)) != DG_OK) return st;
+        c->cd.xyzf_cap = (size_t)c->G;
+    }
     CoarseArgs a{};
     a.xyz = c->xyz;
+    a.xyzf = c->cd.xyzf;
+    a.ephf = c->cd.ephf;
+    a.fsc_hi = (float)(c->fs / kC);
+    a.fsc_lo = (float)(c->fs / kC - (double)a.fsc_hi);
+    a.ilf_hi = (float)(1.0 / (c->lambda * c->fs));
+    a.ilf_lo = (float)(1.0 / (c->lambda * c->fs) - (double)a.ilf_hi);
     a.G = c->G;
     a.nlat = c->gd.nlat;
     a.nlon = c->gd.nlon;
@@ -1699,7 +1765,8 @@ dg_status dg_coarse_maps(dg_ctx *c, int32_t bins, int32_t chunk, float *maps)
     a.err = c->err_d;
     {
         Timed t(c, DG_K_COARSE);
-        int n = 0;
+        int n = 1;
+        CK(c, launch_ecef_split(c->xyz, c->G, c->cd.xyzf, c->stream));
         CK(c, launch_coarse(a, c->stream, &n));
         t.done(n);
     }
@@ -1739,6 +1806,66 @@ dg_status dg_coarse_inspect(dg_ctx *c, float *caf, dg_coarse_step *steps, int32_
         }
         return check_latched(c);
     }
+    return DG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Search of several regions with one host synchronisation.
+// ---------------------------------------------------------------------------
+dg_status dg_search_regions(dg_ctx *c, const dg_grid *regions, int32_t n, void *costs, double spacing_m,
+                            double window_m, dg_fix *out, int32_t *best)
+{
+    if (!c) return fail(nullptr, DG_EINVAL, "ctx is NULL");
+    c->err.clear();
+    if (!regions || !costs || !out) return fail(c, DG_EINVAL, "regions, costs and out must not be NULL");
+    if (n < 1 || n > 256) return fail(c, DG_EINVAL, "n = %d outside 1..256", n);
+    for (int r = 0; r < n; ++r) {
+        dg_status st = validate_grid(c, &regions[r]);
+        if (st != DG_OK) return st;
+        if (regions[r].nlat != regions[0].nlat || regions[r].nlon != regions[0].nlon)
+            return fail(c, DG_EINVAL, "regions must all have the same number of nodes");
+    }
+    for (int k = 0; k < c->K; ++k)
+        if (!c->steps[k].loaded) return fail(c, DG_ESTATE, "snapshot %d has not been loaded", k);
+    const int64_t G = (int64_t)regions[0].nlat * regions[0].nlon;
+    const size_t esz = c->opt.prec == DG_PREC_FP64 ? 8 : 4;
+    if (c->reg_cap < (size_t)n) {
+        if (c->reg_res) CK(c, cudaFreeAsync(c->reg_res, c->stream));
+        c->reg_res = nullptr;
+        if (c->reg_host) {
+            CK(c, cudaStreamSynchronize(c->stream));
+            cudaFreeHost(c->reg_host);
+            c->reg_host = nullptr;
+        }
+        c->reg_cap = 0;
+        CK(c, cudaMallocAsync((void **)&c->reg_res, sizeof(ArgmaxResult) * n, c->stream));
+        CK(c, cudaMallocHost((void **)&c->reg_host, sizeof(ArgmaxResult) * n));
+        c->reg_cap = (size_t)n;
+    }
+    dg_status st;
+    for (int r = 0; r < n; ++r) {
+        if ((st = dg_set_grid(c, &regions[r])) != DG_OK) return st;
+        if ((st = ensure(c, &c->surf, &c->surf_bytes, esz * (size_t)G * c->K)) != DG_OK) return st;
+        if ((st = ensure(c, &c->amax_tmp, &c->amax_tmp_bytes, argmax_tmp_bytes(G))) != DG_OK) return st;
+        void *cr = (char *)costs + esz * (size_t)G * r;
+        if ((st = run_surface(c, c->gd, c->xyz, G, c->surf, cr, false)) != DG_OK) return st;
+        int nl = 0;
+        {
+            Timed t(c, DG_K_ARGMAX);
+            CK(c, launch_argmax(cr, G, c->opt.prec, c->gd, c->amax_tmp, c->reg_res + r, &nl, c->stream));
+            t.done(nl);
+        }
+    }
+    CK(c, cudaMemcpyAsync(c->reg_host, c->reg_res, sizeof(ArgmaxResult) * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if ((st = check_latched(c)) != DG_OK) return st;
+    int b = -1;
+    for (int r = 0; r < n; ++r)
+        if (c->reg_host[r].idx >= 0 && (b < 0 || c->reg_host[r].val > c->reg_host[b].val)) b = r;
+    if (b < 0) return fail(c, DG_EINVAL, "no region holds a finite value");
+    if ((st = dg_set_grid(c, &regions[b])) != DG_OK) return st;
+    if ((st = dg_argmax_refine(c, (char *)costs + esz * (size_t)G * b, spacing_m, window_m, out)) != DG_OK) return st;
+    if (best) *best = b;
     return DG_OK;
 }
 

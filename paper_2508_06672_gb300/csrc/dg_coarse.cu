@@ -18,8 +18,9 @@
 // map over the delay-Doppler box of the cell).
 //
 // Kernels:
-//   k_coarse_init / k_coarse_geo / k_coarse_params   node lags and FDOAs (FP64
-//       geometry, Eq. 3-10), their ranges per snapshot, the map parameters;
+//   k_coarse_init / k_coarse_geo / k_coarse_params   node lags and FDOAs
+//       (double-float geometry, Eq. 3-10), their ranges per snapshot, the
+//       map parameters;
 //   k_caf_lags   the chunk sums: for one chunk and a tile of 896 lags, both
 //       sample windows sit in shared memory; each thread slides a register
 //       window of y2 across 7 consecutive lags (7 is odd, so the lanes'
@@ -40,7 +41,6 @@ constexpr int kCafThreads = 128;
 constexpr int kCafTile = kCafR * kCafThreads;     // lags per k_caf_lags CTA
 constexpr int kBinLags = 32;                      // lags per k_caf_bins CTA
 constexpr int kBinChunks = 32;                    // chunks staged at a time
-constexpr int kBinMaxPerThread = 32;              // Q <= 256 over 8 warps
 
 __device__ __forceinline__ float2 load_iq(const void *b, int fmt, int idx)
 {
@@ -71,27 +71,39 @@ __global__ void k_coarse_init(int *lmm, unsigned long long *nmm, int K)
     }
 }
 
-// One thread per (node, snapshot k = blockIdx.y): Eq. 3-10 in FP64, the lag of
-// Eq. 9 (round half away from zero) and the FDOA; block minima / maxima, then
-// one atomic per block.
+// One thread per (node, snapshot k = blockIdx.y): Eq. 3-10 in double-float
+// arithmetic on the FP32 pipes (ranges to about 1e-7 m), the lag of Eq. 9
+// (round half away from zero; decided by the FP64 expression where D lies
+// within 1e-6 of a rounding boundary) and the FDOA rounded to FP32; block
+// minima / maxima, then one atomic per warp.
 __global__ void __launch_bounds__(256) k_coarse_geo(CoarseArgs a)
 {
     const int k = blockIdx.y;
-    double e[12];
+    dfl ed[12];
 #pragma unroll
-    for (int t = 0; t < 12; ++t) e[t] = __ldg(a.eph + 12 * k + t);
+    for (int t = 0; t < 12; ++t) ed[t] = {__ldg(a.ephf + 24 * k + 2 * t), __ldg(a.ephf + 24 * k + 2 * t + 1)};
+    const dfl fsc = {a.fsc_hi, a.fsc_lo}, ilf = {a.ilf_hi, a.ilf_lo};
     int lmin = INT_MAX, lmax = INT_MIN;
     unsigned long long nmin = ~0ull, nmax = 0ull;
     const int64_t G = a.G;
+    const float *xf = a.xyzf;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < G; p += (int64_t)gridDim.x * blockDim.x) {
-        double D, nu;
-        geometry(a.xyz[p], a.xyz[G + p], a.xyz[2 * G + p], e, a.fs, a.lambda, D, nu);
-        const int L = lag_of(D, DG_DELAY_INTEGER);
+        dfl D;
+        float nu;
+        geometry_df({xf[p], xf[G + p]}, {xf[2 * G + p], xf[3 * G + p]}, {xf[4 * G + p], xf[5 * G + p]}, ed, fsc, ilf,
+                    D, nu);
+        int L;
+        if (!round_df(D, L)) {
+            double e[12], D64, nu64;
+            for (int t = 0; t < 12; ++t) e[t] = a.eph[12 * k + t];
+            geometry(a.xyz[p], a.xyz[G + p], a.xyz[2 * G + p], e, a.fs, a.lambda, D64, nu64);
+            L = lag_of(D64, DG_DELAY_INTEGER);
+        }
         a.lag[k * G + p] = L;
         a.nu[k * G + p] = nu;
         lmin = min(lmin, L);
         lmax = max(lmax, L);
-        const unsigned long long key = dkey(nu);
+        const unsigned long long key = dkey((double)nu);
         nmin = min(nmin, key);
         nmax = max(nmax, key);
     }
@@ -209,7 +221,9 @@ __global__ void __launch_bounds__(kCafThreads) k_caf_lags(CoarseArgs a)
 }
 
 // Xc at the Q bins for 32 lags of snapshot k = blockIdx.y; warp w takes the
-// bins w, w + 8, ...; A = |Xc|^2 and the block's sum of A (in a fixed order).
+// bins w, w + 8, ..., at most UQ of them (UQ >= Q / 8); A = |Xc|^2 and the
+// block's sum of A (in a fixed order).
+template <int UQ>
 __global__ void __launch_bounds__(256) k_caf_bins(CoarseArgs a)
 {
     extern __shared__ float2 sm[];
@@ -227,9 +241,9 @@ __global__ void __launch_bounds__(256) k_caf_bins(CoarseArgs a)
     const int nb = (a.steps[k].n + M - 1) / M;
     float2 *tw = sm;                       // [Q][32]
     float2 *ps = sm + Q * kBinChunks;      // [32 chunks][32 lags]
-    float xr[kBinMaxPerThread], xi[kBinMaxPerThread];
+    float xr[UQ], xi[UQ];
 #pragma unroll
-    for (int u = 0; u < kBinMaxPerThread; ++u) xr[u] = xi[u] = 0.f;
+    for (int u = 0; u < UQ; ++u) xr[u] = xi[u] = 0.f;
     for (int b0 = 0; b0 < nb; b0 += kBinChunks) {
         __syncthreads();
         for (int i = threadIdx.x; i < Q * kBinChunks; i += blockDim.x) {
@@ -249,7 +263,7 @@ __global__ void __launch_bounds__(256) k_caf_bins(CoarseArgs a)
         for (int bb = 0; bb < kBinChunks; ++bb) {
             const float2 p = ps[bb * kBinLags + lane];
 #pragma unroll
-            for (int u = 0; u < kBinMaxPerThread; ++u) {
+            for (int u = 0; u < UQ; ++u) {
                 const int q = wq + 8 * u;
                 if (q < Q) {
                     const float2 w = tw[q * kBinChunks + bb];
@@ -264,7 +278,7 @@ __global__ void __launch_bounds__(256) k_caf_bins(CoarseArgs a)
     if (t < st.nlag) {
         float *Ak = a.A + ((size_t)k * a.nlag_cap + t) * Q;
 #pragma unroll
-        for (int u = 0; u < kBinMaxPerThread; ++u) {
+        for (int u = 0; u < UQ; ++u) {
             const int q = wq + 8 * u;
             if (q < Q) {
                 const float v = fmaf(xr[u], xr[u], xi[u] * xi[u]);
@@ -310,7 +324,7 @@ __global__ void __launch_bounds__(256) k_coarse_backproject(CoarseArgs a)
     const int nlon = a.nlon, ncol = nlon - 1;
     const int64_t ncell = (int64_t)(a.nlat - 1) * ncol;
     const int *lag = a.lag + (size_t)k * a.G;
-    const double *nu = a.nu + (size_t)k * a.G;
+    const float *nu = a.nu + (size_t)k * a.G;
     const float *Ak = a.A + (size_t)k * a.nlag_cap * Q;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = c / ncol, j = c % ncol;
@@ -322,8 +336,8 @@ __global__ void __launch_bounds__(256) k_coarse_backproject(CoarseArgs a)
         for (int u = 0; u < 4; ++u) {
             la = min(la, lag[pc[u]]);
             lb = max(lb, lag[pc[u]]);
-            vmin = fmin(vmin, nu[pc[u]]);
-            vmax = fmax(vmax, nu[pc[u]]);
+            vmin = fmin(vmin, (double)nu[pc[u]]);
+            vmax = fmax(vmax, (double)nu[pc[u]]);
         }
         la = max(0, la - st.l0);
         lb = min(st.nlag - 1, lb - st.l0);
@@ -367,11 +381,14 @@ cudaError_t launch_coarse(const CoarseArgs &a, cudaStream_t s, int *launches)
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int ntb = coarse_bin_tiles(a.nlag_cap);
     const size_t bin_smem = sizeof(float2) * ((size_t)a.Q * kBinChunks + kBinChunks * kBinLags);
+    const int uq = (a.Q + 7) / 8;
+    auto bins = uq <= 1 ? k_caf_bins<1> : uq <= 2 ? k_caf_bins<2> : uq <= 4 ? k_caf_bins<4>
+              : uq <= 8 ? k_caf_bins<8> : uq <= 16 ? k_caf_bins<16> : k_caf_bins<32>;
     if (bin_smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_caf_bins, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_smem);
+        e = cudaFuncSetAttribute(bins, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bin_smem);
         if (e != cudaSuccess) return e;
     }
-    k_caf_bins<<<dim3(ntb, a.K), 256, bin_smem, s>>>(a);
+    bins<<<dim3(ntb, a.K), 256, bin_smem, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_caf_mean<<<a.K, 256, 0, s>>>(a, ntb);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

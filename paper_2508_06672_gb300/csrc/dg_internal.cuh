@@ -425,13 +425,17 @@ struct CoarseArgs {
     const double *xyz;            // [3][G] node ECEF (whole grid)
     int64_t G;
     int nlat, nlon;
+    const float *xyzf;            // [6][G] node ECEF as double-float (x hi, x lo, y hi, ...)
     const double *eph;            // [K][12]
+    const float *ephf;            // [K][24] ephemerides as double-float
     const StepDesc *steps;        // [K]
     int K;
     double fs, lambda;
+    float fsc_hi, fsc_lo;         // fs / c as double-float
+    float ilf_hi, ilf_lo;         // 1 / (lambda fs) as double-float
     int Q, M, nlag_cap, nb_max;   // bins, chunk, lag and chunk capacities
     int *lag;                     // [K][G] node lags
-    double *nu;                   // [K][G] node FDOAs
+    float *nu;                    // [K][G] node FDOAs
     int *lmm;                     // [K][2] lag min / max
     unsigned long long *nmm;      // [K][2] FDOA min / max (ordered keys)
     CoarseStep *st;               // [K]

@@ -9,11 +9,14 @@
 //   relu, its backward, the weighted binary cross-entropy on logits (loss and
 //   gradient), and one Adam step.
 //
-// The network is small (tens of channels on a coarse map), so the kernels
-// are direct: each thread of the convolutions produces one pixel for
-// kOB output channels, reusing each input value kOB times from registers;
-// the weight reductions are one CTA per (o, c) pair with a fixed-order tree,
-// so every gradient is deterministic.
+// The convolutions are direct, FP32: each CTA stages a 16 x 32 pixel tile
+// of one input channel (with its halo) and the matching 3 x 3 x 16 weights in
+// shared memory and accumulates 16 output channels over all input channels;
+// the data gradient is the same kernel on the flipped, transposed weights.
+// The weight and bias gradients are summed per (8 output channels, input
+// channel, pixel split), then over the splits in a fixed order, so every
+// result is deterministic.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 
@@ -22,82 +25,168 @@
 namespace dg {
 
 namespace {
-constexpr int kOB = 8;  // output channels per thread (forward and data backward)
+// Convolution tiles: a CTA of 128 threads computes a 16 x 32 pixel tile of
+// 16 output channels; thread (ty, tx) owns 4 neighbouring pixels of row ty
+// for all 16 channels (64 accumulators). Per input channel the 18 x 34 input
+// window (with its halo) and the 9 x 16 weights sit in shared memory; per
+// kernel row a thread reads 6 inputs and, per tap, 16 weights (4 float4
+// broadcasts) for 64 FMAs.
+constexpr int kTH = 16, kTW = 32, kOC = 16, kPX = 4;
+constexpr int kXR = kTH + 2, kXC = kTW + 2, kXS = kTW + 4;  // window rows, columns, row stride
 
-__global__ void __launch_bounds__(256) k_conv3x3_fwd(const float *__restrict__ x, const float *__restrict__ w,
-                                                      const float *__restrict__ b, float *__restrict__ y, int B,
-                                                      int Ci, int Co, int H, int W)
+// y = conv(x) (+ b), or, with TR, the data gradient of a convolution: then x
+// is dy (CI = that convolution's output channels), y is dx (CO = its input
+// channels) and w keeps that convolution's [CI][CO][3][3] layout, read with
+// the taps flipped.
+template <bool TR>
+__global__ void __launch_bounds__(128) k_conv3x3_tiled(const float *__restrict__ x, const float *__restrict__ w,
+                                                        const float *__restrict__ b, float *__restrict__ y, int CI,
+                                                        int CO, int H, int W)
 {
-    const int nob = (Co + kOB - 1) / kOB;
-    const int64_t total = (int64_t)B * nob * H * W;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int j = (int)(t % W), i = (int)((t / W) % H);
-        const int ob = (int)((t / ((int64_t)W * H)) % nob), n = (int)(t / ((int64_t)W * H * nob));
-        const int o0 = ob * kOB;
-        float acc[kOB];
+    __shared__ __align__(16) float xs[kXR][kXS];
+    __shared__ __align__(16) float ws[9][kOC];
+    const int ocb = (CO + kOC - 1) / kOC;
+    const int n = blockIdx.z / ocb, oc0 = (blockIdx.z % ocb) * kOC;
+    const int i0 = blockIdx.y * kTH, j0 = blockIdx.x * kTW;
+    const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+    float acc[kOC][kPX];
 #pragma unroll
-        for (int k = 0; k < kOB; ++k) acc[k] = (o0 + k < Co) ? b[o0 + k] : 0.f;
-        for (int c = 0; c < Ci; ++c) {
-            const float *xc = x + ((size_t)n * Ci + c) * H * W;
+    for (int o = 0; o < kOC; ++o)
 #pragma unroll
-            for (int u = 0; u < 3; ++u) {
-                const int ii = i + u - 1;
-                if (ii < 0 || ii >= H) continue;
+        for (int p = 0; p < kPX; ++p) acc[o][p] = 0.f;
+    for (int ic = 0; ic < CI; ++ic) {
+        __syncthreads();
+        const float *xc = x + ((size_t)n * CI + ic) * H * W;
+        for (int idx = threadIdx.x; idx < kXR * kXC; idx += 128) {
+            const int r = idx / kXC, cc = idx % kXC;
+            const int gi = i0 + r - 1, gj = j0 + cc - 1;
+            xs[r][cc] = (gi >= 0 && gi < H && gj >= 0 && gj < W) ? __ldg(xc + (size_t)gi * W + gj) : 0.f;
+        }
+        for (int idx = threadIdx.x; idx < 9 * kOC; idx += 128) {
+            const int t = idx / kOC, o = idx % kOC, oc = oc0 + o;
+            float v = 0.f;
+            if (oc < CO)
+                v = TR ? __ldg(w + ((size_t)ic * CO + oc) * 9 + (8 - t)) : __ldg(w + ((size_t)oc * CI + ic) * 9 + t);
+            ws[t][o] = v;
+        }
+        __syncthreads();
 #pragma unroll
-                for (int v = 0; v < 3; ++v) {
-                    const int jj = j + v - 1;
-                    if (jj < 0 || jj >= W) continue;
-                    const float xv = __ldg(xc + (size_t)ii * W + jj);
+        for (int u = 0; u < 3; ++u) {
+            const float4 xa = *reinterpret_cast<const float4 *>(&xs[ty + u][4 * tx]);
+            const float2 xb = *reinterpret_cast<const float2 *>(&xs[ty + u][4 * tx + 4]);
+            const float xr[6] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y};
 #pragma unroll
-                    for (int k = 0; k < kOB; ++k)
-                        if (o0 + k < Co) acc[k] = fmaf(__ldg(w + (((size_t)(o0 + k) * Ci + c) * 3 + u) * 3 + v), xv, acc[k]);
+            for (int v = 0; v < 3; ++v) {
+#pragma unroll
+                for (int o4 = 0; o4 < kOC / 4; ++o4) {
+                    const float4 wv = *reinterpret_cast<const float4 *>(&ws[3 * u + v][4 * o4]);
+                    const float wo[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+#pragma unroll
+                        for (int p = 0; p < kPX; ++p) acc[4 * o4 + q][p] = fmaf(wo[q], xr[p + v], acc[4 * o4 + q][p]);
                 }
             }
         }
-#pragma unroll
-        for (int k = 0; k < kOB; ++k)
-            if (o0 + k < Co) y[(((size_t)n * Co + o0 + k) * H + i) * W + j] = acc[k];
     }
-}
-
-// dx: the transposed convolution of dy with w (flipped taps, channels swapped)
-__global__ void __launch_bounds__(256) k_conv3x3_bwd_data(const float *__restrict__ dy, const float *__restrict__ w,
-                                                           float *__restrict__ dx, int B, int Ci, int Co, int H,
-                                                           int W)
-{
-    const int ncb = (Ci + kOB - 1) / kOB;
-    const int64_t total = (int64_t)B * ncb * H * W;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int j = (int)(t % W), i = (int)((t / W) % H);
-        const int cb = (int)((t / ((int64_t)W * H)) % ncb), n = (int)(t / ((int64_t)W * H * ncb));
-        const int c0 = cb * kOB;
-        float acc[kOB];
+    const int i = i0 + ty;
+    if (i >= H) return;
 #pragma unroll
-        for (int k = 0; k < kOB; ++k) acc[k] = 0.f;
-        for (int o = 0; o < Co; ++o) {
-            const float *dyo = dy + ((size_t)n * Co + o) * H * W;
+    for (int o = 0; o < kOC; ++o) {
+        const int oc = oc0 + o;
+        if (oc >= CO) break;
+        const float bias = b ? __ldg(b + oc) : 0.f;
+        float *yr = y + (((size_t)n * CO + oc) * H + i) * W;
 #pragma unroll
-            for (int u = 0; u < 3; ++u) {
-                const int ii = i - u + 1;
-                if (ii < 0 || ii >= H) continue;
-#pragma unroll
-                for (int v = 0; v < 3; ++v) {
-                    const int jj = j - v + 1;
-                    if (jj < 0 || jj >= W) continue;
-                    const float g = __ldg(dyo + (size_t)ii * W + jj);
-#pragma unroll
-                    for (int k = 0; k < kOB; ++k)
-                        if (c0 + k < Ci) acc[k] = fmaf(__ldg(w + (((size_t)o * Ci + c0 + k) * 3 + u) * 3 + v), g, acc[k]);
-                }
-            }
+        for (int p = 0; p < kPX; ++p) {
+            const int j = j0 + 4 * tx + p;
+            if (j < W) yr[j] = acc[o][p] + bias;
         }
-#pragma unroll
-        for (int k = 0; k < kOB; ++k)
-            if (c0 + k < Ci) dx[(((size_t)n * Ci + c0 + k) * H + i) * W + j] = acc[k];
     }
 }
 
-// Fixed-order block sum of 9 (or 1) values per thread: 256 threads.
+// Weight and bias gradients, first pass: CTA (o-block of 8, input channel c,
+// pixel split s) sums dy[n,o,p] x[n,c,p + tap] over its share of the B*H*W
+// pixels, 9 taps x 8 output channels per thread, then a fixed-order
+// reduction over the CTA; partial[s][o][c][tap] (and, for c = 0,
+// partial_b[s][o]).
+constexpr int kDwO = 8;
+
+__global__ void __launch_bounds__(256) k_conv3x3_dw(const float *__restrict__ x, const float *__restrict__ dy,
+                                                     float *__restrict__ part, float *__restrict__ part_b, int B,
+                                                     int Ci, int Co, int H, int W, int S)
+{
+    __shared__ float red[8][kDwO * 10];
+    const int ob = blockIdx.x, c = blockIdx.y, s = blockIdx.z;
+    const int o0 = ob * kDwO;
+    const int64_t HW = (int64_t)H * W, P = (int64_t)B * HW;
+    const int64_t p0 = P * s / S, p1 = P * (s + 1) / S;
+    float acc[kDwO][10];  // 9 taps + the bias term
+#pragma unroll
+    for (int o = 0; o < kDwO; ++o)
+#pragma unroll
+        for (int t = 0; t < 10; ++t) acc[o][t] = 0.f;
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        const int64_t n = p / HW, q = p % HW;
+        const int i = (int)(q / W), j = (int)(q % W);
+        const float *xc = x + ((size_t)n * Ci + c) * HW;
+        float xv[9];
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+                const int ii = i + u - 1, jj = j + v - 1;
+                xv[3 * u + v] = (ii >= 0 && ii < H && jj >= 0 && jj < W) ? __ldg(xc + (size_t)ii * W + jj) : 0.f;
+            }
+#pragma unroll
+        for (int o = 0; o < kDwO; ++o) {
+            if (o0 + o >= Co) break;
+            const float g = __ldg(dy + ((size_t)n * Co + o0 + o) * HW + q);
+#pragma unroll
+            for (int t = 0; t < 9; ++t) acc[o][t] = fmaf(g, xv[t], acc[o][t]);
+            acc[o][9] += g;
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 0; o < kDwO; ++o)
+#pragma unroll
+        for (int t = 0; t < 10; ++t) {
+            float v = acc[o][t];
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+            if (lane == 0) red[warp][o * 10 + t] = v;
+        }
+    __syncthreads();
+    for (int e = threadIdx.x; e < kDwO * 10; e += blockDim.x) {
+        const int o = e / 10, t = e % 10;
+        if (o0 + o >= Co) continue;
+        float v = 0.f;
+        for (int q = 0; q < 8; ++q) v += red[q][e];
+        if (t < 9) part[(((size_t)s * Co + o0 + o) * Ci + c) * 9 + t] = v;
+        else if (c == 0) part_b[(size_t)s * Co + o0 + o] = v;
+    }
+}
+
+// Second pass: dw = sum over splits in order; db likewise.
+__global__ void k_conv3x3_dw_sum(const float *__restrict__ part, const float *__restrict__ part_b,
+                                 float *__restrict__ dw, float *__restrict__ db, int Co, int Ci, int S)
+{
+    const int64_t nw = (int64_t)Co * Ci * 9;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nw + Co; e += (int64_t)gridDim.x * blockDim.x) {
+        float v = 0.f;
+        if (e < nw) {
+            for (int s = 0; s < S; ++s) v += part[(size_t)s * nw + e];
+            dw[e] = v;
+        } else {
+            const int64_t o = e - nw;
+            for (int s = 0; s < S; ++s) v += part_b[(size_t)s * Co + o];
+            db[o] = v;
+        }
+    }
+}
+
+// Fixed-order block sum of V values per thread (256 threads).
 template <int V>
 __device__ __forceinline__ void block_sum(float (&v)[V], float (&out)[V])
 {
@@ -118,47 +207,6 @@ __device__ __forceinline__ void block_sum(float (&v)[V], float (&out)[V])
             for (int q = 0; q < 8; ++q) s += sm[q][k];
             out[k] = s;
         }
-}
-
-// One CTA per (o, c): the 9 taps of dw[o, c]; the CTAs with c == 0 also
-// give db[o].
-__global__ void __launch_bounds__(256) k_conv3x3_bwd_weight(const float *__restrict__ x, const float *__restrict__ dy,
-                                                             float *__restrict__ dw, float *__restrict__ db, int B,
-                                                             int Ci, int Co, int H, int W)
-{
-    const int o = blockIdx.x / Ci, c = blockIdx.x % Ci;
-    float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    float accb[1] = {0.f};
-    const int64_t HW = (int64_t)H * W;
-    for (int n = 0; n < B; ++n) {
-        const float *dyo = dy + ((size_t)n * Co + o) * HW;
-        const float *xc = x + ((size_t)n * Ci + c) * HW;
-        for (int64_t p = threadIdx.x; p < HW; p += blockDim.x) {
-            const int i = (int)(p / W), j = (int)(p % W);
-            const float g = __ldg(dyo + p);
-            if (c == 0) accb[0] += g;
-#pragma unroll
-            for (int u = 0; u < 3; ++u) {
-                const int ii = i + u - 1;
-#pragma unroll
-                for (int v = 0; v < 3; ++v) {
-                    const int jj = j + v - 1;
-                    const float xv = (ii >= 0 && ii < H && jj >= 0 && jj < W) ? __ldg(xc + (size_t)ii * W + jj) : 0.f;
-                    acc[3 * u + v] = fmaf(g, xv, acc[3 * u + v]);
-                }
-            }
-        }
-    }
-    float out[9];
-    block_sum<9>(acc, out);
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 9; ++k) dw[((size_t)o * Ci + c) * 9 + k] = out[k];
-    if (c == 0) {
-        __syncthreads();
-        float ob[1];
-        block_sum<1>(accb, ob);
-        if (threadIdx.x == 0) db[o] = ob[0];
-    }
 }
 
 __global__ void k_relu_fwd(const float *__restrict__ z, float *__restrict__ h, int64_t n)
@@ -247,29 +295,51 @@ dg_status nn_done(cudaError_t e, const char *what)
 bool conv_shape_ok(int B, int Ci, int Co, int H, int W)
 {
     return B > 0 && Ci > 0 && Co > 0 && H > 0 && W > 0 && Ci <= 4096 && Co <= 4096 &&
+           (int64_t)B * ((std::max(Ci, Co) + 15) / 16) <= 65535 && (H + 15) / 16 <= 65535 &&
            (int64_t)H * W <= (int64_t)1 << 30 && (int64_t)B * Ci * H * W <= ((int64_t)1 << 40) &&
            (int64_t)B * Co * H * W <= ((int64_t)1 << 40) && (int64_t)Co * Ci <= ((int64_t)1 << 31) - 1;
 }
 }  // namespace
 
+int64_t nn_conv_splits(int B, int Ci, int Co, int H, int W)
+{
+    const int64_t ctas = (int64_t)((Co + kDwO - 1) / kDwO) * Ci;
+    const int64_t P = (int64_t)B * H * W;
+    int64_t S = (152 * 4 + ctas - 1) / ctas;     // about four CTAs per SM
+    S = std::min<int64_t>(S, std::max<int64_t>(1, P / 2048));
+    return std::max<int64_t>(1, std::min<int64_t>(S, 1024));
+}
+
+int64_t nn_conv_scratch(int B, int Ci, int Co, int H, int W)
+{
+    return nn_conv_splits(B, Ci, Co, H, W) * ((int64_t)Co * Ci * 9 + Co);
+}
+
 cudaError_t launch_nn_conv_fwd(const float *x, const float *w, const float *b, float *y, int B, int Ci, int Co, int H,
                                int W, cudaStream_t s)
 {
-    const int64_t total = (int64_t)B * ((Co + kOB - 1) / kOB) * H * W;
-    k_conv3x3_fwd<<<grid_of(total), 256, 0, s>>>(x, w, b, y, B, Ci, Co, H, W);
+    const dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH, B * ((Co + kOC - 1) / kOC));
+    k_conv3x3_tiled<false><<<grid, 128, 0, s>>>(x, w, b, y, Ci, Co, H, W);
     return cudaGetLastError();
 }
 
 cudaError_t launch_nn_conv_bwd(const float *x, const float *w, const float *dy, float *dx, float *dw, float *db, int B,
-                               int Ci, int Co, int H, int W, cudaStream_t s)
+                               int Ci, int Co, int H, int W, float *scratch, cudaStream_t s)
 {
     if (dx) {
-        const int64_t total = (int64_t)B * ((Ci + kOB - 1) / kOB) * H * W;
-        k_conv3x3_bwd_data<<<grid_of(total), 256, 0, s>>>(dy, w, dx, B, Ci, Co, H, W);
+        const dim3 grid((W + kTW - 1) / kTW, (H + kTH - 1) / kTH, B * ((Ci + kOC - 1) / kOC));
+        k_conv3x3_tiled<true><<<grid, 128, 0, s>>>(dy, w, nullptr, dx, Co, Ci, H, W);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    k_conv3x3_bwd_weight<<<(unsigned)(Co * Ci), 256, 0, s>>>(x, dy, dw, db, B, Ci, Co, H, W);
+    const int S = (int)nn_conv_splits(B, Ci, Co, H, W);
+    float *part = scratch, *part_b = scratch + (size_t)S * Co * Ci * 9;
+    k_conv3x3_dw<<<dim3((Co + kDwO - 1) / kDwO, Ci, S), 256, 0, s>>>(x, dy, part, part_b, B, Ci, Co, H, W, S);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t nw = (int64_t)Co * Ci * 9 + Co;
+    k_conv3x3_dw_sum<<<(unsigned)std::min<int64_t>((nw + 255) / 256, 152 * 8), 256, 0, s>>>(part, part_b, dw, db, Co,
+                                                                                             Ci, S);
     return cudaGetLastError();
 }
 
@@ -317,14 +387,22 @@ dg_status dg_nn_conv3x3_forward(const float *x, const float *w, const float *b, 
                        "dg_nn_conv3x3_forward");
 }
 
-dg_status dg_nn_conv3x3_backward(const float *x, const float *w, const float *dy, float *dx, float *dw, float *db,
-                                 int32_t B, int32_t Ci, int32_t Co, int32_t H, int32_t W, void *stream)
+int64_t dg_nn_conv3x3_scratch(int32_t B, int32_t Ci, int32_t Co, int32_t H, int32_t W)
 {
-    if (!x || !w || !dy || !dw || !db) return dg::nn_fail(DG_EINVAL, "dg_nn_conv3x3_backward: null pointer");
+    if (!dg::conv_shape_ok(B, Ci, Co, H, W)) return -1;
+    return dg::nn_conv_scratch(B, Ci, Co, H, W);
+}
+
+dg_status dg_nn_conv3x3_backward(const float *x, const float *w, const float *dy, float *dx, float *dw, float *db,
+                                 int32_t B, int32_t Ci, int32_t Co, int32_t H, int32_t W, float *scratch,
+                                 void *stream)
+{
+    if (!x || !w || !dy || !dw || !db || !scratch)
+        return dg::nn_fail(DG_EINVAL, "dg_nn_conv3x3_backward: null pointer");
     if (!dg::conv_shape_ok(B, Ci, Co, H, W))
         return dg::nn_fail(DG_EINVAL, "dg_nn_conv3x3_backward: bad shape B=%d Ci=%d Co=%d H=%d W=%d", B, Ci, Co, H,
                            W);
-    return dg::nn_done(dg::launch_nn_conv_bwd(x, w, dy, dx, dw, db, B, Ci, Co, H, W, (cudaStream_t)stream),
+    return dg::nn_done(dg::launch_nn_conv_bwd(x, w, dy, dx, dw, db, B, Ci, Co, H, W, scratch, (cudaStream_t)stream),
                        "dg_nn_conv3x3_backward");
 }
 

@@ -63,9 +63,9 @@ EXPORTED_SYMBOLS = [
     "dg_noalloc_last_error", "dg_cdft_work", "dg_detect", "dg_cdft_chunks",
     "dg_graph_capture", "dg_graph_launch", "dg_graph_fix", "dg_batch_capture", "dg_batch_launch",
     "dg_batch_fixes", "dg_batch_launch_count", "dg_batch_destroy", "dg_autotune",
-    "dg_nn_conv3x3_forward", "dg_nn_conv3x3_backward", "dg_nn_relu_forward", "dg_nn_relu_backward",
-    "dg_nn_bce_scratch", "dg_nn_bce_logits", "dg_nn_adam", "dg_nn_last_error",
-    "dg_coarse_maps", "dg_coarse_inspect",
+    "dg_nn_conv3x3_forward", "dg_nn_conv3x3_backward", "dg_nn_conv3x3_scratch", "dg_nn_relu_forward",
+    "dg_nn_relu_backward", "dg_nn_bce_scratch", "dg_nn_bce_logits", "dg_nn_adam", "dg_nn_last_error",
+    "dg_coarse_maps", "dg_coarse_inspect", "dg_set_grid", "dg_search_regions",
 ]
 DG_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
@@ -197,12 +197,19 @@ def lib():
             L.dg_noalloc_last_error.argtypes = []
             L.dg_noalloc_last_error.restype = C.c_char_p
             flt = C.c_float
+            L.dg_search_regions.argtypes = [vp, C.POINTER(dg_grid), i32, vp, dbl, dbl, C.POINTER(dg_fix),
+                                            C.POINTER(i32)]
+            L.dg_search_regions.restype = C.c_int
+            L.dg_set_grid.argtypes = [vp, C.POINTER(dg_grid)]
+            L.dg_set_grid.restype = C.c_int
             L.dg_coarse_maps.argtypes = [vp, i32, i32, vp]
             L.dg_coarse_maps.restype = C.c_int
             L.dg_coarse_inspect.argtypes = [vp, vp, C.POINTER(dg_coarse_step), C.POINTER(i32)]
             L.dg_coarse_inspect.restype = C.c_int
             L.dg_nn_conv3x3_forward.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, i32, vp]
-            L.dg_nn_conv3x3_backward.argtypes = [vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, i32, vp]
+            L.dg_nn_conv3x3_backward.argtypes = [vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, i32, vp, vp]
+            L.dg_nn_conv3x3_scratch.argtypes = [i32, i32, i32, i32, i32]
+            L.dg_nn_conv3x3_scratch.restype = i64
             L.dg_nn_relu_forward.argtypes = [vp, vp, i64, vp]
             L.dg_nn_relu_backward.argtypes = [vp, vp, vp, i64, vp]
             L.dg_nn_bce_scratch.argtypes = [i64]
@@ -429,16 +436,23 @@ def dg_nn_conv3x3_forward(x, w, b, y, stream=None):
                                           _stream(stream, x)))
 
 
-def dg_nn_conv3x3_backward(x, w, dy, dx, dw, db, stream=None):
-    """Gradients of sum(dy * conv3x3(x, w, b)): dx (None: skipped), dw, db."""
-    _f32(x, w, dy, dx, dw, db)
+def dg_nn_conv3x3_backward(x, w, dy, dx, dw, db, scratch=None, stream=None):
+    """Gradients of sum(dy * conv3x3(x, w, b)): dx (None: skipped), dw, db.
+    scratch: dg_nn_conv3x3_scratch floats (allocated here when None)."""
+    import torch
     B, Ci, H, W = x.shape
     Co = w.shape[0]
+    need = int(lib().dg_nn_conv3x3_scratch(B, Ci, Co, H, W))
+    if need < 0:
+        raise ValueError("dg_nn_conv3x3_backward: shape out of range")
+    if scratch is None:
+        scratch = torch.empty(max(1, need), dtype=torch.float32, device=x.device)
+    _f32(x, w, dy, dx, dw, db, scratch)
     if (tuple(dy.shape) != (B, Co, H, W) or tuple(dw.shape) != (Co, Ci, 3, 3) or tuple(db.shape) != (Co,)
-            or (dx is not None and tuple(dx.shape) != tuple(x.shape))):
+            or (dx is not None and tuple(dx.shape) != tuple(x.shape)) or scratch.numel() < need):
         raise ValueError("dg_nn_conv3x3_backward: shape mismatch")
     _nn_check(lib().dg_nn_conv3x3_backward(_ptr(x), _ptr(w), _ptr(dy), _ptr(dx), _ptr(dw), _ptr(db),
-                                           B, Ci, Co, H, W, _stream(stream, x)))
+                                           B, Ci, Co, H, W, _ptr(scratch), _stream(stream, x)))
 
 
 def dg_nn_relu_forward(z, h, stream=None):
@@ -617,6 +631,33 @@ class Geolocator:
 
     def cdft_work(self):
         return dg_cdft_work(self.ctx)
+
+    def set_grid(self, grid):
+        """Move the context to another (whole) grid, keeping its captures."""
+        g = grid if isinstance(grid, dg_grid) else dg_grid.from_dict(grid)
+        _check(lib().dg_set_grid(self.ctx, C.byref(g)), self.ctx)
+        self.grid = {k: getattr(g, k) for k, _ in dg_grid._fields_}
+        self.nrows = int(g.nlat)
+        self.nlon = int(g.nlon)
+
+    def search_regions(self, regions, refine_spacing_m=0.0, refine_window_m=0.0, costs=None):
+        """Cost surfaces of several equal-size regions, then the dense
+        re-evaluation around the best one: (fix dict, best index, costs)."""
+        torch = self.torch
+        arr = (dg_grid * len(regions))(*[g if isinstance(g, dg_grid) else dg_grid.from_dict(g) for g in regions])
+        n = len(regions)
+        shape = (n, int(arr[0].nlat), int(arr[0].nlon))
+        if costs is None:
+            costs = torch.empty(shape, dtype=self.dtype, device=self.device)
+        if costs.dtype != self.dtype or not costs.is_cuda or not costs.is_contiguous() or costs.numel() < np.prod(shape):
+            raise ValueError("costs must be a contiguous CUDA tensor of the context's precision")
+        fix, best = dg_fix(), C.c_int32()
+        _check(lib().dg_search_regions(self.ctx, arr, n, C.c_void_p(costs.data_ptr()), float(refine_spacing_m),
+                                       float(refine_window_m), C.byref(fix), C.byref(best)), self.ctx)
+        g = arr[best.value]
+        self.grid = {k: getattr(g, k) for k, _ in dg_grid._fields_}
+        self.nrows, self.nlon = int(g.nlat), int(g.nlon)
+        return fix.as_dict(), best.value, costs
 
     def coarse_maps(self, bins=0, chunk=0, out=None):
         """Coarse delay-Doppler maps back-projected onto the grid's cells:

@@ -127,6 +127,22 @@ def truth_delay_doppler(formation: Formation, t, p_e, fc_hz, h=1e-3):
     return r0 / C_LIGHT, -rate / lam
 
 
+def track_point(formation: Formation, t_mid, along_km, cross_km):
+    """The point on the sphere of radius WGS84_A reached from the formation's
+    sub-satellite point at t_mid by along_km along the track and cross_km
+    across it (positive: the side of velocity x up), as (lat_deg, lon_deg)."""
+    p1, v1, p2, v2 = formation.states(t_mid)
+    pm, vm = 0.5 * (p1 + p2), 0.5 * (v1 + v2)
+    g = pm / np.linalg.norm(pm)
+    t = vm - np.dot(vm, g) * g
+    t /= np.linalg.norm(t)
+    x = np.cross(g, t)
+    a = along_km * 1e3 / WGS84_A
+    c = cross_km * 1e3 / WGS84_A
+    e = math.cos(c) * (math.cos(a) * g + math.sin(a) * t) + math.sin(c) * x
+    return math.degrees(math.asin(e[2])), math.degrees(math.atan2(e[1], e[0]))
+
+
 def pick_emitter(rng, formation: Formation, t_mid, along_km=(-150.0, 150.0), cross_km=(150.0, 450.0)):
     """Seeded emitter site near the formation's ground track at t_mid.
 
@@ -290,6 +306,7 @@ def make_scene(
     formation: Formation | None = None,
     integer_delays: bool = False,
     grid_offset_cells: tuple = (0, 0),
+    emitter: tuple | None = None,
 ) -> Scene:
     """Build one seeded scene.
 
@@ -298,11 +315,13 @@ def make_scene(
     differential delay rounded to a whole sample (noise waveform only), so the
     true alignment is an exact integer lag. The grid is centred on the emitter
     unless grid_offset_cells moves its centre by whole cells (lat, lon).
+    emitter = (lat_deg, lon_deg) places the emitter there instead of at a
+    seeded site near the ground track.
     """
     rng = np.random.default_rng(seed)
     form = formation or Formation()
     t_mid = form.t0_s + 0.5 * (k_steps - 1) * form.dt_s
-    lat_e, lon_e = pick_emitter(rng, form, t_mid)
+    lat_e, lon_e = pick_emitter(rng, form, t_mid) if emitter is None else emitter
     p_e = geodetic_to_ecef(lat_e, lon_e, 0.0)
     ephem = form.ephemerides(k_steps)
     nlat, nlon = (grid_n, grid_n) if isinstance(grid_n, int) else grid_n
@@ -332,6 +351,9 @@ def make_scene(
     taus = np.empty((k_steps, 2))
     fds = np.empty((k_steps, 2))
     chirp_t0 = rng.uniform(0.0, chirp_period_s)
+    if waveform == "gps_ca":
+        code = gold_code_prn1()
+        bits = rng.choice(np.array([-1, 1], dtype=np.int8), size=4096)
     for k in range(k_steps):
         tk = form.t0_s + k * form.dt_s
         tau, fd = truth_delay_doppler(form, tk, p_e, fc_hz)
@@ -355,6 +377,8 @@ def make_scene(
             sig = [sawtooth(chirp_t0 + t_n - tau[i], chirp_bw_hz, chirp_period_s) for i in range(2)]
         elif waveform == "tone":
             sig = [tone(t_n - tau[i], tone_hz) for i in range(2)]
+        elif waveform == "gps_ca":
+            sig = [gps_ca(tk + t_n - tau[i], code, bits) for i in range(2)]
         else:
             raise ValueError(f"unknown waveform {waveform!r}")
         for i, dst in enumerate((y1, y2)):
@@ -536,6 +560,44 @@ def four_jammers(seed: int = 5, **kw) -> MultiScene:
 # --------------------------------------------------------------------------
 # the workloads (sizes, formats, waveforms and SNRs of the five workloads)
 # --------------------------------------------------------------------------
+def learned(seed: int = 5, *, n_samples: int = 65536, k_steps: int = 20, footprint_m: float = 2.0e6,
+            judge_spacing_m: float = 500.0, snr_db=(-21.0, -12.0), waveforms=("noise", "chirp", "gps_ca"),
+            margin_m: float = 60e3, cross_km: float = 1200.0, fs_hz: float = 12.5e6) -> Scene:
+    """One scene of the learned-proposal workload: a footprint_m square
+    (lat/lon grid at judge_spacing_m, the full-grid search) centred cross_km
+    from the ground track on the equator side, with the formation near the
+    northern apex of its orbit (u0 = 86 deg), where the track runs east-west
+    and the footprint lies wholly on one side of it (no mirror image inside).
+    The emitter sits at a seeded point of the footprint (at least margin_m
+    from its edges), with a seeded waveform and SNR (uniform in snr_db);
+    K = 20 snapshots 1 s apart of N = 65536 complex int16 samples at
+    12.5 MHz. The noise is 10 MHz wide; the chirp sweeps 10 MHz every 2 ms
+    and the GPS C/A spoofer repeats every 1 ms, both longer than the
+    footprint's delay span (a chirp repeating every 10 us would put a
+    copy of the emitter's delay ridge every 125 lags)."""
+    rng = np.random.default_rng(seed)
+    form = Formation(u0_deg=86.0)
+    t_mid = form.t0_s + 0.5 * (k_steps - 1) * form.dt_s
+    north = track_point(form, t_mid, 0.0, 1.0)[0] > track_point(form, t_mid, 0.0, -1.0)[0]
+    lat_c, lon_c = track_point(form, t_mid, 0.0, -cross_km if north else cross_km)
+    half = 0.5 * footprint_m - margin_m
+    di_m, dj_m = rng.uniform(-half, half), rng.uniform(-half, half)
+    dlat, dlon = _cell_degrees(lat_c, 1.0)  # degrees per metre at the centre
+    lat_e, lon_e = lat_c + di_m * dlat, lon_c + dj_m * dlon
+    waveform = str(waveforms[int(rng.integers(len(waveforms)))])
+    snr = float(rng.uniform(*snr_db)) if isinstance(snr_db, tuple) else float(snr_db)
+    n_side = int(round(footprint_m / judge_spacing_m)) + 1
+    sc = make_scene(seed=int(rng.integers(1 << 31)), fs_hz=fs_hz, n_samples=n_samples, k_steps=k_steps,
+                    fmt="ci16", waveform=waveform, snr_db=snr, grid_n=n_side, grid_spacing_m=judge_spacing_m,
+                    bw_hz=10e6, chirp_bw_hz=10e6, chirp_period_s=2e-3, formation=form,
+                    emitter=(lat_e, lon_e))
+    sc.grid = dict(lat0_deg=lat_c, lon0_deg=lon_c, dlat_m=judge_spacing_m, dlon_m=judge_spacing_m,
+                   nlat=n_side, nlon=n_side)
+    sc.meta.update(workload="learned", footprint_m=footprint_m, emitter_offset_m=(di_m, dj_m),
+                   waveform=waveform, snr_db=snr)
+    return sc
+
+
 def tiny(seed: int = 1, **kw) -> Scene:
     """101x101 grid at 1 km, K=1 x N=4096 complex64, 2 MHz noise, fs 5 MHz, -5 dB."""
     args = dict(seed=seed, fs_hz=5e6, n_samples=4096, k_steps=1, fmt="c64", waveform="noise",
@@ -564,4 +626,5 @@ def large(seed: int = 3, **kw) -> Scene:
 
 
 WORKLOADS = {"tiny": tiny, "mid": mid, "large": large}
+LEARNED = learned
 MULTI_WORKLOADS = {"crowded": crowded, "four_jammers": four_jammers}
