@@ -641,6 +641,149 @@ def run_batch(a, rank, world, local_rank):
         g.close()
 
 
+LEARNED_WEIGHTS = os.path.join(ROOT, "paper_2508_06672_gb300", "weights", "proposal_2000km.npz")
+LEARNED_SEEDS = [5] + list(range(300000, 300015))   # held out: training used seeds 1000..
+
+
+def run_learned(a, rank, world, local_rank):
+    """The learned-proposal search against the full-grid search on the 2000 km
+    footprint (sim.learned): per step one held-out scene, both searches on
+    the same resident captures, CUDA events on the shared stream."""
+    import torch
+
+    import paper_2508_06672_gb300 as P
+    import sim
+    from paper_2508_06672_gb300 import learned as L
+    from paper_2508_06672_gb300.proposal import ProposalNet
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n_sc = max(1, min(len(LEARNED_SEEDS), a.steps))
+    scenes = [sim.learned(sd) for sd in LEARNED_SEEDS[:n_sc]]
+    net = ProposalNet.load(LEARNED_WEIGHTS, device=dev)
+    st = torch.cuda.Stream(dev)
+    s0 = scenes[0]
+    search = L.LearnedSearch(s0.grid, s0.ephem, s0.fs_hz, s0.fc_hz, net, stream=st)
+    judge = P.Geolocator(s0.grid, s0.ephem, s0.fs_hz, s0.fc_hz, algo="cdft", contract="bf16x3", stream=st)
+    cost = torch.empty((s0.grid["nlat"], s0.grid["nlon"]), dtype=torch.float32, device=dev)
+    sumnet = L.SumNet(search.K, device=dev)
+    dev_caps = [(torch.from_numpy(sc.y1).to(dev), torch.from_numpy(sc.y2).to(dev)) for sc in scenes]
+    host_caps = [(torch.from_numpy(sc.y1).pin_memory(), torch.from_numpy(sc.y2).pin_memory()) for sc in scenes]
+    with torch.cuda.stream(st):
+        flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+
+    def load(i, caps):
+        with torch.cuda.stream(st):
+            judge.load_captures(scenes[i].fmt, *caps[i])
+            search.load_captures(scenes[i].fmt, *caps[i])
+
+    for w in range(a.warmup):
+        load(w % n_sc, dev_caps)
+        judge.cost_surface(out=cost)
+        judge.argmax_refine(cost, 25.0, 500.0)
+        search.search()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    learned_ms, full_ms, rec, rec_sum, err_l, err_f = [], [], [], [], [], []
+    l0 = search.geo.launch_count() + search.hm.launch_count()
+    nn_launches = 2 * len(net.params) - 1
+    clk = ClockSampler(_smi_id(local_rank))
+    with clk:
+        for i in range(a.steps):
+            sc = scenes[i % n_sc]
+            load(i % n_sc, dev_caps)
+            with torch.cuda.stream(st):
+                flush.zero_()
+            torch.cuda.synchronize(dev)
+            ev[0].record(st)
+            judge.cost_surface(out=cost)
+            jf = judge.argmax_refine(cost, 25.0, 500.0)
+            ev[1].record(st)
+            with torch.cuda.stream(st):
+                flush.zero_()
+            ev[1].synchronize()
+            e_mid = torch.cuda.Event(enable_timing=True)
+            e_mid.record(st)
+            lf, _, peaks = search.search()
+            ev[2].record(st)
+            torch.cuda.synchronize(dev)
+            full_ms.append(ev[0].elapsed_time(ev[1]))
+            learned_ms.append(e_mid.elapsed_time(ev[2]))
+
+            def covered(pk):
+                for p in pk:
+                    g = search.region_grid(p["lat_deg"], p["lon_deg"])
+                    ci, cj = L.node_of(s0.grid, g["lat0_deg"], g["lon0_deg"])
+                    if abs(jf["i"] - round(ci)) <= search.half and abs(jf["j"] - round(cj)) <= search.half:
+                        return True
+                return False
+
+            rec.append(covered(peaks))
+            err_f.append(L.distance_m(jf["refined_lat_deg"], jf["refined_lon_deg"], sc.emitter_lat_deg,
+                                      sc.emitter_lon_deg))
+            err_l.append(L.distance_m(lf["refined_lat_deg"], lf["refined_lon_deg"], sc.emitter_lat_deg,
+                                      sc.emitter_lon_deg))
+            if i < n_sc:
+                _, _, speaks = search.search(sumnet)
+                rec_sum.append(covered(speaks))
+    launches = search.geo.launch_count() + search.hm.launch_count() - l0
+    launches_per_search = launches / (a.steps + len(rec_sum)) + nn_launches
+    # end to end: pinned host captures in, the fix out
+    e2e = []
+    for i in range(min(a.steps, n_sc)):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        with torch.cuda.stream(st):
+            search.load_captures(scenes[i].fmt, *host_caps[i])
+        search.search()
+        e2e.append(1e3 * (time.perf_counter() - t0))
+    h2d = sum(t.numel() * t.element_size() for t in host_caps[0])
+    # the network's forward on the 512 x 512 coarse maps, timed alone
+    x = search.maps.view(1, search.K, search.cells, search.cells)
+    with torch.cuda.stream(st):
+        for _ in range(3):
+            net.forward(x)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(20):
+            net.forward(x)
+        e1.record(st)
+    torch.cuda.synchronize(dev)
+    fwd_ms = e0.elapsed_time(e1) / 20
+    fwd_flops = sum(2 * 9 * w.shape[0] * w.shape[1] * search.cells * search.cells for w, _ in net.params)
+    fp32_peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    clocks = clk.summary()
+    if rank == 0:
+        med_l, med_f = statistics.median(learned_ms), statistics.median(full_ms)
+        line = {
+            "metric": "learned-proposal search latency (2000 km footprint; full-grid search timed beside it)",
+            "value": med_l, "unit": "ms", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": med_l, "higher_is_better": False, "scaling": "replicas", "vs_baseline": None,
+            "dtype": "f32 (CDFT contraction bf16x3)", "data": "synthetic",
+            "config": {"workload": "learned: 2000 km square footprint (4001^2 nodes at 500 m), K = 20 x N = 65536 "
+                                   "ci16 at 12.5 MHz, noise / 2 ms chirp / GPS C/A at -21..-12 dB; 512^2 coarse "
+                                   "cells -> network [20,32,64,64,1] -> top 8 regions of 50 x 50 km at 500 m -> "
+                                   "25 m re-evaluation (+-500 m)",
+                       "scenes": n_sc, "seeds": LEARNED_SEEDS[:n_sc], "weights": os.path.relpath(LEARNED_WEIGHTS, ROOT),
+                       "l2": "flushed before each timed search (256 MB write outside the events)"},
+            "full_grid_ms": med_f, "speedup_vs_full_grid": med_f / med_l,
+            "recall": float(np.mean(rec)), "recall_coarse_sum_without_network": float(np.mean(rec_sum)),
+            "error_m": {"learned_p50": float(np.median(err_l)), "learned_p90": float(np.percentile(err_l, 90)),
+                        "full_grid_p50": float(np.median(err_f)), "full_grid_p90": float(np.percentile(err_f, 90))},
+            "e2e": {"value": statistics.median(e2e), "unit": "ms", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": 84},
+            "gpu_launches": int(round(launches_per_search * a.steps)),
+            "roofline": {"bound": "alu", "achieved": fwd_flops / (fwd_ms / 1e3) / 1e12, "peak": fp32_peak,
+                         "unit": "TFLOP/s", "frac": fwd_flops / (fwd_ms / 1e3) / 1e12 / fp32_peak, "traffic": None,
+                         "kernel": "k_conv3x3_tiled (the network's forward on the 512^2 maps, timed alone)",
+                         "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"},
+            "cpu_baseline": None,
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    search.close()
+    judge.close()
+
+
 def _smi_id(local_rank):
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     if vis:
@@ -656,7 +799,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["dg", "reference"], default="dg")
-    ap.add_argument("--workload", choices=["mid", "tiny", "large", "batch"], default="mid")
+    ap.add_argument("--workload", choices=["mid", "tiny", "large", "batch", "learned"], default="mid")
     ap.add_argument("--algo", choices=["direct", "cdft"], default="cdft")
     ap.add_argument("--chunk", type=int, default=0, help="CDFT samples per chunk; 0 = automatic")
     ap.add_argument("--contract", choices=["fp32", "bf16", "fp16", "bf16x3", "fp16x3"], default="fp16x3")
@@ -684,6 +827,8 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     if a.workload == "batch":
         run_batch(a, rank, world, local_rank)
+    elif a.workload == "learned":
+        run_learned(a, rank, world, local_rank)
     else:
         run_dg(a, rank, world, local_rank)
     if world > 1:

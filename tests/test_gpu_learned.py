@@ -1,0 +1,88 @@
+"""What the trained proposal network gains.
+
+On held-out scenes of the 2000 km learned-proposal workload (seeds never used
+in training), three searches run on the same captures:
+
+* the full-grid search: Algorithm 1 on every node of the footprint at 500 m
+  (4001 x 4001), then the dense re-evaluation at 25 m around its argmax;
+* the learned search: coarse maps -> the trained network (weights trained on
+  the GPU by the library's own kernels, paper_2508_06672_gb300/weights) ->
+  top-8 regions of 50 x 50 km at 500 m -> the same dense re-evaluation;
+* the same search without the network, ranking cells by the sum of the
+  coarse maps (the method's own non-coherent sum).
+
+Recall is the fraction of scenes whose full-grid argmax lies inside one of the
+proposed regions. The network must lift recall well above the sum's, keep
+the localisation error of the full-grid search, and take less time.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import sim
+from gpu_common import package, torch_cuda
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+SEEDS = list(range(200000, 200012))
+WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2508_06672_gb300",
+                       "weights", "proposal_2000km.npz")
+
+
+def test_trained_network_gains_over_the_coarse_sum():
+    torch = torch_cuda()
+    package()
+    from paper_2508_06672_gb300 import Geolocator
+    from paper_2508_06672_gb300 import learned as L
+    from paper_2508_06672_gb300.proposal import ProposalNet
+
+    net = ProposalNet.load(WEIGHTS)
+    first = sim.learned(SEEDS[0])
+    search = L.LearnedSearch(first.grid, first.ephem, first.fs_hz, first.fc_hz, net)
+    judge = Geolocator(first.grid, first.ephem, first.fs_hz, first.fc_hz, algo="cdft", contract="bf16x3",
+                       stream=search.geo.stream)
+    cost = torch.empty((first.grid["nlat"], first.grid["nlon"]), dtype=torch.float32, device="cuda")
+    sumnet = L.SumNet(search.K)
+    rec_net, rec_sum, err_j, err_n, t_j, t_n = [], [], [], [], [], []
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for seed in SEEDS:
+        s = first if seed == SEEDS[0] else sim.learned(seed)
+        y1, y2 = torch.from_numpy(s.y1).cuda(), torch.from_numpy(s.y2).cuda()
+        judge.load_captures(s.fmt, y1, y2)
+        search.load_captures(s.fmt, y1, y2)
+        torch.cuda.synchronize()
+        ev[0].record(search.geo.stream)
+        judge.cost_surface(out=cost)
+        jf = judge.argmax_refine(cost, 25.0, 500.0)
+        ev[1].record(search.geo.stream)
+        nf, _, peaks = search.search(net)
+        ev[2].record(search.geo.stream)
+        _, _, speaks = search.search(sumnet)
+        torch.cuda.synchronize()
+
+        def covered(pk):
+            for p in pk:
+                g = search.region_grid(p["lat_deg"], p["lon_deg"])
+                ci, cj = L.node_of(first.grid, g["lat0_deg"], g["lon0_deg"])
+                if abs(jf["i"] - round(ci)) <= search.half and abs(jf["j"] - round(cj)) <= search.half:
+                    return True
+            return False
+
+        rec_net.append(covered(peaks))
+        rec_sum.append(covered(speaks))
+        err_j.append(L.distance_m(jf["refined_lat_deg"], jf["refined_lon_deg"], s.emitter_lat_deg, s.emitter_lon_deg))
+        err_n.append(L.distance_m(nf["refined_lat_deg"], nf["refined_lon_deg"], s.emitter_lat_deg, s.emitter_lon_deg))
+        t_j.append(ev[0].elapsed_time(ev[1]))
+        t_n.append(ev[1].elapsed_time(ev[2]))
+    judge.close()
+    search.close()
+    n = len(SEEDS)
+    print(f"recall: network {sum(rec_net)}/{n}, coarse sum {sum(rec_sum)}/{n}; median error (m): full grid "
+          f"{np.median(err_j):.0f}, learned {np.median(err_n):.0f}; median time (ms): full grid {np.median(t_j):.1f}, "
+          f"learned {np.median(t_n):.1f}")
+    assert sum(rec_net) >= n - 1
+    assert sum(rec_net) >= sum(rec_sum) + 3
+    assert np.median(err_n) <= 1.25 * np.median(err_j) + 500.0
+    assert np.median(t_n) < 0.6 * np.median(t_j)
