@@ -761,7 +761,7 @@ def run_learned(a, rank, world, local_rank):
             "dtype": "f32 (CDFT contraction bf16x3)", "data": "synthetic",
             "config": {"workload": "learned: 2000 km square footprint (4001^2 nodes at 500 m), K = 20 x N = 65536 "
                                    "ci16 at 12.5 MHz, noise / 2 ms chirp / GPS C/A at -21..-12 dB; 512^2 coarse "
-                                   "cells -> network [20,32,64,64,1] -> top 8 regions of 50 x 50 km at 500 m -> "
+                                   f"cells -> network {net.channels} -> top 8 regions of 50 x 50 km at 500 m -> "
                                    "25 m re-evaluation (+-500 m)",
                        "scenes": n_sc, "seeds": LEARNED_SEEDS[:n_sc], "weights": os.path.relpath(LEARNED_WEIGHTS, ROOT),
                        "l2": "flushed before each timed search (256 MB write outside the events)"},
