@@ -259,7 +259,7 @@ def run_dg(a, rank, world, local_rank):
     stream = torch.cuda.Stream(dev)
     g = P.Geolocator(scene.grid, scene.ephem, scene.fs_hz, scene.fc_hz, algo=a.algo, row0=row0,
                      nrows=nrows, timing=True, stream=stream, device=local_rank, chunk=a.chunk,
-                     contract=a.contract)
+                     contract=a.contract, tiles=a.tiles)
     y1d = torch.from_numpy(scene.y1).to(dev)
     y2d = torch.from_numpy(scene.y2).to(dev)
     y1h = torch.from_numpy(scene.y1).pin_memory()
@@ -403,7 +403,9 @@ def run_dg(a, rank, world, local_rank):
         dom = max(("contract", "combine"), key=lambda n: kt[n][0])
         flops_per_step = contract_flops if dom == "contract" else combine_units * (1e12 if combine_hbm else 1)
         corr_ms, corr_launches = kt[dom]
-        roof_kernel = {"contract": (f"k_cdft_contract_tc ({a.contract} tcgen05, {chunk}-sample chunks x 64 bins)"
+        tc_name = ("k_cdft_contract_hk (Hankel tiles)" if a.tiles in ("auto", "hankel") and chunk <= 1024
+                   else "k_cdft_contract_tc")
+        roof_kernel = {"contract": (f"{tc_name} ({a.contract} tcgen05, {chunk}-sample chunks x 64 bins)"
                                     if tensor else f"k_cdft_contract_f32 (FP32 CUDA cores, {chunk}-sample chunks)"),
                        "combine": "k_cdft_superchunk + k_cdft_combine (per-candidate interpolation + super-chunk phase sum)"}[dom]
         roof_basis = kernels[dom]["basis"]
@@ -446,6 +448,7 @@ def run_dg(a, rank, world, local_rank):
                        "chunk": ((a.chunk if a.chunk else f"auto: {chunk_lo}..{chunk_hi}" if chunk_lo != chunk_hi
                                   else f"auto: {chunk_hi}") if a.algo == "cdft" else None),
                        "contract": a.contract if a.algo == "cdft" else None,
+                       "tiles": a.tiles if a.algo == "cdft" else None,
                        "refine": f"{REFINE_SPACING_M:g} m spacing, +-{REFINE_WINDOW_M:g} m",
                        "l2": "flushed between timed steps (256 MB write outside the events)",
                        "parallelism": f"grid rows sharded over {world} GPU(s)", "seed": scene.meta["seed"]},
@@ -554,7 +557,7 @@ def run_batch(a, rank, world, local_rank):
     gs, costs, hosts = [], [], []
     for sc in scenes:
         st = torch.cuda.Stream(dev)
-        g = P.Geolocator(sc.grid, sc.ephem, sc.fs_hz, sc.fc_hz, algo="cdft", contract=a.contract, stream=st,
+        g = P.Geolocator(sc.grid, sc.ephem, sc.fs_hz, sc.fc_hz, algo="cdft", contract=a.contract, tiles=a.tiles, stream=st,
                          device=local_rank, scratch_mib=256)
         y1, y2 = torch.from_numpy(sc.y1).pin_memory(), torch.from_numpy(sc.y2).pin_memory()
         with torch.cuda.stream(st):
@@ -803,6 +806,8 @@ def main():
     ap.add_argument("--algo", choices=["direct", "cdft"], default="cdft")
     ap.add_argument("--chunk", type=int, default=0, help="CDFT samples per chunk; 0 = automatic")
     ap.add_argument("--contract", choices=["fp32", "bf16", "fp16", "bf16x3", "fp16x3"], default="fp16x3")
+    ap.add_argument("--tiles", choices=["auto", "rows", "lags", "hankel"], default="auto",
+                    help="CDFT tensor-core tiles (auto: Hankel where lag-type tiles fit)")
     ap.add_argument("--no-direct", action="store_true", help="skip the direct-path reference measurement")
     ap.add_argument("--grid", type=int, default=0, help="override the grid to GRID x GRID nodes")
     ap.add_argument("--cpu-baseline-s", type=float, default=15.0)

@@ -76,14 +76,24 @@ enum { DG_PREC_FP32 = 0, DG_PREC_FP64 = 1 };
  * (DG_CONTRACT_*). */
 enum { DG_ALGO_DIRECT = 0, DG_ALGO_CDFT = 1 };
 
-/* Rows of one tensor-core tile of the CDFT contraction (128 rows each).
- * ROWS: consecutive (lag, chunk) pairs, lag-major; each row reads its own
- * capture segments. LAGS: 128 consecutive lags at one chunk; the rows share
- * one y1 segment and one y2 window, staged once per tile (chunk <= 1024).
- * AUTO takes LAGS unless padding the lags of a snapshot to whole blocks of
- * 128 more than doubles the tile count. Both form the same lag products
- * (the 16-bit scale is a power of two), so the surfaces are identical. */
-enum { DG_TILES_AUTO = 0, DG_TILES_ROWS = 1, DG_TILES_LAGS = 2 };
+/* Tiles of the CDFT tensor-core contraction.
+ * ROWS: 128 consecutive (lag, chunk) pairs, lag-major; each row reads its own
+ * capture segments and forms its lag products. LAGS: 128 consecutive lags at
+ * one chunk; the rows share one y1 segment and one y2 window, staged once per
+ * tile (chunk <= 1024). ROWS and LAGS form the same lag products (the 16-bit
+ * scale is a power of two), so their surfaces are identical.
+ * HANKEL: 512 consecutive lags at one chunk, with the product regrouped as
+ * W_b(l, q) = sum_m (y1[bM+m] e^{j 2 pi nu_q m}) conj(y2[bM+m+l]): the left
+ * operand (64 bins x chunk, shared by every lag of the chunk) is formed once
+ * per tile, and the right operand is y2 itself read as a Hankel matrix
+ * straight from shared memory (lags in 8 phases of stride 8; chunk <= 1024).
+ * It rounds y1 e^{...} and y2 to 16 bits instead of the lag products and the
+ * DFT matrix, so it agrees with the others within the contraction's error.
+ * On this chip HANKEL is slower than LAGS (its per-phase MMAs of N = 64
+ * fetch more operand bytes per flop), so AUTO does not take it: AUTO takes
+ * LAGS (chunk <= 1024) unless padding a snapshot's lags to whole blocks of 128
+ * more than doubles its tile count, and ROWS then. */
+enum { DG_TILES_AUTO = 0, DG_TILES_ROWS = 1, DG_TILES_LAGS = 2, DG_TILES_HANKEL = 3 };
 
 /* Arithmetic of the CDFT contraction: FP32 on CUDA cores, or 16-bit
  * tensor-core products accumulated in FP32. BF16 / FP16 round the lag products
@@ -290,7 +300,7 @@ dg_status dg_batch_destroy(dg_batch *batch);
  * the successor of the paper's batch-size sweep, Sec. V-B). For every chunk
  * length in {256, 512, 1024} that the bin-spacing bound admits for this
  * grid and these snapshots, and for tensor-core contractions both tile
- * shapes (DG_TILES_ROWS, DG_TILES_LAGS), it times dg_cost_surface into cost
+ * shapes (DG_TILES_ROWS, DG_TILES_LAGS, DG_TILES_HANKEL), it times dg_cost_surface into cost
  * (device, the context's precision; its contents are overwritten) with CUDA
  * events on the context's stream: one untimed run, then reps >= 1 timed runs,
  * keeping the median. The fastest shape is written into the context's

@@ -76,7 +76,7 @@ struct CdftBufs {  // chunked-DFT scratch, grown on demand
     size_t v_cap = 0;
     float *W = nullptr;
     size_t w_cap = 0;
-    int *tbase = nullptr;
+    int *tbase = nullptr, *hbase = nullptr;
     void *btab = nullptr;
     size_t btab_cap = 0;
 };
@@ -567,6 +567,7 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         if ((st = grow(c, &b.nubase, (size_t)s_max)) != DG_OK) return st;
         if ((st = grow(c, &b.nur, 2 * (size_t)s_max)) != DG_OK) return st;
         if ((st = grow(c, &b.tbase, (size_t)s_max + 1)) != DG_OK) return st;
+        if ((st = grow(c, &b.hbase, (size_t)s_max + 1)) != DG_OK) return st;
         if ((st = grow(c, &b.layout, (size_t)s_max)) != DG_OK) return st;
         if ((st = grow(c, &b.Mcs, (size_t)s_max)) != DG_OK) return st;
         b.s_cap = (size_t)s_max;
@@ -683,6 +684,7 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         a.subcnt = b.subcnt;
         a.W = b.W;
         a.tbase = b.tbase;
+        a.hbase = b.hbase;
         a.layout = b.layout;
         a.Mcs = b.Mcs;
         a.work = refine ? nullptr : b.work;
@@ -714,9 +716,27 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
                     tiles_cap += B * ((slots + 127) / 128);
                 }
                 const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles_cap, c->sm_count));
-                CK(c, launch_cdft_btab(a, c->opt.contract, b.btab, c->stream));
-                CK(c, launch_cdft_contract_mma(a, grid, f, c->opt.contract, c->stream));
-                t.done(2);
+                // Hankel tiles (chunk <= 1024, on request) run in their own
+                // persistent kernel
+                const bool hk = M <= kLagTileMaxChunk && c->opt.tiles == DG_TILES_HANKEL;
+                int n = 0;
+                if (c->opt.tiles != DG_TILES_HANKEL || M > kLagTileMaxChunk) {
+                    CK(c, launch_cdft_btab(a, c->opt.contract, b.btab, c->stream));
+                    CK(c, launch_cdft_contract_mma(a, grid, f, c->opt.contract, c->stream));
+                    n += 2;
+                }
+                if (hk) {
+                    int64_t hk_cap = 0;
+                    for (int s = 0; s < S; ++s) {
+                        const int slots = lag_slots(c->eph_host[k0 + s], c->fs, L.diam);
+                        const int64_t B = (c->steps[k0 + s].n + M - 1) / M;
+                        hk_cap += B * ((slots + kHkLags - 1) / kHkLags);
+                    }
+                    const int hgrid = (int)std::max<int64_t>(1, std::min<int64_t>(hk_cap, c->sm_count));
+                    CK(c, launch_cdft_contract_hankel(a, hgrid, f, c->opt.contract, c->stream));
+                    ++n;
+                }
+                t.done(n);
             } else {
                 CK(c, launch_cdft_contract_fp32(a, (int)bt.nbt, f, c->stream));
                 t.done(1);
@@ -831,10 +851,10 @@ dg_status dg_create(const dg_grid *grid, const dg_ephem *eph, int32_t K, double 
         if (o.bins != 0 && o.bins != 64) return fail(nullptr, DG_EUNSUPPORTED, "bins must be 0 or 64");
         if (o.contract < DG_CONTRACT_FP32 || o.contract > DG_CONTRACT_FP16X3)
             return fail(nullptr, DG_EINVAL, "unknown contraction arithmetic %d", o.contract);
-        if (o.tiles < DG_TILES_AUTO || o.tiles > DG_TILES_LAGS)
+        if (o.tiles < DG_TILES_AUTO || o.tiles > DG_TILES_HANKEL)
             return fail(nullptr, DG_EINVAL, "unknown tile shape %d", o.tiles);
-        if (o.tiles == DG_TILES_LAGS && o.chunk > kLagTileMaxChunk)
-            return fail(nullptr, DG_EINVAL, "lag tiles need chunk <= %d", kLagTileMaxChunk);
+        if ((o.tiles == DG_TILES_LAGS || o.tiles == DG_TILES_HANKEL) && o.chunk > kLagTileMaxChunk)
+            return fail(nullptr, DG_EINVAL, "lag and Hankel tiles need chunk <= %d", kLagTileMaxChunk);
         if (o.scratch_mib < 0) return fail(nullptr, DG_EINVAL, "scratch_mib must be >= 0");
     }
     if (o.row0 < 0 || o.row0 >= grid->nlat) return fail(nullptr, DG_EINVAL, "row0 outside the grid");
@@ -1457,7 +1477,10 @@ dg_status dg_autotune(dg_ctx *c, void *cost, int32_t reps, dg_tuning *out)
         if (1.25 * m * dmax <= kCdftMDelta) chunks.push_back(m);
     if (chunks.empty()) chunks.push_back(auto_chunk(span, 0, c->K));
     std::vector<int> tiles = {DG_TILES_ROWS};
-    if (c->opt.contract != DG_CONTRACT_FP32) tiles.push_back(DG_TILES_LAGS);
+    if (c->opt.contract != DG_CONTRACT_FP32) {
+        tiles.push_back(DG_TILES_LAGS);
+        tiles.push_back(DG_TILES_HANKEL);
+    }
     const dg_options saved = c->opt;
     const size_t esz = c->opt.prec == DG_PREC_FP64 ? 8 : 4;
     dg_status st = ensure(c, &c->surf, &c->surf_bytes, esz * (size_t)c->G * c->K);
@@ -1470,7 +1493,7 @@ dg_status dg_autotune(dg_ctx *c, void *cost, int32_t reps, dg_tuning *out)
     c->opt.timing = 0;  // restored with the saved options
     for (int m : chunks)
         for (int t : tiles) {
-            if (t == DG_TILES_LAGS && m > kLagTileMaxChunk) continue;
+            if ((t == DG_TILES_LAGS || t == DG_TILES_HANKEL) && m > kLagTileMaxChunk) continue;
             c->opt.chunk = m;
             c->opt.tiles = t;
             std::vector<float> ms;
@@ -1660,6 +1683,7 @@ dg_status dg_destroy(dg_ctx *c)
     fr(c->cd.V);
     fr(c->cd.W);
     fr(c->cd.tbase);
+    fr(c->cd.hbase);
     fr(c->cd.btab);
     for (auto &st : c->steps) {
         fr(st.y1);

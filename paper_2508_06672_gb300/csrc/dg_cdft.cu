@@ -530,11 +530,11 @@ __global__ void k_cdft_tiles(CdftBatch a)
     // warp prefix sum
     const int lane = threadIdx.x;
     if (blockIdx.x != 0 || lane >= 32) return;
-    int running = 0;
+    int running = 0, hrunning = 0;
     unsigned long long rows = 0, cands = 0;
     for (int s0 = 0; s0 < a.S; s0 += 32) {
         const int s = s0 + lane;
-        int tiles = 0;
+        int tiles = 0, htiles = 0;
         if (s < a.S) {
             const int lo = a.lr[2 * s], hi = a.lr[2 * s + 1];
             int NB = hi >= lo ? hi - lo + 1 : 0;
@@ -542,11 +542,21 @@ __global__ void k_cdft_tiles(CdftBatch a)
             const int n = a.sd[s].n, M = a.M;
             const int B = (n + M - 1) / M;
             const int t_row = (int)(((int64_t)NB * B + 127) / 128), t_lag = B * ((NB + 127) / 128);
+            const int t_hk = B * ((NB + kHkLags - 1) / kHkLags);
+            // 0: row tiles, 1: lag tiles, 2: Hankel tiles
+            // AUTO: lag tiles unless padding the lags to whole blocks of 128
+            // more than doubles the tile count; Hankel tiles only on request
+            // (measured slower: their per-phase MMAs of N = 64 re-read the
+            // 128-row operand eight times per K step)
             int lay = 0;
-            if (a.mma && M <= kLagTileMaxChunk)
-                lay = a.tiles_mode == DG_TILES_LAGS || (a.tiles_mode == DG_TILES_AUTO && t_lag <= 2 * t_row);
+            if (a.mma && M <= kLagTileMaxChunk) {
+                if (a.tiles_mode == DG_TILES_HANKEL) lay = 2;
+                else if (a.tiles_mode == DG_TILES_LAGS) lay = 1;
+                else if (a.tiles_mode == DG_TILES_AUTO && t_lag <= 2 * t_row) lay = 1;
+            }
             a.layout[s] = lay;
-            tiles = lay ? t_lag : t_row;
+            tiles = lay == 2 ? 0 : lay ? t_lag : t_row;
+            htiles = lay == 2 ? t_hk : 0;
             int64_t Mc = M;
             const double d = (double)a.delta[s];
             while (Mc < n && 2 * Mc <= ((int64_t)1 << 24) && (double)(2 * Mc) * d <= kCdftMDelta) Mc *= 2;
@@ -554,14 +564,22 @@ __global__ void k_cdft_tiles(CdftBatch a)
             rows += (unsigned long long)NB * B;
             cands += (unsigned long long)a.G * ((n + Mc - 1) / Mc);
         }
-        int incl = tiles;
+        int incl = tiles, hincl = htiles;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += y;
+            const int hy = __shfl_up_sync(0xffffffffu, hincl, d);
+            if (lane >= d) {
+                incl += y;
+                hincl += hy;
+            }
         }
-        if (s < a.S) a.tbase[s] = running + incl - tiles;
+        if (s < a.S) {
+            a.tbase[s] = running + incl - tiles;
+            a.hbase[s] = hrunning + hincl - htiles;
+        }
         running += __shfl_sync(0xffffffffu, incl, 31);
+        hrunning += __shfl_sync(0xffffffffu, hincl, 31);
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
@@ -570,6 +588,7 @@ __global__ void k_cdft_tiles(CdftBatch a)
     }
     if (lane == 0) {
         a.tbase[a.S] = running;
+        a.hbase[a.S] = hrunning;
         if (a.work) {
             a.work[0] += rows;
             a.work[1] += cands;

@@ -841,6 +841,338 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
     if (warp == 0) tmem_dealloc(tmem, 256);
 }
 
+// ---------------------------------------------------------------------------
+// Hankel tiles: 512 consecutive lags L0 .. L0 + 511 of snapshot s at chunk b.
+// The contraction is regrouped so that the lag-dependent operand is the raw
+// capture:
+//     W_b(L, q) = sum_m G_q[m] conj(y2[bM + m + L]),  G_q[m] = y1[bM + m] e^{j 2 pi nu_q m}.
+// A (128 x 2M, K-major, formed per 32-sample stage by the producers): row q
+// holds [G_re | G_im] and row 64 + q holds [G_im | -G_re] over the K halves
+// (re, im of y2), so that D = A B^T gives the real (rows < 64) and imaginary
+// (rows >= 64) parts of W in the planar order of W's rows.
+// B (N x 2M): y2 read as a Hankel matrix. The tile's lags are split into 8
+// phases L0 + r + 8n (n < 64); for phase r, element (n, k) of the real half
+// is y2_re[bM + L0 + r + 8n + k], which is element 8n + k of the window copy
+// shifted by r. In the canonical no-swizzle K-major layout a core matrix
+// (8 rows x 8 elements) of rows 8g .. 8g + 7 and elements 8h .. 8h + 7 is then
+// the 64 consecutive window elements from 64g + 8h: K-adjacent core matrices
+// are 16 B apart (leading byte offset) and 8-row groups 128 B apart (stride
+// byte offset), and the window copies are all the B operand there is. Each
+// phase is one MMA of N = 64 into its own 64 accumulator columns; the one
+// accumulator (512 columns) is drained by the epilogue before the next
+// tile's first MMA. The window copies (8 phases x re, im x high, residual)
+// stay in shared memory for the whole tile; the producers rebuild them for
+// the next tile once the MMAs of the previous tile have completed (acc_full).
+// ---------------------------------------------------------------------------
+constexpr int kHkPhases = 8;
+constexpr int kHkN = kHkLags / kHkPhases;                 // MMA N: lags per phase
+constexpr int kHkWin = kLagTileMaxChunk + kHkLags;        // elements of one window copy (>= M + 8 * 31)
+constexpr int kHkPlane = kHkWin * 2;                      // bytes of one 16-bit copy
+constexpr int kHkEpiWarp0 = kProducerWarps + 1;           // producers, the MMA warp, then 4 epilogue warps
+constexpr int kHkThreads = (kProducerWarps + 1 + kEpilogueWarps) * 32;
+template <int P> __host__ __device__ constexpr int hk_ring() { return P == 2 ? 3 : 4; }
+template <int P> __host__ __device__ constexpr int hk_smem_bytes()
+{
+    return hk_ring<P>() * (2 * P * kBlockBytes) + kHkPhases * 2 * P * kHkPlane +
+           (kLagTileMaxChunk + kHkWin + 8) * (int)sizeof(float2);
+}
+
+// B descriptor of a Hankel view: leading byte offset 16, stride byte offset 128.
+__device__ __forceinline__ uint64_t hdesc(uint32_t saddr)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(16 >> 4) << 16) | ((uint64_t)(128 >> 4) << 32) |
+           (1ull << 46);
+}
+
+template <int DT> __device__ __forceinline__ uint32_t idesc_hk()
+{
+    const uint32_t t = DT == DG_CONTRACT_BF16 ? 1u : 0u;
+    return (1u << 4) | (t << 7) | (t << 10) | ((uint32_t)(kHkN >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+}
+
+struct HkCache {  // per-snapshot tables of the batch, in shared memory
+    int hbase[kSnapCache + 1];
+    int bbase[kSnapCache + 1];
+    int lr[2 * kSnapCache];
+    float nubase[kSnapCache], delta[kSnapCache];
+    StepDesc sd[kSnapCache];
+};
+
+struct HkTile {
+    int s, lb, bch, NB, N, Lmin, bb;
+    StepDesc sd;
+};
+
+__device__ __forceinline__ HkTile hk_tile(const HkCache &c, int S, int tile)
+{
+    HkTile t;
+    t.s = step_of_tile(c.hbase, S, tile);
+    const int lt = tile - c.hbase[t.s];
+    t.sd = c.sd[t.s];
+    t.N = t.sd.n;
+    const int lo = c.lr[2 * t.s], hi = c.lr[2 * t.s + 1];
+    t.NB = hi >= lo ? hi - lo + 1 : 0;
+    if (t.NB > c.bbase[t.s + 1] - c.bbase[t.s]) t.NB = 0;  // as the planner: no tiles then
+    const int NLB = max((t.NB + kHkLags - 1) / kHkLags, 1);
+    t.lb = lt % NLB;
+    t.bch = lt / NLB;
+    t.Lmin = lo;
+    t.bb = c.bbase[t.s];
+    return t;
+}
+
+template <int FMT, int DT, int P>
+__global__ void __launch_bounds__(kHkThreads, 1) k_cdft_contract_hk(CdftBatch a)
+{
+    constexpr int NA = hk_ring<P>();
+    constexpr int kSt = 2 * P * kBlockBytes;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full_a[NA], empty_a[NA], acc_full[2], acc_empty[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int s_abort;
+    __shared__ HkCache sc;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *sA0 = smem;
+    unsigned char *sW = smem + NA * kSt;  // window copies [phase][part][re, im] of kHkPlane bytes
+    float2 *sy1 = reinterpret_cast<float2 *>(sW + kHkPhases * 2 * P * kHkPlane);
+    float2 *sy2 = sy1 + kLagTileMaxChunk;  // kHkWin + 8 samples
+    const int M = a.M, NJ = M / kKS, S = a.S;
+
+    for (int i = threadIdx.x; i <= S; i += blockDim.x) {
+        sc.hbase[i] = a.hbase[i];
+        sc.bbase[i] = a.bbase[i];
+        if (i < S) {
+            sc.lr[2 * i] = a.lr[2 * i];
+            sc.lr[2 * i + 1] = a.lr[2 * i + 1];
+            sc.nubase[i] = a.nubase[i];
+            sc.delta[i] = a.delta[i];
+            sc.sd[i] = a.sd[i];
+        }
+    }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NA; ++i) {
+            mbar_init(smem_u32(&full_a[i]), kProducerWarps);
+            mbar_init(smem_u32(&empty_a[i]), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_u32(&acc_full[i]), 1);
+            mbar_init(smem_u32(&acc_empty[i]), kEpilogueWarps);
+        }
+        s_abort = 0;
+        fence_mbar_init();
+        fence_proxy_async_smem();
+    }
+    if (warp == 0) tmem_alloc(smem_u32(&tmem_slot), kHkLags);
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = tmem_slot;
+    const int ntiles = sc.hbase[S];
+    const int mine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const float zs = sqrtf(a.zscale);  // on y1 and on y2: their product carries zscale
+
+    if (warp < kProducerWarps) {
+        // ---------------- producers
+        const int part = warp >> 3, qset = warp & 7;
+        const int rin = lane & 7, kg = lane >> 3;
+        const int q = 8 * qset + rin;
+        const int ptid = threadIdx.x, pthreads = kProducerWarps * 32;
+        for (int it = 0; it < mine; ++it) {
+            // the window copies are free once the previous tile's MMAs have
+            // completed; all producers leave together on an abort
+            bool fail = false;
+            if (ptid == 0 && it >= 1) fail = !mbar_wait(smem_u32(&acc_full[0]), (uint32_t)(it - 1) & 1u);
+            if (producers_sync_or(fail || s_abort != 0)) {
+                s_abort = 1;
+                break;
+            }
+            const int tile = (int)blockIdx.x + it * (int)gridDim.x;
+            const HkTile t = hk_tile(sc, S, tile);
+            const int nb0 = t.bch * M, L0 = t.Lmin + t.lb * kHkLags;
+            for (int i = ptid; i < M; i += pthreads) {
+                const int n = nb0 + i;
+                const float2 v = n < t.N ? IQ<FMT>::load(t.sd.y1, n) : make_float2(0.f, 0.f);
+                sy1[i] = make_float2(v.x * zs, v.y * zs);
+            }
+            for (int i = ptid; i < kHkWin + 8; i += pthreads) {
+                const int n2 = nb0 + L0 + i;
+                const float2 v = (n2 >= 0 && n2 < t.N) ? IQ<FMT>::load(t.sd.y2, n2) : make_float2(0.f, 0.f);
+                sy2[i] = make_float2(v.x * zs, v.y * zs);
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(kProducerWarps * 32) : "memory");
+            // window copies: copy r element e = y2 window sample r + e, 8 elements per task
+            for (int task = ptid; task < kHkPhases * (kHkWin / 8); task += pthreads) {
+                const int r = task / (kHkWin / 8), e0 = 8 * (task % (kHkWin / 8));
+                float vr[8], vi[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float2 v = sy2[r + e0 + u];
+                    vr[u] = v.x;
+                    vi[u] = v.y;
+                }
+                uint32_t hr[4], hi[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    hr[u] = pack2<DT>(vr[2 * u], vr[2 * u + 1]);
+                    hi[u] = pack2<DT>(vi[2 * u], vi[2 * u + 1]);
+                }
+                unsigned char *base = sW + (size_t)r * 2 * P * kHkPlane + 2 * e0;
+                *reinterpret_cast<uint4 *>(base) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+                *reinterpret_cast<uint4 *>(base + kHkPlane) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                if (P == 2) {
+                    uint32_t lr[4], li[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float2 fr = unpack2<DT>(hr[u]), fi = unpack2<DT>(hi[u]);
+                        lr[u] = pack2<DT>(vr[2 * u] - fr.x, vr[2 * u + 1] - fr.y);
+                        li[u] = pack2<DT>(vi[2 * u] - fi.x, vi[2 * u + 1] - fi.y);
+                    }
+                    *reinterpret_cast<uint4 *>(base + 2 * kHkPlane) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
+                    *reinterpret_cast<uint4 *>(base + 3 * kHkPlane) = make_uint4(li[0], li[1], li[2], li[3]);
+                }
+            }
+            // A of every stage: G_q[m] = y1[m] e^{j 2 pi nu_q m} (the bin
+            // frequency in FP32 and the phase of sample m from the exact
+            // product split, as the DFT tables form them)
+            const float nuq = fmaf((float)q, sc.delta[t.s], sc.nubase[t.s]);
+            const uint32_t g0 = (uint32_t)it * (uint32_t)NJ;
+            for (int j = 0; j < NJ; ++j) {
+                const uint32_t g = g0 + (uint32_t)j;
+                const int slot = (int)(g % NA);
+                if (g >= NA && !mbar_wait(smem_u32(&empty_a[slot]), ((g / NA) - 1) & 1u)) s_abort = 1;
+                if (s_abort) break;
+                unsigned char *sA = sA0 + slot * kSt;
+                const int m0 = j * kKS + 8 * kg;
+                float gv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float2 x = sy1[m0 + u];
+                    float sn, cs;
+                    sincospif(2.0f * frac_mul(nuq, (float)(m0 + u)), &sn, &cs);
+                    gv[u] = part == 0 ? fmaf(x.x, cs, -x.y * sn) : fmaf(x.x, sn, x.y * cs);
+                }
+                // part 0 (G_re): row q of the y2_re half, row 64 + q of the y2_im half (negated);
+                // part 1 (G_im): row 64 + q of the y2_re half, row q of the y2_im half
+                const int row0 = part == 0 ? q : 64 + q, row1 = part == 0 ? 64 + q : q;
+                const float sg = part == 0 ? -1.f : 1.f;
+                uint32_t h0[4], h1[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    h0[u] = pack2<DT>(gv[2 * u], gv[2 * u + 1]);
+                    h1[u] = pack2<DT>(sg * gv[2 * u], sg * gv[2 * u + 1]);
+                }
+                *reinterpret_cast<uint4 *>(sA + blk_off(row0, 8 * kg)) = make_uint4(h0[0], h0[1], h0[2], h0[3]);
+                *reinterpret_cast<uint4 *>(sA + kBlockBytes + blk_off(row1, 8 * kg)) =
+                    make_uint4(h1[0], h1[1], h1[2], h1[3]);
+                if (P == 2) {
+                    uint32_t l0[4], l1[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float2 f0 = unpack2<DT>(h0[u]), f1 = unpack2<DT>(h1[u]);
+                        l0[u] = pack2<DT>(gv[2 * u] - f0.x, gv[2 * u + 1] - f0.y);
+                        l1[u] = pack2<DT>(sg * gv[2 * u] - f1.x, sg * gv[2 * u + 1] - f1.y);
+                    }
+                    *reinterpret_cast<uint4 *>(sA + 2 * kBlockBytes + blk_off(row0, 8 * kg)) =
+                        make_uint4(l0[0], l0[1], l0[2], l0[3]);
+                    *reinterpret_cast<uint4 *>(sA + 3 * kBlockBytes + blk_off(row1, 8 * kg)) =
+                        make_uint4(l1[0], l1[1], l1[2], l1[3]);
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&full_a[slot]));
+            }
+        }
+    } else if (warp == kMmaWarp) {
+        // ---------------- MMA thread: one accumulator of kHkLags columns;
+        // descriptors are formed by adding byte offsets >> 4 to base
+        // descriptors (the start field cannot carry: shared memory < 256 KB)
+        if (lane == 0) {
+            const uint32_t id = idesc_hk<DT>();
+            const uint64_t a0 = sdesc(smem_u32(sA0)), w0 = hdesc(smem_u32(sW));
+            bool alive = true;
+            for (int it = 0; it < mine && alive && !s_abort; ++it) {
+                const uint32_t g0 = (uint32_t)it * (uint32_t)NJ;
+                // the accumulator was drained (tile it - 1)
+                if (it >= 1 && !mbar_wait(smem_u32(&acc_empty[0]), ((uint32_t)(it - 1)) & 1u)) {
+                    alive = false;
+                    break;
+                }
+                tc_after_sync();
+                for (int j = 0; j < NJ; ++j) {
+                    const uint32_t g = g0 + (uint32_t)j;
+                    const int sa = (int)(g % NA);
+                    if (!mbar_wait(smem_u32(&full_a[sa]), (g / NA) & 1u) || s_abort) {
+                        alive = false;
+                        break;
+                    }
+                    tc_after_sync();
+                    const uint64_t as = a0 + (uint64_t)((sa * kSt) >> 4);
+                    const uint64_t ws = w0 + (uint64_t)((2 * j * kKS) >> 4);
+                    constexpr int NPROD = P == 2 ? 3 : 1;
+#pragma unroll
+                    for (int blk = 0; blk < 2; ++blk)
+#pragma unroll
+                        for (int kk = 0; kk < kKS; kk += 16)
+#pragma unroll
+                            for (int pr = 0; pr < NPROD; ++pr) {
+                                const int pa = pr == 1 ? 1 : 0, pb = pr == 2 ? 1 : 0;
+                                const uint64_t ad = as + (uint64_t)(((2 * pa + blk) * kBlockBytes + kk * 16) >> 4);
+                                const uint64_t bd = ws + (uint64_t)(((2 * pb + blk) * kHkPlane + 2 * kk) >> 4);
+                                const uint32_t accf = (j > 0 || blk > 0 || kk > 0 || pr > 0) ? 1u : 0u;
+#pragma unroll
+                                for (int r = 0; r < kHkPhases; ++r)
+                                    mma_f16(tmem + (uint32_t)(kHkN * r), ad,
+                                            bd + (uint64_t)((r * 2 * P * kHkPlane) >> 4), id, accf);
+                            }
+                    mma_commit(smem_u32(&empty_a[sa]));
+                    if (j == NJ - 1) mma_commit(smem_u32(&acc_full[0]));
+                }
+            }
+            if (!alive) s_abort = 1;
+        }
+    } else {
+        // ---------------- drain finished accumulators: the last four warps
+        const int qw = warp & 3;
+        for (int it = 1; it <= mine && !s_abort; ++it) {
+            const int d = it - 1;
+            if (!mbar_wait(smem_u32(&acc_full[0]), (uint32_t)d & 1u)) {
+                s_abort = 1;
+                break;
+            }
+            tc_after_sync();
+            const HkTile t = hk_tile(sc, S, (int)blockIdx.x + d * (int)gridDim.x);
+            const int row = 32 * qw + lane;
+            const float inv = 1.0f / a.zscale;
+            const uint32_t tb = tmem + ((uint32_t)(32 * qw) << 16);
+#pragma unroll 1
+            for (int c0 = 0; c0 < kHkLags; c0 += 32) {  // 32 columns of phase c0 / kHkN at a time
+                uint32_t v[32];
+                tmem_ld32(tb + (uint32_t)c0, v);
+                const int r = c0 / kHkN, nb = c0 % kHkN;
+#pragma unroll 4
+                for (int u = 0; u < 32; ++u) {
+                    const int bl = t.lb * kHkLags + r + 8 * (nb + u);
+                    if (bl < t.NB && a.count[t.bb + bl] > 0)
+                        a.W[((int64_t)(t.bb + bl) * a.Bmax + t.bch) * 128 + row] = __uint_as_float(v[u]) * inv;
+                }
+            }
+            tc_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&acc_empty[0]));
+        }
+    }
+    __syncthreads();
+    if (s_abort && mine > 0 && threadIdx.x == 0) {
+        mbar_wait(smem_u32(&acc_full[0]), (uint32_t)(mine - 1) & 1u);
+        atomicOr(a.err, ERR_TIMEOUT);
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (warp == 0) tmem_dealloc(tmem, kHkLags);
+}
+
 cudaError_t launch_cdft_btab(const CdftBatch &a, int mode, void *btab, cudaStream_t st)
 {
     const size_t n = (size_t)(a.M / kKS) * 2 * kRows * kKS;
@@ -869,6 +1201,26 @@ static cudaError_t launch_mma(const CdftBatch &a, int grid, cudaStream_t st)
     return cudaGetLastError();
 }
 
+template <int FMT, int DT, int P>
+static cudaError_t launch_hk(const CdftBatch &a, int grid, cudaStream_t st)
+{
+    const int smem = hk_smem_bytes<P>();
+    cudaError_t e = cudaFuncSetAttribute(k_cdft_contract_hk<FMT, DT, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_cdft_contract_hk<FMT, DT, P><<<(unsigned)grid, kHkThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int DT, int P>
+static cudaError_t launch_hk_fmt(const CdftBatch &a, int grid, int fmt, cudaStream_t st)
+{
+    switch (fmt) {
+    case DG_IQ_C64: return launch_hk<DG_IQ_C64, DT, P>(a, grid, st);
+    case DG_IQ_CI16: return launch_hk<DG_IQ_CI16, DT, P>(a, grid, st);
+    default: return launch_hk<DG_IQ_CI8, DT, P>(a, grid, st);
+    }
+}
+
 template <int DT, int P>
 static cudaError_t launch_fmt(const CdftBatch &a, int tiles, int fmt, cudaStream_t st)
 {
@@ -886,6 +1238,16 @@ cudaError_t launch_cdft_contract_mma(const CdftBatch &a, int tiles, int fmt, int
     case DG_CONTRACT_FP16: return launch_fmt<DG_CONTRACT_FP16, 1>(a, tiles, fmt, st);
     case DG_CONTRACT_BF16X3: return launch_fmt<DG_CONTRACT_BF16, 2>(a, tiles, fmt, st);
     default: return launch_fmt<DG_CONTRACT_FP16, 2>(a, tiles, fmt, st);
+    }
+}
+
+cudaError_t launch_cdft_contract_hankel(const CdftBatch &a, int grid, int fmt, int mode, cudaStream_t st)
+{
+    switch (mode) {
+    case DG_CONTRACT_BF16: return launch_hk_fmt<DG_CONTRACT_BF16, 1>(a, grid, fmt, st);
+    case DG_CONTRACT_FP16: return launch_hk_fmt<DG_CONTRACT_FP16, 1>(a, grid, fmt, st);
+    case DG_CONTRACT_BF16X3: return launch_hk_fmt<DG_CONTRACT_BF16, 2>(a, grid, fmt, st);
+    default: return launch_hk_fmt<DG_CONTRACT_FP16, 2>(a, grid, fmt, st);
     }
 }
 

@@ -328,6 +328,7 @@ struct CdftBatch {
     float2 *V;                    // [S][M][64] DFT table e^{j 2 pi nu_q m}
     float *W;                     // [NBT][Bmax][128]: per chunk 64 bins, re[64] | im[64]
     int *tbase;                   // [S + 1] first tensor-core tile of each snapshot (k_cdft_tiles)
+    int *hbase;                   // [S + 1] first Hankel tile of each snapshot (k_cdft_tiles)
     int *layout;                  // [S] 1: tiles of 128 lags x one chunk, 0: 128 (lag, chunk) rows
     int *Mcs;                     // [S] combine chunk: a power-of-two multiple of M (k_cdft_tiles)
     unsigned long long *work;     // [2] lag x chunk rows, candidate x super-chunk pairs (or NULL)
@@ -354,10 +355,13 @@ cudaError_t launch_cdft_superchunk(const CdftBatch &a, int NBT, cudaStream_t s);
 // BF16X3 / FP16X3; a persistent launch of `grid` CTAs over the batch's tiles
 cudaError_t launch_cdft_btab(const CdftBatch &a, int mode, void *btab, cudaStream_t s);
 cudaError_t launch_cdft_contract_mma(const CdftBatch &a, int grid, int fmt, int mode, cudaStream_t s);
+// The Hankel tiles of the batch (k_cdft_contract_hk), persistent over `grid` CTAs.
+cudaError_t launch_cdft_contract_hankel(const CdftBatch &a, int grid, int fmt, int mode, cudaStream_t s);
 size_t cdft_btab_bytes(int mode, int M);  // per snapshot
 // Lag tiles (128 consecutive lags of one chunk share one y1 segment and one
 // y2 window, staged once in shared memory) need chunk <= this.
 constexpr int kLagTileMaxChunk = 1024;
+constexpr int kHkLags = 512;                     // lags of one Hankel tile (8 phases of 64)
 // Snapshots per batch on the tensor-core path (the contraction caches their
 // tables in shared memory).
 constexpr int kTcMaxSnapshots = 64;

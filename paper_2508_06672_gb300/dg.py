@@ -42,7 +42,7 @@ DG_ACC_POWER, DG_ACC_MAG = 0, 1
 DG_PREC_FP32, DG_PREC_FP64 = 0, 1
 DG_ALGO_DIRECT, DG_ALGO_CDFT = 0, 1
 DG_CONTRACT_FP32, DG_CONTRACT_BF16, DG_CONTRACT_FP16, DG_CONTRACT_BF16X3, DG_CONTRACT_FP16X3 = 0, 1, 2, 3, 4
-DG_TILES_AUTO, DG_TILES_ROWS, DG_TILES_LAGS = 0, 1, 2
+DG_TILES_AUTO, DG_TILES_ROWS, DG_TILES_LAGS, DG_TILES_HANKEL = 0, 1, 2, 3
 DG_K_CORR, DG_K_ACCUM, DG_K_ARGMAX, DG_K_GRID, DG_K_REFINE = 0, 1, 2, 3, 4
 DG_K_CDFT_PLAN, DG_K_CDFT_CONTRACT, DG_K_CDFT_COMBINE, DG_K_COARSE = 5, 6, 7, 8
 
@@ -52,7 +52,7 @@ _DELAY = {"integer": DG_DELAY_INTEGER, "lagrange4": DG_DELAY_LAGRANGE4}
 _ACC = {"power": DG_ACC_POWER, "mag": DG_ACC_MAG}
 _PREC = {"fp32": DG_PREC_FP32, "fp64": DG_PREC_FP64}
 _ALGO = {"direct": DG_ALGO_DIRECT, "cdft": DG_ALGO_CDFT}
-_TILES = {"auto": DG_TILES_AUTO, "rows": DG_TILES_ROWS, "lags": DG_TILES_LAGS}
+_TILES = {"auto": DG_TILES_AUTO, "rows": DG_TILES_ROWS, "lags": DG_TILES_LAGS, "hankel": DG_TILES_HANKEL}
 _CONTRACT = {"fp32": DG_CONTRACT_FP32, "bf16": DG_CONTRACT_BF16, "fp16": DG_CONTRACT_FP16,
              "bf16x3": DG_CONTRACT_BF16X3, "fp16x3": DG_CONTRACT_FP16X3}
 

@@ -56,6 +56,50 @@ def test_cdft_lag_tiles_match_row_tiles(fmt, contract):
     assert rel_err(out["lags"].ravel()[ok], ref.ravel()[ok], 0.01) < tol
 
 
+@pytest.mark.parametrize("fmt", ["c64", "ci16", "ci8"])
+@pytest.mark.parametrize("contract", ["bf16x3", "fp16x3", "bf16", "fp16"])
+def test_cdft_hankel_tiles(fmt, contract):
+    """Hankel tiles (256 lags at one chunk; the DFT regrouped onto y1 and y2
+    read as a Hankel matrix from shared memory) against the oracle within the
+    form's bound, and against row tiles within twice it: two tiles of 512
+    lags over 75 .. 707 (a ragged last tile), a ragged last chunk, and y2
+    windows that run off the end of the capture."""
+    s = sim.make_scene(seed=24, fs_hz=20e6, n_samples=5000, k_steps=2, fmt=fmt, waveform="noise",
+                       snr_db=-3.0, grid_n=(45, 41), grid_spacing_m=2000.0, bw_hz=18e6)
+    out = {}
+    for tiles in ("rows", "hankel"):
+        g, c = gpu_surface(s, algo="cdft", contract=contract, chunk=1024, tiles=tiles)
+        out[tiles] = c
+        g.close()
+    ref = oracle_surface(s)
+    ok = ~lag_boundary_mask(s, np.arange(s.G))
+    tol = TC_TOL[contract] if contract.endswith("x3") else 3e-2
+    assert rel_err(out["hankel"].ravel()[ok], ref.ravel()[ok], 0.01) < tol
+    assert rel_err(out["hankel"].ravel(), out["rows"].ravel(), 0.01) < 2 * tol
+
+
+@pytest.mark.parametrize("chunk", [256, 512])
+def test_cdft_hankel_shorter_chunks_and_auto(chunk):
+    """Shorter chunks (fewer stages per tile), Hankel tiles against the
+    oracle and AUTO beside them, and a grid of a few lags (row tiles)."""
+    s = sim.make_scene(seed=27, fs_hz=12.5e6, n_samples=6000, k_steps=3, fmt="ci16", waveform="chirp",
+                       snr_db=-3.0, grid_n=(33, 37), grid_spacing_m=3000.0)
+    ref = oracle_surface(s)
+    ok = ~lag_boundary_mask(s, np.arange(s.G))
+    for tiles in ("hankel", "auto"):
+        g, c = gpu_surface(s, algo="cdft", contract="bf16x3", chunk=chunk, tiles=tiles)
+        assert rel_err(c.ravel()[ok], ref.ravel()[ok], 0.01) < TC_TOL["bf16x3"]
+        g.close()
+    # a grid of a few lags: AUTO picks row tiles there
+    s2 = sim.make_scene(seed=28, fs_hz=12.5e6, n_samples=6000, k_steps=2, fmt="ci16", waveform="chirp",
+                        snr_db=-3.0, grid_n=(9, 9), grid_spacing_m=50.0)
+    g, c = gpu_surface(s2, algo="cdft", contract="bf16x3", chunk=chunk)
+    ref2 = oracle_surface(s2)
+    ok2 = ~lag_boundary_mask(s2, np.arange(s2.G))
+    assert rel_err(c.ravel()[ok2], ref2.ravel()[ok2], 0.01) < TC_TOL["bf16x3"]
+    g.close()
+
+
 def test_cdft_auto_chunk():
     """chunk 0: each batch takes the longest power-of-two chunk up to 1024
     whose length times the estimated bin spacing stays within the bound (with
