@@ -43,12 +43,41 @@ __global__ void __launch_bounds__(128) k_conv3x3_tiled(const float *__restrict__
                                                         const float *__restrict__ b, float *__restrict__ y, int CI,
                                                         int CO, int H, int W)
 {
+    // per-thread shares of the window (kXR x kXC) and of the weights (9 x kOC)
+    constexpr int kXPer = (kXR * kXC + 127) / 128, kWPer = (9 * kOC + 127) / 128;
     __shared__ __align__(16) float xs[kXR][kXS];
     __shared__ __align__(16) float ws[9][kOC];
     const int ocb = (CO + kOC - 1) / kOC;
     const int n = blockIdx.z / ocb, oc0 = (blockIdx.z % ocb) * kOC;
     const int i0 = blockIdx.y * kTH, j0 = blockIdx.x * kTW;
     const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+    // the window elements and weights this thread stages, resolved once:
+    // source offset within a channel plane (or -1: zero padding) and slot
+    int xoff[kXPer], xslot[kXPer], woff[kWPer], wslot[kWPer];
+#pragma unroll
+    for (int e = 0; e < kXPer; ++e) {
+        const int idx = threadIdx.x + 128 * e;
+        const int r = idx / kXC, cc = idx % kXC;
+        const int gi = i0 + r - 1, gj = j0 + cc - 1;
+        xslot[e] = idx < kXR * kXC ? r * kXS + cc : -1;
+        xoff[e] = (idx < kXR * kXC && gi >= 0 && gi < H && gj >= 0 && gj < W) ? gi * W + gj : -1;
+    }
+#pragma unroll
+    for (int e = 0; e < kWPer; ++e) {
+        const int idx = threadIdx.x + 128 * e;
+        const int t = idx / kOC, o = idx % kOC, oc = oc0 + o;
+        wslot[e] = idx < 9 * kOC ? t * kOC + o : -1;
+        woff[e] = (idx < 9 * kOC && oc < CO) ? (TR ? oc * 9 + (8 - t) : oc * CI * 9 + t) : -1;
+    }
+    const size_t plane = (size_t)H * W;
+    const float *xn = x + (size_t)n * CI * plane;
+    // weight of (oc, ic, tap): w[(oc CI + ic) 9 + tap]; transposed: w[(ic CO + oc) 9 + 8 - tap]
+    const size_t wstep = TR ? (size_t)CO * 9 : 9;
+    float px[kXPer], pw[kWPer];
+#pragma unroll
+    for (int e = 0; e < kXPer; ++e) px[e] = xoff[e] >= 0 ? __ldg(xn + xoff[e]) : 0.f;
+#pragma unroll
+    for (int e = 0; e < kWPer; ++e) pw[e] = woff[e] >= 0 ? __ldg(w + woff[e]) : 0.f;
     float acc[kOC][kPX];
 #pragma unroll
     for (int o = 0; o < kOC; ++o)
@@ -56,20 +85,21 @@ __global__ void __launch_bounds__(128) k_conv3x3_tiled(const float *__restrict__
         for (int p = 0; p < kPX; ++p) acc[o][p] = 0.f;
     for (int ic = 0; ic < CI; ++ic) {
         __syncthreads();
-        const float *xc = x + ((size_t)n * CI + ic) * H * W;
-        for (int idx = threadIdx.x; idx < kXR * kXC; idx += 128) {
-            const int r = idx / kXC, cc = idx % kXC;
-            const int gi = i0 + r - 1, gj = j0 + cc - 1;
-            xs[r][cc] = (gi >= 0 && gi < H && gj >= 0 && gj < W) ? __ldg(xc + (size_t)gi * W + gj) : 0.f;
-        }
-        for (int idx = threadIdx.x; idx < 9 * kOC; idx += 128) {
-            const int t = idx / kOC, o = idx % kOC, oc = oc0 + o;
-            float v = 0.f;
-            if (oc < CO)
-                v = TR ? __ldg(w + ((size_t)ic * CO + oc) * 9 + (8 - t)) : __ldg(w + ((size_t)oc * CI + ic) * 9 + t);
-            ws[t][o] = v;
-        }
+#pragma unroll
+        for (int e = 0; e < kXPer; ++e)
+            if (xslot[e] >= 0) (&xs[0][0])[xslot[e]] = px[e];
+#pragma unroll
+        for (int e = 0; e < kWPer; ++e)
+            if (wslot[e] >= 0) (&ws[0][0])[wslot[e]] = pw[e];
         __syncthreads();
+        if (ic + 1 < CI) {  // the next channel's loads, in flight during this channel's FMAs
+            const float *xc = xn + (size_t)(ic + 1) * plane;
+            const float *wc = w + (size_t)(ic + 1) * wstep;
+#pragma unroll
+            for (int e = 0; e < kXPer; ++e) px[e] = xoff[e] >= 0 ? __ldg(xc + xoff[e]) : 0.f;
+#pragma unroll
+            for (int e = 0; e < kWPer; ++e) pw[e] = woff[e] >= 0 ? __ldg(wc + woff[e]) : 0.f;
+        }
 #pragma unroll
         for (int u = 0; u < 3; ++u) {
             const float4 xa = *reinterpret_cast<const float4 *>(&xs[ty + u][4 * tx]);

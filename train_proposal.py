@@ -45,7 +45,25 @@ def main(argv=None):
     ap.add_argument("--out", default="")
     ap.add_argument("--weights", default="", help="evaluate these weights instead of training")
     ap.add_argument("--report", default="")
+    ap.add_argument("--profile-kernels", action="store_true",
+                    help="only run the coarse maps and the network forward on one scene, 3 times (a small "
+                         "case for a profiler: ~0.5 GB of device memory)")
     args = ap.parse_args(argv)
+    if args.profile_kernels:
+        import torch
+        from paper_2508_06672_gb300 import learned as L
+        from paper_2508_06672_gb300.proposal import ProposalNet
+        sc = scene(5)
+        net = ProposalNet.load(args.weights or os.path.join(ROOT, "paper_2508_06672_gb300", "weights",
+                                                            "proposal_2000km.npz"))
+        search = L.LearnedSearch(sc["grid"], sc["ephem"], sc["fs"], sc["fc"], net, cells=args.cells)
+        search.load_captures(sc["fmt"], torch.from_numpy(sc["y1"]).cuda(), torch.from_numpy(sc["y2"]).cuda())
+        for _ in range(3):
+            search.heatmap()
+        torch.cuda.synchronize()
+        search.close()
+        print("profiled: coarse maps + network forward x 3")
+        return
     ctx = mp.get_context("spawn")
     with ctx.Pool(args.workers or max(1, min(16, (os.cpu_count() or 2) - 1))) as pool:
         def scenes(seeds):
