@@ -149,6 +149,28 @@ __device__ __forceinline__ void mma_f16(uint32_t d, uint64_t ad, uint64_t bd, ui
         : "memory");
 }
 
+// The same MMA with A in tensor memory (128 lanes = rows, K along columns,
+// two 16-bit elements per 32-bit column, the even one in the low half).
+__device__ __forceinline__ void mma_f16_ta(uint32_t d, uint32_t at, uint64_t bd, uint32_t id, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d),
+        "r"(at), "l"(bd), "r"(id), "r"(acc)
+        : "memory");
+}
+
+// 4 consecutive 32-bit columns of this thread's tensor-memory lane.
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t (&r)[4])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(r[0]), "r"(r[1]),
+                 "r"(r[2]), "r"(r[3])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void mma_commit(uint32_t bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -453,8 +475,14 @@ template <int P> __host__ __device__ constexpr int ring_a() { return P == 2 ? 3 
 template <int P> __host__ __device__ constexpr int ring_b() { return P == 2 ? 3 : 6; }
 template <int P> __host__ __device__ constexpr int ws_smem_bytes()
 {
-    return (ring_a<P>() + ring_b<P>()) * (2 * P * kBlockBytes);
+    return ring_b<P>() * (2 * P * kBlockBytes);  // the A stages live in tensor memory
 }
+// tensor memory: two accumulators of 128 columns, then the A ring, each stage
+// (high, residual) x (re, im) blocks of 16 columns (32 samples)
+constexpr int kAccCols = 256;
+template <int P> __host__ __device__ constexpr int a_stage_cols() { return 2 * P * 16; }
+static_assert(kAccCols + 3 * a_stage_cols<2>() <= 512 && kAccCols + 4 * a_stage_cols<1>() <= 512,
+              "accumulators and the A ring must fit the 512 tensor-memory columns");
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
@@ -577,9 +605,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
     __shared__ SnapCache sc;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char *sA0 = smem;
-    unsigned char *sB0 = smem + NA * kSt;
-    float2 *sy1 = reinterpret_cast<float2 *>(smem + (NA + NB) * kSt);
+    unsigned char *sB0 = smem;
+    float2 *sy1 = reinterpret_cast<float2 *>(smem + NB * kSt);
     float2 *sy2 = sy1 + kLagTileMaxChunk;
     const int M = a.M, NJ = M / kKS, S = a.S;
 
@@ -610,7 +637,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
         fence_mbar_init();
         fence_proxy_async_smem();
     }
-    if (warp == 0) tmem_alloc(smem_u32(&tmem_slot), 256);
+    if (warp == 0) tmem_alloc(smem_u32(&tmem_slot), 512);
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
@@ -620,8 +647,13 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
     const float zs = a.zscale;
 
     if (warp < kProducerWarps) {
-        // ---------------- producers
-        const int rin = lane & 7, kg = lane >> 3;
+        // ---------------- producers: lane l of warp w forms row 32 (w % 4) + l
+        // (a warp reaches only its quarter of the tensor-memory lanes), samples
+        // 8 (w / 4) .. 8 (w / 4) + 7 of every 32-sample stage, and writes them
+        // with tcgen05.st into the stage's A columns
+        const int qd = warp & 3, sg = warp >> 2;
+        const int row = 32 * qd + lane;
+        const uint32_t tlane = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(kAccCols + 4 * sg);
         for (int it = 0; it < mine; ++it) {
             // every producer is done with the previous tile's windows; all
             // leave together on an abort
@@ -632,19 +664,16 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                 stage_windows<FMT>(t, M, zs, sy1, sy2, threadIdx.x, kProducerWarps * 32);
                 asm volatile("bar.sync 1, %0;" ::"r"(kProducerWarps * 32) : "memory");
             }
-            int pL[kRowSets] = {}, pn0[kRowSets] = {};
-            bool pv[kRowSets] = {};
+            int pL = 0, pn0 = 0;
+            bool pv = false;
             if (!t.lay) {
                 const int64_t R = (int64_t)t.NB * t.Bs;
-#pragma unroll
-                for (int h = 0; h < kRowSets; ++h) {
-                    const int64_t g = (int64_t)t.ltile * kRows + 8 * (kRowSets * warp + h) + rin;
-                    if (g < R) {
-                        const int bl = (int)(g / t.Bs);
-                        pn0[h] = (int)(g % t.Bs) * M + 8 * kg;
-                        pL[h] = t.Lmin + bl;
-                        pv[h] = a.count[t.bb + bl] > 0;
-                    }
+                const int64_t g = (int64_t)t.ltile * kRows + row;
+                if (g < R) {
+                    const int bl = (int)(g / t.Bs);
+                    pn0 = (int)(g % t.Bs) * M + 8 * sg;
+                    pL = t.Lmin + bl;
+                    pv = a.count[t.bb + bl] > 0;
                 }
             }
             const uint32_t g0 = (uint32_t)it * (uint32_t)NJ;
@@ -653,63 +682,55 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                 const int slot = (int)(g % NA);
                 if (g >= NA && !mbar_wait(smem_u32(&empty_a[slot]), ((g / NA) - 1) & 1u)) s_abort = 1;
                 if (s_abort) break;
-                unsigned char *sA = sA0 + slot * kSt;
-                float2 x[8];
+                tc_after_sync();
+                float2 x[8], y[8];
                 if (t.lay) {
-                    const int m0 = j * kKS + 8 * kg;
+                    const int m0 = j * kKS + 8 * sg;
 #pragma unroll
                     for (int u = 0; u < 8; u += 2) {
                         const float4 q = *reinterpret_cast<const float4 *>(sy1 + m0 + u);
                         x[u] = make_float2(q.x, q.y);
                         x[u + 1] = make_float2(q.z, q.w);
                     }
+                    const float2 *py = sy2 + m0 + row;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) y[u] = py[u];
+                } else {
+                    Raw<FMT> raw;
+                    const int n = pn0 + j * kKS;
+                    raw.fetch(t.sd.y1, t.sd.y2, n, n + pL, t.N, pv);
+                    raw.decode(t.sd.y1, t.sd.y2, t.N, pv, x, y);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) x[u] = make_float2(x[u].x * zs, x[u].y * zs);
                 }
+                float zr[8], zi[8];
 #pragma unroll
-                for (int h = 0; h < kRowSets; ++h) {
-                    const int row = 8 * (kRowSets * warp + h) + rin;
-                    float2 y[8];
-                    if (t.lay) {
-                        const float2 *py = sy2 + j * kKS + 8 * kg + row;
+                for (int u = 0; u < 8; ++u) {
+                    zr[u] = fmaf(x[u].x, y[u].x, x[u].y * y[u].y);
+                    zi[u] = fmaf(x[u].y, y[u].x, -x[u].x * y[u].y);
+                }
+                uint32_t hr[4], hi[4];
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) y[u] = py[u];
-                    } else {
-                        Raw<FMT> raw;
-                        const int n = pn0[h] + j * kKS;
-                        raw.fetch(t.sd.y1, t.sd.y2, n, n + pL[h], t.N, pv[h]);
-                        raw.decode(t.sd.y1, t.sd.y2, t.N, pv[h], x, y);
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) x[u] = make_float2(x[u].x * zs, x[u].y * zs);
-                    }
-                    float zr[8], zi[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        zr[u] = fmaf(x[u].x, y[u].x, x[u].y * y[u].y);
-                        zi[u] = fmaf(x[u].y, y[u].x, -x[u].x * y[u].y);
-                    }
-                    uint32_t hr[4], hi[4];
+                for (int u = 0; u < 4; ++u) {
+                    hr[u] = pack2<DT>(zr[2 * u], zr[2 * u + 1]);
+                    hi[u] = pack2<DT>(zi[2 * u], zi[2 * u + 1]);
+                }
+                const uint32_t ta = tlane + (uint32_t)(slot * a_stage_cols<P>());
+                tmem_st4(ta, hr);       // high part, multiplies the re rows of B
+                tmem_st4(ta + 16, hi);  // high part, im rows
+                if (P == 2) {  // residuals z - high part, rounded to 16 bits
+                    uint32_t lr[4], li[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        hr[u] = pack2<DT>(zr[2 * u], zr[2 * u + 1]);
-                        hi[u] = pack2<DT>(zi[2 * u], zi[2 * u + 1]);
+                        const float2 fr = unpack2<DT>(hr[u]), fi = unpack2<DT>(hi[u]);
+                        lr[u] = pack2<DT>(zr[2 * u] - fr.x, zr[2 * u + 1] - fr.y);
+                        li[u] = pack2<DT>(zi[2 * u] - fi.x, zi[2 * u + 1] - fi.y);
                     }
-                    *reinterpret_cast<uint4 *>(sA + blk_off(row, 8 * kg)) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
-                    *reinterpret_cast<uint4 *>(sA + kBlockBytes + blk_off(row, 8 * kg)) =
-                        make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                    if (P == 2) {  // residuals z - high part, rounded to 16 bits
-                        uint32_t lr[4], li[4];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const float2 fr = unpack2<DT>(hr[u]), fi = unpack2<DT>(hi[u]);
-                            lr[u] = pack2<DT>(zr[2 * u] - fr.x, zr[2 * u + 1] - fr.y);
-                            li[u] = pack2<DT>(zi[2 * u] - fi.x, zi[2 * u + 1] - fi.y);
-                        }
-                        *reinterpret_cast<uint4 *>(sA + 2 * kBlockBytes + blk_off(row, 8 * kg)) =
-                            make_uint4(lr[0], lr[1], lr[2], lr[3]);
-                        *reinterpret_cast<uint4 *>(sA + 3 * kBlockBytes + blk_off(row, 8 * kg)) =
-                            make_uint4(li[0], li[1], li[2], li[3]);
-                    }
+                    tmem_st4(ta + 32, lr);
+                    tmem_st4(ta + 48, li);
                 }
-                fence_proxy_async_smem();
+                tmem_wait_st();
+                tc_before_sync();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&full_a[slot]));
             }
@@ -762,7 +783,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                         break;
                     }
                     tc_after_sync();
-                    const unsigned char *sA = sA0 + sa * kSt;
+                    const uint32_t at0 = tmem + (uint32_t)(kAccCols + sa * a_stage_cols<P>());
                     const unsigned char *sB = sB0 + sb * kSt;
                     constexpr int NPROD = P == 2 ? 3 : 1;
 #pragma unroll
@@ -772,9 +793,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
 #pragma unroll
                             for (int pr = 0; pr < NPROD; ++pr) {
                                 const int pa = pr == 1 ? 1 : 0, pb = pr == 2 ? 1 : 0;
-                                const uint64_t ad = sdesc(smem_u32(sA + (2 * pa + blk) * kBlockBytes) + kk * 16);
+                                const uint32_t at = at0 + (uint32_t)((2 * pa + blk) * 16 + kk / 2);
                                 const uint64_t bd = sdesc(smem_u32(sB + (2 * pb + blk) * kBlockBytes) + kk * 16);
-                                mma_f16(dtm, ad, bd, id, (j > 0 || blk > 0 || kk > 0 || pr > 0) ? 1u : 0u);
+                                mma_f16_ta(dtm, at, bd, id, (j > 0 || blk > 0 || kk > 0 || pr > 0) ? 1u : 0u);
                             }
                     mma_commit(smem_u32(&empty_a[sa]));
                     mma_commit(smem_u32(&empty_b[sb]));
@@ -838,7 +859,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
-    if (warp == 0) tmem_dealloc(tmem, 256);
+    if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
 // ---------------------------------------------------------------------------
