@@ -471,8 +471,8 @@ constexpr int kSnapCache = kTcMaxSnapshots;  // per-snapshot tables cached in sh
 // then the epilogue warps
 constexpr int kMmaWarp = kProducerWarps, kLoadWarp = kProducerWarps + 1;
 constexpr int kWsThreads = (kProducerWarps + 2 + kEpilogueWarps) * 32;
-template <int P> __host__ __device__ constexpr int ring_a() { return P == 2 ? 3 : 4; }
-template <int P> __host__ __device__ constexpr int ring_b() { return P == 2 ? 3 : 6; }
+template <int P> __host__ __device__ constexpr int ring_a() { return P == 2 ? 4 : 8; }
+template <int P> __host__ __device__ constexpr int ring_b() { return P == 2 ? 5 : 10; }
 template <int P> __host__ __device__ constexpr int ws_smem_bytes()
 {
     return ring_b<P>() * (2 * P * kBlockBytes);  // the A stages live in tensor memory
@@ -481,7 +481,7 @@ template <int P> __host__ __device__ constexpr int ws_smem_bytes()
 // (high, residual) x (re, im) blocks of 16 columns (32 samples)
 constexpr int kAccCols = 256;
 template <int P> __host__ __device__ constexpr int a_stage_cols() { return 2 * P * 16; }
-static_assert(kAccCols + 3 * a_stage_cols<2>() <= 512 && kAccCols + 4 * a_stage_cols<1>() <= 512,
+static_assert(kAccCols + ring_a<2>() * a_stage_cols<2>() <= 512 && kAccCols + ring_a<1>() * a_stage_cols<1>() <= 512,
               "accumulators and the A ring must fit the 512 tensor-memory columns");
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar)
