@@ -576,6 +576,71 @@ __device__ __forceinline__ void stage_windows(const TileInfo &t, int M, float zs
     }
 }
 
+// The capture windows of the next lag tile, prefetched into the producers'
+// registers while the current tile's stages run: element e of thread tid is
+// window element tid + 512 e (y1[bM + i] for i < M, then y2[bM + L0 + i - M]),
+// kept raw (2, 4 or 8 bytes) and decoded only when the tile starts.
+constexpr int kPfPer = (2 * kLagTileMaxChunk + kRows + kProducerWarps * 32 - 1) / (kProducerWarps * 32);
+template <int FMT> struct RawIQ;
+template <> struct RawIQ<DG_IQ_C64> {
+    float2 v[kPfPer];
+    __device__ __forceinline__ void load(int e, const void *b, int i) { v[e] = __ldg(reinterpret_cast<const float2 *>(b) + i); }
+    __device__ __forceinline__ void zero(int e) { v[e] = make_float2(0.f, 0.f); }
+    __device__ __forceinline__ float2 get(int e) const { return v[e]; }
+};
+template <> struct RawIQ<DG_IQ_CI16> {
+    int v[kPfPer];
+    __device__ __forceinline__ void load(int e, const void *b, int i) { v[e] = __ldg(reinterpret_cast<const int *>(b) + i); }
+    __device__ __forceinline__ void zero(int e) { v[e] = 0; }
+    __device__ __forceinline__ float2 get(int e) const
+    {
+        return make_float2((float)(short)(v[e] & 0xffff), (float)(short)(v[e] >> 16));
+    }
+};
+template <> struct RawIQ<DG_IQ_CI8> {
+    short v[kPfPer];
+    __device__ __forceinline__ void load(int e, const void *b, int i)
+    {
+        v[e] = (short)__ldg(reinterpret_cast<const unsigned short *>(b) + i);
+    }
+    __device__ __forceinline__ void zero(int e) { v[e] = 0; }
+    __device__ __forceinline__ float2 get(int e) const
+    {
+        return make_float2((float)(signed char)(v[e] & 0xff), (float)(signed char)((v[e] >> 8) & 0xff));
+    }
+};
+
+template <int FMT>
+__device__ __forceinline__ void prefetch_windows(const TileInfo &t, int M, RawIQ<FMT> &pf, int tid)
+{
+    const int nb0 = t.bch * M, L0 = t.Lmin + t.lb * kRows;
+#pragma unroll
+    for (int e = 0; e < kPfPer; ++e) {
+        const int i = tid + kProducerWarps * 32 * e;
+        int n = -1;
+        const void *src = t.sd.y1;
+        if (i < M) n = nb0 + i;
+        else if (i < 2 * M + kRows) {
+            n = nb0 + L0 + (i - M);
+            src = t.sd.y2;
+        }
+        if (n >= 0 && n < t.N) pf.load(e, src, n);
+        else pf.zero(e);
+    }
+}
+
+template <int FMT>
+__device__ __forceinline__ void store_windows(const RawIQ<FMT> &pf, int M, float zs, float2 *sy1, float2 *sy2, int tid)
+{
+#pragma unroll
+    for (int e = 0; e < kPfPer; ++e) {
+        const int i = tid + kProducerWarps * 32 * e;
+        const float2 v = pf.get(e);
+        if (i < M) sy1[i] = make_float2(v.x * zs, v.y * zs);
+        else if (i < 2 * M + kRows) sy2[i - M] = v;
+    }
+}
+
 // Barrier of the producer warps (named barrier 1) that also ORs a flag over
 // them: every producer gets the same answer, so they leave the tile loop
 // together (no producer is left waiting at a later barrier).
@@ -654,6 +719,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
         const int qd = warp & 3, sg = warp >> 2;
         const int row = 32 * qd + lane;
         const uint32_t tlane = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(kAccCols + 4 * sg);
+        RawIQ<FMT> pf;
+        bool have_pf = false;  // pf holds the windows of the tile about to start
         for (int it = 0; it < mine; ++it) {
             // every producer is done with the previous tile's windows; all
             // leave together on an abort
@@ -661,8 +728,18 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
             const int tile = (int)blockIdx.x + it * (int)gridDim.x;
             const TileInfo t = tile_info(sc, S, M, tile);
             if (t.lay) {
-                stage_windows<FMT>(t, M, zs, sy1, sy2, threadIdx.x, kProducerWarps * 32);
+                if (have_pf) store_windows<FMT>(pf, M, zs, sy1, sy2, threadIdx.x);
+                else stage_windows<FMT>(t, M, zs, sy1, sy2, threadIdx.x, kProducerWarps * 32);
                 asm volatile("bar.sync 1, %0;" ::"r"(kProducerWarps * 32) : "memory");
+            }
+            // the next lag tile's windows travel while this tile's stages run
+            have_pf = false;
+            if (it + 1 < mine) {
+                const TileInfo tn = tile_info(sc, S, M, tile + (int)gridDim.x);
+                if (tn.lay) {
+                    prefetch_windows<FMT>(tn, M, pf, threadIdx.x);
+                    have_pf = true;
+                }
             }
             int pL = 0, pn0 = 0;
             bool pv = false;
