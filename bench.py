@@ -67,8 +67,8 @@ def workload(name, rank=0, world=1, grid=None):
 # DRAM traffic of one contraction launch on the default workload, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the
 # kernel source it was measured on
-CONTRACT_TRAFFIC = {"source_sha1_16": "b3cad56ad14a73ae", "workload": "mid", "contract": "fp16x3", "chunk": 1024,
-                    "bytes_per_launch": 241.90e6}
+CONTRACT_TRAFFIC = {"source_sha1_16": "cf6f44f45b6f029b", "workload": "mid", "contract": "fp16x3", "chunk": 1024,
+                    "bytes_per_launch": 242.19e6}
 
 
 def contract_traffic(workload, contract, chunk):
@@ -403,8 +403,7 @@ def run_dg(a, rank, world, local_rank):
         dom = max(("contract", "combine"), key=lambda n: kt[n][0])
         flops_per_step = contract_flops if dom == "contract" else combine_units * (1e12 if combine_hbm else 1)
         corr_ms, corr_launches = kt[dom]
-        tc_name = ("k_cdft_contract_hk (Hankel tiles)" if a.tiles in ("auto", "hankel") and chunk <= 1024
-                   else "k_cdft_contract_tc")
+        tc_name = "k_cdft_contract_hk (Hankel tiles)" if a.tiles == "hankel" and chunk <= 1024 else "k_cdft_contract_tc"
         roof_kernel = {"contract": (f"{tc_name} ({a.contract} tcgen05, {chunk}-sample chunks x 64 bins)"
                                     if tensor else f"k_cdft_contract_f32 (FP32 CUDA cores, {chunk}-sample chunks)"),
                        "combine": "k_cdft_superchunk + k_cdft_combine (per-candidate interpolation + super-chunk phase sum)"}[dom]
