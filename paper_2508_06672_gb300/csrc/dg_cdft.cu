@@ -452,6 +452,14 @@ __global__ void __launch_bounds__(kCdftCombineThreads) k_cdft_combine(CdftBatch 
     const int b = sh_b;
     if (b < 0) return;  // uniform
     const int s = sh_s, M = sh_M, B = sh_B, n = sh_n;
+    const float *Wb = a.W + (size_t)b * a.Bmax * 128;
+    // the first segment of DFTs depends on the bucket only: its loads travel
+    // together with the candidates' below
+    for (int i = threadIdx.x; i < min(kSeg, B) * 64; i += kCdftCombineThreads) {
+        const int ch = i >> 6, q = i & 63;
+        const float *row = Wb + (size_t)ch * 128;
+        ws[ch][q] = make_float2(row[q], row[64 + q]);
+    }
     const size_t sp0 = (size_t)s * a.G + a.offs[b] + sh_first;
     int c[kCdftCombinePer], q0[kCdftCombinePer];
     float wm[kCdftCombinePer], w0[kCdftCombinePer], wp[kCdftCombinePer], ex[kCdftCombinePer],
@@ -475,14 +483,15 @@ __global__ void __launch_bounds__(kCdftCombineThreads) k_cdft_combine(CdftBatch 
         sincospif(2.0f * frac_mul(nu[k], (float)M), &ey[k], &ex[k]);
         cx[k] = cy[k] = 0.f;
     }
-    const float *Wb = a.W + (size_t)b * a.Bmax * 128;
     for (int s0 = 0; s0 < B; s0 += kSeg) {
         const int slen = min(kSeg, B - s0);
-        __syncthreads();
-        for (int i = threadIdx.x; i < slen * 64; i += kCdftCombineThreads) {
-            const int ch = i >> 6, q = i & 63;
-            const float *row = Wb + (size_t)(s0 + ch) * 128;
-            ws[ch][q] = make_float2(row[q], row[64 + q]);
+        if (s0 > 0) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < slen * 64; i += kCdftCombineThreads) {
+                const int ch = i >> 6, q = i & 63;
+                const float *row = Wb + (size_t)(s0 + ch) * 128;
+                ws[ch][q] = make_float2(row[q], row[64 + q]);
+            }
         }
         __syncthreads();
 #pragma unroll
