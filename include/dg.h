@@ -146,7 +146,14 @@ typedef struct dg_ctx dg_ctx;
 
 /* Result of dg_argmax_refine. The coarse fields refer to the context's grid
  * (global row index i, even for a shard); the refined fields to the local
- * grid of the refinement (refine_n = 0 when no refinement was asked for). */
+ * grid of the refinement (refine_n = 0 when no refinement was asked for).
+ * sub_lat_deg / sub_lon_deg (not in the paper) are a parabolic three-point
+ * estimate around the final maximum (the refined one when there is a
+ * refinement): along each axis the node moves by
+ * 0.5 (a - d) / (a - 2 b + d) nodes (a, b, d the values before, at and after
+ * it), kept within [-0.5, 0.5], and by 0 at the surface's edge (a shard's
+ * first or last row included), where a - 2 b + d >= 0, or where a value is
+ * not finite. It is reported beside the grid maximum and never replaces it. */
 typedef struct {
     int64_t index;             /* linear index in the shard's surface         */
     int32_t i, j;              /* global row, column of the coarse maximum    */
@@ -156,6 +163,7 @@ typedef struct {
     int32_t ri, rj;            /* maximum within the refinement grid          */
     int32_t pad;
     double refined_lat_deg, refined_lon_deg, refined_cost;
+    double sub_lat_deg, sub_lon_deg;  /* parabolic sub-node estimate          */
 } dg_fix;
 
 /* Kernel classes for dg_kernel_time: the main surface's correlation and

@@ -234,6 +234,32 @@ def detect(cost, threshold, radius, max_peaks=64):
     return out[:n].copy()
 
 
+def parabola_offset(a, b, d):
+    """Vertex of the parabola through (-1, a), (0, b), (1, d), in nodes:
+    0.5 (a - d) / (a - 2 b + d) where that curvature is negative (kept within
+    [-0.5, 0.5]), else 0 (not in the paper: a sub-node estimate reported
+    beside the grid maximum)."""
+    den = (a - 2.0 * b) + d
+    if not (den < 0.0):
+        return 0.0
+    x = 0.5 * (a - d) / den
+    return 0.0 if x != x else min(0.5, max(-0.5, x))
+
+
+def subcell(cost, i, j):
+    """(di, dj): the parabolic offsets of node (i, j) of a surface (nlat, nlon)
+    along rows and columns; 0 at an edge or with a non-finite neighbour."""
+    c = np.asarray(cost, dtype=np.float64)
+    n0, n1 = c.shape
+    di = parabola_offset(c[i - 1, j], c[i, j], c[i + 1, j]) if 0 < i < n0 - 1 else 0.0
+    dj = parabola_offset(c[i, j - 1], c[i, j], c[i, j + 1]) if 0 < j < n1 - 1 else 0.0
+    if not np.all(np.isfinite([c[max(i - 1, 0), j], c[min(i + 1, n0 - 1), j]])):
+        di = 0.0
+    if not np.all(np.isfinite([c[i, max(j - 1, 0)], c[i, min(j + 1, n1 - 1)]])):
+        dj = 0.0
+    return di, dj
+
+
 def refine_grid(grid, index, spacing_m, window_m):
     """Local grid for dense re-evaluation around a coarse cell: centred on the
     cell's latitude/longitude, spacing_m apart, half-width window_m."""

@@ -1064,6 +1064,8 @@ dg_status dg_argmax_refine(dg_ctx *c, const void *cost, double spacing_m, double
     f.lat_deg = r.lat_rad * (180.0 / kPi);
     f.lon_deg = r.lon_rad * (180.0 / kPi);
     f.cost = r.val;
+    f.sub_lat_deg = r.sub_lat_rad * (180.0 / kPi);
+    f.sub_lon_deg = r.sub_lon_rad * (180.0 / kPi);
     if (refine) {
         const int n = 2 * half + 1;
         dg_grid lg;
@@ -1096,6 +1098,8 @@ dg_status dg_argmax_refine(dg_ctx *c, const void *cost, double spacing_m, double
         f.refined_lat_deg = q.lat_rad * (180.0 / kPi);
         f.refined_lon_deg = q.lon_rad * (180.0 / kPi);
         f.refined_cost = q.val;
+        f.sub_lat_deg = q.sub_lat_rad * (180.0 / kPi);
+        f.sub_lon_deg = q.sub_lon_rad * (180.0 / kPi);
     }
     *out = f;
     return DG_OK;

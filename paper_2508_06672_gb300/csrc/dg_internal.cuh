@@ -394,6 +394,7 @@ struct ArgmaxResult {
     double val;
     int64_t idx;                 // -1 if every value is NaN
     double lat_rad, lon_rad;     // node of idx in the grid g (if idx >= 0)
+    double sub_lat_rad, sub_lon_rad;  // parabolic three-point estimate around it
 };
 
 // Argmax of v[0..n) (ties to the lowest index, NaN never wins); tmp must hold

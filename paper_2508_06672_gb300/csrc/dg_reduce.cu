@@ -89,8 +89,24 @@ __global__ void __launch_bounds__(1024) k_argmax_partial(const T *__restrict__ v
     if (threadIdx.x == 0) part[blockIdx.x] = best;
 }
 
+// Offset (in nodes, within [-0.5, 0.5]) of the vertex of the parabola
+// through the values at c - stride, c, c + stride: 0.5 (a - d) / (a - 2b + d)
+// where that curvature is negative, 0 at an edge, on a flat or non-concave
+// triple, or with a non-finite neighbour.
+template <typename T>
+__device__ __forceinline__ double parabola_offset(const T *v, int64_t c, int64_t stride, bool lo, bool hi)
+{
+    if (!lo || !hi) return 0.0;
+    const double a = (double)v[c - stride], b = (double)v[c], d = (double)v[c + stride];
+    const double den = __dadd_rn(__dsub_rn(a, __dmul_rn(2.0, b)), d);
+    if (!(den < 0.0)) return 0.0;
+    const double x = __ddiv_rn(__dmul_rn(0.5, __dsub_rn(a, d)), den);
+    return x != x ? 0.0 : fmin(0.5, fmax(-0.5, x));
+}
+
 __global__ void __launch_bounds__(1024) k_argmax_final(const VI *part, int nparts, GridDev g,
-                                                       ArgmaxResult *res, const ArgmaxResult *centre)
+                                                       ArgmaxResult *res, const ArgmaxResult *centre,
+                                                       const void *v, int prec)
 {
     if (centre) centre_on(g, centre);
     VI best{0.0, -1};
@@ -102,12 +118,28 @@ __global__ void __launch_bounds__(1024) k_argmax_final(const VI *part, int npart
         res->idx = best.idx;
         res->lat_rad = 0.0;
         res->lon_rad = 0.0;
+        res->sub_lat_rad = 0.0;
+        res->sub_lon_rad = 0.0;
         if (best.idx >= 0) {
             const GridStep st = grid_step(g);
+            const int il = (int)(best.idx / g.nlon), j = (int)(best.idx % g.nlon);
             double lat, lon;
-            grid_node(g, st, g.row0 + (int)(best.idx / g.nlon), (int)(best.idx % g.nlon), lat, lon);
+            grid_node(g, st, g.row0 + il, j, lat, lon);
             res->lat_rad = lat;
             res->lon_rad = lon;
+            // neighbours within the surface (the shard's rows, the grid's columns)
+            double di, dj;
+            if (prec == DG_PREC_FP64) {
+                const double *d = (const double *)v;
+                di = parabola_offset(d, best.idx, g.nlon, il > 0, il < g.nrows - 1);
+                dj = parabola_offset(d, best.idx, 1, j > 0, j < g.nlon - 1);
+            } else {
+                const float *f = (const float *)v;
+                di = parabola_offset(f, best.idx, g.nlon, il > 0, il < g.nrows - 1);
+                dj = parabola_offset(f, best.idx, 1, j > 0, j < g.nlon - 1);
+            }
+            res->sub_lat_rad = __dadd_rn(lat, __dmul_rn(di, st.dlat));
+            res->sub_lon_rad = __dadd_rn(lon, __dmul_rn(dj, st.dlon));
         }
     }
 }
@@ -133,7 +165,7 @@ cudaError_t launch_argmax(const void *v, int64_t n, int prec, const GridDev &g, 
         k_argmax_partial<float><<<nb, 1024, 0, s>>>((const float *)v, n, part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_argmax_final<<<1, 1024, 0, s>>>(part, nb, g, res, centre);
+    k_argmax_final<<<1, 1024, 0, s>>>(part, nb, g, res, centre, v, prec);
     if (launches) *launches += 2;
     return cudaGetLastError();
 }
@@ -152,6 +184,8 @@ __global__ void k_make_fix(const ArgmaxResult *coarse, const ArgmaxResult *fine,
     f.lat_deg = coarse->lat_rad * (180.0 / kPi);
     f.lon_deg = coarse->lon_rad * (180.0 / kPi);
     f.cost = coarse->val;
+    f.sub_lat_deg = coarse->sub_lat_rad * (180.0 / kPi);
+    f.sub_lon_deg = coarse->sub_lon_rad * (180.0 / kPi);
     if (fine && coarse->idx >= 0) {
         f.refine_n = n;
         f.ri = f.rj = -1;  // no finite value on the refinement grid
@@ -162,6 +196,10 @@ __global__ void k_make_fix(const ArgmaxResult *coarse, const ArgmaxResult *fine,
         f.refined_lat_deg = fine->lat_rad * (180.0 / kPi);
         f.refined_lon_deg = fine->lon_rad * (180.0 / kPi);
         f.refined_cost = fine->val;
+        if (fine->idx >= 0) {
+            f.sub_lat_deg = fine->sub_lat_rad * (180.0 / kPi);
+            f.sub_lon_deg = fine->sub_lon_rad * (180.0 / kPi);
+        }
     }
     *out = f;
 }

@@ -127,7 +127,7 @@ class dg_fix(C.Structure):
                 ("lon_deg", C.c_double), ("cost", C.c_double), ("refine_n", C.c_int32),
                 ("ri", C.c_int32), ("rj", C.c_int32), ("pad", C.c_int32),
                 ("refined_lat_deg", C.c_double), ("refined_lon_deg", C.c_double),
-                ("refined_cost", C.c_double)]
+                ("refined_cost", C.c_double), ("sub_lat_deg", C.c_double), ("sub_lon_deg", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}

@@ -50,8 +50,9 @@ def test_struct_layouts_match_c(P):
 #include <stddef.h>
 #include "dg.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(dg_grid), sizeof(dg_ephem),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(dg_grid), sizeof(dg_ephem),
          sizeof(dg_options), sizeof(dg_fix), offsetof(dg_fix, refine_n), offsetof(dg_fix, refined_lat_deg),
+         offsetof(dg_fix, sub_lat_deg), sizeof(dg_coarse_step), offsetof(dg_coarse_step, mu),
          offsetof(dg_options, timing), offsetof(dg_options, tiles), sizeof(dg_peak), offsetof(dg_peak, lat_deg),
          sizeof(dg_tuning), offsetof(dg_tuning, ms), offsetof(dg_tuning, cached));
   return 0;
@@ -64,7 +65,8 @@ int main(void) {
         subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     want = [C.sizeof(P.dg_grid), C.sizeof(P.dg_ephem), C.sizeof(P.dg_options), C.sizeof(P.dg_fix),
-            P.dg_fix.refine_n.offset, P.dg_fix.refined_lat_deg.offset, P.dg_options.timing.offset,
+            P.dg_fix.refine_n.offset, P.dg_fix.refined_lat_deg.offset, P.dg_fix.sub_lat_deg.offset,
+            C.sizeof(P.dg_coarse_step), P.dg_coarse_step.mu.offset, P.dg_options.timing.offset,
             P.dg_options.tiles.offset, C.sizeof(P.dg_peak), P.dg_peak.lat_deg.offset, C.sizeof(P.dg_tuning),
             P.dg_tuning.ms.offset, P.dg_tuning.cached.offset]
     assert vals == want

@@ -229,9 +229,21 @@ def test_argmax_and_refine_match_oracle():
     lam = oracle.argmax(lref)
     assert (fix["ri"], fix["rj"]) == divmod(lam, lg["nlon"])
     assert abs(fix["refined_cost"] / lref.ravel()[lam] - 1) < FP64_TOL
-    # no refinement requested
+    # the parabolic sub-node estimate around the refined maximum, from the
+    # oracle's refinement surface (FP64 on both sides: offsets agree to 1e-4 node)
+    ri, rj = divmod(lam, lg["nlon"])
+    di, dj = oracle.subcell(lref.reshape(lg["nlat"], lg["nlon"]), ri, rj)
+    dlat, dlon = oracle.grid_step_rad(lg)
+    assert abs(fix["sub_lat_deg"] - fix["refined_lat_deg"] - np.degrees(di * dlat)) <= 1e-4 * np.degrees(dlat)
+    assert abs(fix["sub_lon_deg"] - fix["refined_lon_deg"] - np.degrees(dj * dlon)) <= 1e-4 * np.degrees(dlon)
+    assert abs(di) <= 0.5 and abs(dj) <= 0.5 and (di, dj) != (0.0, 0.0)
+    # no refinement requested: around the grid maximum
     f0 = g.argmax_refine(cost)
     assert f0["refine_n"] == 0 and f0["index"] == am
+    di, dj = oracle.subcell(ref.reshape(s.grid["nlat"], s.grid["nlon"]), *divmod(am, s.grid["nlon"]))
+    dlat, dlon = oracle.grid_step_rad(s.grid)
+    assert abs(f0["sub_lat_deg"] - f0["lat_deg"] - np.degrees(di * dlat)) <= 1e-4 * np.degrees(dlat)
+    assert abs(f0["sub_lon_deg"] - f0["lon_deg"] - np.degrees(dj * dlon)) <= 1e-4 * np.degrees(dlon)
     g.close()
 
 
