@@ -92,7 +92,9 @@ enum { DG_ALGO_DIRECT = 0, DG_ALGO_CDFT = 1 };
  * On this chip HANKEL is slower than LAGS (its per-phase MMAs of N = 64
  * fetch more operand bytes per flop), so AUTO does not take it: AUTO takes
  * LAGS (chunk <= 1024) unless padding a snapshot's lags to whole blocks of 128
- * more than doubles its tile count, and ROWS then. */
+ * more than doubles its tile count, and ROWS then; when the last block of a
+ * snapshot would hold fewer than 64 lags, AUTO puts those lags in ROWS tiles
+ * and keeps LAGS tiles for the whole blocks. */
 enum { DG_TILES_AUTO = 0, DG_TILES_ROWS = 1, DG_TILES_LAGS = 2, DG_TILES_HANKEL = 3 };
 
 /* Arithmetic of the CDFT contraction: FP32 on CUDA cores, or 16-bit

@@ -552,19 +552,25 @@ __global__ void k_cdft_tiles(CdftBatch a)
             const int B = (n + M - 1) / M;
             const int t_row = (int)(((int64_t)NB * B + 127) / 128), t_lag = B * ((NB + 127) / 128);
             const int t_hk = B * ((NB + kHkLags - 1) / kHkLags);
+            const int NFB = NB / 128, rem = NB - 128 * NFB;
+            const int t_mix = NFB * B + (int)(((int64_t)rem * B + 127) / 128);
             // 0: row tiles, 1: lag tiles, 2: Hankel tiles
             // AUTO: lag tiles unless padding the lags to whole blocks of 128
-            // more than doubles the tile count; Hankel tiles only on request
-            // (measured slower: their per-phase MMAs of N = 64 re-read the
-            // 128-row operand eight times per K step)
+            // more than doubles the tile count; and when the last block holds
+            // fewer than 64 lags, those lags go into row tiles (packed (lag,
+            // chunk) rows, about two lag tiles' cost each) instead of a mostly
+            // empty block (3: mixed). Hankel tiles only on request (measured
+            // slower: their per-phase MMAs of N = 64 re-read the 128-row operand
+            // eight times per K step)
             int lay = 0;
             if (a.mma && M <= kLagTileMaxChunk) {
                 if (a.tiles_mode == DG_TILES_HANKEL) lay = 2;
                 else if (a.tiles_mode == DG_TILES_LAGS) lay = 1;
-                else if (a.tiles_mode == DG_TILES_AUTO && t_lag <= 2 * t_row) lay = 1;
+                else if (a.tiles_mode == DG_TILES_AUTO && t_lag <= 2 * t_row)
+                    lay = (NFB >= 1 && rem > 0 && rem < 64) ? 3 : 1;
             }
             a.layout[s] = lay;
-            tiles = lay == 2 ? 0 : lay ? t_lag : t_row;
+            tiles = lay == 2 ? 0 : lay == 3 ? t_mix : lay ? t_lag : t_row;
             htiles = lay == 2 ? t_hk : 0;
             int64_t Mc = M;
             const double d = (double)a.delta[s];

@@ -537,6 +537,7 @@ struct SnapCache {  // per-snapshot tables of the batch, in shared memory
 
 struct TileInfo {
     int s, ltile, N, Bs, NB, lay, lb, bch, Lmin, bb;
+    int rt, rNB, rl0;  // row tiles: tile index among them, their lags, first lag bucket
     StepDesc sd;
 };
 
@@ -550,10 +551,31 @@ __device__ __forceinline__ TileInfo tile_info(const SnapCache &c, int S, int M, 
     t.Bs = (t.N + M - 1) / M;
     const int lo = c.lr[2 * t.s], hi = c.lr[2 * t.s + 1];
     t.NB = hi >= lo ? hi - lo + 1 : 0;
-    t.lay = c.layout[t.s];
-    const int NLB = max((t.NB + kRows - 1) / kRows, 1);
-    t.lb = t.lay ? t.ltile % NLB : 0;
-    t.bch = t.lay ? t.ltile / NLB : 0;
+    // layout 0: row tiles over every lag; 1: lag tiles over every lag;
+    // 3 (mixed): lag tiles over the whole blocks of 128 lags, then row tiles
+    // over the remaining lags; t.lay is this tile's kind (1 lags, 0 rows)
+    const int lay = c.layout[t.s];
+    t.lay = lay == 1 ? 1 : 0;
+    t.lb = t.bch = 0;
+    t.rt = t.ltile;
+    t.rNB = t.NB;
+    t.rl0 = 0;
+    if (lay == 1) {
+        const int NLB = max((t.NB + kRows - 1) / kRows, 1);
+        t.lb = t.ltile % NLB;
+        t.bch = t.ltile / NLB;
+    } else if (lay == 3) {
+        const int NFB = max(t.NB / kRows, 1), nlt = NFB * t.Bs;
+        if (t.ltile < nlt) {
+            t.lay = 1;
+            t.lb = t.ltile % NFB;
+            t.bch = t.ltile / NFB;
+        } else {
+            t.rt = t.ltile - nlt;
+            t.rl0 = NFB * kRows;
+            t.rNB = max(t.NB - t.rl0, 0);
+        }
+    }
     t.Lmin = lo;
     t.bb = c.bbase[t.s];
     return t;
@@ -744,10 +766,10 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
             int pL = 0, pn0 = 0;
             bool pv = false;
             if (!t.lay) {
-                const int64_t R = (int64_t)t.NB * t.Bs;
-                const int64_t g = (int64_t)t.ltile * kRows + row;
+                const int64_t R = (int64_t)t.rNB * t.Bs;
+                const int64_t g = (int64_t)t.rt * kRows + row;
                 if (g < R) {
-                    const int bl = (int)(g / t.Bs);
+                    const int bl = t.rl0 + (int)(g / t.Bs);
                     pn0 = (int)(g % t.Bs) * M + 8 * sg;
                     pL = t.Lmin + bl;
                     pv = a.count[t.bb + bl] > 0;
@@ -901,9 +923,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                 valid = bl < t.NB && a.count[t.bb + bl] > 0;
                 wrow = ((int64_t)(t.bb + bl) * a.Bmax + t.bch) * 128;
             } else {
-                const int64_t g = (int64_t)t.ltile * kRows + row;
-                valid = g < (int64_t)t.NB * t.Bs;
-                const int bl = valid ? (int)(g / t.Bs) : 0;
+                const int64_t g = (int64_t)t.rt * kRows + row;
+                valid = g < (int64_t)t.rNB * t.Bs;
+                const int bl = valid ? t.rl0 + (int)(g / t.Bs) : 0;
                 valid = valid && a.count[t.bb + bl] > 0;
                 wrow = ((int64_t)(t.bb + bl) * a.Bmax + (valid ? g % t.Bs : 0)) * 128;
             }

@@ -57,6 +57,28 @@ def test_cdft_lag_tiles_match_row_tiles(fmt, contract):
 
 
 @pytest.mark.parametrize("fmt", ["c64", "ci16", "ci8"])
+def test_cdft_mixed_tiles_match_row_and_lag_tiles(fmt):
+    """AUTO on snapshots of 391 and 390 lags (three whole blocks of 128 and a
+    remainder of 7 and 6): lag tiles over the whole blocks, row tiles over the
+    remaining lags. Every tile kind forms the same lag products, so the three
+    surfaces are bit-identical, and within the bound of the oracle."""
+    s = sim.make_scene(seed=24, fs_hz=20e6, n_samples=5000, k_steps=2, fmt=fmt, waveform="noise",
+                       snr_db=-3.0, grid_n=(45, 41), grid_spacing_m=1300.0, bw_hz=18e6)
+    D, _ = oracle.node_geometry(s.grid, s.ephem, s.fs_hz, s.fc_hz)
+    nb = [int(np.ptp(np.sign(d) * np.floor(np.abs(d) + 0.5))) + 1 for d in D]
+    assert all(0 < n % 128 < 64 and n >= 128 for n in nb), nb  # the case AUTO splits
+    out = {}
+    for tiles in ("auto", "rows", "lags"):
+        g, c = gpu_surface(s, algo="cdft", contract="fp16x3", chunk=1024, tiles=tiles)
+        out[tiles] = c
+        g.close()
+    assert np.array_equal(out["auto"], out["rows"]) and np.array_equal(out["auto"], out["lags"])
+    ref = oracle_surface(s)
+    ok = ~lag_boundary_mask(s, np.arange(s.G))
+    assert rel_err(out["auto"].ravel()[ok], ref.ravel()[ok], 0.01) < FP32_TOL
+
+
+@pytest.mark.parametrize("fmt", ["c64", "ci16", "ci8"])
 @pytest.mark.parametrize("contract", ["bf16x3", "fp16x3", "bf16", "fp16"])
 def test_cdft_hankel_tiles(fmt, contract):
     """Hankel tiles (256 lags at one chunk; the DFT regrouped onto y1 and y2
