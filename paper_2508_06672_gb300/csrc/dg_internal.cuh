@@ -295,8 +295,10 @@ cudaError_t launch_accumulate(const void *surf, int K, int64_t G, int prec, void
 // per lag lr[2s] .. lr[2s+1]; combine groups of snapshot s are gbase[s] ..
 // gbase[s+1]-1 (an upper bound; surplus CTAs exit).
 // ---------------------------------------------------------------------------
-constexpr int kCdftCombineThreads = 256;
-constexpr int kCdftCombinePer = 4;  // candidates per combine thread
+constexpr int kCdftCombineThreads = 128;
+// candidates per combine thread; a group of 256 candidates per CTA measured best
+// on mid (128 x 2 or 64 x 4: 0.30 ms; 256 x 4: 0.35; 256 x 8: 0.49; 512 x 2: 0.40)
+constexpr int kCdftCombinePer = 2;
 constexpr int kCdftCombineGroup = kCdftCombineThreads * kCdftCombinePer;  // candidates per combine CTA
 
 struct CdftBatch {
