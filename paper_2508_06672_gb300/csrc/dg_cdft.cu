@@ -61,7 +61,7 @@ __device__ __forceinline__ int step_of(const int *base, int S, int b)
 // ---------------------------------------------------------------------------
 // geo: lag and FDOA of every (candidate, snapshot), lag range per snapshot.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_cdft_geo(CdftBatch a)
+__global__ void __launch_bounds__(256, 4) k_cdft_geo(CdftBatch a)
 {
     __shared__ int smin[8], smax[8];
     const int s = blockIdx.y;
