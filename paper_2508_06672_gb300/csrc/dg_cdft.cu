@@ -24,8 +24,8 @@
 //   hist     count per (snapshot, lag) bucket, aggregated in shared memory;
 //   scan     one CTA per snapshot: bucket offsets, combine-group offsets and
 //            the snapshot's bins;
-//   scatter  candidate indices sorted by bucket (grid order within), and
-//            their FDOAs in the same order;
+//   scatter  candidate indices sorted by bucket (grouped by grid tile
+//            within), and their FDOAs in the same order;
 //   contract W[bucket][chunk] = 64 bins, stored planar (64 real parts then 64
 //            imaginary parts); FP32 CUDA cores here, tensor cores in
 //            dg_cdft_mma.cu;
@@ -256,29 +256,84 @@ __global__ void __launch_bounds__(1024) k_cdft_scan(CdftBatch a)
 }
 
 // ---------------------------------------------------------------------------
-// scatter: counting sort by lag bucket (the offsets come from the scan).
-// Within a bucket the candidates keep about their grid order, so the
-// combine's surface writes stay close together.
+// scatter: counting sort by lag bucket (the offsets come from the scan). A CTA
+// takes the hist kernel's 64 x 64 tile of one snapshot. Its candidates are
+// ranked per lag in shared memory, one global atomic per (tile, lag)
+// reserves a contiguous range of the bucket, and each candidate takes its
+// rank within that range: the candidates of one tile and lag sit together,
+// which keeps the combine's surface writes close. Tiles whose lag span
+// exceeds kHistBins take one global atomic per (warp, lag) instead.
 // ---------------------------------------------------------------------------
+constexpr int kScatterPer = kHistTile * kHistTile / 256;  // candidates per thread
+
 __global__ void __launch_bounds__(256) k_cdft_scatter(CdftBatch a)
 {
+    __shared__ int s_cnt[kHistBins], s_base[kHistBins];
+    __shared__ int s_min, s_max;
     const int s = blockIdx.y;
     const int lmin = a.lr[2 * s], bb = a.bbase[s];
     if (a.lr[2 * s + 1] - lmin >= a.bbase[s + 1] - bb) return;  // reported by k_cdft_hist
-    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < a.G; p += (int64_t)gridDim.x * blockDim.x) {
-        const int l = a.candL[(size_t)s * a.G + p];
-        if (l == INT_MIN) continue;
-        const int b = bb + l - lmin;
-        // one atomic per distinct bucket in the warp; the peers take
-        // consecutive positions in lane order
-        const unsigned peers = __match_any_sync(__activemask(), b);
-        const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    const int tiles_j = (a.nlon + kHistTile - 1) / kHistTile;
+    const int r0 = (blockIdx.x / tiles_j) * kHistTile, c0 = (blockIdx.x % tiles_j) * kHistTile;
+    const int *Ls = a.candL + (size_t)s * a.G;
+    if (threadIdx.x == 0) {
+        s_min = INT_MAX;
+        s_max = INT_MIN;
+    }
+    // thread t holds tile entries t + 256 k: a warp reads 32 consecutive
+    // nodes of one grid row
+    int l[kScatterPer];
+    int lo = INT_MAX, hi = INT_MIN;
+#pragma unroll
+    for (int k = 0; k < kScatterPer; ++k) {
+        const int i = threadIdx.x + 256 * k;
+        const int r = r0 + i / kHistTile, c = c0 + i % kHistTile;
+        l[k] = (r < a.nrows && c < a.nlon) ? Ls[(int64_t)r * a.nlon + c] : INT_MIN;
+        if (l[k] != INT_MIN) {
+            lo = min(lo, l[k]);
+            hi = max(hi, l[k]);
+        }
+    }
+    __syncthreads();
+    atomicMin(&s_min, lo);
+    atomicMax(&s_max, hi);
+    __syncthreads();
+    if (s_max < s_min) return;  // no node with a representable lag (uniform)
+    const int tlo = s_min;
+    const bool local = (int64_t)s_max - s_min < kHistBins;
+    const int span = local ? s_max - s_min + 1 : 0;
+    for (int i = threadIdx.x; i < span; i += blockDim.x) s_cnt[i] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    int rank[kScatterPer];
+#pragma unroll
+    for (int k = 0; k < kScatterPer; ++k) {
+        // one atomic per distinct lag in the warp; the peers take
+        // consecutive ranks in lane order
+        const unsigned peers = __match_any_sync(0xffffffffu, l[k]);
+        const int leader = __ffs(peers) - 1;
         int base = 0;
-        if (lane == leader) base = atomicAdd(a.subcnt + b, __popc(peers));
-        base = __shfl_sync(peers, base, leader);
-        const int pos = a.offs[b] + base + __popc(peers & ((1u << lane) - 1u));
-        a.order[(size_t)s * a.G + pos] = (int)p;
-        a.nuS[(size_t)s * a.G + pos] = a.candNu[(size_t)s * a.G + p];
+        if (lane == leader && l[k] != INT_MIN)
+            base = local ? atomicAdd(s_cnt + (l[k] - tlo), __popc(peers))
+                         : atomicAdd(a.subcnt + bb + l[k] - lmin, __popc(peers));
+        rank[k] = __shfl_sync(0xffffffffu, base, leader) + __popc(peers & ((1u << lane) - 1u));
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < span; i += blockDim.x) {
+        const int n = s_cnt[i];
+        s_base[i] = n ? atomicAdd(a.subcnt + bb + tlo + i - lmin, n) : 0;
+    }
+    __syncthreads();
+    const size_t so = (size_t)s * a.G;
+#pragma unroll
+    for (int k = 0; k < kScatterPer; ++k) {
+        if (l[k] == INT_MIN) continue;
+        const int i = threadIdx.x + 256 * k;
+        const int64_t p = (int64_t)(r0 + i / kHistTile) * a.nlon + c0 + i % kHistTile;
+        const int b = bb + l[k] - lmin;
+        const int pos = a.offs[b] + (local ? s_base[l[k] - tlo] : 0) + rank[k];
+        a.order[so + pos] = (int)p;
+        a.nuS[so + pos] = a.candNu[so + p];
     }
 }
 
@@ -658,8 +713,7 @@ cudaError_t launch_cdft_plan(const CdftBatch &a, int NBT, cudaStream_t st)
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_cdft_scan<<<a.S, 1024, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    dim3 gp(grid_for(a.G, 256 * 4, 152 * 8), (unsigned)a.S);
-    k_cdft_scatter<<<gp, 256, 0, st>>>(a);
+    k_cdft_scatter<<<gh, 256, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (a.mma) return cudaSuccess;  // the FP32 table serves the CUDA-core contraction only
     dim3 gv(grid_for((int64_t)a.M * 64, 256, 64), (unsigned)a.S);

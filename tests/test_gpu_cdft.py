@@ -142,6 +142,22 @@ def test_cdft_auto_chunk():
     assert chunks[1] < chunks[0]
 
 
+def test_cdft_tile_spanning_more_lags_than_shared_buckets():
+    """A 1000 km grid at 20 MHz: the one 64 x 64 node tile of each snapshot
+    spans about 4900 lags, more than the 2048 shared-memory buckets of the
+    histogram and the scatter, so both take their global-atomic path; the
+    surface stays within the FP32 bound of the oracle."""
+    s = sim.make_scene(seed=27, fs_hz=20e6, n_samples=20000, k_steps=2, fmt="ci16", waveform="noise",
+                       snr_db=-3.0, grid_n=(41, 39), grid_spacing_m=25000.0, bw_hz=18e6)
+    D, _ = oracle.node_geometry(s.grid, s.ephem, s.fs_hz, s.fc_hz)
+    assert all(np.ptp(np.sign(d) * np.floor(np.abs(d) + 0.5)) >= 2048 for d in D)
+    g, c = gpu_surface(s, algo="cdft")
+    ref = oracle_surface(s)
+    ok = ~lag_boundary_mask(s, np.arange(s.G))
+    assert rel_err(c.ravel()[ok], ref.ravel()[ok], 0.01) < FP32_TOL
+    g.close()
+
+
 @pytest.mark.parametrize("contract", ["fp32", "fp16x3"])
 def test_cdft_superchunks(contract):
     """The combine sums chunks at the bin frequencies into super-chunks as
