@@ -142,40 +142,69 @@ __global__ void k_cdft_lr_init(int *lr, unsigned *nur, int S)
 }
 
 // ---------------------------------------------------------------------------
-// hist: per bucket count and FDOA range. A CTA takes a 64 x 64 tile of grid
-// nodes of one snapshot; their lags span a few hundred values at most, so
-// counts and ranges are aggregated in shared memory first (global atomics
-// only for tiles whose lag span exceeds kHistBins).
+// hist: count per (snapshot, lag) bucket. A CTA takes a 64 x 64 tile of grid
+// nodes of one snapshot, held in registers (thread t: tile entries t + 256 k,
+// so a warp reads 32 consecutive nodes of one grid row). Their lags span a
+// few hundred values at most, so the counts are aggregated in shared memory
+// first, one atomic per distinct lag in a warp (global atomics only for tiles
+// whose lag span exceeds kHistBins).
 // ---------------------------------------------------------------------------
 constexpr int kHistTile = 64;     // tile side (nodes)
 constexpr int kHistBins = 2048;   // shared-memory buckets per CTA
+constexpr int kTilePer = kHistTile * kHistTile / 256;  // tile entries per thread
+
+// The tile's lags (INT_MIN outside the grid) and their range over the CTA
+// (s_min > s_max when no node has a representable lag).
+__device__ __forceinline__ void load_lag_tile(const CdftBatch &a, int s, int (&l)[kTilePer], int &s_min, int &s_max)
+{
+    const int tiles_j = (a.nlon + kHistTile - 1) / kHistTile;
+    const int r0 = (blockIdx.x / tiles_j) * kHistTile, c0 = (blockIdx.x % tiles_j) * kHistTile;
+    const int *Ls = a.candL + (size_t)s * a.G;
+    if (threadIdx.x == 0) {
+        s_min = INT_MAX;
+        s_max = INT_MIN;
+    }
+    int lo = INT_MAX, hi = INT_MIN;
+#pragma unroll
+    for (int k = 0; k < kTilePer; ++k) {
+        const int i = threadIdx.x + 256 * k;
+        const int r = r0 + i / kHistTile, c = c0 + i % kHistTile;
+        l[k] = (r < a.nrows && c < a.nlon) ? Ls[(int64_t)r * a.nlon + c] : INT_MIN;
+        if (l[k] != INT_MIN) {
+            lo = min(lo, l[k]);
+            hi = max(hi, l[k]);
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, d));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, d));
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&s_min, lo);
+        atomicMax(&s_max, hi);
+    }
+    __syncthreads();
+}
+
+// Grid index of tile entry k of this thread.
+__device__ __forceinline__ int64_t tile_node(const CdftBatch &a, int k)
+{
+    const int tiles_j = (a.nlon + kHistTile - 1) / kHistTile;
+    const int i = threadIdx.x + 256 * k;
+    return (int64_t)((blockIdx.x / tiles_j) * kHistTile + i / kHistTile) * a.nlon
+         + (blockIdx.x % tiles_j) * kHistTile + i % kHistTile;
+}
 
 __global__ void __launch_bounds__(256) k_cdft_hist(CdftBatch a)
 {
     __shared__ int s_cnt[kHistBins];
     __shared__ int s_min, s_max;
     const int s = blockIdx.y;
-    const int tiles_j = (a.nlon + kHistTile - 1) / kHistTile;
-    const int r0 = (blockIdx.x / tiles_j) * kHistTile, c0 = (blockIdx.x % tiles_j) * kHistTile;
-    const int *L = a.candL + (size_t)s * a.G;
     const int lmin = a.lr[2 * s], bb = a.bbase[s], cap = a.bbase[s + 1] - bb;
-    if (threadIdx.x == 0) {
-        s_min = INT_MAX;
-        s_max = INT_MIN;
-    }
-    __syncthreads();
-    int lo = INT_MAX, hi = INT_MIN;
-    for (int i = threadIdx.x; i < kHistTile * kHistTile; i += blockDim.x) {
-        const int r = r0 + i / kHistTile, c = c0 + i % kHistTile;
-        if (r >= a.nrows || c >= a.nlon) continue;
-        const int l = L[(int64_t)r * a.nlon + c];
-        if (l == INT_MIN) continue;
-        lo = min(lo, l);
-        hi = max(hi, l);
-    }
-    atomicMin(&s_min, lo);
-    atomicMax(&s_max, hi);
-    __syncthreads();
+    int l[kTilePer];
+    load_lag_tile(a, s, l, s_min, s_max);
     if (s_max < s_min) return;  // no node with a representable lag (uniform)
     if (a.lr[2 * s + 1] - lmin >= cap) {  // more lags than the snapshot's bucket slots
         if (threadIdx.x == 0) atomicOr(a.err, ERR_LAG_RANGE);
@@ -186,15 +215,16 @@ __global__ void __launch_bounds__(256) k_cdft_hist(CdftBatch a)
     const int span = local ? s_max - s_min + 1 : 0;
     for (int i = threadIdx.x; i < span; i += blockDim.x) s_cnt[i] = 0;
     __syncthreads();
-    for (int i = threadIdx.x; i < kHistTile * kHistTile; i += blockDim.x) {
-        const int r = r0 + i / kHistTile, c = c0 + i % kHistTile;
-        if (r >= a.nrows || c >= a.nlon) continue;
-        const int l = L[(int64_t)r * a.nlon + c];
-        if (l == INT_MIN) continue;
-        if (local)
-            atomicAdd(s_cnt + (l - tlo), 1);
-        else
-            atomicAdd(a.count + bb + l - lmin, 1);
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < kTilePer; ++k) {
+        const unsigned peers = __match_any_sync(0xffffffffu, l[k]);
+        if (lane == __ffs(peers) - 1 && l[k] != INT_MIN) {
+            if (local)
+                atomicAdd(s_cnt + (l[k] - tlo), __popc(peers));
+            else
+                atomicAdd(a.count + bb + l[k] - lmin, __popc(peers));
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < span; i += blockDim.x)
@@ -264,8 +294,6 @@ __global__ void __launch_bounds__(1024) k_cdft_scan(CdftBatch a)
 // which keeps the combine's surface writes close. Tiles whose lag span
 // exceeds kHistBins take one global atomic per (warp, lag) instead.
 // ---------------------------------------------------------------------------
-constexpr int kScatterPer = kHistTile * kHistTile / 256;  // candidates per thread
-
 __global__ void __launch_bounds__(256) k_cdft_scatter(CdftBatch a)
 {
     __shared__ int s_cnt[kHistBins], s_base[kHistBins];
@@ -273,31 +301,8 @@ __global__ void __launch_bounds__(256) k_cdft_scatter(CdftBatch a)
     const int s = blockIdx.y;
     const int lmin = a.lr[2 * s], bb = a.bbase[s];
     if (a.lr[2 * s + 1] - lmin >= a.bbase[s + 1] - bb) return;  // reported by k_cdft_hist
-    const int tiles_j = (a.nlon + kHistTile - 1) / kHistTile;
-    const int r0 = (blockIdx.x / tiles_j) * kHistTile, c0 = (blockIdx.x % tiles_j) * kHistTile;
-    const int *Ls = a.candL + (size_t)s * a.G;
-    if (threadIdx.x == 0) {
-        s_min = INT_MAX;
-        s_max = INT_MIN;
-    }
-    // thread t holds tile entries t + 256 k: a warp reads 32 consecutive
-    // nodes of one grid row
-    int l[kScatterPer];
-    int lo = INT_MAX, hi = INT_MIN;
-#pragma unroll
-    for (int k = 0; k < kScatterPer; ++k) {
-        const int i = threadIdx.x + 256 * k;
-        const int r = r0 + i / kHistTile, c = c0 + i % kHistTile;
-        l[k] = (r < a.nrows && c < a.nlon) ? Ls[(int64_t)r * a.nlon + c] : INT_MIN;
-        if (l[k] != INT_MIN) {
-            lo = min(lo, l[k]);
-            hi = max(hi, l[k]);
-        }
-    }
-    __syncthreads();
-    atomicMin(&s_min, lo);
-    atomicMax(&s_max, hi);
-    __syncthreads();
+    int l[kTilePer];
+    load_lag_tile(a, s, l, s_min, s_max);
     if (s_max < s_min) return;  // no node with a representable lag (uniform)
     const int tlo = s_min;
     const bool local = (int64_t)s_max - s_min < kHistBins;
@@ -305,9 +310,9 @@ __global__ void __launch_bounds__(256) k_cdft_scatter(CdftBatch a)
     for (int i = threadIdx.x; i < span; i += blockDim.x) s_cnt[i] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    int rank[kScatterPer];
+    int rank[kTilePer];
 #pragma unroll
-    for (int k = 0; k < kScatterPer; ++k) {
+    for (int k = 0; k < kTilePer; ++k) {
         // one atomic per distinct lag in the warp; the peers take
         // consecutive ranks in lane order
         const unsigned peers = __match_any_sync(0xffffffffu, l[k]);
@@ -326,10 +331,9 @@ __global__ void __launch_bounds__(256) k_cdft_scatter(CdftBatch a)
     __syncthreads();
     const size_t so = (size_t)s * a.G;
 #pragma unroll
-    for (int k = 0; k < kScatterPer; ++k) {
+    for (int k = 0; k < kTilePer; ++k) {
         if (l[k] == INT_MIN) continue;
-        const int i = threadIdx.x + 256 * k;
-        const int64_t p = (int64_t)(r0 + i / kHistTile) * a.nlon + c0 + i % kHistTile;
+        const int64_t p = tile_node(a, k);
         const int b = bb + l[k] - lmin;
         const int pos = a.offs[b] + (local ? s_base[l[k] - tlo] : 0) + rank[k];
         a.order[so + pos] = (int)p;
