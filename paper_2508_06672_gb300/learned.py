@@ -10,10 +10,10 @@ dense re-evaluation around the argmax) is replaced by:
    each cell;
 3. the top ``regions`` cells of that map, at least ``2 radius + 1`` cells
    apart (dg_detect on the cell-centre grid);
-4. around each, the cost surface of Algorithm 1 on a square region of side
-   ``region_m`` at the full search's node spacing, its argmax and the same
-   dense re-evaluation as the full search (dg_set_grid, dg_cost_surface,
-   dg_argmax_refine on one context that keeps the captures);
+4. around each, the cost surface of Algorithm 1 on the full search's nodes
+   within a square of side ``region_m``, its argmax and the same dense
+   re-evaluation as the full search (dg_set_grid, dg_search_regions on one
+   context that keeps the captures);
 5. the region whose argmax holds the largest cost gives the fix.
 
 The method without the network ranks the cells by the sum of the K coarse
@@ -135,17 +135,23 @@ class LearnedSearch:
             return self.hm.detect(logits, float(v), relative=False, radius=self.radius, max_peaks=self.regions)
 
     def region_grid(self, lat_deg, lon_deg):
-        """The region around a point, centred on the nearest node of the full
-        search's grid, at its spacing."""
+        """The region around a point: the nodes of the full search's grid
+        within ``half`` rows and columns of the node nearest to the point.
+        A grid's node spacing is set in metres and turned into degrees at its
+        own centre latitude, so the region takes the spacing in metres that
+        gives the full grid's degree steps at the region's centre: its nodes
+        are then nodes of the full grid."""
         i, j = node_of(self.grid, lat_deg, lon_deg)
         i = min(max(int(round(i)), 0), int(self.grid["nlat"]) - 1)
         j = min(max(int(round(j)), 0), int(self.grid["nlon"]) - 1)
-        dlat, dlon = degrees_per_metre(float(self.grid["lat0_deg"]))
-        lat = float(self.grid["lat0_deg"]) + (i - 0.5 * (int(self.grid["nlat"]) - 1)) * dlat * float(self.grid["dlat_m"])
-        lon = float(self.grid["lon0_deg"]) + (j - 0.5 * (int(self.grid["nlon"]) - 1)) * dlon * float(self.grid["dlon_m"])
+        dlat0, dlon0 = degrees_per_metre(float(self.grid["lat0_deg"]))
+        step_lat = dlat0 * float(self.grid["dlat_m"])  # degrees per row and per column of the full grid
+        step_lon = dlon0 * float(self.grid["dlon_m"])
+        lat = float(self.grid["lat0_deg"]) + (i - 0.5 * (int(self.grid["nlat"]) - 1)) * step_lat
+        lon = float(self.grid["lon0_deg"]) + (j - 0.5 * (int(self.grid["nlon"]) - 1)) * step_lon
+        dlat, dlon = degrees_per_metre(lat)
         n = 2 * self.half + 1
-        return dict(lat0_deg=lat, lon0_deg=lon, dlat_m=float(self.grid["dlat_m"]), dlon_m=float(self.grid["dlon_m"]),
-                    nlat=n, nlon=n)
+        return dict(lat0_deg=lat, lon0_deg=lon, dlat_m=step_lat / dlat, dlon_m=step_lon / dlon, nlat=n, nlon=n)
 
     def search(self, net=None):
         """(fix, index of the region it came from, proposals)."""
