@@ -63,7 +63,7 @@ struct CdftBufs {  // chunked-DFT scratch, grown on demand
     int *candL = nullptr, *order = nullptr;
     float *candNu = nullptr, *nuS = nullptr;
     size_t sg_cap = 0;
-    int2 *g2b = nullptr;
+    int4 *g2b = nullptr;
     size_t g2b_cap = 0;
     float *xyzf = nullptr;
     size_t xyzf_cap = 0;
@@ -699,7 +699,7 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         {
             Timed t(c, kplan);
             CK(c, launch_cdft_geo(a, c->stream));
-            CK(c, cudaMemsetAsync(b.g2b, 0xff, sizeof(int2) * (size_t)bt.groups, c->stream));
+            CK(c, cudaMemsetAsync(b.g2b, 0xff, sizeof(int4) * (size_t)bt.groups, c->stream));
             CK(c, launch_cdft_plan(a, (int)bt.nbt, c->stream));
             CK(c, launch_cdft_tiles(a, c->stream));
             t.done(mma ? 6 : 7);

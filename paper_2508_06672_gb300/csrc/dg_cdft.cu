@@ -270,7 +270,9 @@ __global__ void __launch_bounds__(1024) k_cdft_scan(CdftBatch a)
         a.gofs[b] = og;
         const int n = a.count[b];
         const int ng = (n + kCdftCombineGroup - 1) / kCdftCombineGroup;
-        for (int g = 0; g < ng; ++g) a.g2b[a.gbase[s] + og + g] = make_int2(b, s);
+        for (int g = 0; g < ng; ++g)
+            a.g2b[a.gbase[s] + og + g] =
+                make_int4(b, s, oc + g * kCdftCombineGroup, min(kCdftCombineGroup, n - g * kCdftCombineGroup));
         oc += n;
         og += ng;
     }
@@ -329,15 +331,21 @@ __global__ void __launch_bounds__(256) k_cdft_scatter(CdftBatch a)
         s_base[i] = n ? atomicAdd(a.subcnt + bb + tlo + i - lmin, n) : 0;
     }
     __syncthreads();
+    // every load before the first store: the stores may alias the loads as
+    // far as the compiler knows, so mixing them would serialise 16 round trips
     const size_t so = (size_t)s * a.G;
+    float nu[kTilePer];
 #pragma unroll
     for (int k = 0; k < kTilePer; ++k) {
         if (l[k] == INT_MIN) continue;
-        const int64_t p = tile_node(a, k);
-        const int b = bb + l[k] - lmin;
-        const int pos = a.offs[b] + (local ? s_base[l[k] - tlo] : 0) + rank[k];
-        a.order[so + pos] = (int)p;
-        a.nuS[so + pos] = a.candNu[so + p];
+        rank[k] += a.offs[bb + l[k] - lmin] + (local ? s_base[l[k] - tlo] : 0);
+        nu[k] = a.candNu[so + tile_node(a, k)];
+    }
+#pragma unroll
+    for (int k = 0; k < kTilePer; ++k) {
+        if (l[k] == INT_MIN) continue;
+        a.order[so + rank[k]] = (int)tile_node(a, k);
+        a.nuS[so + rank[k]] = nu[k];
     }
 }
 
@@ -486,31 +494,17 @@ __global__ void __launch_bounds__(kCdftCombineThreads) k_cdft_combine(CdftBatch 
 {
     // per (super-)chunk and bin: the DFT value (re, im)
     __shared__ __align__(16) float2 ws[kSeg][64];
-    __shared__ int sh_b, sh_s, sh_first, sh_n, sh_M, sh_B;
-    __shared__ float sh_base, sh_inv;
     // one CTA per combine group of the batch's upper bound; groups past a
-    // snapshot's last are -1 in the scan's group-to-bucket map
-    if (threadIdx.x == 0) {
-        const int gid = blockIdx.x;
-        const int2 bs = a.g2b[gid];
-        const int b = bs.x;
-        sh_b = b;
-        if (b >= 0) {
-            const int s = bs.y;
-            const int lgid = gid - a.gbase[s];
-            sh_s = s;
-            sh_first = (lgid - a.gofs[b]) * kCdftCombineGroup;
-            sh_n = a.count[b] - sh_first;
-            sh_M = a.Mcs[s];
-            sh_B = (a.sd[s].n + sh_M - 1) / sh_M;
-            sh_base = a.nubase[s];
-            sh_inv = 1.0f / a.delta[s];
-        }
-    }
-    __syncthreads();
-    const int b = sh_b;
+    // snapshot's last are -1 in the scan's group map. Every thread reads the
+    // group's record and its snapshot's constants itself (broadcast loads),
+    // so the bucket's DFTs and the candidates are one round trip behind it.
+    const int4 gr = a.g2b[blockIdx.x];
+    const int b = gr.x;
     if (b < 0) return;  // uniform
-    const int s = sh_s, M = sh_M, B = sh_B, n = sh_n;
+    const int s = gr.y, n = gr.w;
+    const int M = a.Mcs[s];
+    const int B = (a.sd[s].n + M - 1) / M;
+    const float nbase = a.nubase[s], inv = 1.0f / a.delta[s];
     const float *Wb = a.W + (size_t)b * a.Bmax * 128;
     // the first segment of DFTs depends on the bucket only: its loads travel
     // together with the candidates' below
@@ -519,7 +513,7 @@ __global__ void __launch_bounds__(kCdftCombineThreads) k_cdft_combine(CdftBatch 
         const float *row = Wb + (size_t)ch * 128;
         ws[ch][q] = make_float2(row[q], row[64 + q]);
     }
-    const size_t sp0 = (size_t)s * a.G + a.offs[b] + sh_first;
+    const size_t sp0 = (size_t)s * a.G + gr.z;
     int c[kCdftCombinePer], q0[kCdftCombinePer];
     float wm[kCdftCombinePer], w0[kCdftCombinePer], wp[kCdftCombinePer], ex[kCdftCombinePer],
         ey[kCdftCombinePer], px[kCdftCombinePer], py[kCdftCombinePer], cx[kCdftCombinePer], cy[kCdftCombinePer],
@@ -529,10 +523,10 @@ __global__ void __launch_bounds__(kCdftCombineThreads) k_cdft_combine(CdftBatch 
         const int j = threadIdx.x + k * kCdftCombineThreads;
         const bool act = j < n;
         c[k] = act ? a.order[sp0 + j] : -1;
-        nu[k] = act ? a.nuS[sp0 + j] : sh_base;
+        nu[k] = act ? a.nuS[sp0 + j] : nbase;
         // quadratic (3-point Lagrange) interpolation on bins q0 - 1, q0, q0 + 1
         // with q0 the nearest bin, kept in [1, 62]; t = offset from bin q0
-        const float u = (nu[k] - sh_base) * sh_inv;
+        const float u = (nu[k] - nbase) * inv;
         q0[k] = max(1, min(62, __float2int_rn(u)));
         const float t = u - (float)q0[k];
         wm[k] = 0.5f * t * (t - 1.f);

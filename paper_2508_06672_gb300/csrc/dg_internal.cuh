@@ -322,7 +322,8 @@ struct CdftBatch {
     float *candNu;                // [S][G] FDOA / fs
     int *order;                   // [S][G] candidates sorted by (bucket, bin)
     float *nuS;                   // [S][G] their FDOAs, in the same order
-    int2 *g2b;                    // [groups] (bucket, snapshot) of each combine group (x = -1: none)
+    int4 *g2b;                    // [groups] per combine group: x bucket (-1: none), y snapshot, z its first
+                                  // position in the snapshot's order slice, w its candidates
     int *count;                   // [NBT]
     int *offs, *gofs;             // [NBT]
     int *subcnt;                  // [NBT] fill cursor of each bucket (scatter)
