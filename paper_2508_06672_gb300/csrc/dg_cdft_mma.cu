@@ -253,6 +253,29 @@ __device__ __forceinline__ int step_of_tile(const int *base, int S, int t)
 // 32-sample stage j, part 0 (high) / 1 (residual, split forms only), blk 0
 // (multiplies z_re) / 1 (multiplies z_im), output column n, sample m = 32 j + k,
 // bin q = n % 64, V = e^{j 2 pi (nubase + q delta) m}.
+//
+// One thread per (bin q, stage j, 8 consecutive samples): one sin/cos per
+// (q, m) serves the four entries it feeds -- (blk 0, n = q) V_re,
+// (blk 0, n = q + 64) V_im, (blk 1, n = q) -V_im, (blk 1, n = q + 64) V_re --
+// and each lands as one 16-byte row of a core matrix.
+template <int DT, int P>
+__device__ __forceinline__ void btab_row(uint16_t *stage, int blk, int n, int kg, const float (&v)[8], float sign)
+{
+    uint32_t h[4], r[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const float x0 = sign * v[2 * e], x1 = sign * v[2 * e + 1];
+        const uint16_t h0 = to16<DT>(x0), h1 = to16<DT>(x1);
+        h[e] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+        if (P == 2)
+            r[e] = (uint32_t)to16<DT>(x0 - from16<DT>(h0)) | ((uint32_t)to16<DT>(x1 - from16<DT>(h1)) << 16);
+    }
+    uint16_t *dst = stage + blk_off(n, 8 * kg) / 2;
+    *reinterpret_cast<uint4 *>(dst + (size_t)blk * (kBlockBytes / 2)) = make_uint4(h[0], h[1], h[2], h[3]);
+    if (P == 2)
+        *reinterpret_cast<uint4 *>(dst + (size_t)(2 + blk) * (kBlockBytes / 2)) = make_uint4(r[0], r[1], r[2], r[3]);
+}
+
 template <int DT, int P>
 __global__ void __launch_bounds__(256) k_cdft_btab(const float *nubase, const float *delta, int M, uint16_t *btab)
 {
@@ -261,24 +284,23 @@ __global__ void __launch_bounds__(256) k_cdft_btab(const float *nubase, const fl
     const size_t per_stage = (size_t)P * 2 * kRows * kKS;  // 16-bit elements
     const size_t per_step = (size_t)NJ * per_stage;
     const float b0 = nubase[s], d = delta[s];
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)NJ * 2 * kRows * kKS;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)NJ * 64 * (kKS / 8);
          i += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(i % kKS);
-        const int n = (int)((i / kKS) % kRows);
-        const int blk = (int)((i / (kKS * kRows)) % 2);
-        const int j = (int)(i / (2 * kKS * kRows));
-        const int m = j * kKS + k, q = n & 63;
+        const int kg = (int)(i % (kKS / 8));
+        const int q = (int)((i / (kKS / 8)) % 64);
+        const int j = (int)(i / (64 * (kKS / 8)));
         // bin frequency in FP32 as the combine forms it; the phase of
         // sample m (< 2^24) from the exact product split
-        float sn, cs;
-        sincospif(2.0f * frac_mul(fmaf((float)q, d, b0), (float)m), &sn, &cs);
-        float v;
-        if (blk == 0) v = n < 64 ? cs : sn;   // z_re * (V_re | V_im)
-        else v = n < 64 ? -sn : cs;           // z_im * (-V_im | V_re)
-        uint16_t *dst = btab + (size_t)s * per_step + (size_t)j * per_stage + blk_off(n, k) / 2;
-        const uint16_t h = to16<DT>(v);
-        dst[(size_t)blk * (kBlockBytes / 2)] = h;
-        if (P == 2) dst[(size_t)(2 + blk) * (kBlockBytes / 2)] = to16<DT>(v - from16<DT>(h));
+        const float fq = fmaf((float)q, d, b0);
+        float sn[8], cs[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+            sincospif(2.0f * frac_mul(fq, (float)(j * kKS + 8 * kg + e)), &sn[e], &cs[e]);
+        uint16_t *stage = btab + (size_t)s * per_step + (size_t)j * per_stage;
+        btab_row<DT, P>(stage, 0, q, kg, cs, 1.0f);        // z_re * V_re
+        btab_row<DT, P>(stage, 0, q + 64, kg, sn, 1.0f);   // z_re * V_im
+        btab_row<DT, P>(stage, 1, q, kg, sn, -1.0f);       // z_im * (-V_im)
+        btab_row<DT, P>(stage, 1, q + 64, kg, cs, 1.0f);   // z_im * V_re
     }
 }
 
@@ -1295,7 +1317,7 @@ __global__ void __launch_bounds__(kHkThreads, 1) k_cdft_contract_hk(CdftBatch a)
 
 cudaError_t launch_cdft_btab(const CdftBatch &a, int mode, void *btab, cudaStream_t st)
 {
-    const size_t n = (size_t)(a.M / kKS) * 2 * kRows * kKS;
+    const size_t n = (size_t)(a.M / kKS) * 64 * (kKS / 8);
     unsigned gx = (unsigned)std::min<size_t>((n + 255) / 256, 1024);
     dim3 grid(gx, (unsigned)a.S);
     switch (mode) {
