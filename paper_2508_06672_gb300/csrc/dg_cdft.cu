@@ -459,16 +459,25 @@ __global__ void __launch_bounds__(256) k_cdft_superchunk(CdftBatch a, int NBT)
     sincospif(2.0f * frac_mul(nq, (float)M), &ey, &ex);
     float *Wb = a.W + (size_t)bg * a.Bmax * 128;
     for (int c = 0; c * R < B; ++c) {
-        float ux = 0.f, uy = 0.f, px = 1.f, py = 0.f;
+        float ux = 0.f, uy = 0.f;
         const int r1 = min(R, B - c * R);
-        for (int r = 0; r < r1; ++r) {
-            const float *w = Wb + (size_t)(c * R + r) * 128;
-            const float wx = w[q], wy = w[64 + q];
-            ux = fmaf(px, wx, fmaf(-py, wy, ux));
-            uy = fmaf(px, wy, fmaf(py, wx, uy));
-            if ((r & 15) == 15) {  // re-anchor the rotation every 16 chunks
-                sincospif(2.0f * frac_mul(nq, (float)((r + 1) * M)), &py, &px);
-            } else {
+        // blocks of 16 chunks: the rotation is anchored at each block's first
+        // chunk and stepped within it; the block's loads are issued together
+        for (int r0 = 0; r0 < r1; r0 += 16) {
+            float px = 1.f, py = 0.f;
+            if (r0 > 0) sincospif(2.0f * frac_mul(nq, (float)(r0 * M)), &py, &px);
+            const float *w = Wb + (size_t)(c * R + r0) * 128;
+            float wx[16], wy[16];
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                wx[r] = r0 + r < r1 ? w[(size_t)r * 128 + q] : 0.f;
+                wy[r] = r0 + r < r1 ? w[(size_t)r * 128 + 64 + q] : 0.f;
+            }
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                if (r0 + r >= r1) break;
+                ux = fmaf(px, wx[r], fmaf(-py, wy[r], ux));
+                uy = fmaf(px, wy[r], fmaf(py, wx[r], uy));
                 const float nx = fmaf(px, ex, -py * ey);
                 py = fmaf(px, ey, py * ex);
                 px = nx;
