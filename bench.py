@@ -739,7 +739,7 @@ def run_learned(a, rank, world, local_rank):
         judge.argmax_refine(cost, 25.0, 500.0)
         search.search()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    learned_ms, full_ms, rec, rec_sum, err_l, err_f = [], [], [], [], [], []
+    learned_ms, full_ms, rec, rec_sum, err_l, err_f, same = [], [], [], [], [], [], []
     l0 = search.geo.launch_count() + search.hm.launch_count()
     nn_launches = 2 * len(net.params) - 1
     clk = ClockSampler(_smi_id(local_rank))
@@ -778,6 +778,8 @@ def run_learned(a, rank, world, local_rank):
                                       sc.emitter_lon_deg))
             err_l.append(L.distance_m(lf["refined_lat_deg"], lf["refined_lon_deg"], sc.emitter_lat_deg,
                                       sc.emitter_lon_deg))
+            same.append(L.distance_m(lf["refined_lat_deg"], lf["refined_lon_deg"], jf["refined_lat_deg"],
+                                     jf["refined_lon_deg"]) < 100.0)
             if i < n_sc:
                 _, _, speaks = search.search(sumnet)
                 rec_sum.append(covered(speaks))
@@ -823,6 +825,7 @@ def run_learned(a, rank, world, local_rank):
                        "l2": "flushed before each timed search (256 MB write outside the events)"},
             "full_grid_ms": med_f, "speedup_vs_full_grid": med_f / med_l,
             "recall": float(np.mean(rec)), "recall_coarse_sum_without_network": float(np.mean(rec_sum)),
+            "same_fix_as_full_grid": float(np.mean(same)),
             "error_m": {"learned_p50": float(np.median(err_l)), "learned_p90": float(np.percentile(err_l, 90)),
                         "full_grid_p50": float(np.median(err_f)), "full_grid_p90": float(np.percentile(err_f, 90))},
             "e2e": {"value": statistics.median(e2e), "unit": "ms", "h2d_bytes_per_step": h2d,
