@@ -69,7 +69,7 @@ struct CdftBufs {  // chunked-DFT scratch, grown on demand
     size_t xyzf_cap = 0;
     float *ephf = nullptr;
     size_t ephf_cap = 0;
-    int *count = nullptr, *offs = nullptr, *gofs = nullptr, *subcnt = nullptr;
+    int *count = nullptr, *offs = nullptr, *subcnt = nullptr;
     size_t nb_cap = 0;
     float *delta = nullptr;
     float2 *V = nullptr;
@@ -590,7 +590,6 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         const size_t n = (size_t)L.nbt_max;
         if ((st = grow(c, &b.count, n)) != DG_OK) return st;
         if ((st = grow(c, &b.offs, n)) != DG_OK) return st;
-        if ((st = grow(c, &b.gofs, n)) != DG_OK) return st;
         if ((st = grow(c, &b.subcnt, n)) != DG_OK) return st;
         b.nb_cap = n;
     }
@@ -680,7 +679,6 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         a.V = b.V;
         a.count = b.count;
         a.offs = b.offs;
-        a.gofs = b.gofs;
         a.subcnt = b.subcnt;
         a.W = b.W;
         a.tbase = b.tbase;
@@ -1679,7 +1677,6 @@ dg_status dg_destroy(dg_ctx *c)
     fr(c->cd.ephf);
     fr(c->cd.count);
     fr(c->cd.offs);
-    fr(c->cd.gofs);
     fr(c->cd.subcnt);
     fr(c->cd.nur);
     fr(c->cd.nubase);

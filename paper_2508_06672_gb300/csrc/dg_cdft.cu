@@ -234,7 +234,8 @@ __global__ void __launch_bounds__(256) k_cdft_hist(CdftBatch a)
 // ---------------------------------------------------------------------------
 // scan: one CTA (1024 threads) per snapshot.
 // offs[b]  = offset of bucket b's candidates within the snapshot's order slice
-// gofs[b]  = first combine group of bucket b, counted from the snapshot's base
+// g2b      = the record of each combine group (bucket, snapshot, first
+//            position in the order slice, size), groups of a bucket in a row
 // nubase[s], delta[s] = the snapshot's bins (from its FDOA range).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_cdft_scan(CdftBatch a)
@@ -267,7 +268,6 @@ __global__ void __launch_bounds__(1024) k_cdft_scan(CdftBatch a)
     for (int i = b0; i < b1; ++i) {
         const int b = b_first + i;
         a.offs[b] = oc;
-        a.gofs[b] = og;
         const int n = a.count[b];
         const int ng = (n + kCdftCombineGroup - 1) / kCdftCombineGroup;
         for (int g = 0; g < ng; ++g)

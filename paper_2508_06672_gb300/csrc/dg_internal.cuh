@@ -325,7 +325,7 @@ struct CdftBatch {
     int4 *g2b;                    // [groups] per combine group: x bucket (-1: none), y snapshot, z its first
                                   // position in the snapshot's order slice, w its candidates
     int *count;                   // [NBT]
-    int *offs, *gofs;             // [NBT]
+    int *offs;                    // [NBT]
     int *subcnt;                  // [NBT] fill cursor of each bucket (scatter)
     float *nubase, *delta;        // [S] bins nu_q = nubase + q delta
     float2 *V;                    // [S][M][64] DFT table e^{j 2 pi nu_q m}
