@@ -134,7 +134,9 @@ typedef struct {
                         0 = chosen per batch of snapshots: the longest power
                         of two <= 1024 whose length x bin spacing is <= 1.2e-2
                         cycles in every snapshot of the batch
-                        (dg_cdft_chunks)                                      */
+                        (dg_cdft_chunks), at most 256 on the refinement grid
+                        of dg_argmax_refine (few lags: shorter chunks give
+                        the contraction more tiles)                           */
     int32_t bins;    /* CDFT: Doppler bins per lag; 0 = 64 (the only value)   */
     int32_t contract;/* CDFT: DG_CONTRACT_*                                   */
     int32_t tiles;   /* CDFT tensor-core tile shape: DG_TILES_*               */

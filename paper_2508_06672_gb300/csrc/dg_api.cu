@@ -556,6 +556,7 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
     for (size_t i = 0; i < L.batches.size(); ++i) {
         const auto &t = L.batches[i];
         Ms[i] = c->opt.chunk ? c->opt.chunk : auto_chunk(span, t.k0, t.S);
+        if (refine && !c->opt.chunk) Ms[i] = std::min(Ms[i], kCdftRefineMaxChunk);
         M_max = std::max(M_max, Ms[i]);
         for (int s = 0; s < t.S; ++s) B_max = std::max<int>(B_max, (int)((c->steps[t.k0 + s].n + Ms[i] - 1) / Ms[i]));
     }

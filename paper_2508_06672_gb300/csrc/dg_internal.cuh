@@ -379,6 +379,10 @@ constexpr int kTcMaxSnapshots = 64;
 // super-chunks keep below it.
 constexpr int kCdftMaxChunk = 4096;
 constexpr int kCdftAutoMaxChunk = 1024;
+// Automatic chunk cap of a refinement surface: its few lags per snapshot give
+// few (lag, chunk) rows, and shorter chunks turn the same tensor work into
+// more and shorter tiles, spread over more SMs.
+constexpr int kCdftRefineMaxChunk = 256;
 constexpr double kCdftMDelta = 1.2e-2;
 
 // Threshold detection (dg_detect.cu). cap: power of two <= kDetectCap candidates
