@@ -439,8 +439,8 @@ __global__ void __launch_bounds__(256) k_cdft_contract_f32(CdftBatch a)
 // Mc = R M samples, exactly at the bin frequencies:
 //     U_c(nu_q) = sum_{r<R} e^{j 2 pi nu_q r M} W_{cR + r}(nu_q).
 // The combine then interpolates U_c between bins, and its error is governed
-// by Mc Delta instead of M Delta; the host picks Mc so that Mc Delta stays
-// within the same bound. One thread per (bucket, bin); each reads its own
+// by Mc Delta instead of M Delta; k_cdft_tiles picks Mc so that Mc Delta
+// stays within the same bound. One thread per (bucket, bin); each reads its own
 // bin of chunks cR .. cR + R - 1 and writes super-chunk c in place (c <= cR,
 // and later super-chunks read only later chunks).
 // ---------------------------------------------------------------------------
