@@ -3,7 +3,9 @@
 The reference arm times the oracle on a bounded sample of the default
 workload and prints one JSON line with the same metric, unit and direction as
 the library's arm. Without a GPU the library's arm must fail (non-zero exit)
-instead of measuring something else."""
+instead of measuring something else. Two helpers of the line: the clock
+summary taken from nvidia-smi samples, and the contraction's DRAM traffic,
+reported only for the kernel source it was captured on."""
 import json
 import os
 import subprocess
@@ -44,3 +46,39 @@ def test_library_arm_fails_without_a_gpu():
     r = _run("--steps", "1", "--warmup", "3", "--no-direct", "--no-cpu-baseline")
     assert r.returncode != 0
     assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+
+
+def _bench():
+    sys.path.insert(0, ROOT)
+    import bench
+    return bench
+
+
+def test_clock_summary_reads_the_sampled_lines():
+    b = _bench()
+    c = b.ClockSampler(0)
+    c.lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "0, 2055, 2070, 1200.5, 0x4, Not Active, Not Active, Not Active, Active",
+               "0, 2070, 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "garbled line", "0, [N/A], 2070, 1, 0, Not Active, Not Active, Not Active, Not Active"]
+    s = c.summary()
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c.lines = ["0, 1200, 2070, 700, 0x8, Active, Not Active, Active, Not Active"]
+    assert c.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    c.lines = []
+    assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_contraction_traffic_only_for_the_source_it_was_measured_on(tmp_path, monkeypatch):
+    b = _bench()
+    t = b.CONTRACT_TRAFFIC
+    assert b.contract_traffic(t["workload"], t["contract"], t["chunk"]) == t["bytes_per_launch"]
+    assert b.contract_traffic(t["workload"], "bf16", t["chunk"]) is None
+    assert b.contract_traffic("large", t["contract"], t["chunk"]) is None
+    assert b.contract_traffic(t["workload"], t["contract"], 256) is None
+    # another kernel source: no traffic figure
+    src = tmp_path / "paper_2508_06672_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "dg_cdft_mma.cu").write_text("// a changed kernel\n")
+    monkeypatch.setattr(b, "ROOT", str(tmp_path))
+    assert b.contract_traffic(t["workload"], t["contract"], t["chunk"]) is None
