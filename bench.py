@@ -196,17 +196,19 @@ def oracle_rate(scene, target_s, seed=0, max_pts=None):
     KN = scene.k_steps * scene.n_samples
     y1, y2 = oracle.iq_to_f64(scene.y1), oracle.iq_to_f64(scene.y2)
     args = (scene.grid, scene.ephem, scene.fs_hz, scene.fc_hz, y1, y2)
+    # every core this process may run on, whatever OMP_NUM_THREADS says (a
+    # launcher such as torchrun sets it to 1): the line reports this count
     cores = host_cores()
     # calibrate on a few points, then size the sample for ~target_s
     cal = rng.integers(0, scene.G, max(4, cores))
     t0 = time.perf_counter()
-    oracle.cost_points(*args, idx=cal)
+    oracle.cost_points(*args, idx=cal, nthreads=cores)
     dt = max(time.perf_counter() - t0, 1e-3)
     rate = cal.size * KN / dt
     npts = int(max(cores, min(target_s * rate / KN, max_pts or 1e12)))
     idx = rng.integers(0, scene.G, npts)
     t0 = time.perf_counter()
-    oracle.cost_points(*args, idx=idx)
+    oracle.cost_points(*args, idx=idx, nthreads=cores)
     dt = time.perf_counter() - t0
     return npts * KN / dt, dt, npts, cores
 

@@ -82,3 +82,22 @@ def test_contraction_traffic_only_for_the_source_it_was_measured_on(tmp_path, mo
     (src / "dg_cdft_mma.cu").write_text("// a changed kernel\n")
     monkeypatch.setattr(b, "ROOT", str(tmp_path))
     assert b.contract_traffic(t["workload"], t["contract"], t["chunk"]) is None
+
+
+def test_reference_arm_under_torchrun_prints_on_rank_0_only():
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+                        "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "3",
+                        "--reference-step-s", "0.3"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [json.loads(ln) for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = lines[0]
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    # torchrun sets OMP_NUM_THREADS=1; the line reports every core of the process's affinity, and
+    # the oracle is given that many threads explicitly
+    assert d["cpu_baseline"]["cores"] == len(os.sched_getaffinity(0))
