@@ -261,11 +261,14 @@ def subcell(cost, i, j):
 
 
 def refine_grid(grid, index, spacing_m, window_m):
-    """Local grid for dense re-evaluation around a coarse cell: centred on the
-    cell's latitude/longitude, spacing_m apart, half-width window_m."""
+    """Local grid for dense re-evaluation around a coarse cell (Algorithm 1's
+    search repeated on a finer lattice): centred on the cell's latitude and
+    longitude, spacing_m apart in metres at that latitude (the grid reading of
+    Sec. III), with round(window_m / spacing_m) nodes on each side of the
+    centre, rounded half away from zero like the lag of Eq. 9."""
     nlon = int(grid["nlon"])
     lat, lon = grid_node(grid, index // nlon, index % nlon)
-    half = int(round(window_m / spacing_m))
+    half = int(np.floor(window_m / spacing_m + 0.5))
     return dict(lat0_deg=np.degrees(lat), lon0_deg=np.degrees(lon), dlat_m=float(spacing_m),
                 dlon_m=float(spacing_m), nlat=2 * half + 1, nlon=2 * half + 1)
 
