@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import sim
-from gpu_common import (assert_argmax_consistent, gpu_surface, lag_boundary_mask, oracle_surface, package,
+from gpu_common import (assert_argmax_consistent, assert_global_argmax, gpu_surface, lag_boundary_mask, oracle_surface, package,
                         rel_err, torch_cuda)
 
 pytestmark = pytest.mark.gpu
@@ -224,20 +224,15 @@ def test_cdft_mid_subgrid_full_k_n():
     g.close()
 
 
-def _sampled(s, c, npts, seed):
+def _sampled(s, c, npts, seed, tol=FP32_TOL):
+    """Pointwise bound on random nodes, then the complete argmax check over
+    every node that can hold the oracle's maximum under that bound."""
     rng = np.random.default_rng(seed)
-    am = int(np.argmax(c.ravel()))
-    nlon = s.grid["nlon"]
-    i, j = divmod(am, nlon)
-    nb = [(i + di) * nlon + (j + dj) for di in (-1, 0, 1) for dj in (-1, 0, 1)
-          if 0 <= i + di < s.grid["nlat"] and 0 <= j + dj < nlon]
-    idx = np.unique(np.concatenate([rng.integers(0, s.G, npts), nb]))
+    idx = np.unique(rng.integers(0, s.G, npts))
     ref = oracle.cost_points(*oracle.scene_args(s), idx=idx)
     ok = ~lag_boundary_mask(s, idx)
-    assert rel_err(c.ravel()[idx][ok], ref[ok]) < FP32_TOL
-    refnb = dict(zip(idx, ref))
-    assert max(nb, key=lambda p: (refnb[p], -p)) == am
-    return am
+    assert rel_err(c.ravel()[idx][ok], ref[ok]) < tol
+    return assert_global_argmax(s, c, tol)
 
 
 def test_cdft_mid_full_size_sampled_and_against_direct():
@@ -266,7 +261,9 @@ def test_cdft_refine_and_unsupported_options():
     cost = g.cost_surface()
     fix = g.argmax_refine(cost, 100.0, 1000.0)
     ref = oracle_surface(s)
-    am = assert_argmax_consistent(cost.cpu().numpy(), ref, FP32_TOL)
+    # the 41 x 41 tiny surface's top two differ by ~1.9e-5 of the maximum: a
+    # near-tie at the FP32 bound
+    am = assert_argmax_consistent(cost.cpu().numpy(), ref, FP32_TOL, near_tie=True)
     lg = oracle.refine_grid(s.grid, fix["index"], 100.0, 1000.0)
     lref = oracle.cost_surface(lg, s.ephem, s.fs_hz, s.fc_hz, s.y1, s.y2)
     ri = fix["ri"] * lg["nlon"] + fix["rj"]
@@ -308,7 +305,9 @@ def test_cdft_tensor_core_mid_subgrid(contract):
     ref = oracle_surface(s)
     ok = ~lag_boundary_mask(s, np.arange(s.G))
     assert rel_err(c.ravel()[ok], ref.ravel()[ok]) < TC_TOL[contract]
-    assert_argmax_consistent(c, ref, TC_TOL[contract])
+    # the sub-grid's top two differ by ~1.1e-3 of the maximum: decisive at the
+    # split forms' bound, a near-tie at the single 16-bit forms'
+    assert_argmax_consistent(c, ref, TC_TOL[contract], near_tie=contract in ("bf16", "fp16"))
     g.close()
 
 

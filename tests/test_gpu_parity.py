@@ -18,8 +18,8 @@ import pytest
 
 import oracle
 import sim
-from gpu_common import (assert_argmax_consistent, gpu_surface, lag_boundary_mask, oracle_surface, package,
-                        rel_err, torch_cuda)
+from gpu_common import (assert_argmax_consistent, assert_global_argmax, gpu_surface, lag_boundary_mask,
+                        oracle_surface, package, rel_err, torch_cuda)
 
 pytestmark = pytest.mark.gpu
 
@@ -119,7 +119,9 @@ def test_mid_geometry_noise_free_peaks_at_emitter(delay, dm):
     ref = oracle_surface(s, dm)
     centre = 10 * 21 + 10
     assert oracle.argmax(ref) == centre
-    assert_argmax_consistent(c, ref, FP32_TOL)
+    # integer lags: the emitter's node leads its neighbour by only ~2.6e-5 of
+    # the maximum (a near-tie at the FP32 bound); Lagrange4: by ~4.4e-4
+    assert_argmax_consistent(c, ref, FP32_TOL, near_tie=(dm == 0))
     assert rel_err(c, ref) < FP32_TOL
     g.close()
 
@@ -262,20 +264,14 @@ def test_argmax_ties_and_nan_on_device():
 
 # --------------------------------------------- workloads at full size, sampled
 def _sampled_check(s, c, npts, seed, floor=0.0):
+    """Pointwise bound on random nodes, then the complete argmax check over
+    every node that can hold the oracle's maximum under that bound."""
     rng = np.random.default_rng(seed)
-    am = int(np.argmax(c.ravel()))
-    nlon = s.grid["nlon"]
-    i, j = divmod(am, nlon)
-    nb = [(i + di) * nlon + (j + dj) for di in (-1, 0, 1) for dj in (-1, 0, 1)
-          if 0 <= i + di < s.grid["nlat"] and 0 <= j + dj < nlon]
-    idx = np.unique(np.concatenate([rng.integers(0, s.G, npts), nb]))
+    idx = np.unique(rng.integers(0, s.G, npts))
     ref = oracle.cost_points(*oracle.scene_args(s), idx=idx)
     ok = ~lag_boundary_mask(s, idx)
     assert rel_err(c.ravel()[idx][ok], ref[ok], floor) < FP32_TOL
-    # the device argmax is a local maximum of the oracle's surface too
-    refnb = dict(zip(idx, ref))
-    assert max(nb, key=lambda p: (refnb[p], -p)) == am
-    return am
+    return assert_global_argmax(s, c, FP32_TOL)
 
 
 def test_mid_workload_full_size_sampled():
