@@ -3,16 +3,19 @@
 One step = one pass of the whole hot path over the workload: the cost surface
 (geometry, delay/Doppler alignment, correlation, accumulation over all K
 snapshots; Sec. III, Eq. 11, Algorithm 1) and the argmax with a dense local
-refinement. The default workload is the mid-size one: a 1001 x 1001 grid at
-100 m, K = 20 snapshots of N = 65536 complex int16 samples at 12.5 MHz from a
-10 MHz / 10 us chirp jammer at -15 dB SNR.
+refinement. The default workload is the large footprint, the largest that the
+method's configurations put on one GPU: a 4001 x 4001 grid at 400 m,
+K = 50 snapshots of N = 131072 complex int8 samples at 20 MHz from a wideband
+(18 MHz) noise jammer at -20 dB SNR. --workload mid runs the 1001 x 1001 /
+100 m grid with K = 20 x N = 65536 complex int16 samples of a 10 MHz / 10 us
+chirp at -15 dB.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dg|reference]
 
 Rank 0 prints one JSON line. --impl reference times the CPU oracle on a
 bounded sample of the same workload (same metric and unit).
-Under torchrun each rank processes its own block of 1001 grid rows (weak
-scaling: the grid grows with the number of GPUs).
+Under torchrun each rank processes its own block of grid rows (weak scaling:
+the grid grows with the number of GPUs).
 """
 from __future__ import annotations
 
@@ -32,7 +35,7 @@ sys.path.insert(0, ROOT)
 
 FLOPS_PER_CAND_SAMPLE = 14          # conj product 6 + derotation 6 + accumulation 2
 CDFT_COMBINE_FLOPS = 18             # per candidate x super-chunk: 3-bin interpolation 10 + phase MAC 8
-SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_PROBE_ITERS = 50000           # ~50 ms per probe launch on a GB300
 METRIC = "candidate·sample correlations/s"
 UNIT = "cand·samples/s"
 REFINE_SPACING_M, REFINE_WINDOW_M = 10.0, 200.0
@@ -64,11 +67,13 @@ def workload(name, rank=0, world=1, grid=None):
     return s, desc
 
 
-# DRAM traffic of one contraction launch on the default workload, from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the
-# kernel source it was measured on
-CONTRACT_TRAFFIC = {"source_sha1_16": "9879c696159e10c5", "workload": "mid", "contract": "fp16x3", "chunk": 1024,
-                    "bytes_per_launch": 241.93e6}
+# DRAM traffic of one contraction launch, from one ncu capture per workload
+# (dram__bytes_read.sum + dram__bytes_write.sum); valid only for the kernel
+# source it was measured on
+CONTRACT_TRAFFIC = [
+    {"source_sha1_16": "9879c696159e10c5", "workload": "mid", "contract": "fp16x3", "chunk": 1024,
+     "bytes_per_launch": 241.93e6},
+]
 
 
 def contract_traffic(workload, contract, chunk):
@@ -80,10 +85,42 @@ def contract_traffic(workload, contract, chunk):
             sha = hashlib.sha1(f.read()).hexdigest()[:16]
     except OSError:
         return None
-    t = CONTRACT_TRAFFIC
-    if (sha, workload, contract, chunk) != (t["source_sha1_16"], t["workload"], t["contract"], t["chunk"]):
-        return None
-    return t["bytes_per_launch"]
+    for t in CONTRACT_TRAFFIC:
+        if (sha, workload, contract, chunk) == (t["source_sha1_16"], t["workload"], t["contract"], t["chunk"]):
+            return t["bytes_per_launch"]
+    return None
+
+
+# arithmetic each contraction form performs, as the line's dtype
+CONTRACT_DTYPE = {
+    "fp32": "f32 (FP32 CUDA-core contraction)",
+    "bf16": "bf16 (one bf16 tensor-core product, fp32 accumulate)",
+    "fp16": "fp16 (one fp16 tensor-core product, fp32 accumulate)",
+    "bf16x3": "bf16x3 (split bf16 products hi*hi + lo*hi + hi*lo, fp32 accumulate)",
+    "fp16x3": "fp16x3 (split fp16 products hi*hi + lo*hi + hi*lo, fp32 accumulate)",
+}
+
+
+def fp32_peak(dev_index, stream=None, reps=5):
+    """Measured FP32 FMA peak of the device (dg_fp32_peak: every SM full of
+    independent FMA chains), median of `reps` launches, with the SM clock
+    sampled meanwhile. Returns a dict."""
+    import torch
+
+    import paper_2508_06672_gb300 as P
+
+    st = stream.cuda_stream if stream is not None else 0
+    runs = []
+    with ClockSampler(_smi_id(dev_index)) as clk:
+        for _ in range(reps):
+            runs.append(P.dg_fp32_peak(FP32_PROBE_ITERS, st))
+    torch.cuda.synchronize(dev_index)
+    tf = statistics.median(r[0] for r in runs)
+    c = clk.summary()
+    return {"tflops": tf, "sm_count": runs[0][2], "ms_per_launch": statistics.median(r[1] for r in runs),
+            "sm_mhz": c["sm_mhz"], "reasons": c["reasons"],
+            "basis": ("dg_fp32_peak: 8 resident 256-thread CTAs per SM, 8 independent FMA chains per thread, "
+                      "2 flop per FMA / CUDA-event time, median of 5 launches")}
 
 
 PEAK_BASIS_TENSOR = ("measured cuBLAS bf16 dense GEMM burst (MEASURED_PEAKS.json bf16_tflops); fp16 has the same "
@@ -186,8 +223,9 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ oracle (CPU)
-def oracle_rate(scene, target_s, seed=0, max_pts=None):
-    """Time the FP64 oracle on a bounded sample of the workload's candidates.
+def oracle_rate(scene, target_s, seed=0, max_pts=None, nthreads=None):
+    """Time the FP64 oracle on a bounded sample of the workload's candidates
+    (nthreads: every core this process may run on, unless given).
     Returns (cand*samples/s, seconds, points, cores)."""
     import oracle
 
@@ -198,7 +236,7 @@ def oracle_rate(scene, target_s, seed=0, max_pts=None):
     args = (scene.grid, scene.ephem, scene.fs_hz, scene.fc_hz, y1, y2)
     # every core this process may run on, whatever OMP_NUM_THREADS says (a
     # launcher such as torchrun sets it to 1): the line reports this count
-    cores = host_cores()
+    cores = nthreads or host_cores()
     # calibrate on a few points, then size the sample for ~target_s
     cal = rng.integers(0, scene.G, max(4, cores))
     t0 = time.perf_counter()
@@ -274,6 +312,8 @@ def run_dg(a, rank, world, local_rank):
     def step():
         g.cost_surface(cost)
         return g.argmax_refine(cost, REFINE_SPACING_M, REFINE_WINDOW_M)
+
+    fp = fp32_peak(local_rank, stream)      # the FP32 ceiling of the ALU rooflines
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -407,6 +447,8 @@ def run_dg(a, rank, world, local_rank):
     d2h = 96 + 2 * 4 if a.graph else 2 * 48 + 2 * 4  # the fix (or two argmax records) and error words
 
     kernels = {}
+    alu_peak = fp["tflops"]
+    issued_per_step = None
     if a.algo == "cdft":
         # every kernel of the chunked-DFT path against its own roofline; the
         # dominant one is the headline
@@ -415,10 +457,10 @@ def run_dg(a, rank, world, local_rank):
         chunk = chunk_hi
         nprod = 3 if a.contract.endswith("x3") else 1
         tensor = a.contract != "fp32"
-        # contraction: one chunk x 64-bin complex DFT per (lag, chunk) = 512 * chunk
-        # real flops; the split forms issue three such products on the tensor cores
-        contract_flops = (nprod if tensor else 1) * 512 * chunk * bucket_chunks
-        alu_peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        # contraction: one chunk x 64-bin complex DFT per (lag, chunk) row =
+        # 512 * chunk real flops of algorithmic work; the split forms issue
+        # three such products on the tensor cores
+        contract_flops = 512 * chunk * bucket_chunks
         tc_peak = tensor_peak(a.contract)
         # combine: when the super-chunks leave about one per candidate the
         # kernel is a gather (order index, FDOA, surface write: 12 B per
@@ -429,7 +471,7 @@ def run_dg(a, rank, world, local_rank):
         combine_units = (12 * gk + 1024 * bucket_chunks) / 1e12 if combine_hbm else CDFT_COMBINE_FLOPS * cand_chunks
         for name, flops, bound, peak, basis, unit in (
                 ("contract", contract_flops, "tensor" if tensor else "alu", tc_peak if tensor else alu_peak,
-                 f"{'3 x ' if nprod == 3 and tensor else ''}512 flop x chunk per (lag, chunk) row", "TFLOP/s"),
+                 "512 flop x chunk per (lag, chunk) row (one complex chunk x 64-bin DFT)", "TFLOP/s"),
                 ("combine", combine_units * (1e12 if combine_hbm else 1), "hbm" if combine_hbm else "alu",
                  hbm_peak() if combine_hbm else alu_peak,
                  ("12 B per candidate x snapshot + 1024 B per (lag, chunk) (super-chunk pass)" if combine_hbm else
@@ -441,8 +483,12 @@ def run_dg(a, rank, world, local_rank):
                 ach = flops * a.steps / (ms / 1e3) / scale
                 kernels[name] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit,
                                  "frac": ach / peak, "ms_per_step": ms / a.steps, "basis": basis}
+                if name == "contract" and tensor and nprod > 1:
+                    kernels[name]["issued_frac"] = nprod * ach / peak
         dom = max(("contract", "combine"), key=lambda n: kt[n][0])
         flops_per_step = contract_flops if dom == "contract" else combine_units * (1e12 if combine_hbm else 1)
+        if dom == "contract" and tensor and nprod > 1:
+            issued_per_step = nprod * contract_flops
         corr_ms, corr_launches = kt[dom]
         tc_name = "k_cdft_contract_hk (Hankel tiles)" if a.tiles == "hankel" and chunk <= 1024 else "k_cdft_contract_tc"
         roof_kernel = {"contract": (f"{tc_name} ({a.contract} tcgen05, {chunk}-sample chunks x 64 bins)"
@@ -454,9 +500,9 @@ def run_dg(a, rank, world, local_rank):
     else:
         roof_unit = "TFLOP/s"
         flops_per_step = FLOPS_PER_CAND_SAMPLE * G_rank * KN
-        roof_kernel = "k_corr_direct (FP32, integer lag, ci16)"
+        roof_kernel = "k_corr_direct (FP32, integer lag)"
         roof_basis = f"{FLOPS_PER_CAND_SAMPLE} flop per candidate*sample x G*K*N per launch"
-        roof_bound, roof_peak = "alu", SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        roof_bound, roof_peak = "alu", alu_peak
     worst = torch.tensor([dev_s, corr_ms / 1e3, sum(e2e_ms) / 1e3,
                           (e2e_pipe_s if e2e_pipe_s is not None else sum(e2e_ms) / 1e3 / a.steps)],
                          dtype=torch.float64)
@@ -483,7 +529,8 @@ def run_dg(a, rank, world, local_rank):
                      if a.graph else "dg_cost_surface + dg_argmax_refine (host-synchronising calls)"),
             "ms_per_step_synchronous_calls": sync_ms_per_step,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * dev_s / a.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": CONTRACT_DTYPE[a.contract] if a.algo == "cdft" else "f32",
             "data": "synthetic",
             "config": {"workload": desc, "G": G_rank * world, "K": scene.k_steps, "N": scene.n_samples,
                        "fmt": scene.fmt, "delay": "integer", "algo": a.algo, "acc": "power",
@@ -504,18 +551,25 @@ def run_dg(a, rank, world, local_rank):
             "gpu_launches": int(launches),
             "roofline": {"bound": roof_bound, "achieved": achieved, "peak": peak, "unit": roof_unit,
                          "frac": achieved / peak,
+                         **({"issued_achieved": issued_per_step * a.steps / corr_s / 1e12,
+                             "issued_frac": issued_per_step * a.steps / corr_s / 1e12 / peak,
+                             "issued_basis": "the split form's three 16-bit products, 3 x 512 flop x chunk per "
+                                             "(lag, chunk) row: tensor-pipe work, not algorithmic work"}
+                            if issued_per_step else {}),
                          "traffic": (contract_traffic(a.workload, a.contract, chunk_hi)
                                      if a.algo == "cdft" and roof_bound == "tensor" and not a.grid else None),
                          "kernel": roof_kernel,
                          "peak_basis": (PEAK_BASIS_TENSOR if roof_bound == "tensor" else
                                         "measured HBM copy (MEASURED_PEAKS.json hbm_gbs)" if roof_bound == "hbm"
-                                        else "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"),
+                                        else "measured FP32 FMA peak (dg_fp32_peak, see device.fp32_peak)"),
                          "achieved_basis": roof_basis + " / CUDA-event time of the launches",
                          "launches": corr_launches, "ms_per_launch": 1e3 * corr_s / max(1, corr_launches)},
             "kernel_ms_per_step": {n: v[0] / a.steps for n, v in kt.items() if v[1]},
             "cdft_work": ({"lag_chunk_rows": bucket_chunks, "candidate_superchunks": cand_chunks}
                           if a.algo == "cdft" else None),
             "kernels": kernels,
+            "device": {"name": torch.cuda.get_device_name(dev), "sm_count": fp["sm_count"],
+                       "fp32_peak": fp},
             "clocks": clocks,
             "fix": {"i": gi, "j": gj, "emitter_cell": list(centre),
                     "offset_cells": [gi - centre[0], gj - centre[1]],
@@ -523,16 +577,25 @@ def run_dg(a, rank, world, local_rank):
             "wall_s": t_wall,
         }
         if world == 1 and a.algo == "cdft" and not a.no_direct:
-            line["direct_path"] = direct_reference(scene, local_rank, stream)
+            line["direct_path"] = direct_reference(scene, local_rank, stream, alu_peak,
+                                                   grid=DIRECT_SUBGRID.get(a.workload))
         if world == 1 and not a.no_cpu_baseline:
             r, dt, npts, cores = oracle_rate(scene, a.cpu_baseline_s)
+            r1, dt1, npts1, _ = oracle_rate(scene, a.cpu_baseline_s / 3, seed=1, nthreads=1)
             line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                    "sample": f"{npts} random grid nodes x all {scene.k_steps} snapshots x {scene.n_samples} samples ({dt:.1f} s, FP64, OpenMP over nodes), {cpu_model()}"}
+                                    "sample": f"{npts} random grid nodes x all {scene.k_steps} snapshots x {scene.n_samples} samples ({dt:.1f} s, FP64, OpenMP over nodes), {cpu_model()}",
+                                    "one_thread": {"value": r1, "unit": UNIT, "cores": 1,
+                                                   "sample": f"{npts1} random grid nodes, same snapshots ({dt1:.1f} s)"}}
         print(json.dumps(line), flush=True)
     g.close()
 
 
-def direct_reference(scene, local_rank, stream, steps=3, warmup=1):
+# the direct path is timed on a sub-grid of workloads whose full grid would
+# take it tens of seconds per surface (same spacing and centre)
+DIRECT_SUBGRID = {"large": 1001}
+
+
+def direct_reference(scene, local_rank, stream, alu_peak, steps=3, warmup=1, grid=None):
     """The direct (sample-by-sample) evaluation of the same surface, timed
     the same way, for context: cand*samples/s and its FP32 roofline."""
     import torch
@@ -540,11 +603,12 @@ def direct_reference(scene, local_rank, stream, steps=3, warmup=1):
     import paper_2508_06672_gb300 as P
 
     dev = torch.device("cuda", local_rank)
-    g = P.Geolocator(scene.grid, scene.ephem, scene.fs_hz, scene.fc_hz, algo="direct", timing=True,
+    gd = dict(scene.grid, nlat=grid, nlon=grid) if grid else scene.grid
+    g = P.Geolocator(gd, scene.ephem, scene.fs_hz, scene.fc_hz, algo="direct", timing=True,
                      stream=stream, device=local_rank)
     with torch.cuda.stream(stream):
         g.load_captures(scene.fmt, torch.from_numpy(scene.y1).to(dev), torch.from_numpy(scene.y2).to(dev))
-        cost = torch.empty((scene.grid["nlat"], scene.grid["nlon"]), dtype=torch.float32, device=dev)
+        cost = torch.empty((gd["nlat"], gd["nlon"]), dtype=torch.float32, device=dev)
         for _ in range(warmup):
             g.cost_surface(cost)
     torch.cuda.synchronize(dev)
@@ -559,12 +623,13 @@ def direct_reference(scene, local_rank, stream, steps=3, warmup=1):
     ms = ev0.elapsed_time(ev1) / steps
     corr_ms, n = g.kernel_time(P.DG_K_CORR)
     g.close()
-    units = scene.G * scene.k_steps * scene.n_samples
+    units = gd["nlat"] * gd["nlon"] * scene.k_steps * scene.n_samples
     ach = FLOPS_PER_CAND_SAMPLE * units * steps / (corr_ms / 1e3) / 1e12
-    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     return {"value": units / (ms / 1e3), "unit": UNIT, "ms_per_surface": ms,
-            "roofline": {"bound": "alu", "kernel": "k_corr_direct", "achieved": ach, "peak": peak,
-                         "unit": "TFLOP/s", "frac": ach / peak}}
+            "grid": f"{gd['nlat']}x{gd['nlon']}" + (" sub-grid (same spacing and centre)" if grid else ""),
+            "roofline": {"bound": "alu", "kernel": "k_corr_direct", "achieved": ach, "peak": alu_peak,
+                         "unit": "TFLOP/s", "frac": ach / alu_peak,
+                         "peak_basis": "measured FP32 FMA peak (dg_fp32_peak)"}}
 
 
 # ------------------------------------------------------- many uneven captures
@@ -666,13 +731,14 @@ def run_batch(a, rank, world, local_rank):
     nprod = 3 if a.contract.endswith("x3") else 1
     step_s = statistics.median(dev_ms) / 1e3
     # issued tensor flops: 512 x chunk per (lag, chunk) row of every context
-    flops = sum(nprod * 512 * g.cdft_work()[0] * g.cdft_chunks()[1] for g in gs) if a.contract != "fp32" else 0
+    # algorithmic contraction flops: 512 x chunk per (lag, chunk) row of every context
+    flops = sum(512 * g.cdft_work()[0] * g.cdft_chunks()[1] for g in gs) if a.contract != "fp32" else 0
     clocks = clk.summary()
     if rank == 0:
         line = {
             "metric": METRIC, "value": units / step_s, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": CONTRACT_DTYPE[a.contract], "data": "synthetic",
             "config": {"workload": f"batch: {len(scenes)} uneven captures (K 5-100, N 2^12-2^18, grids 256-2048^2 "
                                    f"at 50-500 m, tone/chirp/noise, ci16, fs 12.5 MHz), one CUDA graph per step",
                        "captures": len(scenes), "cand_samples_per_step": units, "algo": "cdft",
@@ -684,8 +750,9 @@ def run_batch(a, rank, world, local_rank):
             "gpu_launches": batch.launch_count() * a.steps,
             "roofline": {"bound": "tensor", "achieved": flops / step_s / 1e12, "peak": tensor_peak(a.contract),
                          "unit": "TFLOP/s", "frac": flops / step_s / 1e12 / tensor_peak(a.contract),
+                         "issued_frac": nprod * flops / step_s / 1e12 / tensor_peak(a.contract),
                          "traffic": None,
-                         "kernel": "k_cdft_contract_tc (issued tensor flops over the whole step: a lower bound)",
+                         "kernel": "k_cdft_contract_tc (algorithmic contraction flops over the whole step: a lower bound)",
                          "peak_basis": PEAK_BASIS_TENSOR},
             "sequential": {"ms_per_step": statistics.median(seq_ms),
                            "value": units / (statistics.median(seq_ms) / 1e3),
@@ -700,7 +767,24 @@ def run_batch(a, rank, world, local_rank):
 
 
 LEARNED_WEIGHTS = os.path.join(ROOT, "paper_2508_06672_gb300", "weights", "proposal_2000km.npz")
-LEARNED_SEEDS = [5] + list(range(300000, 300015))   # held out: training used seeds 1000..
+LEARNED_SEEDS = [5] + list(range(300000, 300199))   # held out: training used seeds 1000..
+
+
+def _learned_scene(seed):
+    import sim
+
+    return sim.learned(seed)
+
+
+def learned_scenes(seeds):
+    """The held-out learned-workload scenes, simulated by a spawned process
+    pool (before any GPU work)."""
+    import multiprocessing as mp
+
+    if len(seeds) <= 2:
+        return [_learned_scene(sd) for sd in seeds]
+    with mp.get_context("spawn").Pool(max(1, min(16, (os.cpu_count() or 2) - 1))) as pool:
+        return pool.map(_learned_scene, seeds, chunksize=1)
 
 
 def run_learned(a, rank, world, local_rank):
@@ -709,15 +793,15 @@ def run_learned(a, rank, world, local_rank):
     the same resident captures, CUDA events on the shared stream."""
     import torch
 
+    n_sc = max(1, min(len(LEARNED_SEEDS), a.steps))
+    scenes = learned_scenes(LEARNED_SEEDS[:n_sc])
+
     import paper_2508_06672_gb300 as P
-    import sim
     from paper_2508_06672_gb300 import learned as L
     from paper_2508_06672_gb300.proposal import ProposalNet
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    n_sc = max(1, min(len(LEARNED_SEEDS), a.steps))
-    scenes = [sim.learned(sd) for sd in LEARNED_SEEDS[:n_sc]]
     net = ProposalNet.load(LEARNED_WEIGHTS, device=dev)
     st = torch.cuda.Stream(dev)
     s0 = scenes[0]
@@ -741,7 +825,7 @@ def run_learned(a, rank, world, local_rank):
         judge.argmax_refine(cost, 25.0, 500.0)
         search.search()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    learned_ms, full_ms, rec, rec_sum, err_l, err_f, same = [], [], [], [], [], [], []
+    learned_ms, full_ms, rec, rec_sum, err_l, err_f, same, fell = [], [], [], [], [], [], [], []
     l0 = search.geo.launch_count() + search.hm.launch_count()
     nn_launches = 2 * len(net.params) - 1
     clk = ClockSampler(_smi_id(local_rank))
@@ -763,6 +847,7 @@ def run_learned(a, rank, world, local_rank):
             e_mid.record(st)
             lf, _, peaks = search.search()
             ev[2].record(st)
+            fell.append(search.fell_back)
             torch.cuda.synchronize(dev)
             full_ms.append(ev[0].elapsed_time(ev[1]))
             learned_ms.append(e_mid.elapsed_time(ev[2]))
@@ -783,7 +868,7 @@ def run_learned(a, rank, world, local_rank):
             same.append(L.distance_m(lf["refined_lat_deg"], lf["refined_lon_deg"], jf["refined_lat_deg"],
                                      jf["refined_lon_deg"]) < 100.0)
             if i < n_sc:
-                _, _, speaks = search.search(sumnet)
+                _, _, speaks = search.search(sumnet, fallback=False)
                 rec_sum.append(covered(speaks))
     launches = search.geo.launch_count() + search.hm.launch_count() - l0
     launches_per_search = launches / (a.steps + len(rec_sum)) + nn_launches
@@ -810,7 +895,8 @@ def run_learned(a, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     fwd_ms = e0.elapsed_time(e1) / 20
     fwd_flops = sum(2 * 9 * w.shape[0] * w.shape[1] * search.cells * search.cells for w, _ in net.params)
-    fp32_peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    fp = fp32_peak(local_rank, st)
+    alu_peak = fp["tflops"]
     clocks = clk.summary()
     if rank == 0:
         med_l, med_f = statistics.median(learned_ms), statistics.median(full_ms)
@@ -826,6 +912,12 @@ def run_learned(a, rank, world, local_rank):
                        "scenes": n_sc, "seeds": LEARNED_SEEDS[:n_sc], "weights": os.path.relpath(LEARNED_WEIGHTS, ROOT),
                        "l2": "flushed before each timed search (256 MB write outside the events)"},
             "full_grid_ms": med_f, "speedup_vs_full_grid": med_f / med_l,
+            "mean_ms": float(np.mean(learned_ms)), "full_grid_mean_ms": float(np.mean(full_ms)),
+            "fallback": {"rule": f"no region proposed, or the best region's argmax within {search.edge} nodes "
+                                 "of its border: the full-grid search runs on the same context",
+                         "rate": float(np.mean(fell)), "count": int(sum(fell)),
+                         "median_ms_when_taken": (float(np.median([t for t, f in zip(learned_ms, fell) if f]))
+                                                  if any(fell) else None)},
             "recall": float(np.mean(rec)), "recall_coarse_sum_without_network": float(np.mean(rec_sum)),
             "same_fix_as_full_grid": float(np.mean(same)),
             "error_m": {"learned_p50": float(np.median(err_l)), "learned_p90": float(np.percentile(err_l, 90)),
@@ -833,10 +925,11 @@ def run_learned(a, rank, world, local_rank):
             "e2e": {"value": statistics.median(e2e), "unit": "ms", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": 100},
             "gpu_launches": int(round(launches_per_search * a.steps)),
-            "roofline": {"bound": "alu", "achieved": fwd_flops / (fwd_ms / 1e3) / 1e12, "peak": fp32_peak,
-                         "unit": "TFLOP/s", "frac": fwd_flops / (fwd_ms / 1e3) / 1e12 / fp32_peak, "traffic": None,
+            "roofline": {"bound": "alu", "achieved": fwd_flops / (fwd_ms / 1e3) / 1e12, "peak": alu_peak,
+                         "unit": "TFLOP/s", "frac": fwd_flops / (fwd_ms / 1e3) / 1e12 / alu_peak, "traffic": None,
                          "kernel": "k_conv3x3_tiled (the network's forward on the 512^2 maps, timed alone)",
-                         "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"},
+                         "peak_basis": "measured FP32 FMA peak (dg_fp32_peak, see device.fp32_peak)"},
+            "device": {"name": torch.cuda.get_device_name(dev), "sm_count": fp["sm_count"], "fp32_peak": fp},
             "cpu_baseline": None,
             "clocks": clocks,
         }
@@ -860,7 +953,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["dg", "reference"], default="dg")
-    ap.add_argument("--workload", choices=["mid", "tiny", "large", "batch", "learned"], default="mid")
+    ap.add_argument("--workload", choices=["large", "mid", "tiny", "batch", "learned"], default="large")
     ap.add_argument("--algo", choices=["direct", "cdft"], default="cdft")
     ap.add_argument("--chunk", type=int, default=0, help="CDFT samples per chunk; 0 = automatic")
     ap.add_argument("--contract", choices=["fp32", "bf16", "fp16", "bf16x3", "fp16x3"], default="fp16x3")

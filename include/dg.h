@@ -265,8 +265,12 @@ typedef struct {
  * plateau gives one peak. relative = 1 reads threshold as a fraction of the
  * surface maximum. Peaks are ordered by value (descending, ties by index);
  * at most max_peaks (<= 2048) are written to out (host, max_peaks entries) and
- * their number to *n_out. 0 <= radius <= 64. DG_EUNSUPPORTED if more than
- * 2048 nodes pass the test (raise the threshold). Synchronises the stream. */
+ * their number to *n_out. 0 <= radius <= 64. When more than 2048 peaks pass
+ * the test, the threshold is raised on the host to the max_peaks-th value of
+ * the 2048 the device kept and the test repeated (at most 8 times): the
+ * max_peaks largest peaks always pass it, so the result is the same.
+ * DG_EUNSUPPORTED only if more than 2048 peaks share the value at which that
+ * stops (raise the threshold). Synchronises the stream. */
 dg_status dg_detect(dg_ctx *ctx, const void *cost, double threshold, int32_t relative, int32_t radius,
                     int32_t max_peaks, dg_peak *out, int32_t *n_out);
 
@@ -380,6 +384,17 @@ int64_t dg_launch_count(const dg_ctx *ctx);
 
 /* DG_ABI_VERSION of the loaded library. */
 int32_t dg_abi_version(void);
+
+/* Measured FP32 peak of the current device (not in the paper: the ceiling the
+ * CUDA-core kernels' rooflines are stated against). One kernel fills every SM
+ * with 2048 resident threads, each running 8 independent chains of `iters` x 16
+ * fused multiply-adds; *tflops = 2 x FMAs / the launch's CUDA-event time, after
+ * one shorter warm-up launch. Runs on cuda_stream (NULL: legacy default) and
+ * synchronises it; allocates and frees a few bytes stream-ordered. *ms (launch
+ * time) and *sm_count (the device's multiprocessor count) may be NULL.
+ * DG_EINVAL for iters <= 0 or tflops NULL; DG_ECUDA / DG_ENOMEM on a CUDA
+ * failure. */
+dg_status dg_fp32_peak(void *cuda_stream, int32_t iters, double *tflops, double *ms, int32_t *sm_count);
 
 /* --- coarse delay-Doppler maps on the footprint ---------------------------
  * Not in the paper as such: the input of the learned proposal. For each

@@ -23,7 +23,7 @@ __all__ = [
     "Batch",
     "dg_options_default", "dg_create", "dg_load_capture", "dg_cost_surface", "dg_argmax_refine",
     "dg_sync", "dg_destroy", "dg_last_error", "dg_grid_ecef", "dg_step_geometry", "dg_kernel_time",
-    "dg_reset_counters", "dg_launch_count", "dg_abi_version", "Geolocator",
+    "dg_reset_counters", "dg_launch_count", "dg_abi_version", "dg_fp32_peak", "Geolocator",
     "dg_cost_surface_noalloc", "dg_noalloc_last_error", "DG_NOALLOC_SCRATCH_BYTES", "dg_cdft_work",
     "DG_OK", "DG_EINVAL", "DG_ENOMEM", "DG_ECUDA", "DG_ESTATE", "DG_ETIMEOUT", "DG_EUNSUPPORTED",
     "DG_IQ_C64", "DG_IQ_CI16", "DG_IQ_CI8", "DG_DELAY_INTEGER", "DG_DELAY_LAGRANGE4",
@@ -65,7 +65,7 @@ EXPORTED_SYMBOLS = [
     "dg_batch_fixes", "dg_batch_launch_count", "dg_batch_destroy", "dg_autotune",
     "dg_nn_conv3x3_forward", "dg_nn_conv3x3_backward", "dg_nn_conv3x3_scratch", "dg_nn_relu_forward",
     "dg_nn_relu_backward", "dg_nn_bce_scratch", "dg_nn_bce_logits", "dg_nn_adam", "dg_nn_last_error",
-    "dg_coarse_maps", "dg_coarse_inspect", "dg_set_grid", "dg_search_regions",
+    "dg_coarse_maps", "dg_coarse_inspect", "dg_set_grid", "dg_search_regions", "dg_fp32_peak",
 ]
 DG_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
@@ -171,6 +171,7 @@ def lib():
             L.dg_launch_count.restype = i64
             L.dg_abi_version.argtypes = []
             L.dg_abi_version.restype = i32
+            L.dg_fp32_peak.argtypes = [vp, i32, C.POINTER(dbl), C.POINTER(dbl), C.POINTER(i32)]
             L.dg_cost_surface_noalloc.argtypes = [C.POINTER(dg_grid), C.POINTER(dg_ephem), i32, dbl, dbl,
                                                   i32, vp, vp, i64, C.POINTER(dg_options), vp, vp]
             L.dg_cost_surface_noalloc.restype = C.c_int
@@ -371,6 +372,16 @@ def dg_launch_count(ctx):
 
 def dg_abi_version():
     return int(lib().dg_abi_version())
+
+
+def dg_fp32_peak(iters=50000, stream=0):
+    """Measured FP32 FMA throughput of the current device (see include/dg.h):
+    returns (TFLOP/s, launch ms, SM count)."""
+    tf, ms, sms = C.c_double(), C.c_double(), C.c_int32()
+    st = lib().dg_fp32_peak(C.c_void_p(int(stream)), int(iters), C.byref(tf), C.byref(ms), C.byref(sms))
+    if st != DG_OK:
+        raise DGError(st, "dg_fp32_peak failed")
+    return tf.value, ms.value, sms.value
 
 
 def dg_noalloc_last_error():

@@ -31,7 +31,7 @@ def test_reference_arm_prints_one_contract_line():
     assert d["metric"] == "candidate·sample correlations/s" and d["unit"] == "cand·samples/s"
     assert d["higher_is_better"] is True and d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 3
     assert d["value"] > 0 and d["ms_per_step"] > 0
-    assert d["config"]["workload"].startswith("mid: 1001x1001")
+    assert d["config"]["workload"].startswith("large: 4001x4001")
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     e2e = d["e2e"]
@@ -70,11 +70,17 @@ def test_clock_summary_reads_the_sampled_lines():
 
 
 def test_contraction_traffic_only_for_the_source_it_was_measured_on(tmp_path, monkeypatch):
+    import hashlib
+
     b = _bench()
-    t = b.CONTRACT_TRAFFIC
+    src = os.path.join(ROOT, "paper_2508_06672_gb300", "csrc", "dg_cdft_mma.cu")
+    with open(src, "rb") as f:
+        sha = hashlib.sha1(f.read()).hexdigest()[:16]
+    t = {"source_sha1_16": sha, "workload": "large", "contract": "fp16x3", "chunk": 1024, "bytes_per_launch": 1.5e9}
+    monkeypatch.setattr(b, "CONTRACT_TRAFFIC", [t])
     assert b.contract_traffic(t["workload"], t["contract"], t["chunk"]) == t["bytes_per_launch"]
     assert b.contract_traffic(t["workload"], "bf16", t["chunk"]) is None
-    assert b.contract_traffic("large", t["contract"], t["chunk"]) is None
+    assert b.contract_traffic("tiny", t["contract"], t["chunk"]) is None
     assert b.contract_traffic(t["workload"], t["contract"], 256) is None
     # another kernel source: no traffic figure
     src = tmp_path / "paper_2508_06672_gb300" / "csrc"
@@ -82,6 +88,9 @@ def test_contraction_traffic_only_for_the_source_it_was_measured_on(tmp_path, mo
     (src / "dg_cdft_mma.cu").write_text("// a changed kernel\n")
     monkeypatch.setattr(b, "ROOT", str(tmp_path))
     assert b.contract_traffic(t["workload"], t["contract"], t["chunk"]) is None
+    # every recorded figure names a workload, a form and a chunk
+    for e in _bench().CONTRACT_TRAFFIC:
+        assert set(e) == {"source_sha1_16", "workload", "contract", "chunk", "bytes_per_launch"}
 
 
 def test_reference_arm_under_torchrun_prints_on_rank_0_only():
