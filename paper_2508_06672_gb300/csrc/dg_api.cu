@@ -1129,20 +1129,30 @@ dg_status dg_detect(dg_ctx *c, const void *cost, double threshold, int32_t relat
         CK(c, cudaMallocAsync((void **)&c->det_cand, sizeof(int64_t) * kCap, c->stream));
         CK(c, cudaMallocAsync((void **)&c->det_out, sizeof(DetectPeak) * kCap, c->stream));
     }
-    {
-        Timed t(c, DG_K_ARGMAX);
-        CK(c, launch_detect(cost, c->opt.prec, c->gd, thr, radius, kCap, max_peaks, c->det_count, c->det_cand,
-                            c->det_out, c->stream));
-        t.done(2);
-    }
     int count = 0;
     std::vector<DetectPeak> pk((size_t)max_peaks);
-    CK(c, cudaMemcpyAsync(&count, c->det_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CK(c, cudaMemcpyAsync(pk.data(), c->det_out, sizeof(DetectPeak) * (size_t)max_peaks, cudaMemcpyDeviceToHost,
-                          c->stream));
-    CK(c, cudaStreamSynchronize(c->stream));
-    if (count > kCap)
-        return fail(c, DG_EUNSUPPORTED, "%d nodes pass the detection test (max %d); raise the threshold", count, kCap);
+    for (int round = 0;; ++round) {
+        {
+            Timed t(c, DG_K_ARGMAX);
+            CK(c, launch_detect(cost, c->opt.prec, c->gd, thr, radius, kCap, max_peaks, c->det_count, c->det_cand,
+                                c->det_out, c->stream));
+            t.done(2);
+        }
+        CK(c, cudaMemcpyAsync(&count, c->det_count, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaMemcpyAsync(pk.data(), c->det_out, sizeof(DetectPeak) * (size_t)max_peaks, cudaMemcpyDeviceToHost,
+                              c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        if (count <= kCap) break;
+        // More peaks pass than the sort holds: it ordered kCap of them (an
+        // arbitrary subset), so at least max_peaks peaks reach its
+        // max_peaks-th value, and so does every one of the max_peaks largest.
+        // That value is the next threshold; far fewer peaks pass it.
+        const double next = pk[(size_t)max_peaks - 1].value;
+        if (!(next > thr) || round >= 8)
+            return fail(c, DG_EUNSUPPORTED, "%d peaks of equal value pass the detection test (max %d); raise the "
+                        "threshold", count, kCap);
+        thr = next;
+    }
     const int n = std::min(count, (int)max_peaks);
     for (int k = 0; k < n; ++k) {
         out[k].index = pk[k].index;

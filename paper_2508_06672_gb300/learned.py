@@ -14,7 +14,11 @@ dense re-evaluation around the argmax) is replaced by:
    within a square of side ``region_m``, its argmax and the same dense
    re-evaluation as the full search (dg_set_grid, dg_search_regions on one
    context that keeps the captures);
-5. the region whose argmax holds the largest cost gives the fix.
+5. the region whose argmax holds the largest cost gives the fix;
+6. the full-grid search on the same context is the fallback: it runs when
+   no region is proposed, or when the winning region's argmax lies within
+   ``edge`` nodes of the region's border (the surface still rises towards
+   the border, so the maximum may lie outside every region).
 
 The method without the network ranks the cells by the sum of the K coarse
 maps instead (the non-coherent sum of Algorithm 1 applied to the coarse
@@ -88,7 +92,7 @@ class LearnedSearch:
 
     def __init__(self, grid, ephem, fs_hz, fc_hz, net, *, cells=512, regions=8, region_m=50e3,
                  refine_spacing_m=25.0, refine_window_m=500.0, bins=0, chunk=0, algo="cdft",
-                 contract="bf16x3", stream=None):
+                 contract="bf16x3", stream=None, edge=2):
         import torch
         self.torch = torch
         self.grid = dict(grid)
@@ -108,6 +112,11 @@ class LearnedSearch:
         self.hm = dg.Geolocator(self.centre_grid, eph, fs_hz, fc_hz, stream=self.geo.stream)
         self.maps = torch.empty((self.K, self.cells, self.cells), dtype=torch.float32, device=self.geo.device)
         self.cost = None
+        self.full_cost = None
+        self.edge = int(edge)
+        self.searches = 0     # search() calls, and how many of them fell back to the full grid
+        self.fallbacks = 0
+        self.fell_back = False
 
     def load_captures(self, fmt, y1, y2):
         self.geo.load_captures(fmt, y1, y2)
@@ -125,14 +134,8 @@ class LearnedSearch:
     def proposals(self, net=None):
         """The top cells as dg_peak dicts (lat_deg, lon_deg, value, i, j)."""
         logits = self.heatmap(net).view(self.cells, self.cells)
-        try:
-            return self.hm.detect(logits, -3.0e38, relative=False, radius=self.radius, max_peaks=self.regions)
-        except dg.DGError as e:
-            if "status 6" not in str(e):
-                raise
-            # more local maxima than dg_detect holds: keep the 2048 largest values
-            v = np.sort(logits.float().cpu().numpy().ravel())[-2048]
-            return self.hm.detect(logits, float(v), relative=False, radius=self.radius, max_peaks=self.regions)
+        # dg_detect returns the largest local maxima however many there are
+        return self.hm.detect(logits, -3.0e38, relative=False, radius=self.radius, max_peaks=self.regions)
 
     def region_grid(self, lat_deg, lon_deg):
         """The region around a point: the nodes of the full search's grid
@@ -153,17 +156,43 @@ class LearnedSearch:
         n = 2 * self.half + 1
         return dict(lat0_deg=lat, lon0_deg=lon, dlat_m=step_lat / dlat, dlon_m=step_lon / dlon, nlat=n, nlon=n)
 
-    def search(self, net=None):
-        """(fix, index of the region it came from, proposals)."""
-        peaks = self.proposals(net)
-        if not peaks:
-            return None, -1, peaks
+    def doubtful(self, fix):
+        """True when a region's fix cannot be trusted: its argmax lies within
+        ``edge`` nodes of the region's border."""
         n = 2 * self.half + 1
-        if self.cost is None:
-            self.cost = self.torch.empty((self.regions, n, n), dtype=self.torch.float32, device=self.geo.device)
-        regions = [self.region_grid(p["lat_deg"], p["lon_deg"]) for p in peaks]
-        fix, best, _ = self.geo.search_regions(regions, *self.refine, costs=self.cost)
-        return fix, best, peaks
+        return min(fix["i"], fix["j"], n - 1 - fix["i"], n - 1 - fix["j"]) < self.edge
+
+    def full_search(self):
+        """The full-grid search (Algorithm 1 on every node, then the same
+        dense re-evaluation) on the same context and captures."""
+        self.geo.set_grid(self.grid)
+        if self.full_cost is None:
+            self.full_cost = self.torch.empty((int(self.grid["nlat"]), int(self.grid["nlon"])),
+                                              dtype=self.torch.float32, device=self.geo.device)
+        self.geo.cost_surface(out=self.full_cost)
+        return self.geo.argmax_refine(self.full_cost, *self.refine)
+
+    def search(self, net=None, fallback=True):
+        """(fix, index of the region it came from, proposals). With fallback,
+        a search that proposes no region or whose fix is doubtful runs the
+        full-grid search instead: its fix is returned with index -1 and
+        ``fell_back`` is set. Without it, no proposal gives (None, -1, [])."""
+        self.searches += 1
+        self.fell_back = False
+        peaks = self.proposals(net)
+        if peaks:
+            n = 2 * self.half + 1
+            if self.cost is None:
+                self.cost = self.torch.empty((self.regions, n, n), dtype=self.torch.float32, device=self.geo.device)
+            regions = [self.region_grid(p["lat_deg"], p["lon_deg"]) for p in peaks]
+            fix, best, _ = self.geo.search_regions(regions, *self.refine, costs=self.cost)
+            if not fallback or not self.doubtful(fix):
+                return fix, best, peaks
+        elif not fallback:
+            return None, -1, peaks
+        self.fallbacks += 1
+        self.fell_back = True
+        return self.full_search(), -1, peaks
 
     def close(self):
         self.geo.close()

@@ -106,9 +106,9 @@ def evaluate(net, args, scenes, first):
         judge.cost_surface(out=cost)
         jf = judge.argmax_refine(cost, search.refine[0], search.refine[1])
         ev[1].record(search.geo.stream)
-        best, _, peaks = search.search(net)
+        best, _, peaks = search.search(net, fallback=False)   # the proposals alone
         ev[2].record(search.geo.stream)
-        sbest, _, speaks = search.search(sumnet)
+        sbest, _, speaks = search.search(sumnet, fallback=False)
         ev[3].record(search.geo.stream)
         torch.cuda.synchronize()
         jn = (jf["i"], jf["j"])

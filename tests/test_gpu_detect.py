@@ -87,7 +87,7 @@ def test_detect_errors():
     with pytest.raises(P.DGError):
         g.detect(v, float("nan"))
     with pytest.raises(P.DGError):
-        g.detect(v, -1.0, radius=0)  # 2500 nodes pass: more than the 2048 the sort holds
+        g.detect(v, -1.0, radius=0)  # 2500 equal peaks: more than the sort holds at any threshold
     # nothing above the threshold: an empty list, not an error
     assert g.detect(v, 1.0, radius=2) == []
     nan = _dev(g, np.full((50, 50), np.nan))
@@ -132,4 +132,24 @@ def test_detect_crowded_scene(crowded, crowded_oracle, opts):
     exact = g.detect(_dev(g, ref), 0.5 * float(np.float32(ref.max())), radius=3)
     assert [p["index"] for p in exact] == list(oracle.detect(ref.astype(np.float32).astype(np.float64),
                                                              0.5 * float(np.float32(ref.max())), 3))
+    g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("max_peaks", [1, 8, 300])
+def test_detect_more_peaks_than_the_sort_holds(prec, max_peaks):
+    """A noisy surface with ~10k local maxima (more than the 2048 the device
+    sort holds) and a wide plateau above most of them: the threshold is
+    raised until the sort holds every peak that passes, and the result is
+    the oracle's, index for index."""
+    rng = np.random.default_rng(11 + max_peaks)
+    v = rng.uniform(0.0, 1.0, size=(300, 301))
+    v[100:160, 50:200] = 0.9995          # one plateau: one peak, its lowest index
+    v[20, 20] = 2.0
+    v = _as_ctx_precision(v, prec)
+    g, _ = _ctx(v.shape, prec)
+    want = oracle.detect(v, -1.0, 1, max_peaks=max_peaks)
+    assert len(oracle.detect(v, -1.0, 1, max_peaks=20000)) > 2048
+    got = g.detect(_dev(g, v), -1.0, radius=1, max_peaks=max_peaks)
+    assert [p["index"] for p in got] == list(want) and len(got) == max_peaks
     g.close()

@@ -15,7 +15,9 @@ Recall is the fraction of scenes whose full-grid argmax lies inside one of the
 proposed regions. The regions are made of the full grid's own nodes, so where
 the full-grid argmax is covered the learned search returns the same fix. The
 network must lift recall well above the sum's, return the full-grid search's
-fix on all scenes but one, and take less time.
+fix on all scenes but one, and take less time. The learned search falls back
+to the full-grid search when its fix is doubtful (argmax at a region's
+border); how often that happens is printed and bounded.
 """
 import math
 import os
@@ -47,7 +49,7 @@ def test_trained_network_gains_over_the_coarse_sum():
                        stream=search.geo.stream)
     cost = torch.empty((first.grid["nlat"], first.grid["nlon"]), dtype=torch.float32, device="cuda")
     sumnet = L.SumNet(search.K)
-    rec_net, rec_sum, err_j, err_n, t_j, t_n, same = [], [], [], [], [], [], []
+    rec_net, rec_sum, err_j, err_n, t_j, t_n, same, fell = [], [], [], [], [], [], [], []
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     for seed in SEEDS:
         s = first if seed == SEEDS[0] else sim.learned(seed)
@@ -61,7 +63,8 @@ def test_trained_network_gains_over_the_coarse_sum():
         ev[1].record(search.geo.stream)
         nf, _, peaks = search.search(net)
         ev[2].record(search.geo.stream)
-        _, _, speaks = search.search(sumnet)
+        fell.append(search.fell_back)
+        _, _, speaks = search.search(sumnet, fallback=False)
         torch.cuda.synchronize()
 
         def covered(pk):
@@ -86,9 +89,11 @@ def test_trained_network_gains_over_the_coarse_sum():
     print(f"recall: network {sum(rec_net)}/{n}, coarse sum {sum(rec_sum)}/{n}; same fix {sum(same)}/{n}; "
           f"median error (m): full grid "
           f"{np.median(err_j):.0f}, learned {np.median(err_n):.0f}; median time (ms): full grid {np.median(t_j):.1f}, "
-          f"learned {np.median(t_n):.1f}")
+          f"learned {np.median(t_n):.1f} (fell back to the full grid on {sum(fell)}/{n}: "
+          f"{[round(t, 1) for t, f in zip(t_n, fell) if f]} ms)")
     assert sum(rec_net) >= n - 1
     assert sum(rec_net) >= sum(rec_sum) + 3
     assert sum(same) >= n - 1
     assert np.median(err_n) <= 1.25 * np.median(err_j) + 500.0
     assert np.median(t_n) < 0.6 * np.median(t_j)
+    assert sum(fell) <= n // 4
