@@ -34,7 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FLOPS_PER_CAND_SAMPLE = 14          # conj product 6 + derotation 6 + accumulation 2
-CDFT_COMBINE_FLOPS = 18             # per candidate x super-chunk: 3-bin interpolation 10 + phase MAC 8
+CDFT_COMBINE_FLOPS = 30             # per candidate x super-chunk: 6-bin interpolation 22 + phase MAC 8
 FP32_PROBE_ITERS = 50000           # ~50 ms per probe launch on a GB300
 METRIC = "candidate·sample correlations/s"
 UNIT = "cand·samples/s"
@@ -475,7 +475,7 @@ def run_dg(a, rank, world, local_rank):
                 ("combine", combine_units * (1e12 if combine_hbm else 1), "hbm" if combine_hbm else "alu",
                  hbm_peak() if combine_hbm else alu_peak,
                  ("12 B per candidate x snapshot + 1024 B per (lag, chunk) (super-chunk pass)" if combine_hbm else
-                  f"{CDFT_COMBINE_FLOPS} flop per candidate x super-chunk (3-bin interpolation 10 + phase MAC 8)"),
+                  f"{CDFT_COMBINE_FLOPS} flop per candidate x super-chunk (6-bin interpolation 22 + phase MAC 8)"),
                  "GB/s" if combine_hbm else "TFLOP/s")):
             ms, n = kt[name]
             if n:

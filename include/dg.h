@@ -70,8 +70,8 @@ enum { DG_PREC_FP32 = 0, DG_PREC_FP64 = 1 };
  * z_L[n] = y1[n] conj(y2[n + L]), so Eq. 11 becomes, per lag, a DFT of z_L
  * in chunks of `chunk` samples at `bins` Doppler frequencies spanning that
  * lag's FDOA range (a dense contraction), followed per candidate by a
- * quadratic interpolation between the three nearest bins and a sum over
- * chunks with the FDOA phase of each chunk's first sample. Its error against the definition is bounded by
+ * 6-point Lagrange interpolation between the bins around its FDOA and a sum
+ * over chunks with the FDOA phase of each chunk's first sample. Its error against the definition is bounded by
  * the bin interpolation and by the arithmetic of the contraction
  * (DG_CONTRACT_*). */
 enum { DG_ALGO_DIRECT = 0, DG_ALGO_CDFT = 1 };
@@ -91,10 +91,11 @@ enum { DG_ALGO_DIRECT = 0, DG_ALGO_CDFT = 1 };
  * DFT matrix, so it agrees with the others within the contraction's error.
  * On this chip HANKEL is slower than LAGS (its per-phase MMAs of N = 64
  * fetch more operand bytes per flop), so AUTO does not take it: AUTO takes
- * LAGS (chunk <= 1024) unless padding a snapshot's lags to whole blocks of 128
- * more than doubles its tile count, and ROWS then; when the last block of a
- * snapshot would hold fewer than 64 lags, AUTO puts those lags in ROWS tiles
- * and keeps LAGS tiles for the whole blocks. */
+ * LAGS (chunk <= 1024 or a multiple of 1024: a longer chunk is staged in
+ * windows of 1024 samples) unless padding a snapshot's lags to whole blocks
+ * of 128 more than doubles its tile count, and ROWS then; when the last block
+ * of a snapshot would hold fewer than 64 lags, AUTO puts those lags in ROWS
+ * tiles and keeps LAGS tiles for the whole blocks. */
 enum { DG_TILES_AUTO = 0, DG_TILES_ROWS = 1, DG_TILES_LAGS = 2, DG_TILES_HANKEL = 3 };
 
 /* Arithmetic of the CDFT contraction: FP32 on CUDA cores, or 16-bit
@@ -130,13 +131,18 @@ typedef struct {
     int32_t row0;    /* first grid row of this context's shard                */
     int32_t nrows;   /* rows in the shard; 0 = all rows from row0             */
     int32_t timing;  /* 1: time kernels with CUDA events (dg_kernel_time)     */
-    int32_t chunk;   /* CDFT: samples per chunk, a multiple of 64 in [64,4096];
-                        0 = chosen per batch of snapshots: the longest power
-                        of two <= 1024 whose length x bin spacing is <= 1.2e-2
-                        cycles in every snapshot of the batch
-                        (dg_cdft_chunks), at most 256 on the refinement grid
-                        of dg_argmax_refine (few lags: shorter chunks give
-                        the contraction more tiles)                           */
+    int32_t chunk;   /* CDFT: samples per chunk, a multiple of 64 in
+                        [64, 16384]; 0 = chosen per batch of snapshots: the
+                        longest power of two whose length x bin spacing is
+                        <= 5e-2 cycles in every snapshot of the batch, up to
+                        1024 (FP32 or Hankel contraction) or, on the tensor
+                        cores, up to 16384 while it fits every capture and
+                        the batch keeps 8 lag tiles per SM (dg_cdft_chunks);
+                        at most 256 on the refinement grid of
+                        dg_argmax_refine (few lags: shorter chunks give the
+                        contraction more tiles). DG_TILES_LAGS needs a chunk
+                        <= 1024 or a multiple of 1024, DG_TILES_HANKEL one
+                        <= 1024                                               */
     int32_t bins;    /* CDFT: Doppler bins per lag; 0 = 64 (the only value)   */
     int32_t contract;/* CDFT: DG_CONTRACT_*                                   */
     int32_t tiles;   /* CDFT tensor-core tile shape: DG_TILES_*               */
@@ -314,9 +320,10 @@ dg_status dg_batch_destroy(dg_batch *batch);
 
 /* Autotuning of the CDFT launch shape (no counterpart in the paper; it is
  * the successor of the paper's batch-size sweep, Sec. V-B). For every chunk
- * length in {256, 512, 1024} that the bin-spacing bound admits for this
- * grid and these snapshots, and for tensor-core contractions both tile
- * shapes (DG_TILES_ROWS, DG_TILES_LAGS, DG_TILES_HANKEL), it times dg_cost_surface into cost
+ * length 256 .. 1024 (tensor cores: .. 16384, within the shortest capture),
+ * in powers of two, that the bin-spacing bound admits for this grid and
+ * these snapshots, and for tensor-core contractions every tile shape that
+ * takes it (DG_TILES_ROWS, DG_TILES_LAGS, DG_TILES_HANKEL), it times dg_cost_surface into cost
  * (device, the context's precision; its contents are overwritten) with CUDA
  * events on the context's stream: one untimed run, then reps >= 1 timed runs,
  * keeping the median. The fastest shape is written into the context's
@@ -366,7 +373,7 @@ dg_status dg_kernel_time(dg_ctx *ctx, int32_t kernel_class, double *ms, int64_t 
  * summed over snapshots: lag-bucket x chunk pairs contracted (each a
  * chunk-by-bins complex DFT) and candidate x super-chunk pairs combined (the
  * combine merges chunks at the bin frequencies into the longest power-of-two
- * multiple of the chunk whose length x bin spacing stays <= 1.2e-2 cycles).
+ * multiple of the chunk whose length x bin spacing stays <= 4e-2 cycles).
  * Host pointers, may be NULL; zeros before the first CDFT surface. */
 dg_status dg_cdft_work(const dg_ctx *ctx, int64_t *bucket_chunks, int64_t *candidate_chunks);
 
@@ -384,6 +391,17 @@ int64_t dg_launch_count(const dg_ctx *ctx);
 
 /* DG_ABI_VERSION of the loaded library. */
 int32_t dg_abi_version(void);
+
+/* Test hook of the tensor-core pipeline's timeout (not in the paper). Every
+ * wait of the CDFT tensor-core contraction is bounded: it gives up after 2 s
+ * of the global timer or a poll limit, the kernel then stops issuing, lets
+ * the MMAs and copies it issued land, frees its tensor memory and returns,
+ * and the next synchronising call reports DG_ETIMEOUT (the surface values
+ * are not valid; the context stays usable). polls > 0 lowers the poll limit
+ * of those waits in every CDFT surface launched afterwards, in every context
+ * of the process, so that a test can make them run out; 0 restores the
+ * default. Not for production use. Always DG_OK. */
+dg_status dg_debug_tc_wait_limit(uint32_t polls);
 
 /* Measured FP32 peak of the current device (not in the paper: the ceiling the
  * CUDA-core kernels' rooflines are stated against). One kernel fills every SM

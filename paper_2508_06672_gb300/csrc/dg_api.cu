@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cstring>
 #include <map>
@@ -55,6 +56,7 @@ struct CdftBufs {  // chunked-DFT scratch, grown on demand
     int *lr = nullptr;
     CdftLayout main_layout, loc_layout;
     std::vector<double> main_span;  // FDOA span estimates per snapshot (main grid)
+    std::vector<double> main_lags;  // and lag-count estimates
     int *layout = nullptr, *Mcs = nullptr;
     unsigned long long *work = nullptr;
     unsigned *nur = nullptr;
@@ -235,7 +237,7 @@ dg_status check_latched(dg_ctx *c)
                         "kernels do not handle it");
         if (e & ERR_BIN_SPACING)
             return fail(c, DG_EUNSUPPORTED,
-                        "CDFT: a snapshot's FDOA span is too wide for its chunk (chunk x bin spacing > 1.2e-2 "
+                        "CDFT: a snapshot's FDOA span is too wide for its chunk (chunk x bin spacing > 4e-2 "
                         "cycles); use a shorter chunk or DIRECT");
         return fail(c, DG_EUNSUPPORTED, "a candidate's lag |D| exceeds 1e9 samples");
     }
@@ -273,6 +275,11 @@ dg_status push_steps(dg_ctx *c)
 
 // Correlation for all snapshots over grid gd (ECEF xyz) into surf [K][G],
 // then the ordered sum into out.
+// Poll limit of the tensor-core pipeline's waits in every CDFT surface
+// launched from now on (0 = the kernels' default); set by
+// dg_debug_tc_wait_limit, for tests of the timeout path.
+static std::atomic<unsigned> g_tc_wait_polls{0};
+
 dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int64_t G, void *surf, void *out,
                            bool refine);
 
@@ -406,7 +413,8 @@ static double grid_diameter(const GridDev &g)
 // to 65 x 65 nodes, fewer on small shards (at least 9 x 9, about one lattice
 // node per 8 grid nodes), the node positions computed once for all
 // snapshots.
-static void fdoa_spans(const dg_ctx *c, const GridDev &g, std::vector<double> &span)
+static void fdoa_spans(const dg_ctx *c, const GridDev &g, std::vector<double> &span,
+                       std::vector<double> *lags = nullptr)
 {
     const int side = std::max(g.nrows, g.nlon);
     const int lattice = std::min(65, std::max(9, side / 8 + 1));
@@ -419,27 +427,59 @@ static void fdoa_spans(const dg_ctx *c, const GridDev &g, std::vector<double> &s
             host_node_ecef(g, std::round(i), std::round(j), &p[3 * ((size_t)a * nj + b)]);
         }
     span.assign(c->K, 0.0);
+    if (lags) lags->assign(c->K, 1.0);
     for (int k = 0; k < c->K; ++k) {
-        double lo = 1e300, hi = -1e300;
+        double lo = 1e300, hi = -1e300, dlo = 1e300, dhi = -1e300;
+        const dg_ephem &e = c->eph_host[k];
         for (size_t q = 0; q < (size_t)ni * nj; ++q) {
-            const double nu = host_nu(&p[3 * q], c->eph_host[k], c->fs, c->lambda);
+            const double *x = &p[3 * q];
+            const double nu = host_nu(x, e, c->fs, c->lambda);
             lo = std::min(lo, nu);
             hi = std::max(hi, nu);
+            if (lags) {  // Eq. 7 and 9: the lattice's lag range
+                double r[2];
+                for (int t = 0; t < 2; ++t) {
+                    const double *pp = t ? e.p2 : e.p1;
+                    r[t] = std::sqrt((pp[0] - x[0]) * (pp[0] - x[0]) + (pp[1] - x[1]) * (pp[1] - x[1]) +
+                                     (pp[2] - x[2]) * (pp[2] - x[2]));
+                }
+                const double D = (r[1] - r[0]) * c->fs / kC;
+                dlo = std::min(dlo, D);
+                dhi = std::max(dhi, D);
+            }
         }
         span[k] = hi - lo;
+        if (lags) (*lags)[k] = std::floor(dhi + 0.5) - std::floor(dlo + 0.5) + 1.0;
     }
 }
 
 // Chunk of a batch with chunk = 0: the longest power of two in
-// [64, kCdftAutoMaxChunk] whose length times the estimated bin spacing stays
-// within kCdftMDelta / 1.25 (a margin for the lattice estimate; the plan
-// kernel checks the bound against the exact spacing).
-static int auto_chunk(const std::vector<double> &span, int k0, int S)
+// [64, kCdftAutoMaxChunk] (tensor cores: [64, kCdftAutoMaxChunkTc]) whose
+// length times the estimated bin spacing stays within kCdftMDelta / 1.1 (a
+// margin for the lattice estimate; the plan kernel checks the bound against
+// the exact spacing). On the tensor cores a chunk above kCdftAutoMaxChunk is
+// kept only while it fits every capture of the batch and the batch still
+// has kCdftMinTilesPerSm lag tiles (128 lags x one chunk, from the lattice's
+// lag counts) per SM: longer chunks mean fewer per-lag DFT rows to write and
+// to merge into super-chunks, but fewer and longer tiles.
+static int auto_chunk(const dg_ctx *c, const std::vector<double> &span, const std::vector<double> &lags, int k0,
+                      int S, bool tc)
 {
     double dmax = 0.0;
-    for (int s = 0; s < S; ++s) dmax = std::max(dmax, span[k0 + s] * (1.0 + 1e-5) / 63.0);
-    int M = kCdftAutoMaxChunk;
-    while (M > 64 && 1.25 * M * dmax > kCdftMDelta) M >>= 1;
+    int64_t nmin = INT64_MAX;
+    for (int s = 0; s < S; ++s) {
+        dmax = std::max(dmax, span[k0 + s] * (1.0 + 1e-5) / kCdftBinSpan);
+        nmin = std::min<int64_t>(nmin, c->steps[k0 + s].n);
+    }
+    int M = tc ? kCdftAutoMaxChunkTc : kCdftAutoMaxChunk;
+    while (M > 64 && 1.1 * M * dmax > kCdftMDelta) M >>= 1;
+    auto tiles = [&](int m) {
+        double t = 0.0;
+        for (int s = 0; s < S; ++s)
+            t += std::ceil((double)c->steps[k0 + s].n / m) * std::ceil(lags[k0 + s] / 128.0);
+        return t;
+    };
+    while (M > kCdftAutoMaxChunk && (M > nmin || tiles(M) < (double)kCdftMinTilesPerSm * c->sm_count)) M >>= 1;
     return M;
 }
 
@@ -550,12 +590,16 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
     // FDOA spans for the automatic chunk, from the main grid (a refinement
     // grid lies around one of its nodes and spans far less)
     std::vector<double> &span = b.main_span;
-    if (c->opt.chunk == 0 && span.size() != (size_t)c->K) fdoa_spans(c, c->gd, span);
+    const bool mma = c->opt.contract != DG_CONTRACT_FP32;
+    if (c->opt.chunk == 0 && (span.size() != (size_t)c->K || b.main_lags.size() != (size_t)c->K))
+        fdoa_spans(c, c->gd, span, &b.main_lags);
     std::vector<int> Ms(L.batches.size());
     int M_max = 64, B_max = 1;
     for (size_t i = 0; i < L.batches.size(); ++i) {
         const auto &t = L.batches[i];
-        Ms[i] = c->opt.chunk ? c->opt.chunk : auto_chunk(span, t.k0, t.S);
+        // Hankel tiles take chunks of at most kLagTileMaxChunk
+        const bool tc = mma && c->opt.tiles != DG_TILES_HANKEL;
+        Ms[i] = c->opt.chunk ? c->opt.chunk : auto_chunk(c, span, b.main_lags, t.k0, t.S, tc);
         if (refine && !c->opt.chunk) Ms[i] = std::min(Ms[i], kCdftRefineMaxChunk);
         M_max = std::max(M_max, Ms[i]);
         for (int s = 0; s < t.S; ++s) B_max = std::max<int>(B_max, (int)((c->steps[t.k0 + s].n + Ms[i] - 1) / Ms[i]));
@@ -583,7 +627,7 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         if ((st = grow(c, &b.nuS, (size_t)s_max * G)) != DG_OK) return st;
         b.sg_cap = (size_t)s_max * G;
     }
-    if (b.v_cap < (size_t)s_max * M_max * 64) {
+    if (!mma && b.v_cap < (size_t)s_max * M_max * 64) {  // the FP32 contraction's DFT table
         if ((st = grow(c, &b.V, (size_t)s_max * M_max * 64)) != DG_OK) return st;
         b.v_cap = (size_t)s_max * M_max * 64;
     }
@@ -606,7 +650,6 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         if ((st = grow(c, &b.g2b, (size_t)L.groups_max)) != DG_OK) return st;
         b.g2b_cap = (size_t)L.groups_max;
     }
-    const bool mma = c->opt.contract != DG_CONTRACT_FP32;
     if (mma) {
         const size_t bt = (size_t)s_max * cdft_btab_bytes(c->opt.contract, M_max);
         if (b.btab_cap < bt) {
@@ -695,6 +738,7 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         const int f = c->steps[k0].fmt;
         const bool fp16 = c->opt.contract == DG_CONTRACT_FP16 || c->opt.contract == DG_CONTRACT_FP16X3;
         a.zscale = (mma && fp16 && f == DG_IQ_CI16) ? 1.0f / 65536.0f : 1.0f;
+        a.wait_polls = g_tc_wait_polls.load(std::memory_order_relaxed);
         {
             Timed t(c, kplan);
             CK(c, launch_cdft_geo(a, c->stream));
@@ -845,15 +889,17 @@ dg_status dg_create(const dg_grid *grid, const dg_ephem *eph, int32_t K, double 
         if (o.delay != DG_DELAY_INTEGER)
             return fail(nullptr, DG_EUNSUPPORTED, "CDFT evaluates integer lags (Eq. 9) only");
         if (o.prec != DG_PREC_FP32) return fail(nullptr, DG_EUNSUPPORTED, "CDFT writes FP32 surfaces only");
-        if (o.chunk != 0 && (o.chunk < 64 || o.chunk > 4096 || o.chunk % 64 != 0))
-            return fail(nullptr, DG_EINVAL, "chunk must be 0 or a multiple of 64 in [64, 4096]");
+        if (o.chunk != 0 && (o.chunk < 64 || o.chunk > kCdftMaxChunk || o.chunk % 64 != 0))
+            return fail(nullptr, DG_EINVAL, "chunk must be 0 or a multiple of 64 in [64, %d]", kCdftMaxChunk);
         if (o.bins != 0 && o.bins != 64) return fail(nullptr, DG_EUNSUPPORTED, "bins must be 0 or 64");
         if (o.contract < DG_CONTRACT_FP32 || o.contract > DG_CONTRACT_FP16X3)
             return fail(nullptr, DG_EINVAL, "unknown contraction arithmetic %d", o.contract);
         if (o.tiles < DG_TILES_AUTO || o.tiles > DG_TILES_HANKEL)
             return fail(nullptr, DG_EINVAL, "unknown tile shape %d", o.tiles);
-        if ((o.tiles == DG_TILES_LAGS || o.tiles == DG_TILES_HANKEL) && o.chunk > kLagTileMaxChunk)
-            return fail(nullptr, DG_EINVAL, "lag and Hankel tiles need chunk <= %d", kLagTileMaxChunk);
+        if (o.tiles == DG_TILES_HANKEL && o.chunk > kLagTileMaxChunk)
+            return fail(nullptr, DG_EINVAL, "Hankel tiles need chunk <= %d", kLagTileMaxChunk);
+        if (o.tiles == DG_TILES_LAGS && o.chunk > kLagTileMaxChunk && o.chunk % kLagTileMaxChunk != 0)
+            return fail(nullptr, DG_EINVAL, "lag tiles need chunk <= %d or a multiple of it", kLagTileMaxChunk);
         if (o.scratch_mib < 0) return fail(nullptr, DG_EINVAL, "scratch_mib must be >= 0");
     }
     if (o.row0 < 0 || o.row0 >= grid->nlat) return fail(nullptr, DG_EINVAL, "row0 outside the grid");
@@ -936,7 +982,8 @@ dg_status dg_set_grid(dg_ctx *c, const dg_grid *grid)
     c->opt.nrows = 0;
     c->gd = make_griddev(*grid, 0, grid->nlat);
     c->G = G;
-    c->cd.main_span.clear();  // FDOA spans of the old grid
+    c->cd.main_span.clear();  // FDOA spans and lag counts of the old grid
+    c->cd.main_lags.clear();
     ++c->steps_gen;           // graphs and batches recorded on the old grid are stale
     {
         Timed t(c, DG_K_GRID);
@@ -1482,13 +1529,19 @@ dg_status dg_autotune(dg_ctx *c, void *cost, int32_t reps, dg_tuning *out)
     }
     // admissible chunks: the automatic rule's bound on the estimated spacing
     std::vector<double> &span = c->cd.main_span;
-    if (span.size() != (size_t)c->K) fdoa_spans(c, c->gd, span);
+    if (span.size() != (size_t)c->K || c->cd.main_lags.size() != (size_t)c->K)
+        fdoa_spans(c, c->gd, span, &c->cd.main_lags);
     double dmax = 0.0;
-    for (int k = 0; k < c->K; ++k) dmax = std::max(dmax, span[k] * (1.0 + 1e-5) / 63.0);
+    int64_t nmin = INT64_MAX;
+    for (int k = 0; k < c->K; ++k) {
+        dmax = std::max(dmax, span[k] * (1.0 + 1e-5) / kCdftBinSpan);
+        nmin = std::min<int64_t>(nmin, c->steps[k].n);
+    }
+    const bool tc = c->opt.contract != DG_CONTRACT_FP32;
     std::vector<int> chunks;
-    for (int m : {256, 512, 1024})
-        if (1.25 * m * dmax <= kCdftMDelta) chunks.push_back(m);
-    if (chunks.empty()) chunks.push_back(auto_chunk(span, 0, c->K));
+    for (int m = 256; m <= (tc ? kCdftAutoMaxChunkTc : kCdftAutoMaxChunk); m *= 2)
+        if (1.1 * m * dmax <= kCdftMDelta && (m <= kCdftAutoMaxChunk || m <= nmin)) chunks.push_back(m);
+    if (chunks.empty()) chunks.push_back(auto_chunk(c, span, c->cd.main_lags, 0, c->K, tc));
     std::vector<int> tiles = {DG_TILES_ROWS};
     if (c->opt.contract != DG_CONTRACT_FP32) {
         tiles.push_back(DG_TILES_LAGS);
@@ -1506,7 +1559,8 @@ dg_status dg_autotune(dg_ctx *c, void *cost, int32_t reps, dg_tuning *out)
     c->opt.timing = 0;  // restored with the saved options
     for (int m : chunks)
         for (int t : tiles) {
-            if ((t == DG_TILES_LAGS || t == DG_TILES_HANKEL) && m > kLagTileMaxChunk) continue;
+            if (t == DG_TILES_HANKEL && m > kLagTileMaxChunk) continue;
+            if (t == DG_TILES_LAGS && m > kLagTileMaxChunk && m % kLagTileMaxChunk != 0) continue;
             c->opt.chunk = m;
             c->opt.tiles = t;
             std::vector<float> ms;
@@ -1906,3 +1960,9 @@ dg_status dg_search_regions(dg_ctx *c, const dg_grid *regions, int32_t n, void *
 }
 
 }  // extern "C"
+
+extern "C" dg_status dg_debug_tc_wait_limit(uint32_t polls)
+{
+    g_tc_wait_polls.store(polls, std::memory_order_relaxed);
+    return DG_OK;
+}

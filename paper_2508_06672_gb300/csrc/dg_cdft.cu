@@ -9,12 +9,13 @@
 // W_b is smooth in nu (spectral width ~1/M) and the FDOAs of one snapshot
 // span a narrow band [nu_min, nu_max] (LEO geometry: < 2e-4 cycles/sample),
 // so W_b is evaluated once per (lag, chunk) on Q = 64 bins
-// nu_q = nu_min + q Delta, Delta = (nu_max - nu_min) / 63 -- a dense
-// [lag x chunk rows] x [M] x [64 bins] contraction whose DFT matrix
-// V[m][q] = e^{j 2 pi nu_q m} is shared by every row of the snapshot -- and
-// each candidate interpolates between the three bins around its own FDOA
-// (quadratic Lagrange). The interpolation error is at most about
-// 0.016 (2 pi M Delta)^3 of the coherent sum; the snapshot is rejected
+// nu_q = nu_min + (q - 2) Delta, Delta = (nu_max - nu_min) / 59 (two bins of
+// padding on each side) -- a dense [lag x chunk rows] x [M] x [64 bins]
+// contraction whose DFT matrix V[m][q] = e^{j 2 pi nu_q m} is shared by every
+// row of the snapshot -- and each candidate interpolates between the six
+// bins around its own FDOA (Lagrange, nodes q0 - 2 .. q0 + 3 with the FDOA
+// between q0 and q0 + 1). The interpolation error is at most about
+// 4.9e-3 (2 pi M Delta)^6 of the coherent sum; the snapshot is rejected
 // (DG_EUNSUPPORTED) if M * Delta > kCdftMDelta.
 //
 // All snapshots of a batch are processed by the same launches:
@@ -278,10 +279,11 @@ __global__ void __launch_bounds__(1024) k_cdft_scan(CdftBatch a)
     }
     if (t == 0) {
         const float lo = unfkey(a.nur[2 * s]), hi = unfkey(a.nur[2 * s + 1]);
-        // 64 bins over [lo, hi], a little wider so that rounding keeps every
-        // candidate strictly inside
-        const float d = fmaxf((hi - lo) * (1.0f + 1e-5f) / 63.0f, 1e-20f);
-        a.nubase[s] = lo;
+        // 64 bins: kCdftBinSpan steps over [lo, hi] (a little wider so that
+        // rounding keeps every candidate inside) and kCdftBinPad more on each
+        // side, so that every candidate's 6-point stencil is centred on it
+        const float d = fmaxf((hi - lo) * (1.0f + 1e-5f) / (float)kCdftBinSpan, 1e-20f);
+        a.nubase[s] = lo - (float)kCdftBinPad * d;
         a.delta[s] = d;
         if ((double)d * (double)a.M > kCdftMDelta) atomicOr(a.err, ERR_BIN_SPACING);
     }
@@ -492,9 +494,9 @@ __global__ void __launch_bounds__(256) k_cdft_superchunk(CdftBatch a, int NBT)
 // combine: kCdftCombineGroup candidates of one bucket per CTA,
 // kCdftCombinePer per thread; the bucket's super-chunk
 // DFTs stream through shared memory in segments of kSeg. Each candidate
-// interpolates the DFT of every super-chunk at its own FDOA from the three
-// nearest bins (quadratic Lagrange), rotates it by the super-chunk's phase
-// e^{j 2 pi nu c Mc}, and sums.
+// interpolates the DFT of every super-chunk at its own FDOA from the six
+// bins around it (Lagrange, the FDOA between the third and fourth),
+// rotates it by the super-chunk's phase e^{j 2 pi nu c Mc}, and sums.
 // ---------------------------------------------------------------------------
 constexpr int kSeg = 32;
 
@@ -524,23 +526,28 @@ __global__ void __launch_bounds__(kCdftCombineThreads) k_cdft_combine(CdftBatch 
     }
     const size_t sp0 = (size_t)s * a.G + gr.z;
     int c[kCdftCombinePer], q0[kCdftCombinePer];
-    float wm[kCdftCombinePer], w0[kCdftCombinePer], wp[kCdftCombinePer], ex[kCdftCombinePer],
-        ey[kCdftCombinePer], px[kCdftCombinePer], py[kCdftCombinePer], cx[kCdftCombinePer], cy[kCdftCombinePer],
-        nu[kCdftCombinePer];
+    float w[kCdftCombinePer][6], ex[kCdftCombinePer], ey[kCdftCombinePer], px[kCdftCombinePer],
+        py[kCdftCombinePer], cx[kCdftCombinePer], cy[kCdftCombinePer], nu[kCdftCombinePer];
 #pragma unroll
     for (int k = 0; k < kCdftCombinePer; ++k) {
         const int j = threadIdx.x + k * kCdftCombineThreads;
         const bool act = j < n;
         c[k] = act ? a.order[sp0 + j] : -1;
-        nu[k] = act ? a.nuS[sp0 + j] : nbase;
-        // quadratic (3-point Lagrange) interpolation on bins q0 - 1, q0, q0 + 1
-        // with q0 the nearest bin, kept in [1, 62]; t = offset from bin q0
+        nu[k] = act ? a.nuS[sp0 + j] : nbase + (float)kCdftBinPad * a.delta[s];
+        // 6-point Lagrange interpolation on bins q0 - 2 .. q0 + 3 with q0 the
+        // bin at or below the FDOA, kept in [2, 60] (the padding keeps the
+        // FDOA in [q0, q0 + 1]); t = offset from bin q0
         const float u = (nu[k] - nbase) * inv;
-        q0[k] = max(1, min(62, __float2int_rn(u)));
+        q0[k] = max(kCdftBinPad, min(62 - kCdftBinPad, __float2int_rd(u)));
         const float t = u - (float)q0[k];
-        wm[k] = 0.5f * t * (t - 1.f);
-        w0[k] = (1.f - t) * (1.f + t);
-        wp[k] = 0.5f * t * (t + 1.f);
+        const float a2 = t + 2.f, a1 = t + 1.f, b1 = t - 1.f, b2 = t - 2.f, b3 = t - 3.f;
+        const float t01 = t * b1, t23 = b2 * b3, s21 = a2 * a1;
+        w[k][0] = -(a1 * t01 * t23) * (1.f / 120.f);
+        w[k][1] = (a2 * t01 * t23) * (1.f / 24.f);
+        w[k][2] = -(s21 * b1 * t23) * (1.f / 12.f);
+        w[k][3] = (s21 * t * t23) * (1.f / 12.f);
+        w[k][4] = -(s21 * t01 * b3) * (1.f / 24.f);
+        w[k][5] = (s21 * t01 * b2) * (1.f / 120.f);
         // chunk-to-chunk phase step e^{j 2 pi nu M}
         sincospif(2.0f * frac_mul(nu[k], (float)M), &ey[k], &ex[k]);
         cx[k] = cy[k] = 0.f;
@@ -567,9 +574,14 @@ __global__ void __launch_bounds__(kCdftCombineThreads) k_cdft_combine(CdftBatch 
             }
 #pragma unroll 4
             for (int i = 0; i < slen; ++i) {
-                const float2 vm = ws[i][q0[k] - 1], v0 = ws[i][q0[k]], vp = ws[i][q0[k] + 1];
-                const float zx = fmaf(wm[k], vm.x, fmaf(w0[k], v0.x, wp[k] * vp.x));
-                const float zy = fmaf(wm[k], vm.y, fmaf(w0[k], v0.y, wp[k] * vp.y));
+                const float2 *wr = &ws[i][q0[k] - 2];
+                float zx = 0.f, zy = 0.f;
+#pragma unroll
+                for (int e = 0; e < 6; ++e) {
+                    const float2 v = wr[e];
+                    zx = fmaf(w[k][e], v.x, zx);
+                    zy = fmaf(w[k][e], v.y, zy);
+                }
                 cx[k] = fmaf(px[k], zx, fmaf(-py[k], zy, cx[k]));
                 cy[k] = fmaf(px[k], zy, fmaf(py[k], zx, cy[k]));
                 const float nx = fmaf(px[k], ex[k], -py[k] * ey[k]);
@@ -590,7 +602,7 @@ __global__ void __launch_bounds__(kCdftCombineThreads) k_cdft_combine(CdftBatch 
 // tiles: one warp, after the scan. Per snapshot of the batch: its lag
 // buckets (from the lag range), the tensor-core tile layout (128 lags x one
 // chunk unless padding the lags to blocks of 128 more than doubles the tile
-// count, or the chunk exceeds kLagTileMaxChunk), the tile offsets, and the
+// count, or a chunk above kLagTileMaxChunk is not a multiple of it), the tile offsets, and the
 // combine chunk: the longest power-of-two multiple of M with
 // Mc x bin spacing <= kCdftMDelta, up to the first length that covers the
 // snapshot and at most 2^24. Also the work counters.
@@ -624,13 +636,14 @@ __global__ void k_cdft_tiles(CdftBatch a)
             // empty block (3: mixed). Hankel tiles only on request (measured
             // slower: their per-phase MMAs of N = 64 re-read the 128-row operand
             // eight times per K step)
+            // lag tiles stage their chunk in windows of kLagTileMaxChunk
+            // samples: chunks up to that length, or whole multiples of it
             int lay = 0;
-            if (a.mma && M <= kLagTileMaxChunk) {
-                if (a.tiles_mode == DG_TILES_HANKEL) lay = 2;
-                else if (a.tiles_mode == DG_TILES_LAGS) lay = 1;
-                else if (a.tiles_mode == DG_TILES_AUTO && t_lag <= 2 * t_row)
-                    lay = (NFB >= 1 && rem > 0 && rem < 64) ? 3 : 1;
-            }
+            const bool windows = M <= kLagTileMaxChunk || M % kLagTileMaxChunk == 0;
+            if (a.mma && a.tiles_mode == DG_TILES_HANKEL && M <= kLagTileMaxChunk) lay = 2;
+            else if (a.mma && windows && a.tiles_mode == DG_TILES_LAGS) lay = 1;
+            else if (a.mma && windows && a.tiles_mode == DG_TILES_AUTO && t_lag <= 2 * t_row)
+                lay = (NFB >= 1 && rem > 0 && rem < 64) ? 3 : 1;
             a.layout[s] = lay;
             tiles = lay == 2 ? 0 : lay == 3 ? t_mix : lay ? t_lag : t_row;
             htiles = lay == 2 ? t_hk : 0;

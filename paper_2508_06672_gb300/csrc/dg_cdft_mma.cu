@@ -2,37 +2,56 @@
 // cores (tcgen05, sm_103a), 16-bit products accumulated in FP32.
 //
 // For one snapshot the contraction is one tall GEMM. Its rows are the
-// (lag bucket, chunk) pairs (NB x B rows), 128 consecutive rows per CTA. For chunk b of lag L the row holds
-// the lag products z[m] = y1[bM + m] conj(y2[bM + m + L]), m < M. Its 128
-// output columns are the real and imaginary parts of
-// W_b(nu_q) = sum_m z[m] e^{j 2 pi nu_q m} on the snapshot's 64 bins. In real
-// arithmetic, per 32-sample stage:
+// (lag bucket, chunk) pairs. For chunk b of lag L the row holds the lag
+// products z[m] = y1[bM + m] conj(y2[bM + m + L]), m < M; its 128 output
+// columns are the real and imaginary parts of W_b(nu_q) = sum_m z[m]
+// e^{j 2 pi nu_q m} on the snapshot's 64 bins. In real arithmetic, per
+// 32-sample stage:
 //     [z_re | z_im] (row, 64) x [[V_re, V_im], [-V_im, V_re]] (64, 128)
-// The right-hand operand depends only on the snapshot, so it is precomputed
-// once per snapshot in 16-bit (bf16 or fp16) in the tensor cores' canonical
-// K-major layout and streamed into shared memory with bulk (TMA) copies. The
-// lag products are formed on the CUDA cores and written into shared memory in
-// the same layout.
+// The right-hand operand depends only on the snapshot: k_cdft_btab writes it
+// once per snapshot in 16 bits (bf16 or fp16; high part and residual for the
+// split forms) in the tensor cores' canonical K-major layout, and the
+// contraction streams it into shared memory with bulk (TMA) copies.
 //
-// One CTA = 128 rows x 128 columns, the accumulator in tensor memory (128
-// columns). The pipeline is warp-specialised over a ring of three stages:
-// eight producer warps form the lag products of a stage on the CUDA cores
-// (each lane 8 consecutive samples of one row, written as one 16-byte
-// core-matrix row, so the stores are conflict-free) and arrive on the stage's
-// "A full" mbarrier; one control thread issues the bulk copy of the stage's
-// DFT operand, waits for both, issues the MMAs and commits them to the
-// stage's "empty" mbarrier, which frees the slot for the producers and for
-// the next bulk copy. The epilogue reads the accumulator with tcgen05.ld and writes
-// W rows (planar: 64 real parts, then 64 imaginary parts) scaled back by
-// 1 / zscale. Every mbarrier wait is bounded: on a timeout the kernel latches
-// ERR_TIMEOUT, stops issuing, waits (bounded) for what it issued, frees its
-// tensor memory and returns.
+// k_cdft_contract_tc is persistent: one CTA of 704 threads per SM walks the
+// batch's tiles (blockIdx.x, + gridDim.x, ...), each 128 rows x 128 columns,
+// laid out on the device by k_cdft_tiles. A tile is either 128 consecutive
+// lags at one chunk (lag tiles: the chunk's y1 and the y2 window of the 128
+// lags are staged in shared memory, in windows of 1024 samples, the next
+// window prefetched into registers while the current one's stages run) or
+// 128 consecutive (lag, chunk) rows (row tiles: each lane loads its row's
+// capture segments). Roles:
+//   16 producer warps  form the lag products of each stage (lane l of warp w
+//                      takes row 32 (w % 4) + l, 8 samples; a warp reaches
+//                      only its quarter of the tensor-memory lanes) and store
+//                      them with tcgen05.st into a ring of 4 A stages in
+//                      tensor memory; a stage's arrival on its "A full"
+//                      barrier follows the next stage's math, so the stores
+//                      land meanwhile;
+//   1 loader thread    streams the DFT operand into a ring of 5 shared-memory
+//                      stages (complete_tx barriers), across tiles;
+//   1 MMA thread       issues tcgen05.mma kind::f16 (A from tensor memory, B
+//                      from shared memory; three products per K step for the
+//                      split forms) and commits them to the stages' "empty"
+//                      barriers and, at a tile's end, to its accumulator;
+//   4 epilogue warps   drain each finished accumulator (tcgen05.ld) into W
+//                      rows (planar: 64 real parts, then 64 imaginary parts,
+//                      scaled back by 1 / zscale) while the next tile's MMAs
+//                      run in the other of the two 128-column accumulators.
+// Every mbarrier wait is bounded (2 s of the global timer, or a poll limit).
+// On a timeout the CTA latches ERR_TIMEOUT and every role stops issuing; the
+// loader waits for its copies in flight and the MMA thread commits to a last
+// barrier that completes when its MMAs have, which is waited for before the
+// tensor memory is freed and the CTA returns.
 //
 // Shared-memory operand layout (no swizzle, K-major): a 128-row x 32-element
 // block is made of 8-row x 16-byte core matrices; element (row, k) is at byte
 // ((row / 8) * 4 + k / 8) * 128 + (row % 8) * 16 + (k % 8) * 2. K-adjacent
 // core matrices are 128 B apart (the descriptor's leading byte offset) and
 // 8-row groups 512 B apart (its stride byte offset).
+//
+// k_cdft_contract_hk (Hankel tiles, on request) regroups the product so that
+// y2 itself is the right operand; see its own comment below.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -92,11 +111,14 @@ __device__ __forceinline__ uint64_t globaltimer_ns()
 
 // Bounded wait on an mbarrier phase: gives up after kWaitBudgetNs of the
 // global timer (checked every 256 polls) or kWaitLimit polls, whichever
-// comes first (try_wait may suspend the thread for a while per poll).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+// comes first (try_wait may suspend the thread for a while per poll). The
+// pipeline's waits take a lower poll limit when one is set for tests
+// (CdftBatch::wait_polls); the waits that drain an aborted pipeline always
+// take the full limit.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit = kWaitLimit)
 {
     uint64_t t0 = 0;
-    for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    for (uint32_t i = 0; i < limit; ++i) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -603,27 +625,34 @@ __device__ __forceinline__ TileInfo tile_info(const SnapCache &c, int S, int M, 
     return t;
 }
 
-// Windows of a lag tile into shared memory, by `nthreads` threads from `tid`.
+// A lag tile's chunk is staged in windows of SW = min(M, kLagTileMaxChunk)
+// samples (M is then a multiple of SW): window w holds y1[n0 .. n0 + SW) and
+// y2[n0 + L0 .. n0 + L0 + SW + 127), n0 = bch M + w SW.
+__device__ __forceinline__ int window_len(int M) { return M < kLagTileMaxChunk ? M : kLagTileMaxChunk; }
+
+// Window w of a lag tile into shared memory, by `nthreads` threads from `tid`.
 template <int FMT>
-__device__ __forceinline__ void stage_windows(const TileInfo &t, int M, float zs, float2 *sy1, float2 *sy2, int tid,
-                                              int nthreads)
+__device__ __forceinline__ void stage_windows(const TileInfo &t, int M, int w, float zs, float2 *sy1, float2 *sy2,
+                                              int tid, int nthreads)
 {
-    const int nb0 = t.bch * M, L0 = t.Lmin + t.lb * kRows;
-    for (int i = tid; i < M; i += nthreads) {
+    const int SW = window_len(M);
+    const int nb0 = t.bch * M + w * SW, L0 = t.Lmin + t.lb * kRows;
+    for (int i = tid; i < SW; i += nthreads) {
         const int n = nb0 + i;
         const float2 v = n < t.N ? IQ<FMT>::load(t.sd.y1, n) : make_float2(0.f, 0.f);
         sy1[i] = make_float2(v.x * zs, v.y * zs);
     }
-    for (int i = tid; i < M + kRows; i += nthreads) {
+    for (int i = tid; i < SW + kRows; i += nthreads) {
         const int n2 = nb0 + L0 + i;
         sy2[i] = (n2 >= 0 && n2 < t.N) ? IQ<FMT>::load(t.sd.y2, n2) : make_float2(0.f, 0.f);
     }
 }
 
-// The capture windows of the next lag tile, prefetched into the producers'
-// registers while the current tile's stages run: element e of thread tid is
-// window element tid + 512 e (y1[bM + i] for i < M, then y2[bM + L0 + i - M]),
-// kept raw (2, 4 or 8 bytes) and decoded only when the tile starts.
+// The next window (of this lag tile or of the next one), prefetched into the
+// producers' registers while the current window's stages run: element e of
+// thread tid is window element tid + 512 e (y1[n0 + i] for i < SW, then
+// y2[n0 + L0 + i - SW]), kept raw (2, 4 or 8 bytes) and decoded only when
+// the window starts.
 constexpr int kPfPer = (2 * kLagTileMaxChunk + kRows + kProducerWarps * 32 - 1) / (kProducerWarps * 32);
 template <int FMT> struct RawIQ;
 template <> struct RawIQ<DG_IQ_C64> {
@@ -655,17 +684,18 @@ template <> struct RawIQ<DG_IQ_CI8> {
 };
 
 template <int FMT>
-__device__ __forceinline__ void prefetch_windows(const TileInfo &t, int M, RawIQ<FMT> &pf, int tid)
+__device__ __forceinline__ void prefetch_windows(const TileInfo &t, int M, int w, RawIQ<FMT> &pf, int tid)
 {
-    const int nb0 = t.bch * M, L0 = t.Lmin + t.lb * kRows;
+    const int SW = window_len(M);
+    const int nb0 = t.bch * M + w * SW, L0 = t.Lmin + t.lb * kRows;
 #pragma unroll
     for (int e = 0; e < kPfPer; ++e) {
         const int i = tid + kProducerWarps * 32 * e;
         int n = -1;
         const void *src = t.sd.y1;
-        if (i < M) n = nb0 + i;
-        else if (i < 2 * M + kRows) {
-            n = nb0 + L0 + (i - M);
+        if (i < SW) n = nb0 + i;
+        else if (i < 2 * SW + kRows) {
+            n = nb0 + L0 + (i - SW);
             src = t.sd.y2;
         }
         if (n >= 0 && n < t.N) pf.load(e, src, n);
@@ -676,12 +706,13 @@ __device__ __forceinline__ void prefetch_windows(const TileInfo &t, int M, RawIQ
 template <int FMT>
 __device__ __forceinline__ void store_windows(const RawIQ<FMT> &pf, int M, float zs, float2 *sy1, float2 *sy2, int tid)
 {
+    const int SW = window_len(M);
 #pragma unroll
     for (int e = 0; e < kPfPer; ++e) {
         const int i = tid + kProducerWarps * 32 * e;
         const float2 v = pf.get(e);
-        if (i < M) sy1[i] = make_float2(v.x * zs, v.y * zs);
-        else if (i < 2 * M + kRows) sy2[i - M] = v;
+        if (i < SW) sy1[i] = make_float2(v.x * zs, v.y * zs);
+        else if (i < 2 * SW + kRows) sy2[i - SW] = v;
     }
 }
 
@@ -709,6 +740,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
     constexpr int kSt = 2 * P * kBlockBytes;  // bytes of one stage's A (or B) blocks
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t full_a[NA], empty_a[NA], full_b[NB], empty_b[NB], acc_full[2], acc_empty[2];
+    __shared__ __align__(8) uint64_t drained;  // the MMA thread's last commit: all its MMAs are done
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_abort;
     __shared__ SnapCache sc;
@@ -742,6 +774,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
             mbar_init(smem_u32(&acc_full[i]), 1);
             mbar_init(smem_u32(&acc_empty[i]), kEpilogueWarps);
         }
+        mbar_init(smem_u32(&drained), 1);
         s_abort = 0;
         fence_mbar_init();
         fence_proxy_async_smem();
@@ -754,6 +787,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
     const int ntiles = sc.tbase[S];
     const int mine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const float zs = a.zscale;
+    const uint32_t wl = a.wait_polls ? a.wait_polls : kWaitLimit;  // poll limit of the pipeline's waits
 
     if (warp < kProducerWarps) {
         // ---------------- producers: lane l of warp w forms row 32 (w % 4) + l
@@ -764,27 +798,26 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
         const int row = 32 * qd + lane;
         const uint32_t tlane = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(kAccCols + 4 * sg);
         RawIQ<FMT> pf;
-        bool have_pf = false;  // pf holds the windows of the tile about to start
-        for (int it = 0; it < mine; ++it) {
-            // every producer is done with the previous tile's windows; all
-            // leave together on an abort
-            if (producers_sync_or(s_abort != 0)) break;
+        bool have_pf = false;  // pf holds the window about to start
+        // stages per window of a lag tile (the whole chunk when M <= 1024)
+        const int SWJ = window_len(M) / kKS;
+        bool stop = false;
+        // A slot whose lag products are stored but not yet announced: its
+        // tcgen05.st completes while the next stage is formed, and the
+        // arrival on its full_a barrier follows then
+        int pend = -1;
+        auto announce = [&]() {
+            if (pend >= 0) {
+                tmem_wait_st();
+                tc_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&full_a[pend]));
+                pend = -1;
+            }
+        };
+        for (int it = 0; it < mine && !stop; ++it) {
             const int tile = (int)blockIdx.x + it * (int)gridDim.x;
             const TileInfo t = tile_info(sc, S, M, tile);
-            if (t.lay) {
-                if (have_pf) store_windows<FMT>(pf, M, zs, sy1, sy2, threadIdx.x);
-                else stage_windows<FMT>(t, M, zs, sy1, sy2, threadIdx.x, kProducerWarps * 32);
-                asm volatile("bar.sync 1, %0;" ::"r"(kProducerWarps * 32) : "memory");
-            }
-            // the next lag tile's windows travel while this tile's stages run
-            have_pf = false;
-            if (it + 1 < mine) {
-                const TileInfo tn = tile_info(sc, S, M, tile + (int)gridDim.x);
-                if (tn.lay) {
-                    prefetch_windows<FMT>(tn, M, pf, threadIdx.x);
-                    have_pf = true;
-                }
-            }
             int pL = 0, pn0 = 0;
             bool pv = false;
             if (!t.lay) {
@@ -798,15 +831,50 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                 }
             }
             const uint32_t g0 = (uint32_t)it * (uint32_t)NJ;
-            for (int j = 0; j < NJ; ++j) {
+            const int NW = t.lay ? NJ / SWJ : 1;          // windows of this tile
+            const int JW = t.lay ? SWJ : NJ;              // stages per window
+            for (int w = 0; w < NW; ++w) {
+                // every producer is done with the previous window's shared
+                // memory; all leave together on an abort (the only place a
+                // producer leaves early, so all pass the same barriers)
+                announce();
+                if (producers_sync_or(s_abort != 0)) {
+                    stop = true;
+                    break;
+                }
+                if (t.lay) {
+                    if (have_pf) store_windows<FMT>(pf, M, zs, sy1, sy2, threadIdx.x);
+                    else stage_windows<FMT>(t, M, w, zs, sy1, sy2, threadIdx.x, kProducerWarps * 32);
+                    asm volatile("bar.sync 1, %0;" ::"r"(kProducerWarps * 32) : "memory");
+                }
+                // the next window travels while this one's stages run: the
+                // next of this tile, else the first of the next lag tile
+                have_pf = false;
+                if (t.lay && w + 1 < NW) {
+                    prefetch_windows<FMT>(t, M, w + 1, pf, threadIdx.x);
+                    have_pf = true;
+                } else if (w + 1 == NW && it + 1 < mine) {
+                    const TileInfo tn = tile_info(sc, S, M, tile + (int)gridDim.x);
+                    if (tn.lay) {
+                        prefetch_windows<FMT>(tn, M, 0, pf, threadIdx.x);
+                        have_pf = true;
+                    }
+                }
+            for (int jw = 0; jw < JW; ++jw) {
+                const int j = w * JW + jw;
                 const uint32_t g = g0 + (uint32_t)j;
                 const int slot = (int)(g % NA);
-                if (g >= NA && !mbar_wait(smem_u32(&empty_a[slot]), ((g / NA) - 1) & 1u)) s_abort = 1;
-                if (s_abort) break;
+                // after an abort the remaining stages are skipped (no wait) up
+                // to the next window's barrier
+                if (s_abort) continue;
+                if (g >= NA && !mbar_wait(smem_u32(&empty_a[slot]), ((g / NA) - 1) & 1u, wl)) {
+                    s_abort = 1;
+                    continue;
+                }
                 tc_after_sync();
                 float2 x[8], y[8];
                 if (t.lay) {
-                    const int m0 = j * kKS + 8 * sg;
+                    const int m0 = jw * kKS + 8 * sg;
 #pragma unroll
                     for (int u = 0; u < 8; u += 2) {
                         const float4 q = *reinterpret_cast<const float4 *>(sy1 + m0 + u);
@@ -836,6 +904,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                     hr[u] = pack2<DT>(zr[2 * u], zr[2 * u + 1]);
                     hi[u] = pack2<DT>(zi[2 * u], zi[2 * u + 1]);
                 }
+                announce();  // the previous stage's stores have had this stage's math to land
                 const uint32_t ta = tlane + (uint32_t)(slot * a_stage_cols<P>());
                 tmem_st4(ta, hr);       // high part, multiplies the re rows of B
                 tmem_st4(ta + 16, hi);  // high part, im rows
@@ -850,18 +919,18 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                     tmem_st4(ta + 32, lr);
                     tmem_st4(ta + 48, li);
                 }
-                tmem_wait_st();
-                tc_before_sync();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&full_a[slot]));
+                pend = slot;
+            }
             }
         }
+        announce();
     } else if (warp == kLoadWarp) {
         // ---------------- operand loader (one thread): B of every stage of
         // every tile, in order, into slot g % NB once the MMAs of stage
         // g - NB are done; it runs ahead of the MMAs by up to NB stages,
         // across tile boundaries
         if (lane == 0) {
+            uint32_t issued = 0;  // stages whose copy has been issued
             for (int it = 0; it < mine && !s_abort; ++it) {
                 const uint32_t g0 = (uint32_t)it * (uint32_t)NJ;
                 const int s = step_of_tile(sc.tbase, S, (int)blockIdx.x + it * (int)gridDim.x);
@@ -869,14 +938,21 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                 for (int j = 0; j < NJ; ++j) {
                     const uint32_t g = g0 + (uint32_t)j;
                     const int slot = (int)(g % NB);
-                    if ((g >= NB && !mbar_wait(smem_u32(&empty_b[slot]), ((g / NB) - 1) & 1u)) || s_abort) {
+                    if ((g >= NB && !mbar_wait(smem_u32(&empty_b[slot]), ((g / NB) - 1) & 1u, wl)) || s_abort) {
                         s_abort = 1;
                         break;
                     }
                     mbar_expect_tx(smem_u32(&full_b[slot]), kSt);
                     bulk_g2s(smem_u32(sB0 + slot * kSt), bsrc + (size_t)j * kSt, kSt, smem_u32(&full_b[slot]));
+                    issued = g + 1;
                 }
             }
+            // after an abort, the copies still in flight (at most the last NB
+            // issued) land before the CTA leaves: shared memory is not
+            // released under a bulk copy
+            if (s_abort)
+                for (uint32_t g = issued > (uint32_t)NB ? issued - NB : 0; g < issued; ++g)
+                    mbar_wait(smem_u32(&full_b[g % NB]), (g / NB) & 1u);
         }
     } else if (warp == kMmaWarp) {
         // ---------------- MMA thread: waits for A and B of each stage,
@@ -889,7 +965,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                 const uint32_t g0 = (uint32_t)it * (uint32_t)NJ;
                 // the accumulator of this tile was drained (tile it - 2)
                 const int acc = it & 1;
-                if (it >= 2 && !mbar_wait(smem_u32(&acc_empty[acc]), ((uint32_t)(it / 2) - 1) & 1u)) {
+                if (it >= 2 && !mbar_wait(smem_u32(&acc_empty[acc]), ((uint32_t)(it / 2) - 1) & 1u, wl)) {
                     alive = false;
                     break;
                 }
@@ -898,8 +974,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                 for (int j = 0; j < NJ; ++j) {
                     const uint32_t g = g0 + (uint32_t)j;
                     const int sa = (int)(g % NA), sb = (int)(g % NB);
-                    if (!mbar_wait(smem_u32(&full_a[sa]), (g / NA) & 1u) ||
-                        !mbar_wait(smem_u32(&full_b[sb]), (g / NB) & 1u) || s_abort) {
+                    if (!mbar_wait(smem_u32(&full_a[sa]), (g / NA) & 1u, wl) ||
+                        !mbar_wait(smem_u32(&full_b[sb]), (g / NB) & 1u, wl) || s_abort) {
                         alive = false;
                         break;
                     }
@@ -924,6 +1000,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                 }
             }
             if (!alive) s_abort = 1;
+            // completes once every MMA this thread issued is done
+            mma_commit(smem_u32(&drained));
         }
     } else {
         // ---------------- drain finished accumulators: the last four warps
@@ -931,7 +1009,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
         for (int it = 1; it <= mine && !s_abort; ++it) {
             // drain tile it - 1
             const int d = it - 1, acc = d & 1;
-            if (!mbar_wait(smem_u32(&acc_full[acc]), (uint32_t)(d / 2) & 1u)) {
+            if (!mbar_wait(smem_u32(&acc_full[acc]), (uint32_t)(d / 2) & 1u, wl)) {
                 s_abort = 1;
                 break;
             }
@@ -971,10 +1049,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
         }
     }
     __syncthreads();
-    // the MMAs of the last tile (if any) must complete before TMEM is freed
-    if (s_abort && mine > 0 && threadIdx.x == 0) {
-        const int last = mine - 1;
-        mbar_wait(smem_u32(&acc_full[last & 1]), (uint32_t)(last / 2) & 1u);
+    // after an abort, every MMA issued must complete before TMEM is freed
+    if (s_abort && threadIdx.x == 0) {
+        mbar_wait(smem_u32(&drained), 0u);
         atomicOr(a.err, ERR_TIMEOUT);
     }
     tc_before_sync();

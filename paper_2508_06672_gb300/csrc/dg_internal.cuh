@@ -340,6 +340,7 @@ struct CdftBatch {
     int ngroups;                  // combine groups of the batch (upper bound; unused ones are -1 in g2b)
     const void *btab;             // [S][M/32][2][128 x 32] 16-bit DFT operand (tensor cores)
     float zscale;                 // lag products are multiplied by this before 16-bit rounding
+    unsigned wait_polls;          // poll limit of the tensor-core pipeline's waits; 0 = the default
 };
 
 cudaError_t launch_cdft_geo(const CdftBatch &a, cudaStream_t s);
@@ -373,17 +374,32 @@ constexpr int kTcMaxSnapshots = 64;
 // takes (longer chunks shorten the combine but lengthen the tables and the
 // contraction's operand stream: 1024 was fastest on the 1001^2 and 4001^2
 // workloads); and the bound on (samples summed per DFT) x (bin spacing), in
-// cycles, for the 3-bin quadratic interpolation of the combine: its relative
-// error is at most about 0.016 (2 pi M Delta)^3 of the coherent sum, 7e-6 at
-// this bound. The plan rejects a chunk above it; the automatic chunk and the
-// super-chunks keep below it.
-constexpr int kCdftMaxChunk = 4096;
+// cycles, for the 6-point Lagrange interpolation of the combine. The bins
+// are padded by two on each side of the snapshot's FDOA range, so every
+// candidate lies between the third and fourth nodes of its stencil
+// (t in [0, 1]); there the error of interpolating a DFT of length L is at
+// most |prod_{k=-2..3} (t - k)| / 6! (2 pi L Delta)^6 <= 4.9e-3 (2 pi L Delta)^6
+// of the coherent sum, 4.7e-6 at this bound. The plan rejects a chunk above
+// it; the automatic chunk and the super-chunks keep below it.
+constexpr int kCdftMaxChunk = 16384;
 constexpr int kCdftAutoMaxChunk = 1024;
+// The tensor-core path takes automatic chunks up to kCdftAutoMaxChunkTc while
+// a batch keeps kCdftMinTilesPerSm lag tiles per SM (the host's estimate).
+// The cap is set by accuracy: the tensor cores' FP32 accumulation adds a
+// relative error that grows with the number of MMAs summed into one
+// accumulator (measured on the 4001^2 footprint against FP64, split fp16
+// products: 1.2e-5 at 1024-sample chunks, 1.5e-4 at 16384, at the peak), so
+// chunks are kept to 2048 samples (about 2.5e-5) and longer sums are formed
+// in FP32 on the CUDA cores (super-chunks).
+constexpr int kCdftAutoMaxChunkTc = 2048;
+constexpr int kCdftMinTilesPerSm = 16;
 // Automatic chunk cap of a refinement surface: its few lags per snapshot give
 // few (lag, chunk) rows, and shorter chunks turn the same tensor work into
 // more and shorter tiles, spread over more SMs.
 constexpr int kCdftRefineMaxChunk = 256;
-constexpr double kCdftMDelta = 1.2e-2;
+constexpr double kCdftMDelta = 5.0e-2;
+constexpr int kCdftBinPad = 2;                  // bins outside the FDOA range on each side
+constexpr int kCdftBinSpan = 63 - 2 * kCdftBinPad;  // bin steps across the FDOA range
 
 // Threshold detection (dg_detect.cu). cap: power of two <= kDetectCap candidates
 // (the sort keeps value + index of each in static shared memory, 32 KiB).

@@ -23,7 +23,7 @@ __all__ = [
     "Batch",
     "dg_options_default", "dg_create", "dg_load_capture", "dg_cost_surface", "dg_argmax_refine",
     "dg_sync", "dg_destroy", "dg_last_error", "dg_grid_ecef", "dg_step_geometry", "dg_kernel_time",
-    "dg_reset_counters", "dg_launch_count", "dg_abi_version", "dg_fp32_peak", "Geolocator",
+    "dg_reset_counters", "dg_launch_count", "dg_abi_version", "dg_fp32_peak", "dg_debug_tc_wait_limit", "Geolocator",
     "dg_cost_surface_noalloc", "dg_noalloc_last_error", "DG_NOALLOC_SCRATCH_BYTES", "dg_cdft_work",
     "DG_OK", "DG_EINVAL", "DG_ENOMEM", "DG_ECUDA", "DG_ESTATE", "DG_ETIMEOUT", "DG_EUNSUPPORTED",
     "DG_IQ_C64", "DG_IQ_CI16", "DG_IQ_CI8", "DG_DELAY_INTEGER", "DG_DELAY_LAGRANGE4",
@@ -66,6 +66,7 @@ EXPORTED_SYMBOLS = [
     "dg_nn_conv3x3_forward", "dg_nn_conv3x3_backward", "dg_nn_conv3x3_scratch", "dg_nn_relu_forward",
     "dg_nn_relu_backward", "dg_nn_bce_scratch", "dg_nn_bce_logits", "dg_nn_adam", "dg_nn_last_error",
     "dg_coarse_maps", "dg_coarse_inspect", "dg_set_grid", "dg_search_regions", "dg_fp32_peak",
+    "dg_debug_tc_wait_limit",
 ]
 DG_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
@@ -172,6 +173,7 @@ def lib():
             L.dg_abi_version.argtypes = []
             L.dg_abi_version.restype = i32
             L.dg_fp32_peak.argtypes = [vp, i32, C.POINTER(dbl), C.POINTER(dbl), C.POINTER(i32)]
+            L.dg_debug_tc_wait_limit.argtypes = [C.c_uint32]
             L.dg_cost_surface_noalloc.argtypes = [C.POINTER(dg_grid), C.POINTER(dg_ephem), i32, dbl, dbl,
                                                   i32, vp, vp, i64, C.POINTER(dg_options), vp, vp]
             L.dg_cost_surface_noalloc.restype = C.c_int
@@ -382,6 +384,12 @@ def dg_fp32_peak(iters=50000, stream=0):
     if st != DG_OK:
         raise DGError(st, "dg_fp32_peak failed")
     return tf.value, ms.value, sms.value
+
+
+def dg_debug_tc_wait_limit(polls):
+    """Test hook (see include/dg.h): poll limit of the tensor-core pipeline's
+    waits in CDFT surfaces launched afterwards; 0 restores the default."""
+    lib().dg_debug_tc_wait_limit(int(polls))
 
 
 def dg_noalloc_last_error():

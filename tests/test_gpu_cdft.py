@@ -124,11 +124,12 @@ def test_cdft_hankel_shorter_chunks_and_auto(chunk):
 
 def test_cdft_auto_chunk():
     """chunk 0: each batch takes the longest power-of-two chunk up to 1024
-    whose length times the estimated bin spacing stays within the bound (with
-    a 25 % margin); the result stays within the FP32 tolerance, and a grid
-    with a wider FDOA span (1000 km at 2 MHz) gets a shorter chunk."""
+    (few tiles here) whose length times the estimated bin spacing stays
+    within the bound (with a 10 % margin); the result stays within the FP32
+    tolerance, and a grid with a wider FDOA span (1000 km at 0.5 MHz) gets a
+    shorter chunk."""
     chunks = []
-    for fs, spacing in ((12.5e6, 100.0), (2e6, 25000.0)):
+    for fs, spacing in ((12.5e6, 100.0), (5e5, 25000.0)):
         s = sim.make_scene(seed=23, fs_hz=fs, n_samples=40000, k_steps=2, fmt="ci16", waveform="chirp",
                            snr_db=-3.0, grid_n=(41, 39), grid_spacing_m=spacing)
         g, c = gpu_surface(s, algo="cdft")
@@ -136,10 +137,54 @@ def test_cdft_auto_chunk():
         assert lo & (lo - 1) == 0 and hi & (hi - 1) == 0 and 64 <= lo <= hi <= 1024
         ref = oracle_surface(s)
         ok = ~lag_boundary_mask(s, np.arange(s.G))
-        assert rel_err(c.ravel()[ok], ref.ravel()[ok], 0.01) < FP32_TOL
+        r, d = ref.ravel()[ok], c.ravel()[ok]
+        strong = r >= 0.1 * r.max()
+        print(f"fs {fs:g}: chunk {hi}, floored error {rel_err(d, r, 0.01, 2.0):.3e}, "
+              f"plain error on nodes >= 10% of the maximum {np.max(np.abs(d - r)[strong] / r[strong]):.3e}")
+        assert rel_err(d, r, 0.01) < FP32_TOL
         chunks.append(hi)
         g.close()
     assert chunks[1] < chunks[0]
+
+
+@pytest.mark.parametrize("chunk", [2048, 3072])
+def test_cdft_long_chunks_in_windows(chunk):
+    """Chunks longer than the 1024-sample capture window: lag tiles stage each
+    chunk in 1024-sample windows (the next prefetched while the current one's
+    stages run). Their surfaces equal the row tiles' bit for bit (the same lag
+    products, the same accumulation order) and the oracle's within the FP32
+    bound, with a ragged last chunk and five blocks of 128 lags."""
+    s = sim.make_scene(seed=28, fs_hz=20e6, n_samples=20001, k_steps=2, fmt="ci8", waveform="noise",
+                       snr_db=-3.0, grid_n=(45, 41), grid_spacing_m=4000.0, bw_hz=18e6)
+    out = {}
+    for tiles in ("rows", "lags"):
+        g, c = gpu_surface(s, algo="cdft", contract="fp16x3", chunk=chunk, tiles=tiles)
+        out[tiles] = c
+        g.close()
+    assert np.array_equal(out["rows"], out["lags"])
+    ref = oracle_surface(s)
+    ok = ~lag_boundary_mask(s, np.arange(s.G))
+    assert rel_err(out["lags"].ravel()[ok], ref.ravel()[ok], 0.01) < FP32_TOL
+
+
+def test_cdft_auto_chunk_above_the_window():
+    """With many snapshots of long captures and a few hundred lags, the
+    automatic chunk on the tensor cores grows past 1024 samples, to its cap
+    of 2048, while the batch keeps enough lag tiles per SM (16 snapshots x
+    about 1190 lags x 64 chunks); the surface stays within the FP32 bound of
+    the oracle."""
+    s = sim.make_scene(seed=29, fs_hz=20e6, n_samples=131072, k_steps=16, fmt="ci8", waveform="noise",
+                       snr_db=-3.0, grid_n=(45, 41), grid_spacing_m=4000.0, bw_hz=18e6)
+    g, c = gpu_surface(s, algo="cdft", contract="fp16x3")
+    lo, hi = g.cdft_chunks()
+    assert lo == hi == 2048, (lo, hi)
+    g.close()
+    rng = np.random.default_rng(3)
+    idx = np.unique(rng.integers(0, s.G, 200))
+    ref = oracle.cost_points(*oracle.scene_args(s), idx=idx)
+    ok = ~lag_boundary_mask(s, idx)
+    assert rel_err(c.ravel()[idx][ok], ref[ok]) < FP32_TOL
+    assert_global_argmax(s, c, FP32_TOL)
 
 
 def test_cdft_tile_spanning_more_lags_than_shared_buckets():
@@ -163,8 +208,8 @@ def test_cdft_superchunks(contract):
     """The combine sums chunks at the bin frequencies into super-chunks as
     long as the bin-spacing bound allows: a 4 km grid (narrow FDOA span)
     needs one super-chunk per snapshot; a 1000 km grid at 5 MHz with 64-sample
-    chunks gets 1024-sample super-chunks. Both stay within the FP32 bound of
-    the oracle."""
+    chunks gets 4096-sample super-chunks (ten per snapshot). Both stay within
+    the FP32 bound of the oracle."""
     for fs, spacing, chunk, one in ((12.5e6, 100.0, 256, True), (5e6, 25000.0, 64, False)):
         s = sim.make_scene(seed=25, fs_hz=fs, n_samples=40000, k_steps=2, fmt="ci16", waveform="chirp",
                            snr_db=-3.0, grid_n=(41, 39), grid_spacing_m=spacing)
@@ -182,12 +227,12 @@ def test_cdft_superchunks(contract):
 
 def test_cdft_rejects_chunk_too_long_for_the_bins():
     """A fixed chunk whose length times the bin spacing exceeds the
-    interpolation bound (4096 samples on a 1000 km grid at 5 MHz) is
-    refused with DG_EUNSUPPORTED when the surface is read; the context
-    stays usable with a shorter chunk."""
+    interpolation bound (4096 samples on a 1000 km grid at 2 MHz: 0.085
+    cycles) is refused with DG_EUNSUPPORTED when the surface is read; the
+    context stays usable with a shorter chunk (1024: 0.021 cycles)."""
     torch = torch_cuda()
     P = package()
-    s = sim.make_scene(seed=26, fs_hz=5e6, n_samples=20000, k_steps=1, fmt="ci16", waveform="chirp",
+    s = sim.make_scene(seed=26, fs_hz=2e6, n_samples=20000, k_steps=1, fmt="ci16", waveform="chirp",
                        snr_db=-3.0, grid_n=(41, 39), grid_spacing_m=25000.0)
     g = P.Geolocator(s.grid, s.ephem, s.fs_hz, s.fc_hz, algo="cdft", chunk=4096)
     g.load_captures(s.fmt, torch.from_numpy(s.y1).cuda(), torch.from_numpy(s.y2).cuda())
@@ -320,4 +365,33 @@ def test_cdft_tensor_core_large_full_size_sampled(contract):
     ref = oracle.cost_points(*oracle.scene_args(s), idx=idx)
     ok = ~lag_boundary_mask(s, idx)
     assert rel_err(c.ravel()[idx][ok], ref[ok]) < TC_TOL[contract]
+    g.close()
+
+
+def test_tensor_pipeline_timeout_is_reported_and_the_context_recovers():
+    """Every wait of the tensor-core pipeline is bounded. With the test hook
+    lowering their poll limit to one poll, the first wait that is not already
+    satisfied gives up: the kernel stops issuing, lets the MMAs and bulk
+    copies it issued land, frees its tensor memory and returns, and the next
+    synchronising call reports DG_ETIMEOUT. With the default limit restored,
+    the same context's next surface matches the oracle."""
+    torch = torch_cuda()
+    P = package()
+    s = sim.make_scene(seed=30, fs_hz=12.5e6, n_samples=8192, k_steps=2, fmt="ci16", waveform="chirp",
+                       snr_db=-3.0, grid_n=(37, 45), grid_spacing_m=150.0)
+    g = P.Geolocator(s.grid, s.ephem, s.fs_hz, s.fc_hz, algo="cdft", contract="fp16x3")
+    g.load_captures(s.fmt, torch.from_numpy(s.y1).cuda(), torch.from_numpy(s.y2).cuda())
+    try:
+        P.dg_debug_tc_wait_limit(1)
+        g.cost_surface()
+        with pytest.raises(P.DGError) as e:
+            g.sync()
+        assert e.value.status == P.DG_ETIMEOUT
+    finally:
+        P.dg_debug_tc_wait_limit(0)
+    c = g.cost_surface()
+    g.sync()
+    ref = oracle_surface(s)
+    ok = ~lag_boundary_mask(s, np.arange(s.G))
+    assert rel_err(c.double().cpu().numpy().ravel()[ok], ref.ravel()[ok], 0.01) < FP32_TOL
     g.close()

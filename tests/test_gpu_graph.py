@@ -137,7 +137,7 @@ def test_autotune_picks_an_admissible_shape(contract):
     s = _scene(50, k_steps=3, n_samples=30000)
     g = _geo(s, torch.cuda.Stream(), algo="cdft", contract=contract)
     t = g.autotune(reps=2)
-    assert t["chunk"] in (256, 512, 1024)
+    assert 256 <= t["chunk"] <= 16384 and t["chunk"] & (t["chunk"] - 1) == 0
     assert t["tiles"] in (1, 2) and (contract != "fp32" or t["tiles"] == 1)
     assert t["cached"] == 0 and t["tried"] >= 3 and t["ms"] > 0
     with torch.cuda.stream(g.stream):
