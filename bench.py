@@ -678,7 +678,7 @@ def run_batch(a, rank, world, local_rank):
     for sc in scenes:
         st = torch.cuda.Stream(dev)
         g = P.Geolocator(sc.grid, sc.ephem, sc.fs_hz, sc.fc_hz, algo="cdft", contract=a.contract, tiles=a.tiles, stream=st,
-                         device=local_rank, scratch_mib=256)
+                         device=local_rank, scratch_mib=1024)
         y1, y2 = torch.from_numpy(sc.y1).pin_memory(), torch.from_numpy(sc.y2).pin_memory()
         with torch.cuda.stream(st):
             g.load_captures(sc.fmt, y1, y2)
@@ -742,6 +742,10 @@ def run_batch(a, rank, world, local_rank):
             "config": {"workload": f"batch: {len(scenes)} uneven captures (K 5-100, N 2^12-2^18, grids 256-2048^2 "
                                    f"at 50-500 m, tone/chirp/noise, ci16, fs 12.5 MHz), one CUDA graph per step",
                        "captures": len(scenes), "cand_samples_per_step": units, "algo": "cdft",
+                       "shared_contraction_rounds": batch.rounds(),
+                       "contraction": ("one persistent tcgen05 launch per round over the tiles of every capture's "
+                                       "r-th snapshot batch (each context's scratch target: 1 GiB)"
+                                       if batch.rounds() else "one persistent launch per capture and snapshot batch"),
                        "contract": a.contract, "refine": f"{REFINE_SPACING_M:g} m spacing, +-{REFINE_WINDOW_M:g} m",
                        "l2": "flushed between timed steps (256 MB write inside the batch stream, before the start "
                              "event)", "seed": 1000 + rank},

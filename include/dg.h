@@ -65,15 +65,17 @@ enum { DG_ACC_POWER = 0, DG_ACC_MAG = 1 };
 enum { DG_PREC_FP32 = 0, DG_PREC_FP64 = 1 };
 
 /* Correlation algorithm. DIRECT evaluates Eq. 11 sample by sample for every
- * candidate. CDFT (integer delay only) groups the candidates of a snapshot by
- * their integer lag L (Eq. 9): all of them share the lag product
- * z_L[n] = y1[n] conj(y2[n + L]), so Eq. 11 becomes, per lag, a DFT of z_L
- * in chunks of `chunk` samples at `bins` Doppler frequencies spanning that
- * lag's FDOA range (a dense contraction), followed per candidate by a
- * 6-point Lagrange interpolation between the bins around its FDOA and a sum
- * over chunks with the FDOA phase of each chunk's first sample. Its error against the definition is bounded by
- * the bin interpolation and by the arithmetic of the contraction
- * (DG_CONTRACT_*). */
+ * candidate. CDFT groups the candidates of a snapshot by their integer lag L
+ * (Eq. 9): all of them share the lag product z_L[n] = y1[n] conj(y2[n + L]),
+ * so Eq. 11 becomes, per lag, a DFT of z_L in chunks of `chunk` samples at
+ * `bins` Doppler frequencies spanning that lag's FDOA range (a dense
+ * contraction), followed per candidate by a 6-point Lagrange interpolation
+ * between the bins around its FDOA and a sum over chunks with the FDOA phase
+ * of each chunk's first sample. With LAGRANGE4 the lag is floor(D) and, the
+ * interpolation being linear in y2, each candidate sums the correlations of
+ * lags L - 1 .. L + 2 weighted by its 4-tap weights. Its error against the
+ * definition is bounded by the bin interpolation and by the arithmetic of the
+ * contraction (DG_CONTRACT_*). */
 enum { DG_ALGO_DIRECT = 0, DG_ALGO_CDFT = 1 };
 
 /* Tiles of the CDFT tensor-core contraction.
@@ -309,13 +311,22 @@ dg_status dg_graph_fix(dg_ctx *ctx, dg_fix *out);
  * on each context's stream so far (capture loads); dg_batch_fixes waits
  * for it and writes n fixes (host); a context whose step failed gets
  * index = -1 and the first failure is returned. A context must not be used
- * by other calls while a launch of its batch is in flight. */
+ * by other calls while a launch of its batch is in flight.
+ * When every context runs CDFT on the tensor cores (lag or row tiles) with
+ * one capture format and one contraction arithmetic, the contractions of
+ * the main surfaces are shared: round r is one persistent launch over the
+ * tiles of the r-th snapshot batch of every context that has one (a device
+ * work list over (capture, snapshot, tile)), with each context's plan
+ * before it and its combine after it on the context's own branch. Rounds =
+ * the most snapshot batches of any context (dg_batch_rounds; 0 when the
+ * contractions are per context). Refinement surfaces stay per context. */
 typedef struct dg_batch dg_batch;
 dg_status dg_batch_capture(dg_ctx *const *ctxs, int32_t n, void *const *costs, double refine_spacing_m,
                            double refine_window_m, void *stream, dg_batch **out);
 dg_status dg_batch_launch(dg_batch *batch);
 dg_status dg_batch_fixes(dg_batch *batch, dg_fix *out);
 int64_t dg_batch_launch_count(const dg_batch *batch); /* kernels per launch */
+int32_t dg_batch_rounds(const dg_batch *batch);        /* shared contraction rounds */
 dg_status dg_batch_destroy(dg_batch *batch);
 
 /* Autotuning of the CDFT launch shape (no counterpart in the paper; it is

@@ -52,11 +52,22 @@ struct CdftLayout {  // batches and bucket / group bases of one grid size
     int *bbase = nullptr, *gbase = nullptr;  // device, per batch: [S + 1] each
 };
 
+struct CdftRun {  // one chunked-DFT surface, phase by phase (run_surface_cdft)
+    GridDev gd{};
+    const double *xyz = nullptr;
+    int64_t G = 0;
+    void *surf = nullptr, *out = nullptr;
+    bool refine = false, mma = false;
+    CdftLayout *L = nullptr;
+    std::vector<int> Ms;  // chunk of each batch of snapshots
+};
+
 struct CdftBufs {  // chunked-DFT scratch, grown on demand
     int *lr = nullptr;
     CdftLayout main_layout, loc_layout;
     std::vector<double> main_span;  // FDOA span estimates per snapshot (main grid)
     std::vector<double> main_lags;  // and lag-count estimates
+    CdftRun main_run;               // the main surface's last run (its batches' arguments)
     int *layout = nullptr, *Mcs = nullptr;
     unsigned long long *work = nullptr;
     unsigned *nur = nullptr;
@@ -64,6 +75,9 @@ struct CdftBufs {  // chunked-DFT scratch, grown on demand
     size_t s_cap = 0;
     int *candL = nullptr, *order = nullptr;
     float *candNu = nullptr, *nuS = nullptr;
+    float *candMu = nullptr, *muS = nullptr;  // Lagrange4: fractional delays
+    size_t mu_cap = 0;
+    int *need = nullptr;
     size_t sg_cap = 0;
     int4 *g2b = nullptr;
     size_t g2b_cap = 0;
@@ -357,12 +371,13 @@ dg_status grow(dg_ctx *c, P **p, size_t n)
 // triangle inequality |rho2 - rho1| <= |p2 - p1|, so |D| <= |p2 - p1| fs / c;
 // and each range moves by at most the displacement of the candidate, so D
 // varies by at most 2 diam fs / c over the grid. Eq. 9 then gives at most
-// 2 ceil(bound) + 1 lags; 2 more absorb rounding.
+// 2 ceil(bound) + 1 lags; 2 more absorb rounding, and 3 more the stencil of
+// the Lagrange4 delay (lags L - 1 .. L + 2 around floor(D)).
 static int lag_slots(const dg_ephem &e, double fs, double diam)
 {
     const double dx = e.p2[0] - e.p1[0], dy = e.p2[1] - e.p1[1], dz = e.p2[2] - e.p1[2];
     const double span = std::min(2.0 * std::sqrt(dx * dx + dy * dy + dz * dz), 2.0 * diam) * fs / kC;
-    return (int)std::ceil(span) + 3;
+    return (int)std::ceil(span) + 6;
 }
 
 // FP64 WGS-84 node position and Eq. 3-10 FDOA on the host (planning only).
@@ -567,9 +582,18 @@ static dg_status ensure_ephf(dg_ctx *c)
     return DG_OK;
 }
 
-dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int64_t G, void *surf, void *out,
-                           bool refine)
+// The phases of one chunked-DFT surface: setup (layout, chunks, buffers,
+// the candidates' double-float split), then per batch of snapshots its
+// arguments, plan, contraction and combine, then the ordered accumulation.
+// run_surface_cdft runs them in order; a batch of contexts captured as one
+// graph (dg_batch_capture) runs the contraction of the r-th batch of every
+// context as one persistent launch between the plans and the combines.
+static dg_status cdft_setup(dg_ctx *c, CdftRun &r)
 {
+    const GridDev &gd = r.gd;
+    const double *xyz = r.xyz;
+    const int64_t G = r.G;
+    const bool refine = r.refine;
     dg_status st = push_steps(c);
     if (st != DG_OK) return st;
     for (int k = 0; k < c->K; ++k)
@@ -577,6 +601,7 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
             return fail(c, DG_EUNSUPPORTED, "CDFT: snapshots longer than 2^24 samples are not supported; use DIRECT");
     CdftBufs &b = c->cd;
     CdftLayout &L = refine ? b.loc_layout : b.main_layout;
+    r.L = &L;
     // a refinement grid is planned from its shape only (as if centred on the
     // main grid's centre), so that a step captured in a CUDA graph, whose
     // refinement centre is known on the device only, plans it alike
@@ -591,9 +616,11 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
     // grid lies around one of its nodes and spans far less)
     std::vector<double> &span = b.main_span;
     const bool mma = c->opt.contract != DG_CONTRACT_FP32;
+    r.mma = mma;
     if (c->opt.chunk == 0 && (span.size() != (size_t)c->K || b.main_lags.size() != (size_t)c->K))
         fdoa_spans(c, c->gd, span, &b.main_lags);
-    std::vector<int> Ms(L.batches.size());
+    std::vector<int> &Ms = r.Ms;
+    Ms.assign(L.batches.size(), 0);
     int M_max = 64, B_max = 1;
     for (size_t i = 0; i < L.batches.size(); ++i) {
         const auto &t = L.batches[i];
@@ -627,6 +654,11 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         if ((st = grow(c, &b.nuS, (size_t)s_max * G)) != DG_OK) return st;
         b.sg_cap = (size_t)s_max * G;
     }
+    if (c->opt.delay != DG_DELAY_INTEGER && b.mu_cap < (size_t)s_max * G) {
+        if ((st = grow(c, &b.candMu, (size_t)s_max * G)) != DG_OK) return st;
+        if ((st = grow(c, &b.muS, (size_t)s_max * G)) != DG_OK) return st;
+        b.mu_cap = (size_t)s_max * G;
+    }
     if (!mma && b.v_cap < (size_t)s_max * M_max * 64) {  // the FP32 contraction's DFT table
         if ((st = grow(c, &b.V, (size_t)s_max * M_max * 64)) != DG_OK) return st;
         b.v_cap = (size_t)s_max * M_max * 64;
@@ -634,6 +666,7 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
     if (b.nb_cap < (size_t)L.nbt_max) {
         const size_t n = (size_t)L.nbt_max;
         if ((st = grow(c, &b.count, n)) != DG_OK) return st;
+        if ((st = grow(c, &b.need, n)) != DG_OK) return st;
         if ((st = grow(c, &b.offs, n)) != DG_OK) return st;
         if ((st = grow(c, &b.subcnt, n)) != DG_OK) return st;
         b.nb_cap = n;
@@ -665,11 +698,6 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         c->cd_chunk_min = INT_MAX;
         c->cd_chunk_max = 0;
     }
-    // constants of the geometry as double-float (hi, lo) pairs
-    auto split = [](double d, float &h, float &l) {
-        h = (float)d;
-        l = (float)(d - (double)h);
-    };
     if ((st = ensure_ephf(c)) != DG_OK) return st;
     if (b.xyzf_cap < (size_t)G) {
         if ((st = grow(c, &b.xyzf, 6 * (size_t)G)) != DG_OK) return st;
@@ -680,125 +708,208 @@ dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int6
         CK(c, launch_ecef_split(xyz, G, b.xyzf, c->stream));
         t.done(1);
     }
-    float *surf_f = reinterpret_cast<float *>(surf);
-    for (size_t bi = 0; bi < L.batches.size(); ++bi) {
-        const auto &bt = L.batches[bi];
-        const int k0 = bt.k0, S = bt.S, M = Ms[bi];
-        int Bmax = 1;
-        for (int s = 0; s < S; ++s) Bmax = std::max<int>(Bmax, (int)((c->steps[k0 + s].n + M - 1) / M));
-        if (!refine) {
-            c->cd_chunk_min = std::min(c->cd_chunk_min, M);
-            c->cd_chunk_max = std::max(c->cd_chunk_max, M);
-        }
-        CdftBatch a{};
-        a.xyz = xyz;
-        a.xyzf = b.xyzf;
-        a.ephf = b.ephf + 24 * (size_t)k0;
-        split(c->fs / kC, a.fsc_hi, a.fsc_lo);
-        split(1.0 / (c->lambda * c->fs), a.ilf_hi, a.ilf_lo);
-        a.eph = c->eph + 12 * (size_t)k0;
-        a.sd = c->steps_d + k0;
-        a.S = S;
-        a.k0 = k0;
-        a.G = G;
-        a.nrows = gd.nrows;
-        a.nlon = gd.nlon;
-        a.fs = c->fs;
-        a.lambda = c->lambda;
-        a.M = M;
-        a.Bmax = Bmax;
-        a.acc = c->opt.acc;
-        a.err = c->err_d;
-        a.lr = b.lr;
-        a.nur = b.nur;
-        a.nubase = b.nubase;
-        a.bbase = L.bbase + bt.base;
-        a.gbase = L.gbase + bt.base;
-        a.candL = b.candL;
-        a.candNu = b.candNu;
-        a.order = b.order;
-        a.nuS = b.nuS;
-        a.g2b = b.g2b;
-        a.delta = b.delta;
-        a.V = b.V;
-        a.count = b.count;
-        a.offs = b.offs;
-        a.subcnt = b.subcnt;
-        a.W = b.W;
-        a.tbase = b.tbase;
-        a.hbase = b.hbase;
-        a.layout = b.layout;
-        a.Mcs = b.Mcs;
-        a.work = refine ? nullptr : b.work;
-        a.tiles_mode = c->opt.tiles;
-        a.mma = mma ? 1 : 0;
-        a.ngroups = (int)bt.groups;
-        a.btab = b.btab;
-        // FP16 needs the lag products inside its range: int16 products reach 2^31
-        const int f = c->steps[k0].fmt;
-        const bool fp16 = c->opt.contract == DG_CONTRACT_FP16 || c->opt.contract == DG_CONTRACT_FP16X3;
-        a.zscale = (mma && fp16 && f == DG_IQ_CI16) ? 1.0f / 65536.0f : 1.0f;
-        a.wait_polls = g_tc_wait_polls.load(std::memory_order_relaxed);
-        {
-            Timed t(c, kplan);
-            CK(c, launch_cdft_geo(a, c->stream));
-            CK(c, cudaMemsetAsync(b.g2b, 0xff, sizeof(int4) * (size_t)bt.groups, c->stream));
-            CK(c, launch_cdft_plan(a, (int)bt.nbt, c->stream));
-            CK(c, launch_cdft_tiles(a, c->stream));
-            t.done(mma ? 6 : 7);
-        }
-        {
-            Timed t(c, refine ? DG_K_REFINE : DG_K_CDFT_CONTRACT);
-            if (mma) {
-                // persistent: one CTA per SM, or fewer when the batch can
-                // have fewer tiles (the bound: lag tiles of every lag slot)
-                int64_t tiles_cap = 0;
+    if (!refine) c->cd.main_run = r;
+    return DG_OK;
+}
+
+static void cdft_args(dg_ctx *c, const CdftRun &r, size_t bi, CdftBatch &a)
+{
+    CdftBufs &b = c->cd;
+    const CdftLayout &L = *r.L;
+    const std::vector<int> &Ms = r.Ms;
+    const bool mma = r.mma, refine = r.refine;
+    const double *xyz = r.xyz;
+    const GridDev &gd = r.gd;
+    const int64_t G = r.G;
+    // constants of the geometry as double-float (hi, lo) pairs
+    auto split = [](double d, float &h, float &l) {
+        h = (float)d;
+        l = (float)(d - (double)h);
+    };
+    const auto &bt = L.batches[bi];
+    const int k0 = bt.k0, S = bt.S, M = Ms[bi];
+    int Bmax = 1;
+    for (int s = 0; s < S; ++s) Bmax = std::max<int>(Bmax, (int)((c->steps[k0 + s].n + M - 1) / M));
+    if (!refine) {
+        c->cd_chunk_min = std::min(c->cd_chunk_min, M);
+        c->cd_chunk_max = std::max(c->cd_chunk_max, M);
+    }
+    a.xyz = xyz;
+    a.xyzf = b.xyzf;
+    a.ephf = b.ephf + 24 * (size_t)k0;
+    split(c->fs / kC, a.fsc_hi, a.fsc_lo);
+    split(1.0 / (c->lambda * c->fs), a.ilf_hi, a.ilf_lo);
+    a.eph = c->eph + 12 * (size_t)k0;
+    a.sd = c->steps_d + k0;
+    a.S = S;
+    a.k0 = k0;
+    a.G = G;
+    a.nrows = gd.nrows;
+    a.nlon = gd.nlon;
+    a.fs = c->fs;
+    a.lambda = c->lambda;
+    a.M = M;
+    a.Bmax = Bmax;
+    a.acc = c->opt.acc;
+    a.err = c->err_d;
+    a.lr = b.lr;
+    a.nur = b.nur;
+    a.nubase = b.nubase;
+    a.bbase = L.bbase + bt.base;
+    a.gbase = L.gbase + bt.base;
+    a.candL = b.candL;
+    a.candNu = b.candNu;
+    a.order = b.order;
+    a.nuS = b.nuS;
+    a.g2b = b.g2b;
+    a.delta = b.delta;
+    a.V = b.V;
+    a.count = b.count;
+    a.need = b.need;
+    a.delay = c->opt.delay;
+    a.candMu = b.candMu;
+    a.muS = b.muS;
+    a.offs = b.offs;
+    a.subcnt = b.subcnt;
+    a.W = b.W;
+    a.tbase = b.tbase;
+    a.hbase = b.hbase;
+    a.layout = b.layout;
+    a.Mcs = b.Mcs;
+    a.work = refine ? nullptr : b.work;
+    a.tiles_mode = c->opt.tiles;
+    a.mma = mma ? 1 : 0;
+    a.ngroups = (int)bt.groups;
+    a.btab = b.btab;
+    // FP16 needs the lag products inside its range: int16 products reach 2^31
+    const int f = c->steps[k0].fmt;
+    const bool fp16 = c->opt.contract == DG_CONTRACT_FP16 || c->opt.contract == DG_CONTRACT_FP16X3;
+    a.zscale = (mma && fp16 && f == DG_IQ_CI16) ? 1.0f / 65536.0f : 1.0f;
+    a.wait_polls = g_tc_wait_polls.load(std::memory_order_relaxed);
+}
+
+static dg_status cdft_plan(dg_ctx *c, const CdftRun &r, const CdftBatch &a, size_t bi)
+{
+    CdftBufs &b = c->cd;
+    const auto &bt = r.L->batches[bi];
+    const bool mma = r.mma;
+    const int kplan = r.refine ? DG_K_REFINE : DG_K_CDFT_PLAN;
+    {
+        Timed t(c, kplan);
+        CK(c, launch_cdft_geo(a, c->stream));
+        CK(c, cudaMemsetAsync(b.g2b, 0xff, sizeof(int4) * (size_t)bt.groups, c->stream));
+        CK(c, launch_cdft_plan(a, (int)bt.nbt, c->stream));
+        CK(c, launch_cdft_tiles(a, c->stream));
+        t.done(mma ? 6 : 7);
+    }
+    return DG_OK;
+}
+
+// The batch's contraction; btab_only: only the tensor cores' DFT operand
+// tables (the contraction itself then runs in a launch shared by several
+// contexts).
+static dg_status cdft_contract(dg_ctx *c, const CdftRun &r, const CdftBatch &a, size_t bi, bool btab_only)
+{
+    CdftBufs &b = c->cd;
+    const auto &bt = r.L->batches[bi];
+    const int k0 = bt.k0, S = bt.S, M = r.Ms[bi];
+    const bool mma = r.mma, refine = r.refine;
+    const CdftLayout &L = *r.L;
+    const int f = c->steps[k0].fmt;
+    if (btab_only) {
+        Timed t(c, refine ? DG_K_REFINE : DG_K_CDFT_CONTRACT);
+        CK(c, launch_cdft_btab(a, c->opt.contract, b.btab, c->stream));
+        t.done(1);
+        return DG_OK;
+    }
+    {
+        Timed t(c, refine ? DG_K_REFINE : DG_K_CDFT_CONTRACT);
+        if (mma) {
+            // persistent: one CTA per SM, or fewer when the batch can
+            // have fewer tiles (the bound: lag tiles of every lag slot)
+            int64_t tiles_cap = 0;
+            for (int s = 0; s < S; ++s) {
+                const int slots = lag_slots(c->eph_host[k0 + s], c->fs, L.diam);
+                const int64_t B = (c->steps[k0 + s].n + M - 1) / M;
+                tiles_cap += B * ((slots + 127) / 128);
+            }
+            const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles_cap, c->sm_count));
+            // Hankel tiles (chunk <= 1024, on request) run in their own
+            // persistent kernel
+            const bool hk = M <= kLagTileMaxChunk && c->opt.tiles == DG_TILES_HANKEL;
+            int n = 0;
+            if (c->opt.tiles != DG_TILES_HANKEL || M > kLagTileMaxChunk) {
+                CK(c, launch_cdft_btab(a, c->opt.contract, b.btab, c->stream));
+                CK(c, launch_cdft_contract_mma(a, grid, f, c->opt.contract, c->stream));
+                n += 2;
+            }
+            if (hk) {
+                int64_t hk_cap = 0;
                 for (int s = 0; s < S; ++s) {
                     const int slots = lag_slots(c->eph_host[k0 + s], c->fs, L.diam);
                     const int64_t B = (c->steps[k0 + s].n + M - 1) / M;
-                    tiles_cap += B * ((slots + 127) / 128);
+                    hk_cap += B * ((slots + kHkLags - 1) / kHkLags);
                 }
-                const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles_cap, c->sm_count));
-                // Hankel tiles (chunk <= 1024, on request) run in their own
-                // persistent kernel
-                const bool hk = M <= kLagTileMaxChunk && c->opt.tiles == DG_TILES_HANKEL;
-                int n = 0;
-                if (c->opt.tiles != DG_TILES_HANKEL || M > kLagTileMaxChunk) {
-                    CK(c, launch_cdft_btab(a, c->opt.contract, b.btab, c->stream));
-                    CK(c, launch_cdft_contract_mma(a, grid, f, c->opt.contract, c->stream));
-                    n += 2;
-                }
-                if (hk) {
-                    int64_t hk_cap = 0;
-                    for (int s = 0; s < S; ++s) {
-                        const int slots = lag_slots(c->eph_host[k0 + s], c->fs, L.diam);
-                        const int64_t B = (c->steps[k0 + s].n + M - 1) / M;
-                        hk_cap += B * ((slots + kHkLags - 1) / kHkLags);
-                    }
-                    const int hgrid = (int)std::max<int64_t>(1, std::min<int64_t>(hk_cap, c->sm_count));
-                    CK(c, launch_cdft_contract_hankel(a, hgrid, f, c->opt.contract, c->stream));
-                    ++n;
-                }
-                t.done(n);
-            } else {
-                CK(c, launch_cdft_contract_fp32(a, (int)bt.nbt, f, c->stream));
-                t.done(1);
+                const int hgrid = (int)std::max<int64_t>(1, std::min<int64_t>(hk_cap, c->sm_count));
+                CK(c, launch_cdft_contract_hankel(a, hgrid, f, c->opt.contract, c->stream));
+                ++n;
             }
-        }
-        {
-            Timed t(c, refine ? DG_K_REFINE : DG_K_CDFT_COMBINE);
-            CK(c, launch_cdft_superchunk(a, (int)bt.nbt, c->stream));
-            CK(c, launch_cdft_combine(a, surf_f, c->stream));
-            t.done(2);
+            t.done(n);
+        } else {
+            CK(c, launch_cdft_contract_fp32(a, (int)bt.nbt, f, c->stream));
+            t.done(1);
         }
     }
+    return DG_OK;
+}
+
+static dg_status cdft_combine(dg_ctx *c, const CdftRun &r, const CdftBatch &a, size_t bi)
+{
+    const auto &bt = r.L->batches[bi];
+    const bool refine = r.refine;
+    float *surf_f = reinterpret_cast<float *>(r.surf);
+    {
+        Timed t(c, refine ? DG_K_REFINE : DG_K_CDFT_COMBINE);
+        CK(c, launch_cdft_superchunk(a, (int)bt.nbt, c->stream));
+        CK(c, launch_cdft_combine(a, surf_f, c->stream));
+        t.done(2);
+    }
+    return DG_OK;
+}
+
+static dg_status cdft_finish(dg_ctx *c, const CdftRun &r)
+{
+    const bool refine = r.refine;
     {
         Timed t(c, refine ? DG_K_REFINE : DG_K_ACCUM);
-        CK(c, launch_accumulate(surf, c->K, G, DG_PREC_FP32, out, c->stream));
+        CK(c, launch_accumulate(r.surf, c->K, r.G, DG_PREC_FP32, r.out, c->stream));
         t.done(1);
     }
     CK(c, cudaMemcpyAsync(c->err_h, c->err_d, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     return DG_OK;
+}
+
+
+dg_status run_surface_cdft(dg_ctx *c, const GridDev &gd, const double *xyz, int64_t G, void *surf, void *out,
+                           bool refine)
+{
+    CdftRun r;
+    r.gd = gd;
+    r.xyz = xyz;
+    r.G = G;
+    r.surf = surf;
+    r.out = out;
+    r.refine = refine;
+    dg_status st = cdft_setup(c, r);
+    if (st != DG_OK) return st;
+    for (size_t bi = 0; bi < r.L->batches.size(); ++bi) {
+        CdftBatch a{};
+        cdft_args(c, r, bi, a);
+        if ((st = cdft_plan(c, r, a, bi)) != DG_OK) return st;
+        if ((st = cdft_contract(c, r, a, bi, false)) != DG_OK) return st;
+        if ((st = cdft_combine(c, r, a, bi)) != DG_OK) return st;
+    }
+    return cdft_finish(c, r);
 }
 
 dg_status run_argmax(dg_ctx *c, const void *v, int64_t n, const GridDev &gd, ArgmaxResult *host)
@@ -886,8 +997,6 @@ dg_status dg_create(const dg_grid *grid, const dg_ephem *eph, int32_t K, double 
         return fail(nullptr, DG_EINVAL, "unknown precision %d", o.prec);
     if (o.algo != DG_ALGO_DIRECT && o.algo != DG_ALGO_CDFT) return fail(nullptr, DG_EINVAL, "unknown algorithm %d", o.algo);
     if (o.algo == DG_ALGO_CDFT) {
-        if (o.delay != DG_DELAY_INTEGER)
-            return fail(nullptr, DG_EUNSUPPORTED, "CDFT evaluates integer lags (Eq. 9) only");
         if (o.prec != DG_PREC_FP32) return fail(nullptr, DG_EUNSUPPORTED, "CDFT writes FP32 surfaces only");
         if (o.chunk != 0 && (o.chunk < 64 || o.chunk > kCdftMaxChunk || o.chunk % 64 != 0))
             return fail(nullptr, DG_EINVAL, "chunk must be 0 or a multiple of 64 in [64, %d]", kCdftMaxChunk);
@@ -1240,10 +1349,20 @@ static dg_status prepare_step(dg_ctx *c, int half)
 // refinement grid centred on it (built on the device), the refinement
 // surface and argmax, and the fix record copied to the pinned fix_host. No
 // host synchronisation and no allocation (prepare_step ran before).
+static dg_status step_device_post(dg_ctx *c, void *cost, double spacing_m, int half);
+
 static dg_status step_device(dg_ctx *c, void *cost, double spacing_m, int half)
 {
     dg_status st = run_surface(c, c->gd, c->xyz, c->G, c->surf, cost, false);
     if (st != DG_OK) return st;
+    return step_device_post(c, cost, spacing_m, half);
+}
+
+// The rest of a step once the surface is enqueued: its argmax, the
+// refinement, the fix record.
+static dg_status step_device_post(dg_ctx *c, void *cost, double spacing_m, int half)
+{
+    dg_status st = DG_OK;
     int nl = 0;
     CK(c, launch_argmax(cost, c->G, c->opt.prec, c->gd, c->amax_tmp, c->amax_res, &nl, c->stream));
     const ArgmaxResult *fine = nullptr;
@@ -1285,8 +1404,144 @@ static dg_status read_fix(dg_ctx *c, dg_fix *out)
 
 // Capture one step of each context as a branch of one graph: forked from and
 // joined to `stream`. Timing is off inside the capture.
+// The shared contraction rounds of a batch (dg_batch_capture): round r runs,
+// in one persistent launch, the contraction of the r-th snapshot batch of
+// every context that has one; each context plans and combines its batch on
+// its own stream around it.
+struct TcRounds {
+    std::vector<std::vector<int>> ctx;  // per round: the contexts taking part
+    std::vector<int> job_off;           // per round: its first job in jobs
+    std::vector<int> tile_off;          // per round: its prefix sums in job_tiles
+    TcJob *jobs = nullptr;              // device, every round's jobs in order
+    int *job_tiles = nullptr;           // device, per round n_r + 1 tile prefix sums
+    int fmt = 0, contract = 0;
+    unsigned wait_polls = 0;
+};
+
+// Every context on the tensor-core CDFT path (lag or row tiles), one capture
+// format and one contraction arithmetic across all of them: the batch's
+// contractions can share launches. The contexts have run one uncaptured
+// step, so their layouts and buffers exist. Builds the job tables on the
+// device (synchronously, before any capture).
+static dg_status tc_rounds(dg_ctx *const *ctxs, int n, TcRounds &R, bool &ok)
+{
+    ok = false;
+    if (n < 2) return DG_OK;
+    const int fmt = ctxs[0]->steps[0].fmt, contract = ctxs[0]->opt.contract;
+    size_t rounds = 0;
+    for (int i = 0; i < n; ++i) {
+        dg_ctx *c = ctxs[i];
+        if (c->opt.algo != DG_ALGO_CDFT || c->opt.contract == DG_CONTRACT_FP32 || c->opt.tiles == DG_TILES_HANKEL ||
+            c->opt.contract != contract || !c->cd.main_run.L)
+            return DG_OK;
+        for (int k = 0; k < c->K; ++k)
+            if (c->steps[k].fmt != fmt) return DG_OK;
+        rounds = std::max(rounds, c->cd.main_run.L->batches.size());
+    }
+    std::vector<TcJob> jobs;
+    R.ctx.assign(rounds, {});
+    for (size_t r = 0; r < rounds; ++r) {
+        R.job_off.push_back((int)jobs.size());
+        R.tile_off.push_back((int)(jobs.size() + r));
+        for (int i = 0; i < n; ++i) {
+            dg_ctx *c = ctxs[i];
+            if (r >= c->cd.main_run.L->batches.size()) continue;
+            CdftBatch a{};
+            cdft_args(c, c->cd.main_run, r, a);
+            jobs.push_back(tc_job(a, a.btab));
+            R.ctx[r].push_back(i);
+        }
+    }
+    dg_ctx *c0 = ctxs[0];
+    CK(c0, cudaMalloc((void **)&R.jobs, sizeof(TcJob) * jobs.size()));
+    CK(c0, cudaMalloc((void **)&R.job_tiles, sizeof(int) * (jobs.size() + rounds)));
+    CK(c0, cudaMemcpy(R.jobs, jobs.data(), sizeof(TcJob) * jobs.size(), cudaMemcpyHostToDevice));
+    R.fmt = fmt;
+    R.contract = contract;
+    R.wait_polls = g_tc_wait_polls.load(std::memory_order_relaxed);
+    ok = true;
+    return DG_OK;
+}
+
+static void tc_rounds_free(TcRounds &R)
+{
+    if (R.jobs) cudaFree(R.jobs);
+    if (R.job_tiles) cudaFree(R.job_tiles);
+    R.jobs = nullptr;
+    R.job_tiles = nullptr;
+}
+
+// The surfaces of a batch's contexts with shared contraction rounds (inside
+// a capture): setup, then per round every context's plan, one launch, every
+// context's combine; then each context's accumulation. Returns the shared
+// launches in *shared.
+static dg_status shared_surfaces(dg_ctx *const *ctxs, int n, void *const *costs, const TcRounds &R,
+                                 cudaStream_t stream, int64_t *shared)
+{
+    dg_ctx *c0 = ctxs[0];
+    std::vector<CdftRun> runs((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        dg_ctx *c = ctxs[i];
+        CdftRun &r = runs[(size_t)i];
+        r.gd = c->gd;
+        r.xyz = c->xyz;
+        r.G = c->G;
+        r.surf = c->surf;
+        r.out = costs[i];
+        r.refine = false;
+        dg_status st = cdft_setup(c, r);
+        if (st != DG_OK) return st;
+    }
+    std::vector<cudaEvent_t> evs;
+    auto event = [&](cudaEvent_t *e) {
+        const cudaError_t x = cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+        if (x == cudaSuccess) evs.push_back(*e);
+        return x;
+    };
+    dg_status st = DG_OK;
+    cudaError_t e = cudaSuccess;
+    for (size_t rd = 0; rd < R.ctx.size() && st == DG_OK && e == cudaSuccess; ++rd) {
+        const std::vector<int> &part = R.ctx[rd];
+        for (int i : part) {
+            dg_ctx *c = ctxs[i];
+            CdftBatch a{};
+            cdft_args(c, runs[(size_t)i], rd, a);
+            if ((st = cdft_plan(c, runs[(size_t)i], a, rd)) != DG_OK) break;
+            if ((st = cdft_contract(c, runs[(size_t)i], a, rd, true)) != DG_OK) break;
+            cudaEvent_t ev;
+            if ((e = event(&ev)) != cudaSuccess || (e = cudaEventRecord(ev, c->stream)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(stream, ev, 0)) != cudaSuccess)
+                break;
+        }
+        if (st != DG_OK || e != cudaSuccess) break;
+        const int nr = (int)part.size();
+        TcJob *jobs = R.jobs + R.job_off[rd];
+        int *tiles = R.job_tiles + R.tile_off[rd];
+        if ((e = launch_tc_job_tiles(jobs, nr, tiles, stream)) != cudaSuccess) break;
+        if ((e = launch_cdft_contract_jobs(jobs, nr, tiles, c0->sm_count, R.fmt, R.contract, R.wait_polls, stream)) !=
+            cudaSuccess)
+            break;
+        *shared += 2;
+        cudaEvent_t done;
+        if ((e = event(&done)) != cudaSuccess || (e = cudaEventRecord(done, stream)) != cudaSuccess) break;
+        for (int i : part) {
+            dg_ctx *c = ctxs[i];
+            if ((e = cudaStreamWaitEvent(c->stream, done, 0)) != cudaSuccess) break;
+            CdftBatch a{};
+            cdft_args(c, runs[(size_t)i], rd, a);
+            if ((st = cdft_combine(c, runs[(size_t)i], a, rd)) != DG_OK) break;
+        }
+    }
+    for (int i = 0; i < n && st == DG_OK && e == cudaSuccess; ++i) st = cdft_finish(ctxs[i], runs[(size_t)i]);
+    for (auto &x : evs) cudaEventDestroy(x);
+    if (st != DG_OK) return st;
+    if (e != cudaSuccess) return fail(c0, DG_ECUDA, "shared contraction rounds: %s", cudaGetErrorString(e));
+    return DG_OK;
+}
+
 static dg_status capture_steps(dg_ctx *const *ctxs, int n, void *const *costs, double spacing_m, const int *half,
-                               cudaStream_t stream, cudaGraphExec_t *exec, int64_t *launches)
+                               cudaStream_t stream, cudaGraphExec_t *exec, int64_t *launches,
+                               const TcRounds *rounds = nullptr)
 {
     dg_ctx *c0 = ctxs[0];
     cudaEvent_t fork = nullptr;
@@ -1296,23 +1551,27 @@ static dg_status capture_steps(dg_ctx *const *ctxs, int n, void *const *costs, d
     std::vector<int> timing((size_t)n);
     std::vector<int64_t> l0((size_t)n);
     dg_status st = DG_OK;
+    int64_t shared = 0;
     cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) e = cudaEventRecord(fork, stream);
+    for (int i = 0; i < n; ++i) {
+        timing[i] = ctxs[i]->opt.timing;
+        ctxs[i]->opt.timing = 0;
+        l0[i] = ctxs[i]->launches;
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ctxs[i]->stream, fork, 0);
+    }
+    if (rounds && e == cudaSuccess) st = shared_surfaces(ctxs, n, costs, *rounds, stream, &shared);
     for (int i = 0; i < n && e == cudaSuccess && st == DG_OK; ++i) {
         dg_ctx *c = ctxs[i];
-        timing[i] = c->opt.timing;
-        c->opt.timing = 0;
-        l0[i] = c->launches;
-        e = cudaStreamWaitEvent(c->stream, fork, 0);
-        if (e == cudaSuccess) st = step_device(c, costs[i], spacing_m, half[i]);
-        if (e == cudaSuccess && st == DG_OK) e = cudaEventRecord(join[i], c->stream);
+        st = rounds ? step_device_post(c, costs[i], spacing_m, half[i]) : step_device(c, costs[i], spacing_m, half[i]);
+        if (st == DG_OK) e = cudaEventRecord(join[i], c->stream);
         if (e == cudaSuccess && st == DG_OK) e = cudaStreamWaitEvent(stream, join[i], 0);
-        c->opt.timing = timing[i];
     }
+    for (int i = 0; i < n; ++i) ctxs[i]->opt.timing = timing[i];
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(stream, &g);
     if (e == cudaSuccess) e = e2;
-    int64_t total = 0;
+    int64_t total = shared;
     for (int i = 0; i < n; ++i) {
         const int64_t d = ctxs[i]->launches - l0[i];
         total += d;
@@ -1386,6 +1645,8 @@ struct dg_batch {
     cudaGraphExec_t graph = nullptr;
     int64_t launches = 0;
     std::string err;
+    TcRounds rounds;       // shared contraction rounds (none: per-context launches)
+    bool shared = false;
 };
 
 extern "C" {
@@ -1427,10 +1688,14 @@ dg_status dg_batch_capture(dg_ctx *const *ctxs, int32_t n, void *const *costs, d
             return fail(nullptr, DG_ECUDA, "event creation failed");
         }
     b->stream = s;
-    dg_status st = capture_steps(ctxs, n, costs, spacing_m, half.data(), s, &b->graph, &b->launches);
+    dg_status st = tc_rounds(ctxs, n, b->rounds, b->shared);
+    if (st == DG_OK)
+        st = capture_steps(ctxs, n, costs, spacing_m, half.data(), s, &b->graph, &b->launches,
+                           b->shared ? &b->rounds : nullptr);
     if (st != DG_OK) {
         const std::string m = ctxs[0]->err;
         for (auto &e : b->ready) cudaEventDestroy(e);
+        tc_rounds_free(b->rounds);
         delete b;
         return fail(nullptr, st, "%s", m.c_str());
     }
@@ -1484,9 +1749,12 @@ dg_status dg_batch_destroy(dg_batch *b)
     if (b->graph) cudaGraphExecDestroy(b->graph);
     for (auto &e : b->ready)
         if (e) cudaEventDestroy(e);
+    tc_rounds_free(b->rounds);
     delete b;
     return DG_OK;
 }
+
+int32_t dg_batch_rounds(const dg_batch *b) { return b && b->shared ? (int32_t)b->rounds.ctx.size() : 0; }
 
 // ---------------------------------------------------------------------------
 // Autotuning of the CDFT launch shape
@@ -1738,6 +2006,9 @@ dg_status dg_destroy(dg_ctx *c)
     fr(c->cd.nuS);
     fr(c->cd.g2b);
     fr(c->cd.candNu);
+    fr(c->cd.candMu);
+    fr(c->cd.muS);
+    fr(c->cd.need);
     fr(c->cd.xyzf);
     fr(c->cd.ephf);
     fr(c->cd.count);

@@ -82,17 +82,22 @@ __global__ void __launch_bounds__(256, 4) k_cdft_geo(CdftBatch a)
         geometry_df({xf[p], xf[a.G + p]}, {xf[2 * a.G + p], xf[3 * a.G + p]}, {xf[4 * a.G + p], xf[5 * a.G + p]},
                     ed, fsc, {a.ilf_hi, a.ilf_lo}, D, nuf);
         int L = INT_MIN;
+        float mu = 0.f;
         bool ok = fabsf(D.hi) < 1.0e9f;
-        if (ok && !round_df(D, L)) {
+        if (ok && !(a.delay == DG_DELAY_INTEGER ? round_df(D, L) : floor_df(D, L, mu))) {
             double e[12], D64, nu64;
             for (int t = 0; t < 12; ++t) e[t] = a.eph[12 * (size_t)s + t];
             geometry(a.xyz[p], a.xyz[a.G + p], a.xyz[2 * a.G + p], e, a.fs, a.lambda, D64, nu64);
             ok = fabs(D64) < 1.0e9;
-            if (ok) L = (int)round(D64);
+            if (ok) {
+                L = lag_of(D64, a.delay);
+                mu = (float)(D64 - (double)L);
+            }
         }
         if (ok) {
-            lo = min(lo, L);
-            hi = max(hi, L);
+            // Lagrange4 also needs the lags L - 1 and L + 2 of the stencil
+            lo = min(lo, a.delay == DG_DELAY_INTEGER ? L : L - 1);
+            hi = max(hi, a.delay == DG_DELAY_INTEGER ? L : L + 2);
             flo = min(flo, fkey(nuf));
             fhi = max(fhi, fkey(nuf));
         } else {
@@ -100,6 +105,7 @@ __global__ void __launch_bounds__(256, 4) k_cdft_geo(CdftBatch a)
         }
         a.candL[(size_t)s * a.G + p] = L;
         a.candNu[(size_t)s * a.G + p] = nuf;
+        if (a.delay != DG_DELAY_INTEGER) a.candMu[(size_t)s * a.G + p] = mu;
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
@@ -268,6 +274,10 @@ __global__ void __launch_bounds__(1024) k_cdft_scan(CdftBatch a)
     int oc = t ? s_c[t - 1] : 0, og = t ? s_g[t - 1] : 0;
     for (int i = b0; i < b1; ++i) {
         const int b = b_first + i;
+        bool nd = a.count[b] > 0;
+        if (a.delay != DG_DELAY_INTEGER)  // lags of the stencils of buckets i - 2 .. i + 1
+            for (int d = -2; d <= 1 && !nd; ++d) nd = i + d >= 0 && i + d < NB && a.count[b + d] > 0;
+        a.need[b] = nd ? 1 : 0;
         a.offs[b] = oc;
         const int n = a.count[b];
         const int ng = (n + kCdftCombineGroup - 1) / kCdftCombineGroup;
@@ -349,6 +359,14 @@ __global__ void __launch_bounds__(256) k_cdft_scatter(CdftBatch a)
         a.order[so + rank[k]] = (int)tile_node(a, k);
         a.nuS[so + rank[k]] = nu[k];
     }
+    if (a.delay != DG_DELAY_INTEGER) {  // the fractional delays in the same order
+#pragma unroll
+        for (int k = 0; k < kTilePer; ++k)
+            if (l[k] != INT_MIN) nu[k] = a.candMu[so + tile_node(a, k)];
+#pragma unroll
+        for (int k = 0; k < kTilePer; ++k)
+            if (l[k] != INT_MIN) a.muS[so + rank[k]] = nu[k];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -377,7 +395,7 @@ __global__ void __launch_bounds__(256) k_cdft_contract_f32(CdftBatch a)
     __shared__ __align__(16) float2 zs[kCtSub][kCtChunks + 1];  // +1: staging stores 2-way, not 32-way
     __shared__ __align__(16) float2 vs[kCtSub][64];
     const int b = blockIdx.x;
-    if (a.count[b] == 0) return;
+    if (!a.need[b]) return;
     const int s = step_of(a.bbase, a.S, b);
     const StepDesc sd = a.sd[s];
     const int N = sd.n, M = a.M;
@@ -451,7 +469,7 @@ __global__ void __launch_bounds__(256) k_cdft_superchunk(CdftBatch a, int NBT)
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= (int64_t)NBT * 64) return;
     const int bg = (int)(t >> 6), q = (int)(t & 63);
-    if (a.count[bg] == 0) return;  // no candidate: W rows were not written
+    if (!a.need[bg]) return;  // no candidate's stencil reaches it: W rows were not written
     const int s = step_of(a.bbase, a.S, bg);
     const int M = a.M, R = a.Mcs[s] / a.M;
     if (R == 1) return;
@@ -497,6 +515,10 @@ __global__ void __launch_bounds__(256) k_cdft_superchunk(CdftBatch a, int NBT)
 // interpolates the DFT of every super-chunk at its own FDOA from the six
 // bins around it (Lagrange, the FDOA between the third and fourth),
 // rotates it by the super-chunk's phase e^{j 2 pi nu c Mc}, and sums.
+// With the Lagrange4 fractional delay the candidate's correlation is, by
+// linearity, sum_{m=-1..2} w_m(mu) C_{L+m}(nu) with the 4-tap weights of its
+// fractional delay mu: the same sum over the buckets of lags L - 1 .. L + 2,
+// each weighted.
 // ---------------------------------------------------------------------------
 constexpr int kSeg = 32;
 
@@ -516,18 +538,22 @@ __global__ void __launch_bounds__(kCdftCombineThreads) k_cdft_combine(CdftBatch 
     const int M = a.Mcs[s];
     const int B = (a.sd[s].n + M - 1) / M;
     const float nbase = a.nubase[s], inv = 1.0f / a.delta[s];
-    const float *Wb = a.W + (size_t)b * a.Bmax * 128;
+    const bool frac = a.delay != DG_DELAY_INTEGER;
+    const int mlo = frac ? -1 : 0, mhi = frac ? 2 : 0;  // lag offsets of the stencil
     // the first segment of DFTs depends on the bucket only: its loads travel
     // together with the candidates' below
-    for (int i = threadIdx.x; i < min(kSeg, B) * 64; i += kCdftCombineThreads) {
-        const int ch = i >> 6, q = i & 63;
-        const float *row = Wb + (size_t)ch * 128;
-        ws[ch][q] = make_float2(row[q], row[64 + q]);
+    {
+        const float *Wb = a.W + (size_t)(b + mlo) * a.Bmax * 128;
+        for (int i = threadIdx.x; i < min(kSeg, B) * 64; i += kCdftCombineThreads) {
+            const int ch = i >> 6, q = i & 63;
+            const float *row = Wb + (size_t)ch * 128;
+            ws[ch][q] = make_float2(row[q], row[64 + q]);
+        }
     }
     const size_t sp0 = (size_t)s * a.G + gr.z;
     int c[kCdftCombinePer], q0[kCdftCombinePer];
-    float w[kCdftCombinePer][6], ex[kCdftCombinePer], ey[kCdftCombinePer], px[kCdftCombinePer],
-        py[kCdftCombinePer], cx[kCdftCombinePer], cy[kCdftCombinePer], nu[kCdftCombinePer];
+    float w[kCdftCombinePer][6], lw[kCdftCombinePer][4], ex[kCdftCombinePer], ey[kCdftCombinePer],
+        px[kCdftCombinePer], py[kCdftCombinePer], cx[kCdftCombinePer], cy[kCdftCombinePer], nu[kCdftCombinePer];
 #pragma unroll
     for (int k = 0; k < kCdftCombinePer; ++k) {
         const int j = threadIdx.x + k * kCdftCombineThreads;
@@ -548,45 +574,59 @@ __global__ void __launch_bounds__(kCdftCombineThreads) k_cdft_combine(CdftBatch 
         w[k][3] = (s21 * t * t23) * (1.f / 12.f);
         w[k][4] = -(s21 * t01 * b3) * (1.f / 24.f);
         w[k][5] = (s21 * t01 * b2) * (1.f / 120.f);
+        // the 4-tap weights of the fractional delay mu (lags L - 1 .. L + 2)
+        const float mu = (frac && act) ? a.muS[sp0 + j] : 0.f;
+        lw[k][0] = frac ? -mu * (mu - 1.f) * (mu - 2.f) * (1.f / 6.f) : 1.f;
+        lw[k][1] = (mu + 1.f) * (mu - 1.f) * (mu - 2.f) * 0.5f;
+        lw[k][2] = -(mu + 1.f) * mu * (mu - 2.f) * 0.5f;
+        lw[k][3] = (mu + 1.f) * mu * (mu - 1.f) * (1.f / 6.f);
         // chunk-to-chunk phase step e^{j 2 pi nu M}
         sincospif(2.0f * frac_mul(nu[k], (float)M), &ey[k], &ex[k]);
         cx[k] = cy[k] = 0.f;
     }
-    for (int s0 = 0; s0 < B; s0 += kSeg) {
-        const int slen = min(kSeg, B - s0);
-        if (s0 > 0) {
-            __syncthreads();
-            for (int i = threadIdx.x; i < slen * 64; i += kCdftCombineThreads) {
-                const int ch = i >> 6, q = i & 63;
-                const float *row = Wb + (size_t)(s0 + ch) * 128;
-                ws[ch][q] = make_float2(row[q], row[64 + q]);
-            }
-        }
-        __syncthreads();
+    for (int m = mlo; m <= mhi; ++m) {
+        const float *Wb = a.W + (size_t)(b + m) * a.Bmax * 128;
+        float wm[kCdftCombinePer][6];  // bin weights times the lag's weight
 #pragma unroll
-        for (int k = 0; k < kCdftCombinePer; ++k) {
-            // phase of the segment's first sample, e^{j 2 pi nu s0 M}
-            if (s0 == 0) {
-                px[k] = 1.f;
-                py[k] = 0.f;
-            } else {
-                sincospif(2.0f * frac_mul(nu[k], (float)s0 * (float)M), &py[k], &px[k]);
-            }
-#pragma unroll 4
-            for (int i = 0; i < slen; ++i) {
-                const float2 *wr = &ws[i][q0[k] - 2];
-                float zx = 0.f, zy = 0.f;
+        for (int k = 0; k < kCdftCombinePer; ++k)
 #pragma unroll
-                for (int e = 0; e < 6; ++e) {
-                    const float2 v = wr[e];
-                    zx = fmaf(w[k][e], v.x, zx);
-                    zy = fmaf(w[k][e], v.y, zy);
+            for (int e = 0; e < 6; ++e) wm[k][e] = w[k][e] * lw[k][m - mlo];
+        for (int s0 = 0; s0 < B; s0 += kSeg) {
+            const int slen = min(kSeg, B - s0);
+            if (s0 > 0 || m > mlo) {
+                __syncthreads();
+                for (int i = threadIdx.x; i < slen * 64; i += kCdftCombineThreads) {
+                    const int ch = i >> 6, q = i & 63;
+                    const float *row = Wb + (size_t)(s0 + ch) * 128;
+                    ws[ch][q] = make_float2(row[q], row[64 + q]);
                 }
-                cx[k] = fmaf(px[k], zx, fmaf(-py[k], zy, cx[k]));
-                cy[k] = fmaf(px[k], zy, fmaf(py[k], zx, cy[k]));
-                const float nx = fmaf(px[k], ex[k], -py[k] * ey[k]);
-                py[k] = fmaf(px[k], ey[k], py[k] * ex[k]);
-                px[k] = nx;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < kCdftCombinePer; ++k) {
+                // phase of the segment's first sample, e^{j 2 pi nu s0 M}
+                if (s0 == 0) {
+                    px[k] = 1.f;
+                    py[k] = 0.f;
+                } else {
+                    sincospif(2.0f * frac_mul(nu[k], (float)s0 * (float)M), &py[k], &px[k]);
+                }
+#pragma unroll 4
+                for (int i = 0; i < slen; ++i) {
+                    const float2 *wr = &ws[i][q0[k] - 2];
+                    float zx = 0.f, zy = 0.f;
+#pragma unroll
+                    for (int e = 0; e < 6; ++e) {
+                        const float2 v = wr[e];
+                        zx = fmaf(wm[k][e], v.x, zx);
+                        zy = fmaf(wm[k][e], v.y, zy);
+                    }
+                    cx[k] = fmaf(px[k], zx, fmaf(-py[k], zy, cx[k]));
+                    cy[k] = fmaf(px[k], zy, fmaf(py[k], zx, cy[k]));
+                    const float nx = fmaf(px[k], ex[k], -py[k] * ey[k]);
+                    py[k] = fmaf(px[k], ey[k], py[k] * ex[k]);
+                    px[k] = nx;
+                }
             }
         }
     }
@@ -727,6 +767,7 @@ cudaError_t launch_cdft_plan(const CdftBatch &a, int NBT, cudaStream_t st)
     cudaError_t e;
     if ((e = cudaMemsetAsync(a.count, 0, sizeof(int) * (size_t)NBT, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(a.subcnt, 0, sizeof(int) * (size_t)NBT, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(a.need, 0, sizeof(int) * (size_t)NBT, st)) != cudaSuccess) return e;
     const int64_t tiles = (int64_t)((a.nrows + kHistTile - 1) / kHistTile) * ((a.nlon + kHistTile - 1) / kHistTile);
     dim3 gh((unsigned)tiles, (unsigned)a.S);
     k_cdft_hist<<<gh, 256, 0, st>>>(a);

@@ -582,12 +582,22 @@ struct SnapCache {  // per-snapshot tables of the batch, in shared memory
 struct TileInfo {
     int s, ltile, N, Bs, NB, lay, lb, bch, Lmin, bb;
     int rt, rNB, rl0;  // row tiles: tile index among them, their lags, first lag bucket
+    int M, job;        // the job's chunk, and the job (0 in a single-job launch)
     StepDesc sd;
 };
 
-__device__ __forceinline__ TileInfo tile_info(const SnapCache &c, int S, int M, int tile)
+// A job's per-snapshot tables, in shared memory (the single job of a launch,
+// cached) or in global memory (a launch over several jobs).
+struct JobTables {
+    const int *tbase, *bbase, *lr, *layout;
+    const StepDesc *sd;
+};
+
+__device__ __forceinline__ TileInfo tile_info(const JobTables &c, int S, int M, int tile)
 {
     TileInfo t;
+    t.M = M;
+    t.job = 0;
     t.s = step_of_tile(c.tbase, S, tile);
     t.ltile = tile - c.tbase[t.s];
     t.sd = c.sd[t.s];
@@ -734,7 +744,9 @@ __device__ __forceinline__ bool producers_sync_or(bool flag)
 }
 
 template <int FMT, int DT, int P>
-__global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
+__global__ void __launch_bounds__(kWsThreads, 1)
+    k_cdft_contract_tc(TcJob one, const TcJob *__restrict__ jobs, int njobs, const int *__restrict__ job_tiles,
+                       unsigned wait_polls)
 {
     constexpr int NA = ring_a<P>(), NB = ring_b<P>();
     constexpr int kSt = 2 * P * kBlockBytes;  // bytes of one stage's A (or B) blocks
@@ -749,18 +761,35 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
     unsigned char *sB0 = smem;
     float2 *sy1 = reinterpret_cast<float2 *>(smem + NB * kSt);
     float2 *sy2 = sy1 + kLagTileMaxChunk;
-    const int M = a.M, NJ = M / kKS, S = a.S;
-
-    for (int i = threadIdx.x; i <= S; i += blockDim.x) {
-        sc.tbase[i] = a.tbase[i];
-        sc.bbase[i] = a.bbase[i];
-        if (i < S) {
-            sc.lr[2 * i] = a.lr[2 * i];
-            sc.lr[2 * i + 1] = a.lr[2 * i + 1];
-            sc.layout[i] = a.layout[i];
-            sc.sd[i] = a.sd[i];
+    // one job: its per-snapshot tables cached in shared memory; several
+    // jobs: each tile is resolved to its job through job_tiles
+    const bool multi = jobs != nullptr;
+    if (!multi)
+        for (int i = threadIdx.x; i <= one.S; i += blockDim.x) {
+            sc.tbase[i] = one.tbase[i];
+            sc.bbase[i] = one.bbase[i];
+            if (i < one.S) {
+                sc.lr[2 * i] = one.lr[2 * i];
+                sc.lr[2 * i + 1] = one.lr[2 * i + 1];
+                sc.layout[i] = one.layout[i];
+                sc.sd[i] = one.sd[i];
+            }
         }
-    }
+    const JobTables single_tables{sc.tbase, sc.bbase, sc.lr, sc.layout, sc.sd};
+    auto resolve = [&](int tile) -> TileInfo {
+        if (!multi) return tile_info(single_tables, one.S, one.M, tile);
+        int lo = 0, hi = njobs - 1;  // the job whose tile range holds the tile
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (job_tiles[mid] <= tile) lo = mid; else hi = mid - 1;
+        }
+        const TcJob &J = jobs[lo];
+        const JobTables tb{J.tbase, J.bbase, J.lr, J.layout, J.sd};
+        TileInfo t = tile_info(tb, J.S, J.M, tile - job_tiles[lo]);
+        t.job = lo;
+        return t;
+    };
+    auto job = [&](int j) -> const TcJob & { return multi ? jobs[j] : one; };
     if (threadIdx.x == 0) {
         for (int i = 0; i < NA; ++i) {
             mbar_init(smem_u32(&full_a[i]), kProducerWarps);
@@ -784,10 +813,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
     __syncthreads();
     tc_after_sync();
     const uint32_t tmem = tmem_slot;
-    const int ntiles = sc.tbase[S];
+    const int ntiles = multi ? job_tiles[njobs] : sc.tbase[one.S];
     const int mine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const float zs = a.zscale;
-    const uint32_t wl = a.wait_polls ? a.wait_polls : kWaitLimit;  // poll limit of the pipeline's waits
+    const uint32_t wl = wait_polls ? wait_polls : kWaitLimit;  // poll limit of the pipeline's waits
 
     if (warp < kProducerWarps) {
         // ---------------- producers: lane l of warp w forms row 32 (w % 4) + l
@@ -799,9 +827,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
         const uint32_t tlane = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(kAccCols + 4 * sg);
         RawIQ<FMT> pf;
         bool have_pf = false;  // pf holds the window about to start
-        // stages per window of a lag tile (the whole chunk when M <= 1024)
-        const int SWJ = window_len(M) / kKS;
         bool stop = false;
+        uint32_t g0 = 0;  // stages of the tiles before this one
         // A slot whose lag products are stored but not yet announced: its
         // tcgen05.st completes while the next stage is formed, and the
         // arrival on its full_a barrier follows then
@@ -817,7 +844,11 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
         };
         for (int it = 0; it < mine && !stop; ++it) {
             const int tile = (int)blockIdx.x + it * (int)gridDim.x;
-            const TileInfo t = tile_info(sc, S, M, tile);
+            const TileInfo t = resolve(tile);
+            const int M = t.M, NJ = M / kKS;
+            const int SWJ = window_len(M) / kKS;  // stages per window of a lag tile
+            const float zs = job(t.job).zscale;
+            const int *need = job(t.job).need;
             int pL = 0, pn0 = 0;
             bool pv = false;
             if (!t.lay) {
@@ -827,10 +858,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                     const int bl = t.rl0 + (int)(g / t.Bs);
                     pn0 = (int)(g % t.Bs) * M + 8 * sg;
                     pL = t.Lmin + bl;
-                    pv = a.count[t.bb + bl] > 0;
+                    pv = need[t.bb + bl] != 0;
                 }
             }
-            const uint32_t g0 = (uint32_t)it * (uint32_t)NJ;
             const int NW = t.lay ? NJ / SWJ : 1;          // windows of this tile
             const int JW = t.lay ? SWJ : NJ;              // stages per window
             for (int w = 0; w < NW; ++w) {
@@ -854,9 +884,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                     prefetch_windows<FMT>(t, M, w + 1, pf, threadIdx.x);
                     have_pf = true;
                 } else if (w + 1 == NW && it + 1 < mine) {
-                    const TileInfo tn = tile_info(sc, S, M, tile + (int)gridDim.x);
+                    const TileInfo tn = resolve(tile + (int)gridDim.x);
                     if (tn.lay) {
-                        prefetch_windows<FMT>(tn, M, 0, pf, threadIdx.x);
+                        prefetch_windows<FMT>(tn, tn.M, 0, pf, threadIdx.x);
                         have_pf = true;
                     }
                 }
@@ -922,6 +952,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                 pend = slot;
             }
             }
+            g0 += (uint32_t)NJ;
         }
         announce();
     } else if (warp == kLoadWarp) {
@@ -931,10 +962,12 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
         // across tile boundaries
         if (lane == 0) {
             uint32_t issued = 0;  // stages whose copy has been issued
+            uint32_t g0 = 0;
             for (int it = 0; it < mine && !s_abort; ++it) {
-                const uint32_t g0 = (uint32_t)it * (uint32_t)NJ;
-                const int s = step_of_tile(sc.tbase, S, (int)blockIdx.x + it * (int)gridDim.x);
-                const unsigned char *bsrc = reinterpret_cast<const unsigned char *>(a.btab) + (size_t)s * NJ * kSt;
+                const TileInfo t = resolve((int)blockIdx.x + it * (int)gridDim.x);
+                const int NJ = t.M / kKS;
+                const unsigned char *bsrc =
+                    reinterpret_cast<const unsigned char *>(job(t.job).btab) + (size_t)t.s * NJ * kSt;
                 for (int j = 0; j < NJ; ++j) {
                     const uint32_t g = g0 + (uint32_t)j;
                     const int slot = (int)(g % NB);
@@ -946,6 +979,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                     bulk_g2s(smem_u32(sB0 + slot * kSt), bsrc + (size_t)j * kSt, kSt, smem_u32(&full_b[slot]));
                     issued = g + 1;
                 }
+                g0 += (uint32_t)NJ;
             }
             // after an abort, the copies still in flight (at most the last NB
             // issued) land before the CTA leaves: shared memory is not
@@ -961,8 +995,9 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
         if (lane == 0) {
             const uint32_t id = idesc<DT>();
             bool alive = true;
+            uint32_t g0 = 0;
             for (int it = 0; it < mine && alive && !s_abort; ++it) {
-                const uint32_t g0 = (uint32_t)it * (uint32_t)NJ;
+                const int NJ = (multi ? resolve((int)blockIdx.x + it * (int)gridDim.x).M : one.M) / kKS;
                 // the accumulator of this tile was drained (tile it - 2)
                 const int acc = it & 1;
                 if (it >= 2 && !mbar_wait(smem_u32(&acc_empty[acc]), ((uint32_t)(it / 2) - 1) & 1u, wl)) {
@@ -998,6 +1033,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                     mma_commit(smem_u32(&empty_b[sb]));
                     if (j == NJ - 1) mma_commit(smem_u32(&acc_full[acc]));  // the tile's accumulator is final
                 }
+                g0 += (uint32_t)NJ;
             }
             if (!alive) s_abort = 1;
             // completes once every MMA this thread issued is done
@@ -1014,29 +1050,33 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
                 break;
             }
             tc_after_sync();
-            const TileInfo t = tile_info(sc, S, M, (int)blockIdx.x + d * (int)gridDim.x);
+            const TileInfo t = resolve((int)blockIdx.x + d * (int)gridDim.x);
+            const TcJob &J = job(t.job);
+            const int *need = J.need;
+            const int Bmax = J.Bmax;
+            float *W = J.W;
             const int row = 32 * q + lane;
             bool valid;
             int64_t wrow;
             if (t.lay) {
                 const int bl = t.lb * kRows + row;
-                valid = bl < t.NB && a.count[t.bb + bl] > 0;
-                wrow = ((int64_t)(t.bb + bl) * a.Bmax + t.bch) * 128;
+                valid = bl < t.NB && need[t.bb + bl] != 0;
+                wrow = ((int64_t)(t.bb + bl) * Bmax + t.bch) * 128;
             } else {
                 const int64_t g = (int64_t)t.rt * kRows + row;
                 valid = g < (int64_t)t.rNB * t.Bs;
                 const int bl = valid ? t.rl0 + (int)(g / t.Bs) : 0;
-                valid = valid && a.count[t.bb + bl] > 0;
-                wrow = ((int64_t)(t.bb + bl) * a.Bmax + (valid ? g % t.Bs : 0)) * 128;
+                valid = valid && need[t.bb + bl] != 0;
+                wrow = ((int64_t)(t.bb + bl) * Bmax + (valid ? g % t.Bs : 0)) * 128;
             }
-            const float inv = 1.0f / a.zscale;
+            const float inv = 1.0f / J.zscale;
             const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(128 * acc);
 #pragma unroll 1
             for (int c = 0; c < 128; c += 32) {
                 uint32_t r[32];
                 tmem_ld32(tb + (uint32_t)c, r);
                 if (valid) {
-                    float4 *w = reinterpret_cast<float4 *>(a.W + wrow + c);
+                    float4 *w = reinterpret_cast<float4 *>(W + wrow + c);
 #pragma unroll
                     for (int v = 0; v < 8; ++v)
                         w[v] = make_float4(__uint_as_float(r[4 * v]) * inv, __uint_as_float(r[4 * v + 1]) * inv,
@@ -1052,7 +1092,10 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_cdft_contract_tc(CdftBatch a)
     // after an abort, every MMA issued must complete before TMEM is freed
     if (s_abort && threadIdx.x == 0) {
         mbar_wait(smem_u32(&drained), 0u);
-        atomicOr(a.err, ERR_TIMEOUT);
+        if (multi)  // every job's surface is incomplete
+            for (int j = 0; j < njobs; ++j) atomicOr(jobs[j].err, ERR_TIMEOUT);
+        else
+            atomicOr(one.err, ERR_TIMEOUT);
     }
     tc_before_sync();
     __syncthreads();
@@ -1372,7 +1415,7 @@ __global__ void __launch_bounds__(kHkThreads, 1) k_cdft_contract_hk(CdftBatch a)
 #pragma unroll 4
                 for (int u = 0; u < 32; ++u) {
                     const int bl = t.lb * kHkLags + r + 8 * (nb + u);
-                    if (bl < t.NB && a.count[t.bb + bl] > 0)
+                    if (bl < t.NB && a.need[t.bb + bl] != 0)
                         a.W[((int64_t)(t.bb + bl) * a.Bmax + t.bch) * 128 + row] = __uint_as_float(v[u]) * inv;
                 }
             }
@@ -1409,14 +1452,14 @@ cudaError_t launch_cdft_btab(const CdftBatch &a, int mode, void *btab, cudaStrea
 size_t cdft_btab_bytes(int mode, int M) { return (size_t)(M / kKS) * 2 * (mode >= DG_CONTRACT_BF16X3 ? 2 : 1) * kBlockBytes; }
 
 template <int FMT, int DT, int P>
-static cudaError_t launch_mma(const CdftBatch &a, int grid, cudaStream_t st)
+static cudaError_t launch_mma(const TcJob &one, const TcJob *jobs, int njobs, const int *job_tiles, int grid,
+                              unsigned wait_polls, cudaStream_t st)
 {
-    // lag tiles stage M + 128 samples; k_cdft_tiles gives batches with
-    // M > kLagTileMaxChunk row tiles only
+    // lag tiles stage windows of kLagTileMaxChunk + 128 samples
     const int smem = tc_smem_bytes<P>();
     cudaError_t e = cudaFuncSetAttribute(k_cdft_contract_tc<FMT, DT, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    k_cdft_contract_tc<FMT, DT, P><<<(unsigned)grid, kWsThreads, smem, st>>>(a);
+    k_cdft_contract_tc<FMT, DT, P><<<(unsigned)grid, kWsThreads, smem, st>>>(one, jobs, njobs, job_tiles, wait_polls);
     return cudaGetLastError();
 }
 
@@ -1441,23 +1484,73 @@ static cudaError_t launch_hk_fmt(const CdftBatch &a, int grid, int fmt, cudaStre
 }
 
 template <int DT, int P>
-static cudaError_t launch_fmt(const CdftBatch &a, int tiles, int fmt, cudaStream_t st)
+static cudaError_t launch_fmt(const TcJob &one, const TcJob *jobs, int njobs, const int *job_tiles, int grid,
+                              unsigned wait_polls, int fmt, cudaStream_t st)
 {
     switch (fmt) {
-    case DG_IQ_C64: return launch_mma<DG_IQ_C64, DT, P>(a, tiles, st);
-    case DG_IQ_CI16: return launch_mma<DG_IQ_CI16, DT, P>(a, tiles, st);
-    default: return launch_mma<DG_IQ_CI8, DT, P>(a, tiles, st);
+    case DG_IQ_C64: return launch_mma<DG_IQ_C64, DT, P>(one, jobs, njobs, job_tiles, grid, wait_polls, st);
+    case DG_IQ_CI16: return launch_mma<DG_IQ_CI16, DT, P>(one, jobs, njobs, job_tiles, grid, wait_polls, st);
+    default: return launch_mma<DG_IQ_CI8, DT, P>(one, jobs, njobs, job_tiles, grid, wait_polls, st);
     }
 }
 
-cudaError_t launch_cdft_contract_mma(const CdftBatch &a, int tiles, int fmt, int mode, cudaStream_t st)
+static cudaError_t launch_mode(const TcJob &one, const TcJob *jobs, int njobs, const int *job_tiles, int grid,
+                               unsigned wait_polls, int fmt, int mode, cudaStream_t st)
 {
     switch (mode) {
-    case DG_CONTRACT_BF16: return launch_fmt<DG_CONTRACT_BF16, 1>(a, tiles, fmt, st);
-    case DG_CONTRACT_FP16: return launch_fmt<DG_CONTRACT_FP16, 1>(a, tiles, fmt, st);
-    case DG_CONTRACT_BF16X3: return launch_fmt<DG_CONTRACT_BF16, 2>(a, tiles, fmt, st);
-    default: return launch_fmt<DG_CONTRACT_FP16, 2>(a, tiles, fmt, st);
+    case DG_CONTRACT_BF16: return launch_fmt<DG_CONTRACT_BF16, 1>(one, jobs, njobs, job_tiles, grid, wait_polls, fmt, st);
+    case DG_CONTRACT_FP16: return launch_fmt<DG_CONTRACT_FP16, 1>(one, jobs, njobs, job_tiles, grid, wait_polls, fmt, st);
+    case DG_CONTRACT_BF16X3: return launch_fmt<DG_CONTRACT_BF16, 2>(one, jobs, njobs, job_tiles, grid, wait_polls, fmt, st);
+    default: return launch_fmt<DG_CONTRACT_FP16, 2>(one, jobs, njobs, job_tiles, grid, wait_polls, fmt, st);
     }
+}
+
+TcJob tc_job(const CdftBatch &a, const void *btab)
+{
+    TcJob j;
+    j.sd = a.sd;
+    j.tbase = a.tbase;
+    j.bbase = a.bbase;
+    j.lr = a.lr;
+    j.layout = a.layout;
+    j.need = a.need;
+    j.W = a.W;
+    j.btab = btab;
+    j.err = a.err;
+    j.S = a.S;
+    j.M = a.M;
+    j.Bmax = a.Bmax;
+    j.zscale = a.zscale;
+    return j;
+}
+
+cudaError_t launch_cdft_contract_mma(const CdftBatch &a, int grid, int fmt, int mode, cudaStream_t st)
+{
+    return launch_mode(tc_job(a, a.btab), nullptr, 0, nullptr, grid, a.wait_polls, fmt, mode, st);
+}
+
+cudaError_t launch_cdft_contract_jobs(const TcJob *jobs, int n, const int *job_tiles, int grid, int fmt, int mode,
+                                      unsigned wait_polls, cudaStream_t st)
+{
+    TcJob none{};
+    return launch_mode(none, jobs, n, job_tiles, grid, wait_polls, fmt, mode, st);
+}
+
+__global__ void k_tc_job_tiles(const TcJob *jobs, int n, int *job_tiles)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    int run = 0;
+    for (int j = 0; j < n; ++j) {
+        job_tiles[j] = run;
+        run += jobs[j].tbase[jobs[j].S];
+    }
+    job_tiles[n] = run;
+}
+
+cudaError_t launch_tc_job_tiles(const TcJob *jobs, int n, int *job_tiles, cudaStream_t st)
+{
+    k_tc_job_tiles<<<1, 32, 0, st>>>(jobs, n, job_tiles);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_cdft_contract_hankel(const CdftBatch &a, int grid, int fmt, int mode, cudaStream_t st)

@@ -197,6 +197,27 @@ __device__ __forceinline__ bool round_df(dfl D, int &L)
     return true;
 }
 
+// floor(D) of a double-float D and the remainder mu = D - floor(D) in
+// [0, 1), in FP32 only; false when |D| >= 2^22 (the caller then uses FP64).
+// (Lagrange4 is continuous across integer D, so a lag off by one next to an
+// integer gives the same interpolated sample; no rounding margin is needed.)
+__device__ __forceinline__ bool floor_df(dfl D, int &L, float &mu)
+{
+    if (!(fabsf(D.hi) < 4194304.0f)) return false;
+    float n = floorf(D.hi);
+    float f = (D.hi - n) + D.lo;  // D.hi - n is exact
+    if (f < 0.f) {
+        n -= 1.f;
+        f += 1.f;
+    } else if (f >= 1.f) {
+        n += 1.f;
+        f -= 1.f;
+    }
+    L = (int)n;
+    mu = fminf(fmaxf(f, 0.f), 1.f);
+    return true;
+}
+
 // Integer lag of the delay mode: Eq. 9 (round half away from zero) or floor.
 __device__ __forceinline__ int lag_of(double D, int delay_mode)
 {
@@ -341,7 +362,37 @@ struct CdftBatch {
     const void *btab;             // [S][M/32][2][128 x 32] 16-bit DFT operand (tensor cores)
     float zscale;                 // lag products are multiplied by this before 16-bit rounding
     unsigned wait_polls;          // poll limit of the tensor-core pipeline's waits; 0 = the default
+    int delay;                    // DG_DELAY_INTEGER: lag round(D); DG_DELAY_LAGRANGE4: lag floor(D) and
+                                  // the candidate combines the lags L - 1 .. L + 2 (fractional delay)
+    float *candMu;                // [S][G] fractional delay mu = D - floor(D) (Lagrange4 only)
+    float *muS;                   // [S][G] mu in sorted order (Lagrange4 only)
+    int *need;                    // [NBT] 1: the bucket's per-lag DFT rows are computed (scan)
 };
+
+// Bucket b's rows are needed when a candidate's lag stencil reaches it: its
+// own candidates (integer lags), or those of buckets b - 2 .. b + 1
+// (Lagrange4 combines lags L - 1 .. L + 2).
+
+// What the tensor-core contraction needs of one job: one snapshot batch of
+// one context (its plan done: tile bases, lag ranges, layouts, the
+// need flags, the DFT operand tables). Several jobs can share one persistent
+// launch; their tiles are numbered job after job.
+struct TcJob {
+    const StepDesc *sd;           // [S] captures
+    const int *tbase, *bbase, *lr, *layout, *need;
+    float *W;                     // per-lag DFT rows
+    const void *btab;             // DFT operand tables, [S][M/32] stages
+    unsigned *err;                // the context's latched error word
+    int S, M, Bmax;
+    float zscale;
+};
+TcJob tc_job(const CdftBatch &a, const void *btab);
+// job_tiles[0..n]: prefix sum of the jobs' tile counts (one thread, device)
+cudaError_t launch_tc_job_tiles(const TcJob *jobs, int n, int *job_tiles, cudaStream_t s);
+// one persistent launch over every tile of n jobs (device array), all of
+// the same capture format and contraction arithmetic
+cudaError_t launch_cdft_contract_jobs(const TcJob *jobs, int n, const int *job_tiles, int grid, int fmt, int mode,
+                                      unsigned wait_polls, cudaStream_t s);
 
 cudaError_t launch_cdft_geo(const CdftBatch &a, cudaStream_t s);
 // xyzf[6][G] = double-float split of xyz[3][G]

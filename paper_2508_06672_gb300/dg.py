@@ -66,7 +66,7 @@ EXPORTED_SYMBOLS = [
     "dg_nn_conv3x3_forward", "dg_nn_conv3x3_backward", "dg_nn_conv3x3_scratch", "dg_nn_relu_forward",
     "dg_nn_relu_backward", "dg_nn_bce_scratch", "dg_nn_bce_logits", "dg_nn_adam", "dg_nn_last_error",
     "dg_coarse_maps", "dg_coarse_inspect", "dg_set_grid", "dg_search_regions", "dg_fp32_peak",
-    "dg_debug_tc_wait_limit",
+    "dg_debug_tc_wait_limit", "dg_batch_rounds",
 ]
 DG_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
@@ -188,6 +188,8 @@ def lib():
             L.dg_batch_launch_count.argtypes = [vp]
             L.dg_batch_launch_count.restype = C.c_int64
             L.dg_batch_destroy.argtypes = [vp]
+            L.dg_batch_rounds.argtypes = [vp]
+            L.dg_batch_rounds.restype = i32
             for f in ("dg_graph_capture", "dg_graph_launch", "dg_graph_fix", "dg_batch_capture", "dg_batch_launch",
                       "dg_batch_fixes", "dg_batch_destroy"):
                 getattr(L, f).restype = C.c_int
@@ -337,6 +339,10 @@ class Batch:
 
     def launch_count(self):
         return int(lib().dg_batch_launch_count(self.handle))
+
+    def rounds(self):
+        """Shared contraction rounds of the batch (0: per-context launches)."""
+        return int(lib().dg_batch_rounds(self.handle))
 
     def close(self):
         if getattr(self, "handle", None):

@@ -125,11 +125,15 @@ def test_cdft_hankel_shorter_chunks_and_auto(chunk):
 def test_cdft_auto_chunk():
     """chunk 0: each batch takes the longest power-of-two chunk up to 1024
     (few tiles here) whose length times the estimated bin spacing stays
-    within the bound (with a 10 % margin); the result stays within the FP32
-    tolerance, and a grid with a wider FDOA span (1000 km at 0.5 MHz) gets a
-    shorter chunk."""
+    within the bound (with a 10 % margin); a grid with a wider FDOA span in
+    cycles per sample (1000 km at 0.5 MHz) gets a shorter chunk. At 12.5 MHz
+    the surface is held to the FP32 bound. At 0.5 MHz the FDOAs reach 6e-3
+    cycles per sample, and their FP32 rounding limits every FP32 path: the
+    direct evaluation measures 1.5e-4 on this scene (chunks of 128 and 512
+    samples 1.2e-4 alike, so not the interpolation); that case is held to
+    2e-4."""
     chunks = []
-    for fs, spacing in ((12.5e6, 100.0), (5e5, 25000.0)):
+    for fs, spacing, tol in ((12.5e6, 100.0, FP32_TOL), (5e5, 25000.0, 2e-4)):
         s = sim.make_scene(seed=23, fs_hz=fs, n_samples=40000, k_steps=2, fmt="ci16", waveform="chirp",
                            snr_db=-3.0, grid_n=(41, 39), grid_spacing_m=spacing)
         g, c = gpu_surface(s, algo="cdft")
@@ -139,9 +143,10 @@ def test_cdft_auto_chunk():
         ok = ~lag_boundary_mask(s, np.arange(s.G))
         r, d = ref.ravel()[ok], c.ravel()[ok]
         strong = r >= 0.1 * r.max()
-        print(f"fs {fs:g}: chunk {hi}, floored error {rel_err(d, r, 0.01, 2.0):.3e}, "
+        floored = np.max(np.abs(d - r) / (r + 0.01 * r.mean()))
+        print(f"fs {fs:g}: chunk {hi}, floored error {floored:.3e}, "
               f"plain error on nodes >= 10% of the maximum {np.max(np.abs(d - r)[strong] / r[strong]):.3e}")
-        assert rel_err(d, r, 0.01) < FP32_TOL
+        assert rel_err(d, r, 0.01) < tol
         chunks.append(hi)
         g.close()
     assert chunks[1] < chunks[0]
@@ -314,7 +319,7 @@ def test_cdft_refine_and_unsupported_options():
     ri = fix["ri"] * lg["nlon"] + fix["rj"]
     assert lref.ravel()[ri] >= lref.max() * (1 - 2 * FP32_TOL)
     g.close()
-    for kw in (dict(delay="lagrange4"), dict(prec="fp64"), dict(chunk=100), dict(bins=32)):
+    for kw in (dict(prec="fp64"), dict(chunk=100), dict(bins=32)):
         with pytest.raises(P.DGError):
             P.Geolocator(s.grid, s.ephem, s.fs_hz, s.fc_hz, algo="cdft", **kw)
 
@@ -395,3 +400,61 @@ def test_tensor_pipeline_timeout_is_reported_and_the_context_recovers():
     ok = ~lag_boundary_mask(s, np.arange(s.G))
     assert rel_err(c.double().cpu().numpy().ravel()[ok], ref.ravel()[ok], 0.01) < FP32_TOL
     g.close()
+
+
+# ------------------------------------------------- fractional delay (Lagrange4)
+@pytest.mark.parametrize("fmt", ["c64", "ci16", "ci8"])
+@pytest.mark.parametrize("contract", ["fp32", "fp16x3"])
+def test_cdft_lagrange4_small_scenes(fmt, contract):
+    """The 4-tap Lagrange fractional delay (L = floor(D), mu = D - L) on the
+    chunked-DFT path: by linearity each candidate combines the DFT rows of
+    lags L - 1 .. L + 2 with its weights w_m(mu). Against the oracle's
+    delay mode 1 (the definition, sample by sample) at the FP32 bound, with
+    ragged tiles and odd N."""
+    s = sim.make_scene(seed=31, fs_hz=12.5e6, n_samples=3001, k_steps=3, fmt=fmt, waveform="chirp",
+                       snr_db=-3.0, grid_n=(37, 45), grid_spacing_m=150.0)
+    g, c = gpu_surface(s, algo="cdft", contract=contract, delay="lagrange4")
+    ref = oracle_surface(s, 1)
+    ok = ~lag_boundary_mask(s, np.arange(s.G), 1)
+    assert rel_err(c.ravel()[ok], ref.ravel()[ok], 0.01) < FP32_TOL
+    g.close()
+
+
+def test_cdft_lagrange4_mid_subgrid_and_noise_free_peak():
+    """Mid geometry: on a 49 x 41 sub-grid at full K and N the Lagrange4
+    surface matches the oracle (delay mode 1) within the FP32 bound and its
+    maximum is a valid one (a near-tie); on the noise-free 21 x 21 scene the
+    maximum is the emitter's node.""" 
+    s = sim.mid(grid_n=(49, 41))
+    g, c = gpu_surface(s, algo="cdft", delay="lagrange4")
+    ref = oracle_surface(s, 1)
+    ok = ~lag_boundary_mask(s, np.arange(s.G), 1)
+    assert rel_err(c.ravel()[ok], ref.ravel()[ok]) < FP32_TOL
+    # with the fractional delay the sub-grid's top two differ by ~5.8e-5 of
+    # the maximum: a near-tie at the FP32 bound
+    assert_argmax_consistent(c, ref, FP32_TOL, near_tie=True)
+    g.close()
+    s = sim.mid(grid_n=(21, 21), snr_db=None, waveform="noise", bw_hz=5e6)
+    g, c = gpu_surface(s, algo="cdft", delay="lagrange4")
+    ref = oracle_surface(s, 1)
+    assert oracle.argmax(ref) == 10 * 21 + 10
+    assert_argmax_consistent(c, ref, FP32_TOL)
+    assert rel_err(c, ref) < FP32_TOL
+    g.close()
+
+
+def test_cdft_lagrange4_equals_direct_lagrange4_at_large_sizes():
+    """Large footprint's captures on a 129 x 129 grid: the chunked-DFT
+    Lagrange4 surface against the direct one (both FP32) and the oracle at
+    sampled nodes."""
+    s = sim.large(grid_n=129)
+    g, c = gpu_surface(s, algo="cdft", delay="lagrange4")
+    g.close()
+    g, d = gpu_surface(s, algo="direct", delay="lagrange4")
+    g.close()
+    assert rel_err(c, d) < 2 * FP32_TOL
+    rng = np.random.default_rng(8)
+    idx = np.unique(rng.integers(0, s.G, 24))
+    ref = oracle.cost_points(*oracle.scene_args(s), idx=idx, delay_mode=1)
+    ok = ~lag_boundary_mask(s, idx, 1)
+    assert rel_err(c.ravel()[idx][ok], ref[ok]) < FP32_TOL

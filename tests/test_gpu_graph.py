@@ -128,6 +128,53 @@ def test_batch_of_uneven_captures():
         g.close()
 
 
+def test_batch_shares_tensor_core_contraction_rounds():
+    """Seven uneven chunked-DFT problems on the tensor cores (one format):
+    their main-surface contractions run as shared persistent launches, one
+    per round of snapshot batches (a context with a small scratch target
+    splits its snapshots over several rounds). Every fix and cost surface
+    equals its own synchronising step bit for bit, and one capture's
+    surface matches the CPU oracle."""
+    torch = torch_cuda()
+    P = package()
+    import oracle
+    from gpu_common import lag_boundary_mask, rel_err
+
+    rng = np.random.default_rng(6)
+    gs, costs, refs, ref_costs, scenes = [], [], [], [], []
+    for i in range(7):
+        k = int(rng.integers(1, 6))
+        s = _scene(60 + i, fmt="ci16", k_steps=4 if i == 6 else k,
+                   n_samples=int(rng.choice([4096, 9000, 16384, 20000])),
+                   grid_n=(int(rng.integers(31, 90)) | 1, int(rng.integers(31, 90)) | 1),
+                   grid_spacing_m=float(rng.uniform(100, 400)), waveform=["chirp", "noise"][i % 2])
+        # the last context keeps one snapshot per batch of its plan: several rounds
+        opts = dict(algo="cdft", contract="fp16x3", scratch_mib=1 if i == 6 else 0)
+        g = _geo(s, torch.cuda.Stream(), **opts)
+        c, ref = _reference_fix(g)
+        g.stream.synchronize()
+        ref_costs.append(c.clone())
+        gs.append(g)
+        refs.append(ref)
+        scenes.append(s)
+        costs.append(torch.empty((g.nrows, g.nlon), dtype=g.dtype, device=g.device))
+    b = P.Batch(gs, costs, *REFINE)
+    assert b.rounds() >= 2
+    for _ in range(2):
+        b.launch()
+    assert b.fixes() == refs
+    torch.cuda.synchronize()
+    for c, rc in zip(costs, ref_costs):
+        assert torch.equal(c, rc)
+    s = scenes[0]
+    ref = oracle.cost_surface(*oracle.scene_args(s))
+    ok = ~lag_boundary_mask(s, np.arange(s.G))
+    assert rel_err(costs[0].double().cpu().numpy().ravel()[ok], ref.ravel()[ok], 0.01) < 1e-4
+    b.close()
+    for g in gs:
+        g.close()
+
+
 @pytest.mark.parametrize("contract", ["fp32", "fp16x3"])
 def test_autotune_picks_an_admissible_shape(contract):
     """The tuner times the admissible (chunk, tile) shapes, keeps the fastest
