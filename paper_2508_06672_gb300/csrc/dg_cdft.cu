@@ -522,7 +522,7 @@ __global__ void __launch_bounds__(256) k_cdft_superchunk(CdftBatch a, int NBT)
 // ---------------------------------------------------------------------------
 constexpr int kSeg = 32;
 
-template <typename T>
+template <typename T, bool FRAC>
 __global__ void __launch_bounds__(kCdftCombineThreads) k_cdft_combine(CdftBatch a, T *surf)
 {
     // per (super-)chunk and bin: the DFT value (re, im)
@@ -538,8 +538,8 @@ __global__ void __launch_bounds__(kCdftCombineThreads) k_cdft_combine(CdftBatch 
     const int M = a.Mcs[s];
     const int B = (a.sd[s].n + M - 1) / M;
     const float nbase = a.nubase[s], inv = 1.0f / a.delta[s];
-    const bool frac = a.delay != DG_DELAY_INTEGER;
-    const int mlo = frac ? -1 : 0, mhi = frac ? 2 : 0;  // lag offsets of the stencil
+    constexpr bool frac = FRAC;  // a.delay != DG_DELAY_INTEGER
+    constexpr int mlo = frac ? -1 : 0, mhi = frac ? 2 : 0;  // lag offsets of the stencil
     // the first segment of DFTs depends on the bucket only: its loads travel
     // together with the candidates' below
     {
@@ -802,7 +802,10 @@ cudaError_t launch_cdft_superchunk(const CdftBatch &a, int NBT, cudaStream_t st)
 
 cudaError_t launch_cdft_combine(const CdftBatch &a, float *surf, cudaStream_t st)
 {
-    k_cdft_combine<float><<<(unsigned)a.ngroups, kCdftCombineThreads, 0, st>>>(a, surf);
+    if (a.delay == DG_DELAY_INTEGER)
+        k_cdft_combine<float, false><<<(unsigned)a.ngroups, kCdftCombineThreads, 0, st>>>(a, surf);
+    else
+        k_cdft_combine<float, true><<<(unsigned)a.ngroups, kCdftCombineThreads, 0, st>>>(a, surf);
     return cudaGetLastError();
 }
 

@@ -373,6 +373,11 @@ struct CdftBatch {
 // own candidates (integer lags), or those of buckets b - 2 .. b + 1
 // (Lagrange4 combines lags L - 1 .. L + 2).
 
+// Status of the network-layer calls (dg_nn_*): the message of the last
+// failure on this thread (dg_nn_last_error).
+dg_status nn_fail(dg_status st, const char *fmt, ...);
+dg_status nn_done(cudaError_t e, const char *what);
+
 // What the tensor-core contraction needs of one job: one snapshot batch of
 // one context (its plan done: tile bases, lag ranges, layouts, the
 // need flags, the DFT operand tables). Several jobs can share one persistent

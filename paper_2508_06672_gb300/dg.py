@@ -33,6 +33,7 @@ __all__ = [
     "DG_K_CDFT_PLAN", "DG_K_CDFT_CONTRACT", "DG_K_CDFT_COMBINE",
     "dg_nn_conv3x3_forward", "dg_nn_conv3x3_backward", "dg_nn_relu_forward", "dg_nn_relu_backward",
     "dg_nn_bce_logits", "dg_nn_adam", "dg_nn_last_error", "dg_coarse_step", "DG_K_COARSE",
+    "dg_nn_conv3x3_forward_tc", "dg_nn_conv3x3_backward_tc", "dg_nn_tc_check",
 ]
 
 DG_OK, DG_EINVAL, DG_ENOMEM, DG_ECUDA, DG_ESTATE, DG_ETIMEOUT, DG_EUNSUPPORTED = range(7)
@@ -66,7 +67,8 @@ EXPORTED_SYMBOLS = [
     "dg_nn_conv3x3_forward", "dg_nn_conv3x3_backward", "dg_nn_conv3x3_scratch", "dg_nn_relu_forward",
     "dg_nn_relu_backward", "dg_nn_bce_scratch", "dg_nn_bce_logits", "dg_nn_adam", "dg_nn_last_error",
     "dg_coarse_maps", "dg_coarse_inspect", "dg_set_grid", "dg_search_regions", "dg_fp32_peak",
-    "dg_debug_tc_wait_limit", "dg_batch_rounds",
+    "dg_debug_tc_wait_limit", "dg_batch_rounds", "dg_nn_conv3x3_forward_tc", "dg_nn_conv3x3_backward_tc",
+    "dg_nn_conv3x3_tc_scratch", "dg_nn_tc_check",
 ]
 DG_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
@@ -215,6 +217,11 @@ def lib():
             L.dg_nn_conv3x3_backward.argtypes = [vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, i32, vp, vp]
             L.dg_nn_conv3x3_scratch.argtypes = [i32, i32, i32, i32, i32]
             L.dg_nn_conv3x3_scratch.restype = i64
+            L.dg_nn_conv3x3_forward_tc.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, i32, vp]
+            L.dg_nn_conv3x3_backward_tc.argtypes = [vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, i32, vp, vp]
+            L.dg_nn_conv3x3_tc_scratch.argtypes = [i32, i32, i32, i32, i32]
+            L.dg_nn_conv3x3_tc_scratch.restype = i64
+            L.dg_nn_tc_check.argtypes = [vp]
             L.dg_nn_relu_forward.argtypes = [vp, vp, i64, vp]
             L.dg_nn_relu_backward.argtypes = [vp, vp, vp, i64, vp]
             L.dg_nn_bce_scratch.argtypes = [i64]
@@ -222,7 +229,8 @@ def lib():
             L.dg_nn_bce_logits.argtypes = [vp, vp, flt, i64, vp, vp, vp, vp]
             L.dg_nn_adam.argtypes = [vp, vp, vp, vp, i64, flt, flt, flt, flt, i32, vp]
             for f in ("dg_nn_conv3x3_forward", "dg_nn_conv3x3_backward", "dg_nn_relu_forward",
-                      "dg_nn_relu_backward", "dg_nn_bce_logits", "dg_nn_adam"):
+                      "dg_nn_relu_backward", "dg_nn_bce_logits", "dg_nn_adam", "dg_nn_conv3x3_forward_tc",
+                      "dg_nn_conv3x3_backward_tc", "dg_nn_tc_check"):
                 getattr(L, f).restype = C.c_int
             L.dg_nn_last_error.argtypes = []
             L.dg_nn_last_error.restype = C.c_char_p
@@ -478,6 +486,41 @@ def dg_nn_conv3x3_backward(x, w, dy, dx, dw, db, scratch=None, stream=None):
         raise ValueError("dg_nn_conv3x3_backward: shape mismatch")
     _nn_check(lib().dg_nn_conv3x3_backward(_ptr(x), _ptr(w), _ptr(dy), _ptr(dx), _ptr(dw), _ptr(db),
                                            B, Ci, Co, H, W, _ptr(scratch), _stream(stream, x)))
+
+
+def dg_nn_conv3x3_forward_tc(x, w, b, y, stream=None):
+    """dg_nn_conv3x3_forward on the tensor cores: BF16 operands, FP32 sums."""
+    _f32(x, w, b, y)
+    B, Ci, H, W = x.shape
+    Co = w.shape[0]
+    if tuple(w.shape) != (Co, Ci, 3, 3) or tuple(b.shape) != (Co,) or tuple(y.shape) != (B, Co, H, W):
+        raise ValueError("dg_nn_conv3x3_forward_tc: shape mismatch")
+    _nn_check(lib().dg_nn_conv3x3_forward_tc(_ptr(x), _ptr(w), _ptr(b), _ptr(y), B, Ci, Co, H, W,
+                                             _stream(stream, x)))
+
+
+def dg_nn_conv3x3_backward_tc(x, w, dy, dx, dw, db, scratch=None, stream=None):
+    """dg_nn_conv3x3_backward on the tensor cores: BF16 operands, FP32 sums;
+    scratch: dg_nn_conv3x3_tc_scratch floats (allocated here when None)."""
+    import torch
+    B, Ci, H, W = x.shape
+    Co = w.shape[0]
+    need = int(lib().dg_nn_conv3x3_tc_scratch(B, Ci, Co, H, W))
+    if need < 0:
+        raise ValueError("dg_nn_conv3x3_backward_tc: shape out of range")
+    if scratch is None:
+        scratch = torch.empty(max(1, need), dtype=torch.float32, device=x.device)
+    _f32(x, w, dy, dx, dw, db, scratch)
+    if (tuple(dy.shape) != (B, Co, H, W) or tuple(dw.shape) != (Co, Ci, 3, 3) or tuple(db.shape) != (Co,)
+            or (dx is not None and tuple(dx.shape) != tuple(x.shape)) or scratch.numel() < need):
+        raise ValueError("dg_nn_conv3x3_backward_tc: shape mismatch")
+    _nn_check(lib().dg_nn_conv3x3_backward_tc(_ptr(x), _ptr(w), _ptr(dy), _ptr(dx), _ptr(dw), _ptr(db),
+                                              B, Ci, Co, H, W, _ptr(scratch), _stream(stream, x)))
+
+
+def dg_nn_tc_check(stream=None):
+    """Raises DGError(DG_ETIMEOUT) if a tensor-core layer's wait ran out."""
+    _nn_check(lib().dg_nn_tc_check(C.c_void_p(stream.cuda_stream if stream is not None else 0)))
 
 
 def dg_nn_relu_forward(z, h, stream=None):
