@@ -303,7 +303,6 @@ unsigned grid_of(int64_t n, int per = 256, int cap = 152 * 16)
 }
 }  // namespace
 
-namespace {
 thread_local char g_nn_msg[256] = "";
 
 dg_status nn_fail(dg_status st, const char *fmt, ...)
@@ -321,6 +320,8 @@ dg_status nn_done(cudaError_t e, const char *what)
     g_nn_msg[0] = 0;
     return DG_OK;
 }
+
+namespace {
 
 bool conv_shape_ok(int B, int Ci, int Co, int H, int W)
 {

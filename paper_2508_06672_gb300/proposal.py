@@ -9,6 +9,11 @@ position. torch is used only to hold device memory.
 
 Architecture: conv3x3-relu blocks, then a conv3x3 to one logit channel
 (``channels`` = [C_in, c1, ..., 1]).
+
+Arithmetic: ``tc=True`` runs the convolutions forward and backward on the
+tensor cores (dg_nn_conv3x3_*_tc: BF16 activations and weights, FP32
+accumulation); the master weights and Adam's moments stay FP32. ``tc=False``
+uses the FP32 CUDA-core kernels (the parity reference).
 """
 from __future__ import annotations
 
@@ -20,8 +25,9 @@ from . import dg
 
 
 class ProposalNet:
-    def __init__(self, channels, seed=0, device="cuda"):
+    def __init__(self, channels, seed=0, device="cuda", tc=False):
         import torch
+        self.tc = bool(tc)
         if len(channels) < 2 or channels[-1] != 1:
             raise ValueError("channels must run from the input channels to 1")
         self.torch = torch
@@ -55,12 +61,15 @@ class ProposalNet:
         arrs = {}
         for k, (w, b) in enumerate(self.state_numpy()):
             arrs[f"w{k}"], arrs[f"b{k}"] = w.astype(np.float32), b.astype(np.float32)
-        np.savez(path, channels=np.array(self.channels), **arrs)
+        np.savez(path, channels=np.array(self.channels), tc=np.array(int(self.tc)), **arrs)
 
     @classmethod
-    def load(cls, path, device="cuda"):
+    def load(cls, path, device="cuda", tc=None):
+        """tc=None: the arithmetic the weights were trained with (stored)."""
         z = np.load(path)
-        net = cls([int(c) for c in z["channels"]], device=device)
+        if tc is None:
+            tc = bool(int(z["tc"])) if "tc" in z.files else False
+        net = cls([int(c) for c in z["channels"]], device=device, tc=tc)
         net.load_numpy([(z[f"w{k}"], z[f"b{k}"]) for k in range(len(net.params))])
         return net
 
@@ -75,7 +84,7 @@ class ProposalNet:
         L = len(self.params)
         for k, (w, b) in enumerate(self.params):
             z = torch.empty((B, w.shape[0], H, W), dtype=torch.float32, device=x.device)
-            dg.dg_nn_conv3x3_forward(h, w, b, z)
+            (dg.dg_nn_conv3x3_forward_tc if self.tc else dg.dg_nn_conv3x3_forward)(h, w, b, z)
             if k < L - 1:
                 hk = torch.empty_like(z) if keep else z
                 dg.dg_nn_relu_forward(z, hk)
@@ -105,7 +114,8 @@ class ProposalNet:
                 d = dz
             x = acts[2 * k]
             dx = torch.empty_like(x) if k > 0 else None
-            dg.dg_nn_conv3x3_backward(x, self.params[k][0], d, dx, self.grads[k][0], self.grads[k][1])
+            (dg.dg_nn_conv3x3_backward_tc if self.tc else dg.dg_nn_conv3x3_backward)(
+                x, self.params[k][0], d, dx, self.grads[k][0], self.grads[k][1])
             d = dx
         return self.grads
 

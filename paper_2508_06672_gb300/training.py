@@ -44,7 +44,8 @@ def train(args, scenes, first):
 
     search = L.LearnedSearch(first["grid"], first["ephem"], first["fs"], first["fc"], None, cells=args.cells)
     K = search.K
-    net = ProposalNet([K] + [int(c) for c in args.channels.split(",")] + [1], seed=args.seed)
+    net = ProposalNet([K] + [int(c) for c in args.channels.split(",")] + [1], seed=args.seed,
+                      tc=getattr(args, "tc", False))
     rng = np.random.default_rng(args.seed)
     X, T = [], []
     t0 = time.time()

@@ -40,6 +40,8 @@ def main(argv=None):
     ap.add_argument("--crop", type=int, default=128)
     ap.add_argument("--cells", type=int, default=512)
     ap.add_argument("--channels", default="32,64,64")
+    ap.add_argument("--tc", action="store_true",
+                    help="convolutions on the tensor cores (BF16 operands, FP32 accumulation)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--workers", type=int, default=0)
     ap.add_argument("--out", default="")
