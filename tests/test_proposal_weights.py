@@ -20,7 +20,8 @@ def test_weights_match_their_metadata():
     with open(WEIGHTS[:-4] + ".json") as f:
         meta = json.load(f)
     net = ProposalNet.load(WEIGHTS, device="cpu")
-    assert net.channels == meta["network"] == [20, 32, 64, 64, 64, 1]
+    assert net.channels == meta["network"] == [20, 32, 64, 128, 64, 1]
+    assert net.tc  # trained with the tensor-core convolutions; load keeps that arithmetic
     for (w, b), ci, co in zip(net.state_numpy(), net.channels[:-1], net.channels[1:]):
         assert w.shape == (co, ci, 3, 3) and b.shape == (co,)
         assert np.all(np.isfinite(w)) and np.all(np.isfinite(b))

@@ -1,7 +1,8 @@
 """Train the learned proposal's network on the GPU and evaluate the learned
 search against the full-grid search, on seeded synthetic scenes.
 
-    python train_proposal.py --train 1500 --eval 64 \\
+    python train_proposal.py --train 20000 --eval 200 --epochs 10 \\
+        --channels 32,64,128,64 --tc \\
         --out paper_2508_06672_gb300/weights/proposal_2000km.npz
 
 Scenes come from sim.learned (a 2000 km footprint, seeded emitter position,
