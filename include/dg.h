@@ -138,8 +138,8 @@ typedef struct {
                         longest power of two whose length x bin spacing is
                         <= 5e-2 cycles in every snapshot of the batch, up to
                         1024 (FP32 or Hankel contraction) or, on the tensor
-                        cores, up to 16384 while it fits every capture and
-                        the batch keeps 8 lag tiles per SM (dg_cdft_chunks);
+                        cores, up to 2048 while it fits every capture and
+                        the batch keeps 16 lag tiles per SM (dg_cdft_chunks);
                         at most 256 on the refinement grid of
                         dg_argmax_refine (few lags: shorter chunks give the
                         contraction more tiles). DG_TILES_LAGS needs a chunk
@@ -152,6 +152,13 @@ typedef struct {
                         snapshots (per-candidate arrays and per-lag DFTs),
                         MiB; 0 = 12288. Fewer snapshots per batch below it
                         (at least one); many contexts sharing a GPU lower it */
+    int32_t rows;    /* DIRECT: grid rows per thread, i.e. candidates per
+                        thread (a CTA takes 8 warps x rows grid rows x 32
+                        grid columns of one snapshot); 0 = 8 (FP32,
+                        INTEGER delay) or 4 (FP32 LAGRANGE4, FP64); FP32
+                        takes 4, 8 or 16 (16 with LAGRANGE4
+                        spills registers), FP64 2 or 4. Changes speed
+                        only: every candidate's arithmetic is the same     */
 } dg_options;
 
 typedef struct dg_ctx dg_ctx;
@@ -329,27 +336,32 @@ int64_t dg_batch_launch_count(const dg_batch *batch); /* kernels per launch */
 int32_t dg_batch_rounds(const dg_batch *batch);        /* shared contraction rounds */
 dg_status dg_batch_destroy(dg_batch *batch);
 
-/* Autotuning of the CDFT launch shape (no counterpart in the paper; it is
- * the successor of the paper's batch-size sweep, Sec. V-B). For every chunk
- * length 256 .. 1024 (tensor cores: .. 16384, within the shortest capture),
- * in powers of two, that the bin-spacing bound admits for this grid and
- * these snapshots, and for tensor-core contractions every tile shape that
- * takes it (DG_TILES_ROWS, DG_TILES_LAGS, DG_TILES_HANKEL), it times dg_cost_surface into cost
- * (device, the context's precision; its contents are overwritten) with CUDA
- * events on the context's stream: one untimed run, then reps >= 1 timed runs,
- * keeping the median. The fastest shape is written into the context's
- * options (chunk, tiles) and reported in *out. Every candidate meets the
- * same interpolation bound, so the choice changes speed, not the error
- * class. Results are cached per process by grid size, snapshot count,
- * lengths and formats, sampling rate and contraction: a cached shape is
- * applied without timing (out->cached = 1). Synchronises. DG_EUNSUPPORTED
- * for DG_ALGO_DIRECT (its tile shape is fixed). */
+/* Autotuning of the launch shape (no counterpart in the paper; it is the
+ * successor of the paper's batch-size sweep, Sec. V-B).
+ * DG_ALGO_CDFT: every chunk length 256 .. 1024 (tensor cores: .. 2048,
+ * within the shortest capture), in powers of two, that the bin-spacing
+ * bound admits for this grid and these snapshots, and for tensor-core
+ * contractions every tile shape that takes it (DG_TILES_ROWS,
+ * DG_TILES_LAGS, DG_TILES_HANKEL). Every candidate meets the same
+ * interpolation bound, so the choice changes speed, not the error class.
+ * DG_ALGO_DIRECT: the grid rows per thread (dg_options.rows: 4, 8, 16 in
+ * FP32, 16 not with LAGRANGE4; 2, 4 in FP64), i.e. the candidates per CTA;
+ * the surface is the same, bit for bit, for every value.
+ * It times dg_cost_surface into cost (device, the context's precision; its
+ * contents are overwritten) with CUDA events on the context's stream: one
+ * untimed run, then reps >= 1 timed runs, keeping the median. The fastest
+ * shape is written into the context's options (chunk and tiles, or rows)
+ * and reported in *out. Results are cached per process by grid size,
+ * snapshot count, lengths and formats, sampling rate, algorithm, precision,
+ * delay mode and contraction: a cached shape is applied without timing
+ * (out->cached = 1). Synchronises. */
 typedef struct {
-    int32_t chunk;    /* samples per chunk chosen                             */
-    int32_t tiles;    /* DG_TILES_* chosen                                    */
+    int32_t chunk;    /* CDFT: samples per chunk chosen (0 for DIRECT)        */
+    int32_t tiles;    /* CDFT: DG_TILES_* chosen (0 for DIRECT)               */
     double ms;        /* its median surface time (0 when cached)              */
     int32_t tried;    /* shapes timed                                         */
     int32_t cached;   /* 1: taken from the process-wide cache                 */
+    int32_t rows;     /* DIRECT: grid rows per thread chosen (0 for CDFT)     */
 } dg_tuning;
 dg_status dg_autotune(dg_ctx *ctx, void *cost, int32_t reps, dg_tuning *out);
 

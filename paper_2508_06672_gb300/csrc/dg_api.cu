@@ -319,6 +319,7 @@ dg_status run_surface(dg_ctx *c, const GridDev &gd, const double *xyz, int64_t G
     a.delay = c->opt.delay;
     a.acc = c->opt.acc;
     a.prec = c->opt.prec;
+    a.rows = c->opt.rows;
     const size_t esz = c->opt.prec == DG_PREC_FP64 ? 8 : 4;
     {
         Timed t(c, refine ? DG_K_REFINE : DG_K_CORR);
@@ -1011,6 +1012,8 @@ dg_status dg_create(const dg_grid *grid, const dg_ephem *eph, int32_t K, double 
             return fail(nullptr, DG_EINVAL, "lag tiles need chunk <= %d or a multiple of it", kLagTileMaxChunk);
         if (o.scratch_mib < 0) return fail(nullptr, DG_EINVAL, "scratch_mib must be >= 0");
     }
+    if (!direct_rows_ok(o.prec, o.rows))
+        return fail(nullptr, DG_EINVAL, "rows must be 0, 4, 8 or 16 (FP32) or 0, 2 or 4 (FP64)");
     if (o.row0 < 0 || o.row0 >= grid->nlat) return fail(nullptr, DG_EINVAL, "row0 outside the grid");
     if (o.nrows < 0 || o.row0 + o.nrows > grid->nlat) return fail(nullptr, DG_EINVAL, "row shard outside the grid");
     for (int k = 0; k < K; ++k)
@@ -1761,12 +1764,18 @@ int32_t dg_batch_rounds(const dg_batch *b) { return b && b->shared ? (int32_t)b-
 // ---------------------------------------------------------------------------
 namespace {
 std::mutex g_tune_mutex;
-std::map<std::string, std::pair<int, int>> g_tune_cache;
+// a tuned shape: chunk and tiles (CDFT) or rows (DIRECT)
+struct TuneShape {
+    int chunk = 0, tiles = 0, rows = 0;
+};
+std::map<std::string, TuneShape> g_tune_cache;
 
 std::string tune_key(const dg_ctx *c)
 {
     std::string k = std::to_string(c->G) + "/" + std::to_string(c->gd.nlon) + "/" + std::to_string(c->K) + "/" +
-                    std::to_string(c->opt.contract) + "/" + std::to_string(c->opt.acc) + "/" + std::to_string(c->fs);
+                    std::to_string(c->opt.algo) + "/" + std::to_string(c->opt.prec) + "/" +
+                    std::to_string(c->opt.delay) + "/" + std::to_string(c->opt.contract) + "/" +
+                    std::to_string(c->opt.acc) + "/" + std::to_string(c->fs);
     for (const auto &st : c->steps) k += "/" + std::to_string(st.n) + ":" + std::to_string(st.fmt);
     return k;
 }
@@ -1778,42 +1787,73 @@ dg_status dg_autotune(dg_ctx *c, void *cost, int32_t reps, dg_tuning *out)
     c->err.clear();
     if (!cost || !out) return fail(c, DG_EINVAL, "cost and out must not be NULL");
     if (reps < 1 || reps > 100) return fail(c, DG_EINVAL, "reps must be in [1, 100]");
-    if (c->opt.algo != DG_ALGO_CDFT) return fail(c, DG_EUNSUPPORTED, "only the CDFT launch shape is tuned");
     for (int k = 0; k < c->K; ++k)
         if (!c->steps[k].loaded) return fail(c, DG_ESTATE, "snapshot %d has not been loaded", k);
     std::memset(out, 0, sizeof *out);
+    const bool cdft = c->opt.algo == DG_ALGO_CDFT;
+    auto apply = [&](const TuneShape &t) {
+        if (cdft) {
+            c->opt.chunk = t.chunk;
+            c->opt.tiles = t.tiles;
+            out->chunk = t.chunk;
+            out->tiles = t.tiles;
+        } else {
+            c->opt.rows = t.rows;
+            out->rows = t.rows;
+        }
+    };
     const std::string key = tune_key(c);
     {
         std::lock_guard<std::mutex> lk(g_tune_mutex);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            c->opt.chunk = it->second.first;
-            c->opt.tiles = it->second.second;
-            out->chunk = c->opt.chunk;
-            out->tiles = c->opt.tiles;
+            apply(it->second);
             out->cached = 1;
             return DG_OK;
         }
     }
-    // admissible chunks: the automatic rule's bound on the estimated spacing
-    std::vector<double> &span = c->cd.main_span;
-    if (span.size() != (size_t)c->K || c->cd.main_lags.size() != (size_t)c->K)
-        fdoa_spans(c, c->gd, span, &c->cd.main_lags);
-    double dmax = 0.0;
-    int64_t nmin = INT64_MAX;
-    for (int k = 0; k < c->K; ++k) {
-        dmax = std::max(dmax, span[k] * (1.0 + 1e-5) / kCdftBinSpan);
-        nmin = std::min<int64_t>(nmin, c->steps[k].n);
-    }
-    const bool tc = c->opt.contract != DG_CONTRACT_FP32;
-    std::vector<int> chunks;
-    for (int m = 256; m <= (tc ? kCdftAutoMaxChunkTc : kCdftAutoMaxChunk); m *= 2)
-        if (1.1 * m * dmax <= kCdftMDelta && (m <= kCdftAutoMaxChunk || m <= nmin)) chunks.push_back(m);
-    if (chunks.empty()) chunks.push_back(auto_chunk(c, span, c->cd.main_lags, 0, c->K, tc));
-    std::vector<int> tiles = {DG_TILES_ROWS};
-    if (c->opt.contract != DG_CONTRACT_FP32) {
-        tiles.push_back(DG_TILES_LAGS);
-        tiles.push_back(DG_TILES_HANKEL);
+    std::vector<TuneShape> shapes;
+    if (cdft) {
+        // admissible chunks: the automatic rule's bound on the estimated spacing
+        std::vector<double> &span = c->cd.main_span;
+        if (span.size() != (size_t)c->K || c->cd.main_lags.size() != (size_t)c->K)
+            fdoa_spans(c, c->gd, span, &c->cd.main_lags);
+        double dmax = 0.0;
+        int64_t nmin = INT64_MAX;
+        for (int k = 0; k < c->K; ++k) {
+            dmax = std::max(dmax, span[k] * (1.0 + 1e-5) / kCdftBinSpan);
+            nmin = std::min<int64_t>(nmin, c->steps[k].n);
+        }
+        const bool tc = c->opt.contract != DG_CONTRACT_FP32;
+        std::vector<int> chunks;
+        for (int m = 256; m <= (tc ? kCdftAutoMaxChunkTc : kCdftAutoMaxChunk); m *= 2)
+            if (1.1 * m * dmax <= kCdftMDelta && (m <= kCdftAutoMaxChunk || m <= nmin)) chunks.push_back(m);
+        if (chunks.empty()) chunks.push_back(auto_chunk(c, span, c->cd.main_lags, 0, c->K, tc));
+        std::vector<int> tiles = {DG_TILES_ROWS};
+        if (tc) {
+            tiles.push_back(DG_TILES_LAGS);
+            tiles.push_back(DG_TILES_HANKEL);
+        }
+        for (int m : chunks)
+            for (int t : tiles) {
+                if (t == DG_TILES_HANKEL && m > kLagTileMaxChunk) continue;
+                if (t == DG_TILES_LAGS && m > kLagTileMaxChunk && m % kLagTileMaxChunk != 0) continue;
+                TuneShape sh;
+                sh.chunk = m;
+                sh.tiles = t;
+                shapes.push_back(sh);
+            }
+    } else {
+        // grid rows per thread: candidates per CTA and the CTA's lag span
+        // (16 rows of 4-tap interpolation weights spill registers: not tried)
+        const std::vector<int> rows = c->opt.prec == DG_PREC_FP64         ? std::vector<int>{2, 4}
+                                      : c->opt.delay == DG_DELAY_INTEGER ? std::vector<int>{4, 8, 16}
+                                                                         : std::vector<int>{4, 8};
+        for (int r : rows) {
+            TuneShape sh;
+            sh.rows = r;
+            shapes.push_back(sh);
+        }
     }
     const dg_options saved = c->opt;
     const size_t esz = c->opt.prec == DG_PREC_FP64 ? 8 : 4;
@@ -1823,37 +1863,37 @@ dg_status dg_autotune(dg_ctx *c, void *cost, int32_t reps, dg_tuning *out)
     CK(c, cudaEventCreate(&e0));
     CK(c, cudaEventCreate(&e1));
     double best = 1e300;
-    int best_m = chunks[0], best_t = tiles[0];
+    TuneShape best_sh = shapes[0];
     c->opt.timing = 0;  // restored with the saved options
-    for (int m : chunks)
-        for (int t : tiles) {
-            if (t == DG_TILES_HANKEL && m > kLagTileMaxChunk) continue;
-            if (t == DG_TILES_LAGS && m > kLagTileMaxChunk && m % kLagTileMaxChunk != 0) continue;
-            c->opt.chunk = m;
-            c->opt.tiles = t;
-            std::vector<float> ms;
-            for (int r = 0; r <= reps && st == DG_OK; ++r) {
-                if (r > 0 && cudaEventRecord(e0, c->stream) != cudaSuccess) st = DG_ECUDA;
-                if (st == DG_OK) st = run_surface(c, c->gd, c->xyz, c->G, c->surf, cost, false);
-                if (st == DG_OK && r > 0 && cudaEventRecord(e1, c->stream) != cudaSuccess) st = DG_ECUDA;
-                if (st == DG_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = DG_ECUDA;
-                if (st == DG_OK) st = check_latched(c);
-                float x = 0.f;
-                if (st == DG_OK && r > 0) {
-                    cudaEventElapsedTime(&x, e0, e1);
-                    ms.push_back(x);
-                }
-            }
-            if (st != DG_OK) break;
-            std::sort(ms.begin(), ms.end());
-            const double med = ms[ms.size() / 2];
-            ++out->tried;
-            if (med < best) {
-                best = med;
-                best_m = m;
-                best_t = t;
+    for (const TuneShape &sh : shapes) {
+        if (cdft) {
+            c->opt.chunk = sh.chunk;
+            c->opt.tiles = sh.tiles;
+        } else {
+            c->opt.rows = sh.rows;
+        }
+        std::vector<float> ms;
+        for (int r = 0; r <= reps && st == DG_OK; ++r) {
+            if (r > 0 && cudaEventRecord(e0, c->stream) != cudaSuccess) st = DG_ECUDA;
+            if (st == DG_OK) st = run_surface(c, c->gd, c->xyz, c->G, c->surf, cost, false);
+            if (st == DG_OK && r > 0 && cudaEventRecord(e1, c->stream) != cudaSuccess) st = DG_ECUDA;
+            if (st == DG_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = DG_ECUDA;
+            if (st == DG_OK) st = check_latched(c);
+            float x = 0.f;
+            if (st == DG_OK && r > 0) {
+                cudaEventElapsedTime(&x, e0, e1);
+                ms.push_back(x);
             }
         }
+        if (st != DG_OK) break;
+        std::sort(ms.begin(), ms.end());
+        const double med = ms[ms.size() / 2];
+        ++out->tried;
+        if (med < best) {
+            best = med;
+            best_sh = sh;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->opt = saved;
@@ -1861,13 +1901,10 @@ dg_status dg_autotune(dg_ctx *c, void *cost, int32_t reps, dg_tuning *out)
         if (c->err.empty()) fail(c, st, "a timed surface failed");
         return st;
     }
-    c->opt.chunk = best_m;
-    c->opt.tiles = best_t;
-    out->chunk = best_m;
-    out->tiles = best_t;
+    apply(best_sh);
     out->ms = best;
     std::lock_guard<std::mutex> lk(g_tune_mutex);
-    g_tune_cache[key] = {best_m, best_t};
+    g_tune_cache[key] = best_sh;
     return DG_OK;
 }
 

@@ -153,8 +153,11 @@ __global__ void k_cdft_lr_init(int *lr, unsigned *nur, int S)
 // nodes of one snapshot, held in registers (thread t: tile entries t + 256 k,
 // so a warp reads 32 consecutive nodes of one grid row). Their lags span a
 // few hundred values at most, so the counts are aggregated in shared memory
-// first, one atomic per distinct lag in a warp (global atomics only for tiles
-// whose lag span exceeds kHistBins).
+// first, one atomic per run of equal lags in a warp (global atomics only for
+// tiles whose lag span exceeds kHistBins). Along a grid row the lag changes
+// smoothly, so equal lags sit in consecutive lanes: a run is found with one
+// shuffle and one ballot, where a general match of equal values costs far
+// more when most lanes differ (a grid step moving the lag by a sample or more).
 // ---------------------------------------------------------------------------
 constexpr int kHistTile = 64;     // tile side (nodes)
 constexpr int kHistBins = 2048;   // shared-memory buckets per CTA
@@ -195,6 +198,26 @@ __device__ __forceinline__ void load_lag_tile(const CdftBatch &a, int s, int (&l
     __syncthreads();
 }
 
+// Runs of equal values over consecutive lanes: run_heads marks the lanes
+// that start one (lane 0, or a value that differs from the previous lane's);
+// run_len is the length of the run a head lane starts, run_head the head lane
+// of this lane's run. Every lane of the warp takes part.
+__device__ __forceinline__ unsigned run_heads(int v)
+{
+    const int lane = threadIdx.x & 31;
+    const int prev = __shfl_up_sync(0xffffffffu, v, 1);
+    return __ballot_sync(0xffffffffu, lane == 0 || prev != v);
+}
+__device__ __forceinline__ int run_len(unsigned heads, int lane)
+{
+    const unsigned above = heads & ~((2u << lane) - 1u);  // heads after this lane (none for lane 31)
+    return (above ? __ffs(above) - 1 : 32) - lane;
+}
+__device__ __forceinline__ int run_head(unsigned heads, int lane)
+{
+    return 31 - __clz(heads & (0xffffffffu >> (31 - lane)));  // the last head at or before this lane
+}
+
 // Grid index of tile entry k of this thread.
 __device__ __forceinline__ int64_t tile_node(const CdftBatch &a, int k)
 {
@@ -225,12 +248,12 @@ __global__ void __launch_bounds__(256) k_cdft_hist(CdftBatch a)
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int k = 0; k < kTilePer; ++k) {
-        const unsigned peers = __match_any_sync(0xffffffffu, l[k]);
-        if (lane == __ffs(peers) - 1 && l[k] != INT_MIN) {
+        const unsigned heads = run_heads(l[k]);
+        if (((heads >> lane) & 1u) && l[k] != INT_MIN) {
             if (local)
-                atomicAdd(s_cnt + (l[k] - tlo), __popc(peers));
+                atomicAdd(s_cnt + (l[k] - tlo), run_len(heads, lane));
             else
-                atomicAdd(a.count + bb + l[k] - lmin, __popc(peers));
+                atomicAdd(a.count + bb + l[k] - lmin, run_len(heads, lane));
         }
     }
     __syncthreads();
@@ -302,11 +325,12 @@ __global__ void __launch_bounds__(1024) k_cdft_scan(CdftBatch a)
 // ---------------------------------------------------------------------------
 // scatter: counting sort by lag bucket (the offsets come from the scan). A CTA
 // takes the hist kernel's 64 x 64 tile of one snapshot. Its candidates are
-// ranked per lag in shared memory, one global atomic per (tile, lag)
+// ranked per lag in shared memory (one atomic per run of equal lags in a
+// warp, as in hist), one global atomic per (tile, lag)
 // reserves a contiguous range of the bucket, and each candidate takes its
 // rank within that range: the candidates of one tile and lag sit together,
 // which keeps the combine's surface writes close. Tiles whose lag span
-// exceeds kHistBins take one global atomic per (warp, lag) instead.
+// exceeds kHistBins take one global atomic per (warp, run) instead.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_cdft_scatter(CdftBatch a)
 {
@@ -327,15 +351,15 @@ __global__ void __launch_bounds__(256) k_cdft_scatter(CdftBatch a)
     int rank[kTilePer];
 #pragma unroll
     for (int k = 0; k < kTilePer; ++k) {
-        // one atomic per distinct lag in the warp; the peers take
+        // one atomic per run of equal lags in the warp; the run's lanes take
         // consecutive ranks in lane order
-        const unsigned peers = __match_any_sync(0xffffffffu, l[k]);
-        const int leader = __ffs(peers) - 1;
+        const unsigned heads = run_heads(l[k]);
+        const int head = run_head(heads, lane);
         int base = 0;
-        if (lane == leader && l[k] != INT_MIN)
-            base = local ? atomicAdd(s_cnt + (l[k] - tlo), __popc(peers))
-                         : atomicAdd(a.subcnt + bb + l[k] - lmin, __popc(peers));
-        rank[k] = __shfl_sync(0xffffffffu, base, leader) + __popc(peers & ((1u << lane) - 1u));
+        if (lane == head && l[k] != INT_MIN)
+            base = local ? atomicAdd(s_cnt + (l[k] - tlo), run_len(heads, lane))
+                         : atomicAdd(a.subcnt + bb + l[k] - lmin, run_len(heads, lane));
+        rank[k] = __shfl_sync(0xffffffffu, base, head) + (lane - head);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < span; i += blockDim.x) {

@@ -1,7 +1,8 @@
 // dg_corr.cu -- direct position-domain correlation (Sec. III, Eq. 11).
 //
 // One CTA handles one tile of candidates (kWarps*R grid rows x 32 grid
-// columns) for one snapshot k. Per candidate it computes the geometry
+// columns) for one snapshot k; R, the grid rows per thread, is a launch
+// choice (dg_options.rows, tuned by dg_autotune). Per candidate it computes the geometry
 // (Eq. 3-10, FP64), then
 //     C = sum_n y1[n] conj(y2~[n]) exp(j 2 pi nu n),
 // y2~[n] = y2[n + L] (Eq. 9) or its 4-tap Lagrange interpolation at n + D,
@@ -31,10 +32,10 @@ template <typename T> struct Cx;
 template <> struct Cx<float> { using t = float2; };
 template <> struct Cx<double> { using t = double2; };
 
-// R candidates per thread, M-sample chunks, W-sample y2 window.
+// M-sample chunks of y1 and a W-sample y2 window in shared memory.
 template <typename T> struct Cfg;
-template <> struct Cfg<float> { static constexpr int R = 8, M = 2048, W = 4096; };
-template <> struct Cfg<double> { static constexpr int R = 4, M = 1024, W = 2048; };
+template <> struct Cfg<float> { static constexpr int M = 2048, W = 4096; };
+template <> struct Cfg<double> { static constexpr int M = 1024, W = 2048; };
 
 __device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
@@ -92,11 +93,11 @@ __device__ __forceinline__ typename Cx<T>::t y2_global(const void *y2, int N, in
     }
 }
 
-template <typename T, int FMT, int DELAY>
+template <typename T, int FMT, int DELAY, int R>
 __global__ void __launch_bounds__(kThreads) k_corr_direct(CorrArgs a, int tiles_j)
 {
     using C2 = typename Cx<T>::t;
-    constexpr int R = Cfg<T>::R, MCH = Cfg<T>::M, WIN = Cfg<T>::W;
+    constexpr int MCH = Cfg<T>::M, WIN = Cfg<T>::W;
     constexpr int TAPS = (DELAY == DG_DELAY_LAGRANGE4) ? 3 : 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C2 *y1s = reinterpret_cast<C2 *>(smem_raw);
@@ -287,15 +288,14 @@ __global__ void __launch_bounds__(kThreads) k_corr_direct(CorrArgs a, int tiles_
     }
 }
 
-template <typename T, int FMT, int DELAY>
+template <typename T, int FMT, int DELAY, int R>
 static cudaError_t launch_one(const CorrArgs &a, cudaStream_t s)
 {
     using C2 = typename Cx<T>::t;
-    constexpr int R = Cfg<T>::R;
     const size_t smem = (size_t)(Cfg<T>::M + Cfg<T>::W) * sizeof(C2);
     // The attribute is per function and device; setting it each launch keeps
     // this correct for every device and thread at negligible cost.
-    cudaError_t e = cudaFuncSetAttribute(k_corr_direct<T, FMT, DELAY>,
+    cudaError_t e = cudaFuncSetAttribute(k_corr_direct<T, FMT, DELAY, R>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int tiles_i = (a.nrows + kWarps * R - 1) / (kWarps * R);
@@ -303,15 +303,39 @@ static cudaError_t launch_one(const CorrArgs &a, cudaStream_t s)
     const int64_t tiles = (int64_t)tiles_i * tiles_j;
     if (tiles > INT_MAX || a.K > 65535) return cudaErrorInvalidValue;
     dim3 grid((unsigned)tiles, (unsigned)a.K);
-    k_corr_direct<T, FMT, DELAY><<<grid, kThreads, smem, s>>>(a, tiles_j);
+    k_corr_direct<T, FMT, DELAY, R><<<grid, kThreads, smem, s>>>(a, tiles_j);
     return cudaGetLastError();
+}
+
+// Grid rows per thread: FP32 4, 8 or 16; FP64 2 or 4. The defaults are the
+// fastest measured on a 1001^2 grid (K = 50, N = 131072): FP32 8 with the
+// integer delay (4 and 16 within 2 %), 4 with LAGRANGE4 (6 % ahead of 8).
+template <typename T, int FMT, int DELAY>
+static cudaError_t launch_rows(const CorrArgs &a, cudaStream_t s)
+{
+    if constexpr (sizeof(T) == 4) {
+        const int rows = a.rows ? a.rows : (DELAY == DG_DELAY_INTEGER ? 8 : 4);
+        switch (rows) {
+        case 4: return launch_one<T, FMT, DELAY, 4>(a, s);
+        case 8: return launch_one<T, FMT, DELAY, 8>(a, s);
+        case 16: return launch_one<T, FMT, DELAY, 16>(a, s);
+        default: return cudaErrorInvalidValue;
+        }
+    } else {
+        switch (a.rows) {
+        case 2: return launch_one<T, FMT, DELAY, 2>(a, s);
+        case 0:
+        case 4: return launch_one<T, FMT, DELAY, 4>(a, s);
+        default: return cudaErrorInvalidValue;
+        }
+    }
 }
 
 template <typename T, int FMT>
 static cudaError_t launch_delay(const CorrArgs &a, cudaStream_t s)
 {
-    return a.delay == DG_DELAY_INTEGER ? launch_one<T, FMT, DG_DELAY_INTEGER>(a, s)
-                                       : launch_one<T, FMT, DG_DELAY_LAGRANGE4>(a, s);
+    return a.delay == DG_DELAY_INTEGER ? launch_rows<T, FMT, DG_DELAY_INTEGER>(a, s)
+                                       : launch_rows<T, FMT, DG_DELAY_LAGRANGE4>(a, s);
 }
 
 template <typename T>

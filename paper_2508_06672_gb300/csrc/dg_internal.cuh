@@ -142,9 +142,12 @@ __device__ __forceinline__ dfl df_div_fast(dfl a, dfl b)
 // to ~1e-7 samples (so that Eq. 9 rounds it as the FP64 expression does
 // wherever D is farther than 1e-6 from a rounding boundary), i.e. the ranges
 // to ~1e-6 m out of 1e6 m: double-float. The candidate and the receivers
-// are exact double-float splits of the FP64 values; every sum carries an
-// error of at most ~2^-44 of its operands' magnitude (~1e-6 m on the range
-// vectors, ~1e-7 m on the ranges), and fs / c is a double-float constant.
+// are double-float splits of the FP64 values: a pair of floats keeps 48 of
+// the 53 significand bits, a relative error of at most 2^-48 (~3e-8 m on
+// ECEF coordinates of 7e6 m, against the 1e-6 sample = 1.5e-5 m at 20 MHz
+// that round_df leaves as its margin). Every sum carries an error of at
+// most ~2^-44 of its operands' magnitude (~1e-6 m on the range vectors,
+// ~1e-7 m on the ranges), and fs / c is a double-float constant.
 // The FDOA, nu = (f2 - f1) / fs with f_i = -(r_i . v_i) / (rho_i lambda),
 // is a difference of two range rates of ~7 km/s whose result is used as the
 // phase rate over the whole capture; at nodes where |C| is a small remainder
@@ -300,7 +303,14 @@ struct CorrArgs {
     int K;
     int fmt;                     // common format of all steps
     int delay, acc, prec;
+    int rows;                    // grid rows per thread (dg_options.rows; 0 = default)
 };
+
+// Admissible dg_options.rows of the direct kernel for a precision.
+inline bool direct_rows_ok(int prec, int rows)
+{
+    return rows == 0 || (prec == DG_PREC_FP64 ? (rows == 2 || rows == 4) : (rows == 4 || rows == 8 || rows == 16));
+}
 
 // Launch the direct correlation for all K snapshots (one launch).
 cudaError_t launch_corr_direct(const CorrArgs &a, cudaStream_t s);

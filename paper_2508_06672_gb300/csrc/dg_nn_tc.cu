@@ -188,34 +188,54 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const float *__restrict__ x,
         // the stage's previous MMAs (block kb - 2) are done before it is rewritten
         if (kb >= 2) ok = ok && nn_wait(smem_addr(&done[sg]), (uint32_t)((kb - 2) >> 1) & 1u);
         unsigned char *sa = stage[sg], *sb = sa + kABytes;
-        // A: this pixel's 32 (channel, tap) values
-#pragma unroll 4
-        for (int kk = 0; kk < kKB; ++kk) {
-            const int k = kb * kKB + kk;
-            float v = 0.f;
-            if (k < K && j < W) {
-                const int c = k / 9, uv = k - 9 * c, u = uv / 3, vv = uv - 3 * u;
-                const int ii = i + u - 1, jj = j + vv - 1;
-                if (ii >= 0 && ii < H && jj >= 0 && jj < W) v = __ldg(xn + ((size_t)c * H + ii) * W + jj);
-            }
-            *reinterpret_cast<uint16_t *>(sa + kmaj(t, kk)) = bf16_bits(v);
-        }
-        // B: output channel o0 + t's 32 weights
-        if (t < NT) {
-            const int o = o0 + t;
-#pragma unroll 4
-            for (int kk = 0; kk < kKB; ++kk) {
-                const int k = kb * kKB + kk;
-                float v = 0.f;
-                if (k < K && o < CO) {
-                    if (!TR) {
-                        v = __ldg(w + (size_t)o * K + k);
-                    } else {  // w[ci][o][2-u][2-v] of the forward convolution
-                        const int ci = k / 9, uv = k - 9 * ci;
-                        v = __ldg(w + ((size_t)ci * CO + o) * 9 + (8 - uv));
+        // A: this pixel's 32 (channel, tap) values, 8 at a time into one
+        // 16-byte core-matrix row; (channel, tap) stepped from the block's start
+        {
+            int k = kb * kKB, c = k / 9, uv = k - 9 * c;
+#pragma unroll
+            for (int g = 0; g < kKB / 8; ++g) {
+                uint32_t pk[4];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    float v = 0.f;
+                    if (k < K && j < W) {
+                        const int u = uv / 3, vv = uv - 3 * u;
+                        const int ii = i + u - 1, jj = j + vv - 1;
+                        if (ii >= 0 && ii < H && jj >= 0 && jj < W) v = __ldg(xn + ((size_t)c * H + ii) * W + jj);
+                    }
+                    const uint32_t h = bf16_bits(v);
+                    pk[e >> 1] = (e & 1) ? (pk[e >> 1] | (h << 16)) : h;
+                    ++k;
+                    if (++uv == 9) {
+                        uv = 0;
+                        ++c;
                     }
                 }
-                *reinterpret_cast<uint16_t *>(sb + kmaj(t, kk)) = bf16_bits(v);
+                *reinterpret_cast<uint4 *>(sa + kmaj(t, 8 * g)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+        }
+        // B: output channel o0 + t's 32 weights, likewise
+        if (t < NT) {
+            const int o = o0 + t;
+            int k = kb * kKB, ci = k / 9, uv = k - 9 * ci;
+#pragma unroll
+            for (int g = 0; g < kKB / 8; ++g) {
+                uint32_t pk[4];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    float v = 0.f;
+                    if (k < K && o < CO)
+                        v = TR ? __ldg(w + ((size_t)ci * CO + o) * 9 + (8 - uv))  // w[ci][o][2-u][2-v]
+                               : __ldg(w + (size_t)o * K + k);
+                    const uint32_t h = bf16_bits(v);
+                    pk[e >> 1] = (e & 1) ? (pk[e >> 1] | (h << 16)) : h;
+                    ++k;
+                    if (++uv == 9) {
+                        uv = 0;
+                        ++ci;
+                    }
+                }
+                *reinterpret_cast<uint4 *>(sb + kmaj(t, 8 * g)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             }
         }
         nn_fence_async();
@@ -317,31 +337,45 @@ __global__ void __launch_bounds__(128) k_conv3x3_dw_tc(const float *__restrict__
         }
         __syncthreads();
         unsigned char *sa = stage[sg], *sb = sa + kABytes;
-        // A: output channel t over the 32 pixels
-#pragma unroll 4
-        for (int kk = 0; kk < kKB; ++kk) {
-            float v = 0.f;
-            if (t < CO && pn[kk] >= 0)
-                v = __ldg(dy + (((size_t)pn[kk] * CO + t) * H + pi[kk]) * W + pj[kk]);
-            *reinterpret_cast<uint16_t *>(sa + kmaj(t, kk)) = bf16_bits(v);
+        // A: output channel t over the 32 pixels, 8 per 16-byte row
+#pragma unroll
+        for (int g = 0; g < kKB / 8; ++g) {
+            uint32_t pk[4];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int kk = 8 * g + e;
+                float v = 0.f;
+                if (t < CO && pn[kk] >= 0)
+                    v = __ldg(dy + (((size_t)pn[kk] * CO + t) * H + pi[kk]) * W + pj[kk]);
+                const uint32_t h = bf16_bits(v);
+                pk[e >> 1] = (e & 1) ? (pk[e >> 1] | (h << 16)) : h;
+            }
+            *reinterpret_cast<uint4 *>(sa + kmaj(t, 8 * g)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
         // B: columns kc0 + t and kc0 + t + 128 over the 32 pixels
         for (int row = t; row < NC; row += 128) {
             const int col = kc0 + row;
             const int c = col / 9, uv = col - 9 * c, u = uv / 3, vv = uv - 3 * u;
-#pragma unroll 4
-            for (int kk = 0; kk < kKB; ++kk) {
-                float v = 0.f;
-                if (pn[kk] >= 0 && col < ncol) {
-                    if (col == ncol - 1) {
-                        v = 1.f;  // the bias column
-                    } else {
-                        const int ii = pi[kk] + u - 1, jj = pj[kk] + vv - 1;
-                        if (ii >= 0 && ii < H && jj >= 0 && jj < W)
-                            v = __ldg(x + (((size_t)pn[kk] * CI + c) * H + ii) * W + jj);
+#pragma unroll
+            for (int g = 0; g < kKB / 8; ++g) {
+                uint32_t pk[4];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int kk = 8 * g + e;
+                    float v = 0.f;
+                    if (pn[kk] >= 0 && col < ncol) {
+                        if (col == ncol - 1) {
+                            v = 1.f;  // the bias column
+                        } else {
+                            const int ii = pi[kk] + u - 1, jj = pj[kk] + vv - 1;
+                            if (ii >= 0 && ii < H && jj >= 0 && jj < W)
+                                v = __ldg(x + (((size_t)pn[kk] * CI + c) * H + ii) * W + jj);
+                        }
                     }
+                    const uint32_t h = bf16_bits(v);
+                    pk[e >> 1] = (e & 1) ? (pk[e >> 1] | (h << 16)) : h;
                 }
-                *reinterpret_cast<uint16_t *>(sb + kmaj(row, kk)) = bf16_bits(v);
+                *reinterpret_cast<uint4 *>(sb + kmaj(row, 8 * g)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             }
         }
         nn_fence_async();

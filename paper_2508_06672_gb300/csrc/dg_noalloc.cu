@@ -122,6 +122,8 @@ extern "C" dg_status dg_cost_surface_noalloc(const dg_grid *grid, const dg_ephem
         return nfail(DG_EINVAL, "unknown delay, accumulation, precision or algorithm option");
     if (o.row0 < 0 || o.row0 >= grid->nlat || o.nrows < 0 || o.row0 + o.nrows > grid->nlat)
         return nfail(DG_EINVAL, "row shard outside the grid");
+    if (!direct_rows_ok(o.prec, o.rows))
+        return nfail(DG_EINVAL, "rows must be 0, 4, 8 or 16 (FP32) or 0, 2 or 4 (FP64)");
     for (int k = 0; k < K; ++k)
         if (!finite_eph(eph[k])) return nfail(DG_EINVAL, "an ephemeris is not finite");
 
@@ -188,6 +190,7 @@ extern "C" dg_status dg_cost_surface_noalloc(const dg_grid *grid, const dg_ephem
     a.delay = o.delay;
     a.acc = o.acc;
     a.prec = o.prec;
+    a.rows = o.rows;
     if ((e = launch_corr_direct(a, s)) != cudaSuccess) return ncuda(e, "correlation kernel");
     if ((e = launch_accumulate(surf, K, G, o.prec, out, s)) != cudaSuccess) return ncuda(e, "accumulation kernel");
     unsigned herr = 0;

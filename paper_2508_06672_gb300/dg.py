@@ -98,12 +98,12 @@ class dg_options(C.Structure):
     _fields_ = [("delay", C.c_int32), ("acc", C.c_int32), ("prec", C.c_int32), ("algo", C.c_int32),
                 ("row0", C.c_int32), ("nrows", C.c_int32), ("timing", C.c_int32),
                 ("chunk", C.c_int32), ("bins", C.c_int32), ("contract", C.c_int32),
-                ("tiles", C.c_int32), ("scratch_mib", C.c_int32)]
+                ("tiles", C.c_int32), ("scratch_mib", C.c_int32), ("rows", C.c_int32)]
 
 
 class dg_tuning(C.Structure):
     _fields_ = [("chunk", C.c_int32), ("tiles", C.c_int32), ("ms", C.c_double), ("tried", C.c_int32),
-                ("cached", C.c_int32)]
+                ("cached", C.c_int32), ("rows", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -569,7 +569,7 @@ class Geolocator:
 
     def __init__(self, grid, ephem, fs_hz, fc_hz, *, delay="integer", acc="power", prec="fp32",
                  algo="direct", row0=0, nrows=0, timing=False, stream=None, device=None,
-                 chunk=0, bins=0, contract="fp32", tiles="auto", scratch_mib=0):
+                 chunk=0, bins=0, contract="fp32", tiles="auto", scratch_mib=0, rows=0):
         import torch
 
         self.torch = torch
@@ -586,6 +586,7 @@ class Geolocator:
         self.opt.chunk, self.opt.bins, self.opt.contract = int(chunk), int(bins), _CONTRACT[contract]
         self.opt.tiles = _TILES[tiles]
         self.opt.scratch_mib = int(scratch_mib)
+        self.opt.rows = int(rows)
         self.nrows = int(nrows) if nrows else int(grid["nlat"]) - int(row0)
         self.nlon = int(grid["nlon"])
         self.dtype = torch.float64 if prec == "fp64" else torch.float32
@@ -641,7 +642,8 @@ class Geolocator:
         return dg_argmax_refine(self.ctx, cost.data_ptr(), refine_spacing_m, window_m).as_dict()
 
     def autotune(self, cost=None, reps=3):
-        """Time the admissible CDFT launch shapes and keep the fastest."""
+        """Time the admissible launch shapes (CDFT: chunk and tiles; DIRECT:
+        grid rows per thread) and keep the fastest."""
         if cost is None:
             cost = self.torch.empty((self.nrows, self.nlon), dtype=self.dtype, device=self.device)
         t = dg_tuning()

@@ -201,3 +201,42 @@ def test_autotune_picks_an_admissible_shape(contract):
     assert t2["cached"] == 1 and (t2["chunk"], t2["tiles"]) == (t["chunk"], t["tiles"])
     for x in (g, h, u):
         x.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,delay", [("fp32", "integer"), ("fp32", "lagrange4"), ("fp64", "integer")])
+def test_direct_rows_per_thread_are_tuned_and_bit_identical(prec, delay):
+    """The direct kernel's grid rows per thread change only the tile shape:
+    every admissible value gives the same surface bit for bit (each
+    candidate's arithmetic is its own), the tuner picks one of them and
+    caches it, and a value outside the admissible set is rejected."""
+    torch = torch_cuda()
+    P = package()
+    s = _scene(51, k_steps=2, n_samples=6000)
+    rows = {"fp32": (4, 8, 16), "fp64": (2, 4)}[prec]
+    surfs = []
+    for r in rows:
+        g = _geo(s, torch.cuda.Stream(), prec=prec, delay=delay, rows=r)
+        with torch.cuda.stream(g.stream):
+            surfs.append(g.cost_surface().clone())
+        torch.cuda.synchronize()
+        g.close()
+    for x in surfs[1:]:
+        assert torch.equal(x, surfs[0])
+    g = _geo(s, torch.cuda.Stream(), prec=prec, delay=delay)
+    t = g.autotune(reps=2)
+    tried = rows if (prec == "fp64" or delay == "integer") else (4, 8)
+    assert t["rows"] in tried and t["tried"] == len(tried) and t["cached"] == 0 and t["ms"] > 0
+    assert t["chunk"] == 0 and t["tiles"] == 0
+    with torch.cuda.stream(g.stream):
+        tuned = g.cost_surface().clone()
+    torch.cuda.synchronize()
+    assert torch.equal(tuned, surfs[0])
+    u = _geo(s, torch.cuda.Stream(), prec=prec, delay=delay)
+    t2 = u.autotune()
+    assert t2["cached"] == 1 and t2["rows"] == t["rows"]
+    for x in (g, u):
+        x.close()
+    bad = 16 if prec == "fp64" else 2
+    with pytest.raises(P.DGError):
+        _geo(s, torch.cuda.Stream(), prec=prec, delay=delay, rows=bad)
