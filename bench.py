@@ -908,7 +908,8 @@ def run_learned(a, rank, world, local_rank):
             "metric": "learned-proposal search latency (2000 km footprint; full-grid search timed beside it)",
             "value": med_l, "unit": "ms", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": med_l, "higher_is_better": False, "scaling": "replicas", "vs_baseline": None,
-            "dtype": "f32 (CDFT contraction bf16x3)", "data": "synthetic",
+            "dtype": ("bf16 network convolutions (tensor cores, fp32 accumulate)" if net.tc else
+                      "f32 network") + ", CDFT contraction bf16x3", "data": "synthetic",
             "config": {"workload": "learned: 2000 km square footprint (4001^2 nodes at 500 m), K = 20 x N = 65536 "
                                    "ci16 at 12.5 MHz, noise / 2 ms chirp / GPS C/A at -21..-12 dB; 512^2 coarse "
                                    f"cells -> network {net.channels} -> top 8 regions of 50 x 50 km at 500 m -> "
@@ -929,10 +930,7 @@ def run_learned(a, rank, world, local_rank):
             "e2e": {"value": statistics.median(e2e), "unit": "ms", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": 100},
             "gpu_launches": int(round(launches_per_search * a.steps)),
-            "roofline": {"bound": "alu", "achieved": fwd_flops / (fwd_ms / 1e3) / 1e12, "peak": alu_peak,
-                         "unit": "TFLOP/s", "frac": fwd_flops / (fwd_ms / 1e3) / 1e12 / alu_peak, "traffic": None,
-                         "kernel": "k_conv3x3_tiled (the network's forward on the 512^2 maps, timed alone)",
-                         "peak_basis": "measured FP32 FMA peak (dg_fp32_peak, see device.fp32_peak)"},
+            "roofline": net_roofline(net, fwd_flops, fwd_ms, alu_peak),
             "device": {"name": torch.cuda.get_device_name(dev), "sm_count": fp["sm_count"], "fp32_peak": fp},
             "cpu_baseline": None,
             "clocks": clocks,
@@ -940,6 +938,22 @@ def run_learned(a, rank, world, local_rank):
         print(json.dumps(line))
     search.close()
     judge.close()
+
+
+def net_roofline(net, fwd_flops, fwd_ms, alu_peak):
+    """Roofline of the network's forward on the 512^2 maps, timed alone: the
+    tensor-core convolution against the dense bf16 peak, or the FP32 one
+    against the measured FP32 FMA peak."""
+    ach = fwd_flops / (fwd_ms / 1e3) / 1e12
+    if net.tc:
+        peak = tensor_peak("bf16")
+        return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": "k_conv3x3_tc (BF16 tcgen05, the network's forward on the 512^2 maps, "
+                                           "timed alone, with its per-layer weight conversion)",
+                "ms_per_forward": fwd_ms, "peak_basis": PEAK_BASIS_TENSOR}
+    return {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
+            "traffic": None, "kernel": "k_conv3x3_tiled (the network's forward on the 512^2 maps, timed alone)",
+            "ms_per_forward": fwd_ms, "peak_basis": "measured FP32 FMA peak (dg_fp32_peak, see device.fp32_peak)"}
 
 
 def _smi_id(local_rank):

@@ -518,19 +518,25 @@ dg_status dg_nn_conv3x3_backward(const float *x, const float *w, const float *dy
                                  float *scratch, void *stream);
 
 /* The same convolution and gradients on the tensor cores (tcgen05): x, w and
- * dy are rounded to BF16, products accumulate in FP32, outputs are FP32 (the
- * the benchmark spec's network arithmetic: BF16 weights and activations, FP32
- * accumulation; not in the paper). Each output then differs from the exact
- * value by at most 2^-7 times the same sum over absolute values (two BF16
- * roundings per product) plus the FP32 accumulation error. The weight
- * gradient splits the pixels over CTAs and adds the partial sums in a fixed
- * order (deterministic). Same shapes and layouts as above; the backward needs
- * Co <= 128 (DG_EUNSUPPORTED otherwise) and dg_nn_conv3x3_tc_scratch floats
- * of scratch (-1: shape out of range). dg_nn_tc_check synchronises the
- * stream and returns DG_ETIMEOUT (clearing it) if a wait of one of these
- * kernels ran out since the last check (their outputs are then invalid). */
+ * dy are rounded to BF16, products accumulate in FP32, outputs are FP32
+ * (the learned proposal's network arithmetic: BF16 weights and
+ * activations, FP32 accumulation; not in the paper). Each output then
+ * differs from the exact value by at most 2^-7 times the same sum over
+ * absolute values (two BF16 roundings per product) plus the FP32
+ * accumulation error. The weight gradient splits the pixels over CTAs and
+ * adds the partial sums in a fixed order (deterministic). Same shapes and
+ * layouts as above; the backward needs Co <= 128 (DG_EUNSUPPORTED
+ * otherwise). Both take scratch: dg_nn_conv3x3_tc_scratch floats (device,
+ * 16-byte aligned; -1: shape out of range; with Co > 128 the forward's
+ * need only), which hold the weights
+ * converted to BF16 blocks (and the backward's partial sums); one scratch
+ * must not serve two calls in flight at once. dg_nn_tc_check synchronises
+ * the stream and returns DG_ETIMEOUT (clearing it) if a wait of one of
+ * these kernels ran out since the last check (their outputs are then
+ * invalid). */
 dg_status dg_nn_conv3x3_forward_tc(const float *x, const float *w, const float *b, float *y, int32_t B,
-                                   int32_t Ci, int32_t Co, int32_t H, int32_t W, void *stream);
+                                   int32_t Ci, int32_t Co, int32_t H, int32_t W, float *scratch,
+                                   void *stream);
 int64_t dg_nn_conv3x3_tc_scratch(int32_t B, int32_t Ci, int32_t Co, int32_t H, int32_t W);
 dg_status dg_nn_conv3x3_backward_tc(const float *x, const float *w, const float *dy, float *dx, float *dw,
                                     float *db, int32_t B, int32_t Ci, int32_t Co, int32_t H, int32_t W,

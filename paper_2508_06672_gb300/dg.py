@@ -217,7 +217,7 @@ def lib():
             L.dg_nn_conv3x3_backward.argtypes = [vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, i32, vp, vp]
             L.dg_nn_conv3x3_scratch.argtypes = [i32, i32, i32, i32, i32]
             L.dg_nn_conv3x3_scratch.restype = i64
-            L.dg_nn_conv3x3_forward_tc.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, i32, vp]
+            L.dg_nn_conv3x3_forward_tc.argtypes = [vp, vp, vp, vp, i32, i32, i32, i32, i32, vp, vp]
             L.dg_nn_conv3x3_backward_tc.argtypes = [vp, vp, vp, vp, vp, vp, i32, i32, i32, i32, i32, vp, vp]
             L.dg_nn_conv3x3_tc_scratch.argtypes = [i32, i32, i32, i32, i32]
             L.dg_nn_conv3x3_tc_scratch.restype = i64
@@ -488,15 +488,23 @@ def dg_nn_conv3x3_backward(x, w, dy, dx, dw, db, scratch=None, stream=None):
                                            B, Ci, Co, H, W, _ptr(scratch), _stream(stream, x)))
 
 
-def dg_nn_conv3x3_forward_tc(x, w, b, y, stream=None):
-    """dg_nn_conv3x3_forward on the tensor cores: BF16 operands, FP32 sums."""
-    _f32(x, w, b, y)
+def dg_nn_conv3x3_forward_tc(x, w, b, y, scratch=None, stream=None):
+    """dg_nn_conv3x3_forward on the tensor cores: BF16 operands, FP32 sums;
+    scratch: dg_nn_conv3x3_tc_scratch floats (allocated here when None)."""
+    import torch
     B, Ci, H, W = x.shape
     Co = w.shape[0]
-    if tuple(w.shape) != (Co, Ci, 3, 3) or tuple(b.shape) != (Co,) or tuple(y.shape) != (B, Co, H, W):
+    need = int(lib().dg_nn_conv3x3_tc_scratch(B, Ci, Co, H, W))
+    if need < 0:
+        raise ValueError("dg_nn_conv3x3_forward_tc: shape out of range")
+    if scratch is None:
+        scratch = torch.empty(max(1, need), dtype=torch.float32, device=x.device)
+    _f32(x, w, b, y, scratch)
+    if (tuple(w.shape) != (Co, Ci, 3, 3) or tuple(b.shape) != (Co,) or tuple(y.shape) != (B, Co, H, W)
+            or scratch.numel() < need):
         raise ValueError("dg_nn_conv3x3_forward_tc: shape mismatch")
     _nn_check(lib().dg_nn_conv3x3_forward_tc(_ptr(x), _ptr(w), _ptr(b), _ptr(y), B, Ci, Co, H, W,
-                                             _stream(stream, x)))
+                                             _ptr(scratch), _stream(stream, x)))
 
 
 def dg_nn_conv3x3_backward_tc(x, w, dy, dx, dw, db, scratch=None, stream=None):

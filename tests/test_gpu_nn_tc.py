@@ -100,11 +100,11 @@ def test_conv_tc_backward_is_deterministic_and_rejects_wide_outputs():
         P.dg_nn_conv3x3_backward_tc(x, w, dy, None, dw, db)
         outs.append((dw.clone(), db.clone()))
     assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
-    # more than 128 output channels: the scratch query says out of range and
-    # the C entry point refuses with DG_EUNSUPPORTED
+    # more than 128 output channels: the scratch query gives the forward's
+    # need only, and the backward's C entry point refuses with DG_EUNSUPPORTED
     import ctypes as C
 
-    assert P.lib().dg_nn_conv3x3_tc_scratch(B, Ci, 130, H, W) == -1
+    assert 0 < P.lib().dg_nn_conv3x3_tc_scratch(B, Ci, 130, H, W) < P.lib().dg_nn_conv3x3_tc_scratch(B, Ci, 128, H, W)
     wide = _dev(rng.standard_normal((130, Ci, 3, 3)))
     dyw = _dev(rng.standard_normal((B, 130, H, W)))
     dww, dbw, scr = torch.empty((130, Ci, 3, 3), device="cuda"), torch.empty(130, device="cuda"), torch.empty(16, device="cuda")
