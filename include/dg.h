@@ -396,7 +396,7 @@ dg_status dg_kernel_time(dg_ctx *ctx, int32_t kernel_class, double *ms, int64_t 
  * summed over snapshots: lag-bucket x chunk pairs contracted (each a
  * chunk-by-bins complex DFT) and candidate x super-chunk pairs combined (the
  * combine merges chunks at the bin frequencies into the longest power-of-two
- * multiple of the chunk whose length x bin spacing stays <= 4e-2 cycles).
+ * multiple of the chunk whose length x bin spacing stays <= 5e-2 cycles).
  * Host pointers, may be NULL; zeros before the first CDFT surface. */
 dg_status dg_cdft_work(const dg_ctx *ctx, int64_t *bucket_chunks, int64_t *candidate_chunks);
 

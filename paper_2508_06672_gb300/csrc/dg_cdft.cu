@@ -326,19 +326,76 @@ __global__ void __launch_bounds__(1024) k_cdft_scan(CdftBatch a)
 // scatter: counting sort by lag bucket (the offsets come from the scan). A CTA
 // takes the hist kernel's 64 x 64 tile of one snapshot. Its candidates are
 // ranked per lag in shared memory (one atomic per run of equal lags in a
-// warp, as in hist), one global atomic per (tile, lag)
-// reserves a contiguous range of the bucket, and each candidate takes its
-// rank within that range: the candidates of one tile and lag sit together,
-// which keeps the combine's surface writes close. Tiles whose lag span
-// exceeds kHistBins take one global atomic per (warp, run) instead.
+// warp, as in hist) and one global atomic per (tile, lag) reserves a
+// contiguous range of the bucket: the candidates of one tile and lag sit
+// together, which keeps the combine's surface writes close. The tile is
+// then put in lag order in shared memory (local offsets from a prefix sum of
+// the per-lag counts), so that consecutive threads write consecutive
+// positions of each range: where a grid step moves the lag by a sample or
+// more, nearly every lane of a warp has a lag of its own and writing in grid
+// order would touch a cache line per lane. Tiles with longer runs of equal
+// lags write in grid order (their writes are grouped already, and the
+// reordering's barriers cost more than it gains), and so do tiles whose lag
+// span exceeds kHistBins, with one global atomic per (warp, run).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_cdft_scatter(CdftBatch a)
+constexpr int kTileN = kHistTile * kHistTile;
+
+// Dynamic shared memory of k_cdft_scatter: per-lag counts (then local
+// offsets) and range bases, then per lag-ordered position the packed
+// (lag index, tile entry), the FDOA and, with LAGRANGE4, the fractional delay.
+size_t scatter_smem_bytes(bool frac)
 {
-    __shared__ int s_cnt[kHistBins], s_base[kHistBins];
-    __shared__ int s_min, s_max;
+    return sizeof(int) * (2 * (size_t)kHistBins + (frac ? 3 : 2) * (size_t)kTileN);
+}
+
+// In-place exclusive prefix sum of v[0, n), n <= 8 * blockDim.x (256
+// threads); returns the total. Every thread of the CTA calls it.
+__device__ __forceinline__ int block_exclusive_scan(int *v, int n, int *s_warp)
+{
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int i0 = 8 * t;
+    int x[8], sum = 0;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        x[e] = i0 + e < n ? v[i0 + e] : 0;
+        sum += x[e];
+    }
+    int inc = sum;  // inclusive scan of the threads' sums within the warp
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        const int ws = s_warp[w];
+        if (w < warp) before += ws;
+        total += ws;
+    }
+    int run = before + inc - sum;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        if (i0 + e < n) v[i0 + e] = run;
+        run += x[e];
+    }
+    __syncthreads();
+    return total;
+}
+
+__global__ void __launch_bounds__(256, 3) k_cdft_scatter(CdftBatch a)
+{
+    extern __shared__ __align__(16) int s_dyn[];
+    int *s_cnt = s_dyn, *s_base = s_dyn + kHistBins;
+    int *s_key = s_dyn + 2 * kHistBins;  // (lag index << 12) | tile entry
+    float *s_nu = reinterpret_cast<float *>(s_key + kTileN);
+    float *s_mu = s_nu + kTileN;  // LAGRANGE4 only
+    __shared__ int s_min, s_max, s_warp[8], s_runs, s_valid;
     const int s = blockIdx.y;
     const int lmin = a.lr[2 * s], bb = a.bbase[s];
     if (a.lr[2 * s + 1] - lmin >= a.bbase[s + 1] - bb) return;  // reported by k_cdft_hist
+    const bool frac = a.delay != DG_DELAY_INTEGER;
     int l[kTilePer];
     load_lag_tile(a, s, l, s_min, s_max);
     if (s_max < s_min) return;  // no node with a representable lag (uniform)
@@ -346,9 +403,10 @@ __global__ void __launch_bounds__(256) k_cdft_scatter(CdftBatch a)
     const bool local = (int64_t)s_max - s_min < kHistBins;
     const int span = local ? s_max - s_min + 1 : 0;
     for (int i = threadIdx.x; i < span; i += blockDim.x) s_cnt[i] = 0;
+    if (threadIdx.x == 0) s_runs = s_valid = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    int rank[kTilePer];
+    int rank[kTilePer], runs = 0, valid = 0;
 #pragma unroll
     for (int k = 0; k < kTilePer; ++k) {
         // one atomic per run of equal lags in the warp; the run's lanes take
@@ -360,36 +418,78 @@ __global__ void __launch_bounds__(256) k_cdft_scatter(CdftBatch a)
             base = local ? atomicAdd(s_cnt + (l[k] - tlo), run_len(heads, lane))
                          : atomicAdd(a.subcnt + bb + l[k] - lmin, run_len(heads, lane));
         rank[k] = __shfl_sync(0xffffffffu, base, head) + (lane - head);
+        runs += __popc(heads);
+        valid += __popc(__ballot_sync(0xffffffffu, l[k] != INT_MIN));
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < span; i += blockDim.x) {
-        const int n = s_cnt[i];
-        s_base[i] = n ? atomicAdd(a.subcnt + bb + tlo + i - lmin, n) : 0;
+    if (lane == 0) {
+        atomicAdd(&s_runs, runs);
+        atomicAdd(&s_valid, valid);
     }
-    __syncthreads();
-    // every load before the first store: the stores may alias the loads as
-    // far as the compiler knows, so mixing them would serialise 16 round trips
     const size_t so = (size_t)s * a.G;
-    float nu[kTilePer];
+    __syncthreads();
+    // lag order pays where runs are short (a mean under 4 lanes: measured,
+    // it gains on a grid whose step moves the lag by 1-1.5 samples and loses
+    // where the step moves it by 0.2); with longer runs the grid-order
+    // writes are already grouped
+    const bool lag_order = local && s_valid < 4 * s_runs;
+    if (local) {
+        // the global range of each (tile, lag)
+        for (int i = threadIdx.x; i < span; i += blockDim.x) {
+            const int n = s_cnt[i];
+            s_base[i] = n ? atomicAdd(a.subcnt + bb + tlo + i - lmin, n) : 0;
+        }
+        if (!lag_order) __syncthreads();
+    }
+    if (!lag_order) {
+        // grid order: every load before the first store (the stores may
+        // alias the loads as far as the compiler knows)
+        float nu[kTilePer];
+#pragma unroll
+        for (int k = 0; k < kTilePer; ++k) {
+            if (l[k] == INT_MIN) continue;
+            rank[k] += a.offs[bb + l[k] - lmin] + (local ? s_base[l[k] - tlo] : 0);
+            nu[k] = a.candNu[so + tile_node(a, k)];
+        }
+#pragma unroll
+        for (int k = 0; k < kTilePer; ++k) {
+            if (l[k] == INT_MIN) continue;
+            a.order[so + rank[k]] = (int)tile_node(a, k);
+            a.nuS[so + rank[k]] = nu[k];
+        }
+        if (frac) {
+#pragma unroll
+            for (int k = 0; k < kTilePer; ++k)
+                if (l[k] != INT_MIN) nu[k] = a.candMu[so + tile_node(a, k)];
+#pragma unroll
+            for (int k = 0; k < kTilePer; ++k)
+                if (l[k] != INT_MIN) a.muS[so + rank[k]] = nu[k];
+        }
+        return;
+    }
+    // local offsets of the lags in the tile's lag order
+    const int total = block_exclusive_scan(s_cnt, span, s_warp);
+    // position p of lag index i goes to s_base[i] + p
+    for (int i = threadIdx.x; i < span; i += blockDim.x)
+        s_base[i] += a.offs[bb + tlo + i - lmin] - s_cnt[i];
+    // lag order in shared memory (the FDOA loads stay coalesced, in grid order)
 #pragma unroll
     for (int k = 0; k < kTilePer; ++k) {
         if (l[k] == INT_MIN) continue;
-        rank[k] += a.offs[bb + l[k] - lmin] + (local ? s_base[l[k] - tlo] : 0);
-        nu[k] = a.candNu[so + tile_node(a, k)];
+        const int li = l[k] - tlo, pos = s_cnt[li] + rank[k];
+        const int64_t node = tile_node(a, k);
+        s_key[pos] = (li << 12) | (int)(threadIdx.x + 256 * k);
+        s_nu[pos] = a.candNu[so + node];
+        if (frac) s_mu[pos] = a.candMu[so + node];
     }
-#pragma unroll
-    for (int k = 0; k < kTilePer; ++k) {
-        if (l[k] == INT_MIN) continue;
-        a.order[so + rank[k]] = (int)tile_node(a, k);
-        a.nuS[so + rank[k]] = nu[k];
-    }
-    if (a.delay != DG_DELAY_INTEGER) {  // the fractional delays in the same order
-#pragma unroll
-        for (int k = 0; k < kTilePer; ++k)
-            if (l[k] != INT_MIN) nu[k] = a.candMu[so + tile_node(a, k)];
-#pragma unroll
-        for (int k = 0; k < kTilePer; ++k)
-            if (l[k] != INT_MIN) a.muS[so + rank[k]] = nu[k];
+    __syncthreads();
+    const int tiles_j = (a.nlon + kHistTile - 1) / kHistTile;
+    const int64_t r0 = (int64_t)(blockIdx.x / tiles_j) * kHistTile, c0 = (int64_t)(blockIdx.x % tiles_j) * kHistTile;
+    for (int p = threadIdx.x; p < total; p += blockDim.x) {
+        const int key = s_key[p], e = key & (kTileN - 1);
+        const int64_t dst = so + s_base[key >> 12] + p;
+        a.order[dst] = (int)((r0 + e / kHistTile) * a.nlon + c0 + e % kHistTile);
+        a.nuS[dst] = s_nu[p];
+        if (frac) a.muS[dst] = s_mu[p];
     }
 }
 
@@ -798,7 +898,13 @@ cudaError_t launch_cdft_plan(const CdftBatch &a, int NBT, cudaStream_t st)
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_cdft_scan<<<a.S, 1024, 0, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_cdft_scatter<<<gh, 256, 0, st>>>(a);
+    {
+        const size_t sm = scatter_smem_bytes(a.delay != DG_DELAY_INTEGER);
+        if ((e = cudaFuncSetAttribute(k_cdft_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
+            cudaSuccess)
+            return e;
+        k_cdft_scatter<<<gh, 256, sm, st>>>(a);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (a.mma) return cudaSuccess;  // the FP32 table serves the CUDA-core contraction only
     dim3 gv(grid_for((int64_t)a.M * 64, 256, 64), (unsigned)a.S);
