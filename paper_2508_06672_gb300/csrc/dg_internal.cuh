@@ -327,9 +327,11 @@ cudaError_t launch_accumulate(const void *surf, int K, int64_t G, int prec, void
 // gbase[s+1]-1 (an upper bound; surplus CTAs exit).
 // ---------------------------------------------------------------------------
 constexpr int kCdftCombineThreads = 128;
-// candidates per combine thread; a group of 256 candidates per CTA measured best
-// on mid (128 x 2 or 64 x 4: 0.30 ms; 256 x 4: 0.35; 256 x 8: 0.49; 512 x 2: 0.40)
-constexpr int kCdftCombinePer = 2;
+// candidates per combine thread. Threads x candidates per CTA, combine ms per
+// step on the large workload (4001^2, K = 50, 8 super-chunks per candidate) /
+// on mid: 128 x 3: 12.03 / 0.237; 128 x 2: 12.62 / 0.239; 128 x 4: 12.28 /
+// 0.241; 64 x 8: 13.12 / 0.253 (earlier, on mid: 256 x 4 and 512 x 2 slower)
+constexpr int kCdftCombinePer = 3;
 constexpr int kCdftCombineGroup = kCdftCombineThreads * kCdftCombinePer;  // candidates per combine CTA
 
 struct CdftBatch {

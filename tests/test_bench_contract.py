@@ -110,3 +110,19 @@ def test_reference_arm_under_torchrun_prints_on_rank_0_only():
     # torchrun sets OMP_NUM_THREADS=1; the line reports every core of the process's affinity, and
     # the oracle is given that many threads explicitly
     assert d["cpu_baseline"]["cores"] == len(os.sched_getaffinity(0))
+
+
+def test_roofline_counts_the_contractions_own_launches():
+    """Each batch of snapshots on the tensor-core path launches its DFT-operand
+    table kernel and then the contraction, both timed in the contraction's
+    class: the roofline's launches are the contraction's, half of them."""
+    import types
+
+    b = _bench()
+    cdft = types.SimpleNamespace(algo="cdft", contract="fp16x3", tiles="auto")
+    f = b.launch_fields(cdft, "contract", 6, 0.06)
+    assert f["launches"] == 3 and abs(f["ms_per_launch"] - 20.0) < 1e-9 and "launches_basis" in f
+    for a, dom in ((types.SimpleNamespace(algo="cdft", contract="fp32", tiles="auto"), "contract"),
+                   (cdft, "combine"), (types.SimpleNamespace(algo="direct", contract="fp16x3", tiles="auto"), "corr")):
+        f = b.launch_fields(a, dom, 6, 0.06)
+        assert f["launches"] == 6 and "launches_basis" not in f
