@@ -1,8 +1,8 @@
 // dg_corr.cu -- direct position-domain correlation (Sec. III, Eq. 11).
 //
 // One CTA handles one tile of candidates (kWarps*R grid rows x 32 grid
-// columns) for one snapshot k; R, the grid rows per thread, is a launch
-// choice (dg_options.rows, tuned by dg_autotune). Per candidate it computes the geometry
+// columns) for one snapshot k; R, the candidates (grid rows) per thread, is a
+// launch choice (dg_options.rows, tuned by dg_autotune). Per candidate it computes the geometry
 // (Eq. 3-10, FP64), then
 //     C = sum_n y1[n] conj(y2~[n]) exp(j 2 pi nu n),
 // y2~[n] = y2[n + L] (Eq. 9) or its 4-tap Lagrange interpolation at n + D,
@@ -107,7 +107,15 @@ __global__ void __launch_bounds__(kThreads) k_corr_direct(CorrArgs a, int tiles_
     const int k = blockIdx.y;
     const int ti = blockIdx.x / tiles_j, tj = blockIdx.x % tiles_j;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j = tj * 32 + lane;
+    // For each r the 32 lanes of a warp take a compact 4-row x 8-column patch
+    // (warp w: columns 8 (w % 4) .. + 7 of the tile, rows 4R (w / 4) .. + 4R - 1;
+    // lane: column lane % 8, row lane / 8, then 4 rows further per r). Their
+    // lags then differ by at most 10 grid steps' worth, not 31 as along one
+    // row, so the y2 window reads of a warp stay within a few banks' rows
+    // where a grid step moves the lag by a sample or more.
+    static_assert(kWarps == 8, "the lane mapping assumes 8 warps: 4 column blocks x 2 row blocks");
+    const int j = tj * 32 + (warp & 3) * 8 + (lane & 7);
+    const int row0 = ti * (kWarps * R) + (warp >> 2) * (4 * R) + (lane >> 3);
     const StepDesc sd = a.steps[k];
     const int N = sd.n;
     const int64_t G = a.G;
@@ -124,7 +132,7 @@ __global__ void __launch_bounds__(kThreads) k_corr_direct(CorrArgs a, int tiles_
     int lmin = INT_MAX, lmax = INT_MIN;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int i = ti * (kWarps * R) + warp * R + r;
+        const int i = row0 + 4 * r;
         ok[r] = (i < a.nrows) && (j < a.nlon);
         off[r] = 0;
         c2[r] = (T)0;
@@ -259,7 +267,7 @@ __global__ void __launch_bounds__(kThreads) k_corr_direct(CorrArgs a, int tiles_
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         if (!ok[r]) continue;
-        const int i = ti * (kWarps * R) + warp * R + r;
+        const int i = row0 + 4 * r;
         const int64_t p = (int64_t)i * a.nlon + j;
         double D, nu;
         geometry(a.xyz[p], a.xyz[G + p], a.xyz[2 * G + p], e, a.fs, a.lambda, D, nu);
@@ -309,7 +317,7 @@ static cudaError_t launch_one(const CorrArgs &a, cudaStream_t s)
 
 // Grid rows per thread: FP32 4, 8 or 16; FP64 2 or 4. The defaults are the
 // fastest measured on a 1001^2 grid (K = 50, N = 131072): FP32 8 with the
-// integer delay (4 and 16 within 2 %), 4 with LAGRANGE4 (6 % ahead of 8).
+// integer delay (4 and 16 within 1 %), 4 with LAGRANGE4 (5 % ahead of 8).
 template <typename T, int FMT, int DELAY>
 static cudaError_t launch_rows(const CorrArgs &a, cudaStream_t s)
 {
