@@ -938,12 +938,17 @@ def run_learned(a, rank, world, local_rank):
             "full_grid_ms": med_f, "speedup_vs_full_grid": med_f / med_l,
             "plain_full_grid": dict(plain, speedup_of_learned=plain["ms_extrapolated"] / med_l),
             "mean_ms": float(np.mean(learned_ms)), "full_grid_mean_ms": float(np.mean(full_ms)),
-            "fallback": {"rule": f"no region proposed, or the best region's argmax within {search.edge} nodes "
-                                 "of its border: the full-grid search runs on the same context",
+            "fallback": {"rule": f"no region proposed, the best region's argmax within {search.edge} nodes "
+                                 f"of its border, the best proposal's logit under {search.min_logit}, or the best "
+                                 f"region's maximum less than {search.min_region_gap} (relative) above the "
+                                 "runner-up's: the full-grid search runs on the same context",
                          "rate": float(np.mean(fell)), "count": int(sum(fell)),
                          "median_ms_when_taken": (float(np.median([t for t, f in zip(learned_ms, fell) if f]))
                                                   if any(fell) else None)},
             "recall": float(np.mean(rec)), "recall_coarse_sum_without_network": float(np.mean(rec_sum)),
+            "recall_with_fallback": float(np.mean([r or f for r, f in zip(rec, fell)])),
+            "recall_basis": ("recall: the full-grid argmax lies inside one of the proposed regions; "
+                             "recall_with_fallback: that, or the fallback ran the full-grid search"),
             "same_fix_as_full_grid": float(np.mean(same)),
             "error_m": {"learned_p50": float(np.median(err_l)), "learned_p90": float(np.percentile(err_l, 90)),
                         "full_grid_p50": float(np.median(err_f)), "full_grid_p90": float(np.percentile(err_f, 90))},

@@ -16,9 +16,12 @@ dense re-evaluation around the argmax) is replaced by:
    context that keeps the captures);
 5. the region whose argmax holds the largest cost gives the fix;
 6. the full-grid search on the same context is the fallback: it runs when
-   no region is proposed, or when the winning region's argmax lies within
+   no region is proposed, when the winning region's argmax lies within
    ``edge`` nodes of the region's border (the surface still rises towards
-   the border, so the maximum may lie outside every region).
+   the border, so the maximum may lie outside every region), or when the
+   search looks unsure: the best proposal's logit is below ``min_logit`` or
+   the best region's maximum exceeds the runner-up's by less than
+   ``min_region_gap`` of it.
 
 The method without the network ranks the cells by the sum of the K coarse
 maps instead (the non-coherent sum of Algorithm 1 applied to the coarse
@@ -92,7 +95,7 @@ class LearnedSearch:
 
     def __init__(self, grid, ephem, fs_hz, fc_hz, net, *, cells=512, regions=8, region_m=50e3,
                  refine_spacing_m=25.0, refine_window_m=500.0, bins=0, chunk=0, algo="cdft",
-                 contract="bf16x3", stream=None, edge=2):
+                 contract="bf16x3", stream=None, edge=2, min_logit=3.6, min_region_gap=0.2):
         import torch
         self.torch = torch
         self.grid = dict(grid)
@@ -114,6 +117,15 @@ class LearnedSearch:
         self.cost = None
         self.full_cost = None
         self.edge = int(edge)
+        # Unsure-search thresholds of the fallback. The defaults are the 2nd
+        # percentiles, over the shipped network's successful searches on the
+        # training script's 200 held-out scenes (seeds 5, 100005...), of the
+        # best proposal's logit (3.6) and of the relative margin of the best
+        # region's maximum over the runner-up's (0.2): about 4 % of searches
+        # fall back. They belong to those weights (the logit scale is the
+        # network's); None switches a criterion off.
+        self.min_logit = min_logit
+        self.min_region_gap = min_region_gap
         self.searches = 0     # search() calls, and how many of them fell back to the full grid
         self.fallbacks = 0
         self.fell_back = False
@@ -162,6 +174,19 @@ class LearnedSearch:
         n = 2 * self.half + 1
         return min(fix["i"], fix["j"], n - 1 - fix["i"], n - 1 - fix["j"]) < self.edge
 
+    def unsure(self, peaks, costs):
+        """True when the proposals do not single out a region: the best
+        proposal's logit is under ``min_logit``, or the best region's
+        maximum cost exceeds the runner-up's by less than ``min_region_gap``
+        of it. ``costs``: the regions' cost surfaces (device)."""
+        if self.min_logit is not None and max(p["value"] for p in peaks) < self.min_logit:
+            return True
+        if self.min_region_gap is not None and len(peaks) > 1:
+            with self.torch.cuda.stream(self.geo.stream):
+                top = self.torch.topk(costs.flatten(1).amax(1), 2).values.tolist()
+            return top[0] - top[1] < self.min_region_gap * top[0]
+        return False
+
     def full_search(self):
         """The full-grid search (Algorithm 1 on every node, then the same
         dense re-evaluation) on the same context and captures."""
@@ -185,8 +210,8 @@ class LearnedSearch:
             if self.cost is None:
                 self.cost = self.torch.empty((self.regions, n, n), dtype=self.torch.float32, device=self.geo.device)
             regions = [self.region_grid(p["lat_deg"], p["lon_deg"]) for p in peaks]
-            fix, best, _ = self.geo.search_regions(regions, *self.refine, costs=self.cost)
-            if not fallback or not self.doubtful(fix):
+            fix, best, costs = self.geo.search_regions(regions, *self.refine, costs=self.cost)
+            if not fallback or not (self.doubtful(fix) or self.unsure(peaks, costs[:len(regions)])):
                 return fix, best, peaks
         elif not fallback:
             return None, -1, peaks

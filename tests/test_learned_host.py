@@ -89,3 +89,28 @@ def test_target_map_and_crops_keep_the_emitter():
         assert np.array_equal(tk, full[i0:i0 + 64, j0:j0 + 64])
         if k < 2:  # the crops around the emitter hold its cell
             assert 0 <= ci - i0 < 64 and 0 <= cj - j0 < 64 and tk[ci - i0, cj - j0] == 1.0
+
+
+def test_unsure_search_criteria():
+    """The fallback's unsure-search rule: the best proposal's logit under
+    min_logit, or the best region's maximum less than min_region_gap
+    (relative) above the runner-up's; either criterion can be switched off."""
+    import types
+
+    import torch
+
+    from paper_2508_06672_gb300.learned import LearnedSearch
+
+    s = types.SimpleNamespace(torch=torch, min_logit=3.6, min_region_gap=0.2,
+                              geo=types.SimpleNamespace(stream=None))
+    costs = torch.zeros((3, 5, 5))
+    costs[0, 2, 2], costs[1, 1, 1], costs[2, 3, 3] = 10.0, 7.0, 1.0
+    peaks = [{"value": 5.0}, {"value": 4.0}, {"value": 1.0}]
+    assert not LearnedSearch.unsure(s, peaks, costs)            # margin 0.3, logit 5
+    costs[1, 1, 1] = 8.5
+    assert LearnedSearch.unsure(s, peaks, costs)                # margin 0.15 < 0.2
+    s.min_region_gap = None
+    assert not LearnedSearch.unsure(s, peaks, costs)
+    assert LearnedSearch.unsure(s, [{"value": 3.5}, {"value": 2.0}], costs[:2])  # logit 3.5 < 3.6
+    s.min_logit = None
+    assert not LearnedSearch.unsure(s, [{"value": 3.5}], costs[:1])
